@@ -1,0 +1,468 @@
+/*
+ * CPU oracle for proton-CT hull detection (SC, MSC, SM).
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is the plain, slow, obviously correct
+ * statement of what the hull-detection path computes.  Only the test suite,
+ * the smoke check and the benchmark's CPU-baseline arm may load it.  It shares
+ * no code, header, table or constant generator with the CUDA library.
+ *
+ * What is computed, and where it comes from:
+ *   - Classification of a history as missed (WEPL below a cutoff) or hit
+ *     (WEPL above a cutoff): Eq. 3.1 and Eq. 3.7, with the paper's cutoffs
+ *     1.0 mm and 5.0 mm on individual WEPL values and no angular cutoff
+ *     (Sec. 3.2 last paragraph, Sec. 3.3 last paragraph, Sec. 3.4 last
+ *     paragraph).
+ *   - The path L_i is the straight segment joining the entry and exit points
+ *     (Sec. 2.1 and the definition of L_i before Eq. 3.2).  The voxel set
+ *     A_i = {v : d(L_i, v) <= d_0} (Eq. 3.2) is read with d_0 = 0 against the
+ *     half-open voxel cube: A_i is the set of voxels whose cube
+ *     [k, k+1)^3 (in voxel units) contains a point of the closed segment.
+ *     This matches the 0/1 system-matrix rows of "intersected voxels"
+ *     (Sec. 2.1).  Geometry is made exact by one rounding of the float32
+ *     inputs to 16 fractional bits, an integer CORDIC for the gantry
+ *     rotation, and integer floor divisions; after that every step is exact.
+ *   - N(v) = |C(v)| over missed histories (Eq. 3.4), M(v) = |C(v)| over hit
+ *     histories (Eq. 3.9), H_1 = V minus the union of A_i (Eq. 3.3, Alg. 1),
+ *     H_2 by the neighbour-difference threshold N_t (Eq. 3.5, Eq. 3.6,
+ *     Alg. 2), H_3 by the steepest-edge threshold M_t (Eq. 3.10, Alg. 3,
+ *     made per slice as Sec. 3.4 describes).
+ *
+ * The voxel set is enumerated from its definition: the voxel function
+ * floor(P(t)) of the segment P(t) = G_in + t (G_out - G_in), t in [0, 1], is
+ * constant between consecutive parameters at which some coordinate crosses a
+ * grid plane, so the set is the voxels at those parameters and at the
+ * midpoints between them.  All parameters are exact rationals.  A second,
+ * independent statement (the per-voxel slab test) checks it on small grids.
+ */
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#include <math.h>
+
+typedef __int128 i128;
+
+#define Q16 65536LL
+
+/* ------------------------------------------------------------ quantisation */
+
+/* Round a float32 to 16 fractional bits, ties to even.  The float32 -> double
+ * conversion and the multiplication by 2^16 are exact, so the only rounding
+ * is the final one. */
+static int64_t q16_of(float x) { return (int64_t)llrint((double)x * 65536.0); }
+
+static int64_t floordiv(int64_t a, int64_t b) /* b > 0 */
+{
+    int64_t q = a / b;
+    if ((a % b) != 0 && a < 0) q -= 1;
+    return q;
+}
+
+static i128 floordiv128(i128 a, i128 b) /* b > 0 */
+{
+    i128 q = a / b;
+    if ((a % b) != 0 && a < 0) q -= 1;
+    return q;
+}
+
+/* ----------------------------------------------------------------- CORDIC */
+
+/* Rotation-mode CORDIC (Volder 1959) of the angle a (degrees, 16 fractional
+ * bits).  theta[i] = round(atan(2^-i) * 180/pi * 2^30) and
+ * K = round(2^30 * prod_i (1 + 2^-2i)^(-1/2)) are supplied by the caller.
+ * Returns cos and sin with 30 fractional bits. */
+void oracle_cordic(int64_t a_q16, const int64_t *theta, int64_t K,
+                   int64_t *cos_q30, int64_t *sin_q30)
+{
+    const int64_t full = 360LL * Q16, quarter = 90LL * Q16;
+    int64_t a = a_q16 % full;
+    if (a < 0) a += full;
+    int64_t k = a / quarter;
+    int64_t r = a - k * quarter;
+    int64_t z = r << 14; /* degrees, 30 fractional bits */
+    int64_t x = K, y = 0;
+    for (int i = 0; i < 32; ++i) {
+        int64_t xs = x >> i, ys = y >> i; /* arithmetic shifts: floor */
+        if (z >= 0) {
+            x = x - ys;
+            y = y + xs;
+            z = z - theta[i];
+        } else {
+            x = x + ys;
+            y = y - xs;
+            z = z + theta[i];
+        }
+    }
+    int64_t c, s;
+    switch (k) {
+    case 0: c = x; s = y; break;
+    case 1: c = -y; s = x; break;
+    case 2: c = -x; s = -y; break;
+    default: c = y; s = -x; break;
+    }
+    *cos_q30 = c;
+    *sin_q30 = s;
+}
+
+/* ---------------------------------------------------------------- geometry */
+
+typedef struct {
+    int32_t nx, ny, nz;
+    float sx, sy, sz;
+    float T; /* tracker half-separation, mm */
+} og_geom;
+
+/* Grid coordinate (voxel units, 16 fractional bits) of a world coordinate w
+ * (mm, 16 fractional bits) on an axis with n voxels of size s_q (mm, Q16),
+ * the grid centred on the origin:  (w + n s / 2) / s. */
+static int64_t to_grid(int64_t w, int32_t n, int64_t s_q)
+{
+    return floordiv((2 * w + (int64_t)n * s_q) * Q16, 2 * s_q);
+}
+
+/* Entry and exit points of one history in grid Q16.  Returns 0 when the
+ * history is usable and 1 when it is rejected (a non-finite or out-of-range
+ * coordinate: |u|, |v| >= 4096 mm, |angle| >= 2^20 degrees, or a grid
+ * coordinate of magnitude >= 2^30). */
+int oracle_grid_endpoints(const og_geom *g, const int64_t *theta, int64_t K,
+                          float angle, float u_in, float v_in, float u_out,
+                          float v_out, int64_t *gin, int64_t *gout)
+{
+    if (!(fabsf(angle) < 1048576.0f)) return 1;
+    if (!(fabsf(u_in) < 4096.0f) || !(fabsf(v_in) < 4096.0f) ||
+        !(fabsf(u_out) < 4096.0f) || !(fabsf(v_out) < 4096.0f))
+        return 1;
+    int64_t c, s;
+    oracle_cordic(q16_of(angle), theta, K, &c, &s);
+    int64_t T = q16_of(g->T);
+    int64_t ui = q16_of(u_in), vi = q16_of(v_in);
+    int64_t uo = q16_of(u_out), vo = q16_of(v_out);
+    /* world point = -/+ T b + u e_u + v e_v, b = (c, s, 0), e_u = (-s, c, 0) */
+    int64_t wx_in = (-T * c - ui * s) >> 30;
+    int64_t wy_in = (-T * s + ui * c) >> 30;
+    int64_t wx_out = (T * c - uo * s) >> 30;
+    int64_t wy_out = (T * s + uo * c) >> 30;
+    int64_t sx = q16_of(g->sx), sy = q16_of(g->sy), sz = q16_of(g->sz);
+    gin[0] = to_grid(wx_in, g->nx, sx);
+    gin[1] = to_grid(wy_in, g->ny, sy);
+    gin[2] = to_grid(vi, g->nz, sz);
+    gout[0] = to_grid(wx_out, g->nx, sx);
+    gout[1] = to_grid(wy_out, g->ny, sy);
+    gout[2] = to_grid(vo, g->nz, sz);
+    const int64_t lim = (int64_t)1 << 30;
+    for (int a = 0; a < 3; ++a)
+        if (gin[a] >= lim || gin[a] <= -lim || gout[a] >= lim || gout[a] <= -lim) return 1;
+    return 0;
+}
+
+/* ----------------------------------------------------- voxel set (Eq. 3.2) */
+
+typedef struct { i128 p, q; } rat; /* p / q with q > 0 */
+
+static int rat_cmp(const void *a, const void *b)
+{
+    const rat *x = (const rat *)a, *y = (const rat *)b;
+    i128 l = x->p * y->q, r = y->p * x->q;
+    return (l < r) ? -1 : (l > r) ? 1 : 0;
+}
+
+static int cmp_i64(const void *a, const void *b)
+{
+    int64_t x = *(const int64_t *)a, y = *(const int64_t *)b;
+    return (x < y) ? -1 : (x > y) ? 1 : 0;
+}
+
+/* Linear index of floor(P(t)) for t = p/q, or -1 when outside the grid. */
+static int64_t voxel_at(const int64_t *gin, const int64_t *d, const int32_t *n, i128 p, i128 q)
+{
+    int64_t idx[3];
+    for (int a = 0; a < 3; ++a) {
+        i128 num = (i128)gin[a] * q + p * (i128)d[a];
+        i128 k = floordiv128(num, q * (i128)Q16);
+        if (k < 0 || k >= n[a]) return -1;
+        idx[a] = (int64_t)k;
+    }
+    return idx[0] + (int64_t)n[0] * (idx[1] + (int64_t)n[1] * idx[2]);
+}
+
+/* The voxel set A_i of the closed segment gin -> gout (grid Q16) as sorted
+ * unique linear indices (x fastest).  Writes at most `cap` indices and
+ * returns the set's size, or -1 on allocation failure. */
+int64_t oracle_voxel_set(const int64_t *gin, const int64_t *gout, int32_t nx, int32_t ny,
+                         int32_t nz, int64_t *out, int64_t cap)
+{
+    const int32_t n[3] = {nx, ny, nz};
+    int64_t d[3];
+    int64_t maxbp = 2;
+    for (int a = 0; a < 3; ++a) {
+        d[a] = gout[a] - gin[a];
+        maxbp += (int64_t)n[a] + 1;
+    }
+    rat *bp = (rat *)malloc(sizeof(rat) * (size_t)maxbp);
+    int64_t *cand = (int64_t *)malloc(sizeof(int64_t) * (size_t)(2 * maxbp + 1));
+    if (!bp || !cand) {
+        free(bp);
+        free(cand);
+        return -1;
+    }
+    int64_t nb = 0;
+    bp[nb].p = 0; bp[nb].q = 1; ++nb;
+    bp[nb].p = 1; bp[nb].q = 1; ++nb;
+    /* parameters at which coordinate a sits on grid plane k (0 <= k <= n_a) */
+    for (int a = 0; a < 3; ++a) {
+        if (d[a] == 0) continue;
+        for (int64_t k = 0; k <= n[a]; ++k) {
+            i128 p = (i128)(k * Q16 - gin[a]);
+            i128 q = (i128)d[a];
+            if (q < 0) { p = -p; q = -q; }
+            if (p < 0 || p > q) continue; /* outside [0, 1] */
+            bp[nb].p = p; bp[nb].q = q; ++nb;
+        }
+    }
+    qsort(bp, (size_t)nb, sizeof(rat), rat_cmp);
+    int64_t nc = 0;
+    for (int64_t j = 0; j < nb; ++j) {
+        int64_t v = voxel_at(gin, d, n, bp[j].p, bp[j].q);
+        if (v >= 0) cand[nc++] = v;
+        if (j + 1 < nb && rat_cmp(&bp[j], &bp[j + 1]) != 0) {
+            /* midpoint of (bp[j], bp[j+1]) */
+            i128 p = bp[j].p * bp[j + 1].q + bp[j + 1].p * bp[j].q;
+            i128 q = 2 * bp[j].q * bp[j + 1].q;
+            v = voxel_at(gin, d, n, p, q);
+            if (v >= 0) cand[nc++] = v;
+        }
+    }
+    qsort(cand, (size_t)nc, sizeof(int64_t), cmp_i64);
+    int64_t m = 0;
+    for (int64_t j = 0; j < nc; ++j) {
+        if (j > 0 && cand[j] == cand[j - 1]) continue;
+        if (m < cap) out[m] = cand[j];
+        ++m;
+    }
+    free(bp);
+    free(cand);
+    return m;
+}
+
+/* Independent statement of the same membership: does the closed segment
+ * gin -> gout meet the half-open cube of voxel (x, y, z)?  Per axis the
+ * parameters with k <= P_a(t) / 2^16 < k + 1 form an interval whose open and
+ * closed ends depend on the direction of travel; the voxel is a member when
+ * the intersection of the three intervals with [0, 1] is not empty. */
+int oracle_segment_meets_voxel(const int64_t *gin, const int64_t *gout, int64_t x, int64_t y,
+                               int64_t z)
+{
+    const int64_t v[3] = {x, y, z};
+    /* running lower bound lo (closed unless lo_open) and upper bound hi */
+    i128 lo_p = 0, lo_q = 1, hi_p = 1, hi_q = 1;
+    int lo_open = 0, hi_open = 0;
+    for (int a = 0; a < 3; ++a) {
+        int64_t d = gout[a] - gin[a];
+        int64_t lo_plane = v[a] * Q16, hi_plane = (v[a] + 1) * Q16;
+        if (d == 0) {
+            if (!(gin[a] >= lo_plane && gin[a] < hi_plane)) return 0;
+            continue;
+        }
+        i128 lp, lq, hp, hq;
+        int l_open, h_open;
+        if (d > 0) { /* lo_plane <= gin + t d  <=>  t >= (lo_plane - gin)/d, closed */
+            lp = lo_plane - gin[a]; lq = d; l_open = 0;
+            hp = hi_plane - gin[a]; hq = d; h_open = 1; /* strict upper */
+        } else {     /* decreasing coordinate */
+            lp = gin[a] - hi_plane; lq = -d; l_open = 1; /* gin + t d < hi  <=>  t > ... */
+            hp = gin[a] - lo_plane; hq = -d; h_open = 0; /* gin + t d >= lo  <=>  t <= ... */
+        }
+        /* lower = max(lower, (lp/lq)); open wins on equality */
+        i128 c = lp * lo_q - lo_p * lq;
+        if (c > 0 || (c == 0 && l_open)) { lo_p = lp; lo_q = lq; lo_open = l_open || (c == 0 && lo_open); }
+        c = hp * hi_q - hi_p * hq;
+        if (c < 0 || (c == 0 && h_open)) { hi_p = hp; hi_q = hq; hi_open = h_open || (c == 0 && hi_open); }
+    }
+    i128 c = lo_p * hi_q - hi_p * lo_q;
+    if (c < 0) return 1;
+    if (c == 0 && !lo_open && !hi_open) return 1;
+    return 0;
+}
+
+/* -------------------------------------------------- classification (3.1/3.7) */
+
+/* 1 = missed (WEPL < tau_l, Eq. 3.1), 2 = hit (WEPL > tau_h, Eq. 3.7),
+ * 0 = neither (including NaN).  Plain IEEE float32 comparisons. */
+int oracle_classify(float wepl, float tau_l, float tau_h)
+{
+    if (wepl < tau_l) return 1;
+    if (wepl > tau_h) return 2;
+    return 0;
+}
+
+/* ------------------------------------------------ accumulation (Alg. 1-3) */
+
+enum { OM_SC = 1, OM_MSC = 2, OM_SM = 4 };
+
+/* stats: [0] histories in, [1] missed, [2] hit, [3] neither,
+ *        [4] rejected (missed or hit, but unusable geometry),
+ *        [5] voxel memberships added from missed histories,
+ *        [6] voxel memberships added from hit histories.
+ * N counts missed histories per voxel (Eq. 3.4), M hit ones (Eq. 3.9),
+ * H1 starts at 1 and is carved to 0 along missed paths (Alg. 1).
+ * N, M and H1 may each be NULL when not wanted.  Returns 0, or -1 when out
+ * of memory. */
+int oracle_accumulate(const og_geom *g, float tau_l, float tau_h, int32_t methods,
+                      const int64_t *theta, int64_t K, const float *angle, const float *u_in,
+                      const float *v_in, const float *u_out, const float *v_out,
+                      const float *wepl, int64_t n, uint32_t *N, uint32_t *M, uint8_t *H1,
+                      int64_t *stats)
+{
+    int64_t cap = (int64_t)g->nx + g->ny + g->nz + 8;
+    int64_t *set = (int64_t *)malloc(sizeof(int64_t) * (size_t)cap);
+    if (!set) return -1;
+    int use_miss = (methods & (OM_SC | OM_MSC)) != 0;
+    int use_hit = (methods & OM_SM) != 0;
+    for (int64_t i = 0; i < n; ++i) {
+        stats[0] += 1;
+        int cls = oracle_classify(wepl[i], tau_l, tau_h);
+        if (cls == 1) stats[1] += 1;
+        else if (cls == 2) stats[2] += 1;
+        else stats[3] += 1;
+        if (!((cls == 1 && use_miss) || (cls == 2 && use_hit))) continue;
+        int64_t gin[3], gout[3];
+        if (oracle_grid_endpoints(g, theta, K, angle[i], u_in[i], v_in[i], u_out[i], v_out[i],
+                                  gin, gout)) {
+            stats[4] += 1;
+            continue;
+        }
+        int64_t m = oracle_voxel_set(gin, gout, g->nx, g->ny, g->nz, set, cap);
+        if (m < 0 || m > cap) {
+            free(set);
+            return -1;
+        }
+        for (int64_t j = 0; j < m; ++j) {
+            int64_t v = set[j];
+            if (cls == 1) {
+                if (N) N[v] += 1;
+                if (H1) H1[v] = 0;
+            } else {
+                if (M) M[v] += 1;
+            }
+        }
+        stats[cls == 1 ? 5 : 6] += m;
+    }
+    free(set);
+    return 0;
+}
+
+/* ------------------------------------------------------ decisions (3.3-3.10) */
+
+/* H_1 = V \ U A_i  (Eq. 3.3) from the count of missed paths through v. */
+void oracle_sc_from_counts(const uint32_t *N, int64_t V, uint8_t *H1)
+{
+    for (int64_t v = 0; v < V; ++v) H1[v] = (N[v] == 0) ? 1 : 0;
+}
+
+/* Neighbourhood B(v) = {w : d(v, w) <= 1} (Eq. 3.5) with d in voxel-index
+ * units: v itself and its face neighbours inside the grid; nbhd = 6 for all
+ * three axes, 4 for the in-plane ones only.  Writes up to 7 indices. */
+static int neighbours(int64_t x, int64_t y, int64_t z, int32_t nx, int32_t ny, int32_t nz,
+                      int nbhd, int64_t *w)
+{
+    int c = 0;
+    int64_t base = x + (int64_t)nx * (y + (int64_t)ny * z);
+    w[c++] = base;
+    if (x > 0) w[c++] = base - 1;
+    if (x + 1 < nx) w[c++] = base + 1;
+    if (y > 0) w[c++] = base - nx;
+    if (y + 1 < ny) w[c++] = base + nx;
+    if (nbhd == 6) {
+        if (z > 0) w[c++] = base - (int64_t)nx * ny;
+        if (z + 1 < nz) w[c++] = base + (int64_t)nx * ny;
+    }
+    return c;
+}
+
+/* MSC decision (Eq. 3.6, Alg. 2): H_2(v) = 0 when N(v) - N(w) >= N_t for some
+ * w in B(v), else 1.  Differences are taken in signed 64-bit arithmetic. */
+void oracle_msc_decide(const uint32_t *N, int32_t nx, int32_t ny, int32_t nz, int32_t Nt,
+                       int32_t nbhd, uint8_t *H2)
+{
+    int64_t w[7];
+    for (int64_t z = 0; z < nz; ++z)
+        for (int64_t y = 0; y < ny; ++y)
+            for (int64_t x = 0; x < nx; ++x) {
+                int64_t v = x + (int64_t)nx * (y + (int64_t)ny * z);
+                H2[v] = 1;
+                int c = neighbours(x, y, z, nx, ny, nz, nbhd, w);
+                for (int j = 0; j < c; ++j)
+                    if ((int64_t)N[v] - (int64_t)N[w[j]] >= (int64_t)Nt) H2[v] = 0;
+            }
+}
+
+/* SM threshold and decision (Eq. 3.10, Alg. 3).  With per_slice = 1 each
+ * slice z is treated on its own with the in-plane neighbourhood (Sec. 3.4:
+ * the steepest edge is found in each slice); with per_slice = 0 the whole
+ * volume is one region with neighbourhood nbhd.  In visiting order (x
+ * fastest) the steepest drop MaxSlope = max M(v) - M(w) is tracked with the
+ * ">=" update of Alg. 3, so the last voxel that reaches the maximum gives
+ * index; M_t = M(index).  H_3(v) = [M(v) >= M_t] when ge = 1 (the text of
+ * Sec. 3.4), [M(v) > M_t] when ge = 0 (Eq. 3.10).  A region whose MaxSlope is
+ * 0 has no edge and gets H_3 = 0.  Outputs per slice: Mt, slope, index (the
+ * same values in every slice when per_slice = 0). */
+void oracle_sm_decide(const uint32_t *M, int32_t nx, int32_t ny, int32_t nz, int32_t per_slice,
+                      int32_t nbhd, int32_t ge, uint32_t *Mt_out, uint32_t *slope_out,
+                      int64_t *index_out, uint8_t *H3)
+{
+    int64_t w[7];
+    int64_t plane = (int64_t)nx * ny;
+    int32_t nregions = per_slice ? nz : 1;
+    int region_nbhd = per_slice ? 4 : nbhd;
+    for (int32_t r = 0; r < nregions; ++r) {
+        int64_t z0 = per_slice ? r : 0, z1 = per_slice ? r + 1 : nz;
+        int64_t max_slope = 0, index = 0;
+        for (int64_t z = z0; z < z1; ++z)
+            for (int64_t y = 0; y < ny; ++y)
+                for (int64_t x = 0; x < nx; ++x) {
+                    int64_t v = x + nx * (y + (int64_t)ny * z);
+                    int c = neighbours(x, y, z, nx, ny, nz, region_nbhd, w);
+                    for (int j = 0; j < c; ++j) {
+                        int64_t diff = (int64_t)M[v] - (int64_t)M[w[j]];
+                        if (diff >= max_slope) {
+                            max_slope = diff;
+                            index = v;
+                        }
+                    }
+                }
+        uint32_t Mt = M[index];
+        for (int64_t z = z0; z < z1; ++z) {
+            Mt_out[z] = Mt;
+            slope_out[z] = (uint32_t)max_slope;
+            index_out[z] = index;
+            for (int64_t q = 0; q < plane; ++q) {
+                int64_t v = z * plane + q;
+                uint8_t in = ge ? (M[v] >= Mt) : (M[v] > Mt);
+                H3[v] = (max_slope == 0) ? 0 : in;
+            }
+        }
+    }
+}
+
+/* ------------------------------------------------ per-voxel sampled counts */
+
+/* |C(v)| for one voxel v = (x, y, z) straight from Eq. 3.4 / Eq. 3.9: the
+ * number of histories of class `cls` (1 missed, 2 hit) whose path meets v,
+ * tested history by history with the slab test.  Independent of the voxel
+ * enumeration above; used to check single voxels of full-size volumes. */
+int64_t oracle_count_through_voxel(const og_geom *g, float tau_l, float tau_h,
+                                   const int64_t *theta, int64_t K, const float *angle,
+                                   const float *u_in, const float *v_in, const float *u_out,
+                                   const float *v_out, const float *wepl, int64_t n,
+                                   int32_t cls, int64_t x, int64_t y, int64_t z)
+{
+    int64_t count = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        if (oracle_classify(wepl[i], tau_l, tau_h) != cls) continue;
+        int64_t gin[3], gout[3];
+        if (oracle_grid_endpoints(g, theta, K, angle[i], u_in[i], v_in[i], u_out[i], v_out[i],
+                                  gin, gout))
+            continue;
+        count += oracle_segment_meets_voxel(gin, gout, x, y, z);
+    }
+    return count;
+}

@@ -1,0 +1,338 @@
+"""Python face of the CPU oracle (test infrastructure only).
+
+The arithmetic lives in hull_oracle.c, compiled here with gcc and called
+through ctypes.  The CORDIC constants are computed below with exact integer
+arithmetic from their definitions; nothing is shared with the CUDA library.
+"""
+from __future__ import annotations
+
+import ctypes
+import dataclasses
+import math
+import os
+import subprocess
+import threading
+from pathlib import Path
+from typing import Dict, Optional, Tuple
+
+import numpy as np
+
+_HERE = Path(__file__).resolve().parent
+_SRC = _HERE / "hull_oracle.c"
+_OUT = _HERE / "_build" / "liboracle.so"
+_lib = None
+_lock = threading.Lock()
+
+SC, MSC, SM = 1, 2, 4
+
+
+# ------------------------------------------------------------------ build
+def build(force: bool = False) -> Path:
+    """Compile the oracle with gcc (plain C99 + __int128, no arch flags)."""
+    if force or not _OUT.exists() or _OUT.stat().st_mtime < _SRC.stat().st_mtime:
+        _OUT.parent.mkdir(exist_ok=True)
+        tmp = _OUT.with_suffix(f".{os.getpid()}.tmp")
+        subprocess.check_call(["gcc", "-O2", "-std=gnu11", "-fPIC", "-shared", "-Wall",
+                               "-o", str(tmp), str(_SRC), "-lm"])
+        os.replace(tmp, _OUT)
+    return _OUT
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            L = ctypes.CDLL(str(build()))
+            i64p = ctypes.POINTER(ctypes.c_int64)
+            f32p = ctypes.POINTER(ctypes.c_float)
+            u32p = ctypes.POINTER(ctypes.c_uint32)
+            u8p = ctypes.POINTER(ctypes.c_uint8)
+            L.oracle_cordic.argtypes = [ctypes.c_int64, i64p, ctypes.c_int64, i64p, i64p]
+            L.oracle_cordic.restype = None
+            L.oracle_grid_endpoints.argtypes = [ctypes.c_void_p, i64p, ctypes.c_int64] + \
+                [ctypes.c_float] * 5 + [i64p, i64p]
+            L.oracle_grid_endpoints.restype = ctypes.c_int
+            L.oracle_voxel_set.argtypes = [i64p, i64p, ctypes.c_int32, ctypes.c_int32,
+                                           ctypes.c_int32, i64p, ctypes.c_int64]
+            L.oracle_voxel_set.restype = ctypes.c_int64
+            L.oracle_segment_meets_voxel.argtypes = [i64p, i64p, ctypes.c_int64,
+                                                     ctypes.c_int64, ctypes.c_int64]
+            L.oracle_segment_meets_voxel.restype = ctypes.c_int
+            L.oracle_classify.argtypes = [ctypes.c_float] * 3
+            L.oracle_classify.restype = ctypes.c_int
+            L.oracle_accumulate.argtypes = [ctypes.c_void_p, ctypes.c_float, ctypes.c_float,
+                                            ctypes.c_int32, i64p, ctypes.c_int64] + \
+                [f32p] * 6 + [ctypes.c_int64, u32p, u32p, u8p, i64p]
+            L.oracle_accumulate.restype = ctypes.c_int
+            L.oracle_sc_from_counts.argtypes = [u32p, ctypes.c_int64, u8p]
+            L.oracle_sc_from_counts.restype = None
+            L.oracle_msc_decide.argtypes = [u32p] + [ctypes.c_int32] * 5 + [u8p]
+            L.oracle_msc_decide.restype = None
+            L.oracle_sm_decide.argtypes = [u32p] + [ctypes.c_int32] * 6 + [u32p, u32p, i64p, u8p]
+            L.oracle_sm_decide.restype = None
+            L.oracle_count_through_voxel.argtypes = [ctypes.c_void_p, ctypes.c_float,
+                                                     ctypes.c_float, i64p, ctypes.c_int64] + \
+                [f32p] * 6 + [ctypes.c_int64, ctypes.c_int32] + [ctypes.c_int64] * 3
+            L.oracle_count_through_voxel.restype = ctypes.c_int64
+            _lib = L
+    return _lib
+
+
+def _p(a: np.ndarray, ct):
+    return a.ctypes.data_as(ctypes.POINTER(ct))
+
+
+# ------------------------------------------------------ CORDIC constants
+def _atan_inv_fixed(m: int, bits: int) -> int:
+    """atan(1/m) * 2^bits by its Taylor series, exact integer arithmetic
+    (error below the number of terms in the last place)."""
+    one = 1 << bits
+    total, k = 0, 0
+    power = m
+    while True:
+        term = one // (power * (2 * k + 1))
+        if term == 0:
+            break
+        total += -term if k & 1 else term
+        k += 1
+        power *= m * m
+    return total
+
+
+def cordic_table(bits: int = 256) -> Tuple[Tuple[int, ...], int]:
+    """theta_i = round(atan(2^-i) * 180/pi * 2^30), i = 0..31, and
+    K = round(2^30 * prod_i (1 + 2^-2i)^(-1/2)), from exact series:
+    pi by Machin's formula pi/4 = 4 atan(1/5) - atan(1/239)."""
+    pi = 4 * (4 * _atan_inv_fixed(5, bits) - _atan_inv_fixed(239, bits))
+    theta = [45 << 30]  # atan(1) = pi/4 = 45 degrees exactly
+    for i in range(1, 32):
+        a = _atan_inv_fixed(1 << i, bits)
+        theta.append((2 * a * 180 * (1 << 30) + pi) // (2 * pi))
+    P = 1
+    for i in range(32):
+        P *= (1 << (2 * i)) + 1
+    Qexp = 2 * sum(range(32))
+    m = 64
+    # K = round(sqrt(2^60 * 2^Qexp / P))
+    s = math.isqrt(((1 << (60 + Qexp + 2 * m)) // P))
+    K = (s + (1 << (m - 1))) >> m
+    return tuple(theta), K
+
+
+_TABLE = None
+
+
+def _table_arrays():
+    global _TABLE
+    if _TABLE is None:
+        theta, K = cordic_table()
+        _TABLE = (np.asarray(theta, dtype=np.int64), int(K))
+    return _TABLE
+
+
+def cordic(angle_q16: int) -> Tuple[int, int]:
+    """(cos, sin) with 30 fractional bits of an angle in degrees * 2^16."""
+    th, K = _table_arrays()
+    c = ctypes.c_int64()
+    s = ctypes.c_int64()
+    lib().oracle_cordic(int(angle_q16), _p(th, ctypes.c_int64), K, ctypes.byref(c),
+                        ctypes.byref(s))
+    return c.value, s.value
+
+
+# ------------------------------------------------------------- geometry
+class _OGeom(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nz", ctypes.c_int32),
+                ("sx", ctypes.c_float), ("sy", ctypes.c_float), ("sz", ctypes.c_float),
+                ("T", ctypes.c_float)]
+
+
+def _ogeom(g) -> _OGeom:
+    return _OGeom(int(g.nx), int(g.ny), int(g.nz), float(g.sx), float(g.sy), float(g.sz),
+                  float(g.T))
+
+
+def grid_endpoints(g, angle, u_in, v_in, u_out, v_out):
+    """(rejected, gin[3], gout[3]) of one history in grid Q16 coordinates."""
+    th, K = _table_arrays()
+    gin = np.zeros(3, np.int64)
+    gout = np.zeros(3, np.int64)
+    og = _ogeom(g)
+    r = lib().oracle_grid_endpoints(ctypes.byref(og), _p(th, ctypes.c_int64), K,
+                                    float(angle), float(u_in), float(v_in), float(u_out),
+                                    float(v_out), _p(gin, ctypes.c_int64),
+                                    _p(gout, ctypes.c_int64))
+    return bool(r), gin, gout
+
+
+def voxel_set(gin, gout, nx: int, ny: int, nz: int) -> np.ndarray:
+    """Sorted linear indices (x fastest) of A_i for the closed segment."""
+    gin = np.ascontiguousarray(gin, dtype=np.int64)
+    gout = np.ascontiguousarray(gout, dtype=np.int64)
+    cap = nx + ny + nz + 8
+    out = np.zeros(cap, np.int64)
+    m = lib().oracle_voxel_set(_p(gin, ctypes.c_int64), _p(gout, ctypes.c_int64), nx, ny, nz,
+                               _p(out, ctypes.c_int64), cap)
+    if m < 0 or m > cap:
+        raise RuntimeError("oracle_voxel_set failed")
+    return out[:m].copy()
+
+
+def segment_meets_voxel(gin, gout, x: int, y: int, z: int) -> bool:
+    gin = np.ascontiguousarray(gin, dtype=np.int64)
+    gout = np.ascontiguousarray(gout, dtype=np.int64)
+    return bool(lib().oracle_segment_meets_voxel(_p(gin, ctypes.c_int64),
+                                                 _p(gout, ctypes.c_int64), x, y, z))
+
+
+def voxel_set_bruteforce(gin, gout, nx: int, ny: int, nz: int) -> np.ndarray:
+    """A_i by testing every voxel of the grid with the slab test."""
+    gin = np.ascontiguousarray(gin, dtype=np.int64)
+    gout = np.ascontiguousarray(gout, dtype=np.int64)
+    f = lib().oracle_segment_meets_voxel
+    pi, po = _p(gin, ctypes.c_int64), _p(gout, ctypes.c_int64)
+    out = [x + nx * (y + ny * z) for z in range(nz) for y in range(ny) for x in range(nx)
+           if f(pi, po, x, y, z)]
+    return np.asarray(out, dtype=np.int64)
+
+
+def count_through_voxel(g, hist, cls: int, x: int, y: int, z: int,
+                        params: Params = None) -> int:
+    """|C(v)| of one voxel by testing every history of class `cls`
+    (1 missed -> N(v), 2 hit -> M(v)) with the slab test."""
+    params = params or Params()
+    th, K = _table_arrays()
+    arrs = [np.ascontiguousarray(a, dtype=np.float32) for a in hist.arrays()]
+    og = _ogeom(g)
+    return int(lib().oracle_count_through_voxel(
+        ctypes.byref(og), params.tau_l, params.tau_h, _p(th, ctypes.c_int64), K,
+        *[_p(a, ctypes.c_float) for a in arrs], len(hist), cls, x, y, z))
+
+
+def classify(wepl, tau_l: float = 1.0, tau_h: float = 5.0) -> np.ndarray:
+    """0 neither, 1 missed (Eq. 3.1), 2 hit (Eq. 3.7), one history at a time."""
+    f = lib().oracle_classify
+    return np.asarray([f(float(w), tau_l, tau_h) for w in np.asarray(wepl, np.float32)],
+                      dtype=np.uint8)
+
+
+# ---------------------------------------------------------------- params
+@dataclasses.dataclass(frozen=True)
+class Params:
+    tau_l: float = 1.0      # missed cutoff on WEPL, mm (Sec. 3.3)
+    tau_h: float = 5.0      # hit cutoff on WEPL, mm (Sec. 3.4)
+    nt: int = 50            # MSC neighbour-difference threshold N_t (Sec. 3.3)
+    nbhd: int = 6           # B(v): 6 face neighbours (index units) or 4 in-plane
+    sm_ge: int = 1          # H_3 uses M >= M_t (1) or M > M_t (0)
+    sm_per_slice: int = 1   # SM threshold per slice (1) or over the volume (0)
+    methods: int = SC | MSC | SM
+
+
+# ----------------------------------------------------------- accumulation
+def accumulate(g, hist, params: Params = Params(), want_h1: bool = True) -> Dict:
+    """N, M, carved H1 and stats over all histories (single thread)."""
+    V = g.nx * g.ny * g.nz
+    N = np.zeros(V, np.uint32)
+    M = np.zeros(V, np.uint32)
+    H1 = np.ones(V, np.uint8) if want_h1 else None
+    stats = np.zeros(8, np.int64)
+    _accumulate_into(g, hist, 0, len(hist), params, N, M, H1, stats)
+    return _pack_acc(N, M, H1, stats)
+
+
+def _pack_acc(N, M, H1, stats):
+    return {"N": N, "M": M, "H1_carved": H1,
+            "stats": {"n_in": int(stats[0]), "n_miss": int(stats[1]), "n_hit": int(stats[2]),
+                      "n_none": int(stats[3]), "n_reject": int(stats[4]),
+                      "steps_miss": int(stats[5]), "steps_hit": int(stats[6])}}
+
+
+def _accumulate_into(g, hist, s, e, params, N, M, H1, stats):
+    th, K = _table_arrays()
+    arrs = [np.ascontiguousarray(a[s:e], dtype=np.float32) for a in hist.arrays()]
+    og = _ogeom(g)
+    r = lib().oracle_accumulate(ctypes.byref(og), params.tau_l, params.tau_h, params.methods,
+                                _p(th, ctypes.c_int64), K,
+                                *[_p(a, ctypes.c_float) for a in arrs], e - s,
+                                _p(N, ctypes.c_uint32), _p(M, ctypes.c_uint32),
+                                _p(H1, ctypes.c_uint8) if H1 is not None else None,
+                                _p(stats, ctypes.c_int64))
+    if r != 0:
+        raise MemoryError("oracle_accumulate")
+
+
+def accumulate_parallel(g, hist, params: Params = Params(), threads: Optional[int] = None,
+                        want_h1: bool = True) -> Dict:
+    """The same sums split over history ranges, each thread with its own
+    volumes, added at the end (integer sums, so the result is identical)."""
+    n = len(hist)
+    threads = threads or os.cpu_count() or 1
+    threads = max(1, min(threads, n // 1000 + 1))
+    V = g.nx * g.ny * g.nz
+    parts = []
+    bounds = np.linspace(0, n, threads + 1).astype(np.int64)
+    for t in range(threads):
+        parts.append((np.zeros(V, np.uint32), np.zeros(V, np.uint32),
+                      np.ones(V, np.uint8) if want_h1 else None, np.zeros(8, np.int64)))
+    ths = [threading.Thread(target=_accumulate_into,
+                            args=(g, hist, int(bounds[t]), int(bounds[t + 1]), params) + parts[t])
+           for t in range(threads)]
+    for t in ths:
+        t.start()
+    for t in ths:
+        t.join()
+    N = np.zeros(V, np.uint32)
+    M = np.zeros(V, np.uint32)
+    H1 = np.ones(V, np.uint8) if want_h1 else None
+    stats = np.zeros(8, np.int64)
+    for pN, pM, pH, ps in parts:
+        N += pN
+        M += pM
+        if want_h1:
+            H1 &= pH
+        stats += ps
+    return _pack_acc(N, M, H1, stats)
+
+
+# -------------------------------------------------------------- decisions
+def sc_from_counts(N: np.ndarray) -> np.ndarray:
+    N = np.ascontiguousarray(N, np.uint32)
+    H1 = np.zeros(N.shape[0], np.uint8)
+    lib().oracle_sc_from_counts(_p(N, ctypes.c_uint32), N.shape[0], _p(H1, ctypes.c_uint8))
+    return H1
+
+
+def msc_decide(N: np.ndarray, dims, nt: int = 50, nbhd: int = 6) -> np.ndarray:
+    nx, ny, nz = dims
+    N = np.ascontiguousarray(N, np.uint32).reshape(-1)
+    H2 = np.zeros(N.shape[0], np.uint8)
+    lib().oracle_msc_decide(_p(N, ctypes.c_uint32), nx, ny, nz, nt, nbhd, _p(H2, ctypes.c_uint8))
+    return H2
+
+
+def sm_decide(M: np.ndarray, dims, per_slice: int = 1, nbhd: int = 6, ge: int = 1) -> Dict:
+    nx, ny, nz = dims
+    M = np.ascontiguousarray(M, np.uint32).reshape(-1)
+    H3 = np.zeros(M.shape[0], np.uint8)
+    Mt = np.zeros(nz, np.uint32)
+    slope = np.zeros(nz, np.uint32)
+    index = np.zeros(nz, np.int64)
+    lib().oracle_sm_decide(_p(M, ctypes.c_uint32), nx, ny, nz, per_slice, nbhd, ge,
+                           _p(Mt, ctypes.c_uint32), _p(slope, ctypes.c_uint32),
+                           _p(index, ctypes.c_int64), _p(H3, ctypes.c_uint8))
+    return {"H3": H3, "Mt": Mt, "slope": slope, "index": index}
+
+
+def run(g, hist, params: Params = Params(), threads: Optional[int] = 1) -> Dict:
+    """Everything the hull-detection path returns for one scan."""
+    if threads == 1:
+        acc = accumulate(g, hist, params)
+    else:
+        acc = accumulate_parallel(g, hist, params, threads)
+    dims = (g.nx, g.ny, g.nz)
+    out = dict(acc)
+    out["H1"] = sc_from_counts(acc["N"])
+    out["H2"] = msc_decide(acc["N"], dims, params.nt, params.nbhd)
+    sm = sm_decide(acc["M"], dims, params.sm_per_slice, params.nbhd, params.sm_ge)
+    out.update(sm)
+    return out
