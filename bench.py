@@ -1,0 +1,354 @@
+#!/usr/bin/env python
+"""Throughput of the GB300 hull-detection path (SC + MSC + SM) on the
+head-sized workload (200x200x32 voxels of 1x1x2.5 mm, 90 angles x 100k =
+9e6 float32 histories, synthetic head phantom).
+
+One step = one scan: reset the counts, add all histories (classify, traverse,
+accumulate N and M), finalize the three hulls.  `value` is histories/s over
+all ranks; `e2e` is the same metric through the C ABI from pinned host
+buffers with the host->device copy of the histories and the device->host
+read of the three masks inside the timed region.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl hulld|reference]
+
+Under torchrun (N > 1) every rank runs its own scan (independent problems,
+no collective on the data path); the step time is the maximum over ranks.
+`--impl reference` times the CPU oracle (the plain C statement of the
+method) on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "proton histories/s (SC+MSC+SM hull detection)"
+UNIT = "histories/s"
+WORKLOAD = "head-200x200x32 voxels 1x1x2.5mm, 90 angles x 100000 = 9e6 float32 histories"
+
+# Algorithmic integer operations per voxel-step of the DDA: choose the next
+# crossing (2 compares), advance the voxel index (1), update two
+# crossing-order terms (2 x 64-bit add = 4), decrement and test the remaining
+# count (2), increment the count or clear the bit (1).
+OPS_PER_STEP = 10
+# GB300: 152 SMs x 128 INT32 lanes per SM per clock.
+SMS, INT32_LANES_PER_SM = 152, 128
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            p = json.load(f)
+        return {"hbm_gbs": float(p["hbm_gbs"]), "sm_max_mhz": float(p.get("sm_max_mhz", 2070.0)),
+                "source": "measured"}
+    except Exception:
+        return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0, "source": "fallback"}
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle-reason sampling during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=2)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[4:8]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def run_reference(args):
+    """The CPU oracle on a bounded sample of the same workload."""
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return
+    import oracle
+    from paper_1402_1720_gb300 import synth
+    oracle.build()
+    frac = args.ref_fraction
+    w = synth.make_config(2, fraction=frac)
+    cores = os.cpu_count() or 1
+    g, h = w.geometry, w.histories
+    for _ in range(args.warmup):
+        oracle.run(g, h, threads=cores)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        r = oracle.run(g, h, threads=cores)
+    dt = (time.perf_counter() - t0) / max(1, args.steps)
+    value = len(h) / dt
+    sample = (f"{len(h)} histories per step = every angle, {frac:g} of each angle's "
+              f"100000 histories, full 200x200x32 grid")
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
+            "data": "synthetic", "impl": "reference",
+            "config": {"workload": WORKLOAD, "sample_fraction": frac},
+            "voxel_steps_per_s": (r["stats"]["steps_miss"] + r["stats"]["steps_hit"]) / dt,
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def cpu_baseline(seconds_target: float):
+    """The oracle as it stands, timed on the host cores on a bounded sample."""
+    import oracle
+    from paper_1402_1720_gb300 import synth
+    oracle.build()
+    cores = os.cpu_count() or 1
+    frac = 0.01
+    w = synth.make_config(2, fraction=frac)
+    t0 = time.perf_counter()
+    r = oracle.run(w.geometry, w.histories, threads=cores)
+    dt = time.perf_counter() - t0
+    # grow the sample toward the target CPU time (bounded)
+    if dt < seconds_target / 4:
+        frac = min(0.2, frac * seconds_target / max(dt, 1e-3) / 2)
+        w = synth.make_config(2, fraction=frac)
+        t0 = time.perf_counter()
+        r = oracle.run(w.geometry, w.histories, threads=cores)
+        dt = time.perf_counter() - t0
+    n = len(w.histories)
+    return {"value": n / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{n} histories (every angle, {frac:.4g} of each angle's histories) "
+                      f"of the same workload on the full 200x200x32 grid, {dt:.1f} s wall",
+            "voxel_steps_per_s": (r["stats"]["steps_miss"] + r["stats"]["steps_hit"]) / dt}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="hulld", choices=["hulld", "reference"])
+    ap.add_argument("--ref-fraction", type=float, default=0.004)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-per-method", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    args = ap.parse_args()
+
+    if args.impl == "reference":
+        run_reference(args)
+        return
+
+    import torch
+    import torch.distributed as dist
+    from paper_1402_1720_gb300 import build as hbuild
+    from paper_1402_1720_gb300 import hulld, synth
+
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    hbuild.build()
+    hulld.load()
+
+    w = synth.make_config(2)
+    g, h = w.geometry, w.histories
+    n = len(h)
+    dev = [torch.from_numpy(a).cuda() for a in h.arrays()]
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if ws > 1:
+            dist.barrier()
+
+    def max_over_ranks(x: float) -> float:
+        if ws == 1:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    def timed(scan, steps, warmup, profile=False, sampler=None):
+        for _ in range(warmup):
+            scan.reset()
+            scan.add(dev)
+            scan.finalize()
+        torch.cuda.synchronize()
+        barrier()
+        torch.cuda.synchronize()
+        if profile:
+            scan.set_profiling(True)
+        l0 = scan.profile()["kernel_launches"]
+        if sampler:
+            sampler.start()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            scan.reset()
+            scan.add(dev)
+            scan.finalize()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        torch.cuda.synchronize()
+        clocks = sampler.stop() if sampler else None
+        ms = e0.elapsed_time(e1) / steps
+        prof = scan.profile()
+        if profile:
+            scan.set_profiling(False)
+        return ms, prof, prof["kernel_launches"] - l0, clocks
+
+    # ---- main measurement: all three methods
+    scan = hulld.Scan(g)
+    sampler = ClockSampler(local)
+    ms, prof, launches, clocks = timed(scan, args.steps, args.warmup, profile=True,
+                                       sampler=sampler)
+    ms = max_over_ranks(ms)
+    st = scan.stats()
+    steps_per_scan = st["steps_miss"] + st["steps_hit"]
+    value = ws * n / (ms * 1e-3)
+
+    # roofline of the dominant kernel (the traversal)
+    peaks = _peaks()
+    trace_ms = prof["ms_trace"] / max(1, prof["trace_launches"])
+    ops = OPS_PER_STEP * steps_per_scan  # one traversal launch covers the whole scan
+    achieved = ops / (trace_ms * 1e-3) / 1e12
+    peak_tops = SMS * INT32_LANES_PER_SM * peaks["sm_max_mhz"] * 1e6 / 1e12
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak_tops, "unit": "Tops/s",
+                "frac": achieved / peak_tops, "traffic": None,
+                "kernel": "trace_kernel", "kernel_ms": trace_ms,
+                "ops_per_voxel_step": OPS_PER_STEP, "voxel_steps_per_launch": steps_per_scan,
+                "peak_source": f"152 SMs x 128 INT32 lanes x {peaks['sm_max_mhz']:.0f} MHz "
+                               f"({peaks['source']} max clock)"}
+    phases = {"ingest_ms": prof["ms_ingest"] / args.steps, "trace_ms": trace_ms,
+              "finalize_ms": prof["ms_finalize"] / args.steps}
+    # ingest is HBM-bound: 24 algorithmic bytes per history
+    phases["ingest_gbs"] = 24.0 * n / (phases["ingest_ms"] * 1e-3) / 1e9
+    phases["hbm_peak_gbs"] = peaks["hbm_gbs"]
+
+    # ---- per method
+    per_method = {}
+    if not args.no_per_method:
+        for name, m in [("sc", hulld.HD_SC), ("msc", hulld.HD_MSC), ("sm", hulld.HD_SM)]:
+            p = hulld.hd_params_default()
+            p.methods = m
+            s2 = hulld.Scan(g, p)
+            k = max(3, args.steps // 2)
+            mms, _, _, _ = timed(s2, k, 3)
+            mms = max_over_ranks(mms)
+            sst = s2.stats()
+            per_method[name] = {"histories_per_s": ws * n / (mms * 1e-3),
+                                "voxel_steps_per_s": ws * (sst["steps_miss"] + sst["steps_hit"]) /
+                                (mms * 1e-3), "ms_per_step": mms}
+            s2.close()
+
+    # ---- end to end through the C ABI from pinned host memory
+    e2e = None
+    if not args.no_e2e:
+        host = [torch.from_numpy(a).pin_memory() for a in h.arrays()]
+        masks = [torch.empty(g.n_voxels, dtype=torch.uint8).pin_memory() for _ in range(3)]
+        s3 = hulld.Scan(g)
+
+        def e2e_step():
+            s3.reset()
+            s3.add(host)
+            s3.finalize()
+            for mk, meth in zip(masks, (hulld.HD_SC, hulld.HD_MSC, hulld.HD_SM)):
+                hulld.hd_scan_get_mask(s3.handle, meth, hulld.HD_MASK_U8, mk)
+            stream.synchronize()
+
+        for _ in range(max(3, args.warmup)):
+            e2e_step()
+        barrier()
+        t0 = time.perf_counter()
+        k = max(3, args.steps // 2)
+        for _ in range(k):
+            e2e_step()
+        dt = max_over_ranks((time.perf_counter() - t0) / k)
+        e2e = {"value": ws * n / dt, "unit": UNIT, "h2d_bytes_per_step": 24 * n,
+               "d2h_bytes_per_step": 3 * g.n_voxels, "ms_per_step": dt * 1e3}
+        s3.close()
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(args.cpu_seconds)
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "int64", "data": "synthetic",
+                "config": {"workload": WORKLOAD, "methods": "SC+MSC+SM",
+                           "inputs": "9e6 x 24 B = 216 MB resident in HBM, larger than L2",
+                           "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
+                "voxel_steps_per_s": ws * steps_per_scan / (ms * 1e-3),
+                "voxel_steps_per_scan": steps_per_scan,
+                "per_method": per_method, "phases": phases,
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": launches, "clocks": clocks}
+        print(json.dumps(line), flush=True)
+    scan.close()
+    if ws > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,238 @@
+/*
+ * hulld.h -- C ABI of the GB300 hull-detection library for proton CT.
+ *
+ * The library computes the three hull-detection methods of Schultze et al.,
+ * "Performance of Hull-Detection Algorithms for Proton Computed Tomography
+ * Reconstruction" (arXiv 1402.1720):
+ *   SC  (silhouette/space carving, Sec. 3.2, Eq. 3.1-3.3, Alg. 1),
+ *   MSC (modified space carving,   Sec. 3.3, Eq. 3.4-3.6, Alg. 2),
+ *   SM  (space modeling,           Sec. 3.4, Eq. 3.7-3.10, Alg. 3),
+ * from proton histories given as gantry angle, entry/exit tracker
+ * coordinates and WEPL (Sec. 2.1-2.2).  All compute runs in CUDA kernels for
+ * sm_103a; there is no CPU fallback.
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * Geometry.  World frame in mm, origin at the centre of the reconstruction
+ * volume, z the vertical rotation axis (Sec. 2.2).  At gantry angle phi
+ * (degrees) the beam runs along b = (cos phi, sin phi, 0), the lateral
+ * tracker axis is e_u = (-sin phi, cos phi, 0), the vertical one e_v = z.
+ * Entry point = -T b + u_in e_u + v_in e_v, exit point = +T b + u_out e_u +
+ * v_out e_v, with T the tracker half-separation.  The path L_i is the closed
+ * straight segment between them (Sec. 2.1; the definition of L_i before
+ * Eq. 3.2).
+ *
+ * Voxels.  nx*ny*nz voxels of sx*sy*sz mm centred on the origin; linear index
+ * x + nx*(y + ny*z) (x fastest).  A_i (Eq. 3.2, read with d_0 = 0) is the set
+ * of voxels whose half-open cube [k, k+1)^3 in voxel units contains a point
+ * of L_i.  Coordinates are made exact by rounding each float32 input to 16
+ * fractional bits (ties to even), an integer CORDIC rotation (Q30 cos/sin)
+ * and integer floor divisions; everything after that is exact integer
+ * arithmetic, so counts and masks are bit-reproducible.
+ *
+ * Classification (Eq. 3.1, Eq. 3.7; cutoffs of Sec. 3.2-3.4): a history is
+ * missed when wepl < wepl_miss_lt, hit when wepl > wepl_hit_gt, otherwise
+ * unused (NaN included).  No angular cutoff is applied (the paper used none).
+ *
+ * Rejection.  A missed or hit history whose angle is not finite or has
+ * |angle| >= 2^20 degrees, whose u/v coordinates are not finite or have
+ * magnitude >= 4096 mm, or whose grid coordinates reach magnitude >= 2^30 /
+ * 2^16 = 16384 voxels, is not traversed and is counted in n_reject.
+ * Histories are never silently clipped.
+ *
+ * Streams and memory.  `stream` arguments are cudaStream_t values passed as
+ * void* (NULL = the legacy default stream).  Work is stream-ordered; the
+ * caller keeps input buffers valid until the stream has passed the call.
+ * All calls on one scan must be ordered by the caller (one stream, or
+ * events between streams).  Pointers flagged `on_device` are device
+ * pointers on the scan's device; otherwise they are host pointers (pinned
+ * memory gives asynchronous copies).  The caller owns every buffer it
+ * passes; the library owns the scan state and frees it in hd_scan_destroy.
+ *
+ * Errors.  Every call returns hd_status and never throws.  A CUDA error is
+ * returned as HD_ERR_CUDA from the call that observed it.
+ */
+#ifndef HULLD_H
+#define HULLD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define HD_API __attribute__((visibility("default")))
+#else
+#define HD_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    HD_OK = 0,
+    HD_ERR_ARG = 1,       /* null pointer, bad enum, bad size or layout */
+    HD_ERR_RANGE = 2,     /* geometry or parameter outside supported range */
+    HD_ERR_NOMEM = 3,     /* device or host allocation failed */
+    HD_ERR_CUDA = 4,      /* a CUDA runtime call failed */
+    HD_ERR_STATE = 5,     /* call not valid in the object's current state */
+    HD_ERR_TIMEOUT = 6,   /* a bounded wait gave up */
+    HD_ERR_ADMISSION = 7, /* serving: request exceeds the memory budget */
+    HD_ERR_OVERFLOW = 8   /* a scan reached 2^32 - 1 histories (uint32 counts) */
+} hd_status;
+
+/* Methods (bit mask). */
+enum { HD_SC = 1, HD_MSC = 2, HD_SM = 4 };
+
+/* Mask layouts for hd_scan_get_mask. */
+enum {
+    HD_MASK_U8 = 0,  /* one byte per voxel, 0 or 1, linear voxel order */
+    HD_MASK_BITS = 1 /* ceil(V/32) uint32 words, voxel v at bit (v & 31) of word v >> 5 */
+};
+
+/* Reconstruction grid.  Supported: 1 <= n <= 4096 per axis, V < 2^31,
+ * voxel sizes in [1/64, 64] mm, n * s <= 8192 mm per axis,
+ * 0 < tracker_half_sep_mm < 4096. */
+typedef struct {
+    int32_t nx, ny, nz;
+    float sx, sy, sz;          /* voxel size, mm */
+    float tracker_half_sep_mm; /* T: trackers at -T and +T along the beam */
+} hd_geometry;
+
+/* Method parameters.  hd_params_default gives the paper's values. */
+typedef struct {
+    float wepl_miss_lt;    /* missed if WEPL < this (1.0 mm, Sec. 3.2/3.3) */
+    float wepl_hit_gt;     /* hit if WEPL > this (5.0 mm, Sec. 3.4) */
+    int32_t msc_nt;        /* MSC threshold N_t (50, Sec. 3.3) */
+    int32_t msc_nbhd;      /* B(v) of Eq. 3.5: 6 = face neighbours, 4 = in-plane only */
+    int32_t sm_ge;         /* H_3 = [M >= M_t] (1, text of Sec. 3.4) or [M > M_t] (0, Eq. 3.10) */
+    int32_t sm_per_slice;  /* M_t per slice (1, Sec. 3.4) or over the whole volume (0, Alg. 3) */
+    uint32_t methods;      /* bit mask of HD_SC | HD_MSC | HD_SM */
+} hd_params;
+
+/* Per-scan counters (cumulative since create/reset). */
+typedef struct {
+    int64_t n_in;       /* histories received */
+    int64_t n_miss;     /* classified missed (Eq. 3.1) */
+    int64_t n_hit;      /* classified hit (Eq. 3.7) */
+    int64_t n_none;     /* neither */
+    int64_t n_reject;   /* missed/hit histories with unusable geometry (not traversed) */
+    int64_t steps_miss; /* sum of |A_i| over traversed missed histories */
+    int64_t steps_hit;  /* sum of |A_i| over traversed hit histories */
+} hd_stats;
+
+/* Kernel-level timing of a scan (enabled by hd_scan_set_profiling):
+ * CUDA-event time on the scan's stream of each phase, summed over calls,
+ * and the number of kernels the library launched (always counted). */
+typedef struct {
+    int64_t kernel_launches;  /* kernels launched by this scan since create */
+    int64_t trace_launches;   /* traversal kernel launches (profiled window) */
+    double ms_ingest;         /* classification + geometry + compaction */
+    double ms_trace;          /* voxel traversal and accumulation */
+    double ms_finalize;       /* decisions (H_1, H_2, M_t, H_3) */
+} hd_profile;
+
+typedef struct hd_scan hd_scan;
+
+/* Human-readable name of a status code (static storage). */
+HD_API const char *hd_status_string(hd_status s);
+
+/* Text of the last CUDA error this thread saw inside the library (the call
+ * and cudaGetErrorString), or "" if none.  Thread-local static storage. */
+HD_API const char *hd_last_cuda_error(void);
+
+/* Fill *out with the paper's parameters: 1.0 mm, 5.0 mm, N_t = 50 (Sec. 3.3),
+ * B6, H_3 with >=, per-slice M_t, all three methods. */
+HD_API hd_status hd_params_default(hd_params *out);
+
+/* Create a scan on the current CUDA device: validates geometry and
+ * parameters, allocates the count volumes N (Eq. 3.4) and M (Eq. 3.9), the
+ * carve mask for SC (Alg. 1 starts from all ones) and the output masks,
+ * and zeroes them on the legacy default stream (synchronised before
+ * return).  HD_ERR_RANGE for unsupported geometry, HD_ERR_ARG for bad
+ * parameters (including wepl_miss_lt > wepl_hit_gt or a NaN cutoff). */
+HD_API hd_status hd_scan_create(const hd_geometry *geom, const hd_params *params, hd_scan **out);
+
+/* Release everything the scan owns.  Synchronises the scan's device first.
+ * NULL is accepted. */
+HD_API hd_status hd_scan_destroy(hd_scan *scan);
+
+/* Zero the counts and statistics and restore the carve mask to all ones,
+ * stream-ordered, so the scan can take a new acquisition. */
+HD_API hd_status hd_scan_reset(hd_scan *scan, void *stream);
+
+/* Add n proton histories (structure of arrays, float32, n entries each):
+ * classify each (Eq. 3.1, Eq. 3.7), traverse the voxel set A_i of every
+ * missed and hit history (Eq. 3.2) and accumulate N (Eq. 3.4), M (Eq. 3.9)
+ * and, when SC runs without MSC, the SC carve (Alg. 1).  Counts stay
+ * resident on the device, so histories may arrive in any number of calls
+ * (streamed per-angle chunks, Sec. 4 online mode) in any order; the result
+ * depends only on the multiset of histories.  on_device = 0 copies from host
+ * memory inside the call (stream-ordered).  n = 0 is a no-op.
+ * HD_ERR_OVERFLOW if the scan would exceed 2^32 - 1 histories. */
+HD_API hd_status hd_scan_add_histories(hd_scan *scan, const float *angle_deg, const float *u_in,
+                                const float *v_in, const float *u_out, const float *v_out,
+                                const float *wepl, int64_t n, int32_t on_device,
+                                void *stream);
+
+/* Compute the hulls from the resident counts, stream-ordered:
+ *   H_1 = V minus the union of missed paths = {v : N(v) = 0} (Eq. 3.3),
+ *   H_2 = {v : max_{w in B(v)} N(v) - N(w) < N_t} (Eq. 3.6),
+ *   H_3 = {v : M(v) >= M_t(z)} (or >), M_t(z) = M(v*) where v* is the last
+ *         voxel (x-fastest order) reaching the steepest drop
+ *         max_{w in B(v)} M(v) - M(w) of its slice (Alg. 3 per slice); a
+ *         slice whose steepest drop is 0 has no edge and H_3 = 0 there.
+ * Only the requested methods are computed.  May be called again after more
+ * histories arrive. */
+HD_API hd_status hd_scan_finalize(hd_scan *scan, void *stream);
+
+/* Copy a finalized mask (method = one of HD_SC, HD_MSC, HD_SM) into dst in
+ * the given layout.  dst_bytes must be at least V (HD_MASK_U8) or
+ * 4*ceil(V/32) (HD_MASK_BITS).  For HD_MASK_BITS, bits past V are 0.
+ * HD_ERR_STATE if the method was not requested or finalize has not run. */
+HD_API hd_status hd_scan_get_mask(hd_scan *scan, int32_t method, int32_t layout, void *dst,
+                           size_t dst_bytes, int32_t dst_on_device, void *stream);
+
+/* Copy the count volume of a method into dst (n >= V uint32):
+ * HD_MSC or HD_SC -> N (missed paths per voxel, Eq. 3.4; requires MSC, or
+ * SC run together with MSC), HD_SM -> M (hit paths per voxel, Eq. 3.9). */
+HD_API hd_status hd_scan_get_counts(hd_scan *scan, int32_t method, uint32_t *dst, int64_t n,
+                             int32_t dst_on_device, void *stream);
+
+/* Copy the SM thresholds of the last finalize to host arrays of nz entries:
+ * M_t per slice, the steepest drop per slice and the linear index of v*.
+ * With sm_per_slice = 0 every slice holds the volume's values.  Any of the
+ * pointers may be NULL.  Synchronises the stream. */
+HD_API hd_status hd_scan_get_thresholds(hd_scan *scan, uint32_t *mt, uint32_t *slope, int64_t *index,
+                                 int32_t nz, void *stream);
+
+/* Read the scan's counters (synchronises the stream). */
+HD_API hd_status hd_scan_get_stats(hd_scan *scan, hd_stats *out, void *stream);
+
+/* Linear indices, ascending, of the voxels in a finalized hull (the
+ * compaction that shrinks the unknown vector x of Sec. 1).  Writes up to
+ * `capacity` int32 indices to dst and the hull size to *count (host).
+ * Synchronises the stream. */
+HD_API hd_status hd_scan_get_hull_indices(hd_scan *scan, int32_t method, int32_t *dst,
+                                   int64_t capacity, int64_t *count, int32_t dst_on_device,
+                                   void *stream);
+
+/* Start (enable = 1) or stop (0) recording CUDA events around the scan's
+ * kernels; starting also clears the accumulated times.  A library aid for
+ * measurement: no counterpart in the paper. */
+HD_API hd_status hd_scan_set_profiling(hd_scan *scan, int32_t enable);
+
+/* Accumulated phase times and launch counts.  Waits for the recorded events
+ * (host synchronisation on them). */
+HD_API hd_status hd_scan_get_profile(hd_scan *scan, hd_profile *out);
+
+/* Classify n WEPL values (Eq. 3.1, Eq. 3.7): cls_out[i] = 1 missed, 2 hit,
+ * 0 neither.  Only the two cutoffs of params are used.  wepl and cls_out
+ * are both device pointers (on_device = 1) or both host pointers. */
+HD_API hd_status hd_classify(const float *wepl, int64_t n, const hd_params *params, uint8_t *cls_out,
+                      int32_t on_device, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HULLD_H */

@@ -1,0 +1,676 @@
+// C ABI of libhulld: scan objects, validation, memory and launch order.
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "hd_internal.cuh"
+
+namespace {
+
+thread_local char g_last_cuda[256] = "";
+
+void note_cuda(cudaError_t e, const char *where)
+{
+    std::snprintf(g_last_cuda, sizeof(g_last_cuda), "%s: %s (%d)", where, cudaGetErrorString(e),
+                  static_cast<int>(e));
+}
+
+#define HD_CUDA(call)                                  \
+    do {                                               \
+        cudaError_t e_ = (call);                       \
+        if (e_ != cudaSuccess) {                       \
+            note_cuda(e_, #call);                      \
+            return HD_ERR_CUDA;                        \
+        }                                              \
+    } while (0)
+
+// Makes `dev` current for the scope and restores the caller's device.
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = true;
+    explicit DeviceGuard(int dev)
+    {
+        if (cudaGetDevice(&prev) != cudaSuccess) {
+            ok = false;
+            return;
+        }
+        if (prev != dev && cudaSetDevice(dev) != cudaSuccess) ok = false;
+    }
+    ~DeviceGuard()
+    {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+constexpr int64_t kChunk = int64_t(1) << 24;  // histories per internal launch pair
+constexpr int64_t kMaxScanHistories = 4294967295LL;
+
+// theta_i = round(atan(2^-i) * 180/pi * 2^30), K = round(2^30 prod (1 + 2^-2i)^-1/2),
+// evaluated in double; the rounding is accepted only when the value is well
+// away from a half-integer, so the integers do not depend on the libm.
+bool make_cordic(hd::Cordic &c)
+{
+    const double pi = 3.14159265358979323846;
+    for (int i = 0; i < 32; ++i) {
+        const double v = std::atan(std::ldexp(1.0, -i)) * (180.0 / pi) * 1073741824.0;
+        const double f = v - std::floor(v);
+        if (std::fabs(f - 0.5) < 5e-5) return false;
+        c.theta[i] = static_cast<long long>(std::floor(v + 0.5));
+    }
+    double k = 1073741824.0;
+    for (int i = 0; i < 32; ++i) k /= std::sqrt(1.0 + std::ldexp(1.0, -2 * i));
+    const double f = k - std::floor(k);
+    if (std::fabs(f - 0.5) < 1e-3) return false;
+    c.K = static_cast<long long>(std::floor(k + 0.5));
+    return true;
+}
+
+long long q16_host(float x) { return std::llrint(static_cast<double>(x) * 65536.0); }
+
+}  // namespace
+
+struct hd_scan {
+    int device = 0;
+    int sm_count = 0;
+    hd_geometry geom{};
+    hd_params params{};
+    hd::GeomQ gq{};
+    hd::Cordic cordic{};
+    int64_t V = 0;
+    int64_t words = 0;
+    uint32_t *N = nullptr, *M = nullptr, *carve = nullptr;
+    uint8_t *H1 = nullptr, *H2 = nullptr, *H3 = nullptr;
+    uint32_t *bits_out = nullptr;
+    unsigned long long *slice_key = nullptr;
+    uint32_t *mt = nullptr, *slope = nullptr;
+    long long *index = nullptr;
+    hd::Ctrl *ctrl = nullptr;
+    // scratch: traversal records and host staging
+    int32_t *rec_buf = nullptr;
+    int64_t rec_cap = 0;
+    float *staging = nullptr;
+    int64_t staging_cap = 0;
+    uint32_t *compact_blocks = nullptr;
+    unsigned long long *d_count = nullptr;
+    int32_t *compact_out = nullptr;
+    uint64_t n_total = 0;
+    bool finalized = false;
+    // profiling: (phase, start, stop) event triples awaiting readout
+    bool profiling = false;
+    struct Pending { int phase; cudaEvent_t a, b; };
+    std::vector<Pending> pending;
+    std::vector<cudaEvent_t> event_pool;
+    double ms[3] = {0.0, 0.0, 0.0};
+    int64_t launches = 0;
+    int64_t trace_launches = 0;
+};
+
+namespace {
+
+cudaEvent_t take_event(hd_scan *s)
+{
+    if (!s->event_pool.empty()) {
+        cudaEvent_t e = s->event_pool.back();
+        s->event_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return e;
+}
+
+// Records a start event for `phase` on st when profiling; returns the event.
+cudaEvent_t prof_begin(hd_scan *s, cudaStream_t st)
+{
+    if (!s->profiling) return nullptr;
+    cudaEvent_t e = take_event(s);
+    if (e) cudaEventRecord(e, st);
+    return e;
+}
+
+void prof_end(hd_scan *s, int phase, cudaEvent_t a, cudaStream_t st)
+{
+    if (!s->profiling || !a) return;
+    cudaEvent_t b = take_event(s);
+    if (!b) return;
+    cudaEventRecord(b, st);
+    s->pending.push_back({phase, a, b});
+}
+
+void drain_profile(hd_scan *s)
+{
+    for (auto &p : s->pending) {
+        float ms = 0.0f;
+        if (cudaEventSynchronize(p.b) == cudaSuccess && cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess)
+            s->ms[p.phase] += ms;
+        cudaGetLastError();
+        s->event_pool.push_back(p.a);
+        s->event_pool.push_back(p.b);
+    }
+    s->pending.clear();
+}
+
+void free_scan(hd_scan *s)
+{
+    drain_profile(s);
+    for (cudaEvent_t e : s->event_pool) cudaEventDestroy(e);
+    void *ptrs[] = {s->N, s->M, s->carve, s->H1, s->H2, s->H3, s->bits_out, s->slice_key,
+                    s->mt, s->slope, s->index, s->ctrl, s->rec_buf, s->staging,
+                    s->compact_blocks, s->d_count, s->compact_out};
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+    delete s;
+}
+
+hd_status validate(const hd_geometry *g, const hd_params *p)
+{
+    if (!g || !p) return HD_ERR_ARG;
+    const int32_t n[3] = {g->nx, g->ny, g->nz};
+    const float s[3] = {g->sx, g->sy, g->sz};
+    int64_t V = 1;
+    for (int a = 0; a < 3; ++a) {
+        if (n[a] < 1 || n[a] > hd::kMaxN) return HD_ERR_RANGE;
+        if (!(s[a] >= 1.0f / 64.0f && s[a] <= 64.0f)) return HD_ERR_RANGE;
+        if (static_cast<double>(n[a]) * s[a] > 8192.0) return HD_ERR_RANGE;
+        V *= n[a];
+    }
+    if (V > (int64_t(1) << 31) - (int64_t(1) << 26)) return HD_ERR_RANGE;
+    if (!(g->tracker_half_sep_mm > 0.0f && g->tracker_half_sep_mm < 4096.0f)) return HD_ERR_RANGE;
+    if (std::isnan(p->wepl_miss_lt) || std::isnan(p->wepl_hit_gt)) return HD_ERR_ARG;
+    if (p->wepl_miss_lt > p->wepl_hit_gt) return HD_ERR_ARG;
+    if (p->msc_nbhd != 4 && p->msc_nbhd != 6) return HD_ERR_ARG;
+    if (p->sm_ge != 0 && p->sm_ge != 1) return HD_ERR_ARG;
+    if (p->sm_per_slice != 0 && p->sm_per_slice != 1) return HD_ERR_ARG;
+    if (p->methods == 0 || (p->methods & ~uint32_t(HD_SC | HD_MSC | HD_SM))) return HD_ERR_ARG;
+    return HD_OK;
+}
+
+hd_status ensure_records(hd_scan *s, int64_t n, cudaStream_t st)
+{
+    if (n <= s->rec_cap) return HD_OK;
+    HD_CUDA(cudaStreamSynchronize(st));
+    if (s->rec_buf) {
+        cudaFree(s->rec_buf);
+        s->rec_buf = nullptr;
+        s->rec_cap = 0;
+    }
+    if (cudaMalloc(&s->rec_buf, sizeof(int32_t) * 6 * static_cast<size_t>(n)) != cudaSuccess) {
+        cudaGetLastError();
+        s->rec_buf = nullptr;
+        return HD_ERR_NOMEM;
+    }
+    s->rec_cap = n;
+    return HD_OK;
+}
+
+hd_status ensure_staging(hd_scan *s, int64_t n, cudaStream_t st)
+{
+    if (n <= s->staging_cap) return HD_OK;
+    HD_CUDA(cudaStreamSynchronize(st));
+    if (s->staging) {
+        cudaFree(s->staging);
+        s->staging = nullptr;
+        s->staging_cap = 0;
+    }
+    if (cudaMalloc(&s->staging, sizeof(float) * 6 * static_cast<size_t>(n)) != cudaSuccess) {
+        cudaGetLastError();
+        s->staging = nullptr;
+        return HD_ERR_NOMEM;
+    }
+    s->staging_cap = n;
+    return HD_OK;
+}
+
+hd::Records records_of(const hd_scan *s, int64_t n)
+{
+    hd::Records r;
+    for (int a = 0; a < 6; ++a) r.g[a] = s->rec_buf + static_cast<size_t>(a) * n;
+    r.cap = n;
+    return r;
+}
+
+hd_status run_chunk(hd_scan *s, const hd::Inputs &in, int64_t n, cudaStream_t st)
+{
+    const uint32_t m = s->params.methods;
+    const int use_miss = (m & (HD_SC | HD_MSC)) ? 1 : 0;
+    const int use_hit = (m & HD_SM) ? 1 : 0;
+    const hd::Records rec = records_of(s, n);
+    HD_CUDA(cudaMemsetAsync(&s->ctrl->rec_miss, 0, 2 * sizeof(unsigned int), st));
+    cudaEvent_t e0 = prof_begin(s, st);
+    HD_CUDA(hd::launch_ingest(in, n, s->gq, s->cordic, s->params.wepl_miss_lt,
+                              s->params.wepl_hit_gt, use_miss, use_hit, rec, s->ctrl, s->sm_count,
+                              st));
+    s->launches += 1;
+    prof_end(s, 0, e0, st);
+    cudaEvent_t e1 = prof_begin(s, st);
+    HD_CUDA(hd::launch_trace(rec, s->ctrl, s->ctrl, use_miss ? n : 0, use_hit ? n : 0, s->gq,
+                             s->N, s->M, s->carve, s->sm_count, st));
+    s->launches += 1;
+    if (s->profiling) s->trace_launches += 1;
+    prof_end(s, 1, e1, st);
+    return HD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *hd_status_string(hd_status s)
+{
+    switch (s) {
+    case HD_OK: return "HD_OK";
+    case HD_ERR_ARG: return "HD_ERR_ARG";
+    case HD_ERR_RANGE: return "HD_ERR_RANGE";
+    case HD_ERR_NOMEM: return "HD_ERR_NOMEM";
+    case HD_ERR_CUDA: return "HD_ERR_CUDA";
+    case HD_ERR_STATE: return "HD_ERR_STATE";
+    case HD_ERR_TIMEOUT: return "HD_ERR_TIMEOUT";
+    case HD_ERR_ADMISSION: return "HD_ERR_ADMISSION";
+    case HD_ERR_OVERFLOW: return "HD_ERR_OVERFLOW";
+    }
+    return "HD_ERR_UNKNOWN";
+}
+
+const char *hd_last_cuda_error(void) { return g_last_cuda; }
+
+hd_status hd_params_default(hd_params *out)
+{
+    if (!out) return HD_ERR_ARG;
+    out->wepl_miss_lt = 1.0f;
+    out->wepl_hit_gt = 5.0f;
+    out->msc_nt = 50;
+    out->msc_nbhd = 6;
+    out->sm_ge = 1;
+    out->sm_per_slice = 1;
+    out->methods = HD_SC | HD_MSC | HD_SM;
+    return HD_OK;
+}
+
+hd_status hd_scan_create(const hd_geometry *geom, const hd_params *params, hd_scan **out)
+{
+    if (!out) return HD_ERR_ARG;
+    *out = nullptr;
+    const hd_status v = validate(geom, params);
+    if (v != HD_OK) return v;
+    hd_scan *s = new (std::nothrow) hd_scan();
+    if (!s) return HD_ERR_NOMEM;
+    s->geom = *geom;
+    s->params = *params;
+    if (!make_cordic(s->cordic)) {
+        delete s;
+        return HD_ERR_RANGE;
+    }
+    cudaError_t e = cudaGetDevice(&s->device);
+    if (e == cudaSuccess)
+        e = cudaDeviceGetAttribute(&s->sm_count, cudaDevAttrMultiProcessorCount, s->device);
+    if (e != cudaSuccess) {
+        note_cuda(e, "hd_scan_create: device query");
+        delete s;
+        return HD_ERR_CUDA;
+    }
+    s->gq.nx = geom->nx;
+    s->gq.ny = geom->ny;
+    s->gq.nz = geom->nz;
+    s->gq.sx = q16_host(geom->sx);
+    s->gq.sy = q16_host(geom->sy);
+    s->gq.sz = q16_host(geom->sz);
+    s->gq.T = q16_host(geom->tracker_half_sep_mm);
+    s->V = int64_t(geom->nx) * geom->ny * geom->nz;
+    s->words = (s->V + 31) / 32;
+    const uint32_t m = params->methods;
+    const size_t V = static_cast<size_t>(s->V);
+    bool ok = true;
+    auto alloc = [&](void **p, size_t bytes) {
+        if (!ok) return;
+        if (cudaMalloc(p, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            *p = nullptr;
+            ok = false;
+        }
+    };
+    if (m & HD_MSC) alloc(reinterpret_cast<void **>(&s->N), sizeof(uint32_t) * V);
+    if ((m & HD_SC) && !(m & HD_MSC))
+        alloc(reinterpret_cast<void **>(&s->carve), sizeof(uint32_t) * s->words);
+    if (m & HD_SM) {
+        alloc(reinterpret_cast<void **>(&s->M), sizeof(uint32_t) * V);
+        alloc(reinterpret_cast<void **>(&s->slice_key), sizeof(unsigned long long) * geom->nz);
+        alloc(reinterpret_cast<void **>(&s->mt), sizeof(uint32_t) * geom->nz);
+        alloc(reinterpret_cast<void **>(&s->slope), sizeof(uint32_t) * geom->nz);
+        alloc(reinterpret_cast<void **>(&s->index), sizeof(long long) * geom->nz);
+        alloc(reinterpret_cast<void **>(&s->H3), V);
+    }
+    if (m & HD_SC) alloc(reinterpret_cast<void **>(&s->H1), V);
+    if (m & HD_MSC) alloc(reinterpret_cast<void **>(&s->H2), V);
+    alloc(reinterpret_cast<void **>(&s->bits_out), sizeof(uint32_t) * s->words);
+    alloc(reinterpret_cast<void **>(&s->ctrl), sizeof(hd::Ctrl));
+    if (!ok) {
+        free_scan(s);
+        return HD_ERR_NOMEM;
+    }
+    const hd_status r = hd_scan_reset(s, nullptr);
+    if (r == HD_OK) e = cudaStreamSynchronize(nullptr);
+    if (r != HD_OK || e != cudaSuccess) {
+        if (e != cudaSuccess) note_cuda(e, "hd_scan_create: sync");
+        free_scan(s);
+        return r != HD_OK ? r : HD_ERR_CUDA;
+    }
+    *out = s;
+    return HD_OK;
+}
+
+hd_status hd_scan_destroy(hd_scan *scan)
+{
+    if (!scan) return HD_OK;
+    DeviceGuard g(scan->device);
+    cudaDeviceSynchronize();
+    free_scan(scan);
+    return HD_OK;
+}
+
+hd_status hd_scan_reset(hd_scan *scan, void *stream)
+{
+    if (!scan) return HD_ERR_ARG;
+    DeviceGuard g(scan->device);
+    if (!g.ok) return HD_ERR_CUDA;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const size_t V = static_cast<size_t>(scan->V);
+    if (scan->N) HD_CUDA(cudaMemsetAsync(scan->N, 0, sizeof(uint32_t) * V, st));
+    if (scan->M) HD_CUDA(cudaMemsetAsync(scan->M, 0, sizeof(uint32_t) * V, st));
+    if (scan->carve) HD_CUDA(cudaMemsetAsync(scan->carve, 0xff, sizeof(uint32_t) * scan->words, st));
+    HD_CUDA(cudaMemsetAsync(scan->ctrl, 0, sizeof(hd::Ctrl), st));
+    scan->n_total = 0;
+    scan->finalized = false;
+    return HD_OK;
+}
+
+hd_status hd_scan_add_histories(hd_scan *scan, const float *angle_deg, const float *u_in,
+                                const float *v_in, const float *u_out, const float *v_out,
+                                const float *wepl, int64_t n, int32_t on_device, void *stream)
+{
+    if (!scan || n < 0) return HD_ERR_ARG;
+    if (n == 0) return HD_OK;
+    if (!angle_deg || !u_in || !v_in || !u_out || !v_out || !wepl) return HD_ERR_ARG;
+    if (static_cast<uint64_t>(n) > static_cast<uint64_t>(kMaxScanHistories) - scan->n_total)
+        return HD_ERR_OVERFLOW;
+    DeviceGuard g(scan->device);
+    if (!g.ok) return HD_ERR_CUDA;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const int64_t chunk = n < kChunk ? n : kChunk;
+    hd_status r = ensure_records(scan, chunk, st);
+    if (r != HD_OK) return r;
+    if (!on_device) {
+        r = ensure_staging(scan, chunk, st);
+        if (r != HD_OK) return r;
+    }
+    const float *src[6] = {angle_deg, u_in, v_in, u_out, v_out, wepl};
+    for (int64_t off = 0; off < n; off += chunk) {
+        const int64_t c = (n - off) < chunk ? (n - off) : chunk;
+        hd::Inputs in;
+        const float **dst[6] = {&in.angle, &in.u_in, &in.v_in, &in.u_out, &in.v_out, &in.wepl};
+        for (int a = 0; a < 6; ++a) {
+            if (on_device) {
+                *dst[a] = src[a] + off;
+            } else {
+                float *d = scan->staging + static_cast<size_t>(a) * scan->staging_cap;
+                HD_CUDA(cudaMemcpyAsync(d, src[a] + off, sizeof(float) * c,
+                                        cudaMemcpyHostToDevice, st));
+                *dst[a] = d;
+            }
+        }
+        r = run_chunk(scan, in, c, st);
+        if (r != HD_OK) return r;
+    }
+    scan->n_total += static_cast<uint64_t>(n);
+    scan->finalized = false;
+    return HD_OK;
+}
+
+hd_status hd_scan_finalize(hd_scan *scan, void *stream)
+{
+    if (!scan) return HD_ERR_ARG;
+    DeviceGuard g(scan->device);
+    if (!g.ok) return HD_ERR_CUDA;
+    hd::DecideArgs a{};
+    a.nx = scan->geom.nx;
+    a.ny = scan->geom.ny;
+    a.nz = scan->geom.nz;
+    a.methods = static_cast<int32_t>(scan->params.methods);
+    a.nt = scan->params.msc_nt;
+    a.nbhd = scan->params.msc_nbhd;
+    a.sm_ge = scan->params.sm_ge;
+    a.sm_per_slice = scan->params.sm_per_slice;
+    a.N = scan->N;
+    a.M = scan->M;
+    a.carve = scan->carve;
+    a.slice_key = scan->slice_key;
+    a.mt = scan->mt;
+    a.slope = scan->slope;
+    a.index = scan->index;
+    a.H1 = scan->H1;
+    a.H2 = scan->H2;
+    a.H3 = scan->H3;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaEvent_t e0 = prof_begin(scan, st);
+    HD_CUDA(hd::launch_finalize(a, scan->sm_count, st));
+    scan->launches += (scan->params.methods & HD_SM) ? 3 : 1;
+    prof_end(scan, 2, e0, st);
+    scan->finalized = true;
+    return HD_OK;
+}
+
+static uint8_t *mask_of(hd_scan *s, int32_t method)
+{
+    switch (method) {
+    case HD_SC: return s->H1;
+    case HD_MSC: return s->H2;
+    case HD_SM: return s->H3;
+    default: return nullptr;
+    }
+}
+
+hd_status hd_scan_get_mask(hd_scan *scan, int32_t method, int32_t layout, void *dst,
+                           size_t dst_bytes, int32_t dst_on_device, void *stream)
+{
+    if (!scan || !dst) return HD_ERR_ARG;
+    if (method != HD_SC && method != HD_MSC && method != HD_SM) return HD_ERR_ARG;
+    if (layout != HD_MASK_U8 && layout != HD_MASK_BITS) return HD_ERR_ARG;
+    if (!(scan->params.methods & static_cast<uint32_t>(method)) || !scan->finalized)
+        return HD_ERR_STATE;
+    uint8_t *src = mask_of(scan, method);
+    const size_t need = layout == HD_MASK_U8 ? static_cast<size_t>(scan->V)
+                                             : sizeof(uint32_t) * static_cast<size_t>(scan->words);
+    if (dst_bytes < need) return HD_ERR_ARG;
+    DeviceGuard g(scan->device);
+    if (!g.ok) return HD_ERR_CUDA;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const cudaMemcpyKind kind = dst_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    if (layout == HD_MASK_U8) {
+        HD_CUDA(cudaMemcpyAsync(dst, src, need, kind, st));
+    } else {
+        uint32_t *bits = dst_on_device ? static_cast<uint32_t *>(dst) : scan->bits_out;
+        HD_CUDA(hd::launch_pack_bits(src, scan->V, bits, st));
+        if (!dst_on_device) HD_CUDA(cudaMemcpyAsync(dst, bits, need, kind, st));
+    }
+    return HD_OK;
+}
+
+hd_status hd_scan_get_counts(hd_scan *scan, int32_t method, uint32_t *dst, int64_t n,
+                             int32_t dst_on_device, void *stream)
+{
+    if (!scan || !dst) return HD_ERR_ARG;
+    const uint32_t *src = nullptr;
+    if (method == HD_MSC || method == HD_SC) src = scan->N;
+    else if (method == HD_SM) src = scan->M;
+    else return HD_ERR_ARG;
+    if (!src) return HD_ERR_STATE;
+    if (n < scan->V) return HD_ERR_ARG;
+    DeviceGuard g(scan->device);
+    if (!g.ok) return HD_ERR_CUDA;
+    HD_CUDA(cudaMemcpyAsync(dst, src, sizeof(uint32_t) * static_cast<size_t>(scan->V),
+                            dst_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                            static_cast<cudaStream_t>(stream)));
+    return HD_OK;
+}
+
+hd_status hd_scan_get_thresholds(hd_scan *scan, uint32_t *mt, uint32_t *slope, int64_t *index,
+                                 int32_t nz, void *stream)
+{
+    if (!scan) return HD_ERR_ARG;
+    if (!(scan->params.methods & HD_SM) || !scan->finalized) return HD_ERR_STATE;
+    if (nz < scan->geom.nz) return HD_ERR_ARG;
+    DeviceGuard g(scan->device);
+    if (!g.ok) return HD_ERR_CUDA;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const size_t z = static_cast<size_t>(scan->geom.nz);
+    if (mt) HD_CUDA(cudaMemcpyAsync(mt, scan->mt, 4 * z, cudaMemcpyDeviceToHost, st));
+    if (slope) HD_CUDA(cudaMemcpyAsync(slope, scan->slope, 4 * z, cudaMemcpyDeviceToHost, st));
+    if (index) HD_CUDA(cudaMemcpyAsync(index, scan->index, 8 * z, cudaMemcpyDeviceToHost, st));
+    HD_CUDA(cudaStreamSynchronize(st));
+    return HD_OK;
+}
+
+hd_status hd_scan_get_stats(hd_scan *scan, hd_stats *out, void *stream)
+{
+    if (!scan || !out) return HD_ERR_ARG;
+    DeviceGuard g(scan->device);
+    if (!g.ok) return HD_ERR_CUDA;
+    hd::Ctrl c;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    HD_CUDA(cudaMemcpyAsync(&c, scan->ctrl, sizeof(c), cudaMemcpyDeviceToHost, st));
+    HD_CUDA(cudaStreamSynchronize(st));
+    out->n_in = static_cast<int64_t>(c.n_in);
+    out->n_miss = static_cast<int64_t>(c.n_miss);
+    out->n_hit = static_cast<int64_t>(c.n_hit);
+    out->n_none = static_cast<int64_t>(c.n_none);
+    out->n_reject = static_cast<int64_t>(c.n_reject);
+    out->steps_miss = static_cast<int64_t>(c.steps_miss);
+    out->steps_hit = static_cast<int64_t>(c.steps_hit);
+    return HD_OK;
+}
+
+hd_status hd_scan_get_hull_indices(hd_scan *scan, int32_t method, int32_t *dst,
+                                   int64_t capacity, int64_t *count, int32_t dst_on_device,
+                                   void *stream)
+{
+    if (!scan || !count || capacity < 0 || (capacity > 0 && !dst)) return HD_ERR_ARG;
+    if (method != HD_SC && method != HD_MSC && method != HD_SM) return HD_ERR_ARG;
+    if (!(scan->params.methods & static_cast<uint32_t>(method)) || !scan->finalized)
+        return HD_ERR_STATE;
+    DeviceGuard g(scan->device);
+    if (!g.ok) return HD_ERR_CUDA;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const int64_t nb = (scan->V + 1023) / 1024;
+    if (!scan->compact_blocks) {
+        if (cudaMalloc(&scan->compact_blocks, sizeof(uint32_t) * (nb + 1)) != cudaSuccess ||
+            cudaMalloc(&scan->d_count, sizeof(unsigned long long)) != cudaSuccess) {
+            cudaGetLastError();
+            return HD_ERR_NOMEM;
+        }
+    }
+    int32_t *out = dst;
+    int64_t cap = capacity;
+    if (!dst_on_device) {
+        if (!scan->compact_out &&
+            cudaMalloc(&scan->compact_out, sizeof(int32_t) * static_cast<size_t>(scan->V)) !=
+                cudaSuccess) {
+            cudaGetLastError();
+            scan->compact_out = nullptr;
+            return HD_ERR_NOMEM;
+        }
+        out = scan->compact_out;
+        cap = scan->V;
+    }
+    HD_CUDA(hd::launch_compact(mask_of(scan, method), scan->V, out, cap, scan->compact_blocks,
+                               scan->d_count, st));
+    unsigned long long total = 0;
+    HD_CUDA(cudaMemcpyAsync(&total, scan->d_count, sizeof(total), cudaMemcpyDeviceToHost, st));
+    HD_CUDA(cudaStreamSynchronize(st));
+    *count = static_cast<int64_t>(total);
+    if (!dst_on_device && capacity > 0) {
+        const int64_t k = static_cast<int64_t>(total) < capacity ? static_cast<int64_t>(total)
+                                                                 : capacity;
+        if (k > 0) {
+            HD_CUDA(cudaMemcpyAsync(dst, out, sizeof(int32_t) * static_cast<size_t>(k),
+                                    cudaMemcpyDeviceToHost, st));
+            HD_CUDA(cudaStreamSynchronize(st));
+        }
+    }
+    return HD_OK;
+}
+
+hd_status hd_scan_set_profiling(hd_scan *scan, int32_t enable)
+{
+    if (!scan) return HD_ERR_ARG;
+    DeviceGuard g(scan->device);
+    if (!g.ok) return HD_ERR_CUDA;
+    drain_profile(scan);
+    if (enable) {
+        scan->ms[0] = scan->ms[1] = scan->ms[2] = 0.0;
+        scan->trace_launches = 0;
+    }
+    scan->profiling = enable != 0;
+    return HD_OK;
+}
+
+hd_status hd_scan_get_profile(hd_scan *scan, hd_profile *out)
+{
+    if (!scan || !out) return HD_ERR_ARG;
+    DeviceGuard g(scan->device);
+    if (!g.ok) return HD_ERR_CUDA;
+    drain_profile(scan);
+    out->kernel_launches = scan->launches;
+    out->trace_launches = scan->trace_launches;
+    out->ms_ingest = scan->ms[0];
+    out->ms_trace = scan->ms[1];
+    out->ms_finalize = scan->ms[2];
+    return HD_OK;
+}
+
+hd_status hd_classify(const float *wepl, int64_t n, const hd_params *params, uint8_t *cls_out,
+                      int32_t on_device, void *stream)
+{
+    if (!params || n < 0) return HD_ERR_ARG;
+    if (n == 0) return HD_OK;
+    if (!wepl || !cls_out) return HD_ERR_ARG;
+    if (std::isnan(params->wepl_miss_lt) || std::isnan(params->wepl_hit_gt) ||
+        params->wepl_miss_lt > params->wepl_hit_gt)
+        return HD_ERR_ARG;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (on_device) {
+        HD_CUDA(hd::launch_classify(wepl, n, params->wepl_miss_lt, params->wepl_hit_gt, cls_out,
+                                    st));
+        return HD_OK;
+    }
+    float *dw = nullptr;
+    uint8_t *dc = nullptr;
+    if (cudaMalloc(&dw, sizeof(float) * static_cast<size_t>(n)) != cudaSuccess ||
+        cudaMalloc(&dc, static_cast<size_t>(n)) != cudaSuccess) {
+        cudaGetLastError();
+        if (dw) cudaFree(dw);
+        return HD_ERR_NOMEM;
+    }
+    hd_status r = HD_OK;
+    cudaError_t e = cudaMemcpyAsync(dw, wepl, sizeof(float) * static_cast<size_t>(n),
+                                    cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+        e = hd::launch_classify(dw, n, params->wepl_miss_lt, params->wepl_hit_gt, dc, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(cls_out, dc, static_cast<size_t>(n), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+        note_cuda(e, "hd_classify");
+        r = HD_ERR_CUDA;
+    }
+    cudaFree(dw);
+    cudaFree(dc);
+    return r;
+}
+
+}  // extern "C"

@@ -1,0 +1,373 @@
+"""Python binding of libhulld (ctypes), same names as the C ABI in hulld.h.
+
+Argument marshalling only: every step of the hull-detection path runs in the
+library's CUDA kernels.  Buffers may be torch CUDA tensors (passed as device
+pointers) or numpy arrays (host pointers); streams are torch.cuda.Stream
+objects, raw cudaStream_t integers, or None for the current torch stream
+(the legacy default stream when torch is not in use).
+If the library has not been built, loading fails loudly; there is no
+fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import threading
+from pathlib import Path
+from typing import Optional, Sequence
+
+import numpy as np
+
+_LIB_PATH = Path(__file__).resolve().parent / "_lib" / "libhulld.so"
+_lib = None
+_lock = threading.Lock()
+
+HD_OK, HD_ERR_ARG, HD_ERR_RANGE, HD_ERR_NOMEM, HD_ERR_CUDA = 0, 1, 2, 3, 4
+HD_ERR_STATE, HD_ERR_TIMEOUT, HD_ERR_ADMISSION, HD_ERR_OVERFLOW = 5, 6, 7, 8
+HD_SC, HD_MSC, HD_SM = 1, 2, 4
+HD_MASK_U8, HD_MASK_BITS = 0, 1
+
+
+class HDError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        lib = _lib
+        name = lib.hd_status_string(status).decode() if lib else str(status)
+        cuda = lib.hd_last_cuda_error().decode() if lib else ""
+        super().__init__(f"{where}: {name}" + (f" [{cuda}]" if cuda and status == HD_ERR_CUDA else ""))
+
+
+class hd_geometry(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nz", ctypes.c_int32),
+                ("sx", ctypes.c_float), ("sy", ctypes.c_float), ("sz", ctypes.c_float),
+                ("tracker_half_sep_mm", ctypes.c_float)]
+
+
+class hd_params(ctypes.Structure):
+    _fields_ = [("wepl_miss_lt", ctypes.c_float), ("wepl_hit_gt", ctypes.c_float),
+                ("msc_nt", ctypes.c_int32), ("msc_nbhd", ctypes.c_int32),
+                ("sm_ge", ctypes.c_int32), ("sm_per_slice", ctypes.c_int32),
+                ("methods", ctypes.c_uint32)]
+
+
+class hd_stats(ctypes.Structure):
+    _fields_ = [("n_in", ctypes.c_int64), ("n_miss", ctypes.c_int64), ("n_hit", ctypes.c_int64),
+                ("n_none", ctypes.c_int64), ("n_reject", ctypes.c_int64),
+                ("steps_miss", ctypes.c_int64), ("steps_hit", ctypes.c_int64)]
+
+    def as_dict(self):
+        return {k: int(getattr(self, k)) for k, _ in self._fields_}
+
+
+class hd_profile(ctypes.Structure):
+    _fields_ = [("kernel_launches", ctypes.c_int64), ("trace_launches", ctypes.c_int64),
+                ("ms_ingest", ctypes.c_double), ("ms_trace", ctypes.c_double),
+                ("ms_finalize", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+# exported symbols and their signatures
+_VP, _I32, _I64, _SZ = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_size_t
+_SIGS = {
+    "hd_status_string": ([ctypes.c_int], ctypes.c_char_p),
+    "hd_last_cuda_error": ([], ctypes.c_char_p),
+    "hd_params_default": ([ctypes.POINTER(hd_params)], ctypes.c_int),
+    "hd_scan_create": ([ctypes.POINTER(hd_geometry), ctypes.POINTER(hd_params),
+                        ctypes.POINTER(_VP)], ctypes.c_int),
+    "hd_scan_destroy": ([_VP], ctypes.c_int),
+    "hd_scan_reset": ([_VP, _VP], ctypes.c_int),
+    "hd_scan_add_histories": ([_VP] + [_VP] * 6 + [_I64, _I32, _VP], ctypes.c_int),
+    "hd_scan_finalize": ([_VP, _VP], ctypes.c_int),
+    "hd_scan_get_mask": ([_VP, _I32, _I32, _VP, _SZ, _I32, _VP], ctypes.c_int),
+    "hd_scan_get_counts": ([_VP, _I32, _VP, _I64, _I32, _VP], ctypes.c_int),
+    "hd_scan_get_thresholds": ([_VP, _VP, _VP, _VP, _I32, _VP], ctypes.c_int),
+    "hd_scan_get_stats": ([_VP, ctypes.POINTER(hd_stats), _VP], ctypes.c_int),
+    "hd_scan_get_hull_indices": ([_VP, _I32, _VP, _I64, ctypes.POINTER(_I64), _I32, _VP],
+                                 ctypes.c_int),
+    "hd_classify": ([_VP, _I64, ctypes.POINTER(hd_params), _VP, _I32, _VP], ctypes.c_int),
+    "hd_scan_set_profiling": ([_VP, _I32], ctypes.c_int),
+    "hd_scan_get_profile": ([_VP, ctypes.POINTER(hd_profile)], ctypes.c_int),
+}
+
+
+def exported_names() -> Sequence[str]:
+    return list(_SIGS)
+
+
+def lib_path() -> Path:
+    return _LIB_PATH
+
+
+def load():
+    """Load libhulld.so (built by paper_1402_1720_gb300.build); raises if absent."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not _LIB_PATH.exists():
+                raise RuntimeError(f"libhulld.so not built ({_LIB_PATH}); run "
+                                   "paper_1402_1720_gb300.build.build() first")
+            L = ctypes.CDLL(str(_LIB_PATH))
+            for name, (args, res) in _SIGS.items():
+                f = getattr(L, name)
+                f.argtypes = args
+                f.restype = res
+            _lib = L
+    return _lib
+
+
+def _check(status: int, where: str):
+    if status != HD_OK:
+        raise HDError(status, where)
+
+
+# ---------------------------------------------------------- marshalling
+def _is_torch(x) -> bool:
+    return type(x).__module__.startswith("torch")
+
+
+def _ptr(x):
+    """(address, on_device) of a torch tensor or numpy array (contiguous)."""
+    if _is_torch(x):
+        if not x.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return x.data_ptr(), 1 if x.is_cuda else 0
+    if isinstance(x, np.ndarray):
+        if not x.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return x.ctypes.data, 0
+    raise TypeError(f"unsupported buffer type {type(x)}")
+
+
+def _stream(stream) -> int:
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available() and torch.cuda.is_initialized():
+                return torch.cuda.current_stream().cuda_stream
+        except Exception:
+            pass
+        return 0
+    if isinstance(stream, int):
+        return stream
+    return int(stream.cuda_stream)
+
+
+def _geometry(g) -> hd_geometry:
+    if isinstance(g, hd_geometry):
+        return g
+    return hd_geometry(int(g.nx), int(g.ny), int(g.nz), float(g.sx), float(g.sy), float(g.sz),
+                       float(getattr(g, "tracker_half_sep_mm", getattr(g, "T", 0.0))))
+
+
+def _params(p) -> hd_params:
+    if p is None:
+        return hd_params_default()
+    if isinstance(p, hd_params):
+        return p
+    return hd_params(float(p.tau_l), float(p.tau_h), int(p.nt), int(p.nbhd), int(p.sm_ge),
+                     int(p.sm_per_slice), int(p.methods))
+
+
+# --------------------------------------------------- C-ABI, same names
+def hd_status_string(status: int) -> str:
+    return load().hd_status_string(status).decode()
+
+
+def hd_last_cuda_error() -> str:
+    return load().hd_last_cuda_error().decode()
+
+
+def hd_params_default() -> hd_params:
+    p = hd_params()
+    _check(load().hd_params_default(ctypes.byref(p)), "hd_params_default")
+    return p
+
+
+def hd_scan_create(geometry, params=None) -> int:
+    h = _VP()
+    g = _geometry(geometry)
+    p = _params(params)
+    _check(load().hd_scan_create(ctypes.byref(g), ctypes.byref(p), ctypes.byref(h)),
+           "hd_scan_create")
+    return h.value
+
+
+def hd_scan_destroy(scan: int) -> None:
+    _check(load().hd_scan_destroy(scan), "hd_scan_destroy")
+
+
+def hd_scan_reset(scan: int, stream=None) -> None:
+    _check(load().hd_scan_reset(scan, _stream(stream)), "hd_scan_reset")
+
+
+def hd_scan_add_histories(scan: int, angle_deg, u_in, v_in, u_out, v_out, wepl,
+                          stream=None) -> None:
+    arrs = [angle_deg, u_in, v_in, u_out, v_out, wepl]
+    ptrs = [_ptr(a) for a in arrs]
+    ons = {o for _, o in ptrs}
+    if len(ons) != 1:
+        raise ValueError("all six arrays must be on the device or all on the host")
+    n = len(arrs[0])
+    for a in arrs:
+        if len(a) != n:
+            raise ValueError("arrays differ in length")
+        dt = str(a.dtype)
+        if dt not in ("float32", "torch.float32"):
+            raise TypeError("history arrays must be float32")
+    _check(load().hd_scan_add_histories(scan, *[p for p, _ in ptrs], n, ons.pop(),
+                                        _stream(stream)), "hd_scan_add_histories")
+
+
+def hd_scan_finalize(scan: int, stream=None) -> None:
+    _check(load().hd_scan_finalize(scan, _stream(stream)), "hd_scan_finalize")
+
+
+def hd_scan_get_mask(scan: int, method: int, layout: int, dst, stream=None) -> None:
+    p, on = _ptr(dst)
+    nbytes = dst.numel() * dst.element_size() if _is_torch(dst) else dst.nbytes
+    _check(load().hd_scan_get_mask(scan, method, layout, p, nbytes, on, _stream(stream)),
+           "hd_scan_get_mask")
+
+
+def hd_scan_get_counts(scan: int, method: int, dst, stream=None) -> None:
+    p, on = _ptr(dst)
+    n = dst.numel() if _is_torch(dst) else dst.size
+    _check(load().hd_scan_get_counts(scan, method, p, n, on, _stream(stream)),
+           "hd_scan_get_counts")
+
+
+def hd_scan_get_thresholds(scan: int, nz: int, stream=None):
+    mt = np.zeros(nz, np.uint32)
+    slope = np.zeros(nz, np.uint32)
+    index = np.zeros(nz, np.int64)
+    _check(load().hd_scan_get_thresholds(scan, mt.ctypes.data, slope.ctypes.data,
+                                         index.ctypes.data, nz, _stream(stream)),
+           "hd_scan_get_thresholds")
+    return mt, slope, index
+
+
+def hd_scan_get_stats(scan: int, stream=None) -> dict:
+    st = hd_stats()
+    _check(load().hd_scan_get_stats(scan, ctypes.byref(st), _stream(stream)),
+           "hd_scan_get_stats")
+    return st.as_dict()
+
+
+def hd_scan_get_hull_indices(scan: int, method: int, dst=None, stream=None):
+    """Returns (count, dst); with dst None a host int32 array is allocated."""
+    count = _I64()
+    if dst is None:
+        # query the size first, then fetch
+        _check(load().hd_scan_get_hull_indices(scan, method, None, 0, ctypes.byref(count), 0,
+                                               _stream(stream)), "hd_scan_get_hull_indices")
+        dst = np.zeros(max(1, count.value), np.int32)
+    p, on = _ptr(dst)
+    cap = dst.numel() if _is_torch(dst) else dst.size
+    _check(load().hd_scan_get_hull_indices(scan, method, p, cap, ctypes.byref(count), on,
+                                           _stream(stream)), "hd_scan_get_hull_indices")
+    return count.value, dst
+
+
+def hd_scan_set_profiling(scan: int, enable: bool) -> None:
+    _check(load().hd_scan_set_profiling(scan, 1 if enable else 0), "hd_scan_set_profiling")
+
+
+def hd_scan_get_profile(scan: int) -> dict:
+    p = hd_profile()
+    _check(load().hd_scan_get_profile(scan, ctypes.byref(p)), "hd_scan_get_profile")
+    return p.as_dict()
+
+
+def hd_classify(wepl, params=None, cls_out=None, stream=None):
+    p = _params(params)
+    wp, on = _ptr(wepl)
+    n = wepl.numel() if _is_torch(wepl) else wepl.size
+    if cls_out is None:
+        if on:
+            import torch
+            cls_out = torch.empty(n, dtype=torch.uint8, device=wepl.device)
+        else:
+            cls_out = np.zeros(n, np.uint8)
+    cp, con = _ptr(cls_out)
+    if con != on:
+        raise ValueError("wepl and cls_out must both be device or both host buffers")
+    _check(load().hd_classify(wp, n, ctypes.byref(p), cp, on, _stream(stream)), "hd_classify")
+    return cls_out
+
+
+# ------------------------------------------------------------- wrapper
+class Scan:
+    """Owning handle of one hd_scan."""
+
+    def __init__(self, geometry, params=None):
+        self.geometry = geometry
+        self.params = _params(params)
+        self.handle = hd_scan_create(geometry, self.params)
+        g = _geometry(geometry)
+        self.dims = (g.nx, g.ny, g.nz)
+        self.V = g.nx * g.ny * g.nz
+
+    def close(self):
+        if self.handle:
+            hd_scan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def reset(self, stream=None):
+        hd_scan_reset(self.handle, stream)
+
+    def add(self, hist_arrays: Sequence, stream=None):
+        hd_scan_add_histories(self.handle, *hist_arrays, stream=stream)
+
+    def finalize(self, stream=None):
+        hd_scan_finalize(self.handle, stream)
+
+    def mask(self, method: int, layout: int = HD_MASK_U8, out=None, stream=None):
+        if out is None:
+            n = self.V if layout == HD_MASK_U8 else 4 * ((self.V + 31) // 32)
+            out = np.zeros(n if layout == HD_MASK_U8 else n // 4,
+                           np.uint8 if layout == HD_MASK_U8 else np.uint32)
+        hd_scan_get_mask(self.handle, method, layout, out, stream)
+        if not _is_torch(out):
+            self.sync(stream)
+        return out
+
+    def counts(self, method: int, out=None, stream=None):
+        if out is None:
+            out = np.zeros(self.V, np.uint32)
+        hd_scan_get_counts(self.handle, method, out, stream)
+        if not _is_torch(out):
+            self.sync(stream)
+        return out
+
+    def thresholds(self, stream=None):
+        return hd_scan_get_thresholds(self.handle, self.dims[2], stream)
+
+    def stats(self, stream=None):
+        return hd_scan_get_stats(self.handle, stream)
+
+    def hull_indices(self, method: int, dst=None, stream=None):
+        return hd_scan_get_hull_indices(self.handle, method, dst, stream)
+
+    def set_profiling(self, enable: bool):
+        hd_scan_set_profiling(self.handle, enable)
+
+    def profile(self) -> dict:
+        return hd_scan_get_profile(self.handle)
+
+    def sync(self, stream=None):
+        # D2H copies into pageable numpy memory are complete when the call
+        # returns; pinned destinations need a stream sync, done via stats
+        hd_scan_get_stats(self.handle, stream)
