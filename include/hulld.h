@@ -126,9 +126,10 @@ typedef struct {
 typedef struct {
     int64_t kernel_launches;  /* kernels launched by this scan since create */
     int64_t trace_launches;   /* traversal kernel launches (profiled window) */
-    double ms_ingest;         /* classification + geometry + compaction */
-    double ms_trace;          /* voxel traversal and accumulation */
+    double ms_ingest;         /* classification, geometry, bucketing by tile */
+    double ms_trace;          /* voxel traversal and accumulation (shared-memory tiles) */
     double ms_finalize;       /* decisions (H_1, H_2, M_t, H_3) */
+    double ms_trace_global;   /* traversal of records outside the tiled path */
 } hd_profile;
 
 typedef struct hd_scan hd_scan;

@@ -2,11 +2,12 @@
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
+#include <cstddef>
 #include <cstring>
 #include <new>
 #include <vector>
 
-#include "hd_internal.cuh"
+#include "hd_geom.cuh"
 
 namespace {
 
@@ -48,6 +49,7 @@ struct DeviceGuard {
 
 constexpr int64_t kChunk = int64_t(1) << 24;  // histories per internal launch pair
 constexpr int64_t kMaxScanHistories = 4294967295LL;
+constexpr int kTileSmemBytes = 200 * 1024;  // shared memory per block for a private tile
 
 // theta_i = round(atan(2^-i) * 180/pi * 2^30), K = round(2^30 prod (1 + 2^-2i)^-1/2),
 // evaluated in double; the rounding is accepted only when the value is well
@@ -69,7 +71,6 @@ bool make_cordic(hd::Cordic &c)
     return true;
 }
 
-long long q16_host(float x) { return std::llrint(static_cast<double>(x) * 65536.0); }
 
 }  // namespace
 
@@ -89,9 +90,16 @@ struct hd_scan {
     uint32_t *mt = nullptr, *slope = nullptr;
     long long *index = nullptr;
     hd::Ctrl *ctrl = nullptr;
-    // scratch: traversal records and host staging
-    int32_t *rec_buf = nullptr;
+    // scratch: traversal records, (record, tile) pairs, jobs, host staging
+    hd::TilePlan tp{};
+    int trace_grid = 0;
+    int32_t *rec_buf = nullptr;   // 7 int32 arrays of rec_cap (6 coordinates + status)
     int64_t rec_cap = 0;
+    uint32_t *pair_buf = nullptr;  // hd::kPackedWords arrays of tp.pair_cap
+    hd::TileJob *jobs = nullptr;
+    int64_t job_cap = 0;
+    uint32_t *tile_count = nullptr;   // 2 * ntiles
+    uint32_t *tile_cursor = nullptr;  // 2 * ntiles
     float *staging = nullptr;
     int64_t staging_cap = 0;
     uint32_t *compact_blocks = nullptr;
@@ -104,7 +112,7 @@ struct hd_scan {
     struct Pending { int phase; cudaEvent_t a, b; };
     std::vector<Pending> pending;
     std::vector<cudaEvent_t> event_pool;
-    double ms[3] = {0.0, 0.0, 0.0};
+    double ms[4] = {0.0, 0.0, 0.0, 0.0};
     int64_t launches = 0;
     int64_t trace_launches = 0;
 };
@@ -163,7 +171,8 @@ void free_scan(hd_scan *s)
     for (cudaEvent_t e : s->event_pool) cudaEventDestroy(e);
     void *ptrs[] = {s->N, s->M, s->carve, s->H1, s->H2, s->H3, s->bits_out, s->slice_key,
                     s->mt, s->slope, s->index, s->ctrl, s->rec_buf, s->staging,
-                    s->compact_blocks, s->d_count, s->compact_out};
+                    s->compact_blocks, s->d_count, s->compact_out, s->pair_buf, s->jobs,
+                    s->tile_count, s->tile_cursor};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     delete s;
@@ -192,18 +201,37 @@ hd_status validate(const hd_geometry *g, const hd_params *p)
     return HD_OK;
 }
 
+// Pairs of a chunk of n records: typical paths touch one or two tiles; a
+// record that does not fit the pair budget takes the global-memory path.
+constexpr int64_t kPairsPerRecord = 2;
+
 hd_status ensure_records(hd_scan *s, int64_t n, cudaStream_t st)
 {
     if (n <= s->rec_cap) return HD_OK;
     HD_CUDA(cudaStreamSynchronize(st));
-    if (s->rec_buf) {
-        cudaFree(s->rec_buf);
-        s->rec_buf = nullptr;
-        s->rec_cap = 0;
+    if (s->rec_buf) cudaFree(s->rec_buf);
+    if (s->pair_buf) cudaFree(s->pair_buf);
+    if (s->jobs) cudaFree(s->jobs);
+    s->rec_buf = nullptr;
+    s->pair_buf = nullptr;
+    s->jobs = nullptr;
+    s->rec_cap = 0;
+    bool ok = cudaMalloc(&s->rec_buf, sizeof(int32_t) * 7 * static_cast<size_t>(n)) == cudaSuccess;
+    if (ok && s->tp.ntiles > 0) {
+        const int64_t pair_cap = kPairsPerRecord * n;
+        const int64_t job_cap = pair_cap / s->tp.job_size + 2 * s->tp.ntiles + 1;
+        ok = cudaMalloc(&s->pair_buf, sizeof(uint32_t) * 16 * static_cast<size_t>(pair_cap)) ==
+                 cudaSuccess &&
+             cudaMalloc(&s->jobs, sizeof(hd::TileJob) * static_cast<size_t>(job_cap)) == cudaSuccess;
+        s->tp.pair_cap = pair_cap;
+        s->job_cap = job_cap;
     }
-    if (cudaMalloc(&s->rec_buf, sizeof(int32_t) * 6 * static_cast<size_t>(n)) != cudaSuccess) {
+    if (!ok) {
         cudaGetLastError();
+        if (s->rec_buf) cudaFree(s->rec_buf);
+        if (s->pair_buf) cudaFree(s->pair_buf);
         s->rec_buf = nullptr;
+        s->pair_buf = nullptr;
         return HD_ERR_NOMEM;
     }
     s->rec_cap = n;
@@ -232,8 +260,60 @@ hd::Records records_of(const hd_scan *s, int64_t n)
 {
     hd::Records r;
     for (int a = 0; a < 6; ++a) r.g[a] = s->rec_buf + static_cast<size_t>(a) * n;
+    r.status = s->rec_buf + static_cast<size_t>(6) * n;
     r.cap = n;
     return r;
+}
+
+hd::Pairs pairs_of(const hd_scan *s)
+{
+    hd::Pairs p;
+    p.v = reinterpret_cast<uint4 *>(s->pair_buf);
+    return p;
+}
+
+// Tiles: one or more z-slices of the full x-y plane when they fit in the
+// shared-memory budget, otherwise x-y strips of one slice.
+void make_tile_plan(hd_scan *s)
+{
+    hd::TilePlan &tp = s->tp;
+    const int nx = s->geom.nx, ny = s->geom.ny, nz = s->geom.nz;
+    const int budget = kTileSmemBytes / 4;
+    tp.nx = nx;
+    tp.ny = ny;
+    tp.nz = nz;
+    const int64_t plane = int64_t(nx) * ny;
+    if (plane <= budget) {
+        tp.tx = nx;
+        tp.ty = ny;
+        tp.tz = static_cast<int>(budget / plane);
+        if (tp.tz > nz) tp.tz = nz;
+        const int ntz = (nz + tp.tz - 1) / tp.tz;
+        tp.tz = (nz + ntz - 1) / ntz;
+    } else {
+        tp.tx = nx;
+        tp.ty = budget / nx;
+        const int nty = (ny + tp.ty - 1) / tp.ty;
+        tp.ty = (ny + nty - 1) / nty;
+        tp.tz = 1;
+    }
+    tp.ntx = (nx + tp.tx - 1) / tp.tx;
+    tp.nty = (ny + tp.ty - 1) / tp.ty;
+    tp.ntz = (nz + tp.tz - 1) / tp.tz;
+    tp.ntiles = tp.ntx * tp.nty * tp.ntz;
+    if (tp.ntiles > hd::kMaxTiles) tp.ntiles = 0;
+    tp.max_tiles = 8;
+    tp.job_size = 16384;  // <= 32767: int16 differences in the tiled traversal
+    tp.refill = 8;
+    // two int16 difference arrays per tile (x runs and y runs)
+    tp.tile_words = 2 * ((tp.tx * tp.ty * tp.tz + 1) / 2);
+    auto magic = [](int t) {
+        return t == 1 ? 0u : static_cast<unsigned>((1ull << 32) / static_cast<unsigned>(t)) + 1u;
+    };
+    tp.mtx = magic(tp.tx);
+    tp.mty = magic(tp.ty);
+    tp.mtz = magic(tp.tz);
+    tp.pair_cap = 0;
 }
 
 hd_status run_chunk(hd_scan *s, const hd::Inputs &in, int64_t n, cudaStream_t st)
@@ -242,19 +322,36 @@ hd_status run_chunk(hd_scan *s, const hd::Inputs &in, int64_t n, cudaStream_t st
     const int use_miss = (m & (HD_SC | HD_MSC)) ? 1 : 0;
     const int use_hit = (m & HD_SM) ? 1 : 0;
     const hd::Records rec = records_of(s, n);
-    HD_CUDA(cudaMemsetAsync(&s->ctrl->rec_miss, 0, 2 * sizeof(unsigned int), st));
+    hd::TilePlan tp = s->tp;
+    if (s->trace_grid <= 0) tp.ntiles = 0;  // tiled path unavailable: global path only
+    HD_CUDA(cudaMemsetAsync(&s->ctrl->rec_miss, 0,
+                            sizeof(hd::Ctrl) - offsetof(hd::Ctrl, rec_miss), st));
+    if (tp.ntiles > 0)
+        HD_CUDA(cudaMemsetAsync(s->tile_count, 0, sizeof(uint32_t) * 2 * tp.ntiles, st));
     cudaEvent_t e0 = prof_begin(s, st);
     HD_CUDA(hd::launch_ingest(in, n, s->gq, s->cordic, s->params.wepl_miss_lt,
-                              s->params.wepl_hit_gt, use_miss, use_hit, rec, s->ctrl, s->sm_count,
-                              st));
+                              s->params.wepl_hit_gt, use_miss, use_hit, tp, rec, s->ctrl,
+                              s->tile_count, s->sm_count, st));
     s->launches += 1;
+    if (tp.ntiles > 0) {
+        HD_CUDA(hd::launch_plan(tp, s->tile_count, s->tile_cursor, s->jobs, s->ctrl, st));
+        HD_CUDA(hd::launch_scatter(tp, rec, s->ctrl, s->tile_cursor, pairs_of(s), n, st));
+        s->launches += 2;
+    }
     prof_end(s, 0, e0, st);
     cudaEvent_t e1 = prof_begin(s, st);
-    HD_CUDA(hd::launch_trace(rec, s->ctrl, s->ctrl, use_miss ? n : 0, use_hit ? n : 0, s->gq,
-                             s->N, s->M, s->carve, s->sm_count, st));
-    s->launches += 1;
-    if (s->profiling) s->trace_launches += 1;
+    if (tp.ntiles > 0) {
+        HD_CUDA(hd::launch_trace_tiles(tp, pairs_of(s), s->jobs, s->ctrl, s->N, s->M, s->carve,
+                                       s->trace_grid, st));
+        s->launches += 1;
+        if (s->profiling) s->trace_launches += 1;
+    }
     prof_end(s, 1, e1, st);
+    cudaEvent_t e2 = prof_begin(s, st);
+    HD_CUDA(hd::launch_trace_global(rec, s->ctrl, n, s->gq, s->N, s->M, s->carve, 0,
+                                    s->sm_count, st));
+    s->launches += 1;
+    prof_end(s, 3, e2, st);
     return HD_OK;
 }
 
@@ -315,13 +412,8 @@ hd_status hd_scan_create(const hd_geometry *geom, const hd_params *params, hd_sc
         delete s;
         return HD_ERR_CUDA;
     }
-    s->gq.nx = geom->nx;
-    s->gq.ny = geom->ny;
-    s->gq.nz = geom->nz;
-    s->gq.sx = q16_host(geom->sx);
-    s->gq.sy = q16_host(geom->sy);
-    s->gq.sz = q16_host(geom->sz);
-    s->gq.T = q16_host(geom->tracker_half_sep_mm);
+    s->gq = hd::make_geomq(geom->nx, geom->ny, geom->nz, geom->sx, geom->sy, geom->sz,
+                           geom->tracker_half_sep_mm);
     s->V = int64_t(geom->nx) * geom->ny * geom->nz;
     s->words = (s->V + 31) / 32;
     const uint32_t m = params->methods;
@@ -349,6 +441,13 @@ hd_status hd_scan_create(const hd_geometry *geom, const hd_params *params, hd_sc
     if (m & HD_SC) alloc(reinterpret_cast<void **>(&s->H1), V);
     if (m & HD_MSC) alloc(reinterpret_cast<void **>(&s->H2), V);
     alloc(reinterpret_cast<void **>(&s->bits_out), sizeof(uint32_t) * s->words);
+    make_tile_plan(s);
+    if (s->tp.ntiles > 0) {
+        alloc(reinterpret_cast<void **>(&s->tile_count), sizeof(uint32_t) * 2 * s->tp.ntiles);
+        alloc(reinterpret_cast<void **>(&s->tile_cursor), sizeof(uint32_t) * 2 * s->tp.ntiles);
+        const int per_sm = hd::trace_tiles_occupancy(s->tp);
+        s->trace_grid = per_sm > 0 ? per_sm * s->sm_count : 0;
+    }
     alloc(reinterpret_cast<void **>(&s->ctrl), sizeof(hd::Ctrl));
     if (!ok) {
         free_scan(s);
@@ -612,7 +711,7 @@ hd_status hd_scan_set_profiling(hd_scan *scan, int32_t enable)
     if (!g.ok) return HD_ERR_CUDA;
     drain_profile(scan);
     if (enable) {
-        scan->ms[0] = scan->ms[1] = scan->ms[2] = 0.0;
+        scan->ms[0] = scan->ms[1] = scan->ms[2] = scan->ms[3] = 0.0;
         scan->trace_launches = 0;
     }
     scan->profiling = enable != 0;
@@ -630,6 +729,7 @@ hd_status hd_scan_get_profile(hd_scan *scan, hd_profile *out)
     out->ms_ingest = scan->ms[0];
     out->ms_trace = scan->ms[1];
     out->ms_finalize = scan->ms[2];
+    out->ms_trace_global = scan->ms[3];
     return HD_OK;
 }
 

@@ -10,6 +10,8 @@ namespace hd {
 
 constexpr int64_t kQ16 = 65536;
 constexpr int kMaxN = 4096;
+constexpr int kMaxTiles = 2048;       // tiles per class for the shared-memory path
+constexpr int kTraceThreads = 512;    // threads per block of the tiled traversal
 
 // Gantry-rotation constants: theta[i] = round(atan(2^-i) * 180/pi * 2^30)
 // (degrees, 30 fractional bits) and K = round(2^30 prod (1 + 2^-2i)^-1/2).
@@ -24,43 +26,91 @@ struct GeomQ {
     int32_t pad;
     long long sx, sy, sz;  // voxel sizes, mm * 2^16
     long long T;           // tracker half-separation, mm * 2^16
+    unsigned long long mx, my, mz;  // floor(2^64 / (2 s)): division by multiply-high
 };
 
-// Device-side counters of one scan.
+// Device-side counters of one scan.  The block from rec_miss to job_next is
+// cleared before every chunk of histories.
 struct Ctrl {
     unsigned long long n_in, n_miss, n_hit, n_none, n_reject;
     unsigned long long steps_miss, steps_hit;
-    unsigned int rec_miss;  // records appended from the front of the list
-    unsigned int rec_hit;   // records appended from the back of the list
-    unsigned long long slice_key_pad;
+    unsigned int rec_miss;    // records appended from the front of the list
+    unsigned int rec_hit;     // records appended from the back of the list
+    unsigned int pairs_used;  // (record, tile) pairs admitted to the tiled path
+    int njobs;                // jobs of the tiled traversal
+    int job_next;             // next job to hand out
+    unsigned int n_fallback;  // records traversed by the global-memory path
 };
 
 // Compacted traversal records: grid Q16 entry and exit points, int32 each
-// (|G| < 2^30).  Missed histories fill [0, rec_miss), hit ones fill
-// [cap - rec_hit, cap).  Structure of arrays.
+// (|G| < 2^30), and a status (1 tiled, 2 global path).  Missed histories
+// fill [0, rec_miss), hit ones [cap - rec_hit, cap).  Structure of arrays.
 struct Records {
     int32_t *g[6];  // x0, y0, z0, x1, y1, z1
+    int32_t *status;
     int64_t cap;
+};
+
+// Tiling of the grid into boxes whose counters fit in shared memory.
+struct TilePlan {
+    int nx, ny, nz;
+    int tx, ty, tz;     // tile size in voxels
+    int ntx, nty, ntz;  // tiles per axis
+    int ntiles;         // tiles per class (0: tiled path off)
+    int max_tiles;      // records touching more tiles take the global path
+    int job_size;       // pairs per job
+    long long pair_cap;
+    int tile_words;     // 32-bit words of shared memory per block
+    int refill;         // idle lanes that trigger a warp refill
+    unsigned mtx, mty, mtz;  // floor(2^32 / t) + 1 (0 when t = 1): division by a tile size
+};
+
+// (record, tile) pairs sorted by tile: the packed run-walk state of the
+// record clipped to the tile, 64 bytes per pair (four uint4), so a pair is
+// written and read as whole 32-byte sectors (class and tile come from the
+// job).
+struct Pairs {
+    uint4 *v;  // 4 per pair
+};
+
+struct TileJob {
+    int tile;   // tile id within its class
+    int cls;    // 0 missed (N or carve), 1 hit (M)
+    int start;  // pair range [start, end)
+    int end;
 };
 
 struct Inputs {
     const float *angle, *u_in, *v_in, *u_out, *v_out, *wepl;
 };
 
-// Which voxel update a traversal applies.
-enum TraceMode : int { kCount = 0, kCarve = 1 };
-
 // ---- launchers (stream-ordered; return the launch's cudaError_t) ----
 cudaError_t launch_ingest(const Inputs &in, int64_t n, const GeomQ &g, const Cordic &cordic,
-                          float tau_l, float tau_h, int use_miss, int use_hit,
-                          const Records &rec, Ctrl *ctrl, int sm_count, cudaStream_t s);
+                          float tau_l, float tau_h, int use_miss, int use_hit, const TilePlan &tp,
+                          const Records &rec, Ctrl *ctrl, uint32_t *tile_count, int sm_count,
+                          cudaStream_t s);
 
-cudaError_t launch_trace(const Records &rec, const Ctrl *ctrl_counts, Ctrl *ctrl_stats,
-                         int64_t miss_upper, int64_t hit_upper, const GeomQ &g,
-                         uint32_t *N, uint32_t *M, uint32_t *carve, int sm_count, cudaStream_t s);
+cudaError_t launch_plan(const TilePlan &tp, const uint32_t *tile_count, uint32_t *tile_cursor,
+                        TileJob *jobs, Ctrl *ctrl, cudaStream_t s);
+
+cudaError_t launch_scatter(const TilePlan &tp, const Records &rec, const Ctrl *ctrl,
+                           uint32_t *tile_cursor, const Pairs &pairs, int64_t n, cudaStream_t s);
+
+cudaError_t launch_trace_tiles(const TilePlan &tp, const Pairs &pairs, const TileJob *jobs,
+                               Ctrl *ctrl, uint32_t *N, uint32_t *M, uint32_t *carve,
+                               int grid, cudaStream_t s);
+
+// Global-memory traversal of the records whose status is 2 (or of every
+// record when all_records is set).
+cudaError_t launch_trace_global(const Records &rec, Ctrl *ctrl, int64_t upper, const GeomQ &g,
+                                uint32_t *N, uint32_t *M, uint32_t *carve, int all_records,
+                                int sm_count, cudaStream_t s);
 
 cudaError_t launch_classify(const float *wepl, int64_t n, float tau_l, float tau_h,
                             uint8_t *cls, cudaStream_t s);
+
+// Blocks per SM the tiled traversal can keep resident with this plan.
+int trace_tiles_occupancy(const TilePlan &tp);
 
 struct DecideArgs {
     int32_t nx, ny, nz;

@@ -1,0 +1,448 @@
+// Shared-memory privatised traversal: the grid is cut into tiles whose
+// counters fit in one block's shared memory, every (record, tile) pair is
+// walked with the exact traversal clipped to the tile, and each block adds
+// its private tile into N or M (or clears the SC carve bits) once per job.
+//
+// Pipeline per chunk of histories (after ingest has counted pairs per tile):
+//   plan     exclusive scan of the tile counts -> cursors and a job table
+//   scatter  counting sort of the pairs by tile (block-level reservation)
+//   trace    persistent blocks take jobs; warps refill idle lanes from the
+//            job's pair range, so lanes do not wait for the longest path
+#include "hd_geom.cuh"
+
+namespace hd {
+
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+constexpr int kScatterThreads = 256;
+constexpr int kScatterPerThread = 16;
+
+__device__ __forceinline__ unsigned warp_incl_scan_u(unsigned v)
+{
+    const unsigned lane = threadIdx.x & 31u;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned t = __shfl_up_sync(kFull, v, o);
+        if (lane >= static_cast<unsigned>(o)) v += t;
+    }
+    return v;
+}
+
+// Exclusive block scan of one value per thread (blockDim.x <= 1024).
+__device__ __forceinline__ unsigned block_excl_scan(unsigned v, unsigned *s_warp, unsigned &total)
+{
+    const unsigned lane = threadIdx.x & 31u, wid = threadIdx.x >> 5;
+    const unsigned nw = blockDim.x >> 5;
+    const unsigned incl = warp_incl_scan_u(v);
+    if (lane == 31) s_warp[wid] = incl;
+    __syncthreads();
+    if (wid == 0) {
+        const unsigned x = lane < nw ? s_warp[lane] : 0u;
+        const unsigned xi = warp_incl_scan_u(x);
+        if (lane < nw) s_warp[lane] = xi - x;
+        if (lane == 31) s_warp[32] = xi;
+    }
+    __syncthreads();
+    const unsigned r = s_warp[wid] + incl - v;
+    total = s_warp[32];
+    __syncthreads();
+    return r;
+}
+
+
+// One block: tile offsets (exclusive scan of the counts), cursors for the
+// scatter, and the job table (chunks of job_size pairs of one tile).
+__global__ void __launch_bounds__(1024) plan_kernel(TilePlan tp, const uint32_t *tile_count,
+                                                    uint32_t *tile_cursor, TileJob *jobs,
+                                                    Ctrl *ctrl)
+{
+    __shared__ unsigned s_warp[33];
+    const int nt = 2 * tp.ntiles;
+    const int per = (nt + blockDim.x - 1) / blockDim.x;
+    const int t0 = threadIdx.x * per;
+    unsigned my_pairs = 0, my_jobs = 0;
+    for (int t = t0; t < t0 + per && t < nt; ++t) {
+        const unsigned c = tile_count[t];
+        my_pairs += c;
+        my_jobs += (c + tp.job_size - 1) / tp.job_size;
+    }
+    unsigned tot_pairs, tot_jobs;
+    unsigned off = block_excl_scan(my_pairs, s_warp, tot_pairs);
+    unsigned joff = block_excl_scan(my_jobs, s_warp, tot_jobs);
+    for (int t = t0; t < t0 + per && t < nt; ++t) {
+        const unsigned c = tile_count[t];
+        tile_cursor[t] = off;
+        for (unsigned s = 0; s < c; s += tp.job_size) {
+            TileJob j;
+            j.tile = t % tp.ntiles;
+            j.cls = t / tp.ntiles;
+            j.start = static_cast<int>(off + s);
+            j.end = static_cast<int>(off + (s + tp.job_size < c ? s + tp.job_size : c));
+            jobs[joff++] = j;
+        }
+        off += c;
+    }
+    if (threadIdx.x == 0) {
+        ctrl->njobs = static_cast<int>(tot_jobs);
+        ctrl->job_next = 0;
+    }
+}
+
+// Counting sort of (record, tile) pairs by tile.  Each block takes a range
+// of record slots, histograms its pairs, reserves one range per tile with a
+// single global atomic, then writes its pairs.
+__global__ void __launch_bounds__(kScatterThreads) scatter_kernel(TilePlan tp, Records rec,
+                                                                  const Ctrl *ctrl,
+                                                                  uint32_t *tile_cursor,
+                                                                  Pairs pairs)
+{
+    extern __shared__ uint32_t s_mem[];
+    const int nt = 2 * tp.ntiles;
+    uint32_t *s_hist = s_mem;
+    uint32_t *s_base = s_mem + nt;
+    for (int t = threadIdx.x; t < nt; t += blockDim.x) s_hist[t] = 0;
+    __syncthreads();
+    const unsigned nm = ctrl->rec_miss, nh = ctrl->rec_hit;
+    const int64_t slot0 = static_cast<int64_t>(blockIdx.x) * kScatterThreads * kScatterPerThread;
+    auto valid = [&](int64_t slot, int &cls) -> bool {
+        if (slot < nm) { cls = 0; }
+        else if (slot >= rec.cap - nh) { cls = 1; }
+        else return false;
+        return rec.status[slot] == 1;
+    };
+    for (int k = 0; k < kScatterPerThread; ++k) {
+        const int64_t slot = slot0 + k * kScatterThreads + threadIdx.x;
+        int cls;
+        if (slot >= rec.cap || !valid(slot, cls)) continue;
+        int32_t r[6];
+#pragma unroll
+        for (int a = 0; a < 6; ++a) r[a] = rec.g[a][slot];
+        int lo[3], hi[3];
+        if (tile_range(tp, r, lo, hi) == 0) continue;
+        for (int z = lo[2]; z <= hi[2]; ++z)
+            for (int y = lo[1]; y <= hi[1]; ++y)
+                for (int x = lo[0]; x <= hi[0]; ++x)
+                    atomicAdd(&s_hist[cls * tp.ntiles + x + tp.ntx * (y + tp.nty * z)], 1u);
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < nt; t += blockDim.x) {
+        const uint32_t c = s_hist[t];
+        s_base[t] = c ? atomicAdd(&tile_cursor[t], c) : 0u;
+        s_hist[t] = 0;
+    }
+    __syncthreads();
+    for (int k = 0; k < kScatterPerThread; ++k) {
+        const int64_t slot = slot0 + k * kScatterThreads + threadIdx.x;
+        int cls;
+        if (slot >= rec.cap || !valid(slot, cls)) continue;
+        int32_t r[6];
+#pragma unroll
+        for (int a = 0; a < 6; ++a) r[a] = rec.g[a][slot];
+        int lo[3], hi[3];
+        if (tile_range(tp, r, lo, hi) == 0) continue;
+        for (int z = lo[2]; z <= hi[2]; ++z)
+            for (int y = lo[1]; y <= hi[1]; ++y)
+                for (int x = lo[0]; x <= hi[0]; ++x) {
+                    const int t = cls * tp.ntiles + x + tp.ntx * (y + tp.nty * z);
+                    const uint32_t pos = s_base[t] + atomicAdd(&s_hist[t], 1u);
+                    // set up the walk of this record clipped to this tile
+                    const int x0 = x * tp.tx, y0 = y * tp.ty, z0 = z * tp.tz;
+                    const int dx = min(tp.tx, tp.nx - x0), dy = min(tp.ty, tp.ny - y0),
+                              dz = min(tp.tz, tp.nz - z0);
+                    const int32_t gi[3] = {r[0] - (x0 << 16), r[1] - (y0 << 16), r[2] - (z0 << 16)};
+                    const int32_t go[3] = {r[3] - (x0 << 16), r[4] - (y0 << 16), r[5] - (z0 << 16)};
+                    RunWalk w;
+                    uint32_t o[kPackedWords];
+                    if (run_begin(w, gi, go, dx, dy, dz)) run_pack(w, o);
+                    else run_pack_empty(o);
+#pragma unroll
+                    for (int a = 0; a < 4; ++a)
+                        pairs.v[4 * static_cast<size_t>(pos) + a] =
+                            make_uint4(o[4 * a], o[4 * a + 1], o[4 * a + 2], o[4 * a + 3]);
+                }
+    }
+}
+
+// ---------------------------------------------------------------- traversal
+//
+// A block's private tile holds two arrays of int16 difference counts over
+// the tile's voxels: one laid out x-fastest for runs along x, one
+// y-fastest for runs along y (z-fastest runs are never formed: z is always
+// a minor axis).  A run lo..hi of a row adds +1 at lo and -1 at hi + 1; the
+// flush takes prefix sums along the rows and adds the two arrays.  Two int16
+// share a 32-bit word; each job covers at most 32767 pairs, so every
+// difference and every prefix sum stays inside int16 and a word read as
+// lo + 65536 hi decodes exactly even after carries between the halves.
+// In carve mode (SC without MSC) the arrays are bit masks instead and a run
+// clears its bits.
+
+__device__ __forceinline__ void load_packed(const Pairs &pairs, int idx, uint32_t o[16])
+{
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+        const uint4 v = __ldg(&pairs.v[4 * static_cast<size_t>(idx) + a]);
+        o[4 * a] = v.x;
+        o[4 * a + 1] = v.y;
+        o[4 * a + 2] = v.z;
+        o[4 * a + 3] = v.w;
+    }
+}
+
+__device__ __forceinline__ void diff_add(uint32_t *arr, int e, int sgn)
+{
+    const uint32_t one = (e & 1) ? 65536u : 1u;
+    atomicAdd(&arr[e >> 1], sgn > 0 ? one : (0u - one));
+}
+
+__device__ __forceinline__ void bits_clear(uint32_t *bits, int e0, int e1)
+{
+    // clear bits e0..e1 inclusive
+    int w = e0 >> 5;
+    const int wl = e1 >> 5;
+    for (; w <= wl; ++w) {
+        const int b0 = w == (e0 >> 5) ? (e0 & 31) : 0;
+        const int b1 = w == wl ? (e1 & 31) : 31;
+        const uint32_t m = (b1 == 31 ? 0xffffffffu : ((2u << b1) - 1u)) & ~((1u << b0) - 1u);
+        if (bits[w] & m) atomicAnd(&bits[w], ~m);
+    }
+}
+
+// In-place inclusive prefix sums of int16 rows: `rows` rows of `len`
+// elements, one warp per row.
+__device__ __forceinline__ void rows_prefix(int16_t *a, int rows, int len)
+{
+    const unsigned lane = threadIdx.x & 31u;
+    const int warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int chunk = (len + 31) >> 5;
+    for (int r = warp; r < rows; r += nw) {
+        int16_t *row = a + static_cast<long long>(r) * len;
+        const int b = lane * chunk;
+        const int e = min(b + chunk, len);
+        int acc = 0;
+        for (int i = b; i < e; ++i) acc += row[i];
+        int incl = acc;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(kFull, incl, o);
+            if (lane >= static_cast<unsigned>(o)) incl += t;
+        }
+        int run = incl - acc;
+        for (int i = b; i < e; ++i) {
+            run += row[i];
+            row[i] = static_cast<int16_t>(run);
+        }
+    }
+}
+
+template <int kThreads>
+__global__ void __launch_bounds__(kThreads, 1) trace_tiles_kernel(
+    TilePlan tp, Pairs pairs, const TileJob *__restrict__ jobs, Ctrl *ctrl, uint32_t *N,
+    uint32_t *M, uint32_t *carve)
+{
+    extern __shared__ uint32_t tile[];
+    __shared__ int s_job;
+    __shared__ unsigned s_next;
+    const unsigned lane = threadIdx.x & 31u;
+    const unsigned warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    unsigned long long st_m = 0, st_h = 0;
+    for (;;) {
+        if (threadIdx.x == 0) {
+            s_job = atomicAdd(&ctrl->job_next, 1);
+            s_next = 0;
+        }
+        __syncthreads();
+        const int j = s_job;
+        if (j >= ctrl->njobs) break;
+        const TileJob job = jobs[j];
+        const int tix = job.tile % tp.ntx;
+        const int tiy = (job.tile / tp.ntx) % tp.nty;
+        const int tiz = job.tile / (tp.ntx * tp.nty);
+        const int x0 = tix * tp.tx, y0 = tiy * tp.ty, z0 = tiz * tp.tz;
+        const int dx = min(tp.tx, tp.nx - x0), dy = min(tp.ty, tp.ny - y0),
+                  dz = min(tp.tz, tp.nz - z0);
+        const int nvox = dx * dy * dz;
+        const bool carve_mode = job.cls == 0 && N == nullptr;
+        // two arrays of nvox int16 (count) or nvox bits (carve)
+        const int arr_words = carve_mode ? (nvox + 31) >> 5 : (nvox + 1) >> 1;
+        uint32_t *arrX = tile;
+        uint32_t *arrY = tile + arr_words;
+        const uint32_t init = carve_mode ? 0xffffffffu : 0u;
+        for (int w = threadIdx.x; w < 2 * arr_words; w += blockDim.x) tile[w] = init;
+        __syncthreads();
+
+        const int total = job.end - job.start;
+        // Each lane walks one pair and holds the packed state of its next one
+        // (loaded a refill ahead, so starting a walk never waits on memory).
+        // A refill happens once enough lanes are idle; then every idle lane
+        // with a prefetched pair starts it and fetches another.
+        RunWalk w;
+        w.flags = 1 << 9;
+        w.nmaj = 0;
+        bool active = false;
+        unsigned steps = 0;
+        uint32_t *arr = arrX;
+        uint32_t ng[kPackedWords];
+        int nidx = -1;
+        {
+            unsigned base = 0;
+            if (lane == 0) base = atomicAdd(&s_next, 32u);
+            base = __shfl_sync(kFull, base, 0);
+            const unsigned r = base + lane;
+            if (r < static_cast<unsigned>(total)) {
+                nidx = job.start + static_cast<int>(r);
+                load_packed(pairs, nidx, ng);
+            }
+        }
+        for (;;) {
+            const unsigned want = __ballot_sync(kFull, !active && nidx >= 0);
+            const unsigned busy = __ballot_sync(kFull, active);
+            if (want == 0 && busy == 0) break;
+            if (want != 0 && (__popc(want) >= static_cast<unsigned>(tp.refill) || busy == 0)) {
+                if (!active && nidx >= 0) {
+                    run_unpack(ng, dx, dy, w);
+                    active = !((w.flags >> 9) & 1);
+                    arr = ((w.flags >> 5) & 1) ? arrY : arrX;
+                    nidx = -1;
+                }
+                unsigned base = 0;
+                const unsigned nw = __popc(want);
+                if (lane == 0) base = atomicAdd(&s_next, nw);
+                base = __shfl_sync(kFull, base, 0);
+                if (want & (1u << lane)) {
+                    const unsigned r = base + __popc(want & ((1u << lane) - 1u));
+                    if (r < static_cast<unsigned>(total)) {
+                        nidx = job.start + static_cast<int>(r);
+                        load_packed(pairs, nidx, ng);
+                    }
+                }
+                continue;
+            }
+            if (active) {
+                int row, lo, hi;
+                if (run_next(w, row, lo, hi)) {
+                    const int base = row * w.nmaj;
+                    steps += static_cast<unsigned>(hi - lo + 1);
+                    if (!carve_mode) {
+                        diff_add(arr, base + lo, 1);
+                        if (hi + 1 < w.nmaj) diff_add(arr, base + hi + 1, -1);
+                    } else {
+                        bits_clear(arr, base + lo, base + hi);
+                    }
+                } else {
+                    active = false;
+                }
+            }
+        }
+        __syncthreads();
+        uint32_t *vol = job.cls == 0 ? N : M;
+        if (!carve_mode) {
+            // a word holds lo + 65536 hi (mod 2^32) after carries between the
+            // halves: split it into two plain int16 values
+            for (int wd = threadIdx.x; wd < 2 * arr_words; wd += blockDim.x) {
+                const uint32_t v = tile[wd];
+                const int lo = static_cast<int16_t>(v & 0xffffu);
+                const int hi = static_cast<int>(v - static_cast<uint32_t>(lo)) >> 16;
+                tile[wd] = (static_cast<uint32_t>(lo) & 0xffffu) | (static_cast<uint32_t>(hi) << 16);
+            }
+            __syncthreads();
+            rows_prefix(reinterpret_cast<int16_t *>(arrX), dy * dz, dx);
+            rows_prefix(reinterpret_cast<int16_t *>(arrY), dx * dz, dy);
+            __syncthreads();
+            const int16_t *X = reinterpret_cast<const int16_t *>(arrX);
+            const int16_t *Y = reinterpret_cast<const int16_t *>(arrY);
+            for (int row = warp; row < dy * dz; row += nwarps) {
+                const int ly = row % dy, lz = row / dy;
+                const long long gbase = x0 + static_cast<long long>(tp.nx) *
+                                                 ((y0 + ly) + static_cast<long long>(tp.ny) * (z0 + lz));
+                for (int lx = lane; lx < dx; lx += 32) {
+                    const int v = X[row * dx + lx] + Y[(lx + dx * lz) * dy + ly];
+                    if (v) atomicAdd(&vol[gbase + lx], static_cast<uint32_t>(v));
+                }
+            }
+        } else {
+            for (int row = warp; row < dy * dz; row += nwarps) {
+                const int ly = row % dy, lz = row / dy;
+                const long long gbase = x0 + static_cast<long long>(tp.nx) *
+                                                 ((y0 + ly) + static_cast<long long>(tp.ny) * (z0 + lz));
+                for (int lx = lane; lx < dx; lx += 32) {
+                    const int ex = row * dx + lx, ey = (lx + dx * lz) * dy + ly;
+                    const bool kept = ((arrX[ex >> 5] >> (ex & 31)) & 1u) &&
+                                      ((arrY[ey >> 5] >> (ey & 31)) & 1u);
+                    if (!kept) {
+                        const long long gv = gbase + lx;
+                        const uint32_t gb = 1u << (gv & 31);
+                        if (__ldcg(&carve[gv >> 5]) & gb) atomicAnd(&carve[gv >> 5], ~gb);
+                    }
+                }
+            }
+        }
+        if (job.cls == 0) st_m += steps; else st_h += steps;
+        __syncthreads();
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        st_m += __shfl_xor_sync(kFull, st_m, o);
+        st_h += __shfl_xor_sync(kFull, st_h, o);
+    }
+    if (lane == 0) {
+        if (st_m) atomicAdd(&ctrl->steps_miss, st_m);
+        if (st_h) atomicAdd(&ctrl->steps_hit, st_h);
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_plan(const TilePlan &tp, const uint32_t *tile_count, uint32_t *tile_cursor,
+                        TileJob *jobs, Ctrl *ctrl, cudaStream_t s)
+{
+    plan_kernel<<<1, 1024, 0, s>>>(tp, tile_count, tile_cursor, jobs, ctrl);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scatter(const TilePlan &tp, const Records &rec, const Ctrl *ctrl,
+                           uint32_t *tile_cursor, const Pairs &pairs, int64_t n, cudaStream_t s)
+{
+    const int64_t per_block = static_cast<int64_t>(kScatterThreads) * kScatterPerThread;
+    const int64_t blocks = (n + per_block - 1) / per_block;
+    if (blocks <= 0) return cudaSuccess;
+    const size_t smem = sizeof(uint32_t) * 4 * static_cast<size_t>(tp.ntiles);
+    scatter_kernel<<<static_cast<unsigned>(blocks), kScatterThreads, smem, s>>>(tp, rec, ctrl,
+                                                                               tile_cursor, pairs);
+    return cudaGetLastError();
+}
+
+static cudaError_t set_tile_smem(const TilePlan &tp)
+{
+    return cudaFuncSetAttribute(trace_tiles_kernel<kTraceThreads>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, tp.tile_words * 4);
+}
+
+int trace_tiles_occupancy(const TilePlan &tp)
+{
+    if (set_tile_smem(tp) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, trace_tiles_kernel<kTraceThreads>, kTraceThreads,
+                                                      static_cast<size_t>(tp.tile_words) * 4) !=
+        cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return nb;
+}
+
+cudaError_t launch_trace_tiles(const TilePlan &tp, const Pairs &pairs, const TileJob *jobs,
+                               Ctrl *ctrl, uint32_t *N, uint32_t *M, uint32_t *carve, int grid,
+                               cudaStream_t s)
+{
+    cudaError_t e = set_tile_smem(tp);
+    if (e != cudaSuccess) return e;
+    trace_tiles_kernel<kTraceThreads><<<grid, kTraceThreads, static_cast<size_t>(tp.tile_words) * 4, s>>>(
+        tp, pairs, jobs, ctrl, N, M, carve);
+    return cudaGetLastError();
+}
+
+}  // namespace hd

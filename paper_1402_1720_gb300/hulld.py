@@ -61,7 +61,7 @@ class hd_stats(ctypes.Structure):
 class hd_profile(ctypes.Structure):
     _fields_ = [("kernel_launches", ctypes.c_int64), ("trace_launches", ctypes.c_int64),
                 ("ms_ingest", ctypes.c_double), ("ms_trace", ctypes.c_double),
-                ("ms_finalize", ctypes.c_double)]
+                ("ms_finalize", ctypes.c_double), ("ms_trace_global", ctypes.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

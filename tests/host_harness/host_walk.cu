@@ -1,0 +1,105 @@
+// Test harness: the library's fixed-point geometry and traversal (hd_geom.cuh),
+// compiled for the host so the CPU test suite can compare them with the oracle.
+#include "../../paper_1402_1720_gb300/csrc/hd_geom.cuh"
+#include <vector>
+struct HostVisit {
+    int32_t *out; int cap; mutable int n = 0;
+    void operator()(uint32_t v) const { if (n < cap) out[n] = (int32_t)v; ++n; }
+};
+extern "C" int hx_walk(const int32_t *gi, const int32_t *go, int nx, int ny, int nz, int32_t *out, int cap)
+{
+    HostVisit v{out, cap};
+    return (int)hd::walk_all(gi, go, nx, ny, nz, v);
+}
+// union of the walks clipped to tiles of size (tx,ty,tz); returns global indices
+extern "C" int hx_walk_tiled(const int32_t *gi, const int32_t *go, int nx, int ny, int nz, int tx, int ty, int tz, int32_t *out, int cap)
+{
+    int n = 0;
+    for (int z0 = 0; z0 < nz; z0 += tz) for (int y0 = 0; y0 < ny; y0 += ty) for (int x0 = 0; x0 < nx; x0 += tx) {
+        int dx = std::min(tx, nx - x0), dy = std::min(ty, ny - y0), dz = std::min(tz, nz - z0);
+        int32_t a[3] = {gi[0] - (x0 << 16), gi[1] - (y0 << 16), gi[2] - (z0 << 16)};
+        int32_t b[3] = {go[0] - (x0 << 16), go[1] - (y0 << 16), go[2] - (z0 << 16)};
+        hd::Walk w;
+        if (!hd::walk_begin(w, a, b, dx, dy, dz)) continue;
+        do {
+            int l = w.idx; int lx = l % dx, ly = (l / dx) % dy, lz = l / (dx * dy);
+            if (lx < 0 || ly < 0 || lz < 0 || lz >= dz) return -1000000;
+            if (n < cap) out[n] = (x0 + lx) + nx * ((y0 + ly) + ny * (z0 + lz));
+            ++n;
+        } while (hd::walk_next(w));
+    }
+    return n;
+}
+extern "C" int hx_endpoints(int nx, int ny, int nz, float sx, float sy, float sz, float T,
+                            const long long *theta, long long K, float a, float ui, float vi, float uo, float vo, int32_t *out)
+{
+    hd::GeomQ g = hd::make_geomq(nx, ny, nz, sx, sy, sz, T);
+    hd::Cordic cd; for (int i = 0; i < 32; ++i) cd.theta[i] = theta[i]; cd.K = K;
+    return hd::endpoints(g, cd, a, ui, vi, uo, vo, out) ? 1 : 0;
+}
+// the voxel set produced as major-axis runs, expanded to linear indices
+extern "C" int hx_runs(const int32_t *gi, const int32_t *go, int nx, int ny, int nz, int32_t *out, int cap, int *nruns)
+{
+    hd::RunWalk w;
+    int n = 0, runs = 0;
+    if (hd::run_begin(w, gi, go, nx, ny, nz)) {
+        const bool ymaj = (w.flags >> 5) & 1;
+        int row, lo, hi;
+        while (hd::run_next(w, row, lo, hi)) {
+            ++runs;
+            if (lo < 0 || hi >= w.nmaj || lo > hi) return -1000000;
+            for (int m = lo; m <= hi; ++m) {
+                int v;
+                if (!ymaj) v = m + nx * row;
+                else v = (row % nx) + nx * (m + ny * (row / nx));
+                if (n < cap) out[n] = v;
+                ++n;
+            }
+            if (runs > 100000) return -2000000;
+        }
+    }
+    *nruns = runs;
+    return n;
+}
+// the same, with the walk state packed and unpacked before the first run
+extern "C" int hx_runs_packed(const int32_t *gi, const int32_t *go, int nx, int ny, int nz, int32_t *out, int cap)
+{
+    hd::RunWalk w0, w;
+    uint32_t o[hd::kPackedWords];
+    if (hd::run_begin(w0, gi, go, nx, ny, nz)) hd::run_pack(w0, o);
+    else hd::run_pack_empty(o);
+    hd::run_unpack(o, nx, ny, w);
+    int n = 0;
+    const bool ymaj = (w.flags >> 5) & 1;
+    int row, lo, hi;
+    while (hd::run_next(w, row, lo, hi)) {
+        if (lo < 0 || hi >= w.nmaj || lo > hi) return -1000000;
+        for (int m = lo; m <= hi; ++m) {
+            int v = !ymaj ? m + nx * row : (row % nx) + nx * (m + ny * (row / nx));
+            if (n < cap) out[n] = v;
+            ++n;
+        }
+    }
+    return n;
+}
+// exhaustive check of the tile-index division used when bucketing records:
+// floor(v / t) for every v in [0, 4096) and tile size t in [1, 4096];
+// returns the number of mismatches
+extern "C" long long hx_check_tile_division(void)
+{
+    long long bad = 0;
+    for (int t = 1; t <= 4096; ++t) {
+        hd::TilePlan tp{};
+        tp.nx = tp.ny = tp.nz = 4096;
+        tp.tx = tp.ty = tp.tz = t;
+        const unsigned m = t == 1 ? 0u : static_cast<unsigned>((1ull << 32) / static_cast<unsigned>(t)) + 1u;
+        tp.mtx = tp.mty = tp.mtz = m;
+        for (int v = 0; v < 4096; ++v) {
+            const int32_t r[6] = {v << 16, v << 16, v << 16, v << 16, v << 16, v << 16};
+            int lo[3], hi[3];
+            hd::tile_range(tp, r, lo, hi);
+            if (lo[0] != v / t || hi[2] != v / t) ++bad;
+        }
+    }
+    return bad;
+}

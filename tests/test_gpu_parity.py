@@ -115,6 +115,35 @@ def test_fuzz_random_histories(hd, oracle_mod, gi):
         _assert_stats(got, ref)
 
 
+# grids whose shared-memory tiles are z-slabs of one or more slices, or x-y
+# strips of one slice, so records are split over several tiles
+TILED_GEOMS = [
+    synth.Geometry(200, 200, 6, 1.0, 1.0, 2.5, 155.0),    # slabs of one slice
+    synth.Geometry(256, 256, 4, 1.0, 1.0, 2.5, 190.0),    # x-y strips, one slice
+    synth.Geometry(64, 64, 40, 1.0, 1.0, 0.5, 100.0),     # slabs of 10 slices
+    synth.Geometry(400, 130, 3, 0.5, 0.5, 1.25, 155.0),   # x-y strips
+]
+
+
+@pytest.mark.parametrize("gi", range(len(TILED_GEOMS)))
+def test_multi_tile_grids(hd, oracle_mod, gi):
+    g = TILED_GEOMS[gi]
+    for seed in range(2):
+        rng = np.random.default_rng(77 + 10 * gi + seed)
+        h = synth.tiny_random_case(rng, 6000, g, span=1.1)
+        # mostly shallow paths, as in a scan, plus the steep ones of the case
+        h.v_out[: len(h) // 2] = h.v_in[: len(h) // 2] + rng.normal(0, 2.0, len(h) // 2).astype(np.float32)
+        ref = oracle_mod.run(g, h, threads=8)
+        got = _run_gpu(hd, g, h)
+        _assert_same(got, ref, ALL)
+        _assert_stats(got, ref)
+    # SC alone uses the carve masks of the same tiles
+    p = oracle_mod.Params(methods=oracle_mod.SC)
+    ref = oracle_mod.run(g, h, p, threads=8)
+    got = _run_gpu(hd, g, h, p)
+    _assert_same(got, ref, ["H1"])
+
+
 def _lattice_histories(rng, g, n):
     """Histories whose entry/exit points sit on voxel planes, edges and
     corners (angles on multiples of 45 degrees, u/v on voxel boundaries), to

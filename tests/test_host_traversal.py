@@ -1,0 +1,159 @@
+"""The CUDA library's geometry and traversal code (hd_geom.cuh), compiled for
+the host, against the CPU oracle: exact voxel sets for adversarial segments,
+the same sets when the walk is clipped to shared-memory tiles, and identical
+fixed-point endpoints.  Runs without a GPU (nvcc compiles host code)."""
+import ctypes
+import os
+import shutil
+import subprocess
+
+import numpy as np
+import pytest
+
+from paper_1402_1720_gb300 import synth
+from tests.test_oracle_pins import _random_segments
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+SRC = os.path.join(HERE, "host_harness", "host_walk.cu")
+I32P = ctypes.POINTER(ctypes.c_int32)
+
+
+@pytest.fixture(scope="module")
+def hx(tmp_path_factory):
+    nvcc = shutil.which("nvcc") or "/usr/local/cuda/bin/nvcc"
+    if not os.path.exists(nvcc):
+        pytest.skip("nvcc not available")
+    out = str(tmp_path_factory.mktemp("hx") / "libhostwalk.so")
+    subprocess.check_call([nvcc, "-O2", "-std=c++17", "-Xcompiler", "-fPIC", "-shared",
+                           "-gencode", "arch=compute_103a,code=sm_103a",
+                           "-diag-suppress", "20014", "-o", out, SRC,
+                           "-I", os.path.join(HERE, "..", "include")])
+    L = ctypes.CDLL(out)
+    L.hx_walk.restype = ctypes.c_int
+    L.hx_walk_tiled.restype = ctypes.c_int
+    L.hx_endpoints.restype = ctypes.c_int
+    L.hx_runs.restype = ctypes.c_int
+    return L
+
+
+def _walk(L, a, b, dims):
+    a = np.asarray(a, np.int32)
+    b = np.asarray(b, np.int32)
+    out = np.zeros(sum(dims) + 16, np.int32)
+    n = L.hx_walk(a.ctypes.data_as(I32P), b.ctypes.data_as(I32P), *dims,
+                  out.ctypes.data_as(I32P), out.size)
+    assert n <= out.size
+    v = out[:n]
+    assert len(np.unique(v)) == n  # each voxel once (C(v) is a set)
+    return np.sort(v)
+
+
+@pytest.mark.parametrize("dims", [(5, 4, 3), (1, 1, 1), (7, 1, 2), (3, 3, 3), (40, 30, 20)])
+def test_walk_equals_oracle(oracle_mod, hx, dims):
+    rng = np.random.default_rng(sum(dims) + 7)
+    for a, b in _random_segments(rng, 4000, dims):
+        assert np.array_equal(_walk(hx, a, b, dims), oracle_mod.voxel_set(a, b, *dims)), \
+            (a.tolist(), b.tolist())
+
+
+@pytest.mark.parametrize("dims,tiles", [((6, 5, 4), (6, 5, 1)), ((17, 13, 11), (17, 4, 1)),
+                                        ((9, 9, 9), (2, 2, 2)), ((40, 30, 6), (40, 30, 2))])
+def test_tiled_walks_partition_the_set(oracle_mod, hx, dims, tiles):
+    rng = np.random.default_rng(sum(dims) + sum(tiles))
+    for a, b in _random_segments(rng, 2000, dims):
+        out = np.zeros(4 * sum(dims) + 64, np.int32)
+        n = hx.hx_walk_tiled(np.asarray(a, np.int32).ctypes.data_as(I32P),
+                             np.asarray(b, np.int32).ctypes.data_as(I32P), *dims, *tiles,
+                             out.ctypes.data_as(I32P), out.size)
+        assert n >= 0
+        assert np.array_equal(np.sort(out[:n]), oracle_mod.voxel_set(a, b, *dims))
+
+
+def test_endpoints_equal_oracle(oracle_mod, hx):
+    theta, K = oracle_mod.cordic_table()
+    th = (ctypes.c_longlong * 32)(*theta)
+    rng = np.random.default_rng(3)
+    for g in [synth.geometry_for(1), synth.geometry_for(2), synth.geometry_for(3),
+              synth.Geometry(8, 8, 8, 0.125, 0.125, 0.125, 100.0)]:
+        h = synth.tiny_random_case(rng, 4000, g, span=3.0)
+        for i in range(len(h)):
+            args = [float(x[i]) for x in h.arrays()[:5]]
+            if i % 97 == 0:
+                args[1] = float("nan")
+            if i % 89 == 0:
+                args[2] = 4096.0
+            rej, gin, gout = oracle_mod.grid_endpoints(g, *args)
+            out = np.zeros(6, np.int32)
+            ok = hx.hx_endpoints(g.nx, g.ny, g.nz, ctypes.c_float(g.sx), ctypes.c_float(g.sy),
+                                 ctypes.c_float(g.sz), ctypes.c_float(g.T), th, K,
+                                 *[ctypes.c_float(x) for x in args], out.ctypes.data_as(I32P))
+            assert bool(ok) != rej
+            if ok:
+                assert out[:3].tolist() == gin.tolist() and out[3:].tolist() == gout.tolist()
+
+
+@pytest.mark.parametrize("dims", [(5, 4, 3), (1, 1, 1), (7, 1, 2), (40, 30, 20), (1, 7, 3),
+                                  (9, 1, 1)])
+def test_run_walk_equals_oracle(oracle_mod, hx, dims):
+    """The run-length form (major-axis runs between minor crossings) gives the
+    same voxel set, each voxel once."""
+    rng = np.random.default_rng(sum(dims) + 11)
+    for a, b in _random_segments(rng, 4000, dims):
+        out = np.zeros(2 * sum(dims) + 64, np.int32)
+        nr = ctypes.c_int(0)
+        n = hx.hx_runs(np.asarray(a, np.int32).ctypes.data_as(I32P),
+                       np.asarray(b, np.int32).ctypes.data_as(I32P), *dims,
+                       out.ctypes.data_as(I32P), out.size, ctypes.byref(nr))
+        assert n >= 0
+        got = np.sort(out[:n])
+        assert len(np.unique(got)) == n
+        assert np.array_equal(got, oracle_mod.voxel_set(a, b, *dims)), (a.tolist(), b.tolist())
+
+
+def test_run_walk_nearly_axis_aligned(oracle_mod, hx):
+    """Minor axes that move by a few 2^-16 voxel units: quotients far beyond
+    the box (the sentinel in the run walk) and minors starting on planes."""
+    Q = 65536
+    rng = np.random.default_rng(5)
+    for dims in [(40, 30, 20), (64, 64, 8), (7, 200, 3)]:
+        hi = np.array(dims) * Q
+        for k in range(3000):
+            a = rng.integers(-2 * Q, hi + 2 * Q)
+            b = a.copy()
+            maj = rng.integers(0, 3)
+            b[maj] = rng.integers(-2 * Q, hi[maj] + 2 * Q)
+            for ax in range(3):
+                if ax != maj:
+                    b[ax] = a[ax] + rng.integers(-3, 4) * (rng.integers(1, 3) if k % 2 else 1)
+            if k % 5 == 0:
+                for ax in range(3):
+                    if ax != maj:
+                        a[ax] = (a[ax] >> 16) << 16
+            out = np.zeros(2 * sum(dims) + 64, np.int32)
+            nr = ctypes.c_int(0)
+            n = hx.hx_runs(np.asarray(a, np.int32).ctypes.data_as(I32P),
+                           np.asarray(b, np.int32).ctypes.data_as(I32P), *dims,
+                           out.ctypes.data_as(I32P), out.size, ctypes.byref(nr))
+            assert n >= 0
+            assert np.array_equal(np.sort(out[:n]), oracle_mod.voxel_set(a, b, *dims))
+
+
+@pytest.mark.parametrize("dims", [(5, 4, 3), (40, 30, 20), (1, 7, 3), (200, 200, 1)])
+def test_packed_run_walk_equals_oracle(oracle_mod, hx, dims):
+    """A walk prepared in one kernel and resumed in another (packed state)."""
+    hx.hx_runs_packed.restype = ctypes.c_int
+    rng = np.random.default_rng(sum(dims) + 13)
+    for a, b in _random_segments(rng, 3000, dims):
+        out = np.zeros(2 * sum(dims) + 64, np.int32)
+        n = hx.hx_runs_packed(np.asarray(a, np.int32).ctypes.data_as(I32P),
+                              np.asarray(b, np.int32).ctypes.data_as(I32P), *dims,
+                              out.ctypes.data_as(I32P), out.size)
+        assert n >= 0
+        assert np.array_equal(np.sort(out[:n]), oracle_mod.voxel_set(a, b, *dims))
+
+
+def test_tile_index_division_exhaustive(hx):
+    """Tile indices by multiply-high equal integer division for every voxel
+    index and tile size the library supports (including tiles of one voxel)."""
+    hx.hx_check_tile_division.restype = ctypes.c_longlong
+    assert hx.hx_check_tile_division() == 0
