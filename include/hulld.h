@@ -226,6 +226,36 @@ HD_API hd_status hd_scan_set_profiling(hd_scan *scan, int32_t enable);
  * (host synchronisation on them). */
 HD_API hd_status hd_scan_get_profile(hd_scan *scan, hd_profile *out);
 
+/* Allocation-free accumulation of path counts, for callers that cannot
+ * allocate device memory when they run it (inside a stream capture that must
+ * stay free of allocation nodes, under a memory pool that forbids
+ * cudaMalloc/cudaFree after start-up, or on a latency-critical path).  The
+ * paper has no counterpart: this is a deployment aid.
+ *
+ * Classifies the n histories (device SoA arrays, as in
+ * hd_scan_add_histories) and ADDS one to N[v] (uint32, V entries, device)
+ * for every voxel v of every missed path and one to M[v] for every voxel of
+ * every hit path, exactly as a scan's N and M accumulate; N is required when
+ * params->methods has HD_SC or HD_MSC, M when it has HD_SM (the other may be
+ * NULL).  The caller zeroes N and M before the first call of an acquisition.
+ * Histories that are rejected or unused leave no trace (no statistics are
+ * kept).
+ *
+ * Scratch: one fixed array of about 7.3 MB in the library's device image
+ * (records of at most 262144 histories per call), held by every GPU that
+ * loads the library until the process exits.  n above 262144 returns
+ * HD_ERR_RANGE: split larger batches into several calls.  The first call on
+ * a device looks up the array's device address (once per device), so make
+ * that first call before any stream capture.  All calls share the array:
+ * calls that overlap on the GPU (different streams, or unordered host
+ * threads) race on it, so order them on one stream.  Nothing is allocated
+ * or freed by any call.  Stream-ordered on `stream`; errors as elsewhere. */
+HD_API hd_status hd_accumulate_noalloc(const hd_geometry *geom, const hd_params *params,
+                                       const float *angle_deg, const float *u_in,
+                                       const float *v_in, const float *u_out,
+                                       const float *v_out, const float *wepl, int64_t n,
+                                       uint32_t *N, uint32_t *M, void *stream);
+
 /* Classify n WEPL values (Eq. 3.1, Eq. 3.7): cls_out[i] = 1 missed, 2 hit,
  * 0 neither.  Only the two cutoffs of params are used.  wepl and cls_out
  * are both device pointers (on_device = 1) or both host pointers. */

@@ -86,6 +86,8 @@ _SIGS = {
     "hd_scan_get_hull_indices": ([_VP, _I32, _VP, _I64, ctypes.POINTER(_I64), _I32, _VP],
                                  ctypes.c_int),
     "hd_classify": ([_VP, _I64, ctypes.POINTER(hd_params), _VP, _I32, _VP], ctypes.c_int),
+    "hd_accumulate_noalloc": ([ctypes.POINTER(hd_geometry), ctypes.POINTER(hd_params)] +
+                              [_VP] * 6 + [_I64, _VP, _VP, _VP], ctypes.c_int),
     "hd_scan_set_profiling": ([_VP, _I32], ctypes.c_int),
     "hd_scan_get_profile": ([_VP, ctypes.POINTER(hd_profile)], ctypes.c_int),
 }
@@ -277,6 +279,27 @@ def hd_scan_get_profile(scan: int) -> dict:
     p = hd_profile()
     _check(load().hd_scan_get_profile(scan, ctypes.byref(p)), "hd_scan_get_profile")
     return p.as_dict()
+
+
+def hd_accumulate_noalloc(geometry, params, angle_deg, u_in, v_in, u_out, v_out, wepl, N, M,
+                          stream=None) -> None:
+    """Allocation-free accumulation into caller-owned device count volumes
+    (for callers that cannot allocate; see hulld.h).  All arrays are torch
+    CUDA tensors; N or M may be None when its class is not requested."""
+    g = _geometry(geometry)
+    p = _params(params)
+    arrs = [angle_deg, u_in, v_in, u_out, v_out, wepl]
+    ptrs = []
+    for a in arrs:
+        ptr, on = _ptr(a)
+        if not on:
+            raise ValueError("hd_accumulate_noalloc takes device arrays")
+        ptrs.append(ptr)
+    n = len(arrs[0])
+    np_ = _ptr(N)[0] if N is not None else None
+    mp_ = _ptr(M)[0] if M is not None else None
+    _check(load().hd_accumulate_noalloc(ctypes.byref(g), ctypes.byref(p), *ptrs, n, np_, mp_,
+                                        _stream(stream)), "hd_accumulate_noalloc")
 
 
 def hd_classify(wepl, params=None, cls_out=None, stream=None):
