@@ -201,9 +201,15 @@ hd_status validate(const hd_geometry *g, const hd_params *p)
     return HD_OK;
 }
 
-// Pairs of a chunk of n records: typical paths touch one or two tiles; a
-// record that does not fit the pair budget takes the global-memory path.
-constexpr int64_t kPairsPerRecord = 2;
+// Pairs of a chunk of n records: a path nearly parallel to the slices
+// touches one or two slabs per x-y tile it crosses (its bounding box is what
+// is counted); a record that does not fit the pair budget takes the
+// global-memory path.
+int64_t pairs_per_record(const hd::TilePlan &tp)
+{
+    int64_t k = 2 * static_cast<int64_t>(tp.ntx) * tp.nty;
+    return k < tp.max_tiles ? k : tp.max_tiles;
+}
 
 hd_status ensure_records(hd_scan *s, int64_t n, cudaStream_t st)
 {
@@ -218,7 +224,7 @@ hd_status ensure_records(hd_scan *s, int64_t n, cudaStream_t st)
     s->rec_cap = 0;
     bool ok = cudaMalloc(&s->rec_buf, sizeof(int32_t) * 7 * static_cast<size_t>(n)) == cudaSuccess;
     if (ok && s->tp.ntiles > 0) {
-        const int64_t pair_cap = kPairsPerRecord * n;
+        const int64_t pair_cap = pairs_per_record(s->tp) * n;
         const int64_t job_cap = pair_cap / s->tp.job_size + 2 * s->tp.ntiles + 1;
         ok = cudaMalloc(&s->pair_buf, sizeof(uint32_t) * 16 * static_cast<size_t>(pair_cap)) ==
                  cudaSuccess &&

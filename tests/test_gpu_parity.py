@@ -374,3 +374,58 @@ def test_config2_full_size_sampled(hd, oracle_mod):
     got_sub = _run_gpu(hd, g, sub)
     _assert_same(got_sub, ref, ALL)
     _assert_stats(got_sub, ref)
+
+
+def test_config3_streamed_sampled(hd, oracle_mod):
+    """The large streamed workload (400x400x128 voxels of 0.5x0.5x1.25 mm,
+    180 angles x 550000 histories, one add call per angle as acquired, Sec. 4
+    online mode): decisions re-derived by the oracle from the GPU counts,
+    single voxels counted by the oracle over every history, sum and
+    classification identities, and an exact oracle comparison on a 1%
+    sample of every angle."""
+    from concurrent.futures import ThreadPoolExecutor
+    g = synth.geometry_for(3)
+    picks = [(200, 200, 64), (60, 200, 64), (200, 30, 40), (340, 260, 100)]
+    totals = {(p, c): 0 for p in picks for c in (1, 2)}
+    n_miss = n_hit = n_all = 0
+    samples = []
+    pool = ThreadPoolExecutor(max_workers=8)
+    futs = []
+    with hd.Scan(g) as s:
+        for chunk in synth.iter_config_chunks(3):
+            s.add([torch.from_numpy(a).cuda() for a in chunk.arrays()])
+            n_all += len(chunk)
+            n_miss += int((chunk.wepl < 1.0).sum())
+            n_hit += int((chunk.wepl > 5.0).sum())
+            samples.append(chunk.take(np.arange(0, len(chunk), 100)))
+            for p in picks:
+                for c in (1, 2):
+                    futs.append(((p, c), pool.submit(oracle_mod.count_through_voxel, g, chunk,
+                                                     c, *p)))
+        s.finalize()
+        torch.cuda.synchronize()
+        st = s.stats()
+        N, M = s.counts(hd.HD_MSC), s.counts(hd.HD_SM)
+        H1, H2, H3 = s.mask(hd.HD_SC), s.mask(hd.HD_MSC), s.mask(hd.HD_SM)
+        mt, slope, index = s.thresholds()
+    for key, f in futs:
+        totals[key] += f.result()
+    pool.shutdown()
+    assert st["n_in"] == n_all == 180 * 550_000
+    assert st["n_miss"] == n_miss and st["n_hit"] == n_hit and st["n_reject"] == 0
+    assert int(N.sum(dtype=np.int64)) == st["steps_miss"]
+    assert int(M.sum(dtype=np.int64)) == st["steps_hit"]
+    for (p, c), val in totals.items():
+        v = p[0] + g.nx * (p[1] + g.ny * p[2])
+        assert (N if c == 1 else M)[v] == val, (p, c)
+    dims = (g.nx, g.ny, g.nz)
+    assert np.array_equal(H1, oracle_mod.sc_from_counts(N))
+    assert np.array_equal(H2, oracle_mod.msc_decide(N, dims))
+    sm = oracle_mod.sm_decide(M, dims)
+    assert np.array_equal(H3, sm["H3"]) and np.array_equal(mt, sm["Mt"])
+    assert np.array_equal(index, sm["index"])
+    sub = synth.Histories.concat(samples)
+    ref = oracle_mod.run(g, sub, threads=16)
+    got = _run_gpu(hd, g, sub)
+    _assert_same(got, ref, ALL)
+    _assert_stats(got, ref)
