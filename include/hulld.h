@@ -226,6 +226,56 @@ HD_API hd_status hd_scan_set_profiling(hd_scan *scan, int32_t enable);
  * (host synchronisation on them). */
 HD_API hd_status hd_scan_get_profile(hd_scan *scan, hd_profile *out);
 
+/* ------------------------------------------------------------------------
+ * Batched execution: many scans of different sizes in one traversal launch.
+ *
+ * A batch collects work items (a scan and a chunk of its histories, device
+ * SoA arrays) without launching anything; hd_batch_run then runs every item:
+ * classification, geometry and bucketing of each item on its own stream (they
+ * overlap on the GPU), ONE persistent traversal launch whose blocks take the
+ * jobs of all scans from a device job counter, the global-memory pass, and
+ * (with HD_BATCH_FINALIZE) each scan's decisions.  With graph replay on (the
+ * default), the first run of a batch shape is captured into a CUDA graph and
+ * later runs with the same items (same scans, pointers and sizes) replay it.
+ * Results are identical to running the items one by one with
+ * hd_scan_add_histories (and hd_scan_finalize).  Batching is the paper's
+ * online mode (Sec. 4) applied to many scans at once; the paper itself
+ * processes one data set at a time.
+ * ------------------------------------------------------------------------ */
+typedef struct hd_batch hd_batch;
+
+enum { HD_BATCH_RESET = 1, HD_BATCH_FINALIZE = 2 };
+
+typedef struct {
+    int64_t runs;            /* hd_batch_run calls */
+    int64_t graph_captures;  /* runs that captured a new CUDA graph */
+    int64_t graph_replays;   /* runs that replayed the cached graph */
+    int64_t kernel_launches; /* kernels launched (a replay counts its graph's kernels) */
+} hd_batch_stats;
+
+/* Create an empty batch on the current device for up to max_items items
+ * (1 <= max_items <= 64; at most 64 different scans per run). */
+HD_API hd_status hd_batch_create(int32_t max_items, hd_batch **out);
+HD_API hd_status hd_batch_destroy(hd_batch *batch);
+
+/* Queue n histories (device arrays, valid until the run has finished on the
+ * GPU) for `scan`.  A scan may appear several times; its items then run in
+ * successive rounds.  Nothing is launched.  HD_ERR_STATE when full. */
+HD_API hd_status hd_batch_add(hd_batch *batch, hd_scan *scan, const float *angle_deg,
+                              const float *u_in, const float *v_in, const float *u_out,
+                              const float *v_out, const float *wepl, int64_t n);
+
+/* Run and then drop the queued items, stream-ordered on `stream`.
+ * flags: HD_BATCH_RESET resets every scan of the batch first (as
+ * hd_scan_reset); HD_BATCH_FINALIZE finalizes every scan afterwards (as
+ * hd_scan_finalize).  May synchronise the stream when scan buffers grow. */
+HD_API hd_status hd_batch_run(hd_batch *batch, int32_t flags, void *stream);
+
+/* Enable (1, default) or disable (0) CUDA-graph capture and replay. */
+HD_API hd_status hd_batch_set_graph(hd_batch *batch, int32_t enable);
+
+HD_API hd_status hd_batch_get_stats(hd_batch *batch, hd_batch_stats *out);
+
 /* Allocation-free accumulation of path counts, for callers that cannot
  * allocate device memory when they run it (inside a stream capture that must
  * stay free of allocation nodes, under a memory pool that forbids

@@ -47,9 +47,8 @@ struct DeviceGuard {
     }
 };
 
-constexpr int64_t kChunk = int64_t(1) << 24;  // histories per internal launch pair
+constexpr int64_t kChunk = int64_t(1) << 25;  // histories per internal launch sequence
 constexpr int64_t kMaxScanHistories = 4294967295LL;
-constexpr int kTileSmemBytes = 200 * 1024;  // shared memory per block for a private tile
 
 // theta_i = round(atan(2^-i) * 180/pi * 2^30), K = round(2^30 prod (1 + 2^-2i)^-1/2),
 // evaluated in double; the rounding is accepted only when the value is well
@@ -98,6 +97,9 @@ struct hd_scan {
     uint32_t *pair_buf = nullptr;  // hd::kPackedWords arrays of tp.pair_cap
     hd::TileJob *jobs = nullptr;
     int64_t job_cap = 0;
+    hd::ScanDesc *desc_dev = nullptr;  // this scan's traversal descriptor
+    hd::ScanDesc desc_host{};
+    bool desc_dirty = true;
     uint32_t *tile_count = nullptr;   // 2 * ntiles
     uint32_t *tile_cursor = nullptr;  // 2 * ntiles
     float *staging = nullptr;
@@ -172,7 +174,7 @@ void free_scan(hd_scan *s)
     void *ptrs[] = {s->N, s->M, s->carve, s->H1, s->H2, s->H3, s->bits_out, s->slice_key,
                     s->mt, s->slope, s->index, s->ctrl, s->rec_buf, s->staging,
                     s->compact_blocks, s->d_count, s->compact_out, s->pair_buf, s->jobs,
-                    s->tile_count, s->tile_cursor};
+                    s->tile_count, s->tile_cursor, s->desc_dev};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     delete s;
@@ -241,6 +243,7 @@ hd_status ensure_records(hd_scan *s, int64_t n, cudaStream_t st)
         return HD_ERR_NOMEM;
     }
     s->rec_cap = n;
+    s->desc_dirty = true;
     return HD_OK;
 }
 
@@ -284,7 +287,7 @@ void make_tile_plan(hd_scan *s)
 {
     hd::TilePlan &tp = s->tp;
     const int nx = s->geom.nx, ny = s->geom.ny, nz = s->geom.nz;
-    const int budget = kTileSmemBytes / 4;
+    const int budget = hd::kTileSmemBytes / 4;
     tp.nx = nx;
     tp.ny = ny;
     tp.nz = nz;
@@ -322,19 +325,44 @@ void make_tile_plan(hd_scan *s)
     tp.pair_cap = 0;
 }
 
-hd_status run_chunk(hd_scan *s, const hd::Inputs &in, int64_t n, cudaStream_t st)
+hd::ScanDesc make_desc(const hd_scan *s)
+{
+    hd::ScanDesc d{};
+    d.tp = s->tp;
+    d.pairs = pairs_of(s);
+    d.jobs = s->jobs;
+    d.ctrl = s->ctrl;
+    d.N = s->N;
+    d.M = s->M;
+    d.carve = s->carve;
+    return d;
+}
+
+hd_status upload_desc(hd_scan *s, cudaStream_t st)
+{
+    if (!s->desc_dirty) return HD_OK;
+    s->desc_host = make_desc(s);
+    HD_CUDA(cudaMemcpyAsync(s->desc_dev, &s->desc_host, sizeof(hd::ScanDesc),
+                            cudaMemcpyHostToDevice, st));
+    HD_CUDA(cudaStreamSynchronize(st));  // desc_host may change before the copy ran
+    s->desc_dirty = false;
+    return HD_OK;
+}
+
+// Classification, geometry and bucketing of one chunk (everything before
+// the traversal).
+hd_status stage_prepare(hd_scan *s, const hd::Inputs &in, int64_t n, cudaStream_t st)
 {
     const uint32_t m = s->params.methods;
     const int use_miss = (m & (HD_SC | HD_MSC)) ? 1 : 0;
     const int use_hit = (m & HD_SM) ? 1 : 0;
     const hd::Records rec = records_of(s, n);
     hd::TilePlan tp = s->tp;
-    if (s->trace_grid <= 0) tp.ntiles = 0;  // tiled path unavailable: global path only
+    if (s->trace_grid <= 0) tp.ntiles = 0;
     HD_CUDA(cudaMemsetAsync(&s->ctrl->rec_miss, 0,
                             sizeof(hd::Ctrl) - offsetof(hd::Ctrl, rec_miss), st));
     if (tp.ntiles > 0)
         HD_CUDA(cudaMemsetAsync(s->tile_count, 0, sizeof(uint32_t) * 2 * tp.ntiles, st));
-    cudaEvent_t e0 = prof_begin(s, st);
     HD_CUDA(hd::launch_ingest(in, n, s->gq, s->cordic, s->params.wepl_miss_lt,
                               s->params.wepl_hit_gt, use_miss, use_hit, tp, rec, s->ctrl,
                               s->tile_count, s->sm_count, st));
@@ -344,19 +372,74 @@ hd_status run_chunk(hd_scan *s, const hd::Inputs &in, int64_t n, cudaStream_t st
         HD_CUDA(hd::launch_scatter(tp, rec, s->ctrl, s->tile_cursor, pairs_of(s), n, st));
         s->launches += 2;
     }
+    return HD_OK;
+}
+
+// Records outside the tiled path, walked with global-memory updates.
+hd_status stage_global(hd_scan *s, int64_t n, cudaStream_t st)
+{
+    HD_CUDA(hd::launch_trace_global(records_of(s, n), s->ctrl, n, s->gq, s->N, s->M, s->carve,
+                                    0, s->sm_count, st));
+    s->launches += 1;
+    return HD_OK;
+}
+
+hd_status stage_reset(hd_scan *scan, cudaStream_t st)
+{
+    const size_t V = static_cast<size_t>(scan->V);
+    if (scan->N) HD_CUDA(cudaMemsetAsync(scan->N, 0, sizeof(uint32_t) * V, st));
+    if (scan->M) HD_CUDA(cudaMemsetAsync(scan->M, 0, sizeof(uint32_t) * V, st));
+    if (scan->carve) HD_CUDA(cudaMemsetAsync(scan->carve, 0xff, sizeof(uint32_t) * scan->words, st));
+    HD_CUDA(cudaMemsetAsync(scan->ctrl, 0, sizeof(hd::Ctrl), st));
+    return HD_OK;
+}
+
+hd_status stage_finalize(hd_scan *scan, cudaStream_t st)
+{
+    hd::DecideArgs a{};
+    a.nx = scan->geom.nx;
+    a.ny = scan->geom.ny;
+    a.nz = scan->geom.nz;
+    a.methods = static_cast<int32_t>(scan->params.methods);
+    a.nt = scan->params.msc_nt;
+    a.nbhd = scan->params.msc_nbhd;
+    a.sm_ge = scan->params.sm_ge;
+    a.sm_per_slice = scan->params.sm_per_slice;
+    a.N = scan->N;
+    a.M = scan->M;
+    a.carve = scan->carve;
+    a.slice_key = scan->slice_key;
+    a.mt = scan->mt;
+    a.slope = scan->slope;
+    a.index = scan->index;
+    a.H1 = scan->H1;
+    a.H2 = scan->H2;
+    a.H3 = scan->H3;
+    HD_CUDA(hd::launch_finalize(a, scan->sm_count, st));
+    return HD_OK;
+}
+
+int finalize_launches(const hd_scan *scan) { return (scan->params.methods & HD_SM) ? 3 : 1; }
+
+hd_status run_chunk(hd_scan *s, const hd::Inputs &in, int64_t n, cudaStream_t st)
+{
+    hd_status r = upload_desc(s, st);
+    if (r != HD_OK) return r;
+    cudaEvent_t e0 = prof_begin(s, st);
+    r = stage_prepare(s, in, n, st);
+    if (r != HD_OK) return r;
     prof_end(s, 0, e0, st);
     cudaEvent_t e1 = prof_begin(s, st);
-    if (tp.ntiles > 0) {
-        HD_CUDA(hd::launch_trace_tiles(tp, pairs_of(s), s->jobs, s->ctrl, s->N, s->M, s->carve,
+    if (s->tp.ntiles > 0 && s->trace_grid > 0) {
+        HD_CUDA(hd::launch_trace_tiles(s->desc_dev, 1, &s->ctrl->job_next, s->tp.tile_words,
                                        s->trace_grid, st));
         s->launches += 1;
         if (s->profiling) s->trace_launches += 1;
     }
     prof_end(s, 1, e1, st);
     cudaEvent_t e2 = prof_begin(s, st);
-    HD_CUDA(hd::launch_trace_global(rec, s->ctrl, n, s->gq, s->N, s->M, s->carve, 0,
-                                    s->sm_count, st));
-    s->launches += 1;
+    r = stage_global(s, n, st);
+    if (r != HD_OK) return r;
     prof_end(s, 3, e2, st);
     return HD_OK;
 }
@@ -451,10 +534,11 @@ hd_status hd_scan_create(const hd_geometry *geom, const hd_params *params, hd_sc
     if (s->tp.ntiles > 0) {
         alloc(reinterpret_cast<void **>(&s->tile_count), sizeof(uint32_t) * 2 * s->tp.ntiles);
         alloc(reinterpret_cast<void **>(&s->tile_cursor), sizeof(uint32_t) * 2 * s->tp.ntiles);
-        const int per_sm = hd::trace_tiles_occupancy(s->tp);
+        const int per_sm = hd::trace_tiles_occupancy(s->tp.tile_words);
         s->trace_grid = per_sm > 0 ? per_sm * s->sm_count : 0;
     }
     alloc(reinterpret_cast<void **>(&s->ctrl), sizeof(hd::Ctrl));
+    alloc(reinterpret_cast<void **>(&s->desc_dev), sizeof(hd::ScanDesc));
     if (!ok) {
         free_scan(s);
         return HD_ERR_NOMEM;
@@ -484,12 +568,8 @@ hd_status hd_scan_reset(hd_scan *scan, void *stream)
     if (!scan) return HD_ERR_ARG;
     DeviceGuard g(scan->device);
     if (!g.ok) return HD_ERR_CUDA;
-    cudaStream_t st = static_cast<cudaStream_t>(stream);
-    const size_t V = static_cast<size_t>(scan->V);
-    if (scan->N) HD_CUDA(cudaMemsetAsync(scan->N, 0, sizeof(uint32_t) * V, st));
-    if (scan->M) HD_CUDA(cudaMemsetAsync(scan->M, 0, sizeof(uint32_t) * V, st));
-    if (scan->carve) HD_CUDA(cudaMemsetAsync(scan->carve, 0xff, sizeof(uint32_t) * scan->words, st));
-    HD_CUDA(cudaMemsetAsync(scan->ctrl, 0, sizeof(hd::Ctrl), st));
+    const hd_status r = stage_reset(scan, static_cast<cudaStream_t>(stream));
+    if (r != HD_OK) return r;
     scan->n_total = 0;
     scan->finalized = false;
     return HD_OK;
@@ -542,29 +622,11 @@ hd_status hd_scan_finalize(hd_scan *scan, void *stream)
     if (!scan) return HD_ERR_ARG;
     DeviceGuard g(scan->device);
     if (!g.ok) return HD_ERR_CUDA;
-    hd::DecideArgs a{};
-    a.nx = scan->geom.nx;
-    a.ny = scan->geom.ny;
-    a.nz = scan->geom.nz;
-    a.methods = static_cast<int32_t>(scan->params.methods);
-    a.nt = scan->params.msc_nt;
-    a.nbhd = scan->params.msc_nbhd;
-    a.sm_ge = scan->params.sm_ge;
-    a.sm_per_slice = scan->params.sm_per_slice;
-    a.N = scan->N;
-    a.M = scan->M;
-    a.carve = scan->carve;
-    a.slice_key = scan->slice_key;
-    a.mt = scan->mt;
-    a.slope = scan->slope;
-    a.index = scan->index;
-    a.H1 = scan->H1;
-    a.H2 = scan->H2;
-    a.H3 = scan->H3;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     cudaEvent_t e0 = prof_begin(scan, st);
-    HD_CUDA(hd::launch_finalize(a, scan->sm_count, st));
-    scan->launches += (scan->params.methods & HD_SM) ? 3 : 1;
+    const hd_status r = stage_finalize(scan, st);
+    if (r != HD_OK) return r;
+    scan->launches += finalize_launches(scan);
     prof_end(scan, 2, e0, st);
     scan->finalized = true;
     return HD_OK;
@@ -777,6 +839,314 @@ hd_status hd_classify(const float *wepl, int64_t n, const hd_params *params, uin
     cudaFree(dw);
     cudaFree(dc);
     return r;
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------------ batches
+
+struct hd_batch {
+    int device = 0;
+    int sm_count = 0;
+    int max_items = 0;
+    struct Item {
+        hd_scan *scan;
+        hd::Inputs in;
+        int64_t n;
+        bool first = false;  // the scan's first item in this run (reset here)
+        bool last = false;   // the scan's last item in this run (finalize here)
+    };
+    std::vector<Item> items;
+    hd::ScanDesc *descs_dev = nullptr;  // kMaxBatch descriptors
+    int *job_counter = nullptr;
+    static constexpr int kSide = 8;
+    cudaStream_t side[kSide] = {};
+    cudaEvent_t fork = nullptr;
+    cudaEvent_t join[kSide] = {};
+    bool use_graph = true;
+    cudaGraphExec_t exec = nullptr;
+    std::vector<uintptr_t> key;  // items and flags the cached graph was made for
+    int64_t graph_kernels = 0;
+    hd_batch_stats stats{};
+};
+
+namespace {
+
+void free_batch(hd_batch *b)
+{
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    for (auto &st : b->side)
+        if (st) cudaStreamDestroy(st);
+    for (auto &e : b->join)
+        if (e) cudaEventDestroy(e);
+    if (b->fork) cudaEventDestroy(b->fork);
+    if (b->descs_dev) cudaFree(b->descs_dev);
+    if (b->job_counter) cudaFree(b->job_counter);
+    delete b;
+}
+
+// One round: every item of `round` (distinct scans), issued on `st` with
+// the per-scan stages forked to the side streams.  Returns the number of
+// kernels issued through *kernels.
+hd_status issue_round(hd_batch *b, const std::vector<hd_batch::Item> &round, int flags,
+                      int grid, cudaStream_t st, int64_t *kernels)
+{
+    const int n_items = static_cast<int>(round.size());
+    int max_words = 0;
+    bool any_tiled = false;
+    for (const auto &it : round) {
+        if (it.scan->tp.ntiles > 0 && it.scan->trace_grid > 0) {
+            any_tiled = true;
+            if (it.scan->tp.tile_words > max_words) max_words = it.scan->tp.tile_words;
+        }
+    }
+    auto fork = [&]() -> hd_status {
+        HD_CUDA(cudaEventRecord(b->fork, st));
+        for (int k = 0; k < hd_batch::kSide; ++k) HD_CUDA(cudaStreamWaitEvent(b->side[k], b->fork, 0));
+        return HD_OK;
+    };
+    auto join = [&]() -> hd_status {
+        for (int k = 0; k < hd_batch::kSide; ++k) {
+            HD_CUDA(cudaEventRecord(b->join[k], b->side[k]));
+            HD_CUDA(cudaStreamWaitEvent(st, b->join[k], 0));
+        }
+        return HD_OK;
+    };
+    hd_status r = fork();
+    if (r != HD_OK) return r;
+    for (int i = 0; i < n_items; ++i) {
+        hd_scan *s = round[i].scan;
+        cudaStream_t ss = b->side[i % hd_batch::kSide];
+        if (round[i].first && (flags & HD_BATCH_RESET)) {
+            r = stage_reset(s, ss);
+            if (r != HD_OK) return r;
+        }
+        r = stage_prepare(s, round[i].in, round[i].n, ss);
+        if (r != HD_OK) return r;
+        *kernels += 1 + ((s->tp.ntiles > 0 && s->trace_grid > 0) ? 2 : 0);
+    }
+    r = join();
+    if (r != HD_OK) return r;
+    if (any_tiled) {
+        HD_CUDA(cudaMemsetAsync(b->job_counter, 0, sizeof(int), st));
+        HD_CUDA(hd::launch_trace_tiles(b->descs_dev, n_items, b->job_counter, max_words, grid, st));
+        *kernels += 1;
+    }
+    r = fork();
+    if (r != HD_OK) return r;
+    for (int i = 0; i < n_items; ++i) {
+        hd_scan *s = round[i].scan;
+        cudaStream_t ss = b->side[i % hd_batch::kSide];
+        r = stage_global(s, round[i].n, ss);
+        if (r != HD_OK) return r;
+        *kernels += 1;
+        if (round[i].last && (flags & HD_BATCH_FINALIZE)) {
+            r = stage_finalize(s, ss);
+            if (r != HD_OK) return r;
+            *kernels += finalize_launches(s);
+        }
+    }
+    return join();
+}
+
+}  // namespace
+
+extern "C" {
+
+hd_status hd_batch_create(int32_t max_items, hd_batch **out)
+{
+    if (!out || max_items < 1 || max_items > hd::kMaxBatch) return HD_ERR_ARG;
+    *out = nullptr;
+    hd_batch *b = new (std::nothrow) hd_batch();
+    if (!b) return HD_ERR_NOMEM;
+    b->max_items = max_items;
+    cudaError_t e = cudaGetDevice(&b->device);
+    if (e == cudaSuccess)
+        e = cudaDeviceGetAttribute(&b->sm_count, cudaDevAttrMultiProcessorCount, b->device);
+    for (int k = 0; e == cudaSuccess && k < hd_batch::kSide; ++k) {
+        e = cudaStreamCreateWithFlags(&b->side[k], cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->join[k], cudaEventDisableTiming);
+    }
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaMalloc(&b->descs_dev, sizeof(hd::ScanDesc) * hd::kMaxBatch);
+    if (e == cudaSuccess) e = cudaMalloc(&b->job_counter, sizeof(int));
+    if (e != cudaSuccess) {
+        note_cuda(e, "hd_batch_create");
+        free_batch(b);
+        return HD_ERR_CUDA;
+    }
+    *out = b;
+    return HD_OK;
+}
+
+hd_status hd_batch_destroy(hd_batch *batch)
+{
+    if (!batch) return HD_OK;
+    DeviceGuard g(batch->device);
+    cudaDeviceSynchronize();
+    free_batch(batch);
+    return HD_OK;
+}
+
+hd_status hd_batch_add(hd_batch *batch, hd_scan *scan, const float *angle_deg,
+                       const float *u_in, const float *v_in, const float *u_out,
+                       const float *v_out, const float *wepl, int64_t n)
+{
+    if (!batch || !scan || n < 0) return HD_ERR_ARG;
+    if (n > 0 && (!angle_deg || !u_in || !v_in || !u_out || !v_out || !wepl)) return HD_ERR_ARG;
+    if (scan->device != batch->device) return HD_ERR_ARG;
+    if (static_cast<int>(batch->items.size()) >= batch->max_items) return HD_ERR_STATE;
+    hd_batch::Item it;
+    it.scan = scan;
+    it.in = hd::Inputs{angle_deg, u_in, v_in, u_out, v_out, wepl};
+    it.n = n;
+    batch->items.push_back(it);
+    return HD_OK;
+}
+
+hd_status hd_batch_set_graph(hd_batch *batch, int32_t enable)
+{
+    if (!batch) return HD_ERR_ARG;
+    batch->use_graph = enable != 0;
+    return HD_OK;
+}
+
+hd_status hd_batch_get_stats(hd_batch *batch, hd_batch_stats *out)
+{
+    if (!batch || !out) return HD_ERR_ARG;
+    *out = batch->stats;
+    return HD_OK;
+}
+
+hd_status hd_batch_run(hd_batch *batch, int32_t flags, void *stream)
+{
+    if (!batch) return HD_ERR_ARG;
+    if (flags & ~(HD_BATCH_RESET | HD_BATCH_FINALIZE)) return HD_ERR_ARG;
+    DeviceGuard g(batch->device);
+    if (!g.ok) return HD_ERR_CUDA;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    auto items = batch->items;
+    batch->items.clear();
+    if (items.empty()) return HD_OK;
+    for (size_t i = 0; i < items.size(); ++i) {
+        items[i].first = items[i].last = true;
+        for (size_t j = 0; j < i; ++j)
+            if (items[j].scan == items[i].scan) items[i].first = false;
+        for (size_t j = i + 1; j < items.size(); ++j)
+            if (items[j].scan == items[i].scan) items[i].last = false;
+    }
+    // rounds: the k-th item of each scan goes to round k
+    std::vector<std::vector<hd_batch::Item>> rounds;
+    std::vector<std::pair<hd_scan *, int>> seen;
+    for (const auto &it : items) {
+        int k = 0;
+        for (auto &p : seen)
+            if (p.first == it.scan) k = ++p.second;
+        if (k == 0) seen.push_back({it.scan, 0});
+        if (static_cast<int>(rounds.size()) <= k) rounds.emplace_back();
+        rounds[k].push_back(it);
+    }
+    // host-side preparation, outside any capture: buffers, limits, descriptors
+    for (const auto &it : items) {
+        hd_scan *s = it.scan;
+        if (it.n > kChunk) return HD_ERR_RANGE;
+        hd_status r = ensure_records(s, it.n > 0 ? it.n : 1, st);
+        if (r != HD_OK) return r;
+        r = upload_desc(s, st);
+        if (r != HD_OK) return r;
+    }
+    for (const auto &p : seen) {
+        uint64_t total = (flags & HD_BATCH_RESET) ? 0 : p.first->n_total;
+        for (const auto &it : items)
+            if (it.scan == p.first) total += static_cast<uint64_t>(it.n);
+        if (total > static_cast<uint64_t>(kMaxScanHistories)) return HD_ERR_OVERFLOW;
+    }
+    std::vector<uintptr_t> key;
+    key.push_back(static_cast<uintptr_t>(flags));
+    for (const auto &it : items) {
+        key.push_back(reinterpret_cast<uintptr_t>(it.scan));
+        key.push_back(reinterpret_cast<uintptr_t>(it.in.angle));
+        key.push_back(reinterpret_cast<uintptr_t>(it.in.u_in));
+        key.push_back(reinterpret_cast<uintptr_t>(it.in.v_in));
+        key.push_back(reinterpret_cast<uintptr_t>(it.in.u_out));
+        key.push_back(reinterpret_cast<uintptr_t>(it.in.v_out));
+        key.push_back(reinterpret_cast<uintptr_t>(it.in.wepl));
+        key.push_back(static_cast<uintptr_t>(it.n));
+        key.push_back(reinterpret_cast<uintptr_t>(it.scan->desc_dev));
+        key.push_back(reinterpret_cast<uintptr_t>(it.scan->pair_buf));
+    }
+    // the legacy default stream cannot be captured: run directly there
+    const bool graphable = batch->use_graph && rounds.size() == 1 && st != nullptr;
+    int max_words = 1;
+    for (const auto &it : items)
+        if (it.scan->tp.ntiles > 0 && it.scan->tp.tile_words > max_words)
+            max_words = it.scan->tp.tile_words;
+    const int per_sm = hd::trace_tiles_occupancy(max_words);
+    const int grid = (per_sm > 0 ? per_sm : 1) * batch->sm_count;
+    batch->stats.runs += 1;
+    if (graphable && batch->exec && key == batch->key) {
+        HD_CUDA(cudaGraphLaunch(batch->exec, st));
+        batch->stats.graph_replays += 1;
+        batch->stats.kernel_launches += batch->graph_kernels;
+    } else {
+        // descriptor table of the (single-round) traversal; multi-round runs
+        // upload one table per round below
+        int64_t kernels = 0;
+        if (graphable) {
+            std::vector<hd::ScanDesc> descs;
+            for (const auto &it : rounds[0]) descs.push_back(it.scan->desc_host);
+            HD_CUDA(cudaMemcpyAsync(batch->descs_dev, descs.data(),
+                                    sizeof(hd::ScanDesc) * descs.size(), cudaMemcpyHostToDevice, st));
+            HD_CUDA(cudaStreamSynchronize(st));
+            if (batch->exec) {
+                cudaGraphExecDestroy(batch->exec);
+                batch->exec = nullptr;
+            }
+            HD_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+            hd_status r = issue_round(batch, rounds[0], flags, grid, st, &kernels);
+            cudaGraph_t graph = nullptr;
+            const cudaError_t ec = cudaStreamEndCapture(st, &graph);
+            if (r != HD_OK) {
+                if (graph) cudaGraphDestroy(graph);
+                return r;
+            }
+            if (ec != cudaSuccess) {
+                note_cuda(ec, "hd_batch_run: capture");
+                return HD_ERR_CUDA;
+            }
+            const cudaError_t ei = cudaGraphInstantiate(&batch->exec, graph, 0);
+            cudaGraphDestroy(graph);
+            if (ei != cudaSuccess) {
+                note_cuda(ei, "hd_batch_run: instantiate");
+                batch->exec = nullptr;
+                return HD_ERR_CUDA;
+            }
+            batch->key = key;
+            batch->graph_kernels = kernels;
+            HD_CUDA(cudaGraphLaunch(batch->exec, st));
+            batch->stats.graph_captures += 1;
+        } else {
+            for (size_t k = 0; k < rounds.size(); ++k) {
+                std::vector<hd::ScanDesc> descs;
+                for (const auto &it : rounds[k]) descs.push_back(it.scan->desc_host);
+                HD_CUDA(cudaMemcpyAsync(batch->descs_dev, descs.data(),
+                                        sizeof(hd::ScanDesc) * descs.size(),
+                                        cudaMemcpyHostToDevice, st));
+                HD_CUDA(cudaStreamSynchronize(st));
+                hd_status r = issue_round(batch, rounds[k], flags, grid, st, &kernels);
+                if (r != HD_OK) return r;
+            }
+        }
+        batch->stats.kernel_launches += kernels;
+    }
+    for (const auto &p : seen) {
+        hd_scan *s = p.first;
+        if (flags & HD_BATCH_RESET) s->n_total = 0;
+        for (const auto &it : items)
+            if (it.scan == s) s->n_total += static_cast<uint64_t>(it.n);
+        s->finalized = (flags & HD_BATCH_FINALIZE) != 0;
+    }
+    return HD_OK;
 }
 
 }  // extern "C"

@@ -12,6 +12,7 @@ constexpr int64_t kQ16 = 65536;
 constexpr int kMaxN = 4096;
 constexpr int kMaxTiles = 2048;       // tiles per class for the shared-memory path
 constexpr int kTraceThreads = 512;    // threads per block of the tiled traversal
+constexpr int kTileSmemBytes = 200 * 1024;  // shared memory per block for a private tile
 
 // Gantry-rotation constants: theta[i] = round(atan(2^-i) * 180/pi * 2^30)
 // (degrees, 30 fractional bits) and K = round(2^30 prod (1 + 2^-2i)^-1/2).
@@ -80,6 +81,18 @@ struct TileJob {
     int end;
 };
 
+// Everything the traversal kernel needs about one scan; a batch passes a
+// table of these and one job counter for all of them.
+struct ScanDesc {
+    TilePlan tp;
+    Pairs pairs;
+    const TileJob *jobs;
+    Ctrl *ctrl;  // njobs of the scan (read) and its step counters (added to)
+    uint32_t *N, *M, *carve;
+};
+
+constexpr int kMaxBatch = 64;  // scans per batched traversal launch
+
 struct Inputs {
     const float *angle, *u_in, *v_in, *u_out, *v_out, *wepl;
 };
@@ -96,9 +109,11 @@ cudaError_t launch_plan(const TilePlan &tp, const uint32_t *tile_count, uint32_t
 cudaError_t launch_scatter(const TilePlan &tp, const Records &rec, const Ctrl *ctrl,
                            uint32_t *tile_cursor, const Pairs &pairs, int64_t n, cudaStream_t s);
 
-cudaError_t launch_trace_tiles(const TilePlan &tp, const Pairs &pairs, const TileJob *jobs,
-                               Ctrl *ctrl, uint32_t *N, uint32_t *M, uint32_t *carve,
-                               int grid, cudaStream_t s);
+// Persistent traversal over the jobs of nscans scans (descs on the device),
+// handed out through *job_counter (zero before the launch).  smem_words is
+// the largest tile of the scans.
+cudaError_t launch_trace_tiles(const ScanDesc *descs, int nscans, int *job_counter,
+                               int smem_words, int grid, cudaStream_t s);
 
 // Global-memory traversal of the records whose status is 2 (or of every
 // record when all_records is set).
@@ -109,8 +124,9 @@ cudaError_t launch_trace_global(const Records &rec, Ctrl *ctrl, int64_t upper, c
 cudaError_t launch_classify(const float *wepl, int64_t n, float tau_l, float tau_h,
                             uint8_t *cls, cudaStream_t s);
 
-// Blocks per SM the tiled traversal can keep resident with this plan.
-int trace_tiles_occupancy(const TilePlan &tp);
+// Blocks per SM the tiled traversal can keep resident with this much shared
+// memory per block.
+int trace_tiles_occupancy(int smem_words);
 
 struct DecideArgs {
     int32_t nx, ny, nz;

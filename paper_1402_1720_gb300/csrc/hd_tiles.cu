@@ -237,24 +237,43 @@ __device__ __forceinline__ void rows_prefix(int16_t *a, int rows, int len)
 
 template <int kThreads>
 __global__ void __launch_bounds__(kThreads, 1) trace_tiles_kernel(
-    TilePlan tp, Pairs pairs, const TileJob *__restrict__ jobs, Ctrl *ctrl, uint32_t *N,
-    uint32_t *M, uint32_t *carve)
+    const ScanDesc *__restrict__ descs, int nscans, int *job_counter)
 {
     extern __shared__ uint32_t tile[];
-    __shared__ int s_job;
+    __shared__ int s_job, s_scan;
     __shared__ unsigned s_next;
+    __shared__ int s_prefix[kMaxBatch + 1];
     const unsigned lane = threadIdx.x & 31u;
     const unsigned warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-    unsigned long long st_m = 0, st_h = 0;
+    // jobs of scan k are the global job numbers [s_prefix[k], s_prefix[k+1])
+    if (threadIdx.x == 0) {
+        int acc = 0;
+        for (int k = 0; k < nscans; ++k) {
+            s_prefix[k] = acc;
+            acc += descs[k].ctrl->njobs;
+        }
+        s_prefix[nscans] = acc;
+    }
+    __syncthreads();
+    const int total_jobs = s_prefix[nscans];
     for (;;) {
         if (threadIdx.x == 0) {
-            s_job = atomicAdd(&ctrl->job_next, 1);
+            const int J = atomicAdd(job_counter, 1);
+            int k = 0;
+            while (k + 1 < nscans && s_prefix[k + 1] <= J) ++k;
+            s_job = J;
+            s_scan = k;
             s_next = 0;
         }
         __syncthreads();
-        const int j = s_job;
-        if (j >= ctrl->njobs) break;
-        const TileJob job = jobs[j];
+        if (s_job >= total_jobs) break;
+        const ScanDesc &d = descs[s_scan];
+        const TilePlan tp = d.tp;
+        const Pairs pairs = d.pairs;
+        uint32_t *const N = d.N;
+        uint32_t *const M = d.M;
+        uint32_t *const carve = d.carve;
+        const TileJob job = d.jobs[s_job - s_prefix[s_scan]];
         const int tix = job.tile % tp.ntx;
         const int tiy = (job.tile / tp.ntx) % tp.nty;
         const int tiz = job.tile / (tp.ntx * tp.nty);
@@ -377,17 +396,12 @@ __global__ void __launch_bounds__(kThreads, 1) trace_tiles_kernel(
                 }
             }
         }
-        if (job.cls == 0) st_m += steps; else st_h += steps;
-        __syncthreads();
-    }
+        // voxel memberships of this job, added to its scan's counters
+        unsigned long long st = steps;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        st_m += __shfl_xor_sync(kFull, st_m, o);
-        st_h += __shfl_xor_sync(kFull, st_h, o);
-    }
-    if (lane == 0) {
-        if (st_m) atomicAdd(&ctrl->steps_miss, st_m);
-        if (st_h) atomicAdd(&ctrl->steps_hit, st_h);
+        for (int o = 16; o > 0; o >>= 1) st += __shfl_xor_sync(kFull, st, o);
+        if (lane == 0 && st) atomicAdd(job.cls == 0 ? &d.ctrl->steps_miss : &d.ctrl->steps_hit, st);
+        __syncthreads();
     }
 }
 
@@ -412,21 +426,20 @@ cudaError_t launch_scatter(const TilePlan &tp, const Records &rec, const Ctrl *c
     return cudaGetLastError();
 }
 
-static cudaError_t set_tile_smem(const TilePlan &tp)
+int trace_tiles_occupancy(int smem_words)
 {
-    return cudaFuncSetAttribute(trace_tiles_kernel<kTraceThreads>,
-                                cudaFuncAttributeMaxDynamicSharedMemorySize, tp.tile_words * 4);
-}
-
-int trace_tiles_occupancy(const TilePlan &tp)
-{
-    if (set_tile_smem(tp) != cudaSuccess) {
+    // allow the largest tile once, so launches (also inside graph capture)
+    // need no attribute change
+    if (cudaFuncSetAttribute(trace_tiles_kernel<kTraceThreads>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, kTileSmemBytes) !=
+        cudaSuccess) {
         cudaGetLastError();
         return 0;
     }
     int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, trace_tiles_kernel<kTraceThreads>, kTraceThreads,
-                                                      static_cast<size_t>(tp.tile_words) * 4) !=
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, trace_tiles_kernel<kTraceThreads>,
+                                                      kTraceThreads,
+                                                      static_cast<size_t>(smem_words) * 4) !=
         cudaSuccess) {
         cudaGetLastError();
         return 0;
@@ -434,14 +447,14 @@ int trace_tiles_occupancy(const TilePlan &tp)
     return nb;
 }
 
-cudaError_t launch_trace_tiles(const TilePlan &tp, const Pairs &pairs, const TileJob *jobs,
-                               Ctrl *ctrl, uint32_t *N, uint32_t *M, uint32_t *carve, int grid,
-                               cudaStream_t s)
+cudaError_t launch_trace_tiles(const ScanDesc *descs, int nscans, int *job_counter,
+                               int smem_words, int grid, cudaStream_t s)
 {
-    cudaError_t e = set_tile_smem(tp);
-    if (e != cudaSuccess) return e;
-    trace_tiles_kernel<kTraceThreads><<<grid, kTraceThreads, static_cast<size_t>(tp.tile_words) * 4, s>>>(
-        tp, pairs, jobs, ctrl, N, M, carve);
+    if (nscans < 1 || nscans > kMaxBatch || smem_words * 4 > kTileSmemBytes)
+        return cudaErrorInvalidValue;
+    trace_tiles_kernel<kTraceThreads>
+        <<<grid, kTraceThreads, static_cast<size_t>(smem_words) * 4, s>>>(descs, nscans,
+                                                                          job_counter);
     return cudaGetLastError();
 }
 

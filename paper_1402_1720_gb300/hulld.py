@@ -67,6 +67,16 @@ class hd_profile(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class hd_batch_stats(ctypes.Structure):
+    _fields_ = [("runs", ctypes.c_int64), ("graph_captures", ctypes.c_int64),
+                ("graph_replays", ctypes.c_int64), ("kernel_launches", ctypes.c_int64)]
+
+    def as_dict(self):
+        return {k: int(getattr(self, k)) for k, _ in self._fields_}
+
+
+HD_BATCH_RESET, HD_BATCH_FINALIZE = 1, 2
+
 # exported symbols and their signatures
 _VP, _I32, _I64, _SZ = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_size_t
 _SIGS = {
@@ -89,6 +99,12 @@ _SIGS = {
     "hd_accumulate_noalloc": ([ctypes.POINTER(hd_geometry), ctypes.POINTER(hd_params)] +
                               [_VP] * 6 + [_I64, _VP, _VP, _VP], ctypes.c_int),
     "hd_scan_set_profiling": ([_VP, _I32], ctypes.c_int),
+    "hd_batch_create": ([_I32, ctypes.POINTER(_VP)], ctypes.c_int),
+    "hd_batch_destroy": ([_VP], ctypes.c_int),
+    "hd_batch_add": ([_VP, _VP] + [_VP] * 6 + [_I64], ctypes.c_int),
+    "hd_batch_run": ([_VP, _I32, _VP], ctypes.c_int),
+    "hd_batch_set_graph": ([_VP, _I32], ctypes.c_int),
+    "hd_batch_get_stats": ([_VP, ctypes.POINTER(hd_batch_stats)], ctypes.c_int),
     "hd_scan_get_profile": ([_VP, ctypes.POINTER(hd_profile)], ctypes.c_int),
 }
 
@@ -317,6 +333,77 @@ def hd_classify(wepl, params=None, cls_out=None, stream=None):
         raise ValueError("wepl and cls_out must both be device or both host buffers")
     _check(load().hd_classify(wp, n, ctypes.byref(p), cp, on, _stream(stream)), "hd_classify")
     return cls_out
+
+
+def hd_batch_create(max_items: int) -> int:
+    h = _VP()
+    _check(load().hd_batch_create(int(max_items), ctypes.byref(h)), "hd_batch_create")
+    return h.value
+
+
+def hd_batch_destroy(batch: int) -> None:
+    _check(load().hd_batch_destroy(batch), "hd_batch_destroy")
+
+
+def hd_batch_add(batch: int, scan: int, angle_deg, u_in, v_in, u_out, v_out, wepl) -> None:
+    arrs = [angle_deg, u_in, v_in, u_out, v_out, wepl]
+    ptrs = []
+    for a in arrs:
+        p, on = _ptr(a)
+        if not on:
+            raise ValueError("batch items take device arrays")
+        ptrs.append(p)
+    _check(load().hd_batch_add(batch, scan, *ptrs, len(arrs[0])), "hd_batch_add")
+
+
+def hd_batch_run(batch: int, flags: int = 0, stream=None) -> None:
+    _check(load().hd_batch_run(batch, int(flags), _stream(stream)), "hd_batch_run")
+
+
+def hd_batch_set_graph(batch: int, enable: bool) -> None:
+    _check(load().hd_batch_set_graph(batch, 1 if enable else 0), "hd_batch_set_graph")
+
+
+def hd_batch_get_stats(batch: int) -> dict:
+    st = hd_batch_stats()
+    _check(load().hd_batch_get_stats(batch, ctypes.byref(st)), "hd_batch_get_stats")
+    return st.as_dict()
+
+
+class Batch:
+    """Owning handle of one hd_batch."""
+
+    def __init__(self, max_items: int = 64):
+        self.handle = hd_batch_create(max_items)
+
+    def close(self):
+        if self.handle:
+            hd_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def add(self, scan: "Scan", arrays):
+        hd_batch_add(self.handle, scan.handle, *arrays)
+
+    def run(self, flags: int = HD_BATCH_FINALIZE, stream=None):
+        hd_batch_run(self.handle, flags, stream)
+
+    def set_graph(self, enable: bool):
+        hd_batch_set_graph(self.handle, enable)
+
+    def stats(self) -> dict:
+        return hd_batch_get_stats(self.handle)
 
 
 # ------------------------------------------------------------- wrapper
