@@ -265,6 +265,14 @@ HD_API hd_status hd_batch_add(hd_batch *batch, hd_scan *scan, const float *angle
                               const float *u_in, const float *v_in, const float *u_out,
                               const float *v_out, const float *wepl, int64_t n);
 
+/* As hd_batch_add, with per-item flags: HD_BATCH_RESET resets the scan just
+ * before this item, HD_BATCH_FINALIZE finalizes it right after this item
+ * (for example when the item carries the scan's last angle). */
+HD_API hd_status hd_batch_add_item(hd_batch *batch, hd_scan *scan, const float *angle_deg,
+                                   const float *u_in, const float *v_in, const float *u_out,
+                                   const float *v_out, const float *wepl, int64_t n,
+                                   int32_t flags);
+
 /* Run and then drop the queued items, stream-ordered on `stream`.
  * flags: HD_BATCH_RESET resets every scan of the batch first (as
  * hd_scan_reset); HD_BATCH_FINALIZE finalizes every scan afterwards (as
@@ -275,6 +283,86 @@ HD_API hd_status hd_batch_run(hd_batch *batch, int32_t flags, void *stream);
 HD_API hd_status hd_batch_set_graph(hd_batch *batch, int32_t enable);
 
 HD_API hd_status hd_batch_get_stats(hd_batch *batch, hd_batch_stats *out);
+
+/* ------------------------------------------------------------------------
+ * Serving: a request loop for streamed scans (continuous batching).
+ *
+ * Clients open scans and submit per-angle chunks as they are acquired (the
+ * online mode of Sec. 4).  A worker thread admits scans first come, first
+ * served while their device footprint fits hbm_budget_bytes, and keeps up to
+ * max_in_flight batched launches queued on the GPU, each taking one pending
+ * chunk from each of up to max_batch admitted scans (one persistent
+ * traversal over all of them, as hd_batch_run).  Chunks that arrive while
+ * others are running join the next launch.  A scan's hulls are computed in
+ * the launch that carries its last chunk; they stay on the device until the
+ * client closes the scan, which returns its memory to the budget.  Results
+ * equal those of the same chunks added to a lone scan.  Times are seconds
+ * since the server was created (-1 when the event has not happened).
+ * ------------------------------------------------------------------------ */
+typedef struct hd_server hd_server;
+
+typedef struct {
+    size_t hbm_budget_bytes; /* device memory the server may give to admitted scans */
+    int64_t max_chunk;       /* largest chunk a client submits (histories) */
+    int32_t max_batch;       /* chunks of different scans per launch, 1..64 */
+    int32_t max_in_flight;   /* launches queued on the GPU at once, 1..8 */
+} hd_server_config;
+
+typedef struct {
+    double t_open, t_admit, t_first_chunk, t_last_chunk, t_ready;
+    int64_t histories;
+    int32_t chunks_submitted, chunks_done;
+    int32_t state; /* 0 waiting for admission, 1 admitted, 2 hulls ready, 3 failed */
+} hd_server_scan_info;
+
+typedef struct {
+    int64_t scans_opened, scans_admitted, scans_done;
+    int64_t chunks_submitted, chunks_launched, launches;
+    int64_t bytes_in_use; /* footprint of the admitted scans */
+} hd_server_stats;
+
+/* 64 GiB budget, chunks up to 100000 histories, 64 scans per launch, 2 in flight. */
+HD_API hd_status hd_server_config_default(hd_server_config *out);
+
+/* Start a server (and its worker thread) on the current device. */
+HD_API hd_status hd_server_create(const hd_server_config *cfg, hd_server **out);
+
+/* Stop the worker, wait for the GPU and release every scan. */
+HD_API hd_status hd_server_destroy(hd_server *server);
+
+/* Queue a scan that will receive n_chunks chunks.  HD_ERR_ADMISSION when its
+ * footprint (counts, masks and chunk scratch) can never fit the budget. */
+HD_API hd_status hd_server_open_scan(hd_server *server, const hd_geometry *geom,
+                                     const hd_params *params, int32_t n_chunks,
+                                     int64_t *scan_id);
+
+/* Submit the next chunk of a scan (1 <= n <= max_chunk; host arrays, or
+ * device arrays with on_device = 1).  The data is copied before the call
+ * returns.  HD_ERR_STATE when the scan already has all its chunks. */
+HD_API hd_status hd_server_submit_chunk(hd_server *server, int64_t scan_id,
+                                        const float *angle_deg, const float *u_in,
+                                        const float *v_in, const float *u_out,
+                                        const float *v_out, const float *wepl, int64_t n,
+                                        int32_t on_device);
+
+/* *done = 1 once the scan's hulls are ready (or it failed: see scan_status). */
+HD_API hd_status hd_server_poll(hd_server *server, int64_t scan_id, int32_t *done,
+                                hd_status *scan_status);
+
+/* Wait at most timeout_ms for the scan's hulls: HD_OK, HD_ERR_TIMEOUT, or the
+ * scan's error. */
+HD_API hd_status hd_server_wait(hd_server *server, int64_t scan_id, int64_t timeout_ms);
+
+/* The finished scan, to read with hd_scan_get_mask and the other getters
+ * (owned by the server until hd_server_close_scan). */
+HD_API hd_status hd_server_scan(hd_server *server, int64_t scan_id, hd_scan **out);
+
+HD_API hd_status hd_server_get_info(hd_server *server, int64_t scan_id,
+                                    hd_server_scan_info *out);
+HD_API hd_status hd_server_get_stats(hd_server *server, hd_server_stats *out);
+
+/* Release a scan that is finished (or has no chunk in flight). */
+HD_API hd_status hd_server_close_scan(hd_server *server, int64_t scan_id);
 
 /* Allocation-free accumulation of path counts, for callers that cannot
  * allocate device memory when they run it (inside a stream capture that must

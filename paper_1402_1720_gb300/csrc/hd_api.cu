@@ -855,6 +855,7 @@ struct hd_batch {
         int64_t n;
         bool first = false;  // the scan's first item in this run (reset here)
         bool last = false;   // the scan's last item in this run (finalize here)
+        int flags = 0;       // per-item HD_BATCH_RESET / HD_BATCH_FINALIZE
     };
     std::vector<Item> items;
     hd::ScanDesc *descs_dev = nullptr;  // kMaxBatch descriptors
@@ -917,7 +918,7 @@ hd_status issue_round(hd_batch *b, const std::vector<hd_batch::Item> &round, int
     for (int i = 0; i < n_items; ++i) {
         hd_scan *s = round[i].scan;
         cudaStream_t ss = b->side[i % hd_batch::kSide];
-        if (round[i].first && (flags & HD_BATCH_RESET)) {
+        if ((round[i].first && (flags & HD_BATCH_RESET)) || (round[i].flags & HD_BATCH_RESET)) {
             r = stage_reset(s, ss);
             if (r != HD_OK) return r;
         }
@@ -940,7 +941,8 @@ hd_status issue_round(hd_batch *b, const std::vector<hd_batch::Item> &round, int
         r = stage_global(s, round[i].n, ss);
         if (r != HD_OK) return r;
         *kernels += 1;
-        if (round[i].last && (flags & HD_BATCH_FINALIZE)) {
+        if ((round[i].last && (flags & HD_BATCH_FINALIZE)) ||
+            (round[i].flags & HD_BATCH_FINALIZE)) {
             r = stage_finalize(s, ss);
             if (r != HD_OK) return r;
             *kernels += finalize_launches(s);
@@ -992,7 +994,15 @@ hd_status hd_batch_add(hd_batch *batch, hd_scan *scan, const float *angle_deg,
                        const float *u_in, const float *v_in, const float *u_out,
                        const float *v_out, const float *wepl, int64_t n)
 {
+    return hd_batch_add_item(batch, scan, angle_deg, u_in, v_in, u_out, v_out, wepl, n, 0);
+}
+
+hd_status hd_batch_add_item(hd_batch *batch, hd_scan *scan, const float *angle_deg,
+                            const float *u_in, const float *v_in, const float *u_out,
+                            const float *v_out, const float *wepl, int64_t n, int32_t flags)
+{
     if (!batch || !scan || n < 0) return HD_ERR_ARG;
+    if (flags & ~(HD_BATCH_RESET | HD_BATCH_FINALIZE)) return HD_ERR_ARG;
     if (n > 0 && (!angle_deg || !u_in || !v_in || !u_out || !v_out || !wepl)) return HD_ERR_ARG;
     if (scan->device != batch->device) return HD_ERR_ARG;
     if (static_cast<int>(batch->items.size()) >= batch->max_items) return HD_ERR_STATE;
@@ -1000,6 +1010,7 @@ hd_status hd_batch_add(hd_batch *batch, hd_scan *scan, const float *angle_deg,
     it.scan = scan;
     it.in = hd::Inputs{angle_deg, u_in, v_in, u_out, v_out, wepl};
     it.n = n;
+    it.flags = flags;
     batch->items.push_back(it);
     return HD_OK;
 }
@@ -1064,6 +1075,7 @@ hd_status hd_batch_run(hd_batch *batch, int32_t flags, void *stream)
     std::vector<uintptr_t> key;
     key.push_back(static_cast<uintptr_t>(flags));
     for (const auto &it : items) {
+        key.push_back(static_cast<uintptr_t>(it.flags));
         key.push_back(reinterpret_cast<uintptr_t>(it.scan));
         key.push_back(reinterpret_cast<uintptr_t>(it.in.angle));
         key.push_back(reinterpret_cast<uintptr_t>(it.in.u_in));
@@ -1144,7 +1156,10 @@ hd_status hd_batch_run(hd_batch *batch, int32_t flags, void *stream)
         if (flags & HD_BATCH_RESET) s->n_total = 0;
         for (const auto &it : items)
             if (it.scan == s) s->n_total += static_cast<uint64_t>(it.n);
-        s->finalized = (flags & HD_BATCH_FINALIZE) != 0;
+        bool fin = (flags & HD_BATCH_FINALIZE) != 0;
+        for (const auto &it : items)
+            if (it.scan == s && (it.flags & HD_BATCH_FINALIZE)) fin = true;
+        s->finalized = fin;
     }
     return HD_OK;
 }

@@ -77,6 +77,32 @@ class hd_batch_stats(ctypes.Structure):
 
 HD_BATCH_RESET, HD_BATCH_FINALIZE = 1, 2
 
+
+class hd_server_config(ctypes.Structure):
+    _fields_ = [("hbm_budget_bytes", ctypes.c_size_t), ("max_chunk", ctypes.c_int64),
+                ("max_batch", ctypes.c_int32), ("max_in_flight", ctypes.c_int32)]
+
+
+class hd_server_scan_info(ctypes.Structure):
+    _fields_ = [("t_open", ctypes.c_double), ("t_admit", ctypes.c_double),
+                ("t_first_chunk", ctypes.c_double), ("t_last_chunk", ctypes.c_double),
+                ("t_ready", ctypes.c_double), ("histories", ctypes.c_int64),
+                ("chunks_submitted", ctypes.c_int32), ("chunks_done", ctypes.c_int32),
+                ("state", ctypes.c_int32)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class hd_server_stats(ctypes.Structure):
+    _fields_ = [("scans_opened", ctypes.c_int64), ("scans_admitted", ctypes.c_int64),
+                ("scans_done", ctypes.c_int64), ("chunks_submitted", ctypes.c_int64),
+                ("chunks_launched", ctypes.c_int64), ("launches", ctypes.c_int64),
+                ("bytes_in_use", ctypes.c_int64)]
+
+    def as_dict(self):
+        return {k: int(getattr(self, k)) for k, _ in self._fields_}
+
 # exported symbols and their signatures
 _VP, _I32, _I64, _SZ = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_size_t
 _SIGS = {
@@ -105,6 +131,20 @@ _SIGS = {
     "hd_batch_run": ([_VP, _I32, _VP], ctypes.c_int),
     "hd_batch_set_graph": ([_VP, _I32], ctypes.c_int),
     "hd_batch_get_stats": ([_VP, ctypes.POINTER(hd_batch_stats)], ctypes.c_int),
+    "hd_batch_add_item": ([_VP, _VP] + [_VP] * 6 + [_I64, _I32], ctypes.c_int),
+    "hd_server_config_default": ([ctypes.POINTER(hd_server_config)], ctypes.c_int),
+    "hd_server_create": ([ctypes.POINTER(hd_server_config), ctypes.POINTER(_VP)], ctypes.c_int),
+    "hd_server_destroy": ([_VP], ctypes.c_int),
+    "hd_server_open_scan": ([_VP, ctypes.POINTER(hd_geometry), ctypes.POINTER(hd_params), _I32,
+                             ctypes.POINTER(_I64)], ctypes.c_int),
+    "hd_server_submit_chunk": ([_VP, _I64] + [_VP] * 6 + [_I64, _I32], ctypes.c_int),
+    "hd_server_poll": ([_VP, _I64, ctypes.POINTER(_I32), ctypes.POINTER(ctypes.c_int)],
+                       ctypes.c_int),
+    "hd_server_wait": ([_VP, _I64, _I64], ctypes.c_int),
+    "hd_server_scan": ([_VP, _I64, ctypes.POINTER(_VP)], ctypes.c_int),
+    "hd_server_get_info": ([_VP, _I64, ctypes.POINTER(hd_server_scan_info)], ctypes.c_int),
+    "hd_server_get_stats": ([_VP, ctypes.POINTER(hd_server_stats)], ctypes.c_int),
+    "hd_server_close_scan": ([_VP, _I64], ctypes.c_int),
     "hd_scan_get_profile": ([_VP, ctypes.POINTER(hd_profile)], ctypes.c_int),
 }
 
@@ -368,6 +408,165 @@ def hd_batch_get_stats(batch: int) -> dict:
     st = hd_batch_stats()
     _check(load().hd_batch_get_stats(batch, ctypes.byref(st)), "hd_batch_get_stats")
     return st.as_dict()
+
+
+def hd_batch_add_item(batch: int, scan: int, angle_deg, u_in, v_in, u_out, v_out, wepl,
+                      flags: int = 0) -> None:
+    arrs = [angle_deg, u_in, v_in, u_out, v_out, wepl]
+    ptrs = []
+    for a in arrs:
+        p, on = _ptr(a)
+        if not on:
+            raise ValueError("batch items take device arrays")
+        ptrs.append(p)
+    _check(load().hd_batch_add_item(batch, scan, *ptrs, len(arrs[0]), int(flags)),
+           "hd_batch_add_item")
+
+
+# ------------------------------------------------------------------ serving
+def hd_server_config_default() -> hd_server_config:
+    c = hd_server_config()
+    _check(load().hd_server_config_default(ctypes.byref(c)), "hd_server_config_default")
+    return c
+
+
+def hd_server_create(cfg: hd_server_config = None) -> int:
+    cfg = cfg or hd_server_config_default()
+    h = _VP()
+    _check(load().hd_server_create(ctypes.byref(cfg), ctypes.byref(h)), "hd_server_create")
+    return h.value
+
+
+def hd_server_destroy(server: int) -> None:
+    _check(load().hd_server_destroy(server), "hd_server_destroy")
+
+
+def hd_server_open_scan(server: int, geometry, params, n_chunks: int) -> int:
+    g = _geometry(geometry)
+    p = _params(params)
+    sid = _I64()
+    _check(load().hd_server_open_scan(server, ctypes.byref(g), ctypes.byref(p), int(n_chunks),
+                                      ctypes.byref(sid)), "hd_server_open_scan")
+    return sid.value
+
+
+def hd_server_submit_chunk(server: int, scan_id: int, angle_deg, u_in, v_in, u_out, v_out,
+                           wepl) -> None:
+    arrs = [angle_deg, u_in, v_in, u_out, v_out, wepl]
+    ptrs = [_ptr(a) for a in arrs]
+    ons = {o for _, o in ptrs}
+    if len(ons) != 1:
+        raise ValueError("all six arrays must be on the device or all on the host")
+    _check(load().hd_server_submit_chunk(server, int(scan_id), *[p for p, _ in ptrs],
+                                         len(arrs[0]), ons.pop()), "hd_server_submit_chunk")
+
+
+def hd_server_poll(server: int, scan_id: int):
+    done = _I32()
+    st = ctypes.c_int()
+    _check(load().hd_server_poll(server, int(scan_id), ctypes.byref(done), ctypes.byref(st)),
+           "hd_server_poll")
+    return bool(done.value), st.value
+
+
+def hd_server_wait(server: int, scan_id: int, timeout_ms: int) -> int:
+    """Returns the status (HD_OK, HD_ERR_TIMEOUT or the scan's error)."""
+    return load().hd_server_wait(server, int(scan_id), int(timeout_ms))
+
+
+def hd_server_scan(server: int, scan_id: int) -> int:
+    h = _VP()
+    _check(load().hd_server_scan(server, int(scan_id), ctypes.byref(h)), "hd_server_scan")
+    return h.value
+
+
+def hd_server_get_info(server: int, scan_id: int) -> dict:
+    i = hd_server_scan_info()
+    _check(load().hd_server_get_info(server, int(scan_id), ctypes.byref(i)), "hd_server_get_info")
+    return i.as_dict()
+
+
+def hd_server_get_stats(server: int) -> dict:
+    st = hd_server_stats()
+    _check(load().hd_server_get_stats(server, ctypes.byref(st)), "hd_server_get_stats")
+    return st.as_dict()
+
+
+def hd_server_close_scan(server: int, scan_id: int) -> None:
+    _check(load().hd_server_close_scan(server, int(scan_id)), "hd_server_close_scan")
+
+
+class ScanView:
+    """Read access to a scan owned by someone else (e.g. the server)."""
+
+    def __init__(self, handle: int, geometry):
+        g = _geometry(geometry)
+        self.handle = handle
+        self.dims = (g.nx, g.ny, g.nz)
+        self.V = g.nx * g.ny * g.nz
+
+    def mask(self, method: int, layout: int = HD_MASK_U8, out=None, stream=None):
+        return Scan.mask(self, method, layout, out, stream)
+
+    def counts(self, method: int, out=None, stream=None):
+        return Scan.counts(self, method, out, stream)
+
+    def thresholds(self, stream=None):
+        return hd_scan_get_thresholds(self.handle, self.dims[2], stream)
+
+    def stats(self, stream=None):
+        return hd_scan_get_stats(self.handle, stream)
+
+    def sync(self, stream=None):
+        hd_scan_get_stats(self.handle, stream)
+
+
+class Server:
+    """Owning handle of one hd_server."""
+
+    def __init__(self, cfg: hd_server_config = None):
+        self.handle = hd_server_create(cfg)
+
+    def close(self):
+        if self.handle:
+            hd_server_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def open_scan(self, geometry, params=None, n_chunks: int = 1) -> int:
+        return hd_server_open_scan(self.handle, geometry, params, n_chunks)
+
+    def submit(self, scan_id: int, arrays):
+        hd_server_submit_chunk(self.handle, scan_id, *arrays)
+
+    def wait(self, scan_id: int, timeout_ms: int) -> int:
+        return hd_server_wait(self.handle, scan_id, timeout_ms)
+
+    def poll(self, scan_id: int):
+        return hd_server_poll(self.handle, scan_id)
+
+    def scan(self, scan_id: int, geometry) -> ScanView:
+        return ScanView(hd_server_scan(self.handle, scan_id), geometry)
+
+    def info(self, scan_id: int) -> dict:
+        return hd_server_get_info(self.handle, scan_id)
+
+    def stats(self) -> dict:
+        return hd_server_get_stats(self.handle)
+
+    def close_scan(self, scan_id: int):
+        hd_server_close_scan(self.handle, scan_id)
 
 
 class Batch:
