@@ -199,6 +199,20 @@ def run_batched(args):
         total += len(h)
         dev.append([torch.from_numpy(a).cuda() for a in h.arrays()])
     scans = [hulld.Scan(sp.geometry) for sp in specs]
+    # launch parameters per volume class, from the autotuner (tuned on the
+    # class's largest scan, cached per grid and GPU)
+    from paper_1402_1720_gb300 import autotune
+    tuning = {}
+    if not args.no_tune:
+        for cls in sorted({(sp.geometry.nx, sp.geometry.ny, sp.geometry.nz) for sp in specs}):
+            k = max((i for i, sp in enumerate(specs)
+                     if (sp.geometry.nx, sp.geometry.ny, sp.geometry.nz) == cls),
+                    key=lambda i: specs[i].n_histories)
+            setting = autotune.tuned_setting(specs[k].geometry, dev[k], repeats=2)
+            tuning["x".join(map(str, cls))] = setting
+        for s, sp in zip(scans, specs):
+            autotune.apply(s, tuning["x".join(map(str, (sp.geometry.nx, sp.geometry.ny,
+                                                        sp.geometry.nz)))])
     stream = torch.cuda.Stream()
     batch = hulld.Batch(len(scans))
     flags = hulld.HD_BATCH_RESET | hulld.HD_BATCH_FINALIZE
@@ -228,14 +242,17 @@ def run_batched(args):
             torch.cuda.synchronize()
         return e0.elapsed_time(e1) / k
 
+    for _ in range(args.warmup):
+        batched_step()
+    torch.cuda.synchronize()
+    st0 = batch.stats()
     sampler = ClockSampler(local)
     sampler.start()
-    ms_b = timed(batched_step, args.steps, args.warmup)
+    ms_b = timed(batched_step, args.steps, 0)
     clocks = sampler.stop()
-    st0 = batch.stats()
-    ms_s = timed(sequential_step, args.steps, args.warmup)
+    launches = (batch.stats()["kernel_launches"] - st0["kernel_launches"]) // max(1, args.steps)
     steps_total = sum(s.stats()["steps_miss"] + s.stats()["steps_hit"] for s in scans)
-    launches = batch.stats()["kernel_launches"] - st0["kernel_launches"]
+    ms_s = timed(sequential_step, args.steps, args.warmup)
     line = {"metric": "proton histories/s (48 batched scans, SC+MSC+SM)",
             "value": total / (ms_b * 1e-3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_b, "higher_is_better": True,
@@ -243,16 +260,143 @@ def run_batched(args):
             "config": {"workload": "48 scans, grids {64x64x16,128x128x32,256x256x64} of "
                                    "1x1x2.5 mm, log-uniform 2e5-2e7 histories each "
                                    f"(x{args.batch_fraction:g}), 90 angles",
-                       "total_histories": total,
+                       "total_histories": total, "tuning": tuning,
                        "grids": [f"{sp.geometry.nx}x{sp.geometry.ny}x{sp.geometry.nz}" for sp in specs]},
             "voxel_steps_per_s": steps_total / (ms_b * 1e-3),
             "sequential_48": {"value": total / (ms_s * 1e-3), "unit": UNIT, "ms_per_step": ms_s},
             "batched_over_sequential": ms_s / ms_b,
-            "graph": batch.stats(), "gpu_launches": launches, "clocks": clocks}
+            "graph": batch.stats(), "gpu_launches_per_step": launches,
+            "gpu_launches": launches * args.steps, "clocks": clocks}
     print(json.dumps(line), flush=True)
     batch.close()
     for s in scans:
         s.close()
+
+
+def run_serving(args):
+    """Poisson arrivals of scans from the 48-scan distribution, each streamed
+    as per-angle chunks of 1e4-1e5 histories from pinned host memory, served
+    by the continuous-batching server.  First the saturated throughput X is
+    measured (all scans at once); then scans arrive at rate
+    0.7 X / (mean histories per scan).  time-to-hull = hull ready - last chunk
+    submitted (and - first chunk)."""
+    import queue
+    import torch
+    from paper_1402_1720_gb300 import build as hbuild
+    from paper_1402_1720_gb300 import hulld, synth
+    _, _, local = _dist()
+    torch.cuda.set_device(local)
+    hbuild.build()
+    hulld.load()
+    rng = np.random.default_rng(20140207)
+    specs = synth.batch_scan_specs(args.serve_scans, fraction=args.batch_fraction)
+    scans = []  # (spec, [chunk views of pinned tensors])
+    total = 0
+    for sp in specs:
+        h = synth.scan_histories(sp)
+        pinned = [torch.from_numpy(a).pin_memory() for a in h.arrays()]
+        bounds = []
+        angles = h.angle_deg
+        starts = np.flatnonzero(np.r_[True, angles[1:] != angles[:-1]])
+        ends = np.r_[starts[1:], len(h)]
+        for a0, a1 in zip(starts, ends):
+            s0 = a0
+            while s0 < a1:
+                e0 = min(a1, s0 + int(rng.integers(10_000, 100_001)))
+                bounds.append((s0, e0))
+                s0 = e0
+        scans.append((sp, [[p[a:b] for p in pinned] for a, b in bounds]))
+        total += len(h)
+    cfg = hulld.hd_server_config_default()
+    cfg.max_chunk = 100_000
+
+    def serve(arrivals):
+        """Run one experiment; arrivals[k] = start time (s) of scan k."""
+        srv = hulld.Server(cfg)
+        ids = [None] * len(scans)
+        t0 = time.perf_counter()
+
+        def client(me):
+            # round-robin over this thread's arrived scans, one chunk each
+            active = []  # [k, next chunk]
+            done = False
+            while not done or active:
+                try:
+                    while True:
+                        k = work[me].get_nowait()
+                        if k is None:
+                            done = True
+                            break
+                        sp, chunks = scans[k]
+                        ids[k] = srv.open_scan(sp.geometry, None, len(chunks))
+                        active.append([k, 0])
+                except queue.Empty:
+                    pass
+                if not active:
+                    if not done:
+                        time.sleep(0.0002)
+                    continue
+                for item in list(active):
+                    k, j = item
+                    srv.submit(ids[k], scans[k][1][j])
+                    item[1] += 1
+                    if item[1] == len(scans[k][1]):
+                        active.remove(item)
+
+        nthreads = args.serve_clients
+        work = [queue.Queue() for _ in range(nthreads)]
+        threads = [threading.Thread(target=client, args=(i,)) for i in range(nthreads)]
+        for t in threads:
+            t.start()
+        for k in np.argsort(arrivals):
+            delay = arrivals[k] - (time.perf_counter() - t0)
+            if delay > 0:
+                time.sleep(delay)
+            work[int(k) % nthreads].put(int(k))
+        for q in work:
+            q.put(None)
+        for t in threads:
+            t.join()
+        infos = []
+        for sid in ids:
+            assert srv.wait(sid, 600_000) == hulld.HD_OK
+            infos.append(srv.info(sid))
+            srv.close_scan(sid)
+        st = srv.stats()
+        srv.close()
+        return infos, st
+
+    # saturated throughput: every scan at time zero
+    infos, st_sat = serve(np.zeros(len(scans)))
+    t_start = min(i["t_open"] for i in infos)
+    makespan = max(i["t_ready"] for i in infos) - t_start
+    X = total / makespan
+    mean_h = total / len(scans)
+    lam = args.serve_load * X / mean_h
+    arrivals = np.cumsum(rng.exponential(1.0 / lam, len(scans)))
+    arrivals -= arrivals[0]
+    infos, st = serve(arrivals)
+    ttl = np.array([i["t_ready"] - i["t_last_chunk"] for i in infos])
+    ttf = np.array([i["t_ready"] - i["t_first_chunk"] for i in infos])
+    span = max(i["t_ready"] for i in infos) - min(i["t_open"] for i in infos)
+    line = {"metric": "served time-to-hull p50 (hull ready - last chunk), 48-scan mix",
+            "value": float(np.percentile(ttl, 50)) * 1e3, "unit": "ms", "n_gpus": 1,
+            "steps": 1, "warmup": 1, "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+            "config": {"workload": f"{len(scans)} scans from the 48-scan distribution, Poisson "
+                                   f"arrivals at {args.serve_load:g} x saturated throughput, "
+                                   "per-angle chunks of 1e4-1e5 histories from pinned host memory",
+                       "total_histories": total, "chunks": int(st["chunks_submitted"]),
+                       "client_threads": args.serve_clients},
+            "time_to_hull_ms": {"p50": float(np.percentile(ttl, 50)) * 1e3,
+                                "p99": float(np.percentile(ttl, 99)) * 1e3,
+                                "max": float(ttl.max()) * 1e3},
+            "time_from_first_chunk_ms": {"p50": float(np.percentile(ttf, 50)) * 1e3,
+                                         "p99": float(np.percentile(ttf, 99)) * 1e3},
+            "served_histories_per_s": total / span,
+            "saturated_histories_per_s": X, "arrival_rate_scans_per_s": lam,
+            "server": st, "server_saturated": st_sat}
+    print(json.dumps(line), flush=True)
 
 
 def main():
@@ -266,12 +410,20 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-per-method", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
-    ap.add_argument("--workload", default="head-200", choices=["head-200", "batched-48"])
+    ap.add_argument("--workload", default="head-200",
+                    choices=["head-200", "batched-48", "serving"])
     ap.add_argument("--batch-fraction", type=float, default=1.0)
+    ap.add_argument("--no-tune", action="store_true")
+    ap.add_argument("--serve-scans", type=int, default=48)
+    ap.add_argument("--serve-load", type=float, default=0.7)
+    ap.add_argument("--serve-clients", type=int, default=8)
     args = ap.parse_args()
 
     if args.workload == "batched-48":
         run_batched(args)
+        return
+    if args.workload == "serving":
+        run_serving(args)
         return
 
     if args.impl == "reference":

@@ -217,6 +217,24 @@ HD_API hd_status hd_scan_get_hull_indices(hd_scan *scan, int32_t method, int32_t
                                    int64_t capacity, int64_t *count, int32_t dst_on_device,
                                    void *stream);
 
+/* Launch parameters of the traversal, chosen per volume class by the
+ * autotuner (paper_1402_1720_gb300/autotune.py) or left at their defaults:
+ *   threads     threads per block of the traversal: 256, 512 or 768 (512)
+ *   refill      idle lanes of a warp that trigger taking new walks, 1..32 (8)
+ *   job_size    (record, tile) pairs per job, 256..32767 (16384)
+ *   slab_depth  z-slices per shared-memory tile when whole x-y planes fit,
+ *               0 = as many as fit (0)
+ * A deployment aid: the paper has no counterpart. */
+typedef struct {
+    int32_t threads, refill, job_size, slab_depth;
+} hd_tuning;
+
+/* Set the scan's traversal parameters.  Only while the scan holds no
+ * histories (after create or reset): HD_ERR_STATE otherwise; HD_ERR_ARG for
+ * values outside the ranges above. */
+HD_API hd_status hd_scan_set_tuning(hd_scan *scan, const hd_tuning *tuning);
+HD_API hd_status hd_scan_get_tuning(hd_scan *scan, hd_tuning *out);
+
 /* Start (enable = 1) or stop (0) recording CUDA events around the scan's
  * kernels; starting also clears the accumulated times.  A library aid for
  * measurement: no counterpart in the paper. */
@@ -306,6 +324,8 @@ typedef struct {
     int64_t max_chunk;       /* largest chunk a client submits (histories) */
     int32_t max_batch;       /* chunks of different scans per launch, 1..64 */
     int32_t max_in_flight;   /* launches queued on the GPU at once, 1..8 */
+    int32_t min_batch;       /* while a launch runs, wait for this many scans with a
+                                pending chunk before queueing the next one (>= 1) */
 } hd_server_config;
 
 typedef struct {
@@ -319,9 +339,12 @@ typedef struct {
     int64_t scans_opened, scans_admitted, scans_done;
     int64_t chunks_submitted, chunks_launched, launches;
     int64_t bytes_in_use; /* footprint of the admitted scans */
+    double issue_seconds; /* host time the worker spent issuing launches */
+    double submit_seconds; /* host time spent inside hd_server_submit_chunk (all threads) */
 } hd_server_stats;
 
-/* 64 GiB budget, chunks up to 100000 histories, 64 scans per launch, 2 in flight. */
+/* 64 GiB budget, chunks up to 100000 histories, 64 scans per launch, 2 in
+ * flight, min_batch 8. */
 HD_API hd_status hd_server_config_default(hd_server_config *out);
 
 /* Start a server (and its worker thread) on the current device. */

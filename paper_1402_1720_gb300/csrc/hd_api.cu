@@ -91,6 +91,7 @@ struct hd_scan {
     hd::Ctrl *ctrl = nullptr;
     // scratch: traversal records, (record, tile) pairs, jobs, host staging
     hd::TilePlan tp{};
+    hd_tuning tuning{512, 8, 16384, 0};
     int trace_grid = 0;
     int32_t *rec_buf = nullptr;   // 7 int32 arrays of rec_cap (6 coordinates + status)
     int64_t rec_cap = 0;
@@ -227,7 +228,8 @@ hd_status ensure_records(hd_scan *s, int64_t n, cudaStream_t st)
     bool ok = cudaMalloc(&s->rec_buf, sizeof(int32_t) * 7 * static_cast<size_t>(n)) == cudaSuccess;
     if (ok && s->tp.ntiles > 0) {
         const int64_t pair_cap = pairs_per_record(s->tp) * n;
-        const int64_t job_cap = pair_cap / s->tp.job_size + 2 * s->tp.ntiles + 1;
+        const int64_t min_job = s->tp.job_size < hd::kMinJob ? s->tp.job_size : hd::kMinJob;
+        const int64_t job_cap = pair_cap / min_job + 2 * s->tp.ntiles + 1;
         ok = cudaMalloc(&s->pair_buf, sizeof(uint32_t) * 16 * static_cast<size_t>(pair_cap)) ==
                  cudaSuccess &&
              cudaMalloc(&s->jobs, sizeof(hd::TileJob) * static_cast<size_t>(job_cap)) == cudaSuccess;
@@ -296,6 +298,7 @@ void make_tile_plan(hd_scan *s)
         tp.tx = nx;
         tp.ty = ny;
         tp.tz = static_cast<int>(budget / plane);
+        if (s->tuning.slab_depth > 0 && s->tuning.slab_depth < tp.tz) tp.tz = s->tuning.slab_depth;
         if (tp.tz > nz) tp.tz = nz;
         const int ntz = (nz + tp.tz - 1) / tp.tz;
         tp.tz = (nz + ntz - 1) / ntz;
@@ -312,8 +315,9 @@ void make_tile_plan(hd_scan *s)
     tp.ntiles = tp.ntx * tp.nty * tp.ntz;
     if (tp.ntiles > hd::kMaxTiles) tp.ntiles = 0;
     tp.max_tiles = 8;
-    tp.job_size = 16384;  // <= 32767: int16 differences in the tiled traversal
-    tp.refill = 8;
+    tp.job_size = s->tuning.job_size;  // <= 32767: int16 differences in the tiled traversal
+    tp.refill = s->tuning.refill;
+    tp.threads = s->tuning.threads;
     // two int16 difference arrays per tile (x runs and y runs)
     tp.tile_words = 2 * ((tp.tx * tp.ty * tp.tz + 1) / 2);
     auto magic = [](int t) {
@@ -368,7 +372,8 @@ hd_status stage_prepare(hd_scan *s, const hd::Inputs &in, int64_t n, cudaStream_
                               s->tile_count, s->sm_count, st));
     s->launches += 1;
     if (tp.ntiles > 0) {
-        HD_CUDA(hd::launch_plan(tp, s->tile_count, s->tile_cursor, s->jobs, s->ctrl, st));
+        HD_CUDA(hd::launch_plan(tp, s->tile_count, s->tile_cursor, s->jobs, s->ctrl, s->sm_count,
+                                st));
         HD_CUDA(hd::launch_scatter(tp, rec, s->ctrl, s->tile_cursor, pairs_of(s), n, st));
         s->launches += 2;
     }
@@ -432,7 +437,7 @@ hd_status run_chunk(hd_scan *s, const hd::Inputs &in, int64_t n, cudaStream_t st
     cudaEvent_t e1 = prof_begin(s, st);
     if (s->tp.ntiles > 0 && s->trace_grid > 0) {
         HD_CUDA(hd::launch_trace_tiles(s->desc_dev, 1, &s->ctrl->job_next, s->tp.tile_words,
-                                       s->trace_grid, st));
+                                       s->tp.threads, s->trace_grid, st));
         s->launches += 1;
         if (s->profiling) s->trace_launches += 1;
     }
@@ -534,7 +539,7 @@ hd_status hd_scan_create(const hd_geometry *geom, const hd_params *params, hd_sc
     if (s->tp.ntiles > 0) {
         alloc(reinterpret_cast<void **>(&s->tile_count), sizeof(uint32_t) * 2 * s->tp.ntiles);
         alloc(reinterpret_cast<void **>(&s->tile_cursor), sizeof(uint32_t) * 2 * s->tp.ntiles);
-        const int per_sm = hd::trace_tiles_occupancy(s->tp.tile_words);
+        const int per_sm = hd::trace_tiles_occupancy(s->tp.tile_words, s->tp.threads);
         s->trace_grid = per_sm > 0 ? per_sm * s->sm_count : 0;
     }
     alloc(reinterpret_cast<void **>(&s->ctrl), sizeof(hd::Ctrl));
@@ -772,6 +777,49 @@ hd_status hd_scan_get_hull_indices(hd_scan *scan, int32_t method, int32_t *dst,
     return HD_OK;
 }
 
+hd_status hd_scan_set_tuning(hd_scan *scan, const hd_tuning *t)
+{
+    if (!scan || !t) return HD_ERR_ARG;
+    if (t->threads != 256 && t->threads != 512 && t->threads != 768) return HD_ERR_ARG;
+    if (t->refill < 1 || t->refill > 32 || t->job_size < 256 || t->job_size > 32767 ||
+        t->slab_depth < 0)
+        return HD_ERR_ARG;
+    if (scan->n_total != 0) return HD_ERR_STATE;
+    DeviceGuard g(scan->device);
+    if (!g.ok) return HD_ERR_CUDA;
+    HD_CUDA(cudaDeviceSynchronize());
+    // drop everything sized by the old plan; it regrows on the next add
+    void *old[] = {scan->tile_count, scan->tile_cursor, scan->rec_buf, scan->pair_buf, scan->jobs};
+    for (void *p : old)
+        if (p) cudaFree(p);
+    scan->tile_count = scan->tile_cursor = nullptr;
+    scan->rec_buf = nullptr;
+    scan->pair_buf = nullptr;
+    scan->jobs = nullptr;
+    scan->rec_cap = 0;
+    scan->tuning = *t;
+    make_tile_plan(scan);
+    scan->trace_grid = 0;
+    if (scan->tp.ntiles > 0) {
+        if (cudaMalloc(&scan->tile_count, sizeof(uint32_t) * 2 * scan->tp.ntiles) != cudaSuccess ||
+            cudaMalloc(&scan->tile_cursor, sizeof(uint32_t) * 2 * scan->tp.ntiles) != cudaSuccess) {
+            cudaGetLastError();
+            return HD_ERR_NOMEM;
+        }
+        const int per_sm = hd::trace_tiles_occupancy(scan->tp.tile_words, scan->tp.threads);
+        scan->trace_grid = per_sm > 0 ? per_sm * scan->sm_count : 0;
+    }
+    scan->desc_dirty = true;
+    return HD_OK;
+}
+
+hd_status hd_scan_get_tuning(hd_scan *scan, hd_tuning *out)
+{
+    if (!scan || !out) return HD_ERR_ARG;
+    *out = scan->tuning;
+    return HD_OK;
+}
+
 hd_status hd_scan_set_profiling(hd_scan *scan, int32_t enable)
 {
     if (!scan) return HD_ERR_ARG;
@@ -859,6 +907,8 @@ struct hd_batch {
     };
     std::vector<Item> items;
     hd::ScanDesc *descs_dev = nullptr;  // kMaxBatch descriptors
+    hd::ScanDesc *descs_pinned = nullptr;  // host staging of the table (pinned)
+    cudaEvent_t descs_copied = nullptr;     // the last upload from descs_pinned is done
     int *job_counter = nullptr;
     static constexpr int kSide = 8;
     cudaStream_t side[kSide] = {};
@@ -868,6 +918,7 @@ struct hd_batch {
     cudaGraphExec_t exec = nullptr;
     std::vector<uintptr_t> key;  // items and flags the cached graph was made for
     int64_t graph_kernels = 0;
+    int threads = 512;
     hd_batch_stats stats{};
 };
 
@@ -882,6 +933,8 @@ void free_batch(hd_batch *b)
         if (e) cudaEventDestroy(e);
     if (b->fork) cudaEventDestroy(b->fork);
     if (b->descs_dev) cudaFree(b->descs_dev);
+    if (b->descs_pinned) cudaFreeHost(b->descs_pinned);
+    if (b->descs_copied) cudaEventDestroy(b->descs_copied);
     if (b->job_counter) cudaFree(b->job_counter);
     delete b;
 }
@@ -930,7 +983,8 @@ hd_status issue_round(hd_batch *b, const std::vector<hd_batch::Item> &round, int
     if (r != HD_OK) return r;
     if (any_tiled) {
         HD_CUDA(cudaMemsetAsync(b->job_counter, 0, sizeof(int), st));
-        HD_CUDA(hd::launch_trace_tiles(b->descs_dev, n_items, b->job_counter, max_words, grid, st));
+        HD_CUDA(hd::launch_trace_tiles(b->descs_dev, n_items, b->job_counter, max_words,
+                                       b->threads, grid, st));
         *kernels += 1;
     }
     r = fork();
@@ -971,6 +1025,9 @@ hd_status hd_batch_create(int32_t max_items, hd_batch **out)
     }
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaMalloc(&b->descs_dev, sizeof(hd::ScanDesc) * hd::kMaxBatch);
+    if (e == cudaSuccess)
+        e = cudaMallocHost(&b->descs_pinned, sizeof(hd::ScanDesc) * hd::kMaxBatch);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->descs_copied, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaMalloc(&b->job_counter, sizeof(int));
     if (e != cudaSuccess) {
         note_cuda(e, "hd_batch_create");
@@ -1086,6 +1143,7 @@ hd_status hd_batch_run(hd_batch *batch, int32_t flags, void *stream)
         key.push_back(static_cast<uintptr_t>(it.n));
         key.push_back(reinterpret_cast<uintptr_t>(it.scan->desc_dev));
         key.push_back(reinterpret_cast<uintptr_t>(it.scan->pair_buf));
+        key.push_back(static_cast<uintptr_t>(it.scan->tp.threads));
     }
     // the legacy default stream cannot be captured: run directly there
     const bool graphable = batch->use_graph && rounds.size() == 1 && st != nullptr;
@@ -1093,7 +1151,9 @@ hd_status hd_batch_run(hd_batch *batch, int32_t flags, void *stream)
     for (const auto &it : items)
         if (it.scan->tp.ntiles > 0 && it.scan->tp.tile_words > max_words)
             max_words = it.scan->tp.tile_words;
-    const int per_sm = hd::trace_tiles_occupancy(max_words);
+    // one launch serves every scan: the first scan's block size
+    batch->threads = items.front().scan->tp.threads;
+    const int per_sm = hd::trace_tiles_occupancy(max_words, batch->threads);
     const int grid = (per_sm > 0 ? per_sm : 1) * batch->sm_count;
     batch->stats.runs += 1;
     if (graphable && batch->exec && key == batch->key) {
@@ -1139,12 +1199,15 @@ hd_status hd_batch_run(hd_batch *batch, int32_t flags, void *stream)
             batch->stats.graph_captures += 1;
         } else {
             for (size_t k = 0; k < rounds.size(); ++k) {
-                std::vector<hd::ScanDesc> descs;
-                for (const auto &it : rounds[k]) descs.push_back(it.scan->desc_host);
-                HD_CUDA(cudaMemcpyAsync(batch->descs_dev, descs.data(),
-                                        sizeof(hd::ScanDesc) * descs.size(),
+                // stream-ordered upload of the table: the pinned staging may be
+                // refilled once the previous upload from it has run
+                HD_CUDA(cudaEventSynchronize(batch->descs_copied));
+                for (size_t i = 0; i < rounds[k].size(); ++i)
+                    batch->descs_pinned[i] = rounds[k][i].scan->desc_host;
+                HD_CUDA(cudaMemcpyAsync(batch->descs_dev, batch->descs_pinned,
+                                        sizeof(hd::ScanDesc) * rounds[k].size(),
                                         cudaMemcpyHostToDevice, st));
-                HD_CUDA(cudaStreamSynchronize(st));
+                HD_CUDA(cudaEventRecord(batch->descs_copied, st));
                 hd_status r = issue_round(batch, rounds[k], flags, grid, st, &kernels);
                 if (r != HD_OK) return r;
             }

@@ -63,6 +63,7 @@ struct TilePlan {
     long long pair_cap;
     int tile_words;     // 32-bit words of shared memory per block
     int refill;         // idle lanes that trigger a warp refill
+    int threads;        // threads per block of the traversal (256, 512, 768)
     unsigned mtx, mty, mtz;  // floor(2^32 / t) + 1 (0 when t = 1): division by a tile size
 };
 
@@ -92,6 +93,7 @@ struct ScanDesc {
 };
 
 constexpr int kMaxBatch = 64;  // scans per batched traversal launch
+constexpr int kMinJob = 2048;  // smallest job the plan makes (pairs), unless the tuning is lower
 
 struct Inputs {
     const float *angle, *u_in, *v_in, *u_out, *v_out, *wepl;
@@ -104,16 +106,16 @@ cudaError_t launch_ingest(const Inputs &in, int64_t n, const GeomQ &g, const Cor
                           cudaStream_t s);
 
 cudaError_t launch_plan(const TilePlan &tp, const uint32_t *tile_count, uint32_t *tile_cursor,
-                        TileJob *jobs, Ctrl *ctrl, cudaStream_t s);
+                        TileJob *jobs, Ctrl *ctrl, int sm_count, cudaStream_t s);
 
 cudaError_t launch_scatter(const TilePlan &tp, const Records &rec, const Ctrl *ctrl,
                            uint32_t *tile_cursor, const Pairs &pairs, int64_t n, cudaStream_t s);
 
 // Persistent traversal over the jobs of nscans scans (descs on the device),
 // handed out through *job_counter (zero before the launch).  smem_words is
-// the largest tile of the scans.
+// the largest tile of the scans; threads is 256, 512 or 768.
 cudaError_t launch_trace_tiles(const ScanDesc *descs, int nscans, int *job_counter,
-                               int smem_words, int grid, cudaStream_t s);
+                               int smem_words, int threads, int grid, cudaStream_t s);
 
 // Global-memory traversal of the records whose status is 2 (or of every
 // record when all_records is set).
@@ -125,8 +127,8 @@ cudaError_t launch_classify(const float *wepl, int64_t n, float tau_l, float tau
                             uint8_t *cls, cudaStream_t s);
 
 // Blocks per SM the tiled traversal can keep resident with this much shared
-// memory per block.
-int trace_tiles_occupancy(int smem_words);
+// memory per block and this many threads (0 when the launch is impossible).
+int trace_tiles_occupancy(int smem_words, int threads);
 
 struct DecideArgs {
     int32_t nx, ny, nz;

@@ -173,6 +173,24 @@ void worker_main(hd_server *sv)
                 slot = &t;
                 break;
             }
+        bool any_busy = false;
+        for (auto &t : sv->ticks) any_busy = any_busy || t.busy;
+        // while a launch runs, let chunks of more scans gather first (a
+        // scan's last chunk never waits for company)
+        if (slot && any_busy) {
+            int ready = 0;
+            bool last_waiting = false;
+            for (const int64_t id : sv->admitted_order) {
+                const SScan &s = sv->scans[id];
+                if (s.state != 1 || s.pending.empty()) continue;
+                ++ready;
+                if (s.submitted == s.n_chunks && s.issued + static_cast<int32_t>(s.pending.size()) ==
+                                                     s.n_chunks &&
+                    s.pending.size() == 1)
+                    last_waiting = true;
+            }
+            if (ready < sv->cfg.min_batch && !last_waiting) slot = nullptr;
+        }
         // gather at most one chunk per admitted scan, round-robin
         std::vector<std::pair<int64_t, Chunk>> take;
         std::vector<bool> finishing;
@@ -191,8 +209,6 @@ void worker_main(hd_server *sv)
             }
             if (na) sv->rr = (sv->rr + 1) % na;
         }
-        bool any_busy = false;
-        for (auto &t : sv->ticks) any_busy = any_busy || t.busy;
         if (take.empty()) {
             // nothing to launch: wait for work, or poll running launches
             if (any_busy) sv->cv_work.wait_for(lock, std::chrono::microseconds(200));
@@ -200,6 +216,7 @@ void worker_main(hd_server *sv)
             continue;
         }
         // issue the launch outside the lock
+        const auto t_issue = std::chrono::steady_clock::now();
         std::vector<hd_scan *> handles;
         for (auto &tk : take) handles.push_back(sv->scans[tk.first].scan);
         lock.unlock();
@@ -232,6 +249,8 @@ void worker_main(hd_server *sv)
         }
         sv->stats.launches += 1;
         sv->stats.chunks_launched += static_cast<int64_t>(take.size());
+        sv->stats.issue_seconds +=
+            std::chrono::duration<double>(std::chrono::steady_clock::now() - t_issue).count();
     }
 }
 
@@ -246,6 +265,7 @@ hd_status hd_server_config_default(hd_server_config *out)
     out->max_chunk = 100000;
     out->max_batch = 64;
     out->max_in_flight = 2;
+    out->min_batch = 8;
     return HD_OK;
 }
 
@@ -254,7 +274,8 @@ hd_status hd_server_create(const hd_server_config *cfg, hd_server **out)
     if (!cfg || !out) return HD_ERR_ARG;
     *out = nullptr;
     if (cfg->max_chunk < 1 || cfg->max_batch < 1 || cfg->max_batch > hd::kMaxBatch ||
-        cfg->max_in_flight < 1 || cfg->max_in_flight > 8 || cfg->hbm_budget_bytes == 0)
+        cfg->max_in_flight < 1 || cfg->max_in_flight > 8 || cfg->hbm_budget_bytes == 0 ||
+        cfg->min_batch < 1)
         return HD_ERR_ARG;
     hd_server *sv = new (std::nothrow) hd_server();
     if (!sv) return HD_ERR_NOMEM;
@@ -339,6 +360,7 @@ hd_status hd_server_submit_chunk(hd_server *sv, int64_t scan_id, const float *an
 {
     if (!sv || n < 1 || n > sv->cfg.max_chunk) return HD_ERR_ARG;
     if (!angle_deg || !u_in || !v_in || !u_out || !v_out || !wepl) return HD_ERR_ARG;
+    const auto t_submit = std::chrono::steady_clock::now();
     {
         std::lock_guard<std::mutex> lock(sv->mu);
         auto it = sv->scans.find(scan_id);
@@ -352,20 +374,21 @@ hd_status hd_server_submit_chunk(hd_server *sv, int64_t scan_id, const float *an
     Chunk c;
     c.n = n;
     const float *src[6] = {angle_deg, u_in, v_in, u_out, v_out, wepl};
-    cudaError_t e = cudaMallocAsync(reinterpret_cast<void **>(&c.dev), sizeof(float) * 6 * n,
-                                    sv->upload);
+    // each client thread uploads on its own per-thread stream, so uploads
+    // from several threads proceed side by side
+    const cudaStream_t up = cudaStreamPerThread;
+    cudaError_t e = cudaMallocAsync(reinterpret_cast<void **>(&c.dev), sizeof(float) * 6 * n, up);
     for (int a = 0; e == cudaSuccess && a < 6; ++a)
         e = cudaMemcpyAsync(c.dev + a * n, src[a], sizeof(float) * n,
-                            on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
-                            sv->upload);
+                            on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, up);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c.ready, cudaEventDisableTiming);
-    if (e == cudaSuccess) e = cudaEventRecord(c.ready, sv->upload);
+    if (e == cudaSuccess) e = cudaEventRecord(c.ready, up);
     // the caller may reuse its buffers as soon as this call returns
-    if (e == cudaSuccess) e = cudaStreamSynchronize(sv->upload);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(up);
     if (prev >= 0 && prev != sv->device) cudaSetDevice(prev);
     if (e != cudaSuccess) {
         cudaGetLastError();
-        if (c.dev) cudaFreeAsync(c.dev, sv->upload);
+        if (c.dev) cudaFreeAsync(c.dev, up);
         if (c.ready) cudaEventDestroy(c.ready);
         return HD_ERR_CUDA;
     }
@@ -383,6 +406,8 @@ hd_status hd_server_submit_chunk(hd_server *sv, int64_t scan_id, const float *an
     s.histories += n;
     s.pending.push_back(c);
     sv->stats.chunks_submitted += 1;
+    sv->stats.submit_seconds +=
+        std::chrono::duration<double>(std::chrono::steady_clock::now() - t_submit).count();
     sv->cv_work.notify_all();
     return HD_OK;
 }

@@ -52,33 +52,45 @@ __device__ __forceinline__ unsigned block_excl_scan(unsigned v, unsigned *s_warp
 
 
 // One block: tile offsets (exclusive scan of the counts), cursors for the
-// scatter, and the job table (chunks of job_size pairs of one tile).
+// scatter, and the job table (chunks of one tile's pairs).  The job size
+// adapts to the amount of work: at most tp.job_size pairs, and small enough
+// that there are about two jobs per SM (not below kMinJob, so a job's flush
+// stays small against its walks).
 __global__ void __launch_bounds__(1024) plan_kernel(TilePlan tp, const uint32_t *tile_count,
                                                     uint32_t *tile_cursor, TileJob *jobs,
-                                                    Ctrl *ctrl)
+                                                    Ctrl *ctrl, int sm_count)
 {
     __shared__ unsigned s_warp[33];
+    __shared__ unsigned s_js;
     const int nt = 2 * tp.ntiles;
     const int per = (nt + blockDim.x - 1) / blockDim.x;
     const int t0 = threadIdx.x * per;
-    unsigned my_pairs = 0, my_jobs = 0;
-    for (int t = t0; t < t0 + per && t < nt; ++t) {
-        const unsigned c = tile_count[t];
-        my_pairs += c;
-        my_jobs += (c + tp.job_size - 1) / tp.job_size;
-    }
-    unsigned tot_pairs, tot_jobs;
+    unsigned my_pairs = 0;
+    for (int t = t0; t < t0 + per && t < nt; ++t) my_pairs += tile_count[t];
+    unsigned tot_pairs;
     unsigned off = block_excl_scan(my_pairs, s_warp, tot_pairs);
+    if (threadIdx.x == 0) {
+        const unsigned want = (tot_pairs + 2u * sm_count - 1u) / (2u * sm_count);
+        unsigned js = want < static_cast<unsigned>(tp.job_size) ? want : tp.job_size;
+        if (js < static_cast<unsigned>(kMinJob)) js = kMinJob;
+        if (js > static_cast<unsigned>(tp.job_size)) js = tp.job_size;
+        s_js = js;
+    }
+    __syncthreads();
+    const unsigned js = s_js;
+    unsigned my_jobs = 0;
+    for (int t = t0; t < t0 + per && t < nt; ++t) my_jobs += (tile_count[t] + js - 1) / js;
+    unsigned tot_jobs;
     unsigned joff = block_excl_scan(my_jobs, s_warp, tot_jobs);
     for (int t = t0; t < t0 + per && t < nt; ++t) {
         const unsigned c = tile_count[t];
         tile_cursor[t] = off;
-        for (unsigned s = 0; s < c; s += tp.job_size) {
+        for (unsigned s = 0; s < c; s += js) {
             TileJob j;
             j.tile = t % tp.ntiles;
             j.cls = t / tp.ntiles;
             j.start = static_cast<int>(off + s);
-            j.end = static_cast<int>(off + (s + tp.job_size < c ? s + tp.job_size : c));
+            j.end = static_cast<int>(off + (s + js < c ? s + js : c));
             jobs[joff++] = j;
         }
         off += c;
@@ -408,9 +420,10 @@ __global__ void __launch_bounds__(kThreads, 1) trace_tiles_kernel(
 }  // namespace
 
 cudaError_t launch_plan(const TilePlan &tp, const uint32_t *tile_count, uint32_t *tile_cursor,
-                        TileJob *jobs, Ctrl *ctrl, cudaStream_t s)
+                        TileJob *jobs, Ctrl *ctrl, int sm_count, cudaStream_t s)
 {
-    plan_kernel<<<1, 1024, 0, s>>>(tp, tile_count, tile_cursor, jobs, ctrl);
+    plan_kernel<<<1, 1024, 0, s>>>(tp, tile_count, tile_cursor, jobs, ctrl,
+                                   sm_count > 0 ? sm_count : 1);
     return cudaGetLastError();
 }
 
@@ -426,19 +439,19 @@ cudaError_t launch_scatter(const TilePlan &tp, const Records &rec, const Ctrl *c
     return cudaGetLastError();
 }
 
-int trace_tiles_occupancy(int smem_words)
+template <int kThreads>
+int occupancy_of(int smem_words)
 {
     // allow the largest tile once, so launches (also inside graph capture)
     // need no attribute change
-    if (cudaFuncSetAttribute(trace_tiles_kernel<kTraceThreads>,
+    if (cudaFuncSetAttribute(trace_tiles_kernel<kThreads>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, kTileSmemBytes) !=
         cudaSuccess) {
         cudaGetLastError();
         return 0;
     }
     int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, trace_tiles_kernel<kTraceThreads>,
-                                                      kTraceThreads,
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, trace_tiles_kernel<kThreads>, kThreads,
                                                       static_cast<size_t>(smem_words) * 4) !=
         cudaSuccess) {
         cudaGetLastError();
@@ -447,14 +460,34 @@ int trace_tiles_occupancy(int smem_words)
     return nb;
 }
 
+int trace_tiles_occupancy(int smem_words, int threads)
+{
+    switch (threads) {
+    case 256: return occupancy_of<256>(smem_words);
+    case 512: return occupancy_of<512>(smem_words);
+    case 768: return occupancy_of<768>(smem_words);
+    default: return 0;
+    }
+}
+
 cudaError_t launch_trace_tiles(const ScanDesc *descs, int nscans, int *job_counter,
-                               int smem_words, int grid, cudaStream_t s)
+                               int smem_words, int threads, int grid, cudaStream_t s)
 {
     if (nscans < 1 || nscans > kMaxBatch || smem_words * 4 > kTileSmemBytes)
         return cudaErrorInvalidValue;
-    trace_tiles_kernel<kTraceThreads>
-        <<<grid, kTraceThreads, static_cast<size_t>(smem_words) * 4, s>>>(descs, nscans,
-                                                                          job_counter);
+    const size_t smem = static_cast<size_t>(smem_words) * 4;
+    switch (threads) {
+    case 256:
+        trace_tiles_kernel<256><<<grid, 256, smem, s>>>(descs, nscans, job_counter);
+        break;
+    case 512:
+        trace_tiles_kernel<512><<<grid, 512, smem, s>>>(descs, nscans, job_counter);
+        break;
+    case 768:
+        trace_tiles_kernel<768><<<grid, 768, smem, s>>>(descs, nscans, job_counter);
+        break;
+    default: return cudaErrorInvalidValue;
+    }
     return cudaGetLastError();
 }
 

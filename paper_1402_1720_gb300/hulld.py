@@ -67,6 +67,14 @@ class hd_profile(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class hd_tuning(ctypes.Structure):
+    _fields_ = [("threads", ctypes.c_int32), ("refill", ctypes.c_int32),
+                ("job_size", ctypes.c_int32), ("slab_depth", ctypes.c_int32)]
+
+    def as_dict(self):
+        return {k: int(getattr(self, k)) for k, _ in self._fields_}
+
+
 class hd_batch_stats(ctypes.Structure):
     _fields_ = [("runs", ctypes.c_int64), ("graph_captures", ctypes.c_int64),
                 ("graph_replays", ctypes.c_int64), ("kernel_launches", ctypes.c_int64)]
@@ -80,7 +88,8 @@ HD_BATCH_RESET, HD_BATCH_FINALIZE = 1, 2
 
 class hd_server_config(ctypes.Structure):
     _fields_ = [("hbm_budget_bytes", ctypes.c_size_t), ("max_chunk", ctypes.c_int64),
-                ("max_batch", ctypes.c_int32), ("max_in_flight", ctypes.c_int32)]
+                ("max_batch", ctypes.c_int32), ("max_in_flight", ctypes.c_int32),
+                ("min_batch", ctypes.c_int32)]
 
 
 class hd_server_scan_info(ctypes.Structure):
@@ -98,10 +107,11 @@ class hd_server_stats(ctypes.Structure):
     _fields_ = [("scans_opened", ctypes.c_int64), ("scans_admitted", ctypes.c_int64),
                 ("scans_done", ctypes.c_int64), ("chunks_submitted", ctypes.c_int64),
                 ("chunks_launched", ctypes.c_int64), ("launches", ctypes.c_int64),
-                ("bytes_in_use", ctypes.c_int64)]
+                ("bytes_in_use", ctypes.c_int64), ("issue_seconds", ctypes.c_double),
+                ("submit_seconds", ctypes.c_double)]
 
     def as_dict(self):
-        return {k: int(getattr(self, k)) for k, _ in self._fields_}
+        return {k: getattr(self, k) for k, _ in self._fields_}
 
 # exported symbols and their signatures
 _VP, _I32, _I64, _SZ = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_size_t
@@ -125,6 +135,8 @@ _SIGS = {
     "hd_accumulate_noalloc": ([ctypes.POINTER(hd_geometry), ctypes.POINTER(hd_params)] +
                               [_VP] * 6 + [_I64, _VP, _VP, _VP], ctypes.c_int),
     "hd_scan_set_profiling": ([_VP, _I32], ctypes.c_int),
+    "hd_scan_set_tuning": ([_VP, ctypes.POINTER(hd_tuning)], ctypes.c_int),
+    "hd_scan_get_tuning": ([_VP, ctypes.POINTER(hd_tuning)], ctypes.c_int),
     "hd_batch_create": ([_I32, ctypes.POINTER(_VP)], ctypes.c_int),
     "hd_batch_destroy": ([_VP], ctypes.c_int),
     "hd_batch_add": ([_VP, _VP] + [_VP] * 6 + [_I64], ctypes.c_int),
@@ -325,6 +337,16 @@ def hd_scan_get_hull_indices(scan: int, method: int, dst=None, stream=None):
     _check(load().hd_scan_get_hull_indices(scan, method, p, cap, ctypes.byref(count), on,
                                            _stream(stream)), "hd_scan_get_hull_indices")
     return count.value, dst
+
+
+def hd_scan_set_tuning(scan: int, tuning: hd_tuning) -> None:
+    _check(load().hd_scan_set_tuning(scan, ctypes.byref(tuning)), "hd_scan_set_tuning")
+
+
+def hd_scan_get_tuning(scan: int) -> dict:
+    t = hd_tuning()
+    _check(load().hd_scan_get_tuning(scan, ctypes.byref(t)), "hd_scan_get_tuning")
+    return t.as_dict()
 
 
 def hd_scan_set_profiling(scan: int, enable: bool) -> None:

@@ -429,3 +429,50 @@ def test_config3_streamed_sampled(hd, oracle_mod):
     got = _run_gpu(hd, g, sub)
     _assert_same(got, ref, ALL)
     _assert_stats(got, ref)
+
+
+@pytest.mark.parametrize("setting", [
+    {"threads": 256, "refill": 4, "job_size": 4096, "slab_depth": 1},
+    {"threads": 768, "refill": 24, "job_size": 32767, "slab_depth": 2},
+    {"threads": 512, "refill": 1, "job_size": 256, "slab_depth": 0},
+])
+def test_tuning_settings_do_not_change_results(hd, oracle_mod, setting):
+    """Launch parameters change speed only: every setting gives the oracle's
+    results, on a one-tile grid and on slabbed grids."""
+    t = hd.hd_tuning(setting["threads"], setting["refill"], setting["job_size"],
+                     setting["slab_depth"])
+    w = synth.make_config(1, fraction=0.2)
+    cases = [(w.geometry, w.histories)]
+    g2 = synth.Geometry(64, 64, 40, 1.0, 1.0, 0.5, 100.0)
+    cases.append((g2, synth.tiny_random_case(np.random.default_rng(8), 8000, g2, span=1.1)))
+    for g, h in cases:
+        ref = oracle_mod.run(g, h, threads=8)
+        with hd.Scan(g) as s:
+            hd.hd_scan_set_tuning(s.handle, t)
+            assert hd.hd_scan_get_tuning(s.handle) == setting
+            s.add([torch.from_numpy(a).cuda() for a in h.arrays()])
+            s.finalize()
+            torch.cuda.synchronize()
+            assert np.array_equal(s.counts(hd.HD_MSC), ref["N"])
+            assert np.array_equal(s.counts(hd.HD_SM), ref["M"])
+            assert np.array_equal(s.mask(hd.HD_MSC), ref["H2"])
+            assert np.array_equal(s.mask(hd.HD_SM), ref["H3"])
+            # tuning is refused while the scan holds histories
+            with pytest.raises(hd.HDError) as e:
+                hd.hd_scan_set_tuning(s.handle, t)
+            assert e.value.status == hd.HD_ERR_STATE
+
+
+def test_autotuner_picks_a_valid_setting(hd, tmp_path):
+    from paper_1402_1720_gb300 import autotune
+    w = synth.make_config(1, fraction=0.3)
+    dev = [torch.from_numpy(a).cuda() for a in w.histories.arrays()]
+    space = {"slab_depth": [0, 2], "threads": [256, 512], "refill": [8, 16],
+             "job_size": [8192, 16384]}
+    res = autotune.autotune(w.geometry, dev, space=space, repeats=1)
+    s = res["setting"]
+    assert s["threads"] in (256, 512) and s["refill"] in (8, 16)
+    assert res["ms"] == min(ms for _, ms in res["trials"])
+    path = str(tmp_path / "cache.json")
+    got = autotune.tuned_setting(w.geometry, dev, path=path, repeats=1)
+    assert autotune.tuned_setting(w.geometry, None, path=path) == got  # from the cache
