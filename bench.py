@@ -376,6 +376,20 @@ def run_serving(args):
     arrivals = np.cumsum(rng.exponential(1.0 / lam, len(scans)))
     arrivals -= arrivals[0]
     infos, st = serve(arrivals)
+    # one scan at a time through the plain scan calls, the same chunks from
+    # the same pinned host memory: each chunk added as it comes, the hulls
+    # after the scan's last chunk
+    seq_stream = torch.cuda.Stream()
+    torch.cuda.synchronize()
+    t_seq = time.perf_counter()
+    with torch.cuda.stream(seq_stream):
+        for sp, chunks in scans:
+            with hulld.Scan(sp.geometry) as s:
+                for c in chunks:
+                    s.add(c, seq_stream)
+                s.finalize(seq_stream)
+                seq_stream.synchronize()
+    seq_s = time.perf_counter() - t_seq
     ttl = np.array([i["t_ready"] - i["t_last_chunk"] for i in infos])
     ttf = np.array([i["t_ready"] - i["t_first_chunk"] for i in infos])
     span = max(i["t_ready"] for i in infos) - min(i["t_open"] for i in infos)
@@ -395,6 +409,10 @@ def run_serving(args):
                                          "p99": float(np.percentile(ttf, 99)) * 1e3},
             "served_histories_per_s": total / span,
             "saturated_histories_per_s": X, "arrival_rate_scans_per_s": lam,
+            "sequential_streamed": {"histories_per_s": total / seq_s, "seconds": seq_s,
+                                    "what": "one scan at a time, each chunk added from pinned "
+                                            "host memory through the plain scan calls"},
+            "saturated_over_sequential": X / (total / seq_s),
             "server": st, "server_saturated": st_sat}
     print(json.dumps(line), flush=True)
 

@@ -161,6 +161,12 @@ HD_API hd_status hd_scan_destroy(hd_scan *scan);
  * stream-ordered, so the scan can take a new acquisition. */
 HD_API hd_status hd_scan_reset(hd_scan *scan, void *stream);
 
+/* Size the scan's per-chunk scratch (records, tile pairs, job table) for
+ * calls of up to n histories now, so that later calls of that size allocate
+ * nothing and never synchronise the stream to grow it.  Optional: the
+ * scratch otherwise grows on demand.  May synchronise `stream`. */
+HD_API hd_status hd_scan_reserve(hd_scan *scan, int64_t n, void *stream);
+
 /* Add n proton histories (structure of arrays, float32, n entries each):
  * classify each (Eq. 3.1, Eq. 3.7), traverse the voxel set A_i of every
  * missed and hit history (Eq. 3.2) and accumulate N (Eq. 3.4), M (Eq. 3.9)
@@ -306,26 +312,35 @@ HD_API hd_status hd_batch_get_stats(hd_batch *batch, hd_batch_stats *out);
  * Serving: a request loop for streamed scans (continuous batching).
  *
  * Clients open scans and submit per-angle chunks as they are acquired (the
- * online mode of Sec. 4).  A worker thread admits scans first come, first
- * served while their device footprint fits hbm_budget_bytes, and keeps up to
- * max_in_flight batched launches queued on the GPU, each taking one pending
- * chunk from each of up to max_batch admitted scans (one persistent
- * traversal over all of them, as hd_batch_run).  Chunks that arrive while
- * others are running join the next launch.  A scan's hulls are computed in
- * the launch that carries its last chunk; they stay on the device until the
- * client closes the scan, which returns its memory to the budget.  Results
- * equal those of the same chunks added to a lone scan.  Times are seconds
- * since the server was created (-1 when the event has not happened).
+ * online mode of Sec. 4).  A submit copies its chunk into the scan's open
+ * staging segment (device memory for segment_histories histories), so the
+ * chunks of a scan that arrive while the GPU is busy lie side by side.  A
+ * worker thread admits scans first come, first served while their device
+ * footprint fits hbm_budget_bytes, and keeps up to max_in_flight batched
+ * launches queued on the GPU, each taking the oldest filled segment of each
+ * of up to max_batch admitted scans (one persistent traversal over all of
+ * them, as hd_batch_run): every chunk a scan received since its last launch
+ * goes in as one item.  A scan's hulls are computed in the launch that
+ * carries its last chunk; they stay on the device until the client closes
+ * the scan, which returns its memory to the budget.  Results equal those of
+ * the same chunks added to a lone scan.  Staging memory is bounded by
+ * staging_bytes: a submit that finds none free waits for a launch to finish
+ * (at most submit_timeout_ms).  Times are seconds since the server was
+ * created (-1 when the event has not happened).
  * ------------------------------------------------------------------------ */
 typedef struct hd_server hd_server;
 
 typedef struct {
     size_t hbm_budget_bytes; /* device memory the server may give to admitted scans */
     int64_t max_chunk;       /* largest chunk a client submits (histories) */
-    int32_t max_batch;       /* chunks of different scans per launch, 1..64 */
+    int32_t max_batch;       /* scans per launch, 1..64 */
     int32_t max_in_flight;   /* launches queued on the GPU at once, 1..8 */
-    int32_t min_batch;       /* while a launch runs, wait for this many scans with a
-                                pending chunk before queueing the next one (>= 1) */
+    int32_t min_batch;       /* while a launch runs, wait for this many scans with
+                                pending chunks before queueing the next one (>= 1) */
+    int64_t segment_histories; /* histories per staging segment, max_chunk..2^25 */
+    size_t staging_bytes;      /* device memory for staging segments (>= one segment,
+                                  24 bytes per history) */
+    int64_t submit_timeout_ms; /* longest a submit waits for staging space (>= 0) */
 } hd_server_config;
 
 typedef struct {
@@ -341,10 +356,12 @@ typedef struct {
     int64_t bytes_in_use; /* footprint of the admitted scans */
     double issue_seconds; /* host time the worker spent issuing launches */
     double submit_seconds; /* host time spent inside hd_server_submit_chunk (all threads) */
+    int64_t items_launched; /* (scan, segment) items over all launches */
 } hd_server_stats;
 
 /* 64 GiB budget, chunks up to 100000 histories, 64 scans per launch, 2 in
- * flight, min_batch 8. */
+ * flight, min_batch 8, segments of 2^19 histories, 4 GiB of staging, 60 s
+ * submit timeout. */
 HD_API hd_status hd_server_config_default(hd_server_config *out);
 
 /* Start a server (and its worker thread) on the current device. */
@@ -361,7 +378,11 @@ HD_API hd_status hd_server_open_scan(hd_server *server, const hd_geometry *geom,
 
 /* Submit the next chunk of a scan (1 <= n <= max_chunk; host arrays, or
  * device arrays with on_device = 1).  The data is copied before the call
- * returns.  HD_ERR_STATE when the scan already has all its chunks. */
+ * returns.  HD_ERR_STATE when the scan already has all its chunks (or is
+ * finished); HD_ERR_TIMEOUT when no staging space freed up within
+ * submit_timeout_ms (the chunk was not taken: submit it again);
+ * HD_ERR_CUDA when the copy failed (the scan is then failed).  Several
+ * threads may submit at once, to the same scan or to different ones. */
 HD_API hd_status hd_server_submit_chunk(hd_server *server, int64_t scan_id,
                                         const float *angle_deg, const float *u_in,
                                         const float *v_in, const float *u_out,

@@ -374,7 +374,8 @@ hd_status stage_prepare(hd_scan *s, const hd::Inputs &in, int64_t n, cudaStream_
     if (tp.ntiles > 0) {
         HD_CUDA(hd::launch_plan(tp, s->tile_count, s->tile_cursor, s->jobs, s->ctrl, s->sm_count,
                                 st));
-        HD_CUDA(hd::launch_scatter(tp, rec, s->ctrl, s->tile_cursor, pairs_of(s), n, st));
+        HD_CUDA(hd::launch_scatter(tp, rec, s->ctrl, s->tile_cursor, pairs_of(s), n, s->sm_count,
+                                   st));
         s->launches += 2;
     }
     return HD_OK;
@@ -578,6 +579,15 @@ hd_status hd_scan_reset(hd_scan *scan, void *stream)
     scan->n_total = 0;
     scan->finalized = false;
     return HD_OK;
+}
+
+hd_status hd_scan_reserve(hd_scan *scan, int64_t n, void *stream)
+{
+    if (!scan || n < 0) return HD_ERR_ARG;
+    if (n == 0) return HD_OK;
+    DeviceGuard g(scan->device);
+    if (!g.ok) return HD_ERR_CUDA;
+    return ensure_records(scan, n < kChunk ? n : kChunk, static_cast<cudaStream_t>(stream));
 }
 
 hd_status hd_scan_add_histories(hd_scan *scan, const float *angle_deg, const float *u_in,

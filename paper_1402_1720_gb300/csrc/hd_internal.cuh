@@ -109,7 +109,8 @@ cudaError_t launch_plan(const TilePlan &tp, const uint32_t *tile_count, uint32_t
                         TileJob *jobs, Ctrl *ctrl, int sm_count, cudaStream_t s);
 
 cudaError_t launch_scatter(const TilePlan &tp, const Records &rec, const Ctrl *ctrl,
-                           uint32_t *tile_cursor, const Pairs &pairs, int64_t n, cudaStream_t s);
+                           uint32_t *tile_cursor, const Pairs &pairs, int64_t n, int sm_count,
+                           cudaStream_t s);
 
 // Persistent traversal over the jobs of nscans scans (descs on the device),
 // handed out through *job_counter (zero before the launch).  smem_words is

@@ -1,19 +1,26 @@
 // Serving: a request loop for streamed scans with continuous batching.
 //
 // Clients open scans and submit per-angle chunks of histories as they are
-// acquired (the online mode of Sec. 4).  A worker thread admits scans while
-// their device footprint fits a memory budget, and repeatedly gathers one
-// pending chunk from each of up to max_batch admitted scans into a batched
-// launch (one persistent traversal over all of them, see hd_batch).  Several
-// such launches are kept queued on the GPU, so chunks that arrive while
-// others are running join the next launch and the device stays busy.  A
-// scan's hulls are computed right after its last chunk, in the same launch.
-// The server uses only the public scan and batch calls.
+// acquired (the online mode of Sec. 4).  A submit copies its chunk into the
+// scan's open staging segment: a recycled device buffer that holds six
+// structure-of-arrays columns of up to segment_histories histories, so the
+// chunks of one scan that arrive while the GPU is busy sit side by side.  A
+// worker thread admits scans while their device footprint fits a memory
+// budget, and repeatedly takes the oldest filled segment of each of up to
+// max_batch admitted scans into one batched launch (one persistent traversal
+// over all of them, see hd_batch): however many chunks a scan received
+// meanwhile, they go to the GPU as one item.  Several launches are kept
+// queued, so the device stays busy while chunks gather for the next one.  A
+// scan's hulls are computed in the launch that carries its last chunk.
+// Staging memory is bounded: a submit that finds no free segment waits (for
+// at most submit_timeout_ms) until a launch finishes and returns its
+// segments.  The server uses only the public scan and batch calls.
 #include <chrono>
 #include <condition_variable>
 #include <cstring>
 #include <deque>
 #include <map>
+#include <memory>
 #include <mutex>
 #include <new>
 #include <thread>
@@ -28,10 +35,17 @@ double now_since(std::chrono::steady_clock::time_point t0)
     return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
 }
 
-struct Chunk {
-    float *dev = nullptr;  // six arrays of n floats, back to back
-    int64_t n = 0;
-    cudaEvent_t ready = nullptr;  // the upload has finished
+// One staging segment: columns angle, u_in, v_in, u_out, v_out, wepl of cap
+// floats each, back to back.  Submits reserve [reserved, reserved + n) under
+// the server lock and copy outside it; the worker takes a segment only when
+// no copy into it is running (writers == 0), so [0, filled) is complete.
+struct Segment {
+    float *dev = nullptr;
+    int64_t reserved = 0;
+    int64_t filled = 0;
+    int32_t chunks = 0;   // chunks whose copies have finished
+    int32_t writers = 0;  // copies running
+    bool sealed = false;  // takes no more reservations
 };
 
 struct SScan {
@@ -39,24 +53,27 @@ struct SScan {
     hd_geometry geom{};
     hd_params params{};
     int32_t n_chunks = 0;
-    int32_t submitted = 0;
-    int32_t issued = 0;   // chunks handed to a launch
+    int32_t reserved_chunks = 0;  // submits that got space (running or done)
+    int32_t submitted = 0;        // submits whose copies have finished
+    int32_t issued = 0;           // chunks handed to a launch
     int32_t done_chunks = 0;
     int64_t histories = 0;
     size_t footprint = 0;
-    int state = 0;        // 0 waiting, 1 admitted, 2 ready, 3 failed
+    int state = 0;  // 0 waiting, 1 admitted, 2 ready, 3 failed
+    bool admitting = false;  // its device state is being created
     hd_status status = HD_OK;
     hd_scan *scan = nullptr;
-    std::deque<Chunk> pending;
+    std::deque<std::unique_ptr<Segment>> segs;  // oldest first; the back may be open
     double t_open = -1, t_admit = -1, t_first = -1, t_last = -1, t_ready = -1;
 };
 
 struct Tick {
     hd_batch *batch = nullptr;
     cudaEvent_t done = nullptr;
-    std::vector<int64_t> scans;     // scans that had a chunk in this launch
-    std::vector<bool> finishing;    // ... and whether it was their last
-    std::vector<Chunk> chunks;      // buffers to release after the launch
+    std::vector<int64_t> scans;     // scans that had an item in this launch
+    std::vector<int32_t> chunks;    // ... how many chunks it carried
+    std::vector<bool> finishing;    // ... and whether it carried the scan's last
+    std::vector<float *> bufs;      // staging segments to recycle after the launch
     bool busy = false;
 };
 
@@ -67,7 +84,7 @@ struct hd_server {
     int device = 0;
     std::chrono::steady_clock::time_point t0;
     std::mutex mu;
-    std::condition_variable cv_work, cv_done;
+    std::condition_variable cv_work, cv_done, cv_space, cv_keep;
     std::map<int64_t, SScan> scans;
     std::deque<int64_t> waiting;  // admission queue (FIFO)
     std::vector<int64_t> admitted_order;
@@ -75,29 +92,62 @@ struct hd_server {
     int64_t next_id = 1;
     size_t rr = 0;  // round-robin position over admitted scans
     bool stop = false;
-    cudaStream_t stream = nullptr;   // launches
-    cudaStream_t upload = nullptr;   // chunk uploads
+    cudaStream_t stream = nullptr;  // launches
+    std::vector<float *> free_bufs;  // staging segments not in use
+    std::vector<float *> all_bufs;   // every staging segment allocated
+    std::vector<hd_scan *> graveyard;  // closed scans to destroy
     std::vector<Tick> ticks;
-    std::thread worker;
+    std::thread worker;  // launches
+    std::thread keeper;  // creates admitted scans and destroys closed ones
     hd_server_stats stats{};
 };
 
 namespace {
 
+size_t segment_bytes(const hd_server_config &cfg)
+{
+    return sizeof(float) * 6 * static_cast<size_t>(cfg.segment_histories);
+}
+
 size_t footprint_of(const hd_geometry &g, const hd_server_config &cfg)
 {
     const size_t V = static_cast<size_t>(g.nx) * g.ny * g.nz;
-    // counts (2 x uint32), three byte masks, bit views, and the per-chunk
-    // scratch: records (28 B) and up to eight packed pairs (64 B each)
-    return V * 11 + V / 4 + static_cast<size_t>(cfg.max_chunk) * (28 + 8 * 64) + (4u << 20);
+    // counts (2 x uint32), three byte masks, bit views, and the scratch of
+    // one segment-sized item: records (28 B) and up to eight packed pairs
+    // (64 B each) per history
+    return V * 11 + V / 4 + static_cast<size_t>(cfg.segment_histories) * (28 + 8 * 64) +
+           (4u << 20);
 }
 
-void release_chunk(Chunk &c, cudaStream_t st)
+// Called with the lock held: a free staging segment, allocating a new one
+// while the staging budget allows; nullptr when none can be had now.
+float *take_buffer(hd_server *sv, hd_status *err)
 {
-    if (c.dev) cudaFreeAsync(c.dev, st);
-    if (c.ready) cudaEventDestroy(c.ready);
-    c.dev = nullptr;
-    c.ready = nullptr;
+    *err = HD_OK;
+    if (!sv->free_bufs.empty()) {
+        float *b = sv->free_bufs.back();
+        sv->free_bufs.pop_back();
+        return b;
+    }
+    if ((sv->all_bufs.size() + 1) * segment_bytes(sv->cfg) > sv->cfg.staging_bytes) return nullptr;
+    float *b = nullptr;
+    if (cudaMalloc(reinterpret_cast<void **>(&b), segment_bytes(sv->cfg)) != cudaSuccess) {
+        cudaGetLastError();
+        *err = HD_ERR_NOMEM;
+        return nullptr;
+    }
+    sv->all_bufs.push_back(b);
+    return b;
+}
+
+// Called with the lock held: return the segments of a scan that will not
+// run (failed or closed) to the free list.
+void recycle_segments(hd_server *sv, SScan &s)
+{
+    for (auto &g : s.segs)
+        if (g->dev && g->writers == 0) sv->free_bufs.push_back(g->dev);
+    s.segs.clear();
+    sv->cv_space.notify_all();
 }
 
 // Called with the lock held: retire finished launches.
@@ -112,7 +162,7 @@ void retire(hd_server *sv)
             auto it = sv->scans.find(t.scans[i]);
             if (it == sv->scans.end()) continue;
             SScan &s = it->second;
-            s.done_chunks += 1;
+            s.done_chunks += t.chunks[i];
             if (q != cudaSuccess) {
                 s.state = 3;
                 s.status = HD_ERR_CUDA;
@@ -123,29 +173,67 @@ void retire(hd_server *sv)
             }
         }
         if (q != cudaSuccess) cudaGetLastError();
+        for (float *b : t.bufs) sv->free_bufs.push_back(b);
         t.scans.clear();
-        t.finishing.clear();
         t.chunks.clear();
+        t.finishing.clear();
+        t.bufs.clear();
         t.busy = false;
     }
     sv->cv_done.notify_all();
+    sv->cv_space.notify_all();
 }
 
-// Called with the lock held: admit waiting scans, first come first served.
-void admit(hd_server *sv)
+// Admission and clean-up, on their own thread so that allocating or
+// freeing a scan's device memory (which may wait for the GPU) stalls
+// neither the launches nor the submits: scans are admitted first come,
+// first served while their footprint fits the budget.
+void keeper_main(hd_server *sv)
 {
-    while (!sv->waiting.empty()) {
-        auto it = sv->scans.find(sv->waiting.front());
-        if (it == sv->scans.end()) {
-            sv->waiting.pop_front();
+    cudaSetDevice(sv->device);
+    std::unique_lock<std::mutex> lock(sv->mu);
+    while (!sv->stop) {
+        if (!sv->graveyard.empty()) {
+            std::vector<hd_scan *> dead;
+            dead.swap(sv->graveyard);
+            lock.unlock();
+            for (hd_scan *h : dead) hd_scan_destroy(h);
+            lock.lock();
             continue;
         }
-        SScan &s = it->second;
-        if (sv->used + s.footprint > sv->cfg.hbm_budget_bytes) break;
+        int64_t id = -1;
+        while (!sv->waiting.empty()) {
+            auto it = sv->scans.find(sv->waiting.front());
+            if (it == sv->scans.end()) {
+                sv->waiting.pop_front();
+                continue;
+            }
+            SScan &s = it->second;
+            if (sv->used + s.footprint <= sv->cfg.hbm_budget_bytes) {
+                id = s.id;
+                sv->waiting.pop_front();
+                s.admitting = true;
+                sv->used += s.footprint;
+            }
+            break;
+        }
+        if (id < 0) {
+            sv->cv_keep.wait(lock);
+            continue;
+        }
+        const hd_geometry geom = sv->scans[id].geom;
+        const hd_params params = sv->scans[id].params;
+        lock.unlock();
         hd_scan *h = nullptr;
-        const hd_status r = hd_scan_create(&s.geom, &s.params, &h);
-        sv->waiting.pop_front();
+        hd_status r = hd_scan_create(&geom, &params, &h);
+        // scratch for a full segment now, so launches never grow it
+        if (r == HD_OK) r = hd_scan_reserve(h, sv->cfg.segment_histories, cudaStreamPerThread);
+        lock.lock();
+        SScan &s = sv->scans[id];  // not closed while admitting
+        s.admitting = false;
         if (r != HD_OK) {
+            if (h) sv->graveyard.push_back(h);
+            sv->used -= s.footprint;
             s.state = 3;
             s.status = r;
             sv->cv_done.notify_all();
@@ -154,19 +242,27 @@ void admit(hd_server *sv)
         s.scan = h;
         s.state = 1;
         s.t_admit = now_since(sv->t0);
-        sv->used += s.footprint;
-        sv->admitted_order.push_back(s.id);
+        sv->admitted_order.push_back(id);
         sv->stats.scans_admitted += 1;
+        sv->cv_work.notify_all();
     }
+}
+
+// A segment the worker may launch now.
+bool takeable(const SScan &s)
+{
+    if (s.state != 1 || s.segs.empty()) return false;
+    const Segment &g = *s.segs.front();
+    return g.writers == 0 && g.filled > 0;
 }
 
 void worker_main(hd_server *sv)
 {
     cudaSetDevice(sv->device);
     std::unique_lock<std::mutex> lock(sv->mu);
+    const int64_t cap = sv->cfg.segment_histories;
     while (!sv->stop) {
         retire(sv);
-        admit(sv);
         Tick *slot = nullptr;
         for (auto &t : sv->ticks)
             if (!t.busy) {
@@ -175,25 +271,29 @@ void worker_main(hd_server *sv)
             }
         bool any_busy = false;
         for (auto &t : sv->ticks) any_busy = any_busy || t.busy;
-        // while a launch runs, let chunks of more scans gather first (a
-        // scan's last chunk never waits for company)
+        // while a launch runs, let work of more scans gather first (a scan
+        // whose last chunk has landed never waits for company)
         if (slot && any_busy) {
             int ready = 0;
             bool last_waiting = false;
             for (const int64_t id : sv->admitted_order) {
                 const SScan &s = sv->scans[id];
-                if (s.state != 1 || s.pending.empty()) continue;
+                if (!takeable(s)) continue;
                 ++ready;
-                if (s.submitted == s.n_chunks && s.issued + static_cast<int32_t>(s.pending.size()) ==
-                                                     s.n_chunks &&
-                    s.pending.size() == 1)
-                    last_waiting = true;
+                if (s.submitted == s.n_chunks) last_waiting = true;
             }
             if (ready < sv->cfg.min_batch && !last_waiting) slot = nullptr;
         }
-        // gather at most one chunk per admitted scan, round-robin
-        std::vector<std::pair<int64_t, Chunk>> take;
-        std::vector<bool> finishing;
+        // take the oldest filled segment of each admitted scan, round-robin
+        struct Take {
+            int64_t id;
+            hd_scan *handle;
+            float *dev;
+            int64_t n;
+            int32_t chunks;
+            bool finishing;
+        };
+        std::vector<Take> take;
         if (slot) {
             const size_t na = sv->admitted_order.size();
             for (size_t k = 0; k < na && static_cast<int>(take.size()) < sv->cfg.max_batch; ++k) {
@@ -201,11 +301,11 @@ void worker_main(hd_server *sv)
                 auto it = sv->scans.find(id);
                 if (it == sv->scans.end()) continue;
                 SScan &s = it->second;
-                if (s.state != 1 || s.pending.empty()) continue;
-                take.push_back({id, s.pending.front()});
-                s.pending.pop_front();
-                s.issued += 1;
-                finishing.push_back(s.issued == s.n_chunks);
+                if (!takeable(s)) continue;
+                std::unique_ptr<Segment> g = std::move(s.segs.front());
+                s.segs.pop_front();
+                s.issued += g->chunks;
+                take.push_back({id, s.scan, g->dev, g->filled, g->chunks, s.issued == s.n_chunks});
             }
             if (na) sv->rr = (sv->rr + 1) % na;
         }
@@ -217,38 +317,35 @@ void worker_main(hd_server *sv)
         }
         // issue the launch outside the lock
         const auto t_issue = std::chrono::steady_clock::now();
-        std::vector<hd_scan *> handles;
-        for (auto &tk : take) handles.push_back(sv->scans[tk.first].scan);
         lock.unlock();
         hd_status r = HD_OK;
         for (size_t i = 0; i < take.size() && r == HD_OK; ++i) {
-            Chunk &c = take[i].second;
-            if (cudaStreamWaitEvent(sv->stream, c.ready, 0) != cudaSuccess) r = HD_ERR_CUDA;
-            const float *p = c.dev;
-            const int64_t n = c.n;
-            if (r == HD_OK)
-                r = hd_batch_add_item(slot->batch, handles[i], p, p + n, p + 2 * n, p + 3 * n,
-                                      p + 4 * n, p + 5 * n, n,
-                                      finishing[i] ? HD_BATCH_FINALIZE : 0);
+            const float *p = take[i].dev;
+            r = hd_batch_add_item(slot->batch, take[i].handle, p, p + cap, p + 2 * cap,
+                                  p + 3 * cap, p + 4 * cap, p + 5 * cap, take[i].n,
+                                  take[i].finishing ? HD_BATCH_FINALIZE : 0);
         }
         if (r == HD_OK) r = hd_batch_run(slot->batch, 0, sv->stream);
-        for (auto &tk : take) release_chunk(tk.second, sv->stream);
         const cudaError_t e = cudaEventRecord(slot->done, sv->stream);
         lock.lock();
         slot->busy = true;
-        for (size_t i = 0; i < take.size(); ++i) {
-            slot->scans.push_back(take[i].first);
-            slot->finishing.push_back(finishing[i] && r == HD_OK && e == cudaSuccess);
-        }
-        if (r != HD_OK || e != cudaSuccess) {
-            for (auto &tk : take) {
-                SScan &s = sv->scans[tk.first];
+        int64_t chunks = 0;
+        for (const Take &tk : take) {
+            slot->scans.push_back(tk.id);
+            slot->chunks.push_back(tk.chunks);
+            slot->finishing.push_back(tk.finishing && r == HD_OK && e == cudaSuccess);
+            slot->bufs.push_back(tk.dev);
+            chunks += tk.chunks;
+            if (r != HD_OK || e != cudaSuccess) {
+                SScan &s = sv->scans[tk.id];
                 s.state = 3;
                 s.status = r != HD_OK ? r : HD_ERR_CUDA;
             }
         }
+        if (r != HD_OK || e != cudaSuccess) sv->cv_done.notify_all();
         sv->stats.launches += 1;
-        sv->stats.chunks_launched += static_cast<int64_t>(take.size());
+        sv->stats.items_launched += static_cast<int64_t>(take.size());
+        sv->stats.chunks_launched += chunks;
         sv->stats.issue_seconds +=
             std::chrono::duration<double>(std::chrono::steady_clock::now() - t_issue).count();
     }
@@ -266,6 +363,9 @@ hd_status hd_server_config_default(hd_server_config *out)
     out->max_batch = 64;
     out->max_in_flight = 2;
     out->min_batch = 8;
+    out->segment_histories = 1 << 19;
+    out->staging_bytes = size_t(4) << 30;
+    out->submit_timeout_ms = 60000;
     return HD_OK;
 }
 
@@ -275,7 +375,9 @@ hd_status hd_server_create(const hd_server_config *cfg, hd_server **out)
     *out = nullptr;
     if (cfg->max_chunk < 1 || cfg->max_batch < 1 || cfg->max_batch > hd::kMaxBatch ||
         cfg->max_in_flight < 1 || cfg->max_in_flight > 8 || cfg->hbm_budget_bytes == 0 ||
-        cfg->min_batch < 1)
+        cfg->min_batch < 1 || cfg->segment_histories < cfg->max_chunk ||
+        cfg->segment_histories > (int64_t(1) << 25) || cfg->submit_timeout_ms < 0 ||
+        cfg->staging_bytes < sizeof(float) * 6 * static_cast<size_t>(cfg->segment_histories))
         return HD_ERR_ARG;
     hd_server *sv = new (std::nothrow) hd_server();
     if (!sv) return HD_ERR_NOMEM;
@@ -283,7 +385,6 @@ hd_status hd_server_create(const hd_server_config *cfg, hd_server **out)
     sv->t0 = std::chrono::steady_clock::now();
     cudaError_t e = cudaGetDevice(&sv->device);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&sv->stream, cudaStreamNonBlocking);
-    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&sv->upload, cudaStreamNonBlocking);
     sv->ticks.resize(static_cast<size_t>(cfg->max_in_flight));
     for (auto &t : sv->ticks) {
         if (e != cudaSuccess) break;
@@ -296,6 +397,7 @@ hd_status hd_server_create(const hd_server_config *cfg, hd_server **out)
         return HD_ERR_CUDA;
     }
     sv->worker = std::thread(worker_main, sv);
+    sv->keeper = std::thread(keeper_main, sv);
     *out = sv;
     return HD_OK;
 }
@@ -308,25 +410,23 @@ hd_status hd_server_destroy(hd_server *sv)
         sv->stop = true;
     }
     sv->cv_work.notify_all();
+    sv->cv_space.notify_all();
+    sv->cv_keep.notify_all();
     if (sv->worker.joinable()) sv->worker.join();
+    if (sv->keeper.joinable()) sv->keeper.join();
     int prev = -1;
     cudaGetDevice(&prev);
     cudaSetDevice(sv->device);
     if (sv->stream) cudaStreamSynchronize(sv->stream);
-    if (sv->upload) cudaStreamSynchronize(sv->upload);
-    for (auto &kv : sv->scans) {
-        for (auto &c : kv.second.pending) release_chunk(c, sv->stream);
+    for (auto &kv : sv->scans)
         if (kv.second.scan) hd_scan_destroy(kv.second.scan);
-    }
+    for (hd_scan *h : sv->graveyard) hd_scan_destroy(h);
     for (auto &t : sv->ticks) {
         if (t.batch) hd_batch_destroy(t.batch);
         if (t.done) cudaEventDestroy(t.done);
     }
-    if (sv->stream) {
-        cudaStreamSynchronize(sv->stream);
-        cudaStreamDestroy(sv->stream);
-    }
-    if (sv->upload) cudaStreamDestroy(sv->upload);
+    for (float *b : sv->all_bufs) cudaFree(b);
+    if (sv->stream) cudaStreamDestroy(sv->stream);
     if (prev >= 0) cudaSetDevice(prev);
     delete sv;
     return HD_OK;
@@ -349,7 +449,7 @@ hd_status hd_server_open_scan(hd_server *sv, const hd_geometry *geom, const hd_p
     sv->scans[s.id] = std::move(s);
     sv->waiting.push_back(*scan_id);
     sv->stats.scans_opened += 1;
-    sv->cv_work.notify_all();
+    sv->cv_keep.notify_all();
     return HD_OK;
 }
 
@@ -361,50 +461,74 @@ hd_status hd_server_submit_chunk(hd_server *sv, int64_t scan_id, const float *an
     if (!sv || n < 1 || n > sv->cfg.max_chunk) return HD_ERR_ARG;
     if (!angle_deg || !u_in || !v_in || !u_out || !v_out || !wepl) return HD_ERR_ARG;
     const auto t_submit = std::chrono::steady_clock::now();
+    const auto deadline = t_submit + std::chrono::milliseconds(sv->cfg.submit_timeout_ms);
+    const int64_t cap = sv->cfg.segment_histories;
+    Segment *seg = nullptr;
+    int64_t off = 0;
     {
-        std::lock_guard<std::mutex> lock(sv->mu);
-        auto it = sv->scans.find(scan_id);
-        if (it == sv->scans.end()) return HD_ERR_ARG;
-        if (it->second.state >= 2 || it->second.submitted >= it->second.n_chunks)
-            return HD_ERR_STATE;
+        // reserve room in the scan's open segment (a new one when it is full)
+        std::unique_lock<std::mutex> lock(sv->mu);
+        for (;;) {
+            auto it = sv->scans.find(scan_id);
+            if (it == sv->scans.end()) return HD_ERR_ARG;
+            SScan &s = it->second;
+            if (s.state >= 2 || s.reserved_chunks >= s.n_chunks) return HD_ERR_STATE;
+            if (!s.segs.empty() && !s.segs.back()->sealed && s.segs.back()->reserved + n <= cap) {
+                seg = s.segs.back().get();
+                break;
+            }
+            hd_status err = HD_OK;
+            float *buf = take_buffer(sv, &err);
+            if (err != HD_OK) return err;
+            if (buf) {
+                if (!s.segs.empty()) s.segs.back()->sealed = true;
+                s.segs.emplace_back(new Segment());
+                s.segs.back()->dev = buf;
+                seg = s.segs.back().get();
+                break;
+            }
+            // staging is full: wait for a launch to return its segments
+            if (sv->stop ||
+                sv->cv_space.wait_until(lock, deadline) == std::cv_status::timeout)
+                return HD_ERR_TIMEOUT;
+        }
+        off = seg->reserved;
+        seg->reserved += n;
+        seg->writers += 1;
+        sv->scans[scan_id].reserved_chunks += 1;
     }
     int prev = -1;
     cudaGetDevice(&prev);
     if (prev != sv->device) cudaSetDevice(sv->device);
-    Chunk c;
-    c.n = n;
-    const float *src[6] = {angle_deg, u_in, v_in, u_out, v_out, wepl};
-    // each client thread uploads on its own per-thread stream, so uploads
+    // each client thread copies on its own per-thread stream, so uploads
     // from several threads proceed side by side
     const cudaStream_t up = cudaStreamPerThread;
-    cudaError_t e = cudaMallocAsync(reinterpret_cast<void **>(&c.dev), sizeof(float) * 6 * n, up);
+    const float *src[6] = {angle_deg, u_in, v_in, u_out, v_out, wepl};
+    cudaError_t e = cudaSuccess;
     for (int a = 0; e == cudaSuccess && a < 6; ++a)
-        e = cudaMemcpyAsync(c.dev + a * n, src[a], sizeof(float) * n,
+        e = cudaMemcpyAsync(seg->dev + a * cap + off, src[a], sizeof(float) * n,
                             on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, up);
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c.ready, cudaEventDisableTiming);
-    if (e == cudaSuccess) e = cudaEventRecord(c.ready, up);
     // the caller may reuse its buffers as soon as this call returns
     if (e == cudaSuccess) e = cudaStreamSynchronize(up);
+    if (e != cudaSuccess) cudaGetLastError();
     if (prev >= 0 && prev != sv->device) cudaSetDevice(prev);
+    std::lock_guard<std::mutex> lock(sv->mu);
+    SScan &s = sv->scans[scan_id];  // cannot be closed while a copy runs
+    seg->writers -= 1;
     if (e != cudaSuccess) {
-        cudaGetLastError();
-        if (c.dev) cudaFreeAsync(c.dev, up);
-        if (c.ready) cudaEventDestroy(c.ready);
+        // the segment has a hole: the scan cannot be completed
+        s.state = 3;
+        s.status = HD_ERR_CUDA;
+        sv->cv_done.notify_all();
         return HD_ERR_CUDA;
     }
-    std::lock_guard<std::mutex> lock(sv->mu);
-    auto it = sv->scans.find(scan_id);
-    if (it == sv->scans.end()) {
-        release_chunk(c, sv->upload);
-        return HD_ERR_ARG;
-    }
-    SScan &s = it->second;
+    seg->filled += n;
+    seg->chunks += 1;
     const double now = now_since(sv->t0);
     if (s.submitted == 0) s.t_first = now;
     s.submitted += 1;
     if (s.submitted == s.n_chunks) s.t_last = now;
     s.histories += n;
-    s.pending.push_back(c);
     sv->stats.chunks_submitted += 1;
     sv->stats.submit_seconds +=
         std::chrono::duration<double>(std::chrono::steady_clock::now() - t_submit).count();
@@ -480,31 +604,31 @@ hd_status hd_server_get_stats(hd_server *sv, hd_server_stats *out)
 hd_status hd_server_close_scan(hd_server *sv, int64_t scan_id)
 {
     if (!sv) return HD_ERR_ARG;
-    hd_scan *h = nullptr;
-    {
-        std::lock_guard<std::mutex> lock(sv->mu);
-        auto it = sv->scans.find(scan_id);
-        if (it == sv->scans.end()) return HD_ERR_ARG;
-        SScan &s = it->second;
-        if (s.state == 1 && s.done_chunks < s.issued) return HD_ERR_STATE;  // still running
-        if (s.state == 1 && !s.pending.empty()) return HD_ERR_STATE;
-        for (auto &c : s.pending) release_chunk(c, sv->upload);
-        h = s.scan;
-        if (s.state >= 1 && h) sv->used -= s.footprint;
-        for (auto ai = sv->admitted_order.begin(); ai != sv->admitted_order.end(); ++ai)
-            if (*ai == scan_id) {
-                sv->admitted_order.erase(ai);
-                break;
-            }
-        for (auto wi = sv->waiting.begin(); wi != sv->waiting.end(); ++wi)
-            if (*wi == scan_id) {
-                sv->waiting.erase(wi);
-                break;
-            }
-        sv->scans.erase(it);
-    }
-    if (h) hd_scan_destroy(h);
-    sv->cv_work.notify_all();
+    std::lock_guard<std::mutex> lock(sv->mu);
+    auto it = sv->scans.find(scan_id);
+    if (it == sv->scans.end()) return HD_ERR_ARG;
+    SScan &s = it->second;
+    if (s.admitting) return HD_ERR_STATE;                                // being created
+    if (s.state == 1 && s.done_chunks < s.issued) return HD_ERR_STATE;  // still running
+    if (s.state == 1 && !s.segs.empty()) return HD_ERR_STATE;
+    for (const auto &g : s.segs)
+        if (g->writers) return HD_ERR_STATE;  // a submit is copying into it
+    if (s.state == 3 && s.done_chunks < s.issued) return HD_ERR_STATE;
+    recycle_segments(sv, s);
+    if (s.state >= 1 && s.scan) sv->used -= s.footprint;
+    if (s.scan) sv->graveyard.push_back(s.scan);  // destroyed by the keeper thread
+    for (auto ai = sv->admitted_order.begin(); ai != sv->admitted_order.end(); ++ai)
+        if (*ai == scan_id) {
+            sv->admitted_order.erase(ai);
+            break;
+        }
+    for (auto wi = sv->waiting.begin(); wi != sv->waiting.end(); ++wi)
+        if (*wi == scan_id) {
+            sv->waiting.erase(wi);
+            break;
+        }
+    sv->scans.erase(it);
+    sv->cv_keep.notify_all();
     return HD_OK;
 }
 

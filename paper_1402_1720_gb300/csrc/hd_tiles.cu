@@ -16,7 +16,7 @@ namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kScatterThreads = 256;
-constexpr int kScatterPerThread = 16;
+constexpr int kScatterPerThread = 16;  // most records a scatter thread takes
 
 __device__ __forceinline__ unsigned warp_incl_scan_u(unsigned v)
 {
@@ -107,7 +107,7 @@ __global__ void __launch_bounds__(1024) plan_kernel(TilePlan tp, const uint32_t 
 __global__ void __launch_bounds__(kScatterThreads) scatter_kernel(TilePlan tp, Records rec,
                                                                   const Ctrl *ctrl,
                                                                   uint32_t *tile_cursor,
-                                                                  Pairs pairs)
+                                                                  Pairs pairs, int per_thread)
 {
     extern __shared__ uint32_t s_mem[];
     const int nt = 2 * tp.ntiles;
@@ -116,14 +116,14 @@ __global__ void __launch_bounds__(kScatterThreads) scatter_kernel(TilePlan tp, R
     for (int t = threadIdx.x; t < nt; t += blockDim.x) s_hist[t] = 0;
     __syncthreads();
     const unsigned nm = ctrl->rec_miss, nh = ctrl->rec_hit;
-    const int64_t slot0 = static_cast<int64_t>(blockIdx.x) * kScatterThreads * kScatterPerThread;
+    const int64_t slot0 = static_cast<int64_t>(blockIdx.x) * kScatterThreads * per_thread;
     auto valid = [&](int64_t slot, int &cls) -> bool {
         if (slot < nm) { cls = 0; }
         else if (slot >= rec.cap - nh) { cls = 1; }
         else return false;
         return rec.status[slot] == 1;
     };
-    for (int k = 0; k < kScatterPerThread; ++k) {
+    for (int k = 0; k < per_thread; ++k) {
         const int64_t slot = slot0 + k * kScatterThreads + threadIdx.x;
         int cls;
         if (slot >= rec.cap || !valid(slot, cls)) continue;
@@ -144,7 +144,7 @@ __global__ void __launch_bounds__(kScatterThreads) scatter_kernel(TilePlan tp, R
         s_hist[t] = 0;
     }
     __syncthreads();
-    for (int k = 0; k < kScatterPerThread; ++k) {
+    for (int k = 0; k < per_thread; ++k) {
         const int64_t slot = slot0 + k * kScatterThreads + threadIdx.x;
         int cls;
         if (slot >= rec.cap || !valid(slot, cls)) continue;
@@ -428,14 +428,21 @@ cudaError_t launch_plan(const TilePlan &tp, const uint32_t *tile_count, uint32_t
 }
 
 cudaError_t launch_scatter(const TilePlan &tp, const Records &rec, const Ctrl *ctrl,
-                           uint32_t *tile_cursor, const Pairs &pairs, int64_t n, cudaStream_t s)
+                           uint32_t *tile_cursor, const Pairs &pairs, int64_t n, int sm_count,
+                           cudaStream_t s)
 {
-    const int64_t per_block = static_cast<int64_t>(kScatterThreads) * kScatterPerThread;
+    if (n <= 0) return cudaSuccess;
+    // records per thread: up to kScatterPerThread, fewer when that would
+    // leave SMs idle (eight blocks of 256 per SM fill it)
+    const int64_t fill = static_cast<int64_t>(sm_count > 0 ? sm_count : 1) * 8 * kScatterThreads;
+    int64_t per = (n + fill - 1) / fill;
+    if (per > kScatterPerThread) per = kScatterPerThread;
+    if (per < 1) per = 1;
+    const int64_t per_block = static_cast<int64_t>(kScatterThreads) * per;
     const int64_t blocks = (n + per_block - 1) / per_block;
-    if (blocks <= 0) return cudaSuccess;
     const size_t smem = sizeof(uint32_t) * 4 * static_cast<size_t>(tp.ntiles);
-    scatter_kernel<<<static_cast<unsigned>(blocks), kScatterThreads, smem, s>>>(tp, rec, ctrl,
-                                                                               tile_cursor, pairs);
+    scatter_kernel<<<static_cast<unsigned>(blocks), kScatterThreads, smem, s>>>(
+        tp, rec, ctrl, tile_cursor, pairs, static_cast<int>(per));
     return cudaGetLastError();
 }
 

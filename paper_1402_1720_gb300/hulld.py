@@ -89,7 +89,8 @@ HD_BATCH_RESET, HD_BATCH_FINALIZE = 1, 2
 class hd_server_config(ctypes.Structure):
     _fields_ = [("hbm_budget_bytes", ctypes.c_size_t), ("max_chunk", ctypes.c_int64),
                 ("max_batch", ctypes.c_int32), ("max_in_flight", ctypes.c_int32),
-                ("min_batch", ctypes.c_int32)]
+                ("min_batch", ctypes.c_int32), ("segment_histories", ctypes.c_int64),
+                ("staging_bytes", ctypes.c_size_t), ("submit_timeout_ms", ctypes.c_int64)]
 
 
 class hd_server_scan_info(ctypes.Structure):
@@ -108,7 +109,7 @@ class hd_server_stats(ctypes.Structure):
                 ("scans_done", ctypes.c_int64), ("chunks_submitted", ctypes.c_int64),
                 ("chunks_launched", ctypes.c_int64), ("launches", ctypes.c_int64),
                 ("bytes_in_use", ctypes.c_int64), ("issue_seconds", ctypes.c_double),
-                ("submit_seconds", ctypes.c_double)]
+                ("submit_seconds", ctypes.c_double), ("items_launched", ctypes.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -123,6 +124,7 @@ _SIGS = {
                         ctypes.POINTER(_VP)], ctypes.c_int),
     "hd_scan_destroy": ([_VP], ctypes.c_int),
     "hd_scan_reset": ([_VP, _VP], ctypes.c_int),
+    "hd_scan_reserve": ([_VP, _I64, _VP], ctypes.c_int),
     "hd_scan_add_histories": ([_VP] + [_VP] * 6 + [_I64, _I32, _VP], ctypes.c_int),
     "hd_scan_finalize": ([_VP, _VP], ctypes.c_int),
     "hd_scan_get_mask": ([_VP, _I32, _I32, _VP, _SZ, _I32, _VP], ctypes.c_int),
@@ -269,6 +271,10 @@ def hd_scan_destroy(scan: int) -> None:
 
 def hd_scan_reset(scan: int, stream=None) -> None:
     _check(load().hd_scan_reset(scan, _stream(stream)), "hd_scan_reset")
+
+
+def hd_scan_reserve(scan: int, n: int, stream=None) -> None:
+    _check(load().hd_scan_reserve(scan, int(n), _stream(stream)), "hd_scan_reserve")
 
 
 def hd_scan_add_histories(scan: int, angle_deg, u_in, v_in, u_out, v_out, wepl,
@@ -658,6 +664,9 @@ class Scan:
 
     def reset(self, stream=None):
         hd_scan_reset(self.handle, stream)
+
+    def reserve(self, n: int, stream=None):
+        hd_scan_reserve(self.handle, n, stream)
 
     def add(self, hist_arrays: Sequence, stream=None):
         hd_scan_add_histories(self.handle, *hist_arrays, stream=stream)

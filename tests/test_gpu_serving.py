@@ -1,6 +1,7 @@
 """Serving (continuous batching of streamed scans): every scan's result is
-identical alone and in the mix, admission by device footprint, and bounded
-waits that give up on a scan whose last chunk never arrives."""
+identical alone and in the mix, admission by device footprint, bounded
+staging memory with bounded submit waits, and bounded waits that give up on
+a scan whose last chunk never arrives."""
 import threading
 
 import numpy as np
@@ -65,13 +66,29 @@ def test_served_equals_alone(hd, scans_case):
     refs = [_alone(hd, sp.geometry, h) for sp, h, _ in scans_case]
     with hd.Server() as srv:
         ids = [srv.open_scan(sp.geometry, None, len(ch)) for sp, _, ch in scans_case]
+        # chunks alternate between pageable numpy arrays, page-locked host
+        # tensors and device tensors
+        payload = []
+        for k, (_, _, ch) in enumerate(scans_case):
+            row = []
+            for j, c in enumerate(ch):
+                kind = (k + j) % 3
+                if kind == 0:
+                    row.append(c.arrays())
+                elif kind == 1:
+                    row.append([torch.from_numpy(a).pin_memory() for a in c.arrays()])
+                else:
+                    row.append([torch.from_numpy(a).cuda() for a in c.arrays()])
+            payload.append(row)
+        torch.cuda.synchronize()
+
         # a client thread interleaves the chunks of all scans
         def client():
             pos = [0] * len(ids)
             while any(p < len(ch) for p, (_, _, ch) in zip(pos, scans_case)):
                 for k, (sid, (_, _, ch)) in enumerate(zip(ids, scans_case)):
                     if pos[k] < len(ch):
-                        srv.submit(sid, ch[pos[k]].arrays())
+                        srv.submit(sid, payload[k][pos[k]])
                         pos[k] += 1
         t = threading.Thread(target=client)
         t.start()
@@ -88,11 +105,13 @@ def test_served_equals_alone(hd, scans_case):
         assert st["scans_done"] == len(ids) and st["bytes_in_use"] == 0
         assert st["chunks_launched"] == sum(len(ch) for _, _, ch in scans_case)
         assert st["launches"] < st["chunks_launched"]  # chunks of several scans per launch
+        assert st["launches"] <= st["items_launched"] <= st["chunks_launched"]
 
 
 def test_admission_by_footprint(hd, scans_case):
     cfg = hd.hd_server_config_default()
     cfg.max_chunk = 20000
+    cfg.segment_histories = 20000
     fp = max(sp.geometry.n_voxels * 11 + sp.geometry.n_voxels // 4 + 20000 * (28 + 512) + (4 << 20)
              for sp, _, _ in scans_case)
     cfg.hbm_budget_bytes = int(2.2 * fp)  # about two scans at a time
@@ -141,3 +160,52 @@ def test_withheld_last_chunk_times_out(hd, scans_case):
             srv.submit(sid, empty.arrays())
         assert e.value.status == hd.HD_ERR_STATE
         srv.close_scan(sid)
+
+
+def test_staging_backpressure(hd, scans_case):
+    """Two staging segments only, and room for one scan: the waiting scan's
+    chunks fill the staging and a further submit gives up after its timeout;
+    once the first scan is closed the second one is admitted, its segments
+    run, and submits go through again.  Both results equal the lone scans."""
+    (sp_a, h_a, ch_a), (sp_b, h_b, ch_b) = scans_case[0], scans_case[1]
+    cfg = hd.hd_server_config_default()
+    cfg.max_chunk = 20000
+    cfg.segment_histories = 40000
+    cfg.staging_bytes = 2 * 24 * 40000
+    cfg.submit_timeout_ms = 300
+    fp = lambda g: g.n_voxels * 11 + g.n_voxels // 4 + 40000 * (28 + 512) + (4 << 20)
+    cfg.hbm_budget_bytes = max(fp(sp_a.geometry), fp(sp_b.geometry)) + 1  # one scan at a time
+    with hd.Server(cfg) as srv:
+        a = srv.open_scan(sp_a.geometry, None, len(ch_a))
+        b = srv.open_scan(sp_b.geometry, None, len(ch_b))
+        for c in ch_a:
+            srv.submit(a, c.arrays())
+        assert srv.wait(a, 60000) == hd.HD_OK
+        assert srv.info(b)["state"] == 0  # not admitted while a is open
+        # b's chunks fill both segments (at least 2 x 20000 histories each)
+        k = 0
+        timed_out = False
+        while k < len(ch_b):
+            try:
+                srv.submit(b, ch_b[k].arrays())
+            except hd.HDError as e:
+                assert e.status == hd.HD_ERR_TIMEOUT
+                timed_out = True
+                break
+            k += 1
+        assert timed_out and 2 <= k < len(ch_b)
+        got_a = _served(hd, srv.scan(a, sp_a.geometry))
+        ref_a = _alone(hd, sp_a.geometry, h_a)
+        for key in ref_a:
+            assert np.array_equal(got_a[key], ref_a[key]), key
+        srv.close_scan(a)
+        for c in ch_b[k:]:  # the refused chunk again, then the rest
+            srv.submit(b, c.arrays())
+        assert srv.wait(b, 60000) == hd.HD_OK
+        got_b = _served(hd, srv.scan(b, sp_b.geometry))
+        ref_b = _alone(hd, sp_b.geometry, h_b)
+        for key in ref_b:
+            assert np.array_equal(got_b[key], ref_b[key]), key
+        st = srv.stats()
+        assert st["chunks_launched"] == len(ch_a) + len(ch_b)
+        srv.close_scan(b)
