@@ -691,6 +691,101 @@ HD_HD bool run_begin(RunWalk &rw, const int32_t gi[3], const int32_t go[3], int 
     return true;
 }
 
+// ---------------------------------------------------------- lean run walk
+//
+// Most walks inside a one-voxel-deep tile are "lean": the in-plane minor
+// axis (minor 0) never crosses at the same parameter as the major axis
+// (rl_0 != 0: D_0 is never a multiple of S_0), z never ties with the major
+// axis (rl_1 != 0) nor with minor 0 (e12 is never a multiple of 2^16, and
+// every update adds one), no tie is pending at the start, and z has no valid
+// crossing inside the box, so its first crossing (if any) ends the walk.
+// Then every event is a lone crossing and the runs have a closed form.
+// Counting major crossings from the start, minor 0's k-th crossing (k >= 1)
+// comes after J_k = q_0 + 1 + (k - 1) Qu_0 + floor((rh_0 + (k - 1) Ru_0) / ad_0)
+// of them (so J_1 = q_0 + 1, and J_{k+1} = J_k + Qu_0 + carry, Bresenham
+// style); z crosses after j_z = q_1 + 1; the major axis runs out after km.
+// Crossing k of minor 0 happens iff k <= kc_0, k <= K_z (the number of
+// minor-0 crossings before z's, from the sign of e12 + k ad_1 2^16) and
+// J_k <= km.  Run k (k = 0, 1, ...) covers major counts J_k .. J_{k+1}
+// (J_0 = 0) in row row_0 + k (the minor-0 row stride), the last run ending
+// at min(J_{K+1}, km, j_z) instead.  These are exactly the runs run_next
+// produces.  A lean walk keeps its state in RunWalk's fields:
+//   q[0] = J_{k+1}, rh[0] = (rh_0 + k Ru_0) mod ad_0, ad[0], Qu[0] (capped at
+//   kLeanQuCap: one step beyond the box suffices), Ru[0], km, kc[0] = crossings
+//   left (K - k), kc[1] = K, q[1] = j_z, im = major index at the start,
+//   run_start = J_k, row, flags bit 12.
+constexpr int kLeanFlag = 1 << 12;
+constexpr int kLeanQuCap = 8192;  // > any box extent (4096)
+
+// Turn a freshly begun walk into its lean form when it is lean; returns
+// whether it did.
+HD_HD bool run_make_lean(RunWalk &w)
+{
+    const int fl = w.flags;
+    if (fl & ((7 << 6) | (1 << 9))) return false;  // a tie pending, or empty
+    const bool act0 = (fl >> 3) & 1, act1 = (fl >> 4) & 1;
+    if (w.kc[1] != 0) return false;             // z crosses inside the box
+    if (!((fl >> 10) & 1) || !((fl >> 11) & 1)) return false;  // a tie with the major axis
+    if (w.q[0] < -1 || w.q[1] < -1) return false;
+    int kz;  // minor-0 crossings before z's (crossings of minor 0 past kc_0 never happen)
+    if (!act0) {
+        kz = 0;
+    } else if (!act1) {
+        kz = w.kc[0];
+    } else {
+        if ((w.e12 & 0xffff) == 0) return false;  // minor 0 and z may tie
+        if (w.e12 > 0) {
+            kz = 0;
+        } else {
+            const long long step = static_cast<long long>(w.ad[1]) << 16;
+            const long long n = (-w.e12 + step - 1) / step;  // ceil(-e12 / step), e12 < 0
+            kz = n < w.kc[0] ? static_cast<int>(n) : w.kc[0];
+        }
+    }
+    const int K = act0 ? (kz < w.kc[0] ? kz : w.kc[0]) : 0;
+    const int jz = act1 ? w.q[1] + 1 : kQBig;
+    const int j1 = act0 ? w.q[0] + 1 : kQBig;
+    w.q[0] = j1;
+    w.q[1] = jz;
+    if (w.Qu[0] > kLeanQuCap) w.Qu[0] = kLeanQuCap;
+    w.kc[0] = K;
+    w.kc[1] = K;
+    w.run_start = 0;
+    w.e12 = 0;
+    w.flags = (fl & (1 | 2 | (1 << 3) | (1 << 5))) | kLeanFlag;
+    return true;
+}
+
+// Next run of a lean walk (the same contract as run_next); when it returns
+// the last run it also adds the walk's voxel count to `steps`.
+HD_HD bool lean_next(RunWalk &w, int &row, int &lo, int &hi, unsigned &steps)
+{
+    if (w.flags & (1 << 9)) return false;
+    const int jn = w.q[0];
+    const bool last = w.kc[0] == 0 || jn > w.km;
+    int e = jn < w.km ? jn : w.km;
+    e = e < w.q[1] ? e : w.q[1];
+    const int sg = (w.flags & 1) ? 1 : -1;
+    const int a = w.im + sg * w.run_start, b = w.im + sg * e;
+    lo = a < b ? a : b;
+    hi = a < b ? b : a;
+    row = w.row;
+    if (last) {
+        // runs k = 0..K cover e + 1 major cells plus one per row change
+        steps += static_cast<unsigned>(e + (w.kc[1] - w.kc[0]) + 1);
+        w.flags |= 1 << 9;
+        return true;
+    }
+    w.run_start = jn;
+    const unsigned rem = w.rh[0] + w.Ru[0];
+    const bool carry = rem >= w.ad[0];
+    w.rh[0] = carry ? rem - w.ad[0] : rem;
+    w.q[0] = jn + w.Qu[0] + (carry ? 1 : 0);
+    --w.kc[0];
+    w.row += w.rstride[0];
+    return true;
+}
+
 // Packed run-walk state: 16 32-bit words, so a walk prepared by one kernel
 // can be resumed by another.  The row strides and the major size follow
 // from the box (nx, ny) and the flags.
@@ -743,7 +838,7 @@ HD_HD void run_unpack(const uint32_t o[kPackedWords], int nx, int ny, RunWalk &w
     w.kc[1] = static_cast<int>(o[14] >> 16);
     w.flags = static_cast<int>(o[15]);
     const bool ymaj = (w.flags >> 5) & 1;
-    w.run_start = w.im;
+    w.run_start = (w.flags & kLeanFlag) ? 0 : w.im;
     w.rstride[0] = (w.flags & 2) ? 1 : -1;
     w.rstride[1] = (w.flags & 4) ? (ymaj ? nx : ny) : -(ymaj ? nx : ny);
     w.nmaj = ymaj ? ny : nx;

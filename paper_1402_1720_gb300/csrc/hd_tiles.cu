@@ -166,8 +166,12 @@ __global__ void __launch_bounds__(kScatterThreads) scatter_kernel(TilePlan tp, R
                     const int32_t go[3] = {r[3] - (x0 << 16), r[4] - (y0 << 16), r[5] - (z0 << 16)};
                     RunWalk w;
                     uint32_t o[kPackedWords];
-                    if (run_begin(w, gi, go, dx, dy, dz)) run_pack(w, o);
-                    else run_pack_empty(o);
+                    if (run_begin(w, gi, go, dx, dy, dz)) {
+                        run_make_lean(w);  // closed-form runs when the walk allows
+                        run_pack(w, o);
+                    } else {
+                        run_pack_empty(o);
+                    }
 #pragma unroll
                     for (int a = 0; a < 4; ++a)
                         pairs.v[4 * static_cast<size_t>(pos) + a] =
@@ -351,9 +355,15 @@ __global__ void __launch_bounds__(kThreads, 1) trace_tiles_kernel(
             }
             if (active) {
                 int row, lo, hi;
-                if (run_next(w, row, lo, hi)) {
+                bool got;
+                if (w.flags & kLeanFlag) {
+                    got = lean_next(w, row, lo, hi, steps);
+                } else {
+                    got = run_next(w, row, lo, hi);
+                    if (got) steps += static_cast<unsigned>(hi - lo + 1);
+                }
+                if (got) {
                     const int base = row * w.nmaj;
-                    steps += static_cast<unsigned>(hi - lo + 1);
                     if (!carve_mode) {
                         diff_add(arr, base + lo, 1);
                         if (hi + 1 < w.nmaj) diff_add(arr, base + hi + 1, -1);

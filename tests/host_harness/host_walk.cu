@@ -103,3 +103,37 @@ extern "C" long long hx_check_tile_division(void)
     }
     return bad;
 }
+// the lean form when the walk has one (through pack and unpack, as the
+// traversal kernel sees it), else the general run walk; *lean says which
+// and *steps is the voxel count the lean walk reports with its last run
+extern "C" int hx_runs_lean(const int32_t *gi, const int32_t *go, int nx, int ny, int nz,
+                            int32_t *out, int cap, int *lean, unsigned *steps)
+{
+    hd::RunWalk w0, w;
+    uint32_t o[hd::kPackedWords];
+    *lean = 0;
+    *steps = 0;
+    if (hd::run_begin(w0, gi, go, nx, ny, nz)) {
+        *lean = hd::run_make_lean(w0) ? 1 : 0;
+        hd::run_pack(w0, o);
+    } else {
+        hd::run_pack_empty(o);
+    }
+    hd::run_unpack(o, nx, ny, w);
+    int n = 0, runs = 0;
+    const bool ymaj = (w.flags >> 5) & 1;
+    int row, lo, hi;
+    for (;;) {
+        const bool got = (w.flags & hd::kLeanFlag) ? hd::lean_next(w, row, lo, hi, *steps)
+                                                   : hd::run_next(w, row, lo, hi);
+        if (!got) break;
+        if (lo < 0 || hi >= w.nmaj || lo > hi) return -1000000;
+        if (++runs > 100000) return -2000000;
+        for (int m = lo; m <= hi; ++m) {
+            int v = !ymaj ? m + nx * row : (row % nx) + nx * (m + ny * (row / nx));
+            if (n < cap) out[n] = v;
+            ++n;
+        }
+    }
+    return n;
+}

@@ -157,3 +157,84 @@ def test_tile_index_division_exhaustive(hx):
     index and tile size the library supports (including tiles of one voxel)."""
     hx.hx_check_tile_division.restype = ctypes.c_longlong
     assert hx.hx_check_tile_division() == 0
+
+
+def _runs_lean(L, a, b, dims):
+    L.hx_runs_lean.restype = ctypes.c_int
+    out = np.zeros(2 * sum(dims) + 64, np.int32)
+    lean = ctypes.c_int(0)
+    steps = ctypes.c_uint(0)
+    n = L.hx_runs_lean(np.asarray(a, np.int32).ctypes.data_as(I32P),
+                       np.asarray(b, np.int32).ctypes.data_as(I32P), *dims,
+                       out.ctypes.data_as(I32P), out.size, ctypes.byref(lean), ctypes.byref(steps))
+    assert n >= 0
+    return np.sort(out[:n]), bool(lean.value), steps.value
+
+
+@pytest.mark.parametrize("dims", [(200, 200, 1), (40, 30, 1), (7, 1, 1), (1, 7, 1), (5, 4, 3),
+                                  (40, 30, 20), (64, 3, 2)])
+def test_lean_run_walk_equals_oracle(oracle_mod, hx, dims):
+    """Walks in their lean form (closed-form runs) give the oracle's voxel set
+    and report its size; adversarial segments (lattice points, shared
+    planes) keep the general form and still agree."""
+    rng = np.random.default_rng(sum(dims) + 17)
+    n_lean = 0
+    for a, b in _random_segments(rng, 4000, dims):
+        got, lean, steps = _runs_lean(hx, a, b, dims)
+        assert len(np.unique(got)) == len(got)
+        assert np.array_equal(got, oracle_mod.voxel_set(a, b, *dims)), (a.tolist(), b.tolist())
+        if lean:
+            n_lean += 1
+            assert steps == len(got)
+    assert n_lean > 0
+
+
+@pytest.mark.parametrize("dims", [(200, 200, 1), (64, 64, 1), (9, 200, 1), (40, 30, 6)])
+def test_lean_run_walk_generic_inputs(oracle_mod, hx, dims):
+    """Segments with arbitrary Q16 endpoints (as from float detector
+    coordinates) and a small z slope: almost every walk is lean."""
+    rng = np.random.default_rng(sum(dims) + 19)
+    Q = 65536
+    hi = np.array(dims, np.int64) * Q
+    n_lean = n_walks = 0
+    for k in range(3000):
+        a = rng.integers(-Q, hi + Q)
+        b = rng.integers(-Q, hi + Q)
+        a[2] = rng.integers(0, hi[2])
+        b[2] = a[2] + rng.integers(-Q // 2, Q // 2 + 1)
+        if k % 7 == 0:
+            b[2] = a[2]  # z does not move
+        got, lean, steps = _runs_lean(hx, a, b, dims)
+        assert np.array_equal(got, oracle_mod.voxel_set(a, b, *dims)), (a.tolist(), b.tolist())
+        n_walks += len(got) > 0
+        if lean:
+            n_lean += 1
+            assert steps == len(got)
+    if dims[2] == 1:
+        assert n_lean > 0.99 * n_walks
+
+
+def test_lean_run_walk_nearly_axis_aligned(oracle_mod, hx):
+    """Lean walks whose minor axes move by a few 2^-16 voxel units (saturated
+    quotients, capped steps) or start on a plane."""
+    Q = 65536
+    rng = np.random.default_rng(23)
+    n_lean = 0
+    for dims in [(200, 200, 1), (64, 7, 1), (40, 30, 3)]:
+        hi = np.array(dims) * Q
+        for k in range(3000):
+            a = rng.integers(-2 * Q, hi + 2 * Q)
+            b = a.copy()
+            maj = rng.integers(0, 2)
+            b[maj] = rng.integers(-2 * Q, hi[maj] + 2 * Q)
+            for ax in range(3):
+                if ax != maj:
+                    b[ax] = a[ax] + rng.integers(-3, 4) * (rng.integers(1, 3) if k % 2 else 1)
+            if k % 5 == 0:
+                a[1 - maj] = (a[1 - maj] >> 16) << 16
+            got, lean, steps = _runs_lean(hx, a, b, dims)
+            assert np.array_equal(got, oracle_mod.voxel_set(a, b, *dims)), (a.tolist(), b.tolist())
+            if lean:
+                n_lean += 1
+                assert steps == len(got)
+    assert n_lean > 1000
