@@ -431,6 +431,9 @@ def main():
     ap.add_argument("--workload", default="head-200",
                     choices=["head-200", "batched-48", "serving"])
     ap.add_argument("--batch-fraction", type=float, default=1.0)
+    ap.add_argument("--fraction", type=float, default=1.0,
+                    help="head-200 workload: keep this fraction of the histories "
+                         "(small profiling captures; 1.0 for the benchmark)")
     ap.add_argument("--no-tune", action="store_true")
     ap.add_argument("--serve-scans", type=int, default=48)
     ap.add_argument("--serve-load", type=float, default=0.7)
@@ -460,7 +463,7 @@ def main():
     hbuild.build()
     hulld.load()
 
-    w = synth.make_config(2)
+    w = synth.make_config(2, fraction=args.fraction) if args.fraction < 1.0 else synth.make_config(2)
     g, h = w.geometry, w.histories
     n = len(h)
     dev = [torch.from_numpy(a).cuda() for a in h.arrays()]
@@ -589,7 +592,9 @@ def main():
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                 "dtype": "int64", "data": "synthetic",
                 "config": {"workload": WORKLOAD, "methods": "SC+MSC+SM",
-                           "inputs": "9e6 x 24 B = 216 MB resident in HBM, larger than L2",
+                           "histories": n, "fraction": args.fraction,
+                           "inputs": f"{n:.3g} x 24 B = {n * 24 / 1e6:.0f} MB resident in HBM"
+                                     + (", larger than L2" if n * 24 > 129e6 else ""),
                            "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
                 "voxel_steps_per_s": ws * steps_per_scan / (ms * 1e-3),
                 "voxel_steps_per_scan": steps_per_scan,

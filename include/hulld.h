@@ -118,6 +118,9 @@ typedef struct {
     int64_t n_reject;   /* missed/hit histories with unusable geometry (not traversed) */
     int64_t steps_miss; /* sum of |A_i| over traversed missed histories */
     int64_t steps_hit;  /* sum of |A_i| over traversed hit histories */
+    int64_t pairs_general; /* (history, tile) pairs of the tiled pass whose walk has a tie
+                              or crosses z inside the tile, walked by the general run walk
+                              in global memory instead of the closed-form lean walk */
 } hd_stats;
 
 /* Kernel-level timing of a scan (enabled by hd_scan_set_profiling):
@@ -225,11 +228,12 @@ HD_API hd_status hd_scan_get_hull_indices(hd_scan *scan, int32_t method, int32_t
 
 /* Launch parameters of the traversal, chosen per volume class by the
  * autotuner (paper_1402_1720_gb300/autotune.py) or left at their defaults:
- *   threads     threads per block of the traversal: 256, 512 or 768 (512)
+ *   threads     threads per block of the traversal: 256, 512, 768 or 1024 (1024)
  *   refill      idle lanes of a warp that trigger taking new walks, 1..32 (8)
  *   job_size    (record, tile) pairs per job, 256..32767 (16384)
  *   slab_depth  z-slices per shared-memory tile when whole x-y planes fit,
- *               0 = as many as fit (0)
+ *               at most as many as fit; 0 = one slice (0).  Walks that cross
+ *               z inside a deeper slab take the general walk in global memory
  * A deployment aid: the paper has no counterpart. */
 typedef struct {
     int32_t threads, refill, job_size, slab_depth;

@@ -15,10 +15,10 @@ from typing import Dict, Iterable, Optional, Sequence
 
 from . import hulld
 
-DEFAULT = {"threads": 512, "refill": 8, "job_size": 16384, "slab_depth": 0}
+DEFAULT = {"threads": 1024, "refill": 8, "job_size": 16384, "slab_depth": 0}
 SPACE = {
-    "slab_depth": [0, 1, 2, 4],
-    "threads": [256, 512, 768],
+    "slab_depth": [0, 2, 4],
+    "threads": [256, 512, 768, 1024],
     "refill": [4, 8, 12, 16, 24],
     "job_size": [4096, 8192, 16384, 32767],
 }

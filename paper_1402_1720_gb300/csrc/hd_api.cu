@@ -91,11 +91,11 @@ struct hd_scan {
     hd::Ctrl *ctrl = nullptr;
     // scratch: traversal records, (record, tile) pairs, jobs, host staging
     hd::TilePlan tp{};
-    hd_tuning tuning{512, 8, 16384, 0};
+    hd_tuning tuning{1024, 8, 16384, 0};
     int trace_grid = 0;
     int32_t *rec_buf = nullptr;   // 7 int32 arrays of rec_cap (6 coordinates + status)
     int64_t rec_cap = 0;
-    uint32_t *pair_buf = nullptr;  // hd::kPackedWords arrays of tp.pair_cap
+    uint32_t *pair_buf = nullptr;  // lean walks (kLeanWords per pair), then the fallback list
     hd::TileJob *jobs = nullptr;
     int64_t job_cap = 0;
     hd::ScanDesc *desc_dev = nullptr;  // this scan's traversal descriptor
@@ -230,8 +230,8 @@ hd_status ensure_records(hd_scan *s, int64_t n, cudaStream_t st)
         const int64_t pair_cap = pairs_per_record(s->tp) * n;
         const int64_t min_job = s->tp.job_size < hd::kMinJob ? s->tp.job_size : hd::kMinJob;
         const int64_t job_cap = pair_cap / min_job + 2 * s->tp.ntiles + 1;
-        ok = cudaMalloc(&s->pair_buf, sizeof(uint32_t) * 16 * static_cast<size_t>(pair_cap)) ==
-                 cudaSuccess &&
+        ok = cudaMalloc(&s->pair_buf, sizeof(uint32_t) * (hd::kLeanWords + 2) *
+                                          static_cast<size_t>(pair_cap)) == cudaSuccess &&
              cudaMalloc(&s->jobs, sizeof(hd::TileJob) * static_cast<size_t>(job_cap)) == cudaSuccess;
         s->tp.pair_cap = pair_cap;
         s->job_cap = job_cap;
@@ -280,6 +280,10 @@ hd::Pairs pairs_of(const hd_scan *s)
 {
     hd::Pairs p;
     p.v = reinterpret_cast<uint4 *>(s->pair_buf);
+    // the fallback list follows the lean walks (kLeanWords words per pair)
+    p.fb = s->pair_buf ? reinterpret_cast<uint2 *>(reinterpret_cast<uint32_t *>(s->pair_buf) +
+                                                   hd::kLeanWords * static_cast<size_t>(s->tp.pair_cap))
+                       : nullptr;
     return p;
 }
 
@@ -295,10 +299,15 @@ void make_tile_plan(hd_scan *s)
     tp.nz = nz;
     const int64_t plane = int64_t(nx) * ny;
     if (plane <= budget) {
+        // slabs of one z-slice by default: walks inside them never cross z, so
+        // nearly all of them have the closed-form (lean) runs; deeper slabs
+        // (slab_depth > 1) cut the pairs per history but send the walks that
+        // cross z inside a slab to the general walk in global memory
         tp.tx = nx;
         tp.ty = ny;
         tp.tz = static_cast<int>(budget / plane);
-        if (s->tuning.slab_depth > 0 && s->tuning.slab_depth < tp.tz) tp.tz = s->tuning.slab_depth;
+        const int depth = s->tuning.slab_depth > 0 ? s->tuning.slab_depth : 1;
+        if (depth < tp.tz) tp.tz = depth;
         if (tp.tz > nz) tp.tz = nz;
         const int ntz = (nz + tp.tz - 1) / tp.tz;
         tp.tz = (nz + ntz - 1) / ntz;
@@ -384,8 +393,10 @@ hd_status stage_prepare(hd_scan *s, const hd::Inputs &in, int64_t n, cudaStream_
 // Records outside the tiled path, walked with global-memory updates.
 hd_status stage_global(hd_scan *s, int64_t n, cudaStream_t st)
 {
+    hd::Pairs pairs = pairs_of(s);
+    if (s->tp.ntiles <= 0 || s->trace_grid <= 0) pairs.fb = nullptr;  // no tiled pass
     HD_CUDA(hd::launch_trace_global(records_of(s, n), s->ctrl, n, s->gq, s->N, s->M, s->carve,
-                                    0, s->sm_count, st));
+                                    0, s->tp, pairs, s->sm_count, st));
     s->launches += 1;
     return HD_OK;
 }
@@ -734,6 +745,7 @@ hd_status hd_scan_get_stats(hd_scan *scan, hd_stats *out, void *stream)
     out->n_reject = static_cast<int64_t>(c.n_reject);
     out->steps_miss = static_cast<int64_t>(c.steps_miss);
     out->steps_hit = static_cast<int64_t>(c.steps_hit);
+    out->pairs_general = static_cast<int64_t>(c.pairs_general);
     return HD_OK;
 }
 
@@ -790,7 +802,8 @@ hd_status hd_scan_get_hull_indices(hd_scan *scan, int32_t method, int32_t *dst,
 hd_status hd_scan_set_tuning(hd_scan *scan, const hd_tuning *t)
 {
     if (!scan || !t) return HD_ERR_ARG;
-    if (t->threads != 256 && t->threads != 512 && t->threads != 768) return HD_ERR_ARG;
+    if (t->threads != 256 && t->threads != 512 && t->threads != 768 && t->threads != 1024)
+        return HD_ERR_ARG;
     if (t->refill < 1 || t->refill > 32 || t->job_size < 256 || t->job_size > 32767 ||
         t->slab_depth < 0)
         return HD_ERR_ARG;

@@ -704,30 +704,39 @@ HD_HD bool run_begin(RunWalk &rw, const int32_t gi[3], const int32_t go[3], int 
 // comes after J_k = q_0 + 1 + (k - 1) Qu_0 + floor((rh_0 + (k - 1) Ru_0) / ad_0)
 // of them (so J_1 = q_0 + 1, and J_{k+1} = J_k + Qu_0 + carry, Bresenham
 // style); z crosses after j_z = q_1 + 1; the major axis runs out after km.
-// Crossing k of minor 0 happens iff k <= kc_0, k <= K_z (the number of
-// minor-0 crossings before z's, from the sign of e12 + k ad_1 2^16) and
-// J_k <= km.  Run k (k = 0, 1, ...) covers major counts J_k .. J_{k+1}
-// (J_0 = 0) in row row_0 + k (the minor-0 row stride), the last run ending
-// at min(J_{K+1}, km, j_z) instead.  These are exactly the runs run_next
-// produces.  A lean walk keeps its state in RunWalk's fields:
-//   q[0] = J_{k+1}, rh[0] = (rh_0 + k Ru_0) mod ad_0, ad[0], Qu[0] (capped at
-//   kLeanQuCap: one step beyond the box suffices), Ru[0], km, kc[0] = crossings
-//   left (K - k), kc[1] = K, q[1] = j_z, im = major index at the start,
-//   run_start = J_k, row, flags bit 12.
-constexpr int kLeanFlag = 1 << 12;
-constexpr int kLeanQuCap = 8192;  // > any box extent (4096)
+// Crossing k of minor 0 happens iff k <= K = min(kc_0, K_z), K_z being the
+// number of minor-0 crossings before z's (from the sign of
+// e12 + k ad_1 2^16), and J_k <= km.  Run k (k = 0, 1, ...) covers major
+// counts J_k .. J_{k+1} (J_0 = 0) in row row_0 + k s_0 (s_0 the signed
+// minor-0 row stride), the last ending at min(J_{k+1}, km, j_z) instead.
+// These are exactly the runs run_next produces.  With kmz = min(km, j_z),
+// run k is the last iff k = K or J_{k+1} > kmz (a crossing k + 1 <= K_z comes
+// no later than z's), and it ends at min(J_{k+1}, kmz).
+struct LeanWalk {
+    unsigned ad, Ru, rem;  // |D_0|, |D_m| mod |D_0|, (rh_0 + k Ru_0) mod ad_0
+    int jn;                // J_{k+1} (capped: any value above kmz acts alike)
+    int Qu;                // floor(|D_m| / |D_0|), capped at kLeanQuCap
+    int kmz;               // min(km, j_z)
+    int kleft, K;          // crossings of minor 0 left, and in all
+    int s;                 // J_k: where the current run starts
+    int im0;               // major index of the first voxel
+    int row;               // row of the current run (major axis' layout)
+    int fl;                // bit 0 major +, bit 1 minor 0 +, bit 2 major is y, bit 3 empty
+};
+constexpr int kLeanWords = 8;   // packed size (32 bytes)
+constexpr int kLeanQuCap = 8192;  // > any box extent (4096): one step beyond the box suffices
+constexpr int kLeanJCap = 16383;
 
-// Turn a freshly begun walk into its lean form when it is lean; returns
-// whether it did.
-HD_HD bool run_make_lean(RunWalk &w)
+// The lean form of a freshly begun walk, when it has one.
+HD_HD bool lean_of(const RunWalk &w, LeanWalk &L)
 {
     const int fl = w.flags;
     if (fl & ((7 << 6) | (1 << 9))) return false;  // a tie pending, or empty
     const bool act0 = (fl >> 3) & 1, act1 = (fl >> 4) & 1;
-    if (w.kc[1] != 0) return false;             // z crosses inside the box
+    if (w.kc[1] != 0) return false;                            // z crosses inside the box
     if (!((fl >> 10) & 1) || !((fl >> 11) & 1)) return false;  // a tie with the major axis
     if (w.q[0] < -1 || w.q[1] < -1) return false;
-    int kz;  // minor-0 crossings before z's (crossings of minor 0 past kc_0 never happen)
+    int kz;  // minor-0 crossings before z's
     if (!act0) {
         kz = 0;
     } else if (!act1) {
@@ -742,47 +751,84 @@ HD_HD bool run_make_lean(RunWalk &w)
             kz = n < w.kc[0] ? static_cast<int>(n) : w.kc[0];
         }
     }
-    const int K = act0 ? (kz < w.kc[0] ? kz : w.kc[0]) : 0;
+    L.K = act0 ? (kz < w.kc[0] ? kz : w.kc[0]) : 0;
+    L.kleft = L.K;
     const int jz = act1 ? w.q[1] + 1 : kQBig;
+    L.kmz = w.km < jz ? w.km : jz;
     const int j1 = act0 ? w.q[0] + 1 : kQBig;
-    w.q[0] = j1;
-    w.q[1] = jz;
-    if (w.Qu[0] > kLeanQuCap) w.Qu[0] = kLeanQuCap;
-    w.kc[0] = K;
-    w.kc[1] = K;
-    w.run_start = 0;
-    w.e12 = 0;
-    w.flags = (fl & (1 | 2 | (1 << 3) | (1 << 5))) | kLeanFlag;
+    L.jn = j1 < kLeanJCap ? j1 : kLeanJCap;
+    L.Qu = w.Qu[0] < kLeanQuCap ? w.Qu[0] : kLeanQuCap;
+    L.ad = w.ad[0];
+    L.Ru = w.Ru[0];
+    L.rem = w.rh[0];
+    L.s = 0;
+    L.im0 = w.im;
+    L.row = w.row;
+    L.fl = (fl & 3) | (((fl >> 5) & 1) << 2);
     return true;
 }
 
-// Next run of a lean walk (the same contract as run_next); when it returns
-// the last run it also adds the walk's voxel count to `steps`.
-HD_HD bool lean_next(RunWalk &w, int &row, int &lo, int &hi, unsigned &steps)
+HD_HD void lean_pack(const LeanWalk &L, uint32_t o[kLeanWords])
 {
-    if (w.flags & (1 << 9)) return false;
-    const int jn = w.q[0];
-    const bool last = w.kc[0] == 0 || jn > w.km;
-    int e = jn < w.km ? jn : w.km;
-    e = e < w.q[1] ? e : w.q[1];
-    const int sg = (w.flags & 1) ? 1 : -1;
-    const int a = w.im + sg * w.run_start, b = w.im + sg * e;
+    o[0] = L.ad;
+    o[1] = L.Ru;
+    o[2] = L.rem;
+    o[3] = static_cast<uint32_t>(L.jn) | (static_cast<uint32_t>(L.Qu) << 16);
+    o[4] = static_cast<uint32_t>(L.kmz) | (static_cast<uint32_t>(L.K) << 16);
+    o[5] = static_cast<uint32_t>(L.im0) | (static_cast<uint32_t>(L.fl) << 16);
+    o[6] = static_cast<uint32_t>(L.row);
+    o[7] = 0;
+}
+
+// A packed walk with no voxel.
+HD_HD void lean_pack_empty(uint32_t o[kLeanWords])
+{
+    for (int i = 0; i < kLeanWords; ++i) o[i] = 0;
+    o[5] = 8u << 16;
+}
+
+HD_HD void lean_unpack(const uint32_t o[kLeanWords], LeanWalk &L)
+{
+    L.ad = o[0];
+    L.Ru = o[1];
+    L.rem = o[2];
+    L.jn = static_cast<int>(o[3] & 0xffffu);
+    L.Qu = static_cast<int>(o[3] >> 16);
+    L.kmz = static_cast<int>(o[4] & 0xffffu);
+    L.K = static_cast<int>(o[4] >> 16);
+    L.kleft = L.K;
+    L.im0 = static_cast<int>(o[5] & 0xffffu);
+    L.fl = static_cast<int>(o[5] >> 16);
+    L.row = static_cast<int>(o[6]);
+    L.s = 0;
+}
+
+HD_HD bool lean_empty(const LeanWalk &L) { return (L.fl >> 3) & 1; }
+
+// The current run of a non-empty lean walk: row, and the inclusive range
+// lo..hi of major indices.  Returns whether more runs follow; with the last
+// run it adds the walk's voxel count (e + K + 1: the major cells covered
+// plus one per row change) to `steps`.
+HD_HD bool lean_step(LeanWalk &L, int &row, int &lo, int &hi, unsigned &steps)
+{
+    const int jn = L.jn;
+    const int e = jn < L.kmz ? jn : L.kmz;
+    const int a = (L.fl & 1) ? L.im0 + L.s : L.im0 - L.s;
+    const int b = (L.fl & 1) ? L.im0 + e : L.im0 - e;
     lo = a < b ? a : b;
     hi = a < b ? b : a;
-    row = w.row;
-    if (last) {
-        // runs k = 0..K cover e + 1 major cells plus one per row change
-        steps += static_cast<unsigned>(e + (w.kc[1] - w.kc[0]) + 1);
-        w.flags |= 1 << 9;
-        return true;
+    row = L.row;
+    if (L.kleft == 0 || jn > L.kmz) {
+        steps += static_cast<unsigned>(e + (L.K - L.kleft) + 1);
+        return false;
     }
-    w.run_start = jn;
-    const unsigned rem = w.rh[0] + w.Ru[0];
-    const bool carry = rem >= w.ad[0];
-    w.rh[0] = carry ? rem - w.ad[0] : rem;
-    w.q[0] = jn + w.Qu[0] + (carry ? 1 : 0);
-    --w.kc[0];
-    w.row += w.rstride[0];
+    L.s = jn;
+    const unsigned rem = L.rem + L.Ru;
+    const bool carry = rem >= L.ad;
+    L.rem = carry ? rem - L.ad : rem;
+    L.jn = jn + L.Qu + (carry ? 1 : 0);
+    --L.kleft;
+    L.row += (L.fl & 2) ? 1 : -1;
     return true;
 }
 
@@ -838,7 +884,7 @@ HD_HD void run_unpack(const uint32_t o[kPackedWords], int nx, int ny, RunWalk &w
     w.kc[1] = static_cast<int>(o[14] >> 16);
     w.flags = static_cast<int>(o[15]);
     const bool ymaj = (w.flags >> 5) & 1;
-    w.run_start = (w.flags & kLeanFlag) ? 0 : w.im;
+    w.run_start = w.im;
     w.rstride[0] = (w.flags & 2) ? 1 : -1;
     w.rstride[1] = (w.flags & 4) ? (ymaj ? nx : ny) : -(ymaj ? nx : ny);
     w.nmaj = ymaj ? ny : nx;

@@ -35,12 +35,14 @@ struct GeomQ {
 struct Ctrl {
     unsigned long long n_in, n_miss, n_hit, n_none, n_reject;
     unsigned long long steps_miss, steps_hit;
+    unsigned long long pairs_general;  // pairs sent to the fallback list (cumulative)
     unsigned int rec_miss;    // records appended from the front of the list
     unsigned int rec_hit;     // records appended from the back of the list
     unsigned int pairs_used;  // (record, tile) pairs admitted to the tiled path
     int njobs;                // jobs of the tiled traversal
     int job_next;             // next job to hand out
     unsigned int n_fallback;  // records traversed by the global-memory path
+    unsigned int n_pair_fallback;  // entries of the pair fallback list
 };
 
 // Compacted traversal records: grid Q16 entry and exit points, int32 each
@@ -63,16 +65,19 @@ struct TilePlan {
     long long pair_cap;
     int tile_words;     // 32-bit words of shared memory per block
     int refill;         // idle lanes that trigger a warp refill
-    int threads;        // threads per block of the traversal (256, 512, 768)
+    int threads;        // threads per block of the traversal (256, 512, 768, 1024)
     unsigned mtx, mty, mtz;  // floor(2^32 / t) + 1 (0 when t = 1): division by a tile size
 };
 
-// (record, tile) pairs sorted by tile: the packed run-walk state of the
-// record clipped to the tile, 64 bytes per pair (four uint4), so a pair is
-// written and read as whole 32-byte sectors (class and tile come from the
-// job).
+// (record, tile) pairs sorted by tile: the packed lean walk of the record
+// clipped to the tile, 32 bytes per pair (two uint4: one 32-byte sector;
+// class and tile come from the job).  A pair whose walk has no lean form
+// (a tie, a pending start, or a z crossing inside the tile) leaves an empty
+// walk in its place and goes to the fallback list, which the global-memory
+// traversal walks with the general run walk.
 struct Pairs {
-    uint4 *v;  // 4 per pair
+    uint4 *v;   // 2 per pair
+    uint2 *fb;  // fallback list: (record slot, 2 tile + class), pair_cap entries
 };
 
 struct TileJob {
@@ -108,21 +113,23 @@ cudaError_t launch_ingest(const Inputs &in, int64_t n, const GeomQ &g, const Cor
 cudaError_t launch_plan(const TilePlan &tp, const uint32_t *tile_count, uint32_t *tile_cursor,
                         TileJob *jobs, Ctrl *ctrl, int sm_count, cudaStream_t s);
 
-cudaError_t launch_scatter(const TilePlan &tp, const Records &rec, const Ctrl *ctrl,
+cudaError_t launch_scatter(const TilePlan &tp, const Records &rec, Ctrl *ctrl,
                            uint32_t *tile_cursor, const Pairs &pairs, int64_t n, int sm_count,
                            cudaStream_t s);
 
 // Persistent traversal over the jobs of nscans scans (descs on the device),
 // handed out through *job_counter (zero before the launch).  smem_words is
-// the largest tile of the scans; threads is 256, 512 or 768.
+// the largest tile of the scans; threads is 256, 512, 768 or 1024.
 cudaError_t launch_trace_tiles(const ScanDesc *descs, int nscans, int *job_counter,
                                int smem_words, int threads, int grid, cudaStream_t s);
 
 // Global-memory traversal of the records whose status is 2 (or of every
-// record when all_records is set).
+// record when all_records is set), then of the pair fallback list when
+// pairs.fb is set (each entry: the record clipped to its tile of tp).
 cudaError_t launch_trace_global(const Records &rec, Ctrl *ctrl, int64_t upper, const GeomQ &g,
                                 uint32_t *N, uint32_t *M, uint32_t *carve, int all_records,
-                                int sm_count, cudaStream_t s);
+                                const TilePlan &tp, const Pairs &pairs, int sm_count,
+                                cudaStream_t s);
 
 cudaError_t launch_classify(const float *wepl, int64_t n, float tau_l, float tau_h,
                             uint8_t *cls, cudaStream_t s);

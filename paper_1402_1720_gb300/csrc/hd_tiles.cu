@@ -8,7 +8,10 @@
 //   scatter  counting sort of the pairs by tile (block-level reservation)
 //   trace    persistent blocks take jobs; warps refill idle lanes from the
 //            job's pair range, so lanes do not wait for the longest path
+#include <cooperative_groups.h>
 #include "hd_geom.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace hd {
 
@@ -105,7 +108,7 @@ __global__ void __launch_bounds__(1024) plan_kernel(TilePlan tp, const uint32_t 
 // of record slots, histograms its pairs, reserves one range per tile with a
 // single global atomic, then writes its pairs.
 __global__ void __launch_bounds__(kScatterThreads) scatter_kernel(TilePlan tp, Records rec,
-                                                                  const Ctrl *ctrl,
+                                                                  Ctrl *ctrl,
                                                                   uint32_t *tile_cursor,
                                                                   Pairs pairs, int per_thread)
 {
@@ -165,17 +168,33 @@ __global__ void __launch_bounds__(kScatterThreads) scatter_kernel(TilePlan tp, R
                     const int32_t gi[3] = {r[0] - (x0 << 16), r[1] - (y0 << 16), r[2] - (z0 << 16)};
                     const int32_t go[3] = {r[3] - (x0 << 16), r[4] - (y0 << 16), r[5] - (z0 << 16)};
                     RunWalk w;
-                    uint32_t o[kPackedWords];
-                    if (run_begin(w, gi, go, dx, dy, dz)) {
-                        run_make_lean(w);  // closed-form runs when the walk allows
-                        run_pack(w, o);
+                    LeanWalk L;
+                    uint32_t o[kLeanWords];
+                    bool fallback = false;
+                    if (!run_begin(w, gi, go, dx, dy, dz)) {
+                        lean_pack_empty(o);
+                    } else if (lean_of(w, L)) {
+                        lean_pack(L, o);
                     } else {
-                        run_pack_empty(o);
+                        lean_pack_empty(o);  // walked from the fallback list instead
+                        fallback = true;
                     }
-#pragma unroll
-                    for (int a = 0; a < 4; ++a)
-                        pairs.v[4 * static_cast<size_t>(pos) + a] =
-                            make_uint4(o[4 * a], o[4 * a + 1], o[4 * a + 2], o[4 * a + 3]);
+                    pairs.v[2 * static_cast<size_t>(pos)] = make_uint4(o[0], o[1], o[2], o[3]);
+                    pairs.v[2 * static_cast<size_t>(pos) + 1] = make_uint4(o[4], o[5], o[6], o[7]);
+                    if (fallback) {
+                        // append to the fallback list, one counter update per
+                        // group of lanes arriving together
+                        cg::coalesced_group grp = cg::coalesced_threads();
+                        unsigned base = 0;
+                        if (grp.thread_rank() == 0) {
+                            base = atomicAdd(&ctrl->n_pair_fallback, grp.size());
+                            atomicAdd(&ctrl->pairs_general, static_cast<unsigned long long>(grp.size()));
+                        }
+                        base = grp.shfl(base, 0);
+                        pairs.fb[base + grp.thread_rank()] = make_uint2(
+                            static_cast<unsigned>(slot),
+                            2u * static_cast<unsigned>(t - cls * tp.ntiles) + static_cast<unsigned>(cls));
+                    }
                 }
     }
 }
@@ -193,16 +212,10 @@ __global__ void __launch_bounds__(kScatterThreads) scatter_kernel(TilePlan tp, R
 // In carve mode (SC without MSC) the arrays are bit masks instead and a run
 // clears its bits.
 
-__device__ __forceinline__ void load_packed(const Pairs &pairs, int idx, uint32_t o[16])
+__device__ __forceinline__ void load_lean(const Pairs &pairs, int idx, uint4 &a, uint4 &b)
 {
-#pragma unroll
-    for (int a = 0; a < 4; ++a) {
-        const uint4 v = __ldg(&pairs.v[4 * static_cast<size_t>(idx) + a]);
-        o[4 * a] = v.x;
-        o[4 * a + 1] = v.y;
-        o[4 * a + 2] = v.z;
-        o[4 * a + 3] = v.w;
-    }
+    a = __ldg(&pairs.v[2 * static_cast<size_t>(idx)]);
+    b = __ldg(&pairs.v[2 * static_cast<size_t>(idx) + 1]);
 }
 
 __device__ __forceinline__ void diff_add(uint32_t *arr, int e, int sgn)
@@ -307,17 +320,17 @@ __global__ void __launch_bounds__(kThreads, 1) trace_tiles_kernel(
         __syncthreads();
 
         const int total = job.end - job.start;
-        // Each lane walks one pair and holds the packed state of its next one
-        // (loaded a refill ahead, so starting a walk never waits on memory).
-        // A refill happens once enough lanes are idle; then every idle lane
-        // with a prefetched pair starts it and fetches another.
-        RunWalk w;
-        w.flags = 1 << 9;
-        w.nmaj = 0;
+        // Each lane walks one pair and holds the packed lean walk of its next
+        // one (loaded a refill ahead, so starting a walk never waits on
+        // memory).  A refill happens once enough lanes are idle; then every
+        // idle lane with a prefetched pair starts it and fetches another.
+        LeanWalk L;
+        L.fl = 8;
         bool active = false;
+        int nmaj = 0;
         unsigned steps = 0;
         uint32_t *arr = arrX;
-        uint32_t ng[kPackedWords];
+        uint4 na = make_uint4(0, 0, 0, 0), nb = na;
         int nidx = -1;
         {
             unsigned base = 0;
@@ -326,7 +339,7 @@ __global__ void __launch_bounds__(kThreads, 1) trace_tiles_kernel(
             const unsigned r = base + lane;
             if (r < static_cast<unsigned>(total)) {
                 nidx = job.start + static_cast<int>(r);
-                load_packed(pairs, nidx, ng);
+                load_lean(pairs, nidx, na, nb);
             }
         }
         for (;;) {
@@ -335,9 +348,12 @@ __global__ void __launch_bounds__(kThreads, 1) trace_tiles_kernel(
             if (want == 0 && busy == 0) break;
             if (want != 0 && (__popc(want) >= static_cast<unsigned>(tp.refill) || busy == 0)) {
                 if (!active && nidx >= 0) {
-                    run_unpack(ng, dx, dy, w);
-                    active = !((w.flags >> 9) & 1);
-                    arr = ((w.flags >> 5) & 1) ? arrY : arrX;
+                    const uint32_t o[kLeanWords] = {na.x, na.y, na.z, na.w, nb.x, nb.y, nb.z, nb.w};
+                    lean_unpack(o, L);
+                    active = !lean_empty(L);
+                    const bool ymaj = (L.fl >> 2) & 1;
+                    arr = ymaj ? arrY : arrX;
+                    nmaj = ymaj ? dy : dx;
                     nidx = -1;
                 }
                 unsigned base = 0;
@@ -348,30 +364,20 @@ __global__ void __launch_bounds__(kThreads, 1) trace_tiles_kernel(
                     const unsigned r = base + __popc(want & ((1u << lane) - 1u));
                     if (r < static_cast<unsigned>(total)) {
                         nidx = job.start + static_cast<int>(r);
-                        load_packed(pairs, nidx, ng);
+                        load_lean(pairs, nidx, na, nb);
                     }
                 }
                 continue;
             }
             if (active) {
                 int row, lo, hi;
-                bool got;
-                if (w.flags & kLeanFlag) {
-                    got = lean_next(w, row, lo, hi, steps);
+                active = lean_step(L, row, lo, hi, steps);
+                const int base = row * nmaj;
+                if (!carve_mode) {
+                    diff_add(arr, base + lo, 1);
+                    if (hi + 1 < nmaj) diff_add(arr, base + hi + 1, -1);
                 } else {
-                    got = run_next(w, row, lo, hi);
-                    if (got) steps += static_cast<unsigned>(hi - lo + 1);
-                }
-                if (got) {
-                    const int base = row * w.nmaj;
-                    if (!carve_mode) {
-                        diff_add(arr, base + lo, 1);
-                        if (hi + 1 < w.nmaj) diff_add(arr, base + hi + 1, -1);
-                    } else {
-                        bits_clear(arr, base + lo, base + hi);
-                    }
-                } else {
-                    active = false;
+                    bits_clear(arr, base + lo, base + hi);
                 }
             }
         }
@@ -437,7 +443,7 @@ cudaError_t launch_plan(const TilePlan &tp, const uint32_t *tile_count, uint32_t
     return cudaGetLastError();
 }
 
-cudaError_t launch_scatter(const TilePlan &tp, const Records &rec, const Ctrl *ctrl,
+cudaError_t launch_scatter(const TilePlan &tp, const Records &rec, Ctrl *ctrl,
                            uint32_t *tile_cursor, const Pairs &pairs, int64_t n, int sm_count,
                            cudaStream_t s)
 {
@@ -483,6 +489,7 @@ int trace_tiles_occupancy(int smem_words, int threads)
     case 256: return occupancy_of<256>(smem_words);
     case 512: return occupancy_of<512>(smem_words);
     case 768: return occupancy_of<768>(smem_words);
+    case 1024: return occupancy_of<1024>(smem_words);
     default: return 0;
     }
 }
@@ -502,6 +509,9 @@ cudaError_t launch_trace_tiles(const ScanDesc *descs, int nscans, int *job_count
         break;
     case 768:
         trace_tiles_kernel<768><<<grid, 768, smem, s>>>(descs, nscans, job_counter);
+        break;
+    case 1024:
+        trace_tiles_kernel<1024><<<grid, 1024, smem, s>>>(descs, nscans, job_counter);
         break;
     default: return cudaErrorInvalidValue;
     }

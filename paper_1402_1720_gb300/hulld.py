@@ -52,7 +52,8 @@ class hd_params(ctypes.Structure):
 class hd_stats(ctypes.Structure):
     _fields_ = [("n_in", ctypes.c_int64), ("n_miss", ctypes.c_int64), ("n_hit", ctypes.c_int64),
                 ("n_none", ctypes.c_int64), ("n_reject", ctypes.c_int64),
-                ("steps_miss", ctypes.c_int64), ("steps_hit", ctypes.c_int64)]
+                ("steps_miss", ctypes.c_int64), ("steps_hit", ctypes.c_int64),
+                ("pairs_general", ctypes.c_int64)]
 
     def as_dict(self):
         return {k: int(getattr(self, k)) for k, _ in self._fields_}

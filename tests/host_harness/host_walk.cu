@@ -109,31 +109,39 @@ extern "C" long long hx_check_tile_division(void)
 extern "C" int hx_runs_lean(const int32_t *gi, const int32_t *go, int nx, int ny, int nz,
                             int32_t *out, int cap, int *lean, unsigned *steps)
 {
-    hd::RunWalk w0, w;
-    uint32_t o[hd::kPackedWords];
+    hd::RunWalk w;
     *lean = 0;
     *steps = 0;
-    if (hd::run_begin(w0, gi, go, nx, ny, nz)) {
-        *lean = hd::run_make_lean(w0) ? 1 : 0;
-        hd::run_pack(w0, o);
-    } else {
-        hd::run_pack_empty(o);
-    }
-    hd::run_unpack(o, nx, ny, w);
     int n = 0, runs = 0;
-    const bool ymaj = (w.flags >> 5) & 1;
-    int row, lo, hi;
-    for (;;) {
-        const bool got = (w.flags & hd::kLeanFlag) ? hd::lean_next(w, row, lo, hi, *steps)
-                                                   : hd::run_next(w, row, lo, hi);
-        if (!got) break;
-        if (lo < 0 || hi >= w.nmaj || lo > hi) return -1000000;
-        if (++runs > 100000) return -2000000;
+    auto emit = [&](bool ymaj, int nmaj, int row, int lo, int hi) {
+        if (lo < 0 || hi >= nmaj || lo > hi) return false;
         for (int m = lo; m <= hi; ++m) {
             int v = !ymaj ? m + nx * row : (row % nx) + nx * (m + ny * (row / nx));
             if (n < cap) out[n] = v;
             ++n;
         }
+        return ++runs <= 100000;
+    };
+    if (!hd::run_begin(w, gi, go, nx, ny, nz)) return 0;
+    hd::LeanWalk L0, L;
+    if (hd::lean_of(w, L0)) {
+        *lean = 1;
+        uint32_t o[hd::kLeanWords];
+        hd::lean_pack(L0, o);
+        hd::lean_unpack(o, L);
+        if (hd::lean_empty(L)) return -3000000;
+        const bool ymaj = (L.fl >> 2) & 1;
+        int row, lo, hi;
+        bool more;
+        do {
+            more = hd::lean_step(L, row, lo, hi, *steps);
+            if (!emit(ymaj, ymaj ? ny : nx, row, lo, hi)) return -1000000;
+        } while (more);
+        return n;
     }
+    const bool ymaj = (w.flags >> 5) & 1;
+    int row, lo, hi;
+    while (hd::run_next(w, row, lo, hi))
+        if (!emit(ymaj, w.nmaj, row, lo, hi)) return -1000000;
     return n;
 }

@@ -78,6 +78,9 @@ def test_config1_full_parity(hd, oracle_mod):
     got = _run_gpu(hd, w.geometry, w.histories)
     _assert_same(got, ref, ALL)
     _assert_stats(got, ref)
+    # generic float inputs: almost every walk has the closed-form lean runs
+    st = got["stats"]
+    assert st["pairs_general"] < 1e-3 * (st["n_miss"] + st["n_hit"])
     # SC: H1 from the carve (Alg. 1) equals {N = 0}
     assert np.array_equal(got["H1"], ref["H1_carved"])
 
@@ -170,6 +173,8 @@ def test_lattice_aligned_ties(hd, oracle_mod, g):
     got = _run_gpu(hd, g, h)
     _assert_same(got, ref, ALL)
     _assert_stats(got, ref)
+    # ties send walks to the general run walk (the fallback list)
+    assert got["stats"]["pairs_general"] > 0
 
 
 @pytest.mark.parametrize("variant", ["sc_only", "msc_only", "sm_only", "sm_gt", "sm_global",
@@ -435,6 +440,7 @@ def test_config3_streamed_sampled(hd, oracle_mod):
     {"threads": 256, "refill": 4, "job_size": 4096, "slab_depth": 1},
     {"threads": 768, "refill": 24, "job_size": 32767, "slab_depth": 2},
     {"threads": 512, "refill": 1, "job_size": 256, "slab_depth": 0},
+    {"threads": 1024, "refill": 8, "job_size": 16384, "slab_depth": 4},
 ])
 def test_tuning_settings_do_not_change_results(hd, oracle_mod, setting):
     """Launch parameters change speed only: every setting gives the oracle's
