@@ -103,7 +103,12 @@ HD_HD float float_of(long long a)
 // no 64-bit division is needed.
 HD_HD long long floordiv_small(long long a, long long b)
 {
+    // an approximate float quotient: the integer steps below make it exact
+#ifdef __CUDA_ARCH__
+    long long q = static_cast<long long>(static_cast<int>(floorf(__fdividef(float_of(a), float_of(b)))));
+#else
     long long q = static_cast<long long>(static_cast<int>(floorf(float_of(a) / float_of(b))));
+#endif
     long long r = a - q * b;
     while (r < 0) {
         --q;
@@ -746,9 +751,16 @@ HD_HD bool lean_of(const RunWalk &w, LeanWalk &L)
         if (w.e12 > 0) {
             kz = 0;
         } else {
+            // ceil(-e12 / step) = floor((-e12 - 1) / step) + 1 (e12 < 0), needed
+            // only up to kc_0 <= 4096: a float estimate settles larger ones
             const long long step = static_cast<long long>(w.ad[1]) << 16;
-            const long long n = (-w.e12 + step - 1) / step;  // ceil(-e12 / step), e12 < 0
-            kz = n < w.kc[0] ? static_cast<int>(n) : w.kc[0];
+            const long long num = -w.e12 - 1;
+            if (float_of(num) >= (static_cast<float>(w.kc[0]) + 2.0f) * float_of(step)) {
+                kz = w.kc[0];
+            } else {
+                const long long n = floordiv_small(num, step) + 1;
+                kz = n < w.kc[0] ? static_cast<int>(n) : w.kc[0];
+            }
         }
     }
     L.K = act0 ? (kz < w.kc[0] ? kz : w.kc[0]) : 0;

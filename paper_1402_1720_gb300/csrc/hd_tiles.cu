@@ -107,7 +107,7 @@ __global__ void __launch_bounds__(1024) plan_kernel(TilePlan tp, const uint32_t 
 // Counting sort of (record, tile) pairs by tile.  Each block takes a range
 // of record slots, histograms its pairs, reserves one range per tile with a
 // single global atomic, then writes its pairs.
-__global__ void __launch_bounds__(kScatterThreads) scatter_kernel(TilePlan tp, Records rec,
+__global__ void __launch_bounds__(kScatterThreads, 3) scatter_kernel(TilePlan tp, Records rec,
                                                                   Ctrl *ctrl,
                                                                   uint32_t *tile_cursor,
                                                                   Pairs pairs, int per_thread)
@@ -147,55 +147,85 @@ __global__ void __launch_bounds__(kScatterThreads) scatter_kernel(TilePlan tp, R
         s_hist[t] = 0;
     }
     __syncthreads();
+    // The warp's (record, tile) pairs are dealt out one per lane, so the
+    // set-up below runs on all lanes whatever each record's tile count.
+    const int lane = static_cast<int>(threadIdx.x & 31u);
     for (int k = 0; k < per_thread; ++k) {
         const int64_t slot = slot0 + k * kScatterThreads + threadIdx.x;
-        int cls;
-        if (slot >= rec.cap || !valid(slot, cls)) continue;
-        int32_t r[6];
+        int cls = 0;
+        int32_t r[6] = {0, 0, 0, 0, 0, 0};
+        int lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
+        int cnt = 0;
+        if (slot < rec.cap && valid(slot, cls)) {
 #pragma unroll
-        for (int a = 0; a < 6; ++a) r[a] = rec.g[a][slot];
-        int lo[3], hi[3];
-        if (tile_range(tp, r, lo, hi) == 0) continue;
-        for (int z = lo[2]; z <= hi[2]; ++z)
-            for (int y = lo[1]; y <= hi[1]; ++y)
-                for (int x = lo[0]; x <= hi[0]; ++x) {
-                    const int t = cls * tp.ntiles + x + tp.ntx * (y + tp.nty * z);
-                    const uint32_t pos = s_base[t] + atomicAdd(&s_hist[t], 1u);
-                    // set up the walk of this record clipped to this tile
-                    const int x0 = x * tp.tx, y0 = y * tp.ty, z0 = z * tp.tz;
-                    const int dx = min(tp.tx, tp.nx - x0), dy = min(tp.ty, tp.ny - y0),
-                              dz = min(tp.tz, tp.nz - z0);
-                    const int32_t gi[3] = {r[0] - (x0 << 16), r[1] - (y0 << 16), r[2] - (z0 << 16)};
-                    const int32_t go[3] = {r[3] - (x0 << 16), r[4] - (y0 << 16), r[5] - (z0 << 16)};
-                    RunWalk w;
-                    LeanWalk L;
-                    uint32_t o[kLeanWords];
-                    bool fallback = false;
-                    if (!run_begin(w, gi, go, dx, dy, dz)) {
-                        lean_pack_empty(o);
-                    } else if (lean_of(w, L)) {
-                        lean_pack(L, o);
-                    } else {
-                        lean_pack_empty(o);  // walked from the fallback list instead
-                        fallback = true;
-                    }
-                    pairs.v[2 * static_cast<size_t>(pos)] = make_uint4(o[0], o[1], o[2], o[3]);
-                    pairs.v[2 * static_cast<size_t>(pos) + 1] = make_uint4(o[4], o[5], o[6], o[7]);
-                    if (fallback) {
-                        // append to the fallback list, one counter update per
-                        // group of lanes arriving together
-                        cg::coalesced_group grp = cg::coalesced_threads();
-                        unsigned base = 0;
-                        if (grp.thread_rank() == 0) {
-                            base = atomicAdd(&ctrl->n_pair_fallback, grp.size());
-                            atomicAdd(&ctrl->pairs_general, static_cast<unsigned long long>(grp.size()));
-                        }
-                        base = grp.shfl(base, 0);
-                        pairs.fb[base + grp.thread_rank()] = make_uint2(
-                            static_cast<unsigned>(slot),
-                            2u * static_cast<unsigned>(t - cls * tp.ntiles) + static_cast<unsigned>(cls));
-                    }
+            for (int a = 0; a < 6; ++a) r[a] = rec.g[a][slot];
+            cnt = tile_range(tp, r, lo, hi);
+        }
+        const int incl = static_cast<int>(warp_incl_scan_u(static_cast<unsigned>(cnt)));
+        const int total = __shfl_sync(kFull, incl, 31);
+        const int ex = hi[0] - lo[0] + 1, ey = hi[1] - lo[1] + 1;
+        for (int first = 0; first < total; first += 32) {
+            const int p = first + lane;
+            const int pc = p < total ? p : total - 1;
+            // owner: the first lane whose inclusive count exceeds pc
+            int own = 0;
+#pragma unroll
+            for (int b = 16; b >= 1; b >>= 1)
+                if (__shfl_sync(kFull, incl, own + b - 1) <= pc) own += b;
+            const int j = pc - (__shfl_sync(kFull, incl, own) - __shfl_sync(kFull, cnt, own));
+            int32_t q[6];
+#pragma unroll
+            for (int a = 0; a < 6; ++a) q[a] = __shfl_sync(kFull, r[a], own);
+            const int lx = __shfl_sync(kFull, lo[0], own), ly = __shfl_sync(kFull, lo[1], own);
+            const int lz = __shfl_sync(kFull, lo[2], own);
+            const int oex = __shfl_sync(kFull, ex, own), oey = __shfl_sync(kFull, ey, own);
+            const int ocls = __shfl_sync(kFull, cls, own);
+            if (p >= total) continue;
+            const int64_t oslot = slot - lane + own;
+            // the j-th tile of the owner's box, x fastest
+            int x = lx, y = ly, z = lz + j;
+            if (oex != 1 || oey != 1) {
+                x = lx + j % oex;
+                y = ly + (j / oex) % oey;
+                z = lz + j / (oex * oey);
+            }
+            const int t = ocls * tp.ntiles + x + tp.ntx * (y + tp.nty * z);
+            const uint32_t pos = s_base[t] + atomicAdd(&s_hist[t], 1u);
+            // set up the walk of this record clipped to this tile
+            const int x0 = x * tp.tx, y0 = y * tp.ty, z0 = z * tp.tz;
+            const int dx = min(tp.tx, tp.nx - x0), dy = min(tp.ty, tp.ny - y0),
+                      dz = min(tp.tz, tp.nz - z0);
+            const int32_t gi[3] = {q[0] - (x0 << 16), q[1] - (y0 << 16), q[2] - (z0 << 16)};
+            const int32_t go[3] = {q[3] - (x0 << 16), q[4] - (y0 << 16), q[5] - (z0 << 16)};
+            RunWalk w;
+            LeanWalk L;
+            uint32_t pk[kLeanWords];
+            bool fallback = false;
+            if (!run_begin(w, gi, go, dx, dy, dz)) {
+                lean_pack_empty(pk);
+            } else if (lean_of(w, L)) {
+                lean_pack(L, pk);
+            } else {
+                lean_pack_empty(pk);  // walked from the fallback list instead
+                fallback = true;
+            }
+            pairs.v[2 * static_cast<size_t>(pos)] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+            pairs.v[2 * static_cast<size_t>(pos) + 1] = make_uint4(pk[4], pk[5], pk[6], pk[7]);
+            if (fallback) {
+                // append to the fallback list, one counter update per group of
+                // lanes arriving together
+                cg::coalesced_group grp = cg::coalesced_threads();
+                unsigned at = 0;
+                if (grp.thread_rank() == 0) {
+                    at = atomicAdd(&ctrl->n_pair_fallback, grp.size());
+                    atomicAdd(&ctrl->pairs_general, static_cast<unsigned long long>(grp.size()));
                 }
+                at = grp.shfl(at, 0) + grp.thread_rank();
+                pairs.fb[at] = make_uint2(static_cast<unsigned>(oslot),
+                                          2u * static_cast<unsigned>(t - ocls * tp.ntiles) +
+                                              static_cast<unsigned>(ocls));
+            }
+        }
     }
 }
 
