@@ -293,7 +293,7 @@ void make_tile_plan(hd_scan *s)
 {
     hd::TilePlan &tp = s->tp;
     const int nx = s->geom.nx, ny = s->geom.ny, nz = s->geom.nz;
-    const int budget = hd::kTileSmemBytes / 4;
+    const int budget = hd::kTileSmemBytes / 4 - 2;  // two int16 arrays and a scratch word
     tp.nx = nx;
     tp.ny = ny;
     tp.nz = nz;
@@ -327,8 +327,9 @@ void make_tile_plan(hd_scan *s)
     tp.job_size = s->tuning.job_size;  // <= 32767: int16 differences in the tiled traversal
     tp.refill = s->tuning.refill;
     tp.threads = s->tuning.threads;
-    // two int16 difference arrays per tile (x runs and y runs)
-    tp.tile_words = 2 * ((tp.tx * tp.ty * tp.tz + 1) / 2);
+    // two int16 difference arrays per tile (x runs and y runs) and a
+    // scratch word for the -1 of runs that end at their row's end
+    tp.tile_words = 2 * ((tp.tx * tp.ty * tp.tz + 1) / 2) + 1;
     auto magic = [](int t) {
         return t == 1 ? 0u : static_cast<unsigned>((1ull << 32) / static_cast<unsigned>(t)) + 1u;
     };

@@ -817,6 +817,63 @@ HD_HD void lean_unpack(const uint32_t o[kLeanWords], LeanWalk &L)
 
 HD_HD bool lean_empty(const LeanWalk &L) { return (L.fl >> 3) & 1; }
 
+// The traversal kernel's form of a lean walk: the same runs, with the row
+// offset (row * nmaj), the run's start and the direction kept as signed
+// increments so that a run costs a few integer operations.
+struct LeanCursor {
+    unsigned ad, Ru, rem;  // as in LeanWalk
+    int jn, Qu, kmz, kleft, K;
+    int im0, sg;  // major index of the first voxel, major direction (+1 or -1)
+    int ms;       // major index where the current run starts
+    int rb;       // row * nmaj of the current run
+    int rstep;    // change of rb per minor-0 crossing (+nmaj or -nmaj)
+};
+
+// A packed lean walk as a cursor over rows of nmaj voxels (nmaj: the box's
+// extent along the walk's major axis).  Returns false for an empty walk.
+HD_HD bool lean_start(const uint32_t o[kLeanWords], int nmaj, LeanCursor &c)
+{
+    const int fl = static_cast<int>(o[5] >> 16);
+    c.ad = o[0];
+    c.Ru = o[1];
+    c.rem = o[2];
+    c.jn = static_cast<int>(o[3] & 0xffffu);
+    c.Qu = static_cast<int>(o[3] >> 16);
+    c.kmz = static_cast<int>(o[4] & 0xffffu);
+    c.K = static_cast<int>(o[4] >> 16);
+    c.kleft = c.K;
+    c.im0 = static_cast<int>(o[5] & 0xffffu);
+    c.sg = (fl & 1) ? 1 : -1;
+    c.ms = c.im0;
+    c.rb = static_cast<int>(o[6]) * nmaj;
+    c.rstep = (fl & 2) ? nmaj : -nmaj;
+    return !((fl >> 3) & 1);
+}
+
+// The current run: *rb its row offset, lo..hi its major range (inclusive).
+// Returns whether more runs follow; with the last one it adds the walk's
+// voxel count to `steps` (see lean_step).  Branch-free: the cursor also
+// advances past the last run, where it is not used again.
+HD_HD bool lean_run(LeanCursor &c, int &rb, int &lo, int &hi, unsigned &steps)
+{
+    const int jn = c.jn;
+    const int e = jn < c.kmz ? jn : c.kmz;
+    const int b = c.im0 + c.sg * e;
+    lo = c.ms < b ? c.ms : b;
+    hi = c.ms < b ? b : c.ms;
+    rb = c.rb;
+    const bool last = c.kleft == 0 || jn > c.kmz;
+    steps += last ? static_cast<unsigned>(e + (c.K - c.kleft) + 1) : 0u;
+    c.ms = b;  // before the last run e = jn: the next run starts where this one ends
+    const unsigned rem = c.rem + c.Ru;
+    const bool carry = rem >= c.ad;
+    c.rem = carry ? rem - c.ad : rem;
+    c.jn = jn + c.Qu + (carry ? 1 : 0);
+    --c.kleft;
+    c.rb += c.rstep;
+    return !last;
+}
+
 // The current run of a non-empty lean walk: row, and the inclusive range
 // lo..hi of major indices.  Returns whether more runs follow; with the last
 // run it adds the walk's voxel count (e + K + 1: the major cells covered

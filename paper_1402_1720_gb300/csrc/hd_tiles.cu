@@ -248,12 +248,6 @@ __device__ __forceinline__ void load_lean(const Pairs &pairs, int idx, uint4 &a,
     b = __ldg(&pairs.v[2 * static_cast<size_t>(idx) + 1]);
 }
 
-__device__ __forceinline__ void diff_add(uint32_t *arr, int e, int sgn)
-{
-    const uint32_t one = (e & 1) ? 65536u : 1u;
-    atomicAdd(&arr[e >> 1], sgn > 0 ? one : (0u - one));
-}
-
 __device__ __forceinline__ void bits_clear(uint32_t *bits, int e0, int e1)
 {
     // clear bits e0..e1 inclusive
@@ -292,6 +286,82 @@ __device__ __forceinline__ void rows_prefix(int16_t *a, int rows, int len)
             row[i] = static_cast<int16_t>(run);
         }
     }
+}
+
+// Walks the pairs [start, start + total) of a job into the block's tile:
+// each lane walks one pair and holds the packed lean walk of its next one
+// (loaded a refill ahead, so starting a walk never waits on memory).  A
+// refill happens once enough lanes are idle; then every idle lane with a
+// prefetched pair starts it and fetches another, the pair index coming from
+// the block's counter *s_next.  Count mode adds +1 at a run's first voxel
+// and -1 just past its last one in the int16 difference arrays (x runs at
+// word 0, y runs at word arr_words; the -1 of a run that ends at its row's
+// end goes to the scratch word 2 arr_words); carve mode clears the run's
+// bits.  Returns the lane's voxel count.
+template <bool kCarve>
+__device__ __forceinline__ unsigned walk_job(uint32_t *tile, int arr_words, int dx, int dy,
+                                             const Pairs &pairs, int start, int total, int refill,
+                                             unsigned *s_next)
+{
+    const unsigned lane = threadIdx.x & 31u;
+    const int scratch = 2 * arr_words;
+    LeanCursor c;
+    bool active = false;
+    int nmaj = 0;
+    int aoff = 0;  // word offset in `tile` of the current walk's array
+    unsigned steps = 0;
+    uint4 na = make_uint4(0, 0, 0, 0), nb = na;
+    int nidx = -1;
+    {
+        unsigned base = 0;
+        if (lane == 0) base = atomicAdd(s_next, 32u);
+        base = __shfl_sync(kFull, base, 0);
+        const unsigned r = base + lane;
+        if (r < static_cast<unsigned>(total)) {
+            nidx = start + static_cast<int>(r);
+            load_lean(pairs, nidx, na, nb);
+        }
+    }
+    for (;;) {
+        const unsigned want = __ballot_sync(kFull, !active && nidx >= 0);
+        const unsigned busy = __ballot_sync(kFull, active);
+        if ((want | busy) == 0) break;
+        if (want != 0 && (__popc(want) >= static_cast<unsigned>(refill) || busy == 0)) {
+            if (!active && nidx >= 0) {
+                const uint32_t o[kLeanWords] = {na.x, na.y, na.z, na.w, nb.x, nb.y, nb.z, nb.w};
+                const bool ymaj = (o[5] >> 18) & 1u;  // LeanWalk::fl bit 2
+                nmaj = ymaj ? dy : dx;
+                aoff = ymaj ? arr_words : 0;
+                active = lean_start(o, nmaj, c);
+                nidx = -1;
+            }
+            unsigned base = 0;
+            const unsigned nw = __popc(want);
+            if (lane == 0) base = atomicAdd(s_next, nw);
+            base = __shfl_sync(kFull, base, 0);
+            if (want & (1u << lane)) {
+                const unsigned r = base + __popc(want & ((1u << lane) - 1u));
+                if (r < static_cast<unsigned>(total)) {
+                    nidx = start + static_cast<int>(r);
+                    load_lean(pairs, nidx, na, nb);
+                }
+            }
+            continue;
+        }
+        if (active) {
+            int rb, lo, hi;
+            active = lean_run(c, rb, lo, hi, steps);
+            if (!kCarve) {
+                const int e0 = rb + lo, e1 = rb + hi + 1;
+                atomicAdd(&tile[aoff + (e0 >> 1)], (e0 & 1) ? 65536u : 1u);
+                atomicAdd(&tile[hi + 1 < nmaj ? aoff + (e1 >> 1) : scratch],
+                          (e1 & 1) ? 0xffff0000u : 0xffffffffu);
+            } else {
+                bits_clear(tile + aoff, rb + lo, rb + hi);
+            }
+        }
+    }
+    return steps;
 }
 
 template <int kThreads>
@@ -350,67 +420,9 @@ __global__ void __launch_bounds__(kThreads, 1) trace_tiles_kernel(
         __syncthreads();
 
         const int total = job.end - job.start;
-        // Each lane walks one pair and holds the packed lean walk of its next
-        // one (loaded a refill ahead, so starting a walk never waits on
-        // memory).  A refill happens once enough lanes are idle; then every
-        // idle lane with a prefetched pair starts it and fetches another.
-        LeanWalk L;
-        L.fl = 8;
-        bool active = false;
-        int nmaj = 0;
-        unsigned steps = 0;
-        uint32_t *arr = arrX;
-        uint4 na = make_uint4(0, 0, 0, 0), nb = na;
-        int nidx = -1;
-        {
-            unsigned base = 0;
-            if (lane == 0) base = atomicAdd(&s_next, 32u);
-            base = __shfl_sync(kFull, base, 0);
-            const unsigned r = base + lane;
-            if (r < static_cast<unsigned>(total)) {
-                nidx = job.start + static_cast<int>(r);
-                load_lean(pairs, nidx, na, nb);
-            }
-        }
-        for (;;) {
-            const unsigned want = __ballot_sync(kFull, !active && nidx >= 0);
-            const unsigned busy = __ballot_sync(kFull, active);
-            if (want == 0 && busy == 0) break;
-            if (want != 0 && (__popc(want) >= static_cast<unsigned>(tp.refill) || busy == 0)) {
-                if (!active && nidx >= 0) {
-                    const uint32_t o[kLeanWords] = {na.x, na.y, na.z, na.w, nb.x, nb.y, nb.z, nb.w};
-                    lean_unpack(o, L);
-                    active = !lean_empty(L);
-                    const bool ymaj = (L.fl >> 2) & 1;
-                    arr = ymaj ? arrY : arrX;
-                    nmaj = ymaj ? dy : dx;
-                    nidx = -1;
-                }
-                unsigned base = 0;
-                const unsigned nw = __popc(want);
-                if (lane == 0) base = atomicAdd(&s_next, nw);
-                base = __shfl_sync(kFull, base, 0);
-                if (want & (1u << lane)) {
-                    const unsigned r = base + __popc(want & ((1u << lane) - 1u));
-                    if (r < static_cast<unsigned>(total)) {
-                        nidx = job.start + static_cast<int>(r);
-                        load_lean(pairs, nidx, na, nb);
-                    }
-                }
-                continue;
-            }
-            if (active) {
-                int row, lo, hi;
-                active = lean_step(L, row, lo, hi, steps);
-                const int base = row * nmaj;
-                if (!carve_mode) {
-                    diff_add(arr, base + lo, 1);
-                    if (hi + 1 < nmaj) diff_add(arr, base + hi + 1, -1);
-                } else {
-                    bits_clear(arr, base + lo, base + hi);
-                }
-            }
-        }
+        const unsigned steps =
+            carve_mode ? walk_job<true>(tile, arr_words, dx, dy, pairs, job.start, total, tp.refill, &s_next)
+                       : walk_job<false>(tile, arr_words, dx, dy, pairs, job.start, total, tp.refill, &s_next);
         __syncthreads();
         uint32_t *vol = job.cls == 0 ? N : M;
         if (!carve_mode) {
