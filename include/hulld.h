@@ -361,6 +361,8 @@ typedef struct {
     double issue_seconds; /* host time the worker spent issuing launches */
     double submit_seconds; /* host time spent inside hd_server_submit_chunk (all threads) */
     int64_t items_launched; /* (scan, segment) items over all launches */
+    double copy_seconds;    /* of submit_seconds: copying chunks (issue and wait) */
+    double alloc_seconds;   /* of submit_seconds: allocating staging segments */
 } hd_server_stats;
 
 /* 64 GiB budget, chunks up to 100000 histories, 64 scans per launch, 2 in

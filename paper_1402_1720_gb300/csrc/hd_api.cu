@@ -561,8 +561,13 @@ hd_status hd_scan_create(const hd_geometry *geom, const hd_params *params, hd_sc
         free_scan(s);
         return HD_ERR_NOMEM;
     }
-    const hd_status r = hd_scan_reset(s, nullptr);
-    if (r == HD_OK) e = cudaStreamSynchronize(nullptr);
+    // zero the counts on a private non-blocking stream: the legacy default
+    // stream would serialise with every blocking stream of the process
+    cudaStream_t init = nullptr;
+    e = cudaStreamCreateWithFlags(&init, cudaStreamNonBlocking);
+    const hd_status r = e == cudaSuccess ? hd_scan_reset(s, init) : HD_ERR_CUDA;
+    if (r == HD_OK) e = cudaStreamSynchronize(init);
+    if (init) cudaStreamDestroy(init);
     if (r != HD_OK || e != cudaSuccess) {
         if (e != cudaSuccess) note_cuda(e, "hd_scan_create: sync");
         free_scan(s);

@@ -191,13 +191,17 @@ HD_HD bool endpoints_cs(const GeomQ &g, long long c, long long s, float ui, floa
     if (!(fabsf(ui) < 4096.0f) || !(fabsf(vi) < 4096.0f) || !(fabsf(uo) < 4096.0f) ||
         !(fabsf(vo) < 4096.0f))
         return false;
-    const long long T = g.T;
-    const long long qui = q16_small(ui), qvi = q16_small(vi), quo = q16_small(uo),
-                    qvo = q16_small(vo);
-    const long long wxi = (-T * c - qui * s) >> 30;
-    const long long wyi = (-T * s + qui * c) >> 30;
-    const long long wxo = (T * c - quo * s) >> 30;
-    const long long wyo = (T * s + quo * c) >> 30;
+    // every factor fits 32 bits (T < 2^28 since the tracker distance is below
+    // 4096 mm, |c|, |s| <= 2^30, |u| Q16 < 2^28): exact 32 x 32 -> 64 products
+    const int T = static_cast<int>(g.T);
+    const int ci = static_cast<int>(c), si = static_cast<int>(s);
+    const int qui = q16_small(ui), quo = q16_small(uo);
+    const long long qvi = q16_small(vi), qvo = q16_small(vo);
+    auto mul = [](int a, int b) { return static_cast<long long>(a) * static_cast<long long>(b); };
+    const long long wxi = (-mul(T, ci) - mul(qui, si)) >> 30;
+    const long long wyi = (-mul(T, si) + mul(qui, ci)) >> 30;
+    const long long wxo = (mul(T, ci) - mul(quo, si)) >> 30;
+    const long long wyo = (mul(T, si) + mul(quo, ci)) >> 30;
     const long long G[6] = {to_grid(wxi, g.nx, g.sx, g.mx), to_grid(wyi, g.ny, g.sy, g.my),
                             to_grid(qvi, g.nz, g.sz, g.mz), to_grid(wxo, g.nx, g.sx, g.mx),
                             to_grid(wyo, g.ny, g.sy, g.my), to_grid(qvo, g.nz, g.sz, g.mz)};

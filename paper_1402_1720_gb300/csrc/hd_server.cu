@@ -95,6 +95,7 @@ struct hd_server {
     cudaStream_t stream = nullptr;  // launches
     std::vector<float *> free_bufs;  // staging segments not in use
     std::vector<float *> all_bufs;   // every staging segment allocated
+    int allocating = 0;              // segments being allocated (outside the lock)
     std::vector<hd_scan *> graveyard;  // closed scans to destroy
     std::vector<Tick> ticks;
     std::thread worker;  // launches
@@ -119,24 +120,39 @@ size_t footprint_of(const hd_geometry &g, const hd_server_config &cfg)
            (4u << 20);
 }
 
-// Called with the lock held: a free staging segment, allocating a new one
-// while the staging budget allows; nullptr when none can be had now.
-float *take_buffer(hd_server *sv, hd_status *err)
-{
-    *err = HD_OK;
-    if (!sv->free_bufs.empty()) {
-        float *b = sv->free_bufs.back();
-        sv->free_bufs.pop_back();
-        return b;
+// The calling thread's upload stream on `device`: non-blocking, so uploads
+// from several client threads proceed side by side and never wait for work
+// on the legacy default stream.  Created on first use, destroyed when the
+// thread exits.
+struct UploadStreams {
+    std::map<int, cudaStream_t> by_device;
+    ~UploadStreams()
+    {
+        for (auto &kv : by_device) cudaStreamDestroy(kv.second);
     }
-    if ((sv->all_bufs.size() + 1) * segment_bytes(sv->cfg) > sv->cfg.staging_bytes) return nullptr;
-    float *b = nullptr;
-    if (cudaMalloc(reinterpret_cast<void **>(&b), segment_bytes(sv->cfg)) != cudaSuccess) {
+};
+
+cudaStream_t upload_stream(int device)
+{
+    thread_local UploadStreams streams;
+    auto it = streams.by_device.find(device);
+    if (it != streams.by_device.end()) return it->second;
+    cudaStream_t st = nullptr;
+    if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
         cudaGetLastError();
-        *err = HD_ERR_NOMEM;
         return nullptr;
     }
-    sv->all_bufs.push_back(b);
+    streams.by_device[device] = st;
+    return st;
+}
+
+// Called with the lock held: a staging segment from the free list, or
+// nullptr.
+float *pop_free_buffer(hd_server *sv)
+{
+    if (sv->free_bufs.empty()) return nullptr;
+    float *b = sv->free_bufs.back();
+    sv->free_bufs.pop_back();
     return b;
 }
 
@@ -227,7 +243,7 @@ void keeper_main(hd_server *sv)
         hd_scan *h = nullptr;
         hd_status r = hd_scan_create(&geom, &params, &h);
         // scratch for a full segment now, so launches never grow it
-        if (r == HD_OK) r = hd_scan_reserve(h, sv->cfg.segment_histories, cudaStreamPerThread);
+        if (r == HD_OK) r = hd_scan_reserve(h, sv->cfg.segment_histories, upload_stream(sv->device));
         lock.lock();
         SScan &s = sv->scans[id];  // not closed while admitting
         s.admitting = false;
@@ -466,26 +482,57 @@ hd_status hd_server_submit_chunk(hd_server *sv, int64_t scan_id, const float *an
     Segment *seg = nullptr;
     int64_t off = 0;
     {
-        // reserve room in the scan's open segment (a new one when it is full)
+        // reserve room in the scan's open segment (a new one when it is
+        // full); device memory for a new segment is allocated outside the lock
         std::unique_lock<std::mutex> lock(sv->mu);
+        float *held = nullptr;  // a segment buffer this call owns
+        auto give_back = [&]() {
+            if (held) sv->free_bufs.push_back(held);
+            held = nullptr;
+            sv->cv_space.notify_all();
+        };
         for (;;) {
             auto it = sv->scans.find(scan_id);
-            if (it == sv->scans.end()) return HD_ERR_ARG;
+            if (it == sv->scans.end()) {
+                give_back();
+                return HD_ERR_ARG;
+            }
             SScan &s = it->second;
-            if (s.state >= 2 || s.reserved_chunks >= s.n_chunks) return HD_ERR_STATE;
+            if (s.state >= 2 || s.reserved_chunks >= s.n_chunks) {
+                give_back();
+                return HD_ERR_STATE;
+            }
             if (!s.segs.empty() && !s.segs.back()->sealed && s.segs.back()->reserved + n <= cap) {
+                seg = s.segs.back().get();
+                give_back();
+                break;
+            }
+            if (!held) held = pop_free_buffer(sv);
+            if (held) {
+                if (!s.segs.empty()) s.segs.back()->sealed = true;
+                s.segs.emplace_back(new Segment());
+                s.segs.back()->dev = held;
+                held = nullptr;
                 seg = s.segs.back().get();
                 break;
             }
-            hd_status err = HD_OK;
-            float *buf = take_buffer(sv, &err);
-            if (err != HD_OK) return err;
-            if (buf) {
-                if (!s.segs.empty()) s.segs.back()->sealed = true;
-                s.segs.emplace_back(new Segment());
-                s.segs.back()->dev = buf;
-                seg = s.segs.back().get();
-                break;
+            const size_t nbufs = sv->all_bufs.size() + static_cast<size_t>(sv->allocating);
+            if ((nbufs + 1) * segment_bytes(sv->cfg) <= sv->cfg.staging_bytes) {
+                sv->allocating += 1;
+                lock.unlock();
+                const auto t_alloc = std::chrono::steady_clock::now();
+                float *b = nullptr;
+                const cudaError_t ea =
+                    cudaMalloc(reinterpret_cast<void **>(&b), segment_bytes(sv->cfg));
+                if (ea != cudaSuccess) cudaGetLastError();
+                lock.lock();
+                sv->allocating -= 1;
+                sv->stats.alloc_seconds +=
+                    std::chrono::duration<double>(std::chrono::steady_clock::now() - t_alloc).count();
+                if (ea != cudaSuccess) return HD_ERR_NOMEM;
+                sv->all_bufs.push_back(b);
+                held = b;
+                continue;  // the scan may have changed meanwhile
             }
             // staging is full: wait for a launch to return its segments
             if (sv->stop ||
@@ -500,11 +547,10 @@ hd_status hd_server_submit_chunk(hd_server *sv, int64_t scan_id, const float *an
     int prev = -1;
     cudaGetDevice(&prev);
     if (prev != sv->device) cudaSetDevice(sv->device);
-    // each client thread copies on its own per-thread stream, so uploads
-    // from several threads proceed side by side
-    const cudaStream_t up = cudaStreamPerThread;
+    const auto t_copy = std::chrono::steady_clock::now();
+    const cudaStream_t up = upload_stream(sv->device);
     const float *src[6] = {angle_deg, u_in, v_in, u_out, v_out, wepl};
-    cudaError_t e = cudaSuccess;
+    cudaError_t e = up ? cudaSuccess : cudaErrorUnknown;
     for (int a = 0; e == cudaSuccess && a < 6; ++a)
         e = cudaMemcpyAsync(seg->dev + a * cap + off, src[a], sizeof(float) * n,
                             on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, up);
@@ -512,7 +558,10 @@ hd_status hd_server_submit_chunk(hd_server *sv, int64_t scan_id, const float *an
     if (e == cudaSuccess) e = cudaStreamSynchronize(up);
     if (e != cudaSuccess) cudaGetLastError();
     if (prev >= 0 && prev != sv->device) cudaSetDevice(prev);
+    const double copy_s =
+        std::chrono::duration<double>(std::chrono::steady_clock::now() - t_copy).count();
     std::lock_guard<std::mutex> lock(sv->mu);
+    sv->stats.copy_seconds += copy_s;
     SScan &s = sv->scans[scan_id];  // cannot be closed while a copy runs
     seg->writers -= 1;
     if (e != cudaSuccess) {
