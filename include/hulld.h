@@ -176,8 +176,12 @@ HD_API hd_status hd_scan_reserve(hd_scan *scan, int64_t n, void *stream);
  * and, when SC runs without MSC, the SC carve (Alg. 1).  Counts stay
  * resident on the device, so histories may arrive in any number of calls
  * (streamed per-angle chunks, Sec. 4 online mode) in any order; the result
- * depends only on the multiset of histories.  on_device = 0 copies from host
- * memory inside the call (stream-ordered).  n = 0 is a no-op.
+ * depends only on the multiset of histories.  on_device = 0 takes host
+ * arrays: page-locked arrays mapped into the device's address space (as
+ * cudaHostAlloc gives) are read in place by the first kernel over the host
+ * link; other host memory is copied to a device staging buffer inside the
+ * call.  Either way the arrays must stay unchanged until the work this call
+ * queued on `stream` has completed.  n = 0 is a no-op.
  * HD_ERR_OVERFLOW if the scan would exceed 2^32 - 1 histories. */
 HD_API hd_status hd_scan_add_histories(hd_scan *scan, const float *angle_deg, const float *u_in,
                                 const float *v_in, const float *u_out, const float *v_out,

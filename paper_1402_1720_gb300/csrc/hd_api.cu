@@ -103,8 +103,8 @@ struct hd_scan {
     bool desc_dirty = true;
     uint32_t *tile_count = nullptr;   // 2 * ntiles
     uint32_t *tile_cursor = nullptr;  // 2 * ntiles
-    float *staging = nullptr;
-    int64_t staging_cap = 0;
+    float *staging = nullptr;  // copied host inputs: 6 columns of staging_half floats
+    int64_t staging_half = 0;
     uint32_t *compact_blocks = nullptr;
     unsigned long long *d_count = nullptr;
     int32_t *compact_out = nullptr;
@@ -172,6 +172,7 @@ void free_scan(hd_scan *s)
 {
     drain_profile(s);
     for (cudaEvent_t e : s->event_pool) cudaEventDestroy(e);
+
     void *ptrs[] = {s->N, s->M, s->carve, s->H1, s->H2, s->H3, s->bits_out, s->slice_key,
                     s->mt, s->slope, s->index, s->ctrl, s->rec_buf, s->staging,
                     s->compact_blocks, s->d_count, s->compact_out, s->pair_buf, s->jobs,
@@ -249,22 +250,41 @@ hd_status ensure_records(hd_scan *s, int64_t n, cudaStream_t st)
     return HD_OK;
 }
 
-hd_status ensure_staging(hd_scan *s, int64_t n, cudaStream_t st)
+
+// Staging for host inputs that the device cannot read in place: six
+// columns of `cap` histories.
+hd_status ensure_staging(hd_scan *s, int64_t cap, cudaStream_t st)
 {
-    if (n <= s->staging_cap) return HD_OK;
+    if (cap <= s->staging_half) return HD_OK;
     HD_CUDA(cudaStreamSynchronize(st));
     if (s->staging) {
         cudaFree(s->staging);
         s->staging = nullptr;
-        s->staging_cap = 0;
+        s->staging_half = 0;
     }
-    if (cudaMalloc(&s->staging, sizeof(float) * 6 * static_cast<size_t>(n)) != cudaSuccess) {
+    if (cudaMalloc(&s->staging, sizeof(float) * 6 * static_cast<size_t>(cap)) != cudaSuccess) {
         cudaGetLastError();
         s->staging = nullptr;
         return HD_ERR_NOMEM;
     }
-    s->staging_cap = n;
+    s->staging_half = cap;
     return HD_OK;
+}
+
+// Whether the device can read all six host arrays in place: page-locked
+// memory mapped at the same address (pageable memory is copied instead).
+bool all_mapped_host(const float *const src[6], int device)
+{
+    for (int a = 0; a < 6; ++a) {
+        cudaPointerAttributes at{};
+        if (cudaPointerGetAttributes(&at, src[a]) != cudaSuccess) {
+            cudaGetLastError();
+            return false;
+        }
+        if (at.type != cudaMemoryTypeHost || at.devicePointer != src[a]) return false;
+        (void)device;
+    }
+    return true;
 }
 
 hd::Records records_of(const hd_scan *s, int64_t n)
@@ -439,6 +459,7 @@ hd_status stage_finalize(hd_scan *scan, cudaStream_t st)
 
 int finalize_launches(const hd_scan *scan) { return (scan->params.methods & HD_SM) ? 3 : 1; }
 
+// One chunk through the whole path on st.
 hd_status run_chunk(hd_scan *s, const hd::Inputs &in, int64_t n, cudaStream_t st)
 {
     hd_status r = upload_desc(s, st);
@@ -619,30 +640,52 @@ hd_status hd_scan_add_histories(hd_scan *scan, const float *angle_deg, const flo
     DeviceGuard g(scan->device);
     if (!g.ok) return HD_ERR_CUDA;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    const int64_t chunk = n < kChunk ? n : kChunk;
-    hd_status r = ensure_records(scan, chunk, st);
-    if (r != HD_OK) return r;
-    if (!on_device) {
+    const float *src[6] = {angle_deg, u_in, v_in, u_out, v_out, wepl};
+    if (on_device) {
+        const int64_t chunk = n < kChunk ? n : kChunk;
+        hd_status r = ensure_records(scan, chunk, st);
+        if (r != HD_OK) return r;
+        for (int64_t off = 0; off < n; off += chunk) {
+            const int64_t c = (n - off) < chunk ? (n - off) : chunk;
+            const hd::Inputs in{src[0] + off, src[1] + off, src[2] + off,
+                                src[3] + off, src[4] + off, src[5] + off};
+            r = run_chunk(scan, in, c, st);
+            if (r != HD_OK) return r;
+        }
+    } else if (all_mapped_host(src, scan->device)) {
+        // page-locked host arrays mapped into the device's address space: the
+        // ingest kernel reads them in place over the host link, so the
+        // transfer happens inside the kernel that consumes it
+        const int64_t chunk = n < kChunk ? n : kChunk;
+        hd_status r = ensure_records(scan, chunk, st);
+        if (r != HD_OK) return r;
+        for (int64_t off = 0; off < n; off += chunk) {
+            const int64_t c = (n - off) < chunk ? (n - off) : chunk;
+            const hd::Inputs in{src[0] + off, src[1] + off, src[2] + off,
+                                src[3] + off, src[4] + off, src[5] + off};
+            r = run_chunk(scan, in, c, st);
+            if (r != HD_OK) return r;
+        }
+    } else {
+        // other host memory: copied to the scan's staging buffer, one chunk
+        // at a time, on st
+        const int64_t chunk = n < kChunk ? n : kChunk;
+        hd_status r = ensure_records(scan, chunk, st);
+        if (r != HD_OK) return r;
         r = ensure_staging(scan, chunk, st);
         if (r != HD_OK) return r;
-    }
-    const float *src[6] = {angle_deg, u_in, v_in, u_out, v_out, wepl};
-    for (int64_t off = 0; off < n; off += chunk) {
-        const int64_t c = (n - off) < chunk ? (n - off) : chunk;
-        hd::Inputs in;
-        const float **dst[6] = {&in.angle, &in.u_in, &in.v_in, &in.u_out, &in.v_out, &in.wepl};
-        for (int a = 0; a < 6; ++a) {
-            if (on_device) {
-                *dst[a] = src[a] + off;
-            } else {
-                float *d = scan->staging + static_cast<size_t>(a) * scan->staging_cap;
-                HD_CUDA(cudaMemcpyAsync(d, src[a] + off, sizeof(float) * c,
+        const int64_t half = scan->staging_half;
+        for (int64_t off = 0; off < n; off += chunk) {
+            const int64_t c = (n - off) < chunk ? (n - off) : chunk;
+            float *base = scan->staging;
+            for (int a = 0; a < 6; ++a)
+                HD_CUDA(cudaMemcpyAsync(base + a * half, src[a] + off, sizeof(float) * c,
                                         cudaMemcpyHostToDevice, st));
-                *dst[a] = d;
-            }
+            const hd::Inputs in{base, base + half, base + 2 * half,
+                                base + 3 * half, base + 4 * half, base + 5 * half};
+            r = run_chunk(scan, in, c, st);
+            if (r != HD_OK) return r;
         }
-        r = run_chunk(scan, in, c, st);
-        if (r != HD_OK) return r;
     }
     scan->n_total += static_cast<uint64_t>(n);
     scan->finalized = false;

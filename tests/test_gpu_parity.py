@@ -484,3 +484,34 @@ def test_autotuner_picks_a_valid_setting(hd, tmp_path):
     path = str(tmp_path / "cache.json")
     got = autotune.tuned_setting(w.geometry, dev, path=path, repeats=1)
     assert autotune.tuned_setting(w.geometry, None, path=path) == got  # from the cache
+
+
+def test_host_inputs_equal_device_inputs(hd):
+    """Host inputs at scale: pageable numpy (copied to the staging buffer),
+    page-locked tensors (read in place by the ingest kernel) and two calls in
+    a row give the device-input counts exactly."""
+    w = synth.make_config(2, fraction=0.5)
+    g, h = w.geometry, w.histories
+    arrs = h.arrays()
+    with hd.Scan(g) as s:
+        s.add([torch.from_numpy(a).cuda() for a in arrs])
+        s.finalize()
+        torch.cuda.synchronize()
+        ref_n, ref_m = s.counts(hd.HD_MSC), s.counts(hd.HD_SM)
+        ref_st = s.stats()
+    pinned = [torch.from_numpy(a).pin_memory() for a in arrs]
+    half = len(h) // 2
+    for inputs in (arrs, pinned, "split"):
+        with hd.Scan(g) as s:
+            if inputs == "split":
+                s.add([a[:half] for a in arrs])
+                s.add([a[half:] for a in arrs])
+            else:
+                s.add(inputs)
+            s.finalize()
+            torch.cuda.synchronize()
+            assert np.array_equal(s.counts(hd.HD_MSC), ref_n)
+            assert np.array_equal(s.counts(hd.HD_SM), ref_m)
+            st = s.stats()
+            for k in ("n_in", "n_miss", "n_hit", "steps_miss", "steps_hit"):
+                assert st[k] == ref_st[k], k
