@@ -323,14 +323,17 @@ HD_API hd_status hd_batch_get_stats(hd_batch *batch, hd_batch_stats *out);
  * online mode of Sec. 4).  A submit copies its chunk into the scan's open
  * staging segment (device memory for segment_histories histories), so the
  * chunks of a scan that arrive while the GPU is busy lie side by side.  A
- * worker thread admits scans first come, first served while their device
- * footprint fits hbm_budget_bytes, and keeps up to max_in_flight batched
+ * housekeeping thread admits scans first come, first served while their
+ * device footprint fits hbm_budget_bytes (and creates and destroys their
+ * device state); a worker thread keeps up to max_in_flight batched
  * launches queued on the GPU, each taking the oldest filled segment of each
  * of up to max_batch admitted scans (one persistent traversal over all of
  * them, as hd_batch_run): every chunk a scan received since its last launch
  * goes in as one item.  A scan's hulls are computed in the launch that
  * carries its last chunk; they stay on the device until the client closes
- * the scan, which returns its memory to the budget.  Results equal those of
+ * the scan.  A closed scan is kept (its memory still counted in the budget)
+ * and reset for a later scan of the same geometry and parameters, or
+ * destroyed when an admission needs its memory.  Results equal those of
  * the same chunks added to a lone scan.  Staging memory is bounded by
  * staging_bytes: a submit that finds none free waits for a launch to finish
  * (at most submit_timeout_ms).  Times are seconds since the server was
@@ -367,6 +370,9 @@ typedef struct {
     int64_t items_launched; /* (scan, segment) items over all launches */
     double copy_seconds;    /* of submit_seconds: copying chunks (issue and wait) */
     double alloc_seconds;   /* of submit_seconds: allocating staging segments */
+    int64_t scans_reused;   /* admissions that reset a pooled scan instead of creating one */
+    int64_t bytes_pooled;   /* footprint of closed scans kept for reuse (counts in the
+                               budget; evicted, oldest first, when an admission needs it) */
 } hd_server_stats;
 
 /* 64 GiB budget, chunks up to 100000 histories, 64 scans per launch, 2 in

@@ -97,6 +97,14 @@ struct hd_server {
     std::vector<float *> all_bufs;   // every staging segment allocated
     int allocating = 0;              // segments being allocated (outside the lock)
     std::vector<hd_scan *> graveyard;  // closed scans to destroy
+    struct Pooled {
+        hd_geometry geom;
+        hd_params params;
+        hd_scan *scan;
+        size_t footprint;
+    };
+    std::deque<Pooled> pool;  // closed scans kept for reuse, oldest first
+    size_t pooled = 0;        // their footprint (part of `used`)
     std::vector<Tick> ticks;
     std::thread worker;  // launches
     std::thread keeper;  // creates admitted scans and destroys closed ones
@@ -200,6 +208,16 @@ void retire(hd_server *sv)
     sv->cv_space.notify_all();
 }
 
+bool same_config(const hd_geometry &a, const hd_geometry &b, const hd_params &p,
+                 const hd_params &q)
+{
+    return a.nx == b.nx && a.ny == b.ny && a.nz == b.nz && a.sx == b.sx && a.sy == b.sy &&
+           a.sz == b.sz && a.tracker_half_sep_mm == b.tracker_half_sep_mm &&
+           p.wepl_miss_lt == q.wepl_miss_lt && p.wepl_hit_gt == q.wepl_hit_gt &&
+           p.msc_nt == q.msc_nt && p.msc_nbhd == q.msc_nbhd && p.sm_ge == q.sm_ge &&
+           p.sm_per_slice == q.sm_per_slice && p.methods == q.methods;
+}
+
 // Admission and clean-up, on their own thread so that allocating or
 // freeing a scan's device memory (which may wait for the GPU) stalls
 // neither the launches nor the submits: scans are admitted first come,
@@ -217,7 +235,11 @@ void keeper_main(hd_server *sv)
             lock.lock();
             continue;
         }
+        // the first waiting scan: a pooled scan of the same geometry and
+        // parameters is reset and reused; otherwise a new one is created once
+        // its footprint fits (evicting pooled scans, oldest first, if needed)
         int64_t id = -1;
+        hd_scan *reuse = nullptr;
         while (!sv->waiting.empty()) {
             auto it = sv->scans.find(sv->waiting.front());
             if (it == sv->scans.end()) {
@@ -225,25 +247,48 @@ void keeper_main(hd_server *sv)
                 continue;
             }
             SScan &s = it->second;
-            if (sv->used + s.footprint <= sv->cfg.hbm_budget_bytes) {
+            for (auto pi = sv->pool.begin(); pi != sv->pool.end(); ++pi)
+                if (same_config(pi->geom, s.geom, pi->params, s.params)) {
+                    reuse = pi->scan;
+                    sv->pooled -= pi->footprint;  // stays in `used`, now for this scan
+                    sv->pool.erase(pi);
+                    break;
+                }
+            if (!reuse && sv->used + s.footprint > sv->cfg.hbm_budget_bytes && !sv->pool.empty()) {
+                const auto victim = sv->pool.front();
+                sv->pool.pop_front();
+                sv->pooled -= victim.footprint;
+                sv->used -= victim.footprint;
+                sv->graveyard.push_back(victim.scan);
+                continue;
+            }
+            if (reuse || sv->used + s.footprint <= sv->cfg.hbm_budget_bytes) {
                 id = s.id;
                 sv->waiting.pop_front();
                 s.admitting = true;
-                sv->used += s.footprint;
+                if (!reuse) sv->used += s.footprint;
             }
             break;
         }
         if (id < 0) {
+            if (!sv->graveyard.empty()) continue;  // evicted scans to destroy first
             sv->cv_keep.wait(lock);
             continue;
         }
         const hd_geometry geom = sv->scans[id].geom;
         const hd_params params = sv->scans[id].params;
         lock.unlock();
-        hd_scan *h = nullptr;
-        hd_status r = hd_scan_create(&geom, &params, &h);
-        // scratch for a full segment now, so launches never grow it
-        if (r == HD_OK) r = hd_scan_reserve(h, sv->cfg.segment_histories, upload_stream(sv->device));
+        hd_scan *h = reuse;
+        hd_status r = HD_OK;
+        const cudaStream_t ks = upload_stream(sv->device);
+        if (reuse) {
+            r = hd_scan_reset(h, ks);
+            if (r == HD_OK && cudaStreamSynchronize(ks) != cudaSuccess) r = HD_ERR_CUDA;
+        } else {
+            r = hd_scan_create(&geom, &params, &h);
+            // scratch for a full segment now, so launches never grow it
+            if (r == HD_OK) r = hd_scan_reserve(h, sv->cfg.segment_histories, ks);
+        }
         lock.lock();
         SScan &s = sv->scans[id];  // not closed while admitting
         s.admitting = false;
@@ -260,6 +305,7 @@ void keeper_main(hd_server *sv)
         s.t_admit = now_since(sv->t0);
         sv->admitted_order.push_back(id);
         sv->stats.scans_admitted += 1;
+        if (reuse) sv->stats.scans_reused += 1;
         sv->cv_work.notify_all();
     }
 }
@@ -437,6 +483,7 @@ hd_status hd_server_destroy(hd_server *sv)
     for (auto &kv : sv->scans)
         if (kv.second.scan) hd_scan_destroy(kv.second.scan);
     for (hd_scan *h : sv->graveyard) hd_scan_destroy(h);
+    for (auto &p : sv->pool) hd_scan_destroy(p.scan);
     for (auto &t : sv->ticks) {
         if (t.batch) hd_batch_destroy(t.batch);
         if (t.done) cudaEventDestroy(t.done);
@@ -646,7 +693,8 @@ hd_status hd_server_get_stats(hd_server *sv, hd_server_stats *out)
     if (!sv || !out) return HD_ERR_ARG;
     std::lock_guard<std::mutex> lock(sv->mu);
     *out = sv->stats;
-    out->bytes_in_use = static_cast<int64_t>(sv->used);
+    out->bytes_in_use = static_cast<int64_t>(sv->used - sv->pooled);
+    out->bytes_pooled = static_cast<int64_t>(sv->pooled);
     return HD_OK;
 }
 
@@ -664,8 +712,14 @@ hd_status hd_server_close_scan(hd_server *sv, int64_t scan_id)
         if (g->writers) return HD_ERR_STATE;  // a submit is copying into it
     if (s.state == 3 && s.done_chunks < s.issued) return HD_ERR_STATE;
     recycle_segments(sv, s);
-    if (s.state >= 1 && s.scan) sv->used -= s.footprint;
-    if (s.scan) sv->graveyard.push_back(s.scan);  // destroyed by the keeper thread
+    if (s.state == 2 && s.scan) {
+        // kept for a later scan of the same geometry and parameters
+        sv->pool.push_back({s.geom, s.params, s.scan, s.footprint});
+        sv->pooled += s.footprint;
+    } else if (s.scan) {
+        if (s.state >= 1) sv->used -= s.footprint;
+        sv->graveyard.push_back(s.scan);  // destroyed by the keeper thread
+    }
     for (auto ai = sv->admitted_order.begin(); ai != sv->admitted_order.end(); ++ai)
         if (*ai == scan_id) {
             sv->admitted_order.erase(ai);

@@ -111,7 +111,8 @@ class hd_server_stats(ctypes.Structure):
                 ("chunks_launched", ctypes.c_int64), ("launches", ctypes.c_int64),
                 ("bytes_in_use", ctypes.c_int64), ("issue_seconds", ctypes.c_double),
                 ("submit_seconds", ctypes.c_double), ("items_launched", ctypes.c_int64),
-                ("copy_seconds", ctypes.c_double), ("alloc_seconds", ctypes.c_double)]
+                ("copy_seconds", ctypes.c_double), ("alloc_seconds", ctypes.c_double),
+                ("scans_reused", ctypes.c_int64), ("bytes_pooled", ctypes.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -209,3 +209,23 @@ def test_staging_backpressure(hd, scans_case):
         st = srv.stats()
         assert st["chunks_launched"] == len(ch_a) + len(ch_b)
         srv.close_scan(b)
+
+
+def test_closed_scans_are_reused(hd, scans_case):
+    """A closed scan is kept and reset for the next scan of the same geometry
+    and parameters: the second scan gets the same results as a lone scan."""
+    sp, h, ch = scans_case[0]
+    ref = _alone(hd, sp.geometry, h)
+    with hd.Server() as srv:
+        for _ in range(2):
+            sid = srv.open_scan(sp.geometry, None, len(ch))
+            for c in ch:
+                srv.submit(sid, c.arrays())
+            assert srv.wait(sid, 60000) == hd.HD_OK
+            got = _served(hd, srv.scan(sid, sp.geometry))
+            for k in ref:
+                assert np.array_equal(got[k], ref[k]), k
+            srv.close_scan(sid)
+        st = srv.stats()
+        assert st["scans_reused"] == 1
+        assert st["bytes_pooled"] > 0 and st["bytes_in_use"] == 0
