@@ -33,6 +33,10 @@
  * grid plane, so the set is the voxels at those parameters and at the
  * midpoints between them.  All parameters are exact rationals.  A second,
  * independent statement (the per-voxel slab test) checks it on small grids.
+ *
+ * Reported only (not a parity reference): the same set definition on
+ * unquantised FP64 geometry, to measure how many voxel memberships and
+ * hull voxels the fixed-point geometry changes.
  */
 #include <stdint.h>
 #include <stdlib.h>
@@ -347,6 +351,177 @@ int oracle_accumulate(const og_geom *g, float tau_l, float tau_h, int32_t method
         stats[cls == 1 ? 5 : 6] += m;
     }
     free(set);
+    return 0;
+}
+
+/* ------------------------------- FP64 geometry comparison (reported only) */
+
+/* The same history with unquantised FP64 geometry: libm cos/sin of the
+ * angle, no rounding of u, v, T or the voxel sizes; grid coordinates in
+ * voxel units, (w + n s / 2) / s.  The same rejection rules as
+ * oracle_grid_endpoints (a grid coordinate of magnitude >= 2^14 voxels,
+ * i.e. 2^30 in Q16).  Returns 0 when usable, 1 when rejected. */
+int oracle_grid_endpoints_fp64(const og_geom *g, float angle, float u_in, float v_in,
+                               float u_out, float v_out, double *gin, double *gout)
+{
+    if (!(fabsf(angle) < 1048576.0f)) return 1;
+    if (!(fabsf(u_in) < 4096.0f) || !(fabsf(v_in) < 4096.0f) ||
+        !(fabsf(u_out) < 4096.0f) || !(fabsf(v_out) < 4096.0f))
+        return 1;
+    const double rad = fmod((double)angle, 360.0) * (acos(-1.0) / 180.0);
+    const double c = cos(rad), s = sin(rad), T = g->T;
+    const double wx_in = -T * c - (double)u_in * s, wy_in = -T * s + (double)u_in * c;
+    const double wx_out = T * c - (double)u_out * s, wy_out = T * s + (double)u_out * c;
+    gin[0] = wx_in / g->sx + g->nx / 2.0;
+    gin[1] = wy_in / g->sy + g->ny / 2.0;
+    gin[2] = (double)v_in / g->sz + g->nz / 2.0;
+    gout[0] = wx_out / g->sx + g->nx / 2.0;
+    gout[1] = wy_out / g->sy + g->ny / 2.0;
+    gout[2] = (double)v_out / g->sz + g->nz / 2.0;
+    for (int a = 0; a < 3; ++a)
+        if (fabs(gin[a]) >= 16384.0 || fabs(gout[a]) >= 16384.0) return 1;
+    return 0;
+}
+
+static int cmp_dbl(const void *a, const void *b)
+{
+    double x = *(const double *)a, y = *(const double *)b;
+    return (x < y) ? -1 : (x > y) ? 1 : 0;
+}
+
+/* Linear index of floor(P(t)) in double, or -1 outside the grid. */
+static int64_t voxel_at_fp64(const double *gin, const double *d, const int32_t *n, double t)
+{
+    int64_t idx[3];
+    for (int a = 0; a < 3; ++a) {
+        double k = floor(gin[a] + t * d[a]);
+        if (k < 0 || k >= n[a]) return -1;
+        idx[a] = (int64_t)k;
+    }
+    return idx[0] + (int64_t)n[0] * (idx[1] + (int64_t)n[1] * idx[2]);
+}
+
+/* The voxel set of the closed segment gin -> gout (grid units, double) by
+ * the definition the fixed-point set uses: floor(P(t)) is constant between
+ * the parameters at which a coordinate crosses a grid plane, so the set is
+ * the voxels at the two ends and at the midpoints between consecutive
+ * crossing parameters (at FP64 inputs a segment passes through an edge or a
+ * corner with probability zero, so the crossing points themselves add no
+ * voxel).  Sorted unique linear indices; returns the size, -1 when out of
+ * memory. */
+int64_t oracle_voxel_set_fp64(const double *gin, const double *gout, int32_t nx, int32_t ny,
+                              int32_t nz, int64_t *out, int64_t cap)
+{
+    const int32_t n[3] = {nx, ny, nz};
+    double d[3];
+    int64_t maxbp = 2;
+    for (int a = 0; a < 3; ++a) {
+        d[a] = gout[a] - gin[a];
+        maxbp += (int64_t)n[a] + 1;
+    }
+    double *bp = (double *)malloc(sizeof(double) * (size_t)maxbp);
+    int64_t *cand = (int64_t *)malloc(sizeof(int64_t) * (size_t)(maxbp + 2));
+    if (!bp || !cand) {
+        free(bp);
+        free(cand);
+        return -1;
+    }
+    int64_t nb = 0;
+    bp[nb++] = 0.0;
+    bp[nb++] = 1.0;
+    for (int a = 0; a < 3; ++a) {
+        if (d[a] == 0.0) continue;
+        for (int64_t k = 0; k <= n[a]; ++k) {
+            const double t = ((double)k - gin[a]) / d[a];
+            if (t > 0.0 && t < 1.0) bp[nb++] = t;
+        }
+    }
+    qsort(bp, (size_t)nb, sizeof(double), cmp_dbl);
+    int64_t nc = 0;
+    int64_t v = voxel_at_fp64(gin, d, n, 0.0);
+    if (v >= 0) cand[nc++] = v;
+    v = voxel_at_fp64(gin, d, n, 1.0);
+    if (v >= 0) cand[nc++] = v;
+    for (int64_t j = 0; j + 1 < nb; ++j) {
+        if (bp[j + 1] <= bp[j]) continue;
+        v = voxel_at_fp64(gin, d, n, 0.5 * (bp[j] + bp[j + 1]));
+        if (v >= 0) cand[nc++] = v;
+    }
+    qsort(cand, (size_t)nc, sizeof(int64_t), cmp_i64);
+    int64_t m = 0;
+    for (int64_t j = 0; j < nc; ++j) {
+        if (j > 0 && cand[j] == cand[j - 1]) continue;
+        if (m < cap) out[m] = cand[j];
+        ++m;
+    }
+    free(bp);
+    free(cand);
+    return m;
+}
+
+/* Each traversed history's fixed-point set (the method as built) against its
+ * FP64-geometry set, and the FP64 counts N64 (missed) and M64 (hit).
+ * cmp: [0] histories traversed with both geometries, [1] their fixed-point
+ * memberships, [2] memberships in exactly one of the two sets, [3] histories
+ * whose two sets differ, [4] histories traversed with one geometry only.
+ * Returns 0, or -1 when out of memory. */
+int oracle_compare_fp64(const og_geom *g, float tau_l, float tau_h, int32_t methods,
+                        const int64_t *theta, int64_t K, const float *angle,
+                        const float *u_in, const float *v_in, const float *u_out,
+                        const float *v_out, const float *wepl, int64_t n, uint32_t *N64,
+                        uint32_t *M64, int64_t *cmp)
+{
+    int64_t cap = (int64_t)g->nx + g->ny + g->nz + 8;
+    int64_t *a = (int64_t *)malloc(sizeof(int64_t) * (size_t)cap);
+    int64_t *b = (int64_t *)malloc(sizeof(int64_t) * (size_t)cap);
+    if (!a || !b) {
+        free(a);
+        free(b);
+        return -1;
+    }
+    int use_miss = (methods & (OM_SC | OM_MSC)) != 0;
+    int use_hit = (methods & OM_SM) != 0;
+    for (int64_t i = 0; i < n; ++i) {
+        int cls = oracle_classify(wepl[i], tau_l, tau_h);
+        if (!((cls == 1 && use_miss) || (cls == 2 && use_hit))) continue;
+        int64_t gin[3], gout[3];
+        double fin[3], fout[3];
+        int rej_q = oracle_grid_endpoints(g, theta, K, angle[i], u_in[i], v_in[i], u_out[i],
+                                          v_out[i], gin, gout);
+        int rej_f = oracle_grid_endpoints_fp64(g, angle[i], u_in[i], v_in[i], u_out[i],
+                                               v_out[i], fin, fout);
+        int64_t ma = 0, mb = 0;
+        if (!rej_q) ma = oracle_voxel_set(gin, gout, g->nx, g->ny, g->nz, a, cap);
+        if (!rej_f) mb = oracle_voxel_set_fp64(fin, fout, g->nx, g->ny, g->nz, b, cap);
+        if (ma < 0 || mb < 0 || ma > cap || mb > cap) {
+            free(a);
+            free(b);
+            return -1;
+        }
+        if (!rej_f)
+            for (int64_t j = 0; j < mb; ++j) {
+                if (cls == 1) N64[b[j]] += 1;
+                else M64[b[j]] += 1;
+            }
+        if (rej_q != rej_f) {
+            cmp[4] += 1;
+            continue;
+        }
+        if (rej_q) continue;
+        /* symmetric difference of two sorted sets */
+        int64_t x = 0, y = 0, only = 0;
+        while (x < ma || y < mb) {
+            if (y >= mb || (x < ma && a[x] < b[y])) { ++only; ++x; }
+            else if (x >= ma || b[y] < a[x]) { ++only; ++y; }
+            else { ++x; ++y; }
+        }
+        cmp[0] += 1;
+        cmp[1] += ma;
+        cmp[2] += only;
+        cmp[3] += only > 0;
+    }
+    free(a);
+    free(b);
     return 0;
 }
 

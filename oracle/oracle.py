@@ -74,6 +74,17 @@ def lib():
                                                      ctypes.c_float, i64p, ctypes.c_int64] + \
                 [f32p] * 6 + [ctypes.c_int64, ctypes.c_int32] + [ctypes.c_int64] * 3
             L.oracle_count_through_voxel.restype = ctypes.c_int64
+            f64p = ctypes.POINTER(ctypes.c_double)
+            L.oracle_grid_endpoints_fp64.argtypes = [ctypes.c_void_p] + [ctypes.c_float] * 5 + \
+                [f64p, f64p]
+            L.oracle_grid_endpoints_fp64.restype = ctypes.c_int
+            L.oracle_voxel_set_fp64.argtypes = [f64p, f64p, ctypes.c_int32, ctypes.c_int32,
+                                                ctypes.c_int32, i64p, ctypes.c_int64]
+            L.oracle_voxel_set_fp64.restype = ctypes.c_int64
+            L.oracle_compare_fp64.argtypes = [ctypes.c_void_p, ctypes.c_float, ctypes.c_float,
+                                              ctypes.c_int32, i64p, ctypes.c_int64] + \
+                [f32p] * 6 + [ctypes.c_int64, u32p, u32p, i64p]
+            L.oracle_compare_fp64.restype = ctypes.c_int
             _lib = L
     return _lib
 
@@ -335,4 +346,85 @@ def run(g, hist, params: Params = Params(), threads: Optional[int] = 1) -> Dict:
     out["H2"] = msc_decide(acc["N"], dims, params.nt, params.nbhd)
     sm = sm_decide(acc["M"], dims, params.sm_per_slice, params.nbhd, params.sm_ge)
     out.update(sm)
+    return out
+
+
+# ------------------------------------------- FP64 geometry (reported only)
+def grid_endpoints_fp64(g, angle, u_in, v_in, u_out, v_out):
+    """(rejected, gin, gout) with unquantised FP64 geometry (voxel units)."""
+    gin = np.zeros(3, np.float64)
+    gout = np.zeros(3, np.float64)
+    og = _ogeom(g)
+    r = lib().oracle_grid_endpoints_fp64(ctypes.byref(og), float(angle), float(u_in),
+                                         float(v_in), float(u_out), float(v_out),
+                                         _p(gin, ctypes.c_double), _p(gout, ctypes.c_double))
+    return bool(r), gin, gout
+
+
+def voxel_set_fp64(gin, gout, nx: int, ny: int, nz: int) -> np.ndarray:
+    gin = np.ascontiguousarray(gin, np.float64)
+    gout = np.ascontiguousarray(gout, np.float64)
+    cap = nx + ny + nz + 8
+    out = np.zeros(cap, np.int64)
+    m = lib().oracle_voxel_set_fp64(_p(gin, ctypes.c_double), _p(gout, ctypes.c_double),
+                                    nx, ny, nz, _p(out, ctypes.c_int64), cap)
+    if m < 0 or m > cap:
+        raise MemoryError("oracle_voxel_set_fp64")
+    return out[:m].copy()
+
+
+def _compare_into(g, hist, s, e, params, N64, M64, cmp):
+    th, K = _table_arrays()
+    arrs = [np.ascontiguousarray(a[s:e], dtype=np.float32) for a in hist.arrays()]
+    og = _ogeom(g)
+    r = lib().oracle_compare_fp64(ctypes.byref(og), params.tau_l, params.tau_h, params.methods,
+                                  _p(th, ctypes.c_int64), K,
+                                  *[_p(a, ctypes.c_float) for a in arrs], e - s,
+                                  _p(N64, ctypes.c_uint32), _p(M64, ctypes.c_uint32),
+                                  _p(cmp, ctypes.c_int64))
+    if r != 0:
+        raise MemoryError("oracle_compare_fp64")
+
+
+def compare_fp64(g, hist, params: Params = Params(), threads: Optional[int] = None,
+                 fixed: Optional[Dict] = None) -> Dict:
+    """How much the fixed-point geometry changes the result against the
+    same set definition on FP64 geometry (reported, not a parity check):
+    the fraction of voxel memberships in exactly one of the two sets, the
+    fraction of histories whose sets differ, and the fraction of voxels whose
+    H_1, H_2 or H_3 decision differs.  `fixed` may pass the fixed-point
+    result (oracle.run or the GPU's) to skip recomputing it."""
+    n = len(hist)
+    threads = threads or os.cpu_count() or 1
+    threads = max(1, min(threads, n // 1000 + 1))
+    V = g.nx * g.ny * g.nz
+    bounds = np.linspace(0, n, threads + 1).astype(np.int64)
+    parts = [(np.zeros(V, np.uint32), np.zeros(V, np.uint32), np.zeros(8, np.int64))
+             for _ in range(threads)]
+    ths = [threading.Thread(target=_compare_into,
+                            args=(g, hist, int(bounds[t]), int(bounds[t + 1]), params) + parts[t])
+           for t in range(threads)]
+    for t in ths:
+        t.start()
+    for t in ths:
+        t.join()
+    N64 = sum(p[0] for p in parts)
+    M64 = sum(p[1] for p in parts)
+    cmp = sum(p[2] for p in parts)
+    if fixed is None:
+        fixed = run(g, hist, params, threads=threads)
+    dims = (g.nx, g.ny, g.nz)
+    H1 = sc_from_counts(N64)
+    H2 = msc_decide(N64, dims, params.nt, params.nbhd)
+    H3 = sm_decide(M64, dims, params.sm_per_slice, params.nbhd, params.sm_ge)["H3"]
+    out = {"histories": int(cmp[0]), "memberships": int(cmp[1]),
+           "membership_diff": int(cmp[2]),
+           "membership_diff_frac": float(cmp[2]) / max(1, int(cmp[1])),
+           "histories_differing_frac": float(cmp[3]) / max(1, int(cmp[0])),
+           "histories_one_geometry_only": int(cmp[4]), "voxels": V}
+    for k, h in (("H1", H1), ("H2", H2), ("H3", H3)):
+        ref = np.asarray(fixed[k])
+        d = int(np.count_nonzero(ref != h))
+        out[f"{k}_voxels_differing"] = d
+        out[f"{k}_diff_frac_of_hull"] = d / max(1, int(np.count_nonzero(ref)))
     return out

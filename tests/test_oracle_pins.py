@@ -371,3 +371,50 @@ def test_sc_hull_contains_deep_object_voxels(oracle_mod):
     assert keep.sum() > 1000
     assert np.all(r["H1"][keep] == 1)
     assert np.all(r["H2"][keep] == 1)
+
+
+# ----------------------------------------- FP64 geometry (reported, not gated)
+def test_fp64_voxel_set_equals_exact_set_on_generic_segments(oracle_mod):
+    """The FP64 statement of the set equals the exact rational one when the
+    endpoints are exactly representable and the segment hits no edge or
+    corner: generic Q16 endpoints agree in all but rare cases, and the rare
+    ones differ by a voxel or two (a crossing within rounding of another)."""
+    rng = np.random.default_rng(71)
+    for dims in [(40, 30, 20), (64, 64, 8), (7, 1, 3)]:
+        hi = np.array(dims) * Q
+        same = 0
+        trials = 3000
+        for _ in range(trials):
+            a = rng.integers(-Q, hi + Q)
+            b = rng.integers(-Q, hi + Q)
+            exact = oracle_mod.voxel_set(a, b, *dims)
+            fp = oracle_mod.voxel_set_fp64(a / Q, b / Q, *dims)
+            if np.array_equal(exact, fp):
+                same += 1
+            else:
+                assert len(np.setxor1d(exact, fp)) <= 2
+        assert same >= 0.995 * trials
+
+
+def test_fp64_endpoints_close_to_fixed_point(oracle_mod):
+    """Unquantised FP64 endpoints and the fixed-point ones differ by the
+    quantisation only (Q16 rounding of u, v, T and the CORDIC's 2^-27)."""
+    rng = np.random.default_rng(72)
+    g = synth.geometry_for(2)
+    h = synth.tiny_random_case(rng, 2000, g, span=1.2)
+    for i in range(len(h)):
+        args = [float(x[i]) for x in h.arrays()[:5]]
+        rq, gin, gout = oracle_mod.grid_endpoints(g, *args)
+        rf, fin, fout = oracle_mod.grid_endpoints_fp64(g, *args)
+        assert rq == rf
+        if not rq:
+            assert np.max(np.abs(np.asarray(gin) / Q - fin)) < 1e-3
+            assert np.max(np.abs(np.asarray(gout) / Q - fout)) < 1e-3
+
+
+def test_fp64_comparison_reports_small_differences(oracle_mod):
+    w = synth.make_config(1, fraction=0.2)
+    r = oracle_mod.compare_fp64(w.geometry, w.histories, threads=4)
+    assert r["histories"] > 30000 and r["histories_one_geometry_only"] == 0
+    assert r["membership_diff_frac"] < 1e-3
+    assert r["H1_diff_frac_of_hull"] < 1e-2 and r["H3_diff_frac_of_hull"] < 1e-2
