@@ -585,6 +585,27 @@ def main():
                 "ops_per_voxel_step": OPS_PER_STEP, "voxel_steps_per_launch": steps_per_scan,
                 "peak_source": f"152 SMs x 128 INT32 lanes x {peaks['sm_max_mhz']:.0f} MHz "
                                f"({peaks['source']} max clock)"}
+    # the traversal against the measured atomic ceilings: a design spending
+    # one shared-memory atomic per voxel-step is bounded by the random-address
+    # probe; this one spends two per run of several voxels
+    runs = st.get("runs", 0)
+    probes = {name: hulld.hd_probe_atomics(kind) for name, kind in
+              [("smem_random", hulld.HD_PROBE_SMEM_RANDOM),
+               ("smem_coherent", hulld.HD_PROBE_SMEM_COHERENT),
+               ("l2_random", hulld.HD_PROBE_L2_RANDOM),
+               ("hbm_random", hulld.HD_PROBE_HBM_RANDOM)]}
+    vsteps = steps_per_scan / (trace_ms * 1e-3)
+    atomic_roofline = {
+        "ceilings_atomics_per_s": probes,
+        "voxel_steps_per_s": vsteps,
+        "voxel_steps_over_smem_random_ceiling": vsteps / probes["smem_random"],
+        "runs_per_scan": runs,
+        "voxels_per_run": steps_per_scan / runs if runs else None,
+        "trace_smem_atomics_per_s": 2.0 * runs / (trace_ms * 1e-3),
+        "trace_smem_atomics_over_smem_random_ceiling":
+            2.0 * runs / (trace_ms * 1e-3) / probes["smem_random"],
+        "probe": "hd_probe_atomics: 1024-thread blocks, xorshift addresses, best of 3"}
+
     # prepare = ingest + plan + scatter (everything before the traversal)
     phases = {"prepare_ms": prof["ms_ingest"] / args.steps, "trace_ms": trace_ms,
               "trace_global_ms": prof["ms_trace_global"] / args.steps,
@@ -653,7 +674,8 @@ def main():
                 "voxel_steps_per_s": ws * steps_per_scan / (ms * 1e-3),
                 "voxel_steps_per_scan": steps_per_scan,
                 "per_method": per_method, "phases": phases,
-                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+                "roofline": roofline, "atomic_roofline": atomic_roofline,
+                "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": launches, "clocks": clocks}
         print(json.dumps(line), flush=True)
     scan.close()

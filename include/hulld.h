@@ -121,6 +121,9 @@ typedef struct {
     int64_t pairs_general; /* (history, tile) pairs of the tiled pass whose walk has a tie
                               or crosses z inside the tile, walked by the general run walk
                               in global memory instead of the closed-form lean walk */
+    int64_t runs;          /* major-axis runs walked by the lean walks of the tiled pass
+                              (each adds +1 and -1 to a difference array: two
+                              shared-memory atomics in count mode) */
 } hd_stats;
 
 /* Kernel-level timing of a scan (enabled by hd_scan_set_profiling):
@@ -423,6 +426,22 @@ HD_API hd_status hd_server_get_stats(hd_server *server, hd_server_stats *out);
 
 /* Release a scan that is finished (or has no chunk in flight). */
 HD_API hd_status hd_server_close_scan(hd_server *server, int64_t scan_id);
+
+/* Atomic-throughput probe: the rate a traversal spending one atomic per
+ * voxel-step could reach, measured by kernels that do nothing else (a
+ * measurement aid for the roofline; the paper has no counterpart).
+ *   HD_PROBE_SMEM_RANDOM    shared-memory atomicAdd to uniformly random words
+ *                           of a 128 KB array, one 1024-thread block per SM
+ *   HD_PROBE_SMEM_COHERENT  the same with a warp's lanes on consecutive words
+ *   HD_PROBE_L2_RANDOM      global atomicAdd to random words of a 16 MB
+ *                           (L2-resident) array
+ *   HD_PROBE_HBM_RANDOM     the same over a 2 GB array
+ * *ops_per_s = atomics per second, the best of three timed launches after a
+ * warm-up.  Allocates and frees its own buffers and synchronises the calling
+ * thread; call it outside any stream capture. */
+enum { HD_PROBE_SMEM_RANDOM = 0, HD_PROBE_SMEM_COHERENT = 1, HD_PROBE_L2_RANDOM = 2,
+       HD_PROBE_HBM_RANDOM = 3 };
+HD_API hd_status hd_probe_atomics(int32_t kind, double *ops_per_s);
 
 /* Allocation-free accumulation of path counts, for callers that cannot
  * allocate device memory when they run it (inside a stream capture that must

@@ -795,6 +795,7 @@ hd_status hd_scan_get_stats(hd_scan *scan, hd_stats *out, void *stream)
     out->steps_miss = static_cast<int64_t>(c.steps_miss);
     out->steps_hit = static_cast<int64_t>(c.steps_hit);
     out->pairs_general = static_cast<int64_t>(c.pairs_general);
+    out->runs = static_cast<int64_t>(c.runs);
     return HD_OK;
 }
 

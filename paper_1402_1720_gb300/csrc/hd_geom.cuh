@@ -826,7 +826,7 @@ HD_HD bool lean_empty(const LeanWalk &L) { return (L.fl >> 3) & 1; }
 // increments so that a run costs a few integer operations.
 struct LeanCursor {
     unsigned ad, Ru, rem;  // as in LeanWalk
-    int jn, Qu, kmz, kleft, K;
+    int jn, Qu, kmz, kleft;
     int im0, sg;  // major index of the first voxel, major direction (+1 or -1)
     int ms;       // major index where the current run starts
     int rb;       // row * nmaj of the current run
@@ -844,8 +844,7 @@ HD_HD bool lean_start(const uint32_t o[kLeanWords], int nmaj, LeanCursor &c)
     c.jn = static_cast<int>(o[3] & 0xffffu);
     c.Qu = static_cast<int>(o[3] >> 16);
     c.kmz = static_cast<int>(o[4] & 0xffffu);
-    c.K = static_cast<int>(o[4] >> 16);
-    c.kleft = c.K;
+    c.kleft = static_cast<int>(o[4] >> 16);
     c.im0 = static_cast<int>(o[5] & 0xffffu);
     c.sg = (fl & 1) ? 1 : -1;
     c.ms = c.im0;
@@ -855,10 +854,12 @@ HD_HD bool lean_start(const uint32_t o[kLeanWords], int nmaj, LeanCursor &c)
 }
 
 // The current run: *rb its row offset, lo..hi its major range (inclusive).
-// Returns whether more runs follow; with the last one it adds the walk's
-// voxel count to `steps` (see lean_step).  Branch-free: the cursor also
-// advances past the last run, where it is not used again.
-HD_HD bool lean_run(LeanCursor &c, int &rb, int &lo, int &hi, unsigned &steps)
+// Returns whether more runs follow.  With the last run it adds e (the major
+// count where the walk ends) to `ends`: the walk's voxel count is e plus its
+// number of runs (see lean_step), so a caller that counts the runs gets the
+// voxels as runs + ends.  Branch-free: the cursor also advances past the
+// last run, where it is not used again.
+HD_HD bool lean_run(LeanCursor &c, int &rb, int &lo, int &hi, unsigned &ends)
 {
     const int jn = c.jn;
     const int e = jn < c.kmz ? jn : c.kmz;
@@ -867,7 +868,7 @@ HD_HD bool lean_run(LeanCursor &c, int &rb, int &lo, int &hi, unsigned &steps)
     hi = c.ms < b ? b : c.ms;
     rb = c.rb;
     const bool last = c.kleft == 0 || jn > c.kmz;
-    steps += last ? static_cast<unsigned>(e + (c.K - c.kleft) + 1) : 0u;
+    ends += last ? static_cast<unsigned>(e) : 0u;
     c.ms = b;  // before the last run e = jn: the next run starts where this one ends
     const unsigned rem = c.rem + c.Ru;
     const bool carry = rem >= c.ad;

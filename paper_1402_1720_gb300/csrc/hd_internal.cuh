@@ -36,6 +36,7 @@ struct Ctrl {
     unsigned long long n_in, n_miss, n_hit, n_none, n_reject;
     unsigned long long steps_miss, steps_hit;
     unsigned long long pairs_general;  // pairs sent to the fallback list (cumulative)
+    unsigned long long runs;           // runs walked by the tiled pass (cumulative)
     unsigned int rec_miss;    // records appended from the front of the list
     unsigned int rec_hit;     // records appended from the back of the list
     unsigned int pairs_used;  // (record, tile) pairs admitted to the tiled path

@@ -297,11 +297,12 @@ __device__ __forceinline__ void rows_prefix(int16_t *a, int rows, int len)
 // and -1 just past its last one in the int16 difference arrays (x runs at
 // word 0, y runs at word arr_words; the -1 of a run that ends at its row's
 // end goes to the scratch word 2 arr_words); carve mode clears the run's
-// bits.  Returns the lane's voxel count.
+// bits.  Adds the lane's runs to `runs` and returns the sum of its walks'
+// end counts (voxels = runs + ends, see lean_run).
 template <bool kCarve>
 __device__ __forceinline__ unsigned walk_job(uint32_t *tile, int arr_words, int dx, int dy,
                                              const Pairs &pairs, int start, int total, int refill,
-                                             unsigned *s_next)
+                                             unsigned *s_next, unsigned &runs)
 {
     const unsigned lane = threadIdx.x & 31u;
     const int scratch = 2 * arr_words;
@@ -309,7 +310,7 @@ __device__ __forceinline__ unsigned walk_job(uint32_t *tile, int arr_words, int 
     bool active = false;
     int nmaj = 0;
     int aoff = 0;  // word offset in `tile` of the current walk's array
-    unsigned steps = 0;
+    unsigned ends = 0;
     uint4 na = make_uint4(0, 0, 0, 0), nb = na;
     int nidx = -1;
     {
@@ -350,7 +351,8 @@ __device__ __forceinline__ unsigned walk_job(uint32_t *tile, int arr_words, int 
         }
         if (active) {
             int rb, lo, hi;
-            active = lean_run(c, rb, lo, hi, steps);
+            active = lean_run(c, rb, lo, hi, ends);
+            ++runs;
             if (!kCarve) {
                 const int e0 = rb + lo, e1 = rb + hi + 1;
                 atomicAdd(&tile[aoff + (e0 >> 1)], (e0 & 1) ? 65536u : 1u);
@@ -361,7 +363,7 @@ __device__ __forceinline__ unsigned walk_job(uint32_t *tile, int arr_words, int 
             }
         }
     }
-    return steps;
+    return ends;
 }
 
 template <int kThreads>
@@ -420,9 +422,12 @@ __global__ void __launch_bounds__(kThreads, 1) trace_tiles_kernel(
         __syncthreads();
 
         const int total = job.end - job.start;
-        const unsigned steps =
-            carve_mode ? walk_job<true>(tile, arr_words, dx, dy, pairs, job.start, total, tp.refill, &s_next)
-                       : walk_job<false>(tile, arr_words, dx, dy, pairs, job.start, total, tp.refill, &s_next);
+        unsigned runs = 0;
+        const unsigned ends =
+            carve_mode ? walk_job<true>(tile, arr_words, dx, dy, pairs, job.start, total, tp.refill,
+                                        &s_next, runs)
+                       : walk_job<false>(tile, arr_words, dx, dy, pairs, job.start, total, tp.refill,
+                                         &s_next, runs);
         __syncthreads();
         uint32_t *vol = job.cls == 0 ? N : M;
         if (!carve_mode) {
@@ -467,10 +472,14 @@ __global__ void __launch_bounds__(kThreads, 1) trace_tiles_kernel(
             }
         }
         // voxel memberships of this job, added to its scan's counters
-        unsigned long long st = steps;
+        unsigned long long ru = runs, st = static_cast<unsigned long long>(ends) + runs;
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) st += __shfl_xor_sync(kFull, st, o);
+        for (int o = 16; o > 0; o >>= 1) {
+            st += __shfl_xor_sync(kFull, st, o);
+            ru += __shfl_xor_sync(kFull, ru, o);
+        }
         if (lane == 0 && st) atomicAdd(job.cls == 0 ? &d.ctrl->steps_miss : &d.ctrl->steps_hit, st);
+        if (lane == 0 && ru) atomicAdd(&d.ctrl->runs, ru);
         __syncthreads();
     }
 }

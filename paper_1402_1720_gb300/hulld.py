@@ -53,7 +53,7 @@ class hd_stats(ctypes.Structure):
     _fields_ = [("n_in", ctypes.c_int64), ("n_miss", ctypes.c_int64), ("n_hit", ctypes.c_int64),
                 ("n_none", ctypes.c_int64), ("n_reject", ctypes.c_int64),
                 ("steps_miss", ctypes.c_int64), ("steps_hit", ctypes.c_int64),
-                ("pairs_general", ctypes.c_int64)]
+                ("pairs_general", ctypes.c_int64), ("runs", ctypes.c_int64)]
 
     def as_dict(self):
         return {k: int(getattr(self, k)) for k, _ in self._fields_}
@@ -128,6 +128,7 @@ _SIGS = {
     "hd_scan_destroy": ([_VP], ctypes.c_int),
     "hd_scan_reset": ([_VP, _VP], ctypes.c_int),
     "hd_scan_reserve": ([_VP, _I64, _VP], ctypes.c_int),
+    "hd_probe_atomics": ([_I32, ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
     "hd_scan_add_histories": ([_VP] + [_VP] * 6 + [_I64, _I32, _VP], ctypes.c_int),
     "hd_scan_finalize": ([_VP, _VP], ctypes.c_int),
     "hd_scan_get_mask": ([_VP, _I32, _I32, _VP, _SZ, _I32, _VP], ctypes.c_int),
@@ -274,6 +275,16 @@ def hd_scan_destroy(scan: int) -> None:
 
 def hd_scan_reset(scan: int, stream=None) -> None:
     _check(load().hd_scan_reset(scan, _stream(stream)), "hd_scan_reset")
+
+
+HD_PROBE_SMEM_RANDOM, HD_PROBE_SMEM_COHERENT, HD_PROBE_L2_RANDOM, HD_PROBE_HBM_RANDOM = 0, 1, 2, 3
+
+
+def hd_probe_atomics(kind: int) -> float:
+    """Atomics per second of one probe kind (see include/hulld.h)."""
+    out = ctypes.c_double(0.0)
+    _check(load().hd_probe_atomics(int(kind), ctypes.byref(out)), "hd_probe_atomics")
+    return out.value
 
 
 def hd_scan_reserve(scan: int, n: int, stream=None) -> None:

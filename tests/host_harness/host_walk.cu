@@ -135,16 +135,17 @@ extern "C" int hx_runs_lean(const int32_t *gi, const int32_t *go, int nx, int ny
         // the kernel's cursor form must give the same runs as lean_step
         hd::LeanCursor c;
         if (!hd::lean_start(o, nmaj, c)) return -3000000;
-        unsigned steps_c = 0;
+        unsigned ends = 0, runs_c = 0;
         int row, lo, hi, rb, lo_c, hi_c;
         bool more;
         do {
             more = hd::lean_step(L, row, lo, hi, *steps);
-            const bool more_c = hd::lean_run(c, rb, lo_c, hi_c, steps_c);
+            const bool more_c = hd::lean_run(c, rb, lo_c, hi_c, ends);
+            ++runs_c;
             if (more_c != more || rb != row * nmaj || lo_c != lo || hi_c != hi) return -4000000;
             if (!emit(ymaj, nmaj, row, lo, hi)) return -1000000;
         } while (more);
-        if (steps_c != *steps) return -4000000;
+        if (ends + runs_c != *steps) return -4000000;  // voxels = runs + end count
         return n;
     }
     const bool ymaj = (w.flags >> 5) & 1;

@@ -515,3 +515,19 @@ def test_host_inputs_equal_device_inputs(hd):
             st = s.stats()
             for k in ("n_in", "n_miss", "n_hit", "steps_miss", "steps_hit"):
                 assert st[k] == ref_st[k], k
+
+
+def test_atomic_probe_and_run_count(hd):
+    """The atomic-throughput probe returns a rate for every kind, and the run
+    count of a scan is consistent with its voxel count (each run covers at
+    least one voxel, and a walk of L voxels has at most L runs)."""
+    rates = [hd.hd_probe_atomics(k) for k in (hd.HD_PROBE_SMEM_RANDOM, hd.HD_PROBE_SMEM_COHERENT,
+                                              hd.HD_PROBE_L2_RANDOM, hd.HD_PROBE_HBM_RANDOM)]
+    assert all(r > 1e8 for r in rates)
+    with pytest.raises(hd.HDError):
+        hd.hd_probe_atomics(7)
+    w = synth.make_config(1, fraction=0.2)
+    got = _run_gpu(hd, w.geometry, w.histories)
+    st = got["stats"]
+    steps = st["steps_miss"] + st["steps_hit"]
+    assert 0 < st["runs"] <= steps
