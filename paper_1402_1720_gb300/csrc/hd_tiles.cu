@@ -19,7 +19,7 @@ namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kScatterThreads = 256;
-constexpr int kScatterPerThread = 16;  // most records a scatter thread takes
+constexpr int kScatterPerThread = 8;  // most records a scatter thread takes
 
 __device__ __forceinline__ unsigned warp_incl_scan_u(unsigned v)
 {
@@ -107,7 +107,7 @@ __global__ void __launch_bounds__(1024) plan_kernel(TilePlan tp, const uint32_t 
 // Counting sort of (record, tile) pairs by tile.  Each block takes a range
 // of record slots, histograms its pairs, reserves one range per tile with a
 // single global atomic, then writes its pairs.
-__global__ void __launch_bounds__(kScatterThreads, 3) scatter_kernel(TilePlan tp, Records rec,
+__global__ void __launch_bounds__(kScatterThreads, 4) scatter_kernel(TilePlan tp, Records rec,
                                                                   Ctrl *ctrl,
                                                                   uint32_t *tile_cursor,
                                                                   Pairs pairs, int per_thread)

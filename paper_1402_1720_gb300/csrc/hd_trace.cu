@@ -40,6 +40,15 @@ struct LaneAcc {
 // Returns 1 (missed record), 2 (hit record) or 0 (nothing to traverse).
 // cos/sin of the last gantry angle a lane quantised (histories arrive
 // grouped by angle, so consecutive ones usually share it).
+// cos/sin of a gantry angle, kept out of line: it runs about once per
+// thread and grid-stride step (histories arrive grouped by angle), and
+// inlining its 32 unrolled iterations into each of the four history slots
+// costs more in instruction fetch than the call.
+__device__ __noinline__ void trig_refresh(float ang, const Cordic &cd, long long &c, long long &s)
+{
+    cordic_cs(q16_of(ang), cd, c, s);
+}
+
 struct TrigCache {
     bool valid = false;
     float ang = 0.0f;
@@ -66,7 +75,7 @@ __device__ __forceinline__ int ingest_one(const GeomQ &g, const Cordic &cd, floa
     bool ok = fabsf(ang) < 1048576.0f;
     if (ok) {
         if (!tc.valid || ang != tc.ang) {
-            cordic_cs(q16_of(ang), cd, tc.c, tc.s);
+            trig_refresh(ang, cd, tc.c, tc.s);
             tc.ang = ang;
             tc.valid = true;
         }
@@ -168,7 +177,7 @@ __device__ __forceinline__ void admit_and_append(const TilePlan &tp, const Recor
 }
 
 template <bool kVec>
-__global__ void __launch_bounds__(256) ingest_kernel(Inputs in, int64_t n, GeomQ g, Cordic cd,
+__global__ void __launch_bounds__(256, 4) ingest_kernel(Inputs in, int64_t n, GeomQ g, Cordic cd,
                                                      float tau_l, float tau_h, int use_miss,
                                                      int use_hit, TilePlan tp, Records rec,
                                                      Ctrl *ctrl, uint32_t *tile_count)
