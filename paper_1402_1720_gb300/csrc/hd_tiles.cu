@@ -20,6 +20,7 @@ namespace {
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kScatterThreads = 256;
 constexpr int kScatterPerThread = 8;  // most records a scatter thread takes
+constexpr int kRunsPerStep = 4;       // runs a traversal lane walks between refill checks
 
 __device__ __forceinline__ unsigned warp_incl_scan_u(unsigned v)
 {
@@ -350,16 +351,22 @@ __device__ __forceinline__ unsigned walk_job(uint32_t *tile, int arr_words, int 
             continue;
         }
         if (active) {
-            int rb, lo, hi;
-            active = lean_run(c, rb, lo, hi, ends);
-            ++runs;
-            if (!kCarve) {
-                const int e0 = rb + lo, e1 = rb + hi + 1;
-                atomicAdd(&tile[aoff + (e0 >> 1)], (e0 & 1) ? 65536u : 1u);
-                atomicAdd(&tile[hi + 1 < nmaj ? aoff + (e1 >> 1) : scratch],
-                          (e1 & 1) ? 0xffff0000u : 0xffffffffu);
-            } else {
-                bits_clear(tile + aoff, rb + lo, rb + hi);
+            // up to kRunsPerStep runs before the warp checks for refills again
+            // (the refill test costs as much as a run)
+#pragma unroll
+            for (int u = 0; u < kRunsPerStep; ++u) {
+                int rb, lo, hi;
+                active = lean_run(c, rb, lo, hi, ends);
+                ++runs;
+                if (!kCarve) {
+                    const int e0 = rb + lo, e1 = rb + hi + 1;
+                    atomicAdd(&tile[aoff + (e0 >> 1)], (e0 & 1) ? 65536u : 1u);
+                    atomicAdd(&tile[hi + 1 < nmaj ? aoff + (e1 >> 1) : scratch],
+                              (e1 & 1) ? 0xffff0000u : 0xffffffffu);
+                } else {
+                    bits_clear(tile + aoff, rb + lo, rb + hi);
+                }
+                if (!active) break;
             }
         }
     }
