@@ -414,10 +414,8 @@ hd_status stage_prepare(hd_scan *s, const hd::Inputs &in, int64_t n, cudaStream_
 // Records outside the tiled path, walked with global-memory updates.
 hd_status stage_global(hd_scan *s, int64_t n, cudaStream_t st)
 {
-    hd::Pairs pairs = pairs_of(s);
-    if (s->tp.ntiles <= 0 || s->trace_grid <= 0) pairs.fb = nullptr;  // no tiled pass
     HD_CUDA(hd::launch_trace_global(records_of(s, n), s->ctrl, n, s->gq, s->N, s->M, s->carve,
-                                    0, s->tp, pairs, s->sm_count, st));
+                                    0, s->sm_count, st));
     s->launches += 1;
     return HD_OK;
 }

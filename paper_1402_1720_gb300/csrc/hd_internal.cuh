@@ -44,6 +44,7 @@ struct Ctrl {
     int job_next;             // next job to hand out
     unsigned int n_fallback;  // records traversed by the global-memory path
     unsigned int n_pair_fallback;  // entries of the pair fallback list
+    unsigned int fb_next;          // next fallback entry to hand out
 };
 
 // Compacted traversal records: grid Q16 entry and exit points, int32 each
@@ -73,12 +74,13 @@ struct TilePlan {
 // (record, tile) pairs sorted by tile: the packed lean walk of the record
 // clipped to the tile, 32 bytes per pair (two uint4: one 32-byte sector;
 // class and tile come from the job).  A pair whose walk has no lean form
-// (a tie, a pending start, or a z crossing inside the tile) leaves an empty
-// walk in its place and goes to the fallback list, which the global-memory
-// traversal walks with the general run walk.
+// (a tie, a pending start, or a z crossing inside the tile) holds instead
+// its tile-local endpoints, tile and class, marked empty for the lean pass,
+// and its position goes to the fallback list; traversal blocks that run out
+// of jobs walk those with the general run walk in global memory.
 struct Pairs {
     uint4 *v;   // 2 per pair
-    uint2 *fb;  // fallback list: (record slot, 2 tile + class), pair_cap entries
+    uint2 *fb;  // fallback list: (pair position, 0), pair_cap entries
 };
 
 struct TileJob {
@@ -125,12 +127,10 @@ cudaError_t launch_trace_tiles(const ScanDesc *descs, int nscans, int *job_count
                                int smem_words, int threads, int grid, cudaStream_t s);
 
 // Global-memory traversal of the records whose status is 2 (or of every
-// record when all_records is set), then of the pair fallback list when
-// pairs.fb is set (each entry: the record clipped to its tile of tp).
+// record when all_records is set).
 cudaError_t launch_trace_global(const Records &rec, Ctrl *ctrl, int64_t upper, const GeomQ &g,
                                 uint32_t *N, uint32_t *M, uint32_t *carve, int all_records,
-                                const TilePlan &tp, const Pairs &pairs, int sm_count,
-                                cudaStream_t s);
+                                int sm_count, cudaStream_t s);
 
 cudaError_t launch_classify(const float *wepl, int64_t n, float tau_l, float tau_h,
                             uint8_t *cls, cudaStream_t s);

@@ -9,7 +9,7 @@
 //   trace    persistent blocks take jobs; warps refill idle lanes from the
 //            job's pair range, so lanes do not wait for the longest path
 #include <cooperative_groups.h>
-#include "hd_geom.cuh"
+#include "hd_fallback.cuh"
 
 namespace cg = cooperative_groups;
 
@@ -182,7 +182,6 @@ __global__ void __launch_bounds__(kScatterThreads, 4) scatter_kernel(TilePlan tp
             const int oex = __shfl_sync(kFull, ex, own), oey = __shfl_sync(kFull, ey, own);
             const int ocls = __shfl_sync(kFull, cls, own);
             if (p >= total) continue;
-            const int64_t oslot = slot - lane + own;
             // the j-th tile of the owner's box, x fastest
             int x = lx, y = ly, z = lz + j;
             if (oex != 1 || oey != 1) {
@@ -207,7 +206,8 @@ __global__ void __launch_bounds__(kScatterThreads, 4) scatter_kernel(TilePlan tp
             } else if (lean_of(w, L)) {
                 lean_pack(L, pk);
             } else {
-                lean_pack_empty(pk);  // walked from the fallback list instead
+                // walked from the fallback list by the general run walk
+                general_pack(gi, go, t - ocls * tp.ntiles, ocls, pk);
                 fallback = true;
             }
             pairs.v[2 * static_cast<size_t>(pos)] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
@@ -222,9 +222,7 @@ __global__ void __launch_bounds__(kScatterThreads, 4) scatter_kernel(TilePlan tp
                     atomicAdd(&ctrl->pairs_general, static_cast<unsigned long long>(grp.size()));
                 }
                 at = grp.shfl(at, 0) + grp.thread_rank();
-                pairs.fb[at] = make_uint2(static_cast<unsigned>(oslot),
-                                          2u * static_cast<unsigned>(t - ocls * tp.ntiles) +
-                                              static_cast<unsigned>(ocls));
+                pairs.fb[at] = make_uint2(pos, 0u);
             }
         }
     }
@@ -373,6 +371,55 @@ __device__ __forceinline__ unsigned walk_job(uint32_t *tile, int arr_words, int 
     return ends;
 }
 
+// No job left: the pairs without a lean form (the fallback lists), walked
+// with the general run walk in global memory, 32 entries per warp claim, so
+// blocks that finish their last job early take them.  Out of line, so its
+// registers do not weigh on the lean walk loop.
+__device__ __noinline__ void walk_fallback_lists(const ScanDesc *__restrict__ descs, int nscans)
+{
+    const unsigned lane = threadIdx.x & 31u;
+    for (int k = 0; k < nscans; ++k) {
+        const ScanDesc &d = descs[k];
+        const unsigned nf = d.ctrl->n_pair_fallback;
+        if (nf == 0) continue;
+        uint32_t *const N = d.N;
+        uint32_t *const M = d.M;
+        for (;;) {
+            unsigned base = 0;
+            if (lane == 0) base = atomicAdd(&d.ctrl->fb_next, 32u);
+            base = __shfl_sync(kFull, base, 0);
+            if (base >= nf) break;
+            const unsigned i = base + lane;
+            unsigned sm = 0, sh = 0;
+            if (i < nf) {
+                const uint32_t pos = d.pairs.fb[i].x;
+                uint4 a, b;
+                load_lean(d.pairs, static_cast<int>(pos), a, b);
+                const int32_t gi[3] = {static_cast<int32_t>(a.x), static_cast<int32_t>(a.y),
+                                       static_cast<int32_t>(a.z)};
+                const int32_t go[3] = {static_cast<int32_t>(a.w), static_cast<int32_t>(b.x),
+                                       static_cast<int32_t>(b.z)};
+                const bool miss = (b.w & 1u) == 0;
+                GlobalVisit v;
+                v.vol = miss ? N : M;
+                v.bits = d.carve;
+                const unsigned c = walk_tile_global(d.tp, gi, go, static_cast<int>(b.w >> 1), v);
+                sm = miss ? c : 0u;
+                sh = miss ? 0u : c;
+            }
+            unsigned long long a0 = sm, a1 = sh;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                a0 += __shfl_xor_sync(kFull, a0, o);
+                a1 += __shfl_xor_sync(kFull, a1, o);
+            }
+            if (lane == 0 && a0) atomicAdd(&d.ctrl->steps_miss, a0);
+            if (lane == 0 && a1) atomicAdd(&d.ctrl->steps_hit, a1);
+        }
+    }
+}
+}
+
 template <int kThreads>
 __global__ void __launch_bounds__(kThreads, 1) trace_tiles_kernel(
     const ScanDesc *__restrict__ descs, int nscans, int *job_counter)
@@ -489,7 +536,8 @@ __global__ void __launch_bounds__(kThreads, 1) trace_tiles_kernel(
         if (lane == 0 && ru) atomicAdd(&d.ctrl->runs, ru);
         __syncthreads();
     }
-}
+    walk_fallback_lists(descs, nscans);
+
 
 }  // namespace
 

@@ -17,7 +17,7 @@
 // just after t, so a mixed tie visits the corner voxel between the two.
 // The walk starts at the parameter where the segment enters the grid box
 // (exact rational), so voxels outside the grid cost nothing.
-#include "hd_geom.cuh"
+#include "hd_fallback.cuh"
 
 namespace hd {
 
@@ -247,57 +247,9 @@ __global__ void __launch_bounds__(256, 4) ingest_kernel(Inputs in, int64_t n, Ge
 
 // ---------------------------------------------------------------- traversal
 
-// Global-memory voxel update of one history: count (atomic add) or SC carve.
-struct GlobalVisit {
-    uint32_t *vol;   // N or M (count mode)
-    uint32_t *bits;  // carve mask (carve mode, vol == nullptr)
-    __device__ __forceinline__ void operator()(uint32_t v) const
-    {
-        if (vol != nullptr) {
-            atomicAdd(vol + v, 1u);
-        } else {
-            const uint32_t w = v >> 5, b = 1u << (v & 31u);
-            if (__ldcg(bits + w) & b) atomicAnd(bits + w, ~b);
-        }
-    }
-};
-
-// The voxels of a record clipped to one tile (a pair with no lean walk),
-// by the general run walk, visited with global indices; returns how many.
-__device__ unsigned walk_pair_global(const TilePlan &tp, const int32_t r[6], int tile,
-                                     const GlobalVisit &visit)
-{
-    const int tix = tile % tp.ntx;
-    const int tiy = (tile / tp.ntx) % tp.nty;
-    const int tiz = tile / (tp.ntx * tp.nty);
-    const int x0 = tix * tp.tx, y0 = tiy * tp.ty, z0 = tiz * tp.tz;
-    const int dx = min(tp.tx, tp.nx - x0), dy = min(tp.ty, tp.ny - y0), dz = min(tp.tz, tp.nz - z0);
-    const int32_t gi[3] = {r[0] - (x0 << 16), r[1] - (y0 << 16), r[2] - (z0 << 16)};
-    const int32_t go[3] = {r[3] - (x0 << 16), r[4] - (y0 << 16), r[5] - (z0 << 16)};
-    RunWalk w;
-    if (!run_begin(w, gi, go, dx, dy, dz)) return 0;
-    const bool ymaj = (w.flags >> 5) & 1;
-    unsigned c = 0;
-    int row, lo, hi;
-    while (run_next(w, row, lo, hi)) {
-        // x-major rows are y + dy z, y-major rows x + dx z (box-local)
-        const int ra = ymaj ? row % dx : row % dy;
-        const int lz = ymaj ? row / dx : row / dy;
-        for (int m = lo; m <= hi; ++m) {
-            const uint32_t X = static_cast<uint32_t>(x0 + (ymaj ? ra : m));
-            const uint32_t Y = static_cast<uint32_t>(y0 + (ymaj ? m : ra));
-            const uint32_t Z = static_cast<uint32_t>(z0 + lz);
-            visit(X + static_cast<uint32_t>(tp.nx) * (Y + static_cast<uint32_t>(tp.ny) * Z));
-        }
-        c += static_cast<unsigned>(hi - lo + 1);
-    }
-    return c;
-}
-
 __global__ void __launch_bounds__(256) trace_global_kernel(Records rec, Ctrl *ctrl, GeomQ g,
                                                            uint32_t *N, uint32_t *M,
-                                                           uint32_t *carve, int all_records,
-                                                           TilePlan tp, Pairs pairs)
+                                                           uint32_t *carve, int all_records)
 {
     const unsigned nm = ctrl->rec_miss, nh = ctrl->rec_hit;
     const int64_t total = static_cast<int64_t>(nm) + nh;
@@ -316,22 +268,6 @@ __global__ void __launch_bounds__(256) trace_global_kernel(Records rec, Ctrl *ct
         const unsigned c = walk_all(gi, go, g.nx, g.ny, g.nz, v);
         if (miss) steps_m += c; else steps_h += c;
         ++taken;
-    }
-    if (pairs.fb != nullptr) {
-        const int64_t nf = ctrl->n_pair_fallback;
-        for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < nf;
-             i += stride) {
-            const uint2 f = pairs.fb[i];
-            const bool miss = (f.y & 1u) == 0;
-            int32_t r[6];
-#pragma unroll
-            for (int a = 0; a < 6; ++a) r[a] = rec.g[a][f.x];
-            GlobalVisit v;
-            v.vol = miss ? N : M;
-            v.bits = carve;
-            const unsigned c = walk_pair_global(tp, r, static_cast<int>(f.y >> 1), v);
-            if (miss) steps_m += c; else steps_h += c;
-        }
     }
     const unsigned sm_ = warp_sum_u32(steps_m), sh_ = warp_sum_u32(steps_h);
     const unsigned tk = warp_sum_u32(taken);
@@ -382,15 +318,14 @@ cudaError_t launch_ingest(const Inputs &in, int64_t n, const GeomQ &g, const Cor
 
 cudaError_t launch_trace_global(const Records &rec, Ctrl *ctrl, int64_t upper, const GeomQ &g,
                                 uint32_t *N, uint32_t *M, uint32_t *carve, int all_records,
-                                const TilePlan &tp, const Pairs &pairs, int sm_count,
-                                cudaStream_t s)
+                                int sm_count, cudaStream_t s)
 {
     if (upper <= 0) return cudaSuccess;
     int64_t blocks = (upper + 255) / 256;
     const int64_t cap_blocks = static_cast<int64_t>(sm_count) * 8;
     if (blocks > cap_blocks) blocks = cap_blocks;
     trace_global_kernel<<<static_cast<unsigned>(blocks), 256, 0, s>>>(rec, ctrl, g, N, M, carve,
-                                                                       all_records, tp, pairs);
+                                                                       all_records);
     return cudaGetLastError();
 }
 
