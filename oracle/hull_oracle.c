@@ -354,6 +354,98 @@ int oracle_accumulate(const og_geom *g, float tau_l, float tau_h, int32_t method
     return 0;
 }
 
+/* ------------------------- hull-restricted system-matrix rows (next row f1) */
+
+/* The voxels of A_i in the order the path meets them (increasing t): the
+ * voxel at each crossing parameter and at each midpoint between two, in
+ * parameter order, repeats dropped (a straight segment meets a convex voxel
+ * in one parameter interval, so a voxel's candidates are consecutive).
+ * Writes at most `cap` indices; returns the count, or -1 when out of memory. */
+int64_t oracle_voxel_path(const int64_t *gin, const int64_t *gout, int32_t nx, int32_t ny,
+                          int32_t nz, int64_t *out, int64_t cap)
+{
+    const int32_t n[3] = {nx, ny, nz};
+    int64_t d[3];
+    int64_t maxbp = 2;
+    for (int a = 0; a < 3; ++a) {
+        d[a] = gout[a] - gin[a];
+        maxbp += (int64_t)n[a] + 1;
+    }
+    rat *bp = (rat *)malloc(sizeof(rat) * (size_t)maxbp);
+    if (!bp) return -1;
+    int64_t nb = 0;
+    bp[nb].p = 0; bp[nb].q = 1; ++nb;
+    bp[nb].p = 1; bp[nb].q = 1; ++nb;
+    for (int a = 0; a < 3; ++a) {
+        if (d[a] == 0) continue;
+        for (int64_t k = 0; k <= n[a]; ++k) {
+            i128 p = (i128)(k * Q16 - gin[a]);
+            i128 q = (i128)d[a];
+            if (q < 0) { p = -p; q = -q; }
+            if (p < 0 || p > q) continue;
+            bp[nb].p = p; bp[nb].q = q; ++nb;
+        }
+    }
+    qsort(bp, (size_t)nb, sizeof(rat), rat_cmp);
+    int64_t m = 0, last = -1;
+    for (int64_t j = 0; j < nb; ++j) {
+        int64_t v = voxel_at(gin, d, n, bp[j].p, bp[j].q);
+        for (int pass = 0; pass < 2; ++pass) {
+            if (v >= 0 && v != last) {
+                if (m < cap) out[m] = v;
+                ++m;
+                last = v;
+            }
+            if (pass == 0) {
+                if (!(j + 1 < nb && rat_cmp(&bp[j], &bp[j + 1]) != 0)) break;
+                i128 p = bp[j].p * bp[j + 1].q + bp[j + 1].p * bp[j].q;
+                i128 q = 2 * bp[j].q * bp[j + 1].q;
+                v = voxel_at(gin, d, n, p, q);
+            }
+        }
+    }
+    free(bp);
+    return m;
+}
+
+/* Rows of the hull-restricted system matrix: row i lists, in path order, the
+ * voxels of A_i that are in the hull (hull[v] != 0).  Every input history
+ * has a row (a history with unusable geometry has an empty one).  row_nnz[i]
+ * receives the row's length; when cols is not NULL the rows are written
+ * back to back (cols must hold their total).  Returns 0, -1 when out of
+ * memory. */
+int oracle_system_rows(const og_geom *g, const int64_t *theta, int64_t K, const float *angle,
+                       const float *u_in, const float *v_in, const float *u_out,
+                       const float *v_out, int64_t n, const uint8_t *hull, int64_t *row_nnz,
+                       int32_t *cols)
+{
+    int64_t cap = (int64_t)g->nx + g->ny + g->nz + 8;
+    int64_t *path = (int64_t *)malloc(sizeof(int64_t) * (size_t)cap);
+    if (!path) return -1;
+    int64_t at = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        int64_t gin[3], gout[3];
+        int64_t cnt = 0;
+        if (!oracle_grid_endpoints(g, theta, K, angle[i], u_in[i], v_in[i], u_out[i], v_out[i],
+                                   gin, gout)) {
+            int64_t m = oracle_voxel_path(gin, gout, g->nx, g->ny, g->nz, path, cap);
+            if (m < 0 || m > cap) {
+                free(path);
+                return -1;
+            }
+            for (int64_t j = 0; j < m; ++j)
+                if (hull[path[j]]) {
+                    if (cols) cols[at] = (int32_t)path[j];
+                    ++at;
+                    ++cnt;
+                }
+        }
+        row_nnz[i] = cnt;
+    }
+    free(path);
+    return 0;
+}
+
 /* ------------------------------- FP64 geometry comparison (reported only) */
 
 /* The same history with unquantised FP64 geometry: libm cos/sin of the

@@ -74,6 +74,12 @@ def lib():
                                                      ctypes.c_float, i64p, ctypes.c_int64] + \
                 [f32p] * 6 + [ctypes.c_int64, ctypes.c_int32] + [ctypes.c_int64] * 3
             L.oracle_count_through_voxel.restype = ctypes.c_int64
+            L.oracle_voxel_path.argtypes = [i64p, i64p, ctypes.c_int32, ctypes.c_int32,
+                                            ctypes.c_int32, i64p, ctypes.c_int64]
+            L.oracle_voxel_path.restype = ctypes.c_int64
+            L.oracle_system_rows.argtypes = [ctypes.c_void_p, i64p, ctypes.c_int64] + \
+                [f32p] * 5 + [ctypes.c_int64, u8p, i64p, ctypes.POINTER(ctypes.c_int32)]
+            L.oracle_system_rows.restype = ctypes.c_int
             f64p = ctypes.POINTER(ctypes.c_double)
             L.oracle_grid_endpoints_fp64.argtypes = [ctypes.c_void_p] + [ctypes.c_float] * 5 + \
                 [f64p, f64p]
@@ -428,3 +434,57 @@ def compare_fp64(g, hist, params: Params = Params(), threads: Optional[int] = No
         out[f"{k}_voxels_differing"] = d
         out[f"{k}_diff_frac_of_hull"] = d / max(1, int(np.count_nonzero(ref)))
     return out
+
+
+# ------------------------ hull-restricted system-matrix rows (next row f1)
+def voxel_path(gin, gout, nx: int, ny: int, nz: int) -> np.ndarray:
+    """The voxels of A_i in the order the path meets them."""
+    gin = np.ascontiguousarray(gin, np.int64)
+    gout = np.ascontiguousarray(gout, np.int64)
+    cap = nx + ny + nz + 8
+    out = np.zeros(cap, np.int64)
+    m = lib().oracle_voxel_path(_p(gin, ctypes.c_int64), _p(gout, ctypes.c_int64), nx, ny, nz,
+                                _p(out, ctypes.c_int64), cap)
+    if m < 0 or m > cap:
+        raise MemoryError("oracle_voxel_path")
+    return out[:m].copy()
+
+
+def _rows_range(g, hist, s, e, hull):
+    th, K = _table_arrays()
+    arrs = [np.ascontiguousarray(a[s:e], dtype=np.float32) for a in hist.arrays()[:5]]
+    og = _ogeom(g)
+    nnz = np.zeros(e - s, np.int64)
+    f = lib().oracle_system_rows
+    args = [ctypes.byref(og), _p(th, ctypes.c_int64), K] + [_p(a, ctypes.c_float) for a in arrs]
+    if f(*args, e - s, _p(hull, ctypes.c_uint8), _p(nnz, ctypes.c_int64), None) != 0:
+        raise MemoryError("oracle_system_rows")
+    cols = np.zeros(max(1, int(nnz.sum())), np.int32)
+    if f(*args, e - s, _p(hull, ctypes.c_uint8), _p(nnz, ctypes.c_int64),
+         _p(cols, ctypes.c_int32)) != 0:
+        raise MemoryError("oracle_system_rows")
+    return nnz, cols[:int(nnz.sum())]
+
+
+def system_rows(g, hist, hull, threads: Optional[int] = 1) -> Tuple[np.ndarray, np.ndarray]:
+    """Rows of the hull-restricted system matrix (CSR): row i lists, in path
+    order, the voxels of A_i that are in the hull (uint8 mask of V voxels).
+    Returns (row_ptr int64 of n + 1, cols int32)."""
+    hull = np.ascontiguousarray(hull, np.uint8)
+    n = len(hist)
+    threads = max(1, min(threads or os.cpu_count() or 1, n // 1000 + 1))
+    bounds = np.linspace(0, n, threads + 1).astype(np.int64)
+    parts = [None] * threads
+
+    def work(t):
+        parts[t] = _rows_range(g, hist, int(bounds[t]), int(bounds[t + 1]), hull)
+    ths = [threading.Thread(target=work, args=(t,)) for t in range(threads)]
+    for t in ths:
+        t.start()
+    for t in ths:
+        t.join()
+    nnz = np.concatenate([p[0] for p in parts]) if n else np.zeros(0, np.int64)
+    cols = np.concatenate([p[1] for p in parts]) if n else np.zeros(0, np.int32)
+    row_ptr = np.zeros(n + 1, np.int64)
+    np.cumsum(nnz, out=row_ptr[1:])
+    return row_ptr, cols

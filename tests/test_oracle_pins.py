@@ -418,3 +418,85 @@ def test_fp64_comparison_reports_small_differences(oracle_mod):
     assert r["histories"] > 30000 and r["histories_one_geometry_only"] == 0
     assert r["membership_diff_frac"] < 1e-3
     assert r["H1_diff_frac_of_hull"] < 1e-2 and r["H3_diff_frac_of_hull"] < 1e-2
+
+
+# ------------------------ hull-restricted system-matrix rows (next row f1)
+def _entry_parameter(a, b, v, dims):
+    """The smallest t in [0, 1] with P(t) in voxel v's half-open cube, in
+    exact fractions (None when the segment misses it)."""
+    from fractions import Fraction
+    lo, hi = Fraction(0), Fraction(1)
+    for ax in range(3):
+        p0, d = Fraction(int(a[ax]), Q), Fraction(int(b[ax]) - int(a[ax]), Q)
+        k = v[ax]
+        if d == 0:
+            if not (k <= p0 < k + 1):
+                return None
+            continue
+        t1, t2 = (k - p0) / d, (k + 1 - p0) / d
+        lo = max(lo, min(t1, t2))
+        hi = min(hi, max(t1, t2))
+    return lo if lo <= hi else None
+
+
+def test_voxel_path_order_is_entry_order(oracle_mod):
+    """On generic segments (no edge or corner crossing) the path order is the
+    voxels sorted by the parameter at which the segment enters them."""
+    rng = np.random.default_rng(81)
+    for dims in [(7, 6, 5), (12, 3, 4)]:
+        hi = np.array(dims) * Q
+        for _ in range(300):
+            a = rng.integers(-Q, hi + Q)
+            b = rng.integers(-Q, hi + Q)
+            path = oracle_mod.voxel_path(a, b, *dims)
+            assert np.array_equal(np.sort(path), oracle_mod.voxel_set(a, b, *dims))
+            nx, ny, _ = dims
+            coords = [(v % nx, (v // nx) % ny, v // (nx * ny)) for v in path]
+            t = [_entry_parameter(a, b, c, dims) for c in coords]
+            assert all(x is not None for x in t)
+            assert all(t[i] <= t[i + 1] for i in range(len(t) - 1))
+
+
+def test_voxel_path_steps_and_monotone(oracle_mod):
+    """Every segment (ties included): consecutive voxels differ by at most one
+    in each index, and each index moves only in the segment's direction."""
+    rng = np.random.default_rng(82)
+    for dims in [(5, 4, 3), (9, 9, 2)]:
+        nx, ny, _ = dims
+        for a, b in _random_segments(rng, 3000, dims):
+            path = oracle_mod.voxel_path(a, b, *dims)
+            assert np.array_equal(np.sort(path), oracle_mod.voxel_set(a, b, *dims))
+            c = np.stack([path % nx, (path // nx) % ny, path // (nx * ny)], 1)
+            if len(c) > 1:
+                step = np.diff(c, axis=0)
+                assert np.all(np.abs(step) <= 1)
+                for ax in range(3):
+                    d = int(b[ax]) - int(a[ax])
+                    if d > 0:
+                        assert np.all(step[:, ax] >= 0)
+                    elif d < 0:
+                        assert np.all(step[:, ax] <= 0)
+                    else:
+                        assert np.all(step[:, ax] == 0)
+
+
+def test_system_rows_are_hull_filtered_paths(oracle_mod):
+    """Rows with an all-ones hull are the exact voxel sets in path order
+    (empty for rejected histories); with a random hull, the hull's voxels of
+    each path in the same order."""
+    rng = np.random.default_rng(83)
+    g = synth.geometry_for(1)
+    h = synth.tiny_random_case(rng, 1500, g, span=1.3)
+    arrs = h.arrays()
+    V = g.n_voxels
+    for hull in (np.ones(V, np.uint8), (rng.random(V) < 0.4).astype(np.uint8)):
+        row_ptr, cols = oracle_mod.system_rows(g, h, hull, threads=3)
+        assert row_ptr[0] == 0 and len(cols) == row_ptr[-1]
+        for i in range(len(h)):
+            rej, gin, gout = oracle_mod.grid_endpoints(g, *[float(x[i]) for x in arrs[:5]])
+            row = cols[row_ptr[i]:row_ptr[i + 1]]
+            if rej:
+                assert len(row) == 0
+                continue
+            path = oracle_mod.voxel_path(gin, gout, g.nx, g.ny, g.nz)
+            assert np.array_equal(row, path[hull[path] != 0])
