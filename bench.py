@@ -469,6 +469,65 @@ def run_serving(args):
     print(json.dumps(line), flush=True)
 
 
+def run_rows(args):
+    """Hull-restricted system-matrix rows of the head-sized scan: the scan
+    (SC+MSC+SM) is built once, then each step emits the CSR rows of all 9e6
+    histories inside its MSC hull through the C ABI (count, offsets, emit,
+    and the read of the total)."""
+    import torch
+    from paper_1402_1720_gb300 import build as hbuild
+    from paper_1402_1720_gb300 import hulld, synth
+    _, _, local = _dist()
+    torch.cuda.set_device(local)
+    hbuild.build()
+    hulld.load()
+    w = synth.make_config(2)
+    g, h = w.geometry, w.histories
+    n = len(h)
+    dev = [torch.from_numpy(a).cuda() for a in h.arrays()]
+    scan = hulld.Scan(g)
+    scan.add(dev)
+    scan.finalize()
+    torch.cuda.synchronize()
+    row_ptr, cols = scan.system_rows(hulld.HD_MSC, dev)
+    nnz = len(cols)
+    stream = torch.cuda.Stream()
+
+    def step():
+        hulld.hd_scan_system_rows(scan.handle, hulld.HD_MSC, *dev[:5], row_ptr, cols, stream)
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            step()
+        torch.cuda.synchronize()
+        sampler = ClockSampler(local)
+        sampler.start()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        clocks = sampler.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    peaks = _peaks()
+    out_bytes = 4.0 * nnz + 8.0 * (n + 1)
+    line = {"metric": "histories/s (hull-restricted system-matrix rows, MSC hull)",
+            "value": n / (ms * 1e-3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+            "config": {"workload": WORKLOAD + "; rows of every history inside the MSC hull",
+                       "histories": n, "nnz": nnz,
+                       "hull_voxels": int(scan.mask(hulld.HD_MSC).sum())},
+            "nnz_per_s": nnz / (ms * 1e-3),
+            "output": {"bytes_per_step": out_bytes,
+                       "gbs": out_bytes / (ms * 1e-3) / 1e9, "hbm_peak_gbs": peaks["hbm_gbs"]},
+            "gpu_launches": 5 * args.steps, "clocks": clocks}
+    print(json.dumps(line), flush=True)
+    scan.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -481,7 +540,7 @@ def main():
     ap.add_argument("--no-per-method", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--workload", default="head-200",
-                    choices=["head-200", "batched-48", "serving"])
+                    choices=["head-200", "batched-48", "serving", "rows"])
     ap.add_argument("--batch-fraction", type=float, default=1.0)
     ap.add_argument("--fraction", type=float, default=1.0,
                     help="head-200 workload: keep this fraction of the histories "
@@ -497,6 +556,9 @@ def main():
         return
     if args.workload == "serving":
         run_serving(args)
+        return
+    if args.workload == "rows":
+        run_rows(args)
         return
 
     if args.impl == "reference":

@@ -427,6 +427,25 @@ HD_API hd_status hd_server_get_stats(hd_server *server, hd_server_stats *out);
 /* Release a scan that is finished (or has no chunk in flight). */
 HD_API hd_status hd_server_close_scan(hd_server *server, int64_t scan_id);
 
+/* Rows of the hull-restricted system matrix (the step the hull exists for:
+ * a reconstruction solves only for the voxels inside it, Sec. 1).  For each
+ * of the n histories (device arrays of n float32, as hd_scan_add_histories
+ * with on_device = 1; WEPL is not needed), row i lists, in the order the
+ * path meets them, the voxels of A_i (Eq. 3.2) that are in the finalised
+ * scan's hull of `method` (HD_SC, HD_MSC or HD_SM).  Every history has a
+ * row; one with unusable geometry has an empty row.  row_ptr (device, n + 1
+ * int64) receives the CSR offsets and *nnz (host) the total; cols (device,
+ * `capacity` int32 voxel indices, x fastest) receives the rows when the
+ * total fits, otherwise HD_ERR_RANGE with row_ptr and *nnz set, so the
+ * caller can size cols and call again.  HD_ERR_STATE when the scan is not
+ * finalised or did not run the method.  Synchronises `stream` (to read the
+ * total).  Not in the paper's evaluation: the next step of its pipeline. */
+HD_API hd_status hd_scan_system_rows(hd_scan *scan, int32_t method, const float *angle_deg,
+                                     const float *u_in, const float *v_in, const float *u_out,
+                                     const float *v_out, int64_t n, int64_t *row_ptr,
+                                     int32_t *cols, int64_t capacity, int64_t *nnz,
+                                     void *stream);
+
 /* Atomic-throughput probe: the rate a traversal spending one atomic per
  * voxel-step could reach, measured by kernels that do nothing else (a
  * measurement aid for the roofline; the paper has no counterpart).

@@ -103,6 +103,8 @@ struct hd_scan {
     bool desc_dirty = true;
     uint32_t *tile_count = nullptr;   // 2 * ntiles
     uint32_t *tile_cursor = nullptr;  // 2 * ntiles
+    int64_t *rows_scratch = nullptr;  // tile sums of the system-row offset scan
+    int64_t rows_scratch_cap = 0;
     float *staging = nullptr;  // copied host inputs: 6 columns of staging_half floats
     int64_t staging_half = 0;
     uint32_t *compact_blocks = nullptr;
@@ -176,6 +178,7 @@ void free_scan(hd_scan *s)
     void *ptrs[] = {s->N, s->M, s->carve, s->H1, s->H2, s->H3, s->bits_out, s->slice_key,
                     s->mt, s->slope, s->index, s->ctrl, s->rec_buf, s->staging,
                     s->compact_blocks, s->d_count, s->compact_out, s->pair_buf, s->jobs,
+                    s->rows_scratch,
                     s->tile_count, s->tile_cursor, s->desc_dev};
     for (void *p : ptrs)
         if (p) cudaFree(p);
@@ -713,6 +716,53 @@ static uint8_t *mask_of(hd_scan *s, int32_t method)
     case HD_SM: return s->H3;
     default: return nullptr;
     }
+}
+
+hd_status hd_scan_system_rows(hd_scan *scan, int32_t method, const float *angle_deg,
+                              const float *u_in, const float *v_in, const float *u_out,
+                              const float *v_out, int64_t n, int64_t *row_ptr, int32_t *cols,
+                              int64_t capacity, int64_t *nnz, void *stream)
+{
+    if (!scan || !nnz || n < 0 || capacity < 0 || !row_ptr || (capacity > 0 && !cols))
+        return HD_ERR_ARG;
+    if (n > 0 && (!angle_deg || !u_in || !v_in || !u_out || !v_out)) return HD_ERR_ARG;
+    if (method != HD_SC && method != HD_MSC && method != HD_SM) return HD_ERR_ARG;
+    if (!(scan->params.methods & static_cast<uint32_t>(method)) || !scan->finalized)
+        return HD_ERR_STATE;
+    DeviceGuard g(scan->device);
+    if (!g.ok) return HD_ERR_CUDA;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    *nnz = 0;
+    if (n == 0) {
+        HD_CUDA(cudaMemsetAsync(row_ptr, 0, sizeof(int64_t), st));
+        HD_CUDA(cudaStreamSynchronize(st));
+        return HD_OK;
+    }
+    const int64_t need = hd::rows_scan_scratch(n);
+    if (need > scan->rows_scratch_cap) {
+        HD_CUDA(cudaStreamSynchronize(st));
+        if (scan->rows_scratch) cudaFree(scan->rows_scratch);
+        scan->rows_scratch = nullptr;
+        scan->rows_scratch_cap = 0;
+        if (cudaMalloc(&scan->rows_scratch, sizeof(int64_t) * static_cast<size_t>(need)) !=
+            cudaSuccess) {
+            cudaGetLastError();
+            return HD_ERR_NOMEM;
+        }
+        scan->rows_scratch_cap = need;
+    }
+    const uint8_t *hull = mask_of(scan, method);
+    const hd::Inputs in{angle_deg, u_in, v_in, u_out, v_out, nullptr};
+    HD_CUDA(hd::launch_rows_count(in, n, scan->gq, scan->cordic, hull, row_ptr, scan->sm_count, st));
+    HD_CUDA(hd::launch_rows_scan(row_ptr + 1, n, scan->rows_scratch, st));
+    int64_t total = 0;
+    HD_CUDA(cudaMemcpyAsync(&total, row_ptr + n, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    HD_CUDA(cudaStreamSynchronize(st));
+    *nnz = total;
+    if (total > capacity) return HD_ERR_RANGE;
+    HD_CUDA(hd::launch_rows_emit(in, n, scan->gq, scan->cordic, hull, row_ptr, cols,
+                                 scan->sm_count, st));
+    return HD_OK;
 }
 
 hd_status hd_scan_get_mask(hd_scan *scan, int32_t method, int32_t layout, void *dst,

@@ -129,6 +129,8 @@ _SIGS = {
     "hd_scan_reset": ([_VP, _VP], ctypes.c_int),
     "hd_scan_reserve": ([_VP, _I64, _VP], ctypes.c_int),
     "hd_probe_atomics": ([_I32, ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
+    "hd_scan_system_rows": ([_VP, _I32] + [_VP] * 5 + [_I64, _VP, _VP, _I64,
+                            ctypes.POINTER(ctypes.c_int64), _VP], ctypes.c_int),
     "hd_scan_add_histories": ([_VP] + [_VP] * 6 + [_I64, _I32, _VP], ctypes.c_int),
     "hd_scan_finalize": ([_VP, _VP], ctypes.c_int),
     "hd_scan_get_mask": ([_VP, _I32, _I32, _VP, _SZ, _I32, _VP], ctypes.c_int),
@@ -285,6 +287,31 @@ def hd_probe_atomics(kind: int) -> float:
     out = ctypes.c_double(0.0)
     _check(load().hd_probe_atomics(int(kind), ctypes.byref(out)), "hd_probe_atomics")
     return out.value
+
+
+def hd_scan_system_rows(scan: int, method: int, angle_deg, u_in, v_in, u_out, v_out,
+                        row_ptr, cols=None, stream=None) -> int:
+    """CSR rows of the hull-restricted system matrix into device tensors
+    (row_ptr: n + 1 int64; cols: int32, may be None to size it first).
+    Returns the total; raises HDError(HD_ERR_RANGE) when cols is too small."""
+    arrs = [angle_deg, u_in, v_in, u_out, v_out]
+    ptrs = [_ptr(a) for a in arrs]
+    if any(on == 0 for _, on in ptrs):
+        raise ValueError("histories must be device arrays")
+    rp, on = _ptr(row_ptr)
+    if not on:
+        raise ValueError("row_ptr must be a device array")
+    cp, cap = (0, 0)
+    if cols is not None:
+        cp, on = _ptr(cols)
+        if not on:
+            raise ValueError("cols must be a device array")
+        cap = len(cols)
+    nnz = ctypes.c_int64(0)
+    _check(load().hd_scan_system_rows(scan, int(method), *[p for p, _ in ptrs], len(arrs[0]),
+                                      rp, cp or None, cap, ctypes.byref(nnz), _stream(stream)),
+           "hd_scan_system_rows")
+    return nnz.value
 
 
 def hd_scan_reserve(scan: int, n: int, stream=None) -> None:
@@ -681,6 +708,23 @@ class Scan:
 
     def reserve(self, n: int, stream=None):
         hd_scan_reserve(self.handle, n, stream)
+
+    def system_rows(self, method: int, hist_arrays: Sequence, stream=None):
+        """(row_ptr, cols) device tensors of the hull-restricted system
+        matrix for device histories (angle, u_in, v_in, u_out, v_out, ...)."""
+        import torch
+        h = list(hist_arrays)[:5]
+        n = len(h[0])
+        row_ptr = torch.empty(n + 1, dtype=torch.int64, device=h[0].device)
+        try:
+            total = hd_scan_system_rows(self.handle, method, *h, row_ptr, None, stream)
+        except HDError as e:
+            if e.status != HD_ERR_RANGE:
+                raise
+            total = int(row_ptr[-1].item())
+        cols = torch.empty(max(1, total), dtype=torch.int32, device=h[0].device)
+        hd_scan_system_rows(self.handle, method, *h, row_ptr, cols, stream)
+        return row_ptr, cols[:total]
 
     def add(self, hist_arrays: Sequence, stream=None):
         hd_scan_add_histories(self.handle, *hist_arrays, stream=stream)
