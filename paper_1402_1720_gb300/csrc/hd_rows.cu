@@ -49,19 +49,14 @@ __device__ __forceinline__ void walk_path(const int32_t r[6], int nx, int ny, in
     const bool ymaj = (w.flags >> 5) & 1;
     const bool plus = w.flags & 1;
     int row, lo, hi;
+    // a run's voxels are base + m stride: x-major rows are y + ny z (stride
+    // 1), y-major rows x + nx z (stride nx)
+    const int stride = ymaj ? nx : 1;
+    const int step = plus ? stride : -stride;
     while (run_next(w, row, lo, hi)) {
-        // x-major rows are y + ny z, y-major rows x + nx z
-        const int n = hi - lo + 1;
-        for (int k = 0; k < n; ++k) {
-            const int m = plus ? lo + k : hi - k;
-            const uint32_t v = ymaj ? static_cast<uint32_t>(row % nx) +
-                                          static_cast<uint32_t>(nx) *
-                                              (static_cast<uint32_t>(m) +
-                                               static_cast<uint32_t>(ny) * static_cast<uint32_t>(row / nx))
-                                    : static_cast<uint32_t>(m) +
-                                          static_cast<uint32_t>(nx) * static_cast<uint32_t>(row);
-            visit(v);
-        }
+        const int base = ymaj ? row % nx + nx * ny * (row / nx) : nx * row;
+        int v = base + (plus ? lo : hi) * stride;
+        for (int k = hi - lo; k >= 0; --k, v += step) visit(static_cast<uint32_t>(v));
     }
 }
 
@@ -165,7 +160,7 @@ __global__ void __launch_bounds__(kScanThreads) scan_tiles_kernel(int64_t *a, in
     if (threadIdx.x == 0) sums[blockIdx.x] = total;
 }
 
-// One block: exclusive scan of the tile sums, kScanPerThread... at a time.
+// One block: exclusive scan of the tile sums, kScanThreads at a time.
 __global__ void __launch_bounds__(kScanThreads) scan_sums_kernel(int64_t *sums, int64_t nb)
 {
     __shared__ long long s_warp[32];
