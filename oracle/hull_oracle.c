@@ -354,6 +354,183 @@ int oracle_accumulate(const og_geom *g, float tau_l, float tau_h, int32_t method
     return 0;
 }
 
+/* ------------------------------- SC as the paper ran it (next row f2) */
+
+/* Binned SC (Sec. 2.2 data cuts; Sec. 3.2, its implementation paragraphs).
+ * Histories are binned by gantry angle and by the lateral and vertical
+ * displacement of the path's mid-point, (u_in + u_out) / 2 and
+ * (v_in + v_out) / 2, from the centre of the volume.  Angle bins are centred
+ * on multiples of the bin size (so a gantry angle falls on a bin centre);
+ * displacement bins are [lo + i size, lo + (i + 1) size).  In each bin, a
+ * history whose WEPL, lateral slope (u_out - u_in) or vertical slope
+ * (v_out - v_in) lies more than k standard deviations from the bin's mean is
+ * cut; the slopes over the fixed tracker separation stand for the relative
+ * angles.  A bin whose kept histories have mean WEPL below the cutoff is
+ * missed: in every slice whose centre height lies in the bin's vertical
+ * interval, the straight line along the beam at the bin's centre angle and
+ * lateral centre, at that slice's centre height, is carved (the bin's line,
+ * one per slice it covers, so that slices thinner than a bin all get lines).
+ * The carved image is averaged over a w x w window in each slice (voxels
+ * outside the grid count as 0) and a voxel is in the hull when its window
+ * holds at least min_count uncarved voxels (the average exceeds
+ * (min_count - 1) / w^2).
+ *
+ * All of it is integer arithmetic: angle, u and v in Q16 as for the paths;
+ * WEPL and slopes in 1/256 mm (rounded to nearest even); per-bin sums in 64
+ * bits (exact while a bin holds fewer than 2^27 histories); and the cut
+ * |x - mean| <= k sigma, with the population sigma, as
+ * (n x - S)^2 <= k^2 (n Q - S^2) in 128 bits.  A history is binned when its
+ * angle and coordinates are in the path's accepted range, |WEPL| < 1024 mm,
+ * both slopes are below 1024 mm and its bin exists. */
+typedef struct {
+    int32_t n_ang, n_u, n_v;   /* bins per axis; n_ang ang_q = 360 degrees */
+    int64_t ang_q, u_q, v_q;   /* bin sizes, Q16 degrees and mm */
+    int64_t u_lo_q, v_lo_q;    /* lower edge of the first u and v bin, Q16 mm */
+    int32_t k;                 /* cut at k standard deviations */
+    int64_t miss_q8;           /* missed: kept mean WEPL below this, 1/256 mm */
+    int32_t w;                 /* averaging window, odd */
+    int32_t min_count;         /* uncarved voxels a window needs */
+} og_binned;
+
+static int64_t q8_of(float x) { return (int64_t)llrint((double)x * 256.0); }
+
+/* Bin of one history, -1 when it is not binned; x receives WEPL, lateral and
+ * vertical slope in 1/256 mm. */
+static int64_t bin_of(const og_binned *b, float angle, float u_in, float v_in, float u_out,
+                      float v_out, float wepl, int64_t x[3])
+{
+    if (!(fabsf(angle) < 1048576.0f) || !(fabsf(wepl) < 1024.0f)) return -1;
+    if (!(fabsf(u_in) < 4096.0f) || !(fabsf(v_in) < 4096.0f) || !(fabsf(u_out) < 4096.0f) ||
+        !(fabsf(v_out) < 4096.0f))
+        return -1;
+    x[0] = q8_of(wepl);
+    x[1] = q8_of(u_out) - q8_of(u_in);
+    x[2] = q8_of(v_out) - q8_of(v_in);
+    if (llabs(x[1]) >= 1024 * 256 || llabs(x[2]) >= 1024 * 256) return -1;
+    const int64_t full = 360LL * Q16;
+    int64_t a = q16_of(angle) % full;
+    if (a < 0) a += full;
+    int64_t ia = floordiv(2 * a + b->ang_q, 2 * b->ang_q); /* nearest centre */
+    if (ia == b->n_ang) ia = 0;
+    const int64_t u2 = q16_of(u_in) + q16_of(u_out), v2 = q16_of(v_in) + q16_of(v_out);
+    const int64_t iu = floordiv(u2 - 2 * b->u_lo_q, 2 * b->u_q);
+    const int64_t iv = floordiv(v2 - 2 * b->v_lo_q, 2 * b->v_q);
+    if (iu < 0 || iu >= b->n_u || iv < 0 || iv >= b->n_v) return -1;
+    return ia + (int64_t)b->n_ang * (iu + (int64_t)b->n_u * iv);
+}
+
+/* x within k standard deviations of the bin's values (n, S, Q). */
+static int within(int64_t n, int64_t S, int64_t Q, int64_t x, int32_t k)
+{
+    const i128 d = (i128)n * x - S;
+    const i128 var_n2 = (i128)n * Q - (i128)S * S; /* n^2 sigma^2 */
+    return d * d <= (i128)k * k * var_n2;
+}
+
+/* Bin bi's centre angle (degrees) and lateral centre (mm). */
+void oracle_bin_line(const og_binned *b, int64_t bi, float *la, float *lu)
+{
+    const int64_t ia = bi % b->n_ang, iu = (bi / b->n_ang) % b->n_u;
+    *la = (float)((double)(ia * b->ang_q) / (double)Q16);
+    *lu = (float)((double)(2 * b->u_lo_q + (2 * iu + 1) * b->u_q) / (2.0 * Q16));
+}
+
+/* Vertical bin of slice z (its centre height, from the Q16 slice thickness),
+ * or -1; *zc receives the centre height in mm. */
+int64_t oracle_slice_bin(const og_geom *g, const og_binned *b, int64_t z, float *zc)
+{
+    const int64_t sz_q = q16_of(g->sz);
+    const int64_t c2 = (2 * z + 1 - g->nz) * sz_q; /* twice the centre, Q16 */
+    *zc = (float)((double)c2 / (2.0 * Q16));
+    const int64_t iv = floordiv(c2 - 2 * b->v_lo_q, 2 * b->v_q);
+    return iv >= 0 && iv < b->n_v ? iv : -1;
+}
+
+/* Binned SC over n histories.  acc (9 int64 per bin, zeroed by the caller):
+ * n, S and Q of WEPL, lateral and vertical slope, then kept n and kept WEPL
+ * sum; carved (V bytes): 1 not carved, 0 carved; mask (V bytes): the hull;
+ * stats (zeroed by the caller): [0] histories binned, [1] histories cut,
+ * [2] bins with histories, [3] missed bins, [4] lines carved (a missed bin
+ * times the slices it covers), [5] lines that miss the volume.  Returns 0,
+ * -1 when out of memory. */
+int oracle_sc_binned(const og_geom *g, const og_binned *b, const int64_t *theta, int64_t K,
+                     const float *angle, const float *u_in, const float *v_in,
+                     const float *u_out, const float *v_out, const float *wepl, int64_t n,
+                     int64_t *acc, uint8_t *carved, uint8_t *mask, int64_t *stats)
+{
+    const int64_t nb = (int64_t)b->n_ang * b->n_u * b->n_v;
+    const int64_t V = (int64_t)g->nx * g->ny * g->nz;
+    const int64_t cap = (int64_t)g->nx + g->ny + g->nz + 8;
+    int64_t *set = (int64_t *)malloc(sizeof(int64_t) * (size_t)cap);
+    if (!set) return -1;
+    int64_t x[3];
+    for (int64_t i = 0; i < n; ++i) { /* bin statistics */
+        const int64_t bi = bin_of(b, angle[i], u_in[i], v_in[i], u_out[i], v_out[i], wepl[i], x);
+        if (bi < 0) continue;
+        int64_t *a = acc + 9 * bi;
+        a[0] += 1;
+        for (int q = 0; q < 3; ++q) {
+            a[1 + q] += x[q];
+            a[4 + q] += x[q] * x[q];
+        }
+        stats[0] += 1;
+    }
+    for (int64_t i = 0; i < n; ++i) { /* data cuts; kept WEPL per bin */
+        const int64_t bi = bin_of(b, angle[i], u_in[i], v_in[i], u_out[i], v_out[i], wepl[i], x);
+        if (bi < 0) continue;
+        int64_t *a = acc + 9 * bi;
+        int keep = 1;
+        for (int q = 0; q < 3; ++q) keep = keep && within(a[0], a[1 + q], a[4 + q], x[q], b->k);
+        if (!keep) {
+            stats[1] += 1;
+            continue;
+        }
+        a[7] += 1;
+        a[8] += x[0];
+    }
+    memset(carved, 1, (size_t)V);
+    for (int64_t bi = 0; bi < nb; ++bi) { /* carve the missed bins' lines */
+        const int64_t *a = acc + 9 * bi;
+        if (a[0] > 0) stats[2] += 1;
+        if (!(a[7] > 0 && a[8] < b->miss_q8 * a[7])) continue;
+        stats[3] += 1;
+        const int64_t iv = bi / ((int64_t)b->n_ang * b->n_u);
+        float la, lu;
+        oracle_bin_line(b, bi, &la, &lu);
+        for (int64_t z = 0; z < g->nz; ++z) {
+            float zc;
+            if (oracle_slice_bin(g, b, z, &zc) != iv) continue;
+            stats[4] += 1;
+            int64_t gin[3], gout[3];
+            if (oracle_grid_endpoints(g, theta, K, la, lu, zc, lu, zc, gin, gout)) {
+                stats[5] += 1;
+                continue;
+            }
+            const int64_t m = oracle_voxel_set(gin, gout, g->nx, g->ny, g->nz, set, cap);
+            if (m < 0 || m > cap) {
+                free(set);
+                return -1;
+            }
+            for (int64_t j = 0; j < m; ++j) carved[set[j]] = 0;
+        }
+    }
+    const int64_t r = b->w / 2; /* w x w in-slice window, outside = 0 */
+    for (int64_t z = 0; z < g->nz; ++z)
+        for (int64_t y = 0; y < g->ny; ++y)
+            for (int64_t xx = 0; xx < g->nx; ++xx) {
+                int64_t c = 0;
+                for (int64_t dy = -r; dy <= r; ++dy)
+                    for (int64_t dx = -r; dx <= r; ++dx) {
+                        const int64_t X = xx + dx, Y = y + dy;
+                        if (X < 0 || X >= g->nx || Y < 0 || Y >= g->ny) continue;
+                        c += carved[X + g->nx * (Y + g->ny * z)];
+                    }
+                mask[xx + g->nx * (y + g->ny * z)] = c >= b->min_count;
+            }
+    free(set);
+    return 0;
+}
+
 /* ------------------------- hull-restricted system-matrix rows (next row f1) */
 
 /* The voxels of A_i in the order the path meets them (increasing t): the

@@ -91,6 +91,15 @@ def lib():
                                               ctypes.c_int32, i64p, ctypes.c_int64] + \
                 [f32p] * 6 + [ctypes.c_int64, u32p, u32p, i64p]
             L.oracle_compare_fp64.restype = ctypes.c_int
+            L.oracle_bin_line.argtypes = [ctypes.c_void_p, ctypes.c_int64, f32p, f32p]
+            L.oracle_bin_line.restype = None
+            L.oracle_slice_bin.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
+                                           f32p]
+            L.oracle_slice_bin.restype = ctypes.c_int64
+            L.oracle_sc_binned.argtypes = [ctypes.c_void_p, ctypes.c_void_p, i64p,
+                                           ctypes.c_int64] + [f32p] * 6 + \
+                [ctypes.c_int64, i64p, u8p, u8p, i64p]
+            L.oracle_sc_binned.restype = ctypes.c_int
             _lib = L
     return _lib
 
@@ -488,3 +497,102 @@ def system_rows(g, hist, hull, threads: Optional[int] = 1) -> Tuple[np.ndarray, 
     row_ptr = np.zeros(n + 1, np.int64)
     np.cumsum(nnz, out=row_ptr[1:])
     return row_ptr, cols
+
+
+# ------------------------------------ SC as the paper ran it (next row f2)
+class _OBinned(ctypes.Structure):
+    _fields_ = [("n_ang", ctypes.c_int32), ("n_u", ctypes.c_int32), ("n_v", ctypes.c_int32),
+                ("ang_q", ctypes.c_int64), ("u_q", ctypes.c_int64), ("v_q", ctypes.c_int64),
+                ("u_lo_q", ctypes.c_int64), ("v_lo_q", ctypes.c_int64), ("k", ctypes.c_int32),
+                ("miss_q8", ctypes.c_int64), ("w", ctypes.c_int32),
+                ("min_count", ctypes.c_int32)]
+
+
+@dataclasses.dataclass(frozen=True)
+class BinnedParams:
+    """Bins of the data cuts and of SC's lines (Sec. 2.2, Sec. 3.1: 4 degree
+    angular, 1 mm lateral and 5 mm vertical bins), the 3 sigma cuts, the 1 mm
+    cutoff on a bin's mean WEPL (Sec. 3.2) and the 5 x 5 average thresholded
+    at 0.4 (a window of 25 needs more than 10 uncarved voxels)."""
+    angle_bin_deg: float = 4.0
+    u_bin_mm: float = 1.0
+    v_bin_mm: float = 5.0
+    u_lo_mm: float = -142.0
+    v_lo_mm: float = -40.0
+    n_u: int = 284
+    v_bins: int = 16
+    k_sigma: int = 3
+    miss_wepl_mm: float = 1.0
+    window: int = 5
+    min_count: int = 11
+
+    def q(self) -> _OBinned:
+        ang_q = int(round(self.angle_bin_deg * 65536))
+        n_ang = (360 * 65536) // ang_q
+        if n_ang * ang_q != 360 * 65536:
+            raise ValueError("angle bins must tile 360 degrees")
+        return _OBinned(n_ang, self.n_u, self.v_bins, ang_q,
+                        int(round(self.u_bin_mm * 65536)), int(round(self.v_bin_mm * 65536)),
+                        int(round(self.u_lo_mm * 65536)), int(round(self.v_lo_mm * 65536)),
+                        self.k_sigma, int(np.rint(np.float64(np.float32(self.miss_wepl_mm))
+                                                  * 256.0)),
+                        self.window, self.min_count)
+
+    @property
+    def n_bins(self) -> int:
+        b = self.q()
+        return b.n_ang * b.n_u * b.n_v
+
+
+def binned_params_for(g, **kw) -> BinnedParams:
+    """Displacement bins covering the volume's lateral half-diagonal and its
+    height, at the paper's bin sizes (overridable by keyword)."""
+    p = BinnedParams(**kw)
+    half_u = math.ceil(math.hypot(g.nx * g.sx, g.ny * g.sy) / 2 / p.u_bin_mm) * p.u_bin_mm
+    half_v = math.ceil(g.nz * g.sz / 2 / p.v_bin_mm) * p.v_bin_mm
+    return dataclasses.replace(p, u_lo_mm=-half_u, n_u=int(round(2 * half_u / p.u_bin_mm)),
+                               v_lo_mm=-half_v, v_bins=int(round(2 * half_v / p.v_bin_mm)),
+                               **kw)
+
+
+def bin_line(bp: BinnedParams, bi: int) -> Tuple[float, float]:
+    """(centre angle, lateral centre) of bin bi's lines."""
+    ob = bp.q()
+    la, lu = ctypes.c_float(), ctypes.c_float()
+    lib().oracle_bin_line(ctypes.byref(ob), int(bi), ctypes.byref(la), ctypes.byref(lu))
+    return la.value, lu.value
+
+
+def slice_bin(g, bp: BinnedParams, z: int) -> Tuple[int, float]:
+    """(vertical bin or -1, centre height) of slice z."""
+    og, ob = _ogeom(g), bp.q()
+    zc = ctypes.c_float()
+    iv = lib().oracle_slice_bin(ctypes.byref(og), ctypes.byref(ob), int(z), ctypes.byref(zc))
+    return int(iv), zc.value
+
+
+def sc_binned(g, hist, bp: BinnedParams) -> Dict:
+    """Binned SC with data cuts and the averaging filter.  Returns the hull
+    mask, the carved image (1 = not carved), the bin table (n_bins x 9 int64:
+    n, S and Q of WEPL / lateral / vertical slope, kept n, kept WEPL sum) and
+    counters."""
+    th, K = _table_arrays()
+    ob = bp.q()
+    nb = ob.n_ang * ob.n_u * ob.n_v
+    V = g.nx * g.ny * g.nz
+    acc = np.zeros((nb, 9), np.int64)
+    carved = np.zeros(V, np.uint8)
+    mask = np.zeros(V, np.uint8)
+    stats = np.zeros(6, np.int64)
+    arrs = [np.ascontiguousarray(a, dtype=np.float32) for a in hist.arrays()]
+    og = _ogeom(g)
+    r = lib().oracle_sc_binned(ctypes.byref(og), ctypes.byref(ob), _p(th, ctypes.c_int64), K,
+                               *[_p(a, ctypes.c_float) for a in arrs], len(hist),
+                               _p(acc, ctypes.c_int64), _p(carved, ctypes.c_uint8),
+                               _p(mask, ctypes.c_uint8), _p(stats, ctypes.c_int64))
+    if r != 0:
+        raise MemoryError("oracle_sc_binned")
+    return {"mask": mask, "carved": carved, "bins": acc,
+            "stats": {"binned": int(stats[0]), "cut": int(stats[1]),
+                      "bins_used": int(stats[2]), "bins_missed": int(stats[3]),
+                      "lines": int(stats[4]), "lines_outside": int(stats[5])}}
