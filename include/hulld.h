@@ -498,6 +498,122 @@ HD_API hd_status hd_accumulate_noalloc(const hd_geometry *geom, const hd_params 
 HD_API hd_status hd_classify(const float *wepl, int64_t n, const hd_params *params, uint8_t *cls_out,
                       int32_t on_device, void *stream);
 
+/* ------------------------------------------------------------------------
+ * Binned SC: SC as the paper ran it (Sec. 2.2 data cuts; Sec. 3.2, its
+ * implementation paragraphs).  Histories are binned by gantry angle and by
+ * the lateral and vertical displacement of the path's mid-point,
+ * ((u_in + u_out) / 2, (v_in + v_out) / 2), from the volume's centre; angle
+ * bins are centred on multiples of the bin size, displacement bin i covers
+ * [lo + i size, lo + (i + 1) size).  In each bin a history is cut when its
+ * WEPL, lateral slope (u_out - u_in) or vertical slope (v_out - v_in) lies
+ * more than k_sigma population standard deviations from the bin's mean (the
+ * slopes over the fixed tracker separation stand for the relative angles).
+ * A bin whose kept histories have mean WEPL below miss_wepl_mm is missed:
+ * in every slice whose centre height lies in its vertical interval, the
+ * straight line along the beam at the bin's centre angle and lateral centre,
+ * at the slice's centre height, is carved.  The carved image is averaged
+ * over a window x window neighbourhood in each slice (outside the grid counts
+ * as carved) and a voxel is in the hull when at least min_count voxels of
+ * its window are not carved (min_count 11 of 25: the average exceeds 0.4).
+ *
+ * Exactness: WEPL and slopes are taken in 1/256 mm (rounded to nearest
+ * even), angles and displacements in Q16 as for the paths, the per-bin sums
+ * in 64-bit integers (exact while a bin holds fewer than 2^27 histories) and
+ * the cut as (n x - S)^2 <= k^2 (n Q - S^2) in 128 bits, so the result does
+ * not depend on the order of histories or chunks.  A history is binned when
+ * its angle and coordinates are in the paths' accepted range, |WEPL| <
+ * 1024 mm, both slopes are below 1024 mm in magnitude and its bin exists;
+ * others are skipped.
+ *
+ * Use: create; hd_binned_add_histories for every chunk (the statistics);
+ * hd_binned_cut_histories for the same histories again (the cuts; the first
+ * call closes the statistics, so add then returns HD_ERR_STATE);
+ * hd_binned_finalize; read the hull.  hd_binned_run does all four for one
+ * resident array.  History arrays are n float32 each, readable by the
+ * device (device, managed or page-locked host memory; HD_ERR_ARG for
+ * pageable host memory).  Calls are stream-ordered on `stream` unless they
+ * say otherwise. */
+typedef struct {
+    float angle_bin_deg;  /* 4.0; 360 / angle_bin_deg bins, tiling 360 exactly in Q16 */
+    float u_bin_mm;       /* lateral bin size, 1.0 */
+    float v_bin_mm;       /* vertical bin size, 5.0 */
+    float u_lo_mm;        /* lower edge of the first lateral bin */
+    float v_lo_mm;        /* lower edge of the first vertical bin */
+    int32_t n_u, n_v;     /* lateral and vertical bins */
+    int32_t k_sigma;      /* cut beyond k standard deviations, 3 */
+    float miss_wepl_mm;   /* missed when the kept mean WEPL is below this, 1.0 */
+    int32_t window;       /* averaging window (odd, 1..15), 5 */
+    int32_t min_count;    /* uncarved voxels a window needs, 11 */
+} hd_binned_params;
+
+typedef struct {
+    int64_t histories_binned; /* histories that fell in a bin */
+    int64_t histories_cut;    /* of those, removed by the cuts */
+    int64_t bins;             /* bins in the table */
+    int64_t bins_used;        /* bins with histories */
+    int64_t bins_missed;      /* bins found missed */
+    int64_t lines;            /* lines carved: missed bins times the slices each covers */
+    int64_t lines_outside;    /* of those, lines whose endpoints are out of range */
+} hd_binned_stats;
+
+typedef struct hd_binned hd_binned;
+
+/* The paper's values for `geom`: displacement bins covering the volume's
+ * in-plane half-diagonal (rounded up to whole bins) and its height. */
+HD_API hd_status hd_binned_params_default(const hd_geometry *geom, hd_binned_params *out);
+
+/* HD_ERR_RANGE when a bin size is outside [1/16, 4096] mm (angle: [1/16,
+ * 360] degrees, dividing 360 in Q16), |lo| > 4096 mm, the table exceeds 2^24
+ * bins, k_sigma is outside [1, 64], the window is even or outside [1, 15],
+ * min_count is outside [0, window^2] or |miss_wepl_mm| >= 1024; otherwise as
+ * hd_scan_create.  Allocates 72 bytes per bin and about
+ * V * 2.2 bytes on the current device. */
+HD_API hd_status hd_binned_create(const hd_geometry *geom, const hd_binned_params *params,
+                                  hd_binned **out);
+HD_API hd_status hd_binned_destroy(hd_binned *b);
+
+/* Empty the bin table and return to the statistics phase. */
+HD_API hd_status hd_binned_reset(hd_binned *b, void *stream);
+
+/* Statistics phase: add n histories' WEPL and slopes to their bins. */
+HD_API hd_status hd_binned_add_histories(hd_binned *b, const float *angle_deg, const float *u_in,
+                                         const float *v_in, const float *u_out,
+                                         const float *v_out, const float *wepl, int64_t n,
+                                         void *stream);
+
+/* Cut phase: test n histories against their bins' statistics and add the
+ * kept ones' WEPL to the bins.  Give every history added, once. */
+HD_API hd_status hd_binned_cut_histories(hd_binned *b, const float *angle_deg, const float *u_in,
+                                         const float *v_in, const float *u_out,
+                                         const float *v_out, const float *wepl, int64_t n,
+                                         void *stream);
+
+/* Decide the missed bins, carve their lines and filter.  HD_ERR_STATE
+ * before any cut call. */
+HD_API hd_status hd_binned_finalize(hd_binned *b, void *stream);
+
+/* reset, add, cut and finalize over one array of n histories. */
+HD_API hd_status hd_binned_run(hd_binned *b, const float *angle_deg, const float *u_in,
+                               const float *v_in, const float *u_out, const float *v_out,
+                               const float *wepl, int64_t n, void *stream);
+
+/* After finalize: the hull (which = HD_BINNED_HULL) or the carved image
+ * before filtering (HD_BINNED_CARVED: 1 = not carved), V bytes in linear
+ * voxel order, to device (dst_on_device = 1) or host memory.  HD_ERR_STATE
+ * before finalize. */
+enum { HD_BINNED_HULL = 0, HD_BINNED_CARVED = 1 };
+HD_API hd_status hd_binned_get_image(hd_binned *b, int32_t which, uint8_t *dst, int64_t n,
+                                     int32_t dst_on_device, void *stream);
+
+/* The bin table, n_bins x 9 int64 (bin index = angle + n_ang (u + n_u v)):
+ * histories, sums of WEPL, lateral and vertical slope (1/256 mm), sums of
+ * their squares, kept histories, kept WEPL sum. */
+HD_API hd_status hd_binned_get_bins(hd_binned *b, int64_t *dst, int64_t n_bins,
+                                    int32_t dst_on_device, void *stream);
+
+/* Counters; synchronises `stream`. */
+HD_API hd_status hd_binned_get_stats(hd_binned *b, hd_binned_stats *out, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -73,6 +73,31 @@ bool make_cordic(hd::Cordic &c)
 
 }  // namespace
 
+namespace hd {
+
+bool make_cordic_table(Cordic &c) { return make_cordic(c); }
+
+void note_cuda_error(cudaError_t e, const char *where) { note_cuda(e, where); }
+
+hd_status check_geometry(const hd_geometry *g)
+{
+    if (!g) return HD_ERR_ARG;
+    const int32_t n[3] = {g->nx, g->ny, g->nz};
+    const float s[3] = {g->sx, g->sy, g->sz};
+    int64_t V = 1;
+    for (int a = 0; a < 3; ++a) {
+        if (n[a] < 1 || n[a] > kMaxN) return HD_ERR_RANGE;
+        if (!(s[a] >= 1.0f / 64.0f && s[a] <= 64.0f)) return HD_ERR_RANGE;
+        if (static_cast<double>(n[a]) * s[a] > 8192.0) return HD_ERR_RANGE;
+        V *= n[a];
+    }
+    if (V > (int64_t(1) << 31) - (int64_t(1) << 26)) return HD_ERR_RANGE;
+    if (!(g->tracker_half_sep_mm > 0.0f && g->tracker_half_sep_mm < 4096.0f)) return HD_ERR_RANGE;
+    return HD_OK;
+}
+
+}  // namespace hd
+
 struct hd_scan {
     int device = 0;
     int sm_count = 0;
@@ -188,17 +213,8 @@ void free_scan(hd_scan *s)
 hd_status validate(const hd_geometry *g, const hd_params *p)
 {
     if (!g || !p) return HD_ERR_ARG;
-    const int32_t n[3] = {g->nx, g->ny, g->nz};
-    const float s[3] = {g->sx, g->sy, g->sz};
-    int64_t V = 1;
-    for (int a = 0; a < 3; ++a) {
-        if (n[a] < 1 || n[a] > hd::kMaxN) return HD_ERR_RANGE;
-        if (!(s[a] >= 1.0f / 64.0f && s[a] <= 64.0f)) return HD_ERR_RANGE;
-        if (static_cast<double>(n[a]) * s[a] > 8192.0) return HD_ERR_RANGE;
-        V *= n[a];
-    }
-    if (V > (int64_t(1) << 31) - (int64_t(1) << 26)) return HD_ERR_RANGE;
-    if (!(g->tracker_half_sep_mm > 0.0f && g->tracker_half_sep_mm < 4096.0f)) return HD_ERR_RANGE;
+    const hd_status gs = hd::check_geometry(g);
+    if (gs != HD_OK) return gs;
     if (std::isnan(p->wepl_miss_lt) || std::isnan(p->wepl_hit_gt)) return HD_ERR_ARG;
     if (p->wepl_miss_lt > p->wepl_hit_gt) return HD_ERR_ARG;
     if (p->msc_nbhd != 4 && p->msc_nbhd != 6) return HD_ERR_ARG;

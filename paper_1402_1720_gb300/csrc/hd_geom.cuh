@@ -700,6 +700,30 @@ HD_HD bool run_begin(RunWalk &rw, const int32_t gi[3], const int32_t go[3], int 
     return true;
 }
 
+// Calls visit(v) for the voxels of the walk gi -> go over the whole grid in
+// path order: runs come in order, and a run is expanded in the direction
+// the major axis moves.
+template <class VisitT>
+HD_HD void walk_path(const int32_t r[6], int nx, int ny, int nz, VisitT &visit)
+{
+    const int32_t gi[3] = {r[0], r[1], r[2]};
+    const int32_t go[3] = {r[3], r[4], r[5]};
+    RunWalk w;
+    if (!run_begin(w, gi, go, nx, ny, nz)) return;
+    const bool ymaj = (w.flags >> 5) & 1;
+    const bool plus = w.flags & 1;
+    int row, lo, hi;
+    // a run's voxels are base + m stride: x-major rows are y + ny z (stride
+    // 1), y-major rows x + nx z (stride nx)
+    const int stride = ymaj ? nx : 1;
+    const int step = plus ? stride : -stride;
+    while (run_next(w, row, lo, hi)) {
+        const int base = ymaj ? row % nx + nx * ny * (row / nx) : nx * row;
+        int v = base + (plus ? lo : hi) * stride;
+        for (int k = hi - lo; k >= 0; --k, v += step) visit(static_cast<uint32_t>(v));
+    }
+}
+
 // ---------------------------------------------------------- lean run walk
 //
 // Most walks inside a one-voxel-deep tile are "lean": the in-plane minor

@@ -173,4 +173,9 @@ cudaError_t launch_pack_bits(const uint8_t *mask, int64_t V, uint32_t *bits, cud
 cudaError_t launch_compact(const uint8_t *mask, int64_t V, int32_t *out, int64_t capacity,
                            uint32_t *block_counts, unsigned long long *d_count, cudaStream_t s);
 
+// Shared host helpers of the C ABI (defined with the scan objects).
+bool make_cordic_table(Cordic &c);
+void note_cuda_error(cudaError_t e, const char *where);
+hd_status check_geometry(const hd_geometry *g);
+
 }  // namespace hd

@@ -117,6 +117,27 @@ class hd_server_stats(ctypes.Structure):
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
+class hd_binned_params(ctypes.Structure):
+    _fields_ = [("angle_bin_deg", ctypes.c_float), ("u_bin_mm", ctypes.c_float),
+                ("v_bin_mm", ctypes.c_float), ("u_lo_mm", ctypes.c_float),
+                ("v_lo_mm", ctypes.c_float), ("n_u", ctypes.c_int32), ("n_v", ctypes.c_int32),
+                ("k_sigma", ctypes.c_int32), ("miss_wepl_mm", ctypes.c_float),
+                ("window", ctypes.c_int32), ("min_count", ctypes.c_int32)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class hd_binned_stats(ctypes.Structure):
+    _fields_ = [("histories_binned", ctypes.c_int64), ("histories_cut", ctypes.c_int64),
+                ("bins", ctypes.c_int64), ("bins_used", ctypes.c_int64),
+                ("bins_missed", ctypes.c_int64), ("lines", ctypes.c_int64),
+                ("lines_outside", ctypes.c_int64)]
+
+    def as_dict(self):
+        return {k: int(getattr(self, k)) for k, _ in self._fields_}
+
+
 # exported symbols and their signatures
 _VP, _I32, _I64, _SZ = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_size_t
 _SIGS = {
@@ -166,6 +187,19 @@ _SIGS = {
     "hd_server_get_stats": ([_VP, ctypes.POINTER(hd_server_stats)], ctypes.c_int),
     "hd_server_close_scan": ([_VP, _I64], ctypes.c_int),
     "hd_scan_get_profile": ([_VP, ctypes.POINTER(hd_profile)], ctypes.c_int),
+    "hd_binned_params_default": ([ctypes.POINTER(hd_geometry), ctypes.POINTER(hd_binned_params)],
+                                 ctypes.c_int),
+    "hd_binned_create": ([ctypes.POINTER(hd_geometry), ctypes.POINTER(hd_binned_params),
+                          ctypes.POINTER(_VP)], ctypes.c_int),
+    "hd_binned_destroy": ([_VP], ctypes.c_int),
+    "hd_binned_reset": ([_VP, _VP], ctypes.c_int),
+    "hd_binned_add_histories": ([_VP] + [_VP] * 6 + [_I64, _VP], ctypes.c_int),
+    "hd_binned_cut_histories": ([_VP] + [_VP] * 6 + [_I64, _VP], ctypes.c_int),
+    "hd_binned_finalize": ([_VP, _VP], ctypes.c_int),
+    "hd_binned_run": ([_VP] + [_VP] * 6 + [_I64, _VP], ctypes.c_int),
+    "hd_binned_get_image": ([_VP, _I32, _VP, _I64, _I32, _VP], ctypes.c_int),
+    "hd_binned_get_bins": ([_VP, _VP, _I64, _I32, _VP], ctypes.c_int),
+    "hd_binned_get_stats": ([_VP, ctypes.POINTER(hd_binned_stats), _VP], ctypes.c_int),
 }
 
 
@@ -769,3 +803,160 @@ class Scan:
         # D2H copies into pageable numpy memory are complete when the call
         # returns; pinned destinations need a stream sync, done via stats
         hd_scan_get_stats(self.handle, stream)
+
+
+# ------------------------------------------------------------ binned SC
+HD_BINNED_HULL, HD_BINNED_CARVED = 0, 1
+
+
+def hd_binned_params_default(geometry) -> hd_binned_params:
+    p = hd_binned_params()
+    g = _geometry(geometry)
+    _check(load().hd_binned_params_default(ctypes.byref(g), ctypes.byref(p)),
+           "hd_binned_params_default")
+    return p
+
+
+def _binned_params(p, geometry) -> hd_binned_params:
+    if p is None:
+        return hd_binned_params_default(geometry)
+    if isinstance(p, hd_binned_params):
+        return p
+    return hd_binned_params(float(p.angle_bin_deg), float(p.u_bin_mm), float(p.v_bin_mm),
+                            float(p.u_lo_mm), float(p.v_lo_mm), int(p.n_u), int(p.v_bins),
+                            int(p.k_sigma), float(p.miss_wepl_mm), int(p.window),
+                            int(p.min_count))
+
+
+def hd_binned_create(geometry, params=None) -> int:
+    h = _VP()
+    g = _geometry(geometry)
+    p = _binned_params(params, geometry)
+    _check(load().hd_binned_create(ctypes.byref(g), ctypes.byref(p), ctypes.byref(h)),
+           "hd_binned_create")
+    return h.value
+
+
+def hd_binned_destroy(b: int) -> None:
+    _check(load().hd_binned_destroy(b), "hd_binned_destroy")
+
+
+def hd_binned_reset(b: int, stream=None) -> None:
+    _check(load().hd_binned_reset(b, _stream(stream)), "hd_binned_reset")
+
+
+def _hist_ptrs(arrs):
+    if len(arrs) != 6:
+        raise ValueError("six history arrays (angle, u_in, v_in, u_out, v_out, wepl)")
+    n = None
+    ptrs = []
+    for a in arrs:
+        p, _ = _ptr(a)
+        m = int(a.numel() if _is_torch(a) else a.size)
+        n = m if n is None else n
+        if m != n:
+            raise ValueError("history arrays differ in length")
+        ptrs.append(p)
+    return ptrs, n or 0
+
+
+def hd_binned_add_histories(b: int, angle_deg, u_in, v_in, u_out, v_out, wepl,
+                            stream=None) -> None:
+    ptrs, n = _hist_ptrs([angle_deg, u_in, v_in, u_out, v_out, wepl])
+    _check(load().hd_binned_add_histories(b, *ptrs, n, _stream(stream)),
+           "hd_binned_add_histories")
+
+
+def hd_binned_cut_histories(b: int, angle_deg, u_in, v_in, u_out, v_out, wepl,
+                            stream=None) -> None:
+    ptrs, n = _hist_ptrs([angle_deg, u_in, v_in, u_out, v_out, wepl])
+    _check(load().hd_binned_cut_histories(b, *ptrs, n, _stream(stream)),
+           "hd_binned_cut_histories")
+
+
+def hd_binned_finalize(b: int, stream=None) -> None:
+    _check(load().hd_binned_finalize(b, _stream(stream)), "hd_binned_finalize")
+
+
+def hd_binned_run(b: int, angle_deg, u_in, v_in, u_out, v_out, wepl, stream=None) -> None:
+    ptrs, n = _hist_ptrs([angle_deg, u_in, v_in, u_out, v_out, wepl])
+    _check(load().hd_binned_run(b, *ptrs, n, _stream(stream)), "hd_binned_run")
+
+
+def hd_binned_get_image(b: int, which: int, dst, stream=None) -> None:
+    p, on = _ptr(dst)
+    n = int(dst.numel() if _is_torch(dst) else dst.size)
+    _check(load().hd_binned_get_image(b, int(which), p, n, on, _stream(stream)),
+           "hd_binned_get_image")
+
+
+def hd_binned_get_bins(b: int, dst, stream=None) -> None:
+    p, on = _ptr(dst)
+    n = int(dst.numel() if _is_torch(dst) else dst.size) // 9
+    _check(load().hd_binned_get_bins(b, p, n, on, _stream(stream)), "hd_binned_get_bins")
+
+
+def hd_binned_get_stats(b: int, stream=None) -> dict:
+    out = hd_binned_stats()
+    _check(load().hd_binned_get_stats(b, ctypes.byref(out), _stream(stream)),
+           "hd_binned_get_stats")
+    return out.as_dict()
+
+
+class Binned:
+    """Binned SC object (owns an hd_binned handle)."""
+
+    def __init__(self, geometry, params=None):
+        self.geometry = geometry
+        self.params = _binned_params(params, geometry)
+        self.handle = hd_binned_create(geometry, self.params)
+        n_ang = int(round(360.0 / self.params.angle_bin_deg))
+        self.n_bins = n_ang * self.params.n_u * self.params.n_v
+
+    def close(self):
+        if self.handle:
+            hd_binned_destroy(self.handle)
+            self.handle = 0
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def run(self, arrays, stream=None):
+        hd_binned_run(self.handle, *arrays, stream=stream)
+
+    def add(self, arrays, stream=None):
+        hd_binned_add_histories(self.handle, *arrays, stream=stream)
+
+    def cut(self, arrays, stream=None):
+        hd_binned_cut_histories(self.handle, *arrays, stream=stream)
+
+    def finalize(self, stream=None):
+        hd_binned_finalize(self.handle, stream)
+
+    def image(self, which: int = HD_BINNED_HULL, stream=None) -> np.ndarray:
+        g = self.geometry
+        out = np.zeros(int(g.nx) * int(g.ny) * int(g.nz), np.uint8)
+        hd_binned_get_image(self.handle, which, out, stream)
+        self._sync(stream)
+        return out
+
+    def bins(self, stream=None) -> np.ndarray:
+        out = np.zeros((self.n_bins, 9), np.int64)
+        hd_binned_get_bins(self.handle, out, stream)
+        self._sync(stream)
+        return out
+
+    def stats(self, stream=None) -> dict:
+        return hd_binned_get_stats(self.handle, stream)
+
+    def _sync(self, stream):
+        hd_binned_get_stats(self.handle, stream)  # synchronises the stream
