@@ -527,15 +527,17 @@ class BinnedParams:
     min_count: int = 11
 
     def q(self) -> _OBinned:
-        ang_q = int(round(self.angle_bin_deg * 65536))
+        """Integer form; the parameters are float32 values, scaled exactly
+        and rounded to nearest even."""
+        def fx(v, scale):
+            return int(np.rint(np.float64(np.float32(v)) * scale))
+        ang_q = fx(self.angle_bin_deg, 65536)
         n_ang = (360 * 65536) // ang_q
         if n_ang * ang_q != 360 * 65536:
             raise ValueError("angle bins must tile 360 degrees")
-        return _OBinned(n_ang, self.n_u, self.v_bins, ang_q,
-                        int(round(self.u_bin_mm * 65536)), int(round(self.v_bin_mm * 65536)),
-                        int(round(self.u_lo_mm * 65536)), int(round(self.v_lo_mm * 65536)),
-                        self.k_sigma, int(np.rint(np.float64(np.float32(self.miss_wepl_mm))
-                                                  * 256.0)),
+        return _OBinned(n_ang, self.n_u, self.v_bins, ang_q, fx(self.u_bin_mm, 65536),
+                        fx(self.v_bin_mm, 65536), fx(self.u_lo_mm, 65536),
+                        fx(self.v_lo_mm, 65536), self.k_sigma, fx(self.miss_wepl_mm, 256),
                         self.window, self.min_count)
 
     @property
