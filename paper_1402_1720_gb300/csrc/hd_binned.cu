@@ -12,9 +12,9 @@
 //                        integers against the finished statistics, kept n
 //                        and kept WEPL sum by 2 atomics
 //   binned_carve_kernel  one block per (angle bin, slice): the lines of the
-//                        block's missed bins walked into a bitmap of the slice
-//                        in shared memory, merged into the volume bitmap with
-//                        one atomicAnd per changed word
+//                        block's missed bins walked run by run into a bitmap
+//                        of the slice in shared memory, merged into the
+//                        volume bitmap with one atomicAnd per changed word
 //   binned_filter_kernel one thread per voxel: the window count of uncarved
 //                        voxels, the hull byte and the carved byte
 #include <cmath>
@@ -34,7 +34,7 @@ struct BinQ {
 namespace {
 
 constexpr int kBinThreads = 256;
-constexpr int kCarveThreads = 128;
+constexpr int kCarveThreads = 192;
 constexpr int kAccWords = 9;
 constexpr int kCtrWords = 8;
 constexpr int kMaxSmemWords = 48 * 1024;  // slice bitmaps up to 192 KB in shared memory
@@ -160,17 +160,32 @@ __global__ void __launch_bounds__(kBinThreads) binned_bins_kernel(const unsigned
     warp_add(missed, ctr + 3);
 }
 
-// Clears the bit of voxel v in a slice bitmap; voxels outside the slice
-// (none, for a line at a slice's centre height) are skipped.
-struct SliceCarve {
-    uint32_t *img;
-    uint32_t base, plane;
-    __device__ __forceinline__ void operator()(uint32_t v) const
-    {
-        const uint32_t l = v - base;
-        if (l < plane) atomicAnd(img + (l >> 5), ~(1u << (l & 31u)));
+// Clears the bits of one run of a line in a slice bitmap (bit x + nx y,
+// 1 = not carved).  An x-major run is a row segment, contiguous bits cleared
+// a word at a time; a y-major run (row = x) is a column segment, one bit per
+// voxel.  Runs come from a walk clipped to the slice, so they lie inside it;
+// the checks only guard the bitmap.
+__device__ __forceinline__ void clear_run(uint32_t *img, bool ymaj, int row, int lo, int hi,
+                                          int nx, uint32_t plane)
+{
+    if (!ymaj) {
+        const uint32_t l0 = static_cast<uint32_t>(row * nx + lo);
+        const uint32_t l1 = static_cast<uint32_t>(row * nx + hi);
+        if (l1 >= plane || l0 > l1) return;
+        const uint32_t w0 = l0 >> 5, w1 = l1 >> 5;
+        for (uint32_t w = w0; w <= w1; ++w) {
+            const uint32_t a = w == w0 ? (l0 & 31u) : 0u;
+            const uint32_t b = w == w1 ? (l1 & 31u) : 31u;
+            const uint32_t m = b - a == 31u ? 0xffffffffu : ((1u << (b - a + 1u)) - 1u) << a;
+            atomicAnd(img + w, ~m);
+        }
+    } else {
+        for (int y = lo; y <= hi; ++y) {
+            const uint32_t l = static_cast<uint32_t>(row + nx * y);
+            if (l < plane) atomicAnd(img + (l >> 5), ~(1u << (l & 31u)));
+        }
     }
-};
+}
 
 // Host-computed line tables: centre angle of each angle bin, lateral centre
 // of each u bin, centre height and vertical bin (or -1) of each slice.
@@ -179,39 +194,75 @@ struct LineTables {
     const int *slice_bin;
 };
 
+constexpr int kMaxLinesPerBlock = 1024;  // lateral bins a block lists at once
+
+// One block per (angle bin, slice): the block's missed bins are listed in
+// shared memory, then each thread walks lines from the list.  A line lies at
+// the slice's centre height, so its walk is clipped to the slice (a box one
+// voxel deep) and is lean unless a crossing ties with another: the runs then
+// come from the closed-form cursor, otherwise from the general run walk.
 template <bool kShared>
 __global__ void __launch_bounds__(kCarveThreads) binned_carve_kernel(
     const unsigned long long *acc, BinQ b, GeomQ g, Cordic cd, LineTables t, uint32_t *bits,
     int wps, unsigned long long *ctr)
 {
     extern __shared__ uint32_t sm[];
+    __shared__ int s_list[kMaxLinesPerBlock];
+    __shared__ int s_n;
     const int ia = blockIdx.x, z = blockIdx.y;
     const int iv = t.slice_bin[z];
     if (iv < 0) return;  // the same for the whole block
     uint32_t *gimg = bits + static_cast<size_t>(z) * wps;
-    if (kShared) {
+    uint32_t *img = kShared ? sm : gimg;
+    if (kShared)
         for (int w = threadIdx.x; w < wps; w += blockDim.x) sm[w] = 0xffffffffu;
-        __syncthreads();
-    }
     const uint32_t plane = static_cast<uint32_t>(g.nx) * static_cast<uint32_t>(g.ny);
-    const SliceCarve carve{kShared ? sm : gimg, static_cast<uint32_t>(z) * plane, plane};
     const float la = t.ang_c[ia], zc = t.zc[z];
     unsigned long long lines = 0, outside = 0;
-    for (int iu = threadIdx.x; iu < b.n_u; iu += blockDim.x) {
-        const long long bi =
-            ia + static_cast<long long>(b.n_ang) * (iu + static_cast<long long>(b.n_u) * iv);
-        if (!bin_missed(acc + kAccWords * bi, b.miss_q8)) continue;
-        ++lines;
-        const float lu = t.u_c[iu];
-        int32_t r[6];
-        if (!endpoints(g, cd, la, lu, zc, lu, zc, r)) {
-            ++outside;
-            continue;
+    for (int base = 0; base < b.n_u; base += kMaxLinesPerBlock) {
+        if (threadIdx.x == 0) s_n = 0;
+        __syncthreads();
+        const int end = min(b.n_u, base + kMaxLinesPerBlock);
+        for (int iu = base + threadIdx.x; iu < end; iu += blockDim.x) {
+            const long long bi = ia + static_cast<long long>(b.n_ang) *
+                                          (iu + static_cast<long long>(b.n_u) * iv);
+            if (bin_missed(acc + kAccWords * bi, b.miss_q8)) s_list[atomicAdd(&s_n, 1)] = iu;
         }
-        walk_path(r, g.nx, g.ny, g.nz, carve);
+        __syncthreads();
+        const int nl = s_n;
+        for (int j = threadIdx.x; j < nl; j += blockDim.x) {
+            ++lines;
+            const float lu = t.u_c[s_list[j]];
+            int32_t r[6];
+            if (!endpoints(g, cd, la, lu, zc, lu, zc, r)) {
+                ++outside;
+                continue;
+            }
+            const int32_t gi[3] = {r[0], r[1], r[2] - (z << 16)};
+            const int32_t go[3] = {r[3], r[4], r[5] - (z << 16)};
+            RunWalk w;
+            if (!run_begin(w, gi, go, g.nx, g.ny, 1)) continue;
+            const bool ymaj = (w.flags >> 5) & 1;
+            LeanWalk L;
+            int row, lo, hi;
+            if (lean_of(w, L)) {
+                uint32_t o[kLeanWords];
+                lean_pack(L, o);
+                LeanCursor c;
+                if (!lean_start(o, 1, c)) continue;  // rows counted one by one
+                unsigned ends = 0;
+                bool more;
+                do {
+                    more = lean_run(c, row, lo, hi, ends);
+                    clear_run(img, ymaj, row, lo, hi, g.nx, plane);
+                } while (more);
+            } else {
+                while (run_next(w, row, lo, hi)) clear_run(img, ymaj, row, lo, hi, g.nx, plane);
+            }
+        }
+        __syncthreads();  // the list is rebuilt next round
     }
     if (kShared) {
-        __syncthreads();
         for (int w = threadIdx.x; w < wps; w += blockDim.x) {
             const uint32_t m = sm[w];
             if (m != 0xffffffffu) atomicAnd(gimg + w, m);
