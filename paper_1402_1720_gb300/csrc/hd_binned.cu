@@ -208,7 +208,8 @@ __global__ void __launch_bounds__(kCarveThreads) binned_carve_kernel(
 {
     extern __shared__ uint32_t sm[];
     __shared__ int s_list[kMaxLinesPerBlock];
-    __shared__ int s_n;
+    __shared__ int s_warp[kCarveThreads / 32];
+    __shared__ long long s_cs[2];
     const int ia = blockIdx.x, z = blockIdx.y;
     const int iv = t.slice_bin[z];
     if (iv < 0) return;  // the same for the whole block
@@ -217,24 +218,46 @@ __global__ void __launch_bounds__(kCarveThreads) binned_carve_kernel(
     if (kShared)
         for (int w = threadIdx.x; w < wps; w += blockDim.x) sm[w] = 0xffffffffu;
     const uint32_t plane = static_cast<uint32_t>(g.nx) * static_cast<uint32_t>(g.ny);
-    const float la = t.ang_c[ia], zc = t.zc[z];
+    const float zc = t.zc[z];
+    if (threadIdx.x == 0) {  // the block's gantry cos and sin, once
+        long long c, sn;
+        cordic_cs(q16_of(t.ang_c[ia]), cd, c, sn);
+        s_cs[0] = c;
+        s_cs[1] = sn;
+    }
+    const unsigned lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
     unsigned long long lines = 0, outside = 0;
     for (int base = 0; base < b.n_u; base += kMaxLinesPerBlock) {
-        if (threadIdx.x == 0) s_n = 0;
-        __syncthreads();
+        // the chunk's missed bins, listed in lateral order (neighbouring
+        // lanes then walk neighbouring, similar lines)
         const int end = min(b.n_u, base + kMaxLinesPerBlock);
-        for (int iu = base + threadIdx.x; iu < end; iu += blockDim.x) {
-            const long long bi = ia + static_cast<long long>(b.n_ang) *
-                                          (iu + static_cast<long long>(b.n_u) * iv);
-            if (bin_missed(acc + kAccWords * bi, b.miss_q8)) s_list[atomicAdd(&s_n, 1)] = iu;
+        int nl = 0;
+        for (int c0 = base; c0 < end; c0 += blockDim.x) {
+            const int iu = c0 + static_cast<int>(threadIdx.x);
+            bool miss = false;
+            if (iu < end) {
+                const long long bi = ia + static_cast<long long>(b.n_ang) *
+                                              (iu + static_cast<long long>(b.n_u) * iv);
+                miss = bin_missed(acc + kAccWords * bi, b.miss_q8);
+            }
+            const unsigned bal = __ballot_sync(0xffffffffu, miss);
+            if (lane == 0) s_warp[warp] = __popc(bal);
+            __syncthreads();
+            int off = nl, tot = 0;
+            for (int k = 0; k < static_cast<int>(blockDim.x >> 5); ++k) {
+                off += k < static_cast<int>(warp) ? s_warp[k] : 0;
+                tot += s_warp[k];
+            }
+            if (miss) s_list[off + __popc(bal & ((1u << lane) - 1u))] = iu;
+            nl += tot;
+            __syncthreads();
         }
-        __syncthreads();
-        const int nl = s_n;
+        const long long cs = s_cs[0], sn = s_cs[1];
         for (int j = threadIdx.x; j < nl; j += blockDim.x) {
             ++lines;
             const float lu = t.u_c[s_list[j]];
             int32_t r[6];
-            if (!endpoints(g, cd, la, lu, zc, lu, zc, r)) {
+            if (!endpoints_cs(g, cs, sn, lu, zc, lu, zc, r)) {
                 ++outside;
                 continue;
             }

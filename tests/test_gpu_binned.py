@@ -215,3 +215,25 @@ def test_config2_full_size(hd, oracle_mod):
     b = _run(hd, g, bp, w.histories)
     _compare(hd, g, bp, b, ref)
     b.close()
+
+
+def test_extreme_values_exact(hd, oracle_mod):
+    """WEPL and slopes near the 1024 mm limit, thousands of histories per
+    bin (sums of squares near 2^48), with rare extreme values that the cuts
+    remove: the integer square root of the cut bounds must be exact."""
+    g = synth.Geometry(16, 16, 4, 1.0, 1.0, 2.5, 30.0)
+    bp = oracle_mod.binned_params_for(g)
+    rng = np.random.default_rng(11)
+    n = 40000
+    ang = rng.integers(0, 3, n) * 4.0
+    um = rng.choice([-3.5, 0.5, 4.5], n)
+    vm = np.full(n, 1.0)
+    du = rng.choice([-1023.9, 1023.9, 0.0, -1000.0, 511.7], n, p=[0.003, 0.003, 0.5, 0.25, 0.244])
+    dv = rng.choice([1023.9, -1023.9, 3.0], n, p=[0.004, 0.002, 0.994])
+    wepl = rng.choice([1023.99, -1023.99, 0.0, 700.5, -0.004], n, p=[0.003, 0.002, 0.3, 0.6, 0.095])
+    h = _hist(ang, um - du / 2, vm - dv / 2, um + du / 2, vm + dv / 2, wepl)
+    ref = oracle_mod.sc_binned(g, h, bp)
+    assert ref["bins"][:, 0].max() > 1000 and ref["stats"]["cut"] > 0
+    b = _run(hd, g, bp, h)
+    _compare(hd, g, bp, b, ref)
+    b.close()
