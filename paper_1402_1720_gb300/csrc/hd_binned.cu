@@ -34,6 +34,7 @@ struct BinQ {
 namespace {
 
 constexpr int kBinThreads = 256;
+constexpr int kPassBlocksPerSm = 6;  // resident blocks of the per-history passes (40 registers)
 constexpr int kCarveThreads = 192;
 constexpr int kAccWords = 9;
 constexpr int kCtrWords = 8;
@@ -89,7 +90,7 @@ __device__ __forceinline__ void warp_add(unsigned long long v, unsigned long lon
     if ((threadIdx.x & 31) == 0 && v != 0) atomicAdd(dst, v);
 }
 
-__global__ void __launch_bounds__(kBinThreads) binned_stats_kernel(Inputs in, int64_t n, BinQ b,
+__global__ void __launch_bounds__(kBinThreads, kPassBlocksPerSm) binned_stats_kernel(Inputs in, int64_t n, BinQ b,
                                                                    unsigned long long *acc,
                                                                    unsigned long long *ctr)
 {
@@ -115,7 +116,7 @@ __global__ void __launch_bounds__(kBinThreads) binned_stats_kernel(Inputs in, in
 
 // Reads words 0-6 of a bin row (fixed since the statistics phase ended)
 // while other threads add to words 7 and 8.
-__global__ void __launch_bounds__(kBinThreads) binned_cut_kernel(Inputs in, int64_t n, BinQ b,
+__global__ void __launch_bounds__(kBinThreads, kPassBlocksPerSm) binned_cut_kernel(Inputs in, int64_t n, BinQ b,
                                                                  unsigned long long *acc,
                                                                  unsigned long long *ctr)
 {
@@ -324,10 +325,10 @@ __global__ void __launch_bounds__(256) binned_filter_kernel(const uint32_t *bits
     carved[v] = static_cast<uint8_t>(bit(x, y));
 }
 
-int grid_for(int64_t n, int sm_count)
+int grid_for(int64_t n, int sm_count, int per_sm = 8)
 {
     int64_t blocks = (n + kBinThreads - 1) / kBinThreads;
-    const int64_t cap = static_cast<int64_t>(sm_count > 0 ? sm_count : 1) * 8;
+    const int64_t cap = static_cast<int64_t>(sm_count > 0 ? sm_count : 1) * per_sm;
     if (blocks > cap) blocks = cap;
     return static_cast<int>(blocks < 1 ? 1 : blocks);
 }
@@ -464,7 +465,7 @@ hd_status pass(hd_binned *b, const float *angle_deg, const float *u_in, const fl
     const hd_status v = check_inputs(p, 6);
     if (v != HD_OK) return v;
     const hd::Inputs in{angle_deg, u_in, v_in, u_out, v_out, wepl};
-    const int grid = hd::grid_for(n, b->sm_count);
+    const int grid = hd::grid_for(n, b->sm_count, hd::kPassBlocksPerSm);  // one wave
     if (cut)
         hd::binned_cut_kernel<<<grid, hd::kBinThreads, 0, st>>>(in, n, b->bq, b->acc, b->ctr);
     else
