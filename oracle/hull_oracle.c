@@ -354,6 +354,79 @@ int oracle_accumulate(const og_geom *g, float tau_l, float tau_h, int32_t method
     return 0;
 }
 
+/* ------------------------------- hull diagnostics (next row f3) */
+
+/* Extra and missing voxels of a hull against the true object (the counts of
+ * Tables 1-2, Sec. 4): per slice z, counts[z] = |{v in z : hull, not object}|
+ * and counts[nz + z] = |{v in z : object, not hull}|; counts[2 nz] and
+ * counts[2 nz + 1] are the totals. */
+void oracle_hull_compare(const uint8_t *hull, const uint8_t *object, int32_t nx, int32_t ny,
+                         int32_t nz, int64_t *counts)
+{
+    const int64_t plane = (int64_t)nx * ny;
+    for (int64_t i = 0; i < 2 * (int64_t)nz + 2; ++i) counts[i] = 0;
+    for (int64_t z = 0; z < nz; ++z)
+        for (int64_t j = 0; j < plane; ++j) {
+            const int h = hull[z * plane + j] != 0, o = object[z * plane + j] != 0;
+            if (h && !o) counts[z] += 1;
+            if (o && !h) counts[nz + z] += 1;
+        }
+    for (int64_t z = 0; z < nz; ++z) {
+        counts[2 * nz] += counts[z];
+        counts[2 * nz + 1] += counts[nz + z];
+    }
+}
+
+/* The voxels of a mask that it encloses within their slice: out = mask
+ * minus every mask voxel joined to the slice's border by a 4-connected path
+ * of mask voxels (a breadth-first search from the border).  Applied to the
+ * literal MSC hull H_2 (Eq. 3.6), which excludes only a shell of steep
+ * drops, it keeps the region the shell encloses.  Returns 0, -1 when out of
+ * memory. */
+int oracle_fill_enclosed(const uint8_t *mask, int32_t nx, int32_t ny, int32_t nz, uint8_t *out)
+{
+    const int64_t plane = (int64_t)nx * ny;
+    int64_t *queue = (int64_t *)malloc(sizeof(int64_t) * (size_t)plane);
+    uint8_t *seen = (uint8_t *)malloc((size_t)plane);
+    if (!queue || !seen) {
+        free(queue);
+        free(seen);
+        return -1;
+    }
+    for (int64_t z = 0; z < nz; ++z) {
+        const uint8_t *m = mask + z * plane;
+        memset(seen, 0, (size_t)plane);
+        int64_t head = 0, tail = 0;
+        for (int64_t y = 0; y < ny; ++y)
+            for (int64_t x = 0; x < nx; ++x) {
+                const int border = x == 0 || y == 0 || x == nx - 1 || y == ny - 1;
+                const int64_t j = x + nx * y;
+                if (border && m[j] && !seen[j]) {
+                    seen[j] = 1;
+                    queue[tail++] = j;
+                }
+            }
+        while (head < tail) {
+            const int64_t j = queue[head++];
+            const int64_t x = j % nx, y = j / nx;
+            const int64_t nb[4][2] = {{x - 1, y}, {x + 1, y}, {x, y - 1}, {x, y + 1}};
+            for (int k = 0; k < 4; ++k) {
+                const int64_t X = nb[k][0], Y = nb[k][1];
+                if (X < 0 || X >= nx || Y < 0 || Y >= ny) continue;
+                const int64_t w = X + nx * Y;
+                if (m[w] && !seen[w]) {
+                    seen[w] = 1;
+                    queue[tail++] = w;
+                }
+            }
+        }
+        for (int64_t j = 0; j < plane; ++j) out[z * plane + j] = m[j] && !seen[j];
+    }
+    free(queue);
+    free(seen);
+    return 0;
+}
+
 /* ------------------------------- SC as the paper ran it (next row f2) */
 
 /* Binned SC (Sec. 2.2 data cuts; Sec. 3.2, its implementation paragraphs).

@@ -91,6 +91,10 @@ def lib():
                                               ctypes.c_int32, i64p, ctypes.c_int64] + \
                 [f32p] * 6 + [ctypes.c_int64, u32p, u32p, i64p]
             L.oracle_compare_fp64.restype = ctypes.c_int
+            L.oracle_hull_compare.argtypes = [u8p, u8p] + [ctypes.c_int32] * 3 + [i64p]
+            L.oracle_hull_compare.restype = None
+            L.oracle_fill_enclosed.argtypes = [u8p] + [ctypes.c_int32] * 3 + [u8p]
+            L.oracle_fill_enclosed.restype = ctypes.c_int
             L.oracle_bin_line.argtypes = [ctypes.c_void_p, ctypes.c_int64, f32p, f32p]
             L.oracle_bin_line.restype = None
             L.oracle_slice_bin.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
@@ -497,6 +501,31 @@ def system_rows(g, hist, hull, threads: Optional[int] = 1) -> Tuple[np.ndarray, 
     row_ptr = np.zeros(n + 1, np.int64)
     np.cumsum(nnz, out=row_ptr[1:])
     return row_ptr, cols
+
+
+# ------------------------------------------ hull diagnostics (next row f3)
+def hull_compare(hull, obj, dims) -> Dict:
+    """Extra (hull, not object) and missing (object, not hull) voxels per
+    slice and in total (the counts of Tables 1-2)."""
+    nx, ny, nz = dims
+    h = np.ascontiguousarray(hull, np.uint8).ravel()
+    o = np.ascontiguousarray(obj, np.uint8).ravel()
+    counts = np.zeros(2 * nz + 2, np.int64)
+    lib().oracle_hull_compare(_p(h, ctypes.c_uint8), _p(o, ctypes.c_uint8), nx, ny, nz,
+                              _p(counts, ctypes.c_int64))
+    return {"extra_per_slice": counts[:nz].copy(), "missing_per_slice": counts[nz:2 * nz].copy(),
+            "extra": int(counts[2 * nz]), "missing": int(counts[2 * nz + 1])}
+
+
+def fill_enclosed(mask, dims) -> np.ndarray:
+    """Mask voxels not joined to their slice's border through the mask
+    (4-connected), per slice."""
+    nx, ny, nz = dims
+    m = np.ascontiguousarray(mask, np.uint8).ravel()
+    out = np.zeros_like(m)
+    if lib().oracle_fill_enclosed(_p(m, ctypes.c_uint8), nx, ny, nz, _p(out, ctypes.c_uint8)):
+        raise MemoryError("oracle_fill_enclosed")
+    return out
 
 
 # ------------------------------------ SC as the paper ran it (next row f2)

@@ -193,6 +193,27 @@ def object_rsp_at(points: np.ndarray, phantom: Sequence[Ellipsoid]) -> np.ndarra
     return rsp
 
 
+def voxel_centres(geom: Geometry) -> np.ndarray:
+    """World coordinates (V, 3) of the voxel centres, x fastest."""
+    xs = (np.arange(geom.nx) + 0.5 - geom.nx / 2) * geom.sx
+    ys = (np.arange(geom.ny) + 0.5 - geom.ny / 2) * geom.sy
+    zs = (np.arange(geom.nz) + 0.5 - geom.nz / 2) * geom.sz
+    Z, Y, X = np.meshgrid(zs, ys, xs, indexing="ij")
+    return np.stack([X.ravel(), Y.ravel(), Z.ravel()], axis=1)
+
+
+def object_mask(geom: Geometry, phantom: Sequence[Ellipsoid]) -> np.ndarray:
+    """The true object as a uint8 voxel mask: voxels whose centre lies inside
+    any ellipsoid of the phantom (air cavities inside the head count as
+    object, as a hull should enclose them)."""
+    pts = voxel_centres(geom)
+    inside = np.zeros(len(pts), bool)
+    for e in phantom:
+        q = (pts - np.asarray(e.center)) / np.asarray(e.semi)
+        inside |= np.einsum("ij,ij->i", q, q) < 1.0
+    return inside.astype(np.uint8)
+
+
 # ---------------------------------------------------------------- histories
 def make_histories(rng: np.random.Generator, geom: Geometry, phantom, angles_deg,
                    per_angle: int, u_half: float, v_half: float,
