@@ -499,6 +499,30 @@ HD_API hd_status hd_classify(const float *wepl, int64_t n, const hd_params *para
                       int32_t on_device, void *stream);
 
 /* ------------------------------------------------------------------------
+ * Hull diagnostics (not steps of the method: the measures the paper reports
+ * and a fill variant of MSC's hull).  All pointers are device pointers; the
+ * volumes are uint8 masks of nx * ny * nz voxels, x fastest.
+ *
+ * Extra and missing voxels of `hull` against the true object `object` (the
+ * counts of Tables 1-2, Sec. 4): counts (device, 2 nz + 2 int64) receives
+ * per slice z the extra voxels (hull, not object) at [z] and the missing
+ * ones (object, not hull) at [nz + z], and the totals at [2 nz] and
+ * [2 nz + 1].  Stream-ordered. */
+HD_API hd_status hd_hull_compare(const uint8_t *hull, const uint8_t *object, int32_t nx,
+                                 int32_t ny, int32_t nz, int64_t *counts, void *stream);
+
+/* The part of `mask` it encloses within each slice: out = mask minus every
+ * mask voxel joined to the slice's border by a 4-connected path of mask
+ * voxels.  Applied to the literal MSC hull H_2 (Eq. 3.6), which excludes only
+ * the shell of voxels with a steep drop of N, it keeps the region the shell
+ * encloses (Eq. 3.6 alone also keeps the far exterior, where N is smooth).
+ * HD_ERR_RANGE when ny * ceil(nx / 32) > 24576 (the two slice bitmaps must
+ * fit shared memory: up to 784 x 784 voxels per slice).  out may not alias
+ * mask.  Stream-ordered. */
+HD_API hd_status hd_fill_enclosed(const uint8_t *mask, int32_t nx, int32_t ny, int32_t nz,
+                                  uint8_t *out, void *stream);
+
+/* ------------------------------------------------------------------------
  * Binned SC: SC as the paper ran it (Sec. 2.2 data cuts; Sec. 3.2, its
  * implementation paragraphs).  Histories are binned by gantry angle and by
  * the lateral and vertical displacement of the path's mid-point,

@@ -187,6 +187,8 @@ _SIGS = {
     "hd_server_get_stats": ([_VP, ctypes.POINTER(hd_server_stats)], ctypes.c_int),
     "hd_server_close_scan": ([_VP, _I64], ctypes.c_int),
     "hd_scan_get_profile": ([_VP, ctypes.POINTER(hd_profile)], ctypes.c_int),
+    "hd_hull_compare": ([_VP, _VP, _I32, _I32, _I32, _VP, _VP], ctypes.c_int),
+    "hd_fill_enclosed": ([_VP, _I32, _I32, _I32, _VP, _VP], ctypes.c_int),
     "hd_binned_params_default": ([ctypes.POINTER(hd_geometry), ctypes.POINTER(hd_binned_params)],
                                  ctypes.c_int),
     "hd_binned_create": ([ctypes.POINTER(hd_geometry), ctypes.POINTER(hd_binned_params),
@@ -960,3 +962,35 @@ class Binned:
 
     def _sync(self, stream):
         hd_binned_get_stats(self.handle, stream)  # synchronises the stream
+
+
+# ------------------------------------------------------- hull diagnostics
+def _dev_ptr(x, what):
+    p, on = _ptr(x)
+    if not on:
+        raise ValueError(f"{what} must be a device tensor")
+    return p
+
+
+def hd_hull_compare(hull, obj, dims, counts=None, stream=None):
+    """Extra/missing voxels per slice and in total (device tensors); returns
+    the counts tensor (2 nz + 2 int64, on the device)."""
+    import torch
+    nx, ny, nz = (int(d) for d in dims)
+    if counts is None:
+        counts = torch.empty(2 * nz + 2, dtype=torch.int64, device=hull.device)
+    _check(load().hd_hull_compare(_dev_ptr(hull, "hull"), _dev_ptr(obj, "object"), nx, ny, nz,
+                                  _dev_ptr(counts, "counts"), _stream(stream)), "hd_hull_compare")
+    return counts
+
+
+def hd_fill_enclosed(mask, dims, out=None, stream=None):
+    """Per slice, the mask voxels not joined to the border (device tensors)."""
+    import torch
+    nx, ny, nz = (int(d) for d in dims)
+    src = _dev_ptr(mask, "mask")
+    if out is None:
+        out = torch.empty_like(mask)
+    _check(load().hd_fill_enclosed(src, nx, ny, nz, _dev_ptr(out, "out"), _stream(stream)),
+           "hd_fill_enclosed")
+    return out
