@@ -169,6 +169,12 @@ static int rat_cmp(const void *a, const void *b)
     return (l < r) ? -1 : (l > r) ? 1 : 0;
 }
 
+static int cmp_u32(const void *a, const void *b)
+{
+    const uint32_t x = *(const uint32_t *)a, y = *(const uint32_t *)b;
+    return (x > y) - (x < y);
+}
+
 static int cmp_i64(const void *a, const void *b)
 {
     int64_t x = *(const int64_t *)a, y = *(const int64_t *)b;
@@ -424,6 +430,143 @@ int oracle_fill_enclosed(const uint8_t *mask, int32_t nx, int32_t ny, int32_t nz
     }
     free(queue);
     free(seen);
+    return 0;
+}
+
+/* ------------------------- SM threshold by edge detection (next row f3) */
+
+/* A documented form of the "modified Canny" picker of Sec. 4 (the paper
+ * names the method, not its modification): per slice of M,
+ *   S   = M smoothed with the 3x3 binomial kernel [1 2 1]^T [1 2 1] (edge
+ *         values replicated beyond the slice),
+ *   G   = Sobel derivatives of S (replicated), magnitude |Gx| + |Gy|,
+ *   NMS = a voxel whose magnitude is at least its neighbour's against the
+ *         gradient and above its neighbour's along it (the gradient points
+ *         to larger M, so a tie keeps the voxel on the object's side);
+ *         direction: along x when 5 |Gy| < 2 |Gx|, along y when
+ *         5 |Gx| < 2 |Gy|, else the diagonal of sign(Gx Gy); neighbours
+ *         outside the slice have magnitude 0,
+ *   edge = NMS voxels with 5 mag >= max (weak) joined through weak voxels
+ *         (8-connected) to one with 2 mag >= max (strong), max = the
+ *         slice's largest NMS magnitude,
+ *   M_t = the element of index floor(q (k - 1) / 100) of the sorted M
+ *         values of the k edge voxels, H_3 = [M >= M_t]; a slice without
+ *         edge voxels (max = 0) gets H_3 = 0 (as the slope picker does).
+ * All integer arithmetic.  Intermediate images are returned when their
+ * pointers are not NULL.  Returns 0, -1 when out of memory. */
+static int64_t clampi(int64_t v, int64_t lo, int64_t hi) { return v < lo ? lo : (v > hi ? hi : v); }
+
+int oracle_sm_canny(const uint32_t *M, int32_t nx, int32_t ny, int32_t nz, int32_t q_pct,
+                    uint32_t *mt, uint8_t *has_edge, uint8_t *H3, int64_t *S_out,
+                    int64_t *gx_out, int64_t *gy_out, int64_t *mag_out, uint8_t *nms_out,
+                    uint8_t *edge_out)
+{
+    const int64_t plane = (int64_t)nx * ny;
+    int64_t *S = (int64_t *)malloc(sizeof(int64_t) * (size_t)plane);
+    int64_t *gx = (int64_t *)malloc(sizeof(int64_t) * (size_t)plane);
+    int64_t *gy = (int64_t *)malloc(sizeof(int64_t) * (size_t)plane);
+    int64_t *mag = (int64_t *)malloc(sizeof(int64_t) * (size_t)plane);
+    uint8_t *nms = (uint8_t *)malloc((size_t)plane);
+    uint8_t *edge = (uint8_t *)malloc((size_t)plane);
+    int64_t *queue = (int64_t *)malloc(sizeof(int64_t) * (size_t)plane);
+    uint32_t *vals = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)plane);
+    if (!S || !gx || !gy || !mag || !nms || !edge || !queue || !vals) {
+        free(S); free(gx); free(gy); free(mag); free(nms); free(edge); free(queue); free(vals);
+        return -1;
+    }
+    static const int64_t bw[3] = {1, 2, 1};
+    for (int64_t z = 0; z < nz; ++z) {
+        const uint32_t *m = M + z * plane;
+        for (int64_t y = 0; y < ny; ++y) /* smoothing */
+            for (int64_t x = 0; x < nx; ++x) {
+                int64_t acc = 0;
+                for (int dy = -1; dy <= 1; ++dy)
+                    for (int dx = -1; dx <= 1; ++dx) {
+                        const int64_t X = clampi(x + dx, 0, nx - 1), Y = clampi(y + dy, 0, ny - 1);
+                        acc += bw[dx + 1] * bw[dy + 1] * (int64_t)m[X + nx * Y];
+                    }
+                S[x + nx * y] = acc;
+            }
+        for (int64_t y = 0; y < ny; ++y) /* Sobel on S */
+            for (int64_t x = 0; x < nx; ++x) {
+                int64_t sx = 0, sy = 0;
+                for (int k = -1; k <= 1; ++k) {
+                    const int64_t Yk = clampi(y + k, 0, ny - 1), Xk = clampi(x + k, 0, nx - 1);
+                    const int64_t Xm = clampi(x - 1, 0, nx - 1), Xp = clampi(x + 1, 0, nx - 1);
+                    const int64_t Ym = clampi(y - 1, 0, ny - 1), Yp = clampi(y + 1, 0, ny - 1);
+                    sx += bw[k + 1] * (S[Xp + nx * Yk] - S[Xm + nx * Yk]);
+                    sy += bw[k + 1] * (S[Xk + nx * Yp] - S[Xk + nx * Ym]);
+                }
+                gx[x + nx * y] = sx;
+                gy[x + nx * y] = sy;
+                mag[x + nx * y] = llabs(sx) + llabs(sy);
+            }
+        int64_t mmax = 0;
+        for (int64_t y = 0; y < ny; ++y) /* non-maximum suppression */
+            for (int64_t x = 0; x < nx; ++x) {
+                const int64_t j = x + nx * y, ax = llabs(gx[j]), ay = llabs(gy[j]);
+                int64_t dx, dy;
+                if (5 * ay < 2 * ax) {
+                    dx = gx[j] > 0 ? 1 : -1;
+                    dy = 0;
+                } else if (5 * ax < 2 * ay) {
+                    dx = 0;
+                    dy = gy[j] > 0 ? 1 : -1;
+                } else {
+                    dx = gx[j] > 0 ? 1 : -1;
+                    dy = gy[j] > 0 ? 1 : -1;
+                }
+                int64_t fwd = 0, bwd = 0; /* along and against the gradient */
+                if (x + dx >= 0 && x + dx < nx && y + dy >= 0 && y + dy < ny)
+                    fwd = mag[(x + dx) + nx * (y + dy)];
+                if (x - dx >= 0 && x - dx < nx && y - dy >= 0 && y - dy < ny)
+                    bwd = mag[(x - dx) + nx * (y - dy)];
+                nms[j] = mag[j] > 0 && mag[j] >= bwd && mag[j] > fwd;
+                if (nms[j] && mag[j] > mmax) mmax = mag[j];
+            }
+        /* hysteresis: weak voxels joined (8-connected) to strong ones */
+        int64_t head = 0, tail = 0;
+        memset(edge, 0, (size_t)plane);
+        for (int64_t j = 0; j < plane; ++j)
+            if (nms[j] && mmax > 0 && 2 * mag[j] >= mmax) {
+                edge[j] = 1;
+                queue[tail++] = j;
+            }
+        while (head < tail) {
+            const int64_t j = queue[head++], x = j % nx, y = j / nx;
+            for (int dy = -1; dy <= 1; ++dy)
+                for (int dx = -1; dx <= 1; ++dx) {
+                    const int64_t X = x + dx, Y = y + dy;
+                    if (X < 0 || X >= nx || Y < 0 || Y >= ny) continue;
+                    const int64_t w = X + nx * Y;
+                    if (!edge[w] && nms[w] && 5 * mag[w] >= mmax) {
+                        edge[w] = 1;
+                        queue[tail++] = w;
+                    }
+                }
+        }
+        int64_t k = 0; /* the threshold: a quantile of M over the edge */
+        for (int64_t j = 0; j < plane; ++j)
+            if (edge[j]) vals[k++] = m[j];
+        uint8_t *h = H3 + z * plane;
+        if (k == 0) {
+            mt[z] = 0;
+            has_edge[z] = 0;
+            memset(h, 0, (size_t)plane);
+        } else {
+            qsort(vals, (size_t)k, sizeof(uint32_t), cmp_u32);
+            mt[z] = vals[((int64_t)q_pct * (k - 1)) / 100];
+            has_edge[z] = 1;
+            for (int64_t j = 0; j < plane; ++j) h[j] = m[j] >= mt[z];
+        }
+        if (S_out) memcpy(S_out + z * plane, S, sizeof(int64_t) * (size_t)plane);
+        if (gx_out) memcpy(gx_out + z * plane, gx, sizeof(int64_t) * (size_t)plane);
+        if (gy_out) memcpy(gy_out + z * plane, gy, sizeof(int64_t) * (size_t)plane);
+        if (mag_out) memcpy(mag_out + z * plane, mag, sizeof(int64_t) * (size_t)plane);
+        if (nms_out) memcpy(nms_out + z * plane, nms, (size_t)plane);
+        if (edge_out) memcpy(edge_out + z * plane, edge, (size_t)plane);
+    }
+    free(S); free(gx); free(gy); free(mag); free(nms); free(edge); free(queue); free(vals);
     return 0;
 }
 

@@ -91,6 +91,9 @@ def lib():
                                               ctypes.c_int32, i64p, ctypes.c_int64] + \
                 [f32p] * 6 + [ctypes.c_int64, u32p, u32p, i64p]
             L.oracle_compare_fp64.restype = ctypes.c_int
+            L.oracle_sm_canny.argtypes = [u32p] + [ctypes.c_int32] * 4 + [u32p, u8p, u8p] + \
+                [i64p] * 4 + [u8p, u8p]
+            L.oracle_sm_canny.restype = ctypes.c_int
             L.oracle_hull_compare.argtypes = [u8p, u8p] + [ctypes.c_int32] * 3 + [i64p]
             L.oracle_hull_compare.restype = None
             L.oracle_fill_enclosed.argtypes = [u8p] + [ctypes.c_int32] * 3 + [u8p]
@@ -525,6 +528,31 @@ def fill_enclosed(mask, dims) -> np.ndarray:
     out = np.zeros_like(m)
     if lib().oracle_fill_enclosed(_p(m, ctypes.c_uint8), nx, ny, nz, _p(out, ctypes.c_uint8)):
         raise MemoryError("oracle_fill_enclosed")
+    return out
+
+
+def sm_canny(M, dims, q_pct: int = 50, debug: bool = False) -> Dict:
+    """SM threshold per slice by the documented edge-detection picker: M_t,
+    whether the slice has an edge, H_3 = [M >= M_t]; with debug, the smoothed
+    image, Sobel derivatives, magnitude, NMS and edge masks."""
+    nx, ny, nz = dims
+    V = nx * ny * nz
+    M = np.ascontiguousarray(M, np.uint32).ravel()
+    mt = np.zeros(nz, np.uint32)
+    he = np.zeros(nz, np.uint8)
+    H3 = np.zeros(V, np.uint8)
+    dbg = [np.zeros(V, np.int64) for _ in range(4)] + [np.zeros(V, np.uint8) for _ in range(2)]
+    ptrs = [_p(a, ctypes.c_int64) for a in dbg[:4]] + [_p(a, ctypes.c_uint8) for a in dbg[4:]]
+    if not debug:
+        ptrs = [None] * 6
+    if lib().oracle_sm_canny(_p(M, ctypes.c_uint32), nx, ny, nz, int(q_pct),
+                             _p(mt, ctypes.c_uint32), _p(he, ctypes.c_uint8),
+                             _p(H3, ctypes.c_uint8), *ptrs):
+        raise MemoryError("oracle_sm_canny")
+    out = {"Mt": mt, "has_edge": he, "H3": H3}
+    if debug:
+        for k, a in zip(("S", "gx", "gy", "mag", "nms", "edge"), dbg):
+            out[k] = a
     return out
 
 
