@@ -522,6 +522,33 @@ HD_API hd_status hd_hull_compare(const uint8_t *hull, const uint8_t *object, int
 HD_API hd_status hd_fill_enclosed(const uint8_t *mask, int32_t nx, int32_t ny, int32_t nz,
                                   uint8_t *out, void *stream);
 
+/* SM threshold by edge detection: a documented form of the "modified Canny"
+ * picker the paper used for M_t (Sec. 4; the paper does not say what it
+ * modified).  Per slice of the SM count volume M (device, uint32, as
+ * hd_scan_get_counts gives it):
+ *   S = M smoothed by the 3x3 binomial kernel (edge values replicated);
+ *   Sobel derivatives of S (replicated), magnitude |Gx| + |Gy|;
+ *   non-maximum suppression along the gradient direction (along x when
+ *   5 |Gy| < 2 |Gx|, along y when 5 |Gx| < 2 |Gy|, else diagonal): a voxel
+ *   is kept when its magnitude is positive, at least its neighbour's against
+ *   the gradient and above its neighbour's along it, so a tie keeps the
+ *   voxel on the side of larger M;
+ *   hysteresis: kept voxels with 2 mag >= the slice's largest kept magnitude
+ *   are edges, and so are kept voxels with 5 mag >= it joined to an edge
+ *   (8-connected);
+ *   M_t = the element of rank floor(q_pct (k - 1) / 100) of the sorted M of
+ *   the k edge voxels; H3 = [M >= M_t].  A slice without edges gets M_t = 0,
+ *   has_edge = 0 and H3 = 0.
+ * Integer arithmetic throughout (exact).  Outputs are device arrays: mt and
+ * has_edge nz entries, H3 nx ny nz bytes.  workspace: device memory of at
+ * least hd_sm_canny_workspace bytes, 256-byte aligned, not used by anything
+ * else while the call's work runs.  HD_ERR_RANGE when ny * ceil(nx / 32) >
+ * 24576 (the slice bitmaps must fit shared memory).  Stream-ordered. */
+HD_API hd_status hd_sm_canny_workspace(int32_t nx, int32_t ny, int32_t nz, size_t *bytes);
+HD_API hd_status hd_sm_canny(const uint32_t *M, int32_t nx, int32_t ny, int32_t nz,
+                             int32_t q_pct, void *workspace, size_t workspace_bytes, uint32_t *mt,
+                             uint8_t *has_edge, uint8_t *H3, void *stream);
+
 /* ------------------------------------------------------------------------
  * Binned SC: SC as the paper ran it (Sec. 2.2 data cuts; Sec. 3.2, its
  * implementation paragraphs).  Histories are binned by gantry angle and by

@@ -188,6 +188,8 @@ _SIGS = {
     "hd_server_close_scan": ([_VP, _I64], ctypes.c_int),
     "hd_scan_get_profile": ([_VP, ctypes.POINTER(hd_profile)], ctypes.c_int),
     "hd_hull_compare": ([_VP, _VP, _I32, _I32, _I32, _VP, _VP], ctypes.c_int),
+    "hd_sm_canny_workspace": ([_I32, _I32, _I32, ctypes.POINTER(_SZ)], ctypes.c_int),
+    "hd_sm_canny": ([_VP, _I32, _I32, _I32, _I32, _VP, _SZ, _VP, _VP, _VP, _VP], ctypes.c_int),
     "hd_fill_enclosed": ([_VP, _I32, _I32, _I32, _VP, _VP], ctypes.c_int),
     "hd_binned_params_default": ([ctypes.POINTER(hd_geometry), ctypes.POINTER(hd_binned_params)],
                                  ctypes.c_int),
@@ -994,3 +996,29 @@ def hd_fill_enclosed(mask, dims, out=None, stream=None):
     _check(load().hd_fill_enclosed(src, nx, ny, nz, _dev_ptr(out, "out"), _stream(stream)),
            "hd_fill_enclosed")
     return out
+
+
+def hd_sm_canny_workspace(dims) -> int:
+    nx, ny, nz = (int(d) for d in dims)
+    out = _SZ(0)
+    _check(load().hd_sm_canny_workspace(nx, ny, nz, ctypes.byref(out)), "hd_sm_canny_workspace")
+    return out.value
+
+
+def hd_sm_canny(M, dims, q_pct: int = 50, workspace=None, stream=None):
+    """SM threshold by the documented edge-detection picker on a device
+    uint32 M volume; returns (mt, has_edge, H3) device tensors."""
+    import torch
+    nx, ny, nz = (int(d) for d in dims)
+    src = _dev_ptr(M, "M")
+    need = hd_sm_canny_workspace(dims)
+    if workspace is None:
+        workspace = torch.empty(need, dtype=torch.uint8, device=M.device)
+    mt = torch.empty(nz, dtype=torch.int32, device=M.device)
+    he = torch.empty(nz, dtype=torch.uint8, device=M.device)
+    H3 = torch.empty(nx * ny * nz, dtype=torch.uint8, device=M.device)
+    _check(load().hd_sm_canny(src, nx, ny, nz, int(q_pct), _dev_ptr(workspace, "workspace"),
+                              int(workspace.numel() * workspace.element_size()), _dev_ptr(mt, "mt"),
+                              _dev_ptr(he, "has_edge"), _dev_ptr(H3, "H3"), _stream(stream)),
+           "hd_sm_canny")
+    return mt, he, H3
