@@ -624,6 +624,85 @@ def run_binned(args):
     b.close()
 
 
+def run_diagnostics(args):
+    """Extra and missing voxels of every hull against the synthetic object
+    (the measures of Tables 1-2) on the head-sized scan, all computed on the
+    GPU: SC, MSC (Eq. 3.6 literal and its enclosed part), SM (the slope
+    picker of Alg. 3 and the documented edge-detection picker) and SC as the
+    paper ran it; plus the device time of the diagnostic operations."""
+    import torch
+    from paper_1402_1720_gb300 import build as hbuild
+    from paper_1402_1720_gb300 import hulld, synth
+    _, _, local = _dist()
+    torch.cuda.set_device(local)
+    hbuild.build()
+    hulld.load()
+    w = synth.make_config(2, fraction=args.fraction)
+    g, h = w.geometry, w.histories
+    dims = (g.nx, g.ny, g.nz)
+    dev = [torch.from_numpy(a).cuda() for a in h.arrays()]
+    obj = torch.from_numpy(synth.object_mask(g, w.phantom)).cuda()
+    scan = hulld.Scan(g)
+    scan.add(dev)
+    scan.finalize()
+    hulls = {}
+    for name, m in (("SC", hulld.HD_SC), ("MSC", hulld.HD_MSC), ("SM", hulld.HD_SM)):
+        hulls[name] = torch.from_numpy(scan.mask(m)).cuda()
+    Mvol = torch.from_numpy(scan.counts(hulld.HD_SM).view(np.int32)).cuda()
+    stream = torch.cuda.Stream()
+    ws = torch.empty(hulld.hd_sm_canny_workspace(dims), dtype=torch.uint8, device="cuda")
+    b = hulld.Binned(g)
+
+    def timed(fn, k):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            for _ in range(args.warmup):
+                fn()
+            e0.record(stream)
+            for _ in range(k):
+                fn()
+            e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / k
+
+    out = {}
+    fill = torch.empty_like(hulls["MSC"])
+    out["fill_enclosed_ms"] = timed(lambda: hulld.hd_fill_enclosed(hulls["MSC"], dims, fill,
+                                                                   stream), args.steps)
+    hulls["MSC enclosed"] = fill
+    res = {}
+    for q in (0, 25, 50):
+        holder = {}
+
+        def canny():
+            holder["r"] = hulld.hd_sm_canny(Mvol, dims, q, ws, stream)
+        t = timed(canny, args.steps)
+        if q == 50:
+            out["sm_canny_ms"] = t
+        res[q] = holder["r"]
+        hulls[f"SM edge q={q}"] = holder["r"][2]
+    with torch.cuda.stream(stream):
+        b.run(dev, stream)
+    torch.cuda.synchronize()
+    hulls["SC binned"] = torch.from_numpy(b.image(hulld.HD_BINNED_HULL)).cuda()
+    counts = torch.empty(2 * g.nz + 2, dtype=torch.int64, device="cuda")
+    out["hull_compare_ms"] = timed(lambda: hulld.hd_hull_compare(hulls["SC"], obj, dims, counts,
+                                                                 stream), args.steps)
+    table = {}
+    for name, hm in hulls.items():
+        c = hulld.hd_hull_compare(hm, obj, dims).cpu().numpy()
+        table[name] = {"hull": int(hm.sum().item()), "extra": int(c[2 * g.nz]),
+                       "missing": int(c[2 * g.nz + 1])}
+    line = {"metric": "extra/missing voxels against the synthetic object (Tables 1-2 measures)",
+            "config": {"workload": WORKLOAD, "fraction": args.fraction,
+                       "object_voxels": int(obj.sum().item())},
+            "hulls": table, "device_ms": out, "steps": args.steps, "warmup": args.warmup}
+    print(json.dumps(line), flush=True)
+    b.close()
+    scan.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -636,7 +715,8 @@ def main():
     ap.add_argument("--no-per-method", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--workload", default="head-200",
-                    choices=["head-200", "batched-48", "serving", "rows", "binned"])
+                    choices=["head-200", "batched-48", "serving", "rows", "binned",
+                             "diagnostics"])
     ap.add_argument("--batch-fraction", type=float, default=1.0)
     ap.add_argument("--fraction", type=float, default=1.0,
                     help="head-200 workload: keep this fraction of the histories "
@@ -658,6 +738,9 @@ def main():
         return
     if args.workload == "binned":
         run_binned(args)
+        return
+    if args.workload == "diagnostics":
+        run_diagnostics(args)
         return
 
     if args.impl == "reference":

@@ -10,8 +10,8 @@
 //   canny_gradient_kernel  thread per voxel: Sobel of S, magnitude, direction
 //   canny_nms_kernel       thread per voxel: local maximum test, slice maximum
 //   canny_slice_kernel     block per slice: hysteresis on bitmaps in shared
-//                          memory, the quantile by a 32-step radix select,
-//                          the hull
+//                          memory, the edge voxels' M listed in shared memory,
+//                          the quantile by a 32-step radix select, the hull
 #include <cuda_runtime.h>
 
 #include "hd_internal.cuh"
@@ -21,6 +21,7 @@ namespace {
 constexpr int kVoxThreads = 256;
 constexpr int kSliceThreads = 1024;
 constexpr int kMaxWords = 24 * 1024;  // two slice bitmaps of 96 KB
+constexpr int kListCap = 4096;        // edge values listed in shared memory
 
 struct CannyWs {
     long long *S, *mag;
@@ -217,9 +218,20 @@ __global__ void __launch_bounds__(kSliceThreads) canny_slice_kernel(
         }
         if (!__syncthreads_or(changed)) break;
     }
-    long long cnt = 0;
-    for (int k = threadIdx.x; k < words; k += blockDim.x) cnt += __popc(E[k]);
-    const long long kedge = block_sum(cnt, s_red);
+    // the edge voxels' M values, listed in shared memory when they fit
+    __shared__ int s_n;
+    uint32_t *L = s_bits + 2 * words;
+    if (threadIdx.x == 0) s_n = 0;
+    __syncthreads();
+    for (int k = threadIdx.x; k < words; k += blockDim.x) {
+        const int y = k / rw, x0 = (k - y * rw) * 32;
+        for (uint32_t bits = E[k]; bits != 0; bits &= bits - 1u) {
+            const int slot = atomicAdd(&s_n, 1);
+            if (slot < kListCap) L[slot] = m[static_cast<int64_t>(y) * nx + x0 + __ffs(bits) - 1];
+        }
+    }
+    __syncthreads();
+    const long long kedge = s_n;
     uint8_t *h = H3 + static_cast<int64_t>(z) * plane;
     if (kedge == 0) {
         for (int64_t j = threadIdx.x; j < plane; j += blockDim.x) h[j] = 0;
@@ -230,16 +242,25 @@ __global__ void __launch_bounds__(kSliceThreads) canny_slice_kernel(
         return;
     }
     // the element of rank t among the edge voxels' M: radix select, MSB first
+    // (over the list, or over the edge bitmap when the list overflowed)
+    const bool listed = kedge <= kListCap;
     long long t = (static_cast<long long>(q_pct) * (kedge - 1)) / 100;
     uint32_t prefix = 0;
     for (int b = 31; b >= 0; --b) {
         const uint32_t hi_mask = b == 31 ? 0u : ~((2u << b) - 1u);  // bits above b
         long long c = 0;
-        for (int64_t j = threadIdx.x; j < plane; j += blockDim.x) {
-            const int y = static_cast<int>(j / nx), x = static_cast<int>(j - static_cast<int64_t>(y) * nx);
-            if ((E[y * rw + (x >> 5)] >> (x & 31)) & 1u) {
-                const uint32_t v = m[j];
+        if (listed) {
+            for (int i = threadIdx.x; i < kedge; i += blockDim.x) {
+                const uint32_t v = L[i];
                 c += ((v & hi_mask) == prefix && !((v >> b) & 1u)) ? 1 : 0;
+            }
+        } else {
+            for (int k = threadIdx.x; k < words; k += blockDim.x) {
+                const int y = k / rw, x0 = (k - y * rw) * 32;
+                for (uint32_t bits = E[k]; bits != 0; bits &= bits - 1u) {
+                    const uint32_t v = m[static_cast<int64_t>(y) * nx + x0 + __ffs(bits) - 1];
+                    c += ((v & hi_mask) == prefix && !((v >> b) & 1u)) ? 1 : 0;
+                }
             }
         }
         const long long zeros = block_sum(c, s_red);
@@ -328,10 +349,10 @@ hd_status hd_sm_canny(const uint32_t *M, int32_t nx, int32_t ny, int32_t nz, int
         canny_nms_kernel<<<blocks, kVoxThreads, 0, st>>>(ws.mag, ws.dir, nx, ny, V, ws.nms,
                                                          ws.smax);
         e = cudaFuncSetAttribute(canny_slice_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 static_cast<int>(2 * sizeof(uint32_t) * kMaxWords));
+                                 static_cast<int>(sizeof(uint32_t) * (2 * kMaxWords + kListCap)));
     }
     if (e == cudaSuccess) {
-        canny_slice_kernel<<<nz, kSliceThreads, 2 * sizeof(uint32_t) * rw * ny, st>>>(
+        canny_slice_kernel<<<nz, kSliceThreads, sizeof(uint32_t) * (2 * rw * ny + kListCap), st>>>(
             M, ws.mag, ws.nms, ws.smax, nx, ny, rw, q_pct, mt, has_edge, H3);
         e = cudaGetLastError();
     }

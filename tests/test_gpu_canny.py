@@ -78,3 +78,15 @@ def test_range(hd):
     with pytest.raises(hd.HDError) as e:
         hd.hd_sm_canny(M, (800, 1000, 1))
     assert e.value.status == hd.HD_ERR_RANGE
+
+
+def test_many_edge_voxels(hd, oracle_mod):
+    """Stripes give more edge voxels than the shared-memory list holds, so
+    the select runs over the edge bitmap."""
+    nx, ny = 300, 200
+    yy, xx = np.mgrid[0:ny, 0:nx]
+    M = np.where((xx // 4) % 2 == 0, 1000 + 7 * yy, 10 + xx % 13).astype(np.uint32)[None]
+    ref = oracle_mod.sm_canny(M, (nx, ny, 1), debug=True)
+    assert ref["edge"].sum() > 4096
+    for q in (0, 50, 100):
+        _check(hd, oracle_mod, M, (nx, ny, 1), q)
