@@ -360,6 +360,79 @@ int oracle_accumulate(const og_geom *g, float tau_l, float tau_h, int32_t method
     return 0;
 }
 
+/* ------------------------------------- thick rays (next row f4) */
+
+/* Thick rays (Eq. 3.2 with d_0 > 0; the paper leaves the distance measure
+ * open): A_i(k) = the voxels within k voxels of a voxel of A_i in the same
+ * slice, by the in-plane Chebyshev distance (|dx| <= k and |dy| <= k, same
+ * z), k = floor(d_0 / in-plane voxel size).  k = 0 is A_i itself.  Counts
+ * N and M as oracle_accumulate does, one per history for every voxel of its
+ * A_i(k): the dilated set of each history is formed voxel by voxel and
+ * stamped, so a voxel reached from several voxels of A_i counts once.
+ * stats as oracle_accumulate ([5], [6]: the voxels of the thick sets). */
+int oracle_accumulate_thick(const og_geom *g, float tau_l, float tau_h, int32_t methods,
+                            const int64_t *theta, int64_t K, int32_t k, const float *angle,
+                            const float *u_in, const float *v_in, const float *u_out,
+                            const float *v_out, const float *wepl, int64_t n, uint32_t *N,
+                            uint32_t *M, int64_t *stats)
+{
+    const int64_t V = (int64_t)g->nx * g->ny * g->nz;
+    const int64_t cap = (int64_t)g->nx + g->ny + g->nz + 8;
+    int64_t *set = (int64_t *)malloc(sizeof(int64_t) * (size_t)cap);
+    int64_t *stamp = (int64_t *)malloc(sizeof(int64_t) * (size_t)V);
+    if (!set || !stamp) {
+        free(set);
+        free(stamp);
+        return -1;
+    }
+    for (int64_t v = 0; v < V; ++v) stamp[v] = -1;
+    const int use_miss = (methods & (OM_SC | OM_MSC)) != 0;
+    const int use_hit = (methods & OM_SM) != 0;
+    for (int64_t i = 0; i < n; ++i) {
+        stats[0] += 1;
+        const int cls = oracle_classify(wepl[i], tau_l, tau_h);
+        if (cls == 1) stats[1] += 1;
+        else if (cls == 2) stats[2] += 1;
+        else stats[3] += 1;
+        if (!((cls == 1 && use_miss) || (cls == 2 && use_hit))) continue;
+        int64_t gin[3], gout[3];
+        if (oracle_grid_endpoints(g, theta, K, angle[i], u_in[i], v_in[i], u_out[i], v_out[i],
+                                  gin, gout)) {
+            stats[4] += 1;
+            continue;
+        }
+        const int64_t m = oracle_voxel_set(gin, gout, g->nx, g->ny, g->nz, set, cap);
+        if (m < 0 || m > cap) {
+            free(set);
+            free(stamp);
+            return -1;
+        }
+        int64_t count = 0;
+        for (int64_t j = 0; j < m; ++j) {
+            const int64_t v = set[j];
+            const int64_t x = v % g->nx, y = (v / g->nx) % g->ny, z = v / ((int64_t)g->nx * g->ny);
+            for (int64_t dy = -k; dy <= k; ++dy)
+                for (int64_t dx = -k; dx <= k; ++dx) {
+                    const int64_t X = x + dx, Y = y + dy;
+                    if (X < 0 || X >= g->nx || Y < 0 || Y >= g->ny) continue;
+                    const int64_t w = X + g->nx * (Y + g->ny * z);
+                    if (stamp[w] == i) continue;
+                    stamp[w] = i;
+                    ++count;
+                    if (cls == 1) {
+                        if (N) N[w] += 1;
+                    } else if (M) {
+                        M[w] += 1;
+                    }
+                }
+        }
+        stats[cls == 1 ? 5 : 6] += count;
+    }
+    free(set);
+    free(stamp);
+    return 0;
+}
+
 /* ------------------------------- hull diagnostics (next row f3) */
 
 /* Extra and missing voxels of a hull against the true object (the counts of

@@ -91,6 +91,11 @@ def lib():
                                               ctypes.c_int32, i64p, ctypes.c_int64] + \
                 [f32p] * 6 + [ctypes.c_int64, u32p, u32p, i64p]
             L.oracle_compare_fp64.restype = ctypes.c_int
+            L.oracle_accumulate_thick.argtypes = [ctypes.c_void_p, ctypes.c_float, ctypes.c_float,
+                                                  ctypes.c_int32, i64p, ctypes.c_int64,
+                                                  ctypes.c_int32] + [f32p] * 6 + \
+                [ctypes.c_int64, u32p, u32p, i64p]
+            L.oracle_accumulate_thick.restype = ctypes.c_int
             L.oracle_sm_canny.argtypes = [u32p] + [ctypes.c_int32] * 4 + [u32p, u8p, u8p] + \
                 [i64p] * 4 + [u8p, u8p]
             L.oracle_sm_canny.restype = ctypes.c_int
@@ -504,6 +509,26 @@ def system_rows(g, hist, hull, threads: Optional[int] = 1) -> Tuple[np.ndarray, 
     row_ptr = np.zeros(n + 1, np.int64)
     np.cumsum(nnz, out=row_ptr[1:])
     return row_ptr, cols
+
+
+# ---------------------------------------------- thick rays (next row f4)
+def accumulate_thick(g, hist, k: int, params: Params = Params()) -> Dict:
+    """N and M with thick rays: A_i dilated by k voxels in-plane (Chebyshev)
+    within each slice; k = 0 gives the counts of accumulate."""
+    th, K = _table_arrays()
+    V = g.nx * g.ny * g.nz
+    N = np.zeros(V, np.uint32)
+    M = np.zeros(V, np.uint32)
+    stats = np.zeros(8, np.int64)
+    arrs = [np.ascontiguousarray(a, dtype=np.float32) for a in hist.arrays()]
+    og = _ogeom(g)
+    if lib().oracle_accumulate_thick(ctypes.byref(og), params.tau_l, params.tau_h,
+                                     params.methods, _p(th, ctypes.c_int64), K, int(k),
+                                     *[_p(a, ctypes.c_float) for a in arrs], len(hist),
+                                     _p(N, ctypes.c_uint32), _p(M, ctypes.c_uint32),
+                                     _p(stats, ctypes.c_int64)):
+        raise MemoryError("oracle_accumulate_thick")
+    return {"N": N, "M": M, "stats": stats}
 
 
 # ------------------------------------------ hull diagnostics (next row f3)

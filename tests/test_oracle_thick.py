@@ -1,0 +1,81 @@
+"""Pins for the oracle's thick rays (next row f4): k = 0 reduces to the thin
+counts, single-history sets equal an exact slab test on the dilated box
+written here with rationals, sums equal the set sizes, and counts grow with
+k."""
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+from paper_1402_1720_gb300 import synth
+
+
+def _meets_box(a, b, lo, hi):
+    """Does the closed segment a -> b meet the half-open box [lo, hi)?"""
+    t_lo, lo_open = Fraction(0), False
+    t_hi, hi_open = Fraction(1), False
+    for ax in range(3):
+        d = b[ax] - a[ax]
+        if d == 0:
+            if not (lo[ax] <= a[ax] < hi[ax]):
+                return False
+            continue
+        if d > 0:
+            l, lop = (lo[ax] - a[ax]) / d, False  # p >= lo: t >= l (closed)
+            h, hop = (hi[ax] - a[ax]) / d, True   # p < hi: t < h (open)
+        else:
+            l, lop = (hi[ax] - a[ax]) / d, True   # p < hi: t > l (open)
+            h, hop = (lo[ax] - a[ax]) / d, False  # p >= lo: t <= h (closed)
+        if l > t_lo or (l == t_lo and lop):
+            t_lo, lo_open = l, lop
+        if h < t_hi or (h == t_hi and hop):
+            t_hi, hi_open = h, hop
+    return t_lo < t_hi or (t_lo == t_hi and not lo_open and not hi_open)
+
+
+def test_k0_equals_thin_counts(oracle_mod):
+    w = synth.make_config(1, fraction=0.2)
+    thick = oracle_mod.accumulate_thick(w.geometry, w.histories, 0)
+    thin = oracle_mod.accumulate(w.geometry, w.histories)
+    assert np.array_equal(thick["N"], thin["N"]) and np.array_equal(thick["M"], thin["M"])
+
+
+@pytest.mark.parametrize("k", [1, 2, 3])
+def test_single_histories_equal_dilated_slab_test(oracle_mod, k):
+    g = synth.Geometry(12, 10, 4, 1.0, 1.0, 2.5, 20.0)
+    rng = np.random.default_rng(10 + k)
+    done = 0
+    while done < 25:
+        ang = float(rng.choice([0.0, 90.0, 45.0, 4.0 * rng.integers(0, 90),
+                                rng.uniform(0, 360)]))
+        u0, u1 = rng.uniform(-7, 7, 2)
+        v0, v1 = rng.uniform(-5, 5, 2)
+        if rng.random() < 0.3:
+            v1 = v0
+        rej, gi, go = oracle_mod.grid_endpoints(g, ang, u0, v0, u1, v1)
+        if rej:
+            continue
+        h = synth.Histories(*[np.array([x], np.float32) for x in (ang, u0, v0, u1, v1, 0.5)])
+        r = oracle_mod.accumulate_thick(g, h, k)
+        a = [Fraction(int(c), 65536) for c in gi]
+        b = [Fraction(int(c), 65536) for c in go]
+        want = np.zeros(g.nx * g.ny * g.nz, np.uint32)
+        for z in range(g.nz):
+            for y in range(g.ny):
+                for x in range(g.nx):
+                    lo = [max(x - k, 0), max(y - k, 0), z]
+                    hi = [min(x + k + 1, g.nx), min(y + k + 1, g.ny), z + 1]
+                    want[x + g.nx * (y + g.ny * z)] = _meets_box(a, b, lo, hi)
+        assert np.array_equal(r["N"], want), (ang, u0, v0, u1, v1)
+        done += 1
+
+
+def test_sums_and_growth(oracle_mod):
+    w = synth.make_config(1, fraction=0.1)
+    prev = None
+    for k in range(4):
+        r = oracle_mod.accumulate_thick(w.geometry, w.histories, k)
+        assert int(r["N"].sum()) == int(r["stats"][5]) and int(r["M"].sum()) == int(r["stats"][6])
+        if prev is not None:
+            assert np.all(r["N"] >= prev["N"]) and np.all(r["M"] >= prev["M"])
+        prev = r
