@@ -499,6 +499,31 @@ HD_API hd_status hd_classify(const float *wepl, int64_t n, const hd_params *para
                       int32_t on_device, void *stream);
 
 /* ------------------------------------------------------------------------
+ * Thick rays (Eq. 3.2 with d_0 > 0; the paper leaves the distance measure
+ * d open).  A_i(k) = the voxels within k voxels of a voxel of A_i (reading
+ * 1) in the same slice, by the in-plane Chebyshev distance: |dx| <= k,
+ * |dy| <= k, same z.  For in-plane voxel size s, k = floor(d_0 / s) (a
+ * thickness below the slice thickness).  k = 0 gives A_i itself.
+ *
+ * Classifies the n histories (device SoA arrays, as hd_scan_add_histories
+ * with on_device = 1) and ADDS one to N[v] for every voxel v of the thick set
+ * of every missed history and to M[v] for every hit one (each voxel once per
+ * history; uint32, V entries, device; N required when params->methods has
+ * HD_SC or HD_MSC, M when it has HD_SM).  The caller zeroes N and M before
+ * the first call; the decisions of hd_scan_finalize are then the caller's
+ * to apply (for instance H_1 = [N = 0]).  workspace: device memory of at
+ * least hd_accumulate_thick_workspace bytes (two int32 difference arrays of
+ * about V entries per class), 256-byte aligned; the call clears it.
+ * HD_ERR_RANGE for k outside [0, 16] or an unsupported geometry.
+ * Stream-ordered on `stream`. */
+HD_API hd_status hd_accumulate_thick_workspace(const hd_geometry *geom, size_t *bytes);
+HD_API hd_status hd_accumulate_thick(const hd_geometry *geom, const hd_params *params, int32_t k,
+                                     const float *angle_deg, const float *u_in, const float *v_in,
+                                     const float *u_out, const float *v_out, const float *wepl,
+                                     int64_t n, uint32_t *N, uint32_t *M, void *workspace,
+                                     size_t workspace_bytes, void *stream);
+
+/* ------------------------------------------------------------------------
  * Hull diagnostics (not steps of the method: the measures the paper reports
  * and a fill variant of MSC's hull).  All pointers are device pointers; the
  * volumes are uint8 masks of nx * ny * nz voxels, x fastest.

@@ -1,0 +1,230 @@
+// Thick rays (Eq. 3.2 with d_0 > 0; the paper leaves the distance measure
+// open): A_i(k) = the voxels within k voxels of a voxel of A_i in the same
+// slice, by the in-plane Chebyshev distance.  Counted into N and M exactly
+// as the thin paths are, once per history for every voxel of its A_i(k).
+//
+// Within one slice the walk of A_i is a run of consecutive rows (one run of
+// voxels along the major in-plane axis per row, rows stepping by one in one
+// direction, the runs abutting).  Dilating it by k, target row t receives
+// the runs of rows t - k .. t + k, whose union grown by k is the single
+// interval [min lo - k, max hi + k]; because lo and hi move monotonically
+// along the walk, the minimum and maximum sit at the window's first and last
+// run.  So each history emits one interval per target row and slice, into a
+// difference array along the major axis (x-major walks along x, y-major ones
+// along y), and row prefix sums turn the differences into counts.
+//
+//   thick_kernel      thread per history: the exact run walk over the whole
+//                     grid, a ring of the last 2k + 1 runs of the current
+//                     slice, one interval per target row (two atomics)
+//   thick_rows_kernel thread per x-row / y-column: prefix sums added to N, M
+#include <cuda_runtime.h>
+
+#include "hd_geom.cuh"
+
+namespace hd {
+namespace {
+
+constexpr int kThickThreads = 256;
+constexpr int kMaxK = 16;
+
+// Difference arrays: along x, (nx + 1) entries per (y, z) row; along y,
+// (ny + 1) entries per (x, z) column.  One pair for N and one for M.
+struct ThickWs {
+    int32_t *dx[2], *dy[2];
+};
+
+struct ThickRing {
+    int lo[2 * kMaxK + 1], hi[2 * kMaxK + 1];
+};
+
+// Emits target row centred on run jc of the current slice: the window's
+// runs are max(0, jc - k) .. min(jc + k, last); its minor index is
+// m0 + s jc.
+__device__ __forceinline__ void emit(const ThickRing &rg, int jc, int last, int k, int m0, int s,
+                                     int nminor, int nmaj, int32_t *diff, int64_t slice_row0)
+{
+    const int t = m0 + s * jc;
+    if (t < 0 || t >= nminor) return;
+    const int ja = max(0, jc - k), jb = min(jc + k, last);
+    const int R = 2 * k + 1;
+    const int la = rg.lo[ja % R], lb = rg.lo[jb % R];
+    const int ha = rg.hi[ja % R], hb = rg.hi[jb % R];
+    const int lo = max(min(la, lb) - k, 0);
+    const int hi = min(max(ha, hb) + k, nmaj - 1);
+    int32_t *row = diff + (slice_row0 + t) * static_cast<int64_t>(nmaj + 1);
+    atomicAdd(row + lo, 1);
+    atomicAdd(row + hi + 1, -1);
+}
+
+__global__ void __launch_bounds__(kThickThreads) thick_kernel(Inputs in, int64_t n, GeomQ g,
+                                                              Cordic cd, float tau_l, float tau_h,
+                                                              int use_miss, int use_hit, int k,
+                                                              ThickWs ws)
+{
+    long long tc_c = 0, tc_s = 0;
+    float tc_ang = 0.0f;
+    bool tc_valid = false;
+    ThickRing rg;
+    const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+    for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
+         i += stride) {
+        const float w = in.wepl[i];
+        const int cls = w < tau_l ? 0 : (w > tau_h ? 1 : -1);
+        if (cls < 0 || (cls == 0 && !use_miss) || (cls == 1 && !use_hit)) continue;
+        const float ang = in.angle[i];
+        if (!(fabsf(ang) < 1048576.0f)) continue;
+        if (!tc_valid || ang != tc_ang) {
+            cordic_cs(q16_of(ang), cd, tc_c, tc_s);
+            tc_ang = ang;
+            tc_valid = true;
+        }
+        int32_t r[6];
+        if (!endpoints_cs(g, tc_c, tc_s, in.u_in[i], in.v_in[i], in.u_out[i], in.v_out[i], r))
+            continue;
+        RunWalk wk;
+        if (!run_begin(wk, r, r + 3, g.nx, g.ny, g.nz)) continue;
+        const bool ymaj = (wk.flags >> 5) & 1;
+        const int s = (wk.flags & 2) ? 1 : -1;  // the in-plane minor axis' direction
+        const int nmaj = ymaj ? g.ny : g.nx, nminor = ymaj ? g.nx : g.ny;
+        int32_t *diff = ymaj ? ws.dy[cls] : ws.dx[cls];
+        const int R = 2 * k + 1;
+        int zc = -1, m0 = 0, j = 0;  // current slice, its first minor index, runs in it
+        int row, lo, hi;
+        // targets are centred on runs -k .. J - 1 + k of a slice of J runs;
+        // the one centred on run j - k is complete once run j has arrived,
+        // the last k when the slice ends
+        auto close_slice = [&]() {
+            const int64_t row0 = static_cast<int64_t>(zc) * nminor;
+            for (int jc = j - k; jc <= j - 1 + k; ++jc)
+                emit(rg, jc, j - 1, k, m0, s, nminor, nmaj, diff, row0);
+        };
+        while (run_next(wk, row, lo, hi)) {
+            const int mz = row / nminor, mm = row - mz * nminor;
+            if (mz != zc) {
+                if (zc >= 0) close_slice();
+                zc = mz;
+                m0 = mm;
+                j = 0;
+            }
+            rg.lo[j % R] = lo;
+            rg.hi[j % R] = hi;
+            emit(rg, j - k, j, k, m0, s, nminor, nmaj, diff, static_cast<int64_t>(zc) * nminor);
+            ++j;
+        }
+        if (zc >= 0) close_slice();
+    }
+}
+
+__global__ void __launch_bounds__(kThickThreads) thick_rows_kernel(const int32_t *diff, int64_t rows,
+                                                                   int nmaj, int stride_maj,
+                                                                   int nminor, int64_t plane,
+                                                                   int major_is_y, uint32_t *out)
+{
+    const int64_t r = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (r >= rows || out == nullptr) return;
+    const int64_t z = r / nminor;
+    const int m = static_cast<int>(r - z * nminor);
+    const int32_t *d = diff + r * static_cast<int64_t>(nmaj + 1);
+    // x-major rows: voxel x + nx (m + ny z); y-major columns: m + nx (y + ny z)
+    uint32_t *o = out + z * plane + (major_is_y ? m : static_cast<int64_t>(m) * nmaj);
+    int acc = 0;
+    for (int a = 0; a < nmaj; ++a) {
+        acc += d[a];
+        if (acc != 0) o[static_cast<int64_t>(a) * stride_maj] += static_cast<uint32_t>(acc);
+    }
+}
+
+size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
+
+size_t thick_layout(const hd_geometry *g, void *base, ThickWs *ws)
+{
+    const size_t nz = static_cast<size_t>(g->nz);
+    const size_t bx = align256(sizeof(int32_t) * (g->nx + 1) * static_cast<size_t>(g->ny) * nz);
+    const size_t by = align256(sizeof(int32_t) * (g->ny + 1) * static_cast<size_t>(g->nx) * nz);
+    if (ws && base) {
+        char *p = static_cast<char *>(base);
+        ws->dx[0] = reinterpret_cast<int32_t *>(p);
+        ws->dx[1] = reinterpret_cast<int32_t *>(p + bx);
+        ws->dy[0] = reinterpret_cast<int32_t *>(p + 2 * bx);
+        ws->dy[1] = reinterpret_cast<int32_t *>(p + 2 * bx + by);
+    }
+    return 2 * bx + 2 * by;
+}
+
+}  // namespace
+}  // namespace hd
+
+extern "C" {
+
+hd_status hd_accumulate_thick_workspace(const hd_geometry *geom, size_t *bytes)
+{
+    if (!geom || !bytes) return HD_ERR_ARG;
+    const hd_status s = hd::check_geometry(geom);
+    if (s != HD_OK) return s;
+    *bytes = hd::thick_layout(geom, nullptr, nullptr);
+    return HD_OK;
+}
+
+hd_status hd_accumulate_thick(const hd_geometry *geom, const hd_params *params, int32_t k,
+                              const float *angle_deg, const float *u_in, const float *v_in,
+                              const float *u_out, const float *v_out, const float *wepl,
+                              int64_t n, uint32_t *N, uint32_t *M, void *workspace,
+                              size_t workspace_bytes, void *stream)
+{
+    if (!geom || !params || n < 0 || !workspace) return HD_ERR_ARG;
+    if (k < 0 || k > hd::kMaxK) return HD_ERR_RANGE;
+    const hd_status gs = hd::check_geometry(geom);
+    if (gs != HD_OK) return gs;
+    if (std::isnan(params->wepl_miss_lt) || std::isnan(params->wepl_hit_gt) ||
+        params->wepl_miss_lt > params->wepl_hit_gt)
+        return HD_ERR_ARG;
+    const uint32_t m = params->methods;
+    if (m == 0 || (m & ~uint32_t(HD_SC | HD_MSC | HD_SM))) return HD_ERR_ARG;
+    const int use_miss = (m & (HD_SC | HD_MSC)) ? 1 : 0;
+    const int use_hit = (m & HD_SM) ? 1 : 0;
+    if ((use_miss && !N) || (use_hit && !M)) return HD_ERR_ARG;
+    if (n > 0 && (!angle_deg || !u_in || !v_in || !u_out || !v_out || !wepl)) return HD_ERR_ARG;
+    const size_t need = hd::thick_layout(geom, nullptr, nullptr);
+    if (workspace_bytes < need || (reinterpret_cast<uintptr_t>(workspace) & 255) != 0)
+        return HD_ERR_ARG;
+    hd::Cordic cd{};
+    if (!hd::make_cordic_table(cd)) return HD_ERR_RANGE;
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+        cudaGetLastError();
+        return HD_ERR_CUDA;
+    }
+    hd::ThickWs ws{};
+    hd::thick_layout(geom, workspace, &ws);
+    const hd::GeomQ gq = hd::make_geomq(geom->nx, geom->ny, geom->nz, geom->sx, geom->sy,
+                                        geom->sz, geom->tracker_half_sep_mm);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaMemsetAsync(workspace, 0, need, st);
+    if (e == cudaSuccess && n > 0) {
+        int64_t blocks = (n + hd::kThickThreads - 1) / hd::kThickThreads;
+        if (blocks > int64_t(sms) * 8) blocks = int64_t(sms) * 8;
+        const hd::Inputs in{angle_deg, u_in, v_in, u_out, v_out, wepl};
+        hd::thick_kernel<<<static_cast<unsigned>(blocks), hd::kThickThreads, 0, st>>>(
+            in, n, gq, cd, params->wepl_miss_lt, params->wepl_hit_gt, use_miss, use_hit, k, ws);
+        e = cudaGetLastError();
+    }
+    const int64_t plane = int64_t(geom->nx) * geom->ny;
+    for (int c = 0; c < 2 && e == cudaSuccess && n > 0; ++c) {
+        uint32_t *out = c == 0 ? (use_miss ? N : nullptr) : (use_hit ? M : nullptr);
+        if (!out) continue;
+        const int64_t rx = int64_t(geom->ny) * geom->nz, ry = int64_t(geom->nx) * geom->nz;
+        hd::thick_rows_kernel<<<static_cast<unsigned>((rx + 255) / 256), 256, 0, st>>>(
+            ws.dx[c], rx, geom->nx, 1, geom->ny, plane, 0, out);
+        hd::thick_rows_kernel<<<static_cast<unsigned>((ry + 255) / 256), 256, 0, st>>>(
+            ws.dy[c], ry, geom->ny, geom->nx, geom->nx, plane, 1, out);
+        e = cudaGetLastError();
+    }
+    if (e != cudaSuccess) {
+        hd::note_cuda_error(e, "hd_accumulate_thick");
+        return HD_ERR_CUDA;
+    }
+    return HD_OK;
+}
+
+}  // extern "C"

@@ -188,6 +188,10 @@ _SIGS = {
     "hd_server_close_scan": ([_VP, _I64], ctypes.c_int),
     "hd_scan_get_profile": ([_VP, ctypes.POINTER(hd_profile)], ctypes.c_int),
     "hd_hull_compare": ([_VP, _VP, _I32, _I32, _I32, _VP, _VP], ctypes.c_int),
+    "hd_accumulate_thick_workspace": ([ctypes.POINTER(hd_geometry), ctypes.POINTER(_SZ)],
+                                      ctypes.c_int),
+    "hd_accumulate_thick": ([ctypes.POINTER(hd_geometry), ctypes.POINTER(hd_params), _I32] +
+                            [_VP] * 6 + [_I64, _VP, _VP, _VP, _SZ, _VP], ctypes.c_int),
     "hd_sm_canny_workspace": ([_I32, _I32, _I32, ctypes.POINTER(_SZ)], ctypes.c_int),
     "hd_sm_canny": ([_VP, _I32, _I32, _I32, _I32, _VP, _SZ, _VP, _VP, _VP, _VP], ctypes.c_int),
     "hd_fill_enclosed": ([_VP, _I32, _I32, _I32, _VP, _VP], ctypes.c_int),
@@ -1022,3 +1026,30 @@ def hd_sm_canny(M, dims, q_pct: int = 50, workspace=None, stream=None):
                               _dev_ptr(he, "has_edge"), _dev_ptr(H3, "H3"), _stream(stream)),
            "hd_sm_canny")
     return mt, he, H3
+
+
+# ------------------------------------------------------------ thick rays
+def hd_accumulate_thick_workspace(geometry) -> int:
+    g = _geometry(geometry)
+    out = _SZ(0)
+    _check(load().hd_accumulate_thick_workspace(ctypes.byref(g), ctypes.byref(out)),
+           "hd_accumulate_thick_workspace")
+    return out.value
+
+
+def hd_accumulate_thick(geometry, params, k: int, arrays, N, M, workspace=None, stream=None):
+    """Adds thick-ray counts (A_i dilated by k voxels in-plane) of device
+    history arrays into device N, M (uint32 viewed as int32 tensors)."""
+    import torch
+    g = _geometry(geometry)
+    p = _params(params)
+    ptrs, n = _hist_ptrs(list(arrays))
+    if workspace is None:
+        workspace = torch.empty(hd_accumulate_thick_workspace(geometry), dtype=torch.uint8,
+                                device="cuda")
+    nptr = _dev_ptr(N, "N") if N is not None else None
+    mptr = _dev_ptr(M, "M") if M is not None else None
+    _check(load().hd_accumulate_thick(ctypes.byref(g), ctypes.byref(p), int(k), *ptrs, n, nptr,
+                                      mptr, _dev_ptr(workspace, "workspace"),
+                                      int(workspace.numel() * workspace.element_size()),
+                                      _stream(stream)), "hd_accumulate_thick")

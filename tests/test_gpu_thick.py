@@ -1,0 +1,67 @@
+"""Thick rays on the GPU against the oracle, bit for bit: N and M for k =
+0, 1, 2 and 5 on the tiny workload, lattice ties on two small grids, a sample
+of the head-sized workload, accumulation over calls, and the range check."""
+import numpy as np
+import pytest
+
+from paper_1402_1720_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():  # pragma: no cover - CPU container
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+
+@pytest.fixture(scope="module")
+def hd():
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1402_1720_gb300 import hulld
+    hulld.load()
+    return hulld
+
+
+def _gpu(hd, g, h, k, times=1):
+    V = g.nx * g.ny * g.nz
+    N = torch.zeros(V, dtype=torch.int32, device="cuda")
+    M = torch.zeros(V, dtype=torch.int32, device="cuda")
+    dev = [torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in h.arrays()]
+    for _ in range(times):
+        hd.hd_accumulate_thick(g, None, k, dev, N, M)
+    torch.cuda.synchronize()
+    return N.cpu().numpy().view(np.uint32), M.cpu().numpy().view(np.uint32)
+
+
+@pytest.mark.parametrize("k", [0, 1, 2, 5])
+def test_tiny_workload(hd, oracle_mod, k):
+    w = synth.make_config(1, fraction=0.3)
+    N, M = _gpu(hd, w.geometry, w.histories, k)
+    ref = oracle_mod.accumulate_thick(w.geometry, w.histories, k)
+    assert np.array_equal(N, ref["N"]) and np.array_equal(M, ref["M"])
+
+
+@pytest.mark.parametrize("g", [synth.Geometry(8, 8, 4, 1.0, 1.0, 1.0, 8.0),
+                               synth.Geometry(16, 16, 2, 1.0, 1.0, 2.5, 16.0)])
+def test_lattice_ties(hd, oracle_mod, g):
+    from tests.test_gpu_parity import _lattice_histories
+    h = _lattice_histories(np.random.default_rng(g.nx + 5), g, 3000)
+    for k in (1, 2):
+        N, M = _gpu(hd, g, h, k)
+        ref = oracle_mod.accumulate_thick(g, h, k)
+        assert np.array_equal(N, ref["N"]) and np.array_equal(M, ref["M"])
+
+
+def test_head_sample_and_accumulation(hd, oracle_mod):
+    w = synth.make_config(2, fraction=0.03)
+    N, M = _gpu(hd, w.geometry, w.histories, 2, times=2)
+    ref = oracle_mod.accumulate_thick(w.geometry, w.histories, 2)
+    assert np.array_equal(N, 2 * ref["N"]) and np.array_equal(M, 2 * ref["M"])
+
+
+def test_k_range(hd):
+    g = synth.Geometry(8, 8, 4, 1.0, 1.0, 1.0, 8.0)
+    h = synth.make_config(1, fraction=0.01).histories
+    with pytest.raises(hd.HDError) as e:
+        _gpu(hd, g, h, 17)
+    assert e.value.status == hd.HD_ERR_RANGE
