@@ -624,6 +624,71 @@ def run_binned(args):
     b.close()
 
 
+def run_thick(args):
+    """Thick rays on the head-sized scan: each step adds the missed and hit
+    counts of all 9e6 histories with A_i dilated by k voxels in-plane
+    (hd_accumulate_thick: clear the difference arrays, walk, prefix sums)."""
+    import torch
+    from paper_1402_1720_gb300 import build as hbuild
+    from paper_1402_1720_gb300 import hulld, synth
+    _, _, local = _dist()
+    torch.cuda.set_device(local)
+    hbuild.build()
+    hulld.load()
+    w = synth.make_config(2, fraction=args.fraction)
+    g, h = w.geometry, w.histories
+    n = len(h)
+    k = args.thick_k
+    dev = [torch.from_numpy(a).cuda() for a in h.arrays()]
+    V = g.nx * g.ny * g.nz
+    N = torch.zeros(V, dtype=torch.int32, device="cuda")
+    M = torch.zeros(V, dtype=torch.int32, device="cuda")
+    ws = torch.empty(hulld.hd_accumulate_thick_workspace(g), dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.Stream()
+
+    def step():
+        hulld.hd_accumulate_thick(g, None, k, dev, N, M, ws, stream)
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            step()
+        torch.cuda.synchronize()
+        N.zero_()
+        M.zero_()
+        torch.cuda.synchronize()
+        sampler = ClockSampler(local)
+        sampler.start()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        clocks = sampler.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    voxels = (int(N.sum().item()) + int(M.sum().item())) // args.steps
+    line = {"metric": f"histories/s (thick rays, k = {k} voxels in-plane, missed and hit counts)",
+            "value": n / (ms * 1e-3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+            "config": {"workload": WORKLOAD + f"; thick rays k = {k}", "histories": n,
+                       "fraction": args.fraction},
+            "thick_voxels_per_step": voxels, "thick_voxels_per_s": voxels / (ms * 1e-3),
+            "gpu_launches": 3 * args.steps, "clocks": clocks}
+    if not args.no_cpu_baseline:
+        import oracle
+        import time as _time
+        sub = synth.make_config(2, fraction=0.005)
+        t0 = _time.perf_counter()
+        oracle.accumulate_thick(g, sub.histories, k)
+        dt = _time.perf_counter() - t0
+        line["cpu_baseline"] = {"value": len(sub.histories) / dt, "unit": UNIT, "cores": 1,
+                                "kind": "oracle",
+                                "sample": f"{len(sub.histories)} histories (0.5% per angle)"}
+    print(json.dumps(line), flush=True)
+
+
 def run_diagnostics(args):
     """Extra and missing voxels of every hull against the synthetic object
     (the measures of Tables 1-2) on the head-sized scan, all computed on the
@@ -716,12 +781,14 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--workload", default="head-200",
                     choices=["head-200", "batched-48", "serving", "rows", "binned",
-                             "diagnostics"])
+                             "diagnostics", "thick"])
     ap.add_argument("--batch-fraction", type=float, default=1.0)
     ap.add_argument("--fraction", type=float, default=1.0,
                     help="head-200 workload: keep this fraction of the histories "
                          "(small profiling captures; 1.0 for the benchmark)")
     ap.add_argument("--no-tune", action="store_true")
+    ap.add_argument("--thick-k", type=int, default=2,
+                    help="thick workload: in-plane dilation in voxels")
     ap.add_argument("--serve-scans", type=int, default=48)
     ap.add_argument("--serve-load", type=float, default=0.7)
     ap.add_argument("--serve-clients", type=int, default=8)
@@ -741,6 +808,9 @@ def main():
         return
     if args.workload == "diagnostics":
         run_diagnostics(args)
+        return
+    if args.workload == "thick":
+        run_thick(args)
         return
 
     if args.impl == "reference":

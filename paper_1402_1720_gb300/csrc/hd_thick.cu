@@ -115,10 +115,9 @@ __global__ void __launch_bounds__(kThickThreads) thick_kernel(Inputs in, int64_t
     }
 }
 
-__global__ void __launch_bounds__(kThickThreads) thick_rows_kernel(const int32_t *diff, int64_t rows,
-                                                                   int nmaj, int stride_maj,
-                                                                   int nminor, int64_t plane,
-                                                                   int major_is_y, uint32_t *out)
+__global__ void __launch_bounds__(kThickThreads) thick_rows_kernel(
+    const int32_t *__restrict__ diff, int64_t rows, int nmaj, int stride_maj, int nminor,
+    int64_t plane, int major_is_y, uint32_t *__restrict__ out)
 {
     const int64_t r = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
     if (r >= rows || out == nullptr) return;
