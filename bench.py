@@ -595,6 +595,8 @@ def run_binned(args):
                    "h2d_bytes_per_step": 24 * n, "d2h_bytes_per_step": int(out.numel())}
     peaks = _peaks()
     atomics = 7 * st["histories_binned"] + 2 * (st["histories_binned"] - st["histories_cut"])
+    l2_rate = hulld.hd_probe_atomics(hulld.HD_PROBE_L2_RANDOM)
+    stats_atomics = 7 * st["histories_binned"]
     line = {"metric": "histories/s (SC with binning, data cuts and filter, as the paper ran it)",
             "value": n / (ms * 1e-3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
@@ -605,6 +607,11 @@ def run_binned(args):
             "phases_ms": {"statistics": t_stats, "cuts": t_cut, "carve_and_filter": t_fin},
             "atomic_rate": {"atomics_per_step": atomics,
                             "per_s": atomics / ((t_stats + t_cut) * 1e-3)},
+            "roofline": {"bound": "l2_atomic", "kernel": "binned_stats_kernel",
+                         "achieved": stats_atomics / (t_stats * 1e-3), "peak": l2_rate,
+                         "unit": "atomics/s", "frac": stats_atomics / (t_stats * 1e-3) / l2_rate,
+                         "atomics_per_launch": stats_atomics,
+                         "peak_source": "hd_probe_atomics L2 random (measured in this run)"},
             "input": {"bytes_per_step": 2 * 24 * n,
                       "gbs": 2 * 24 * n / ((t_stats + t_cut) * 1e-3) / 1e9,
                       "hbm_peak_gbs": peaks["hbm_gbs"]},
@@ -646,8 +653,10 @@ def run_thick(args):
     ws = torch.empty(hulld.hd_accumulate_thick_workspace(g), dtype=torch.uint8, device="cuda")
     stream = torch.cuda.Stream()
 
+    counter = torch.zeros(1, dtype=torch.int64, device="cuda")
+
     def step():
-        hulld.hd_accumulate_thick(g, None, k, dev, N, M, ws, stream)
+        hulld.hd_accumulate_thick(g, None, k, dev, N, M, ws, stream, counter)
 
     with torch.cuda.stream(stream):
         for _ in range(args.warmup):
@@ -668,6 +677,9 @@ def run_thick(args):
         clocks = sampler.stop()
     ms = e0.elapsed_time(e1) / args.steps
     voxels = (int(N.sum().item()) + int(M.sum().item())) // args.steps
+    atomics = 2 * int(counter.item())
+    peaks = _peaks()
+    l2_rate = hulld.hd_probe_atomics(hulld.HD_PROBE_L2_RANDOM)
     line = {"metric": f"histories/s (thick rays, k = {k} voxels in-plane, missed and hit counts)",
             "value": n / (ms * 1e-3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
@@ -675,6 +687,12 @@ def run_thick(args):
             "config": {"workload": WORKLOAD + f"; thick rays k = {k}", "histories": n,
                        "fraction": args.fraction},
             "thick_voxels_per_step": voxels, "thick_voxels_per_s": voxels / (ms * 1e-3),
+            "roofline": {"bound": "l2_atomic", "kernel": "thick_kernel",
+                         "achieved": atomics / (ms * 1e-3), "peak": l2_rate,
+                         "unit": "atomics/s", "frac": atomics / (ms * 1e-3) / l2_rate,
+                         "atomics_per_step": atomics,
+                         "peak_source": "hd_probe_atomics L2 random (measured in this run)",
+                         "hbm_peak_gbs": peaks["hbm_gbs"]},
             "gpu_launches": 3 * args.steps, "clocks": clocks}
     if not args.no_cpu_baseline:
         import oracle

@@ -514,6 +514,8 @@ HD_API hd_status hd_classify(const float *wepl, int64_t n, const hd_params *para
  * to apply (for instance H_1 = [N = 0]).  workspace: device memory of at
  * least hd_accumulate_thick_workspace bytes (two int32 difference arrays of
  * about V entries per class), 256-byte aligned; the call clears it.
+ * intervals (device, one int64, may be NULL) receives the number of dilated
+ * row intervals the call added (each costs two atomics; a measurement aid).
  * HD_ERR_RANGE for k outside [0, 16] or an unsupported geometry.
  * Stream-ordered on `stream`. */
 HD_API hd_status hd_accumulate_thick_workspace(const hd_geometry *geom, size_t *bytes);
@@ -521,7 +523,7 @@ HD_API hd_status hd_accumulate_thick(const hd_geometry *geom, const hd_params *p
                                      const float *angle_deg, const float *u_in, const float *v_in,
                                      const float *u_out, const float *v_out, const float *wepl,
                                      int64_t n, uint32_t *N, uint32_t *M, void *workspace,
-                                     size_t workspace_bytes, void *stream);
+                                     size_t workspace_bytes, int64_t *intervals, void *stream);
 
 /* ------------------------------------------------------------------------
  * Hull diagnostics (not steps of the method: the measures the paper reports

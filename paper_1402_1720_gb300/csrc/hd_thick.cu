@@ -31,40 +31,39 @@ constexpr int kMaxK = 16;
 // (ny + 1) entries per (x, z) column.  One pair for N and one for M.
 struct ThickWs {
     int32_t *dx[2], *dy[2];
+    unsigned long long *intervals;  // row intervals emitted (two atomics each)
 };
 
 struct ThickRing {
     int lo[2 * kMaxK + 1], hi[2 * kMaxK + 1];
 };
 
-// Emits target row centred on run jc of the current slice: the window's
-// runs are max(0, jc - k) .. min(jc + k, last); its minor index is
-// m0 + s jc.
-__device__ __forceinline__ void emit(const ThickRing &rg, int jc, int last, int k, int m0, int s,
-                                     int nminor, int nmaj, int32_t *diff, int64_t slice_row0)
+// Emits the interval of target row t from the window's first and last runs
+// (their ring slots pa and pb); returns 1 when t is inside the slice.
+__device__ __forceinline__ unsigned emit(const ThickRing &rg, int pa, int pb, int t, int k,
+                                         int nminor, int nmaj, int32_t *diff, int64_t slice_row0)
 {
-    const int t = m0 + s * jc;
-    if (t < 0 || t >= nminor) return;
-    const int ja = max(0, jc - k), jb = min(jc + k, last);
-    const int R = 2 * k + 1;
-    const int la = rg.lo[ja % R], lb = rg.lo[jb % R];
-    const int ha = rg.hi[ja % R], hb = rg.hi[jb % R];
-    const int lo = max(min(la, lb) - k, 0);
-    const int hi = min(max(ha, hb) + k, nmaj - 1);
+    if (t < 0 || t >= nminor) return 0;
+    const int lo = max(min(rg.lo[pa], rg.lo[pb]) - k, 0);
+    const int hi = min(max(rg.hi[pa], rg.hi[pb]) + k, nmaj - 1);
     int32_t *row = diff + (slice_row0 + t) * static_cast<int64_t>(nmaj + 1);
     atomicAdd(row + lo, 1);
     atomicAdd(row + hi + 1, -1);
+    return 1;
 }
 
 __global__ void __launch_bounds__(kThickThreads) thick_kernel(Inputs in, int64_t n, GeomQ g,
                                                               Cordic cd, float tau_l, float tau_h,
                                                               int use_miss, int use_hit, int k,
-                                                              ThickWs ws)
+                                                              ThickWs ws,
+                                                              unsigned long long *intervals)
 {
     long long tc_c = 0, tc_s = 0;
     float tc_ang = 0.0f;
     bool tc_valid = false;
     ThickRing rg;
+    unsigned emitted = 0;
+    const int R = 2 * k + 1;
     const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
     for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
          i += stride) {
@@ -87,32 +86,47 @@ __global__ void __launch_bounds__(kThickThreads) thick_kernel(Inputs in, int64_t
         const int s = (wk.flags & 2) ? 1 : -1;  // the in-plane minor axis' direction
         const int nmaj = ymaj ? g.ny : g.nx, nminor = ymaj ? g.nx : g.ny;
         int32_t *diff = ymaj ? ws.dy[cls] : ws.dx[cls];
-        const int R = 2 * k + 1;
-        int zc = -1, m0 = 0, j = 0;  // current slice, its first minor index, runs in it
+        // Targets are centred on runs -k .. J - 1 + k of a slice of J runs
+        // (target minor index m0 + s jc); the one centred on run jc = j - k
+        // has its whole window (runs max(0, j - 2k) .. j) once run j has
+        // arrived, the last k when the slice ends.  Run j sits in ring slot
+        // p = j mod (2k + 1), so run j - 2k is in the next slot.
+        int zc = -1, m0 = 0, j = 0, p = 0;
+        int64_t row0 = 0;
         int row, lo, hi;
-        // targets are centred on runs -k .. J - 1 + k of a slice of J runs;
-        // the one centred on run j - k is complete once run j has arrived,
-        // the last k when the slice ends
         auto close_slice = [&]() {
-            const int64_t row0 = static_cast<int64_t>(zc) * nminor;
-            for (int jc = j - k; jc <= j - 1 + k; ++jc)
-                emit(rg, jc, j - 1, k, m0, s, nminor, nmaj, diff, row0);
+            // centres j - k .. j - 1 + k, windows from max(0, jc - k) to the
+            // last run (slot p - 1)
+            const int pb = p == 0 ? R - 1 : p - 1;
+            for (int jc = j - k; jc <= j - 1 + k; ++jc) {
+                const int ja = jc - k;
+                const int pa = ja <= 0 ? 0 : (ja % R);
+                emitted += emit(rg, pa, pb, m0 + s * jc, k, nminor, nmaj, diff, row0);
+            }
         };
         while (run_next(wk, row, lo, hi)) {
-            const int mz = row / nminor, mm = row - mz * nminor;
+            const int mz = row / nminor;
             if (mz != zc) {
                 if (zc >= 0) close_slice();
                 zc = mz;
-                m0 = mm;
+                m0 = row - mz * nminor;
+                row0 = static_cast<int64_t>(zc) * nminor;
                 j = 0;
+                p = 0;
             }
-            rg.lo[j % R] = lo;
-            rg.hi[j % R] = hi;
-            emit(rg, j - k, j, k, m0, s, nminor, nmaj, diff, static_cast<int64_t>(zc) * nminor);
+            rg.lo[p] = lo;
+            rg.hi[p] = hi;
+            const int pa = j >= 2 * k ? (p + 1 == R ? 0 : p + 1) : 0;
+            emitted += emit(rg, pa, p, m0 + s * (j - k), k, nminor, nmaj, diff, row0);
             ++j;
+            p = p + 1 == R ? 0 : p + 1;
         }
         if (zc >= 0) close_slice();
     }
+    unsigned long long e = emitted;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) e += __shfl_xor_sync(0xffffffffu, e, o);
+    if ((threadIdx.x & 31) == 0 && e != 0) atomicAdd(intervals, e);
 }
 
 __global__ void __launch_bounds__(kThickThreads) thick_rows_kernel(
@@ -146,8 +160,9 @@ size_t thick_layout(const hd_geometry *g, void *base, ThickWs *ws)
         ws->dx[1] = reinterpret_cast<int32_t *>(p + bx);
         ws->dy[0] = reinterpret_cast<int32_t *>(p + 2 * bx);
         ws->dy[1] = reinterpret_cast<int32_t *>(p + 2 * bx + by);
+        ws->intervals = reinterpret_cast<unsigned long long *>(p + 2 * bx + 2 * by);
     }
-    return 2 * bx + 2 * by;
+    return 2 * bx + 2 * by + 256;
 }
 
 }  // namespace
@@ -168,7 +183,7 @@ hd_status hd_accumulate_thick(const hd_geometry *geom, const hd_params *params, 
                               const float *angle_deg, const float *u_in, const float *v_in,
                               const float *u_out, const float *v_out, const float *wepl,
                               int64_t n, uint32_t *N, uint32_t *M, void *workspace,
-                              size_t workspace_bytes, void *stream)
+                              size_t workspace_bytes, int64_t *intervals, void *stream)
 {
     if (!geom || !params || n < 0 || !workspace) return HD_ERR_ARG;
     if (k < 0 || k > hd::kMaxK) return HD_ERR_RANGE;
@@ -205,7 +220,8 @@ hd_status hd_accumulate_thick(const hd_geometry *geom, const hd_params *params, 
         if (blocks > int64_t(sms) * 8) blocks = int64_t(sms) * 8;
         const hd::Inputs in{angle_deg, u_in, v_in, u_out, v_out, wepl};
         hd::thick_kernel<<<static_cast<unsigned>(blocks), hd::kThickThreads, 0, st>>>(
-            in, n, gq, cd, params->wepl_miss_lt, params->wepl_hit_gt, use_miss, use_hit, k, ws);
+            in, n, gq, cd, params->wepl_miss_lt, params->wepl_hit_gt, use_miss, use_hit, k, ws,
+            ws.intervals);
         e = cudaGetLastError();
     }
     const int64_t plane = int64_t(geom->nx) * geom->ny;
@@ -219,6 +235,8 @@ hd_status hd_accumulate_thick(const hd_geometry *geom, const hd_params *params, 
             ws.dy[c], ry, geom->ny, geom->nx, geom->nx, plane, 1, out);
         e = cudaGetLastError();
     }
+    if (e == cudaSuccess && intervals)
+        e = cudaMemcpyAsync(intervals, ws.intervals, sizeof(int64_t), cudaMemcpyDeviceToDevice, st);
     if (e != cudaSuccess) {
         hd::note_cuda_error(e, "hd_accumulate_thick");
         return HD_ERR_CUDA;

@@ -100,12 +100,25 @@ __device__ __forceinline__ unsigned warp_incl_scan(unsigned v)
     return v;
 }
 
-// Decide tiled / global path for up to 4 records per lane (one pair-budget
-// reservation per warp), count tiles in the block histogram, and append the
-// records with one pair of atomics per warp.
+// Per-block staging of the appends: each warp's pair demand and record
+// counts, and the block's bases (two sets, alternating by iteration, so that
+// a warp starting the next iteration never overwrites what a slower warp of
+// this one still reads).
+constexpr int kIngestWarps = 8;  // 256-thread blocks
+struct AppendStage {
+    unsigned pairs[2][kIngestWarps];
+    unsigned recs[2][kIngestWarps];  // missed + 65536 hit
+    unsigned base_pairs[2], base_miss[2], base_hit[2];
+};
+
+// Decide tiled / global path for up to 4 records per lane, count tiles in
+// the block histogram, and append the records.  The pair budget and the two
+// record counters are reserved once per block and iteration (all threads
+// call this together): same-address atomics on the three counters are what
+// limit a warp-per-reservation scheme.
 __device__ __forceinline__ void admit_and_append(const TilePlan &tp, const Records &rec,
                                                  Ctrl *ctrl, uint32_t *s_hist, int cls[4],
-                                                 const int32_t r[4][6])
+                                                 const int32_t r[4][6], AppendStage &st, int par)
 {
     const unsigned lane = threadIdx.x & 31u;
     int tcount[4];
@@ -123,12 +136,36 @@ __device__ __forceinline__ void admit_and_append(const TilePlan &tp, const Recor
         tcount[k] = (tp.ntiles > 0 && c <= tp.max_tiles) ? c : -1;
         if (tcount[k] > 0) demand += static_cast<unsigned>(c);
     }
-    // pair-budget reservation
+    // records this lane appends: missed + 65536 hit (a record kept here
+    // keeps its class whatever path it takes)
+    unsigned mine = 0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) mine += (cls[k] == 1) ? 1u : (cls[k] == 2 ? 65536u : 0u);
+    const unsigned warp = threadIdx.x >> 5;
     const unsigned incl = warp_incl_scan(demand);
-    const unsigned wtotal = __shfl_sync(0xffffffffu, incl, 31);
-    unsigned base = 0;
-    if (lane == 31 && wtotal) base = atomicAdd(&ctrl->pairs_used, wtotal);
-    base = __shfl_sync(0xffffffffu, base, 31);
+    const unsigned inc2 = warp_incl_scan(mine);
+    if (lane == 31) {
+        st.pairs[par][warp] = incl;
+        st.recs[par][warp] = inc2;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned tp_ = 0, tr = 0;
+        for (int w = 0; w < kIngestWarps; ++w) {
+            tp_ += st.pairs[par][w];
+            tr += st.recs[par][w];
+        }
+        st.base_pairs[par] = tp_ ? atomicAdd(&ctrl->pairs_used, tp_) : 0u;
+        st.base_miss[par] = (tr & 0xffffu) ? atomicAdd(&ctrl->rec_miss, tr & 0xffffu) : 0u;
+        st.base_hit[par] = (tr >> 16) ? atomicAdd(&ctrl->rec_hit, tr >> 16) : 0u;
+    }
+    __syncthreads();
+    unsigned wp = 0, wr = 0;  // earlier warps' pairs and records
+    for (unsigned w = 0; w < warp; ++w) {
+        wp += st.pairs[par][w];
+        wr += st.recs[par][w];
+    }
+    const unsigned base = st.base_pairs[par] + wp;
     unsigned long long end = static_cast<unsigned long long>(base) + (incl - demand);
     int status[4];
 #pragma unroll
@@ -148,23 +185,11 @@ __device__ __forceinline__ void admit_and_append(const TilePlan &tp, const Recor
                         atomicAdd(&s_hist[off + x + tp.ntx * (y + tp.nty * z)], 1u);
         }
     }
-    // append
-    unsigned mine = 0;
-#pragma unroll
-    for (int k = 0; k < 4; ++k) mine += (cls[k] == 1) ? 1u : (cls[k] == 2 ? 65536u : 0u);
-    const unsigned inc2 = warp_incl_scan(mine);
-    const unsigned total = __shfl_sync(0xffffffffu, inc2, 31);
-    if (total == 0) return;
-    unsigned base_m = 0, base_h = 0;
-    if (lane == 31) {
-        if (total & 0xffffu) base_m = atomicAdd(&ctrl->rec_miss, total & 0xffffu);
-        if (total >> 16) base_h = atomicAdd(&ctrl->rec_hit, total >> 16);
-    }
-    base_m = __shfl_sync(0xffffffffu, base_m, 31);
-    base_h = __shfl_sync(0xffffffffu, base_h, 31);
+    // append at the block's bases plus the earlier warps' and lanes' records
+    if (mine == 0) return;
     const unsigned excl = inc2 - mine;
-    unsigned pm = base_m + (excl & 0xffffu);
-    unsigned ph = base_h + (excl >> 16);
+    unsigned pm = st.base_miss[par] + (wr & 0xffffu) + (excl & 0xffffu);
+    unsigned ph = st.base_hit[par] + (wr >> 16) + (excl >> 16);
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
         if (cls[k] == 0) continue;
@@ -183,6 +208,7 @@ __global__ void __launch_bounds__(256, 4) ingest_kernel(Inputs in, int64_t n, Ge
                                                      Ctrl *ctrl, uint32_t *tile_count)
 {
     extern __shared__ uint32_t s_hist[];  // 2 * ntiles counters
+    __shared__ AppendStage s_stage;
     const int nh = 2 * tp.ntiles;
     for (int t = threadIdx.x; t < nh; t += blockDim.x) s_hist[t] = 0;
     __syncthreads();
@@ -228,7 +254,7 @@ __global__ void __launch_bounds__(256, 4) ingest_kernel(Inputs in, int64_t n, Ge
             cls[0] = ingest_one(g, cd, tau_l, tau_h, use_miss, use_hit, in.angle[u], in.u_in[u],
                                 in.v_in[u], in.u_out[u], in.v_out[u], in.wepl[u], r[0], acc, tc);
         }
-        admit_and_append(tp, rec, ctrl, s_hist, cls, r);
+        admit_and_append(tp, rec, ctrl, s_hist, cls, r, s_stage, static_cast<int>(it & 1));
     }
     const unsigned a0 = warp_sum_u32(acc.n_in), a1 = warp_sum_u32(acc.n_miss),
                    a2 = warp_sum_u32(acc.n_hit), a3 = warp_sum_u32(acc.n_none),

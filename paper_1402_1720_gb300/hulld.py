@@ -191,7 +191,7 @@ _SIGS = {
     "hd_accumulate_thick_workspace": ([ctypes.POINTER(hd_geometry), ctypes.POINTER(_SZ)],
                                       ctypes.c_int),
     "hd_accumulate_thick": ([ctypes.POINTER(hd_geometry), ctypes.POINTER(hd_params), _I32] +
-                            [_VP] * 6 + [_I64, _VP, _VP, _VP, _SZ, _VP], ctypes.c_int),
+                            [_VP] * 6 + [_I64, _VP, _VP, _VP, _SZ, _VP, _VP], ctypes.c_int),
     "hd_sm_canny_workspace": ([_I32, _I32, _I32, ctypes.POINTER(_SZ)], ctypes.c_int),
     "hd_sm_canny": ([_VP, _I32, _I32, _I32, _I32, _VP, _SZ, _VP, _VP, _VP, _VP], ctypes.c_int),
     "hd_fill_enclosed": ([_VP, _I32, _I32, _I32, _VP, _VP], ctypes.c_int),
@@ -1037,9 +1037,12 @@ def hd_accumulate_thick_workspace(geometry) -> int:
     return out.value
 
 
-def hd_accumulate_thick(geometry, params, k: int, arrays, N, M, workspace=None, stream=None):
+def hd_accumulate_thick(geometry, params, k: int, arrays, N, M, workspace=None, stream=None,
+                        intervals=None):
     """Adds thick-ray counts (A_i dilated by k voxels in-plane) of device
-    history arrays into device N, M (uint32 viewed as int32 tensors)."""
+    history arrays into device N, M (uint32 viewed as int32 tensors);
+    `intervals` (a one-element int64 device tensor) receives the number of
+    row intervals emitted."""
     import torch
     g = _geometry(geometry)
     p = _params(params)
@@ -1049,7 +1052,8 @@ def hd_accumulate_thick(geometry, params, k: int, arrays, N, M, workspace=None, 
                                 device="cuda")
     nptr = _dev_ptr(N, "N") if N is not None else None
     mptr = _dev_ptr(M, "M") if M is not None else None
+    iptr = _dev_ptr(intervals, "intervals") if intervals is not None else None
     _check(load().hd_accumulate_thick(ctypes.byref(g), ctypes.byref(p), int(k), *ptrs, n, nptr,
                                       mptr, _dev_ptr(workspace, "workspace"),
-                                      int(workspace.numel() * workspace.element_size()),
+                                      int(workspace.numel() * workspace.element_size()), iptr,
                                       _stream(stream)), "hd_accumulate_thick")
