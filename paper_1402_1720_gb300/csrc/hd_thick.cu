@@ -13,9 +13,11 @@
 // difference array along the major axis (x-major walks along x, y-major ones
 // along y), and row prefix sums turn the differences into counts.
 //
-//   thick_kernel      thread per history: the exact run walk over the whole
-//                     grid, a ring of the last 2k + 1 runs of the current
-//                     slice, one interval per target row (two atomics)
+//   thick_kernel      persistent warps, a lane per history (lanes refilled
+//                     from a work counter when enough are idle): the exact
+//                     run walk over the whole grid, a ring of the last 2k + 1
+//                     runs of the current slice, one interval per target row
+//                     (two atomics)
 //   thick_rows_kernel thread per x-row / y-column: prefix sums added to N, M
 #include <cuda_runtime.h>
 
@@ -32,6 +34,7 @@ constexpr int kMaxK = 16;
 struct ThickWs {
     int32_t *dx[2], *dy[2];
     unsigned long long *intervals;  // row intervals emitted (two atomics each)
+    unsigned long long *next;       // next history to hand out
 };
 
 struct ThickRing {
@@ -52,81 +55,143 @@ __device__ __forceinline__ unsigned emit(const ThickRing &rg, int pa, int pb, in
     return 1;
 }
 
+// One lane's walk: the run walk and the state of its current slice.
+// Targets of a slice of J runs are centred on runs -k .. J - 1 + k (target
+// minor index m0 + s jc); the one centred on run jc = j - k has its whole
+// window (runs max(0, j - 2k) .. j) once run j has arrived, the last k when
+// the slice ends.  Run j sits in ring slot p = j mod (2k + 1), so run j - 2k
+// is in the next slot.
+struct ThickLane {
+    RunWalk wk;
+    int32_t *diff;
+    int nmaj, nminor, s;
+    int zc, m0, j, p;
+    int prev_row;
+    int64_t row0;
+};
+
+__device__ __forceinline__ unsigned close_slice(const ThickLane &L, const ThickRing &rg, int k)
+{
+    const int R = 2 * k + 1;
+    const int pb = L.p == 0 ? R - 1 : L.p - 1;  // the slice's last run
+    unsigned e = 0;
+    for (int jc = L.j - k; jc <= L.j - 1 + k; ++jc) {
+        const int ja = jc - k;
+        const int pa = ja <= 0 ? 0 : (ja % R);
+        e += emit(rg, pa, pb, L.m0 + L.s * jc, k, L.nminor, L.nmaj, L.diff, L.row0);
+    }
+    return e;
+}
+
+// Starts history i on a lane: classification, geometry, walk set-up; false
+// when it has nothing to add.
+__device__ __forceinline__ bool start_history(const Inputs &in, int64_t i, const GeomQ &g,
+                                              const Cordic &cd, float tau_l, float tau_h,
+                                              int use_miss, int use_hit, const ThickWs &ws,
+                                              ThickLane &L, float &tc_ang, bool &tc_valid,
+                                              long long &tc_c, long long &tc_s)
+{
+    const float w = in.wepl[i];
+    const int cls = w < tau_l ? 0 : (w > tau_h ? 1 : -1);
+    if (cls < 0 || (cls == 0 && !use_miss) || (cls == 1 && !use_hit)) return false;
+    const float ang = in.angle[i];
+    if (!(fabsf(ang) < 1048576.0f)) return false;
+    if (!tc_valid || ang != tc_ang) {
+        cordic_cs(q16_of(ang), cd, tc_c, tc_s);
+        tc_ang = ang;
+        tc_valid = true;
+    }
+    int32_t r[6];
+    if (!endpoints_cs(g, tc_c, tc_s, in.u_in[i], in.v_in[i], in.u_out[i], in.v_out[i], r))
+        return false;
+    if (!run_begin(L.wk, r, r + 3, g.nx, g.ny, g.nz)) return false;
+    const bool ymaj = (L.wk.flags >> 5) & 1;
+    L.s = (L.wk.flags & 2) ? 1 : -1;  // the in-plane minor axis' direction
+    L.nmaj = ymaj ? g.ny : g.nx;
+    L.nminor = ymaj ? g.nx : g.ny;
+    L.diff = ymaj ? ws.dy[cls] : ws.dx[cls];
+    L.zc = -1;
+    L.m0 = L.j = L.p = 0;
+    L.prev_row = 0;
+    L.row0 = 0;
+    return true;
+}
+
+constexpr int kThickRefill = 8;     // idle lanes that trigger a refill
+constexpr int kThickRunsPerStep = 4;
+
+// Persistent warps: each lane walks one history at a time; once enough
+// lanes are idle, they take the next histories together (one atomic per
+// warp on the work counter), so lanes do not idle behind a long walk.
 __global__ void __launch_bounds__(kThickThreads) thick_kernel(Inputs in, int64_t n, GeomQ g,
                                                               Cordic cd, float tau_l, float tau_h,
                                                               int use_miss, int use_hit, int k,
                                                               ThickWs ws,
                                                               unsigned long long *intervals)
 {
+    const unsigned lane = threadIdx.x & 31u;
     long long tc_c = 0, tc_s = 0;
     float tc_ang = 0.0f;
     bool tc_valid = false;
     ThickRing rg;
+    ThickLane L;
+    bool active = false, drained = false;
     unsigned emitted = 0;
     const int R = 2 * k + 1;
-    const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
-    for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
-         i += stride) {
-        const float w = in.wepl[i];
-        const int cls = w < tau_l ? 0 : (w > tau_h ? 1 : -1);
-        if (cls < 0 || (cls == 0 && !use_miss) || (cls == 1 && !use_hit)) continue;
-        const float ang = in.angle[i];
-        if (!(fabsf(ang) < 1048576.0f)) continue;
-        if (!tc_valid || ang != tc_ang) {
-            cordic_cs(q16_of(ang), cd, tc_c, tc_s);
-            tc_ang = ang;
-            tc_valid = true;
-        }
-        int32_t r[6];
-        if (!endpoints_cs(g, tc_c, tc_s, in.u_in[i], in.v_in[i], in.u_out[i], in.v_out[i], r))
+    for (;;) {
+        const unsigned idle = __ballot_sync(0xffffffffu, !active);
+        if (drained && idle == 0xffffffffu) break;
+        if (!drained && (__popc(idle) >= kThickRefill || idle == 0xffffffffu)) {
+            unsigned long long base = 0;
+            if (lane == 0) base = atomicAdd(ws.next, static_cast<unsigned long long>(__popc(idle)));
+            base = __shfl_sync(0xffffffffu, base, 0);
+            if (base >= static_cast<unsigned long long>(n)) drained = true;
+            if (!active) {
+                const unsigned long long i = base + __popc(idle & ((1u << lane) - 1u));
+                if (i < static_cast<unsigned long long>(n))
+                    active = start_history(in, static_cast<int64_t>(i), g, cd, tau_l, tau_h,
+                                           use_miss, use_hit, ws, L, tc_ang, tc_valid, tc_c,
+                                           tc_s);
+            }
             continue;
-        RunWalk wk;
-        if (!run_begin(wk, r, r + 3, g.nx, g.ny, g.nz)) continue;
-        const bool ymaj = (wk.flags >> 5) & 1;
-        const int s = (wk.flags & 2) ? 1 : -1;  // the in-plane minor axis' direction
-        const int nmaj = ymaj ? g.ny : g.nx, nminor = ymaj ? g.nx : g.ny;
-        int32_t *diff = ymaj ? ws.dy[cls] : ws.dx[cls];
-        // Targets are centred on runs -k .. J - 1 + k of a slice of J runs
-        // (target minor index m0 + s jc); the one centred on run jc = j - k
-        // has its whole window (runs max(0, j - 2k) .. j) once run j has
-        // arrived, the last k when the slice ends.  Run j sits in ring slot
-        // p = j mod (2k + 1), so run j - 2k is in the next slot.
-        int zc = -1, m0 = 0, j = 0, p = 0;
-        int64_t row0 = 0;
-        int row, lo, hi;
-        auto close_slice = [&]() {
-            // centres j - k .. j - 1 + k, windows from max(0, jc - k) to the
-            // last run (slot p - 1)
-            const int pb = p == 0 ? R - 1 : p - 1;
-            for (int jc = j - k; jc <= j - 1 + k; ++jc) {
-                const int ja = jc - k;
-                const int pa = ja <= 0 ? 0 : (ja % R);
-                emitted += emit(rg, pa, pb, m0 + s * jc, k, nminor, nmaj, diff, row0);
-            }
-        };
-        while (run_next(wk, row, lo, hi)) {
-            const int mz = row / nminor;
-            if (mz != zc) {
-                if (zc >= 0) close_slice();
-                zc = mz;
-                m0 = row - mz * nminor;
-                row0 = static_cast<int64_t>(zc) * nminor;
-                j = 0;
-                p = 0;
-            }
-            rg.lo[p] = lo;
-            rg.hi[p] = hi;
-            const int pa = j >= 2 * k ? (p + 1 == R ? 0 : p + 1) : 0;
-            emitted += emit(rg, pa, p, m0 + s * (j - k), k, nminor, nmaj, diff, row0);
-            ++j;
-            p = p + 1 == R ? 0 : p + 1;
         }
-        if (zc >= 0) close_slice();
+        if (!active) continue;
+#pragma unroll 1
+        for (int u = 0; u < kThickRunsPerStep; ++u) {
+            int row, lo, hi;
+            if (!run_next(L.wk, row, lo, hi)) {
+                if (L.zc >= 0) emitted += close_slice(L, rg, k);
+                active = false;
+                break;
+            }
+            // rows are minor + nminor z: inside a slice consecutive runs
+            // differ by one row, so only a larger step can start a new slice
+            const int step = row - L.prev_row;
+            L.prev_row = row;
+            if (L.zc < 0 || step > 1 || step < -1 || L.nminor <= 2) {
+                const int mz = row / L.nminor;
+                if (mz != L.zc) {
+                    if (L.zc >= 0) emitted += close_slice(L, rg, k);
+                    L.zc = mz;
+                    L.m0 = row - mz * L.nminor;
+                    L.row0 = static_cast<int64_t>(mz) * L.nminor;
+                    L.j = 0;
+                    L.p = 0;
+                }
+            }
+            rg.lo[L.p] = lo;
+            rg.hi[L.p] = hi;
+            const int pa = L.j >= 2 * k ? (L.p + 1 == R ? 0 : L.p + 1) : 0;
+            emitted += emit(rg, pa, L.p, L.m0 + L.s * (L.j - k), k, L.nminor, L.nmaj, L.diff,
+                            L.row0);
+            ++L.j;
+            L.p = L.p + 1 == R ? 0 : L.p + 1;
+        }
     }
     unsigned long long e = emitted;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) e += __shfl_xor_sync(0xffffffffu, e, o);
-    if ((threadIdx.x & 31) == 0 && e != 0) atomicAdd(intervals, e);
+    if (lane == 0 && e != 0) atomicAdd(intervals, e);
 }
 
 __global__ void __launch_bounds__(kThickThreads) thick_rows_kernel(
@@ -161,6 +226,7 @@ size_t thick_layout(const hd_geometry *g, void *base, ThickWs *ws)
         ws->dy[0] = reinterpret_cast<int32_t *>(p + 2 * bx);
         ws->dy[1] = reinterpret_cast<int32_t *>(p + 2 * bx + by);
         ws->intervals = reinterpret_cast<unsigned long long *>(p + 2 * bx + 2 * by);
+        ws->next = ws->intervals + 1;
     }
     return 2 * bx + 2 * by + 256;
 }
@@ -217,7 +283,7 @@ hd_status hd_accumulate_thick(const hd_geometry *geom, const hd_params *params, 
     cudaError_t e = cudaMemsetAsync(workspace, 0, need, st);
     if (e == cudaSuccess && n > 0) {
         int64_t blocks = (n + hd::kThickThreads - 1) / hd::kThickThreads;
-        if (blocks > int64_t(sms) * 8) blocks = int64_t(sms) * 8;
+        if (blocks > int64_t(sms) * 4) blocks = int64_t(sms) * 4;  // resident, persistent
         const hd::Inputs in{angle_deg, u_in, v_in, u_out, v_out, wepl};
         hd::thick_kernel<<<static_cast<unsigned>(blocks), hd::kThickThreads, 0, st>>>(
             in, n, gq, cd, params->wepl_miss_lt, params->wepl_hit_gt, use_miss, use_hit, k, ws,
