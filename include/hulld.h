@@ -252,6 +252,19 @@ typedef struct {
 HD_API hd_status hd_scan_set_tuning(hd_scan *scan, const hd_tuning *tuning);
 HD_API hd_status hd_scan_get_tuning(hd_scan *scan, hd_tuning *out);
 
+/* Thick rays for this scan (Eq. 3.2 with d_0 > 0): every history's A_i is
+ * replaced by A_i(k), the voxels within k voxels of A_i in-plane in the same
+ * slice (see hd_accumulate_thick), for all three methods; N, M, the hulls,
+ * thresholds and statistics follow from the thick sets (the statistics'
+ * voxel counts are the thick sets' sizes; runs and pairs_general stay 0).
+ * k = 0 restores the thin paths.  Only before any histories (after create or
+ * reset): HD_ERR_STATE otherwise; HD_ERR_RANGE for k outside [0, 16].  A scan
+ * with SC and without MSC then counts N (H_1 = [N = 0]) instead of keeping a
+ * carve mask; allocates the thick rays' difference arrays (about 16 bytes
+ * per voxel).  Thick scans cannot join a batch (hd_batch_add_item returns
+ * HD_ERR_STATE). */
+HD_API hd_status hd_scan_set_thick(hd_scan *scan, int32_t k);
+
 /* Start (enable = 1) or stop (0) recording CUDA events around the scan's
  * kernels; starting also clears the accumulated times.  A library aid for
  * measurement: no counterpart in the paper. */

@@ -531,6 +531,18 @@ def accumulate_thick(g, hist, k: int, params: Params = Params()) -> Dict:
     return {"N": N, "M": M, "stats": stats}
 
 
+def run_thick(g, hist, k: int, params: Params = Params()) -> Dict:
+    """run() with every A_i replaced by its thick set A_i(k): counts from
+    accumulate_thick, then the same decisions (H_1 = [N = 0])."""
+    acc = accumulate_thick(g, hist, k, params)
+    dims = (g.nx, g.ny, g.nz)
+    out = dict(acc)
+    out["H1"] = sc_from_counts(acc["N"])
+    out["H2"] = msc_decide(acc["N"], dims, params.nt, params.nbhd)
+    out.update(sm_decide(acc["M"], dims, params.sm_per_slice, params.nbhd, params.sm_ge))
+    return out
+
+
 # ------------------------------------------ hull diagnostics (next row f3)
 def hull_compare(hull, obj, dims) -> Dict:
     """Extra (hull, not object) and missing (object, not hull) voxels per

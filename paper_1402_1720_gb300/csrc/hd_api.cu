@@ -8,6 +8,7 @@
 #include <vector>
 
 #include "hd_geom.cuh"
+#include "hd_thick.cuh"
 
 namespace {
 
@@ -130,6 +131,8 @@ struct hd_scan {
     uint32_t *tile_cursor = nullptr;  // 2 * ntiles
     int64_t *rows_scratch = nullptr;  // tile sums of the system-row offset scan
     int64_t rows_scratch_cap = 0;
+    int32_t thick_k = 0;             // thick rays: in-plane dilation (0 = thin paths)
+    void *thick_ws = nullptr;        // their difference arrays
     float *staging = nullptr;  // copied host inputs: 6 columns of staging_half floats
     int64_t staging_half = 0;
     uint32_t *compact_blocks = nullptr;
@@ -203,7 +206,7 @@ void free_scan(hd_scan *s)
     void *ptrs[] = {s->N, s->M, s->carve, s->H1, s->H2, s->H3, s->bits_out, s->slice_key,
                     s->mt, s->slope, s->index, s->ctrl, s->rec_buf, s->staging,
                     s->compact_blocks, s->d_count, s->compact_out, s->pair_buf, s->jobs,
-                    s->rows_scratch,
+                    s->rows_scratch, s->thick_ws,
                     s->tile_count, s->tile_cursor, s->desc_dev};
     for (void *p : ptrs)
         if (p) cudaFree(p);
@@ -479,6 +482,15 @@ int finalize_launches(const hd_scan *scan) { return (scan->params.methods & HD_S
 // One chunk through the whole path on st.
 hd_status run_chunk(hd_scan *s, const hd::Inputs &in, int64_t n, cudaStream_t st)
 {
+    if (s->thick_k > 0) {  // thick rays: their own walk, same counts
+        const uint32_t m = s->params.methods;
+        HD_CUDA(hd::launch_thick(in, n, &s->geom, s->gq, s->cordic, s->params.wepl_miss_lt,
+                                 s->params.wepl_hit_gt, (m & (HD_SC | HD_MSC)) ? 1 : 0,
+                                 (m & HD_SM) ? 1 : 0, s->thick_k, s->thick_ws, s->N, s->M,
+                                 &s->ctrl->n_in, nullptr, s->sm_count, st));
+        s->launches += 1;
+        return HD_OK;
+    }
     hd_status r = upload_desc(s, st);
     if (r != HD_OK) return r;
     cudaEvent_t e0 = prof_begin(s, st);
@@ -913,6 +925,40 @@ hd_status hd_scan_get_hull_indices(hd_scan *scan, int32_t method, int32_t *dst,
     return HD_OK;
 }
 
+hd_status hd_scan_set_thick(hd_scan *scan, int32_t k)
+{
+    if (!scan) return HD_ERR_ARG;
+    if (k < 0 || k > 16) return HD_ERR_RANGE;
+    if (scan->n_total != 0) return HD_ERR_STATE;
+    DeviceGuard g(scan->device);
+    if (!g.ok) return HD_ERR_CUDA;
+    if (k > 0) {
+        HD_CUDA(cudaDeviceSynchronize());
+        if (!scan->thick_ws) {
+            if (cudaMalloc(&scan->thick_ws, hd::thick_workspace_bytes(&scan->geom)) !=
+                cudaSuccess) {
+                cudaGetLastError();
+                scan->thick_ws = nullptr;
+                return HD_ERR_NOMEM;
+            }
+        }
+        // SC alone keeps a carve mask; thick rays count N instead, and
+        // H_1 = [N = 0] (the decision reads N whenever it exists)
+        if (!scan->N && (scan->params.methods & HD_SC)) {
+            if (cudaMalloc(&scan->N, sizeof(uint32_t) * static_cast<size_t>(scan->V)) !=
+                cudaSuccess) {
+                cudaGetLastError();
+                scan->N = nullptr;
+                return HD_ERR_NOMEM;
+            }
+            HD_CUDA(cudaMemset(scan->N, 0, sizeof(uint32_t) * static_cast<size_t>(scan->V)));
+            scan->desc_dirty = true;
+        }
+    }
+    scan->thick_k = k;
+    return HD_OK;
+}
+
 hd_status hd_scan_set_tuning(hd_scan *scan, const hd_tuning *t)
 {
     if (!scan || !t) return HD_ERR_ARG;
@@ -1199,6 +1245,7 @@ hd_status hd_batch_add_item(hd_batch *batch, hd_scan *scan, const float *angle_d
     if (flags & ~(HD_BATCH_RESET | HD_BATCH_FINALIZE)) return HD_ERR_ARG;
     if (n > 0 && (!angle_deg || !u_in || !v_in || !u_out || !v_out || !wepl)) return HD_ERR_ARG;
     if (scan->device != batch->device) return HD_ERR_ARG;
+    if (scan->thick_k > 0) return HD_ERR_STATE;  // batches run the tiled thin paths
     if (static_cast<int>(batch->items.size()) >= batch->max_items) return HD_ERR_STATE;
     hd_batch::Item it;
     it.scan = scan;

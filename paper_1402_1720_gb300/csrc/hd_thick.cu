@@ -22,6 +22,7 @@
 #include <cuda_runtime.h>
 
 #include "hd_geom.cuh"
+#include "hd_thick.cuh"
 
 namespace hd {
 namespace {
@@ -33,8 +34,8 @@ constexpr int kMaxK = 16;
 // (ny + 1) entries per (x, z) column.  One pair for N and one for M.
 struct ThickWs {
     int32_t *dx[2], *dy[2];
-    unsigned long long *intervals;  // row intervals emitted (two atomics each)
-    unsigned long long *next;       // next history to hand out
+    unsigned long long *stats;  // 8 counters (see thick_kernel)
+    unsigned long long *next;   // next history to hand out
 };
 
 struct ThickRing {
@@ -44,7 +45,8 @@ struct ThickRing {
 // Emits the interval of target row t from the window's first and last runs
 // (their ring slots pa and pb); returns 1 when t is inside the slice.
 __device__ __forceinline__ unsigned emit(const ThickRing &rg, int pa, int pb, int t, int k,
-                                         int nminor, int nmaj, int32_t *diff, int64_t slice_row0)
+                                         int nminor, int nmaj, int32_t *diff, int64_t slice_row0,
+                                         unsigned &voxels)
 {
     if (t < 0 || t >= nminor) return 0;
     const int lo = max(min(rg.lo[pa], rg.lo[pb]) - k, 0);
@@ -52,6 +54,7 @@ __device__ __forceinline__ unsigned emit(const ThickRing &rg, int pa, int pb, in
     int32_t *row = diff + (slice_row0 + t) * static_cast<int64_t>(nmaj + 1);
     atomicAdd(row + lo, 1);
     atomicAdd(row + hi + 1, -1);
+    voxels += static_cast<unsigned>(hi - lo + 1);
     return 1;
 }
 
@@ -64,13 +67,15 @@ __device__ __forceinline__ unsigned emit(const ThickRing &rg, int pa, int pb, in
 struct ThickLane {
     RunWalk wk;
     int32_t *diff;
+    int cls;  // 0 missed, 1 hit
     int nmaj, nminor, s;
     int zc, m0, j, p;
     int prev_row;
     int64_t row0;
 };
 
-__device__ __forceinline__ unsigned close_slice(const ThickLane &L, const ThickRing &rg, int k)
+__device__ __forceinline__ unsigned close_slice(const ThickLane &L, const ThickRing &rg, int k,
+                                                unsigned &voxels)
 {
     const int R = 2 * k + 1;
     const int pb = L.p == 0 ? R - 1 : L.p - 1;  // the slice's last run
@@ -78,10 +83,15 @@ __device__ __forceinline__ unsigned close_slice(const ThickLane &L, const ThickR
     for (int jc = L.j - k; jc <= L.j - 1 + k; ++jc) {
         const int ja = jc - k;
         const int pa = ja <= 0 ? 0 : (ja % R);
-        e += emit(rg, pa, pb, L.m0 + L.s * jc, k, L.nminor, L.nmaj, L.diff, L.row0);
+        e += emit(rg, pa, pb, L.m0 + L.s * jc, k, L.nminor, L.nmaj, L.diff, L.row0, voxels);
     }
     return e;
 }
+
+// Per-lane statistics: histories, missed, hit, neither, rejected.
+struct ThickCounts {
+    unsigned n_in = 0, n_miss = 0, n_hit = 0, n_none = 0, n_reject = 0;
+};
 
 // Starts history i on a lane: classification, geometry, walk set-up; false
 // when it has nothing to add.
@@ -89,22 +99,32 @@ __device__ __forceinline__ bool start_history(const Inputs &in, int64_t i, const
                                               const Cordic &cd, float tau_l, float tau_h,
                                               int use_miss, int use_hit, const ThickWs &ws,
                                               ThickLane &L, float &tc_ang, bool &tc_valid,
-                                              long long &tc_c, long long &tc_s)
+                                              long long &tc_c, long long &tc_s, ThickCounts &nc)
 {
     const float w = in.wepl[i];
     const int cls = w < tau_l ? 0 : (w > tau_h ? 1 : -1);
+    nc.n_in += 1;
+    nc.n_miss += cls == 0 ? 1 : 0;
+    nc.n_hit += cls == 1 ? 1 : 0;
+    nc.n_none += cls < 0 ? 1 : 0;
     if (cls < 0 || (cls == 0 && !use_miss) || (cls == 1 && !use_hit)) return false;
     const float ang = in.angle[i];
-    if (!(fabsf(ang) < 1048576.0f)) return false;
-    if (!tc_valid || ang != tc_ang) {
-        cordic_cs(q16_of(ang), cd, tc_c, tc_s);
-        tc_ang = ang;
-        tc_valid = true;
-    }
+    bool ok = fabsf(ang) < 1048576.0f;
     int32_t r[6];
-    if (!endpoints_cs(g, tc_c, tc_s, in.u_in[i], in.v_in[i], in.u_out[i], in.v_out[i], r))
+    if (ok) {
+        if (!tc_valid || ang != tc_ang) {
+            cordic_cs(q16_of(ang), cd, tc_c, tc_s);
+            tc_ang = ang;
+            tc_valid = true;
+        }
+        ok = endpoints_cs(g, tc_c, tc_s, in.u_in[i], in.v_in[i], in.u_out[i], in.v_out[i], r);
+    }
+    if (!ok) {
+        nc.n_reject += 1;
         return false;
+    }
     if (!run_begin(L.wk, r, r + 3, g.nx, g.ny, g.nz)) return false;
+    L.cls = cls;
     const bool ymaj = (L.wk.flags >> 5) & 1;
     L.s = (L.wk.flags & 2) ? 1 : -1;  // the in-plane minor axis' direction
     L.nmaj = ymaj ? g.ny : g.nx;
@@ -127,9 +147,11 @@ __global__ void __launch_bounds__(kThickThreads) thick_kernel(Inputs in, int64_t
                                                               Cordic cd, float tau_l, float tau_h,
                                                               int use_miss, int use_hit, int k,
                                                               ThickWs ws,
-                                                              unsigned long long *intervals)
+                                                              unsigned long long *stats)
 {
     const unsigned lane = threadIdx.x & 31u;
+    ThickCounts nc;
+    unsigned vox[2] = {0, 0};  // voxel memberships added, missed and hit
     long long tc_c = 0, tc_s = 0;
     float tc_ang = 0.0f;
     bool tc_valid = false;
@@ -151,7 +173,7 @@ __global__ void __launch_bounds__(kThickThreads) thick_kernel(Inputs in, int64_t
                 if (i < static_cast<unsigned long long>(n))
                     active = start_history(in, static_cast<int64_t>(i), g, cd, tau_l, tau_h,
                                            use_miss, use_hit, ws, L, tc_ang, tc_valid, tc_c,
-                                           tc_s);
+                                           tc_s, nc);
             }
             continue;
         }
@@ -160,7 +182,7 @@ __global__ void __launch_bounds__(kThickThreads) thick_kernel(Inputs in, int64_t
         for (int u = 0; u < kThickRunsPerStep; ++u) {
             int row, lo, hi;
             if (!run_next(L.wk, row, lo, hi)) {
-                if (L.zc >= 0) emitted += close_slice(L, rg, k);
+                if (L.zc >= 0) emitted += close_slice(L, rg, k, vox[L.cls]);
                 active = false;
                 break;
             }
@@ -171,7 +193,7 @@ __global__ void __launch_bounds__(kThickThreads) thick_kernel(Inputs in, int64_t
             if (L.zc < 0 || step > 1 || step < -1 || L.nminor <= 2) {
                 const int mz = row / L.nminor;
                 if (mz != L.zc) {
-                    if (L.zc >= 0) emitted += close_slice(L, rg, k);
+                    if (L.zc >= 0) emitted += close_slice(L, rg, k, vox[L.cls]);
                     L.zc = mz;
                     L.m0 = row - mz * L.nminor;
                     L.row0 = static_cast<int64_t>(mz) * L.nminor;
@@ -183,15 +205,22 @@ __global__ void __launch_bounds__(kThickThreads) thick_kernel(Inputs in, int64_t
             rg.hi[L.p] = hi;
             const int pa = L.j >= 2 * k ? (L.p + 1 == R ? 0 : L.p + 1) : 0;
             emitted += emit(rg, pa, L.p, L.m0 + L.s * (L.j - k), k, L.nminor, L.nmaj, L.diff,
-                            L.row0);
+                            L.row0, vox[L.cls]);
             ++L.j;
             L.p = L.p + 1 == R ? 0 : L.p + 1;
         }
     }
-    unsigned long long e = emitted;
+    // stats[0..6]: histories, missed, hit, neither, rejected, voxels of
+    // missed and of hit histories; stats[7]: row intervals
+    const unsigned long long part[8] = {nc.n_in, nc.n_miss, nc.n_hit, nc.n_none, nc.n_reject,
+                                        vox[0], vox[1], emitted};
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) e += __shfl_xor_sync(0xffffffffu, e, o);
-    if (lane == 0 && e != 0) atomicAdd(intervals, e);
+    for (int q = 0; q < 8; ++q) {
+        unsigned long long e = part[q];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) e += __shfl_xor_sync(0xffffffffu, e, o);
+        if (lane == 0 && e != 0) atomicAdd(stats + q, e);
+    }
 }
 
 __global__ void __launch_bounds__(kThickThreads) thick_rows_kernel(
@@ -225,13 +254,60 @@ size_t thick_layout(const hd_geometry *g, void *base, ThickWs *ws)
         ws->dx[1] = reinterpret_cast<int32_t *>(p + bx);
         ws->dy[0] = reinterpret_cast<int32_t *>(p + 2 * bx);
         ws->dy[1] = reinterpret_cast<int32_t *>(p + 2 * bx + by);
-        ws->intervals = reinterpret_cast<unsigned long long *>(p + 2 * bx + 2 * by);
-        ws->next = ws->intervals + 1;
+        ws->stats = reinterpret_cast<unsigned long long *>(p + 2 * bx + 2 * by);
+        ws->next = ws->stats + 8;
     }
     return 2 * bx + 2 * by + 256;
 }
 
+__global__ void thick_stats_kernel(const unsigned long long *from, unsigned long long *to,
+                                   int64_t *intervals)
+{
+    if (threadIdx.x < 7 && to != nullptr && from[threadIdx.x] != 0)
+        atomicAdd(to + threadIdx.x, from[threadIdx.x]);
+    if (threadIdx.x == 7 && intervals != nullptr)
+        *intervals = static_cast<int64_t>(from[7]);
+}
+
 }  // namespace
+
+size_t thick_workspace_bytes(const hd_geometry *geom) { return thick_layout(geom, nullptr, nullptr); }
+
+cudaError_t launch_thick(const Inputs &in, int64_t n, const hd_geometry *geom, const GeomQ &g,
+                         const Cordic &cd, float tau_l, float tau_h, int use_miss, int use_hit,
+                         int k, void *workspace, uint32_t *N, uint32_t *M,
+                         unsigned long long *stats, int64_t *intervals, int sm_count,
+                         cudaStream_t st)
+{
+    ThickWs ws{};
+    const size_t need = thick_layout(geom, workspace, &ws);
+    cudaError_t e = cudaMemsetAsync(workspace, 0, need, st);
+    if (e == cudaSuccess && n > 0) {
+        int64_t blocks = (n + kThickThreads - 1) / kThickThreads;
+        const int64_t cap = int64_t(sm_count > 0 ? sm_count : 1) * 4;
+        if (blocks > cap) blocks = cap;  // resident, persistent
+        thick_kernel<<<static_cast<unsigned>(blocks), kThickThreads, 0, st>>>(
+            in, n, g, cd, tau_l, tau_h, use_miss, use_hit, k, ws, ws.stats);
+        e = cudaGetLastError();
+    }
+    const int64_t plane = int64_t(geom->nx) * geom->ny;
+    for (int c = 0; c < 2 && e == cudaSuccess && n > 0; ++c) {
+        uint32_t *out = c == 0 ? (use_miss ? N : nullptr) : (use_hit ? M : nullptr);
+        if (!out) continue;
+        const int64_t rx = int64_t(geom->ny) * geom->nz, ry = int64_t(geom->nx) * geom->nz;
+        thick_rows_kernel<<<static_cast<unsigned>((rx + 255) / 256), 256, 0, st>>>(
+            ws.dx[c], rx, geom->nx, 1, geom->ny, plane, 0, out);
+        thick_rows_kernel<<<static_cast<unsigned>((ry + 255) / 256), 256, 0, st>>>(
+            ws.dy[c], ry, geom->ny, geom->nx, geom->nx, plane, 1, out);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess && (stats || intervals)) {
+        thick_stats_kernel<<<1, 32, 0, st>>>(ws.stats, stats, intervals);
+        e = cudaGetLastError();
+    }
+    return e;
+}
+
 }  // namespace hd
 
 extern "C" {
@@ -241,7 +317,7 @@ hd_status hd_accumulate_thick_workspace(const hd_geometry *geom, size_t *bytes)
     if (!geom || !bytes) return HD_ERR_ARG;
     const hd_status s = hd::check_geometry(geom);
     if (s != HD_OK) return s;
-    *bytes = hd::thick_layout(geom, nullptr, nullptr);
+    *bytes = hd::thick_workspace_bytes(geom);
     return HD_OK;
 }
 
@@ -264,8 +340,8 @@ hd_status hd_accumulate_thick(const hd_geometry *geom, const hd_params *params, 
     const int use_hit = (m & HD_SM) ? 1 : 0;
     if ((use_miss && !N) || (use_hit && !M)) return HD_ERR_ARG;
     if (n > 0 && (!angle_deg || !u_in || !v_in || !u_out || !v_out || !wepl)) return HD_ERR_ARG;
-    const size_t need = hd::thick_layout(geom, nullptr, nullptr);
-    if (workspace_bytes < need || (reinterpret_cast<uintptr_t>(workspace) & 255) != 0)
+    if (workspace_bytes < hd::thick_workspace_bytes(geom) ||
+        (reinterpret_cast<uintptr_t>(workspace) & 255) != 0)
         return HD_ERR_ARG;
     hd::Cordic cd{};
     if (!hd::make_cordic_table(cd)) return HD_ERR_RANGE;
@@ -275,34 +351,13 @@ hd_status hd_accumulate_thick(const hd_geometry *geom, const hd_params *params, 
         cudaGetLastError();
         return HD_ERR_CUDA;
     }
-    hd::ThickWs ws{};
-    hd::thick_layout(geom, workspace, &ws);
     const hd::GeomQ gq = hd::make_geomq(geom->nx, geom->ny, geom->nz, geom->sx, geom->sy,
                                         geom->sz, geom->tracker_half_sep_mm);
-    cudaStream_t st = static_cast<cudaStream_t>(stream);
-    cudaError_t e = cudaMemsetAsync(workspace, 0, need, st);
-    if (e == cudaSuccess && n > 0) {
-        int64_t blocks = (n + hd::kThickThreads - 1) / hd::kThickThreads;
-        if (blocks > int64_t(sms) * 4) blocks = int64_t(sms) * 4;  // resident, persistent
-        const hd::Inputs in{angle_deg, u_in, v_in, u_out, v_out, wepl};
-        hd::thick_kernel<<<static_cast<unsigned>(blocks), hd::kThickThreads, 0, st>>>(
-            in, n, gq, cd, params->wepl_miss_lt, params->wepl_hit_gt, use_miss, use_hit, k, ws,
-            ws.intervals);
-        e = cudaGetLastError();
-    }
-    const int64_t plane = int64_t(geom->nx) * geom->ny;
-    for (int c = 0; c < 2 && e == cudaSuccess && n > 0; ++c) {
-        uint32_t *out = c == 0 ? (use_miss ? N : nullptr) : (use_hit ? M : nullptr);
-        if (!out) continue;
-        const int64_t rx = int64_t(geom->ny) * geom->nz, ry = int64_t(geom->nx) * geom->nz;
-        hd::thick_rows_kernel<<<static_cast<unsigned>((rx + 255) / 256), 256, 0, st>>>(
-            ws.dx[c], rx, geom->nx, 1, geom->ny, plane, 0, out);
-        hd::thick_rows_kernel<<<static_cast<unsigned>((ry + 255) / 256), 256, 0, st>>>(
-            ws.dy[c], ry, geom->ny, geom->nx, geom->nx, plane, 1, out);
-        e = cudaGetLastError();
-    }
-    if (e == cudaSuccess && intervals)
-        e = cudaMemcpyAsync(intervals, ws.intervals, sizeof(int64_t), cudaMemcpyDeviceToDevice, st);
+    const hd::Inputs in{angle_deg, u_in, v_in, u_out, v_out, wepl};
+    const cudaError_t e = hd::launch_thick(in, n, geom, gq, cd, params->wepl_miss_lt,
+                                           params->wepl_hit_gt, use_miss, use_hit, k, workspace, N,
+                                           M, nullptr, intervals, sms,
+                                           static_cast<cudaStream_t>(stream));
     if (e != cudaSuccess) {
         hd::note_cuda_error(e, "hd_accumulate_thick");
         return HD_ERR_CUDA;

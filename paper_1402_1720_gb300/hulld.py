@@ -164,6 +164,7 @@ _SIGS = {
     "hd_accumulate_noalloc": ([ctypes.POINTER(hd_geometry), ctypes.POINTER(hd_params)] +
                               [_VP] * 6 + [_I64, _VP, _VP, _VP], ctypes.c_int),
     "hd_scan_set_profiling": ([_VP, _I32], ctypes.c_int),
+    "hd_scan_set_thick": ([_VP, _I32], ctypes.c_int),
     "hd_scan_set_tuning": ([_VP, ctypes.POINTER(hd_tuning)], ctypes.c_int),
     "hd_scan_get_tuning": ([_VP, ctypes.POINTER(hd_tuning)], ctypes.c_int),
     "hd_batch_create": ([_I32, ctypes.POINTER(_VP)], ctypes.c_int),
@@ -436,6 +437,10 @@ def hd_scan_get_tuning(scan: int) -> dict:
     t = hd_tuning()
     _check(load().hd_scan_get_tuning(scan, ctypes.byref(t)), "hd_scan_get_tuning")
     return t.as_dict()
+
+
+def hd_scan_set_thick(scan: int, k: int) -> None:
+    _check(load().hd_scan_set_thick(scan, int(k)), "hd_scan_set_thick")
 
 
 def hd_scan_set_profiling(scan: int, enable: bool) -> None:
@@ -750,6 +755,10 @@ class Scan:
 
     def reserve(self, n: int, stream=None):
         hd_scan_reserve(self.handle, n, stream)
+
+    def set_thick(self, k: int):
+        """Thick rays: A_i dilated by k voxels in-plane (before any add)."""
+        hd_scan_set_thick(self.handle, k)
 
     def system_rows(self, method: int, hist_arrays: Sequence, stream=None):
         """(row_ptr, cols) device tensors of the hull-restricted system

@@ -65,3 +65,64 @@ def test_k_range(hd):
     with pytest.raises(hd.HDError) as e:
         _gpu(hd, g, h, 17)
     assert e.value.status == hd.HD_ERR_RANGE
+
+
+def _scan_thick(hd, g, h, k, params=None):
+    s = hd.Scan(g, params)
+    s.set_thick(k)
+    s.add([torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in h.arrays()])
+    s.finalize()
+    torch.cuda.synchronize()
+    return s
+
+
+@pytest.mark.parametrize("k", [1, 3])
+def test_scan_with_thick_rays(hd, oracle_mod, k):
+    """All three methods on thick sets: counts, hulls, thresholds and
+    statistics equal the oracle's run on A_i(k)."""
+    w = synth.make_config(1, fraction=0.5)
+    g, h = w.geometry, w.histories
+    s = _scan_thick(hd, g, h, k)
+    ref = oracle_mod.run_thick(g, h, k)
+    assert np.array_equal(s.counts(hd.HD_MSC), ref["N"])
+    assert np.array_equal(s.counts(hd.HD_SM), ref["M"])
+    for m, key in ((hd.HD_SC, "H1"), (hd.HD_MSC, "H2"), (hd.HD_SM, "H3")):
+        assert np.array_equal(s.mask(m), ref[key]), key
+    mt, slope, index = s.thresholds()
+    assert np.array_equal(np.asarray(mt), ref["Mt"])
+    st = s.stats()
+    r = ref["stats"]
+    assert (st["n_in"], st["n_miss"], st["n_hit"], st["n_none"], st["n_reject"]) == \
+        tuple(int(x) for x in r[:5])
+    assert (st["steps_miss"], st["steps_hit"]) == (int(r[5]), int(r[6]))
+    s.close()
+
+
+def test_scan_thick_sc_only_chunks_and_states(hd, oracle_mod):
+    """SC alone counts N for its thick sets; chunks add up; k is fixed once
+    histories have arrived; thick scans stay out of batches."""
+    w = synth.make_config(1, fraction=0.3)
+    g, h = w.geometry, w.histories
+    params = oracle_mod.Params(methods=oracle_mod.SC)
+    s = hd.Scan(g, params)
+    s.set_thick(2)
+    dev = [torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in h.arrays()]
+    n = len(h)
+    s.add([a[: n // 3] for a in dev])
+    with pytest.raises(hd.HDError) as e:
+        s.set_thick(1)
+    assert e.value.status == hd.HD_ERR_STATE
+    s.add([a[n // 3:] for a in dev])
+    s.finalize()
+    torch.cuda.synchronize()
+    ref = oracle_mod.run_thick(g, h, 2, params)
+    assert np.array_equal(s.mask(hd.HD_SC), ref["H1"])
+    b = hd.hd_batch_create(4)
+    with pytest.raises(hd.HDError) as e:
+        hd.hd_batch_add(b, s.handle, *dev)
+    assert e.value.status == hd.HD_ERR_STATE
+    hd.hd_batch_destroy(b)
+    s.close()
+    with pytest.raises(hd.HDError) as e:
+        hd.Scan(g).set_thick(17)
+    assert e.value.status == hd.HD_ERR_RANGE
