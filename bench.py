@@ -680,6 +680,30 @@ def run_thick(args):
     atomics = 2 * int(counter.item())
     peaks = _peaks()
     l2_rate = hulld.hd_probe_atomics(hulld.HD_PROBE_L2_RANDOM)
+    # the whole method on thick sets: a scan set to thick rays (SC, MSC, SM,
+    # the tiled thick traversal on this grid), reset, add and finalize per step
+    scan = hulld.Scan(g)
+    scan.set_thick(k)
+
+    def scan_step():
+        hulld.hd_scan_reset(scan.handle, stream)
+        hulld.hd_scan_add_histories(scan.handle, *dev, stream=stream)
+        hulld.hd_scan_finalize(scan.handle, stream)
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            scan_step()
+        torch.cuda.synchronize()
+        f0 = torch.cuda.Event(enable_timing=True)
+        f1 = torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        for _ in range(args.steps):
+            scan_step()
+        f1.record(stream)
+        torch.cuda.synchronize()
+    ms_scan = f0.elapsed_time(f1) / args.steps
+    scan_stats = scan.stats()
+    scan.close()
     line = {"metric": f"histories/s (thick rays, k = {k} voxels in-plane, missed and hit counts)",
             "value": n / (ms * 1e-3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
@@ -687,6 +711,11 @@ def run_thick(args):
             "config": {"workload": WORKLOAD + f"; thick rays k = {k}", "histories": n,
                        "fraction": args.fraction},
             "thick_voxels_per_step": voxels, "thick_voxels_per_s": voxels / (ms * 1e-3),
+            "scan": {"what": "SC+MSC+SM scan on the thick sets (hd_scan_set_thick), reset + add "
+                             "+ finalize per step",
+                     "ms_per_step": ms_scan, "histories_per_s": n / (ms_scan * 1e-3),
+                     "thick_voxels_per_s": (scan_stats["steps_miss"] + scan_stats["steps_hit"])
+                     / (ms_scan * 1e-3)},
             "roofline": {"bound": "l2_atomic", "kernel": "thick_kernel",
                          "achieved": atomics / (ms * 1e-3), "peak": l2_rate,
                          "unit": "atomics/s", "frac": atomics / (ms * 1e-3) / l2_rate,

@@ -482,7 +482,22 @@ int finalize_launches(const hd_scan *scan) { return (scan->params.methods & HD_S
 // One chunk through the whole path on st.
 hd_status run_chunk(hd_scan *s, const hd::Inputs &in, int64_t n, cudaStream_t st)
 {
-    if (s->thick_k > 0) {  // thick rays: their own walk, same counts
+    if (s->thick_k > 0) {
+        const hd::TilePlan &tp = s->tp;
+        if (tp.ntiles > 0 && tp.ntx == 1 && tp.nty == 1 && tp.tz == 1) {
+            // thick rays on the tiled path: the same records and pairs,
+            // dilated in the traversal
+            hd_status r = upload_desc(s, st);
+            if (r != HD_OK) return r;
+            r = stage_prepare(s, in, n, st);
+            if (r != HD_OK) return r;
+            HD_CUDA(hd::launch_thick_scan(s->desc_dev, &s->geom, records_of(s, n), s->ctrl, n,
+                                          s->gq, s->thick_k, s->thick_ws, s->N, s->M,
+                                          tp.tile_words, tp.threads, s->sm_count, st));
+            s->launches += 4;
+            return HD_OK;
+        }
+        // other plans: a lane per history over the whole grid
         const uint32_t m = s->params.methods;
         HD_CUDA(hd::launch_thick(in, n, &s->geom, s->gq, s->cordic, s->params.wepl_miss_lt,
                                  s->params.wepl_hit_gt, (m & (HD_SC | HD_MSC)) ? 1 : 0,

@@ -28,7 +28,7 @@ namespace hd {
 namespace {
 
 constexpr int kThickThreads = 256;
-constexpr int kMaxK = 16;
+constexpr int kMaxK = kThickMaxK;
 
 // Difference arrays: along x, (nx + 1) entries per (y, z) row; along y,
 // (ny + 1) entries per (x, z) column.  One pair for N and one for M.
@@ -37,26 +37,6 @@ struct ThickWs {
     unsigned long long *stats;  // 8 counters (see thick_kernel)
     unsigned long long *next;   // next history to hand out
 };
-
-struct ThickRing {
-    int lo[2 * kMaxK + 1], hi[2 * kMaxK + 1];
-};
-
-// Emits the interval of target row t from the window's first and last runs
-// (their ring slots pa and pb); returns 1 when t is inside the slice.
-__device__ __forceinline__ unsigned emit(const ThickRing &rg, int pa, int pb, int t, int k,
-                                         int nminor, int nmaj, int32_t *diff, int64_t slice_row0,
-                                         unsigned &voxels)
-{
-    if (t < 0 || t >= nminor) return 0;
-    const int lo = max(min(rg.lo[pa], rg.lo[pb]) - k, 0);
-    const int hi = min(max(rg.hi[pa], rg.hi[pb]) + k, nmaj - 1);
-    int32_t *row = diff + (slice_row0 + t) * static_cast<int64_t>(nmaj + 1);
-    atomicAdd(row + lo, 1);
-    atomicAdd(row + hi + 1, -1);
-    voxels += static_cast<unsigned>(hi - lo + 1);
-    return 1;
-}
 
 // One lane's walk: the run walk and the state of its current slice.
 // Targets of a slice of J runs are centred on runs -k .. J - 1 + k (target
@@ -83,7 +63,8 @@ __device__ __forceinline__ unsigned close_slice(const ThickLane &L, const ThickR
     for (int jc = L.j - k; jc <= L.j - 1 + k; ++jc) {
         const int ja = jc - k;
         const int pa = ja <= 0 ? 0 : (ja % R);
-        e += emit(rg, pa, pb, L.m0 + L.s * jc, k, L.nminor, L.nmaj, L.diff, L.row0, voxels);
+        e += thick_emit_global(rg, pa, pb, L.m0 + L.s * jc, k, L.nminor, L.nmaj, L.diff, L.row0,
+                               voxels);
     }
     return e;
 }
@@ -204,8 +185,8 @@ __global__ void __launch_bounds__(kThickThreads) thick_kernel(Inputs in, int64_t
             rg.lo[L.p] = lo;
             rg.hi[L.p] = hi;
             const int pa = L.j >= 2 * k ? (L.p + 1 == R ? 0 : L.p + 1) : 0;
-            emitted += emit(rg, pa, L.p, L.m0 + L.s * (L.j - k), k, L.nminor, L.nmaj, L.diff,
-                            L.row0, vox[L.cls]);
+            emitted += thick_emit_global(rg, pa, L.p, L.m0 + L.s * (L.j - k), k, L.nminor,
+                                         L.nmaj, L.diff, L.row0, vox[L.cls]);
             ++L.j;
             L.p = L.p + 1 == R ? 0 : L.p + 1;
         }
@@ -220,6 +201,42 @@ __global__ void __launch_bounds__(kThickThreads) thick_kernel(Inputs in, int64_t
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) e += __shfl_xor_sync(0xffffffffu, e, o);
         if (lane == 0 && e != 0) atomicAdd(stats + q, e);
+    }
+}
+
+// The records of a chunk that take the global path (status 2: too many
+// tiles, or beyond the pair budget): each walked whole over the grid into the
+// global difference arrays; voxel memberships added to the scan's counters.
+__global__ void __launch_bounds__(kThickThreads) thick_records_kernel(Records rec, Ctrl *ctrl,
+                                                                      GeomQ g, int k,
+                                                                      ThickDiff td)
+{
+    const unsigned nm = ctrl->rec_miss, nh = ctrl->rec_hit;
+    const int64_t total = static_cast<int64_t>(nm) + nh;
+    const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+    ThickRing rg;
+    unsigned vox[2] = {0, 0};
+    for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < total;
+         i += stride) {
+        const bool miss = i < nm;
+        const int64_t slot = miss ? i : rec.cap - 1 - (i - nm);
+        if (rec.status[slot] != 2) continue;
+        const int32_t gi[3] = {rec.g[0][slot], rec.g[1][slot], rec.g[2][slot]};
+        const int32_t go[3] = {rec.g[3][slot], rec.g[4][slot], rec.g[5][slot]};
+        RunWalk wk;
+        if (!run_begin(wk, gi, go, g.nx, g.ny, g.nz)) continue;
+        const bool ymaj = (wk.flags >> 5) & 1;
+        const int cls = miss ? 0 : 1;
+        thick_walk_all(wk, ymaj ? g.nx : g.ny, ymaj ? g.ny : g.nx, 0, k, (wk.flags & 2) ? 1 : -1,
+                       ymaj ? td.dy[cls] : td.dx[cls], rg, vox[cls]);
+    }
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+        unsigned long long e = vox[c];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) e += __shfl_xor_sync(0xffffffffu, e, o);
+        if ((threadIdx.x & 31) == 0 && e != 0)
+            atomicAdd(c == 0 ? &ctrl->steps_miss : &ctrl->steps_hit, e);
     }
 }
 
@@ -305,6 +322,59 @@ cudaError_t launch_thick(const Inputs &in, int64_t n, const hd_geometry *geom, c
         thick_stats_kernel<<<1, 32, 0, st>>>(ws.stats, stats, intervals);
         e = cudaGetLastError();
     }
+    return e;
+}
+
+ThickDiff thick_diff_of(const hd_geometry *geom, void *workspace)
+{
+    ThickWs ws{};
+    thick_layout(geom, workspace, &ws);
+    ThickDiff td{};
+    for (int c = 0; c < 2; ++c) {
+        td.dx[c] = ws.dx[c];
+        td.dy[c] = ws.dy[c];
+    }
+    return td;
+}
+
+// Adds the global difference arrays to N and M (row prefix sums).
+static cudaError_t launch_thick_rows(const hd_geometry *geom, const ThickWs &ws, uint32_t *N,
+                                     uint32_t *M, cudaStream_t st)
+{
+    const int64_t plane = int64_t(geom->nx) * geom->ny;
+    for (int c = 0; c < 2; ++c) {
+        uint32_t *out = c == 0 ? N : M;
+        if (!out) continue;
+        const int64_t rx = int64_t(geom->ny) * geom->nz, ry = int64_t(geom->nx) * geom->nz;
+        thick_rows_kernel<<<static_cast<unsigned>((rx + 255) / 256), 256, 0, st>>>(
+            ws.dx[c], rx, geom->nx, 1, geom->ny, plane, 0, out);
+        thick_rows_kernel<<<static_cast<unsigned>((ry + 255) / 256), 256, 0, st>>>(
+            ws.dy[c], ry, geom->ny, geom->nx, geom->nx, plane, 1, out);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_thick_scan(const ScanDesc *desc_dev, const hd_geometry *geom,
+                              const Records &rec, Ctrl *ctrl, int64_t upper, const GeomQ &g,
+                              int k, void *workspace, uint32_t *N, uint32_t *M, int smem_words,
+                              int threads, int sm_count, cudaStream_t st)
+{
+    ThickWs ws{};
+    const size_t need = thick_layout(geom, workspace, &ws);
+    const ThickDiff td = thick_diff_of(geom, workspace);
+    cudaError_t e = cudaMemsetAsync(workspace, 0, need, st);
+    if (e == cudaSuccess)
+        e = launch_trace_thick(desc_dev, &ctrl->job_next, k, td, smem_words, threads,
+                               sm_count > 0 ? sm_count : 1, st);
+    if (e == cudaSuccess && upper > 0) {
+        int64_t blocks = (upper + kThickThreads - 1) / kThickThreads;
+        const int64_t cap = int64_t(sm_count > 0 ? sm_count : 1) * 8;
+        if (blocks > cap) blocks = cap;
+        thick_records_kernel<<<static_cast<unsigned>(blocks), kThickThreads, 0, st>>>(rec, ctrl, g,
+                                                                                      k, td);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = launch_thick_rows(geom, ws, N, M, st);
     return e;
 }
 

@@ -126,3 +126,37 @@ def test_scan_thick_sc_only_chunks_and_states(hd, oracle_mod):
     with pytest.raises(hd.HDError) as e:
         hd.Scan(g).set_thick(17)
     assert e.value.status == hd.HD_ERR_RANGE
+
+
+@pytest.mark.parametrize("case", ["strips", "deep_slabs", "head_sample"])
+def test_scan_thick_plans(hd, oracle_mod, case):
+    """Whole-plane one-slice tiles take the tiled thick traversal; other
+    plans (x-y strips, slabs two slices deep) the lane walk over the grid;
+    both equal the oracle."""
+    if case == "strips":
+        g = synth.Geometry(256, 256, 4, 1.0, 1.0, 2.5, 200.0)
+        h = synth.make_histories(np.random.default_rng(21), g, synth.head_phantom(0.9),
+                                 np.arange(0, 360, 30), 400, 150.0, 5.0, 2.0, 0.01, 0.3)
+    elif case == "deep_slabs":
+        w = synth.make_config(1, fraction=0.2)
+        g, h = w.geometry, w.histories
+    else:
+        w = synth.make_config(2, fraction=0.02)
+        g, h = w.geometry, w.histories
+    s = hd.Scan(g)
+    if case == "deep_slabs":
+        t = hd.hd_scan_get_tuning(s.handle)
+        tun = hd.hd_tuning(t["threads"], t["refill"], t["job_size"], 2)
+        hd.hd_scan_set_tuning(s.handle, tun)
+    s.set_thick(2)
+    s.add([torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in h.arrays()])
+    s.finalize()
+    torch.cuda.synchronize()
+    ref = oracle_mod.run_thick(g, h, 2)
+    assert np.array_equal(s.counts(hd.HD_MSC), ref["N"])
+    assert np.array_equal(s.counts(hd.HD_SM), ref["M"])
+    for m, key in ((hd.HD_SC, "H1"), (hd.HD_MSC, "H2"), (hd.HD_SM, "H3")):
+        assert np.array_equal(s.mask(m), ref[key]), key
+    st = s.stats()
+    assert (st["steps_miss"], st["steps_hit"]) == (int(ref["stats"][5]), int(ref["stats"][6]))
+    s.close()
