@@ -84,7 +84,8 @@ __device__ __forceinline__ unsigned thick_walk_job(uint32_t *tile, int arr_words
     ThickRing rg;
     bool active = false;
     int nmaj = 0, nminor = 0, aoff = 0;
-    int r0 = 0, s = 1, j = 0, p = 0;  // first row and direction of the walk, runs, ring slot
+    int r0 = 0, s = 1, j = 0, p = 0;  // first row and direction of the walk, step, ring slot
+    int jlast = -1, pb_last = 0;      // runs of the walk once they are all walked, last slot
     unsigned vox = 0, ends = 0;
     uint4 na = make_uint4(0, 0, 0, 0), nb = na;
     int nidx = -1;
@@ -114,6 +115,7 @@ __device__ __forceinline__ unsigned thick_walk_job(uint32_t *tile, int arr_words
                 s = c.rstep;
                 j = 0;
                 p = 0;
+                jlast = -1;
                 nidx = -1;
             }
             unsigned base = 0;
@@ -130,25 +132,29 @@ __device__ __forceinline__ unsigned thick_walk_job(uint32_t *tile, int arr_words
             continue;
         }
         if (active) {
+            // Step j emits the target centred on run j - k (row r0 + s (j - k)),
+            // whose window is runs max(0, j - 2k) .. min(j, J - 1): steps
+            // 0 .. J - 1 walk the J runs, steps J .. J - 1 + 2k only emit, so
+            // every step of every lane costs the same and lanes stay together.
 #pragma unroll 1
             for (int u = 0; u < kThickRunsPerStep; ++u) {
-                int rb, lo, hi;
-                const bool more = lean_run(c, rb, lo, hi, ends);
-                rg.lo[p] = lo;
-                rg.hi[p] = hi;
-                // the target centred on run j - k (row rb - s k) is complete
-                vox += emit_tile(rg, j >= 2 * k ? (p + 1 == R ? 0 : p + 1) : 0, p, rb - s * k, k,
-                                 nminor, nmaj, tile, aoff, scratch);
+                int pb = pb_last;
+                if (jlast < 0) {
+                    int rb, lo, hi;
+                    const bool more = lean_run(c, rb, lo, hi, ends);
+                    rg.lo[p] = lo;
+                    rg.hi[p] = hi;
+                    pb = p;
+                    if (!more) {
+                        jlast = j + 1;
+                        pb_last = p;
+                    }
+                }
+                vox += emit_tile(rg, j >= 2 * k ? (p + 1 == R ? 0 : p + 1) : 0, pb,
+                                 r0 + s * (j - k), k, nminor, nmaj, tile, aoff, scratch);
                 ++j;
                 p = p + 1 == R ? 0 : p + 1;
-                if (!more) {
-                    // the last k targets: centres j - k .. j - 1 + k
-                    const int pb = p == 0 ? R - 1 : p - 1;
-                    for (int jc = j - k; jc <= j - 1 + k; ++jc) {
-                        const int ja = jc - k;
-                        vox += emit_tile(rg, ja <= 0 ? 0 : ja % R, pb, r0 + s * jc, k, nminor,
-                                         nmaj, tile, aoff, scratch);
-                    }
+                if (jlast >= 0 && j >= jlast + 2 * k) {
                     active = false;
                     break;
                 }
