@@ -694,6 +694,8 @@ def run_thick(args):
         for _ in range(args.warmup):
             scan_step()
         torch.cuda.synchronize()
+        sampler = ClockSampler(local)
+        sampler.start()
         f0 = torch.cuda.Event(enable_timing=True)
         f1 = torch.cuda.Event(enable_timing=True)
         f0.record(stream)
@@ -701,28 +703,34 @@ def run_thick(args):
             scan_step()
         f1.record(stream)
         torch.cuda.synchronize()
+        clocks_scan = sampler.stop()
     ms_scan = f0.elapsed_time(f1) / args.steps
     scan_stats = scan.stats()
     scan.close()
-    line = {"metric": f"histories/s (thick rays, k = {k} voxels in-plane, missed and hit counts)",
-            "value": n / (ms * 1e-3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+    line = {"metric": f"histories/s (SC+MSC+SM on thick rays, k = {k} voxels in-plane)",
+            "value": n / (ms_scan * 1e-3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_scan, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
             "config": {"workload": WORKLOAD + f"; thick rays k = {k}", "histories": n,
-                       "fraction": args.fraction},
-            "thick_voxels_per_step": voxels, "thick_voxels_per_s": voxels / (ms * 1e-3),
-            "scan": {"what": "SC+MSC+SM scan on the thick sets (hd_scan_set_thick), reset + add "
-                             "+ finalize per step",
-                     "ms_per_step": ms_scan, "histories_per_s": n / (ms_scan * 1e-3),
-                     "thick_voxels_per_s": (scan_stats["steps_miss"] + scan_stats["steps_hit"])
-                     / (ms_scan * 1e-3)},
-            "roofline": {"bound": "l2_atomic", "kernel": "thick_kernel",
-                         "achieved": atomics / (ms * 1e-3), "peak": l2_rate,
-                         "unit": "atomics/s", "frac": atomics / (ms * 1e-3) / l2_rate,
-                         "atomics_per_step": atomics,
-                         "peak_source": "hd_probe_atomics L2 random (measured in this run)",
-                         "hbm_peak_gbs": peaks["hbm_gbs"]},
-            "gpu_launches": 3 * args.steps, "clocks": clocks}
+                       "fraction": args.fraction,
+                       "step": "a scan set to thick rays (hd_scan_set_thick): reset, add, "
+                               "finalize; the tiled thick traversal on this grid"},
+            "thick_voxels_per_s": (scan_stats["steps_miss"] + scan_stats["steps_hit"])
+            / (ms_scan * 1e-3),
+            "standalone": {"what": "hd_accumulate_thick (counts only; a lane per history "
+                                   "over the whole grid)",
+                           "ms_per_step": ms, "histories_per_s": n / (ms * 1e-3),
+                           "thick_voxels_per_s": voxels / (ms * 1e-3),
+                           "roofline": {"bound": "l2_atomic", "kernel": "thick_kernel",
+                                        "achieved": atomics / (ms * 1e-3), "peak": l2_rate,
+                                        "unit": "atomics/s",
+                                        "frac": atomics / (ms * 1e-3) / l2_rate,
+                                        "atomics_per_step": atomics,
+                                        "peak_source": "hd_probe_atomics L2 random "
+                                                       "(measured in this run)",
+                                        "hbm_peak_gbs": peaks["hbm_gbs"]}},
+            "gpu_launches": 12 * args.steps, "clocks": clocks_scan,
+            "clocks_standalone": clocks}
     if not args.no_cpu_baseline:
         import oracle
         import time as _time
