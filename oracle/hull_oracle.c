@@ -433,6 +433,68 @@ int oracle_accumulate_thick(const og_geom *g, float tau_l, float tau_h, int32_t 
     return 0;
 }
 
+/* Does the closed segment gin -> gout (grid Q16) meet the half-open box
+ * [lo, hi) (voxel units)?  The slab test of oracle_segment_meets_voxel on a
+ * box: a voxel v is in A_i(k) exactly when the segment meets the box of
+ * voxels within k of v in-plane, clipped to the grid. */
+int oracle_segment_meets_box(const int64_t *gin, const int64_t *gout, const int64_t *lo,
+                             const int64_t *hi)
+{
+    i128 lo_p = 0, lo_q = 1, hi_p = 1, hi_q = 1;
+    int lo_open = 0, hi_open = 0;
+    for (int a = 0; a < 3; ++a) {
+        const int64_t d = gout[a] - gin[a];
+        const int64_t lo_plane = lo[a] * Q16, hi_plane = hi[a] * Q16;
+        if (d == 0) {
+            if (!(gin[a] >= lo_plane && gin[a] < hi_plane)) return 0;
+            continue;
+        }
+        i128 lp, lq, hp, hq;
+        int l_open, h_open;
+        if (d > 0) {
+            lp = lo_plane - gin[a]; lq = d; l_open = 0;
+            hp = hi_plane - gin[a]; hq = d; h_open = 1;
+        } else {
+            lp = gin[a] - hi_plane; lq = -d; l_open = 1;
+            hp = gin[a] - lo_plane; hq = -d; h_open = 0;
+        }
+        i128 c = lp * lo_q - lo_p * lq;
+        if (c > 0 || (c == 0 && l_open)) { lo_p = lp; lo_q = lq; lo_open = l_open || (c == 0 && lo_open); }
+        c = hp * hi_q - hi_p * hq;
+        if (c < 0 || (c == 0 && h_open)) { hi_p = hp; hi_q = hq; hi_open = h_open || (c == 0 && hi_open); }
+    }
+    const i128 c = lo_p * hi_q - hi_p * lo_q;
+    if (c < 0) return 1;
+    if (c == 0 && !lo_open && !hi_open) return 1;
+    return 0;
+}
+
+/* Thick-ray counts of chosen voxels by testing every history: counts[b]
+ * (zeroed by the caller) = histories of class cls (1 missed, 2 hit) whose
+ * thick set A_i(k) holds voxel vox[b] (linear index), for nb voxels. */
+void oracle_count_thick_voxels(const og_geom *g, float tau_l, float tau_h, const int64_t *theta,
+                               int64_t K, int32_t k, const float *angle, const float *u_in,
+                               const float *v_in, const float *u_out, const float *v_out,
+                               const float *wepl, int64_t n, int32_t cls, const int64_t *vox,
+                               int64_t nb, int64_t *counts)
+{
+    for (int64_t i = 0; i < n; ++i) {
+        if (oracle_classify(wepl[i], tau_l, tau_h) != cls) continue;
+        int64_t gin[3], gout[3];
+        if (oracle_grid_endpoints(g, theta, K, angle[i], u_in[i], v_in[i], u_out[i], v_out[i],
+                                  gin, gout))
+            continue;
+        for (int64_t b = 0; b < nb; ++b) {
+            const int64_t x = vox[b] % g->nx, y = (vox[b] / g->nx) % g->ny;
+            const int64_t z = vox[b] / ((int64_t)g->nx * g->ny);
+            const int64_t lo[3] = {x - k < 0 ? 0 : x - k, y - k < 0 ? 0 : y - k, z};
+            const int64_t hi[3] = {x + k + 1 > g->nx ? g->nx : x + k + 1,
+                                   y + k + 1 > g->ny ? g->ny : y + k + 1, z + 1};
+            counts[b] += oracle_segment_meets_box(gin, gout, lo, hi);
+        }
+    }
+}
+
 /* ------------------------------- hull diagnostics (next row f3) */
 
 /* Extra and missing voxels of a hull against the true object (the counts of

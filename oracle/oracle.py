@@ -96,6 +96,13 @@ def lib():
                                                   ctypes.c_int32] + [f32p] * 6 + \
                 [ctypes.c_int64, u32p, u32p, i64p]
             L.oracle_accumulate_thick.restype = ctypes.c_int
+            L.oracle_segment_meets_box.argtypes = [i64p, i64p, i64p, i64p]
+            L.oracle_segment_meets_box.restype = ctypes.c_int
+            L.oracle_count_thick_voxels.argtypes = [ctypes.c_void_p, ctypes.c_float,
+                                                    ctypes.c_float, i64p, ctypes.c_int64,
+                                                    ctypes.c_int32] + [f32p] * 6 + \
+                [ctypes.c_int64, ctypes.c_int32, i64p, ctypes.c_int64, i64p]
+            L.oracle_count_thick_voxels.restype = None
             L.oracle_sm_canny.argtypes = [u32p] + [ctypes.c_int32] * 4 + [u32p, u8p, u8p] + \
                 [i64p] * 4 + [u8p, u8p]
             L.oracle_sm_canny.restype = ctypes.c_int
@@ -529,6 +536,29 @@ def accumulate_thick(g, hist, k: int, params: Params = Params()) -> Dict:
                                      _p(stats, ctypes.c_int64)):
         raise MemoryError("oracle_accumulate_thick")
     return {"N": N, "M": M, "stats": stats}
+
+
+def segment_meets_box(gin, gout, lo, hi) -> bool:
+    """Slab test of the closed segment against the half-open box [lo, hi)."""
+    arrs = [np.ascontiguousarray(a, dtype=np.int64) for a in (gin, gout, lo, hi)]
+    return bool(lib().oracle_segment_meets_box(*[_p(a, ctypes.c_int64) for a in arrs]))
+
+
+def count_thick_voxels(g, hist, k: int, cls: int, voxels, params: Params = None) -> np.ndarray:
+    """For each voxel (linear index), the histories of class cls (1 missed,
+    2 hit) whose thick set A_i(k) holds it, by the slab test of the dilated
+    box against every history."""
+    params = params or Params()
+    th, K = _table_arrays()
+    vox = np.ascontiguousarray(voxels, dtype=np.int64)
+    counts = np.zeros(len(vox), np.int64)
+    arrs = [np.ascontiguousarray(a, dtype=np.float32) for a in hist.arrays()]
+    og = _ogeom(g)
+    lib().oracle_count_thick_voxels(ctypes.byref(og), params.tau_l, params.tau_h,
+                                    _p(th, ctypes.c_int64), K, int(k),
+                                    *[_p(a, ctypes.c_float) for a in arrs], len(hist), int(cls),
+                                    _p(vox, ctypes.c_int64), len(vox), _p(counts, ctypes.c_int64))
+    return counts
 
 
 def run_thick(g, hist, k: int, params: Params = Params()) -> Dict:

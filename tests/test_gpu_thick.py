@@ -160,3 +160,31 @@ def test_scan_thick_plans(hd, oracle_mod, case):
     st = s.stats()
     assert (st["steps_miss"], st["steps_hit"]) == (int(ref["stats"][5]), int(ref["stats"][6]))
     s.close()
+
+
+def test_scan_thick_config2_full_size(hd, oracle_mod):
+    """The head-sized workload, all 9e6 histories, k = 2, in the launch
+    configuration the bench times: sampled voxels (random and on the object's
+    boundary) counted by the oracle's slab test of the dilated box over every
+    history; the decisions re-derived by the oracle from the GPU's counts; the
+    count identities."""
+    w = synth.make_config(2)
+    g, h = w.geometry, w.histories
+    dims = (g.nx, g.ny, g.nz)
+    s = _scan_thick(hd, g, h, 2)
+    N = s.counts(hd.HD_MSC)
+    M = s.counts(hd.HD_SM)
+    rng = np.random.default_rng(33)
+    obj = synth.object_mask(g, w.phantom).reshape(g.nz, g.ny, g.nx)
+    edge = np.flatnonzero((obj ^ np.roll(obj, 1, axis=2)).ravel())
+    vox = np.concatenate([rng.choice(g.nx * g.ny * g.nz, 10, replace=False),
+                          rng.choice(edge, 10, replace=False)])
+    assert np.array_equal(N[vox], oracle_mod.count_thick_voxels(g, h, 2, 1, vox))
+    assert np.array_equal(M[vox], oracle_mod.count_thick_voxels(g, h, 2, 2, vox))
+    assert np.array_equal(s.mask(hd.HD_SC), (N == 0).astype(np.uint8))
+    assert np.array_equal(s.mask(hd.HD_MSC), oracle_mod.msc_decide(N, dims))
+    assert np.array_equal(s.mask(hd.HD_SM), oracle_mod.sm_decide(M, dims)["H3"])
+    st = s.stats()
+    assert st["steps_miss"] == int(N.sum()) and st["steps_hit"] == int(M.sum())
+    assert st["n_in"] == len(h)
+    s.close()

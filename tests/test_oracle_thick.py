@@ -79,3 +79,30 @@ def test_sums_and_growth(oracle_mod):
         if prev is not None:
             assert np.all(r["N"] >= prev["N"]) and np.all(r["M"] >= prev["M"])
         prev = r
+
+
+def test_box_test_equals_rational_slab_test(oracle_mod):
+    """The oracle's box slab test against the rational one written here, on
+    random segments and boxes (ties on box faces included)."""
+    rng = np.random.default_rng(31)
+    for _ in range(3000):
+        a = rng.integers(-3 * 65536, 12 * 65536, 3)
+        b = rng.integers(-3 * 65536, 12 * 65536, 3)
+        if rng.random() < 0.3:
+            a = (a // 65536) * 65536  # on lattice planes
+        if rng.random() < 0.2:
+            b[2] = a[2]
+        lo = rng.integers(0, 8, 3)
+        hi = lo + rng.integers(1, 5, 3)
+        want = _meets_box([Fraction(int(c), 65536) for c in a],
+                          [Fraction(int(c), 65536) for c in b], list(lo), list(hi))
+        assert oracle_mod.segment_meets_box(a, b, lo, hi) == want
+
+
+def test_count_thick_voxels_equals_accumulation(oracle_mod):
+    w = synth.make_config(1, fraction=0.05)
+    g = w.geometry
+    r = oracle_mod.accumulate_thick(g, w.histories, 2)
+    vox = np.random.default_rng(32).choice(g.nx * g.ny * g.nz, 40, replace=False)
+    assert np.array_equal(oracle_mod.count_thick_voxels(g, w.histories, 2, 1, vox), r["N"][vox])
+    assert np.array_equal(oracle_mod.count_thick_voxels(g, w.histories, 2, 2, vox), r["M"][vox])
