@@ -481,7 +481,7 @@ def run_rows(args):
     torch.cuda.set_device(local)
     hbuild.build()
     hulld.load()
-    w = synth.make_config(2)
+    w = synth.make_config(2, fraction=args.fraction)
     g, h = w.geometry, w.histories
     n = len(h)
     dev = [torch.from_numpy(a).cuda() for a in h.arrays()]
