@@ -8,6 +8,7 @@
 #include <vector>
 
 #include "hd_geom.cuh"
+#include "hd_rows.cuh"
 #include "hd_thick.cuh"
 
 namespace {
@@ -131,6 +132,7 @@ struct hd_scan {
     uint32_t *tile_cursor = nullptr;  // 2 * ntiles
     int64_t *rows_scratch = nullptr;  // tile sums of the system-row offset scan
     int64_t rows_scratch_cap = 0;
+    uint32_t *rows_bits = nullptr;    // the hull packed for the row passes
     int32_t thick_k = 0;             // thick rays: in-plane dilation (0 = thin paths)
     void *thick_ws = nullptr;        // their difference arrays
     float *staging = nullptr;  // copied host inputs: 6 columns of staging_half floats
@@ -206,7 +208,7 @@ void free_scan(hd_scan *s)
     void *ptrs[] = {s->N, s->M, s->carve, s->H1, s->H2, s->H3, s->bits_out, s->slice_key,
                     s->mt, s->slope, s->index, s->ctrl, s->rec_buf, s->staging,
                     s->compact_blocks, s->d_count, s->compact_out, s->pair_buf, s->jobs,
-                    s->rows_scratch, s->thick_ws,
+                    s->rows_scratch, s->rows_bits, s->thick_ws,
                     s->tile_count, s->tile_cursor, s->desc_dev};
     for (void *p : ptrs)
         if (p) cudaFree(p);
@@ -795,16 +797,26 @@ hd_status hd_scan_system_rows(hd_scan *scan, int32_t method, const float *angle_
         scan->rows_scratch_cap = need;
     }
     const uint8_t *hull = mask_of(scan, method);
+    if (!scan->rows_bits) {
+        if (cudaMalloc(&scan->rows_bits, sizeof(uint32_t) * static_cast<size_t>(scan->words)) !=
+            cudaSuccess) {
+            cudaGetLastError();
+            scan->rows_bits = nullptr;
+            return HD_ERR_NOMEM;
+        }
+    }
+    HD_CUDA(hd::launch_pack_bits(hull, scan->V, scan->rows_bits, st));
     const hd::Inputs in{angle_deg, u_in, v_in, u_out, v_out, nullptr};
-    HD_CUDA(hd::launch_rows_count(in, n, scan->gq, scan->cordic, hull, row_ptr, scan->sm_count, st));
+    HD_CUDA(hd::launch_rows_count(in, n, scan->gq, scan->cordic, hull, scan->rows_bits, row_ptr,
+                                  scan->sm_count, st));
     HD_CUDA(hd::launch_rows_scan(row_ptr + 1, n, scan->rows_scratch, st));
     int64_t total = 0;
     HD_CUDA(cudaMemcpyAsync(&total, row_ptr + n, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
     HD_CUDA(cudaStreamSynchronize(st));
     *nnz = total;
     if (total > capacity) return HD_ERR_RANGE;
-    HD_CUDA(hd::launch_rows_emit(in, n, scan->gq, scan->cordic, hull, row_ptr, cols,
-                                 scan->sm_count, st));
+    HD_CUDA(hd::launch_rows_emit(in, n, scan->gq, scan->cordic, hull, scan->rows_bits, row_ptr,
+                                 cols, scan->sm_count, st));
     return HD_OK;
 }
 

@@ -135,17 +135,6 @@ cudaError_t launch_trace_global(const Records &rec, Ctrl *ctrl, int64_t upper, c
 cudaError_t launch_classify(const float *wepl, int64_t n, float tau_l, float tau_h,
                             uint8_t *cls, cudaStream_t s);
 
-// Rows of the hull-restricted system matrix: count (row_ptr[i + 1] = row
-// length, row_ptr[0] = 0), in-place inclusive scan of row_ptr[1..n] (scratch
-// of rows_scan_scratch(n) int64), and emit into cols at row_ptr[i].
-cudaError_t launch_rows_count(const Inputs &in, int64_t n, const GeomQ &g, const Cordic &cd,
-                              const uint8_t *hull, int64_t *row_ptr, int sm_count, cudaStream_t s);
-int64_t rows_scan_scratch(int64_t n);
-cudaError_t launch_rows_scan(int64_t *a, int64_t n, int64_t *scratch, cudaStream_t s);
-cudaError_t launch_rows_emit(const Inputs &in, int64_t n, const GeomQ &g, const Cordic &cd,
-                             const uint8_t *hull, const int64_t *row_ptr, int32_t *cols,
-                             int sm_count, cudaStream_t s);
-
 // Blocks per SM the tiled traversal can keep resident with this much shared
 // memory per block and this many threads (0 when the launch is impossible).
 int trace_tiles_occupancy(int smem_words, int threads);

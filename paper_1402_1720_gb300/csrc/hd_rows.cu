@@ -1,16 +1,19 @@
 // Rows of the hull-restricted system matrix: for each history, the voxels of
-// its path A_i that lie inside a hull, in the order the path meets them.  The
+// its path A_i that lie inside a hull, in the order the path meets them.
+// The hull's bitmap sits in each block's shared memory when it fits, so the
+// per-voxel hull test is a shared-memory read.  The
 // hull exists to shrink the unknowns of the reconstruction to these voxels
 // (Sec. 1); the rows are what an iterative solver reads.  Two passes over
 // the histories (count, then emit into CSR offsets from an exclusive scan),
 // each walking the path with the exact run walk over the whole grid.
 #include "hd_geom.cuh"
+#include "hd_rows.cuh"
 
 namespace hd {
 
 namespace {
 
-constexpr int kRowsThreads = 256;
+constexpr int kRowsThreads = 1024;  // one block per SM when the hull sits in shared memory
 constexpr int kScanThreads = 1024;
 constexpr int kScanPerThread = 4;
 constexpr int kScanTile = kScanThreads * kScanPerThread;
@@ -36,48 +39,79 @@ __device__ __forceinline__ bool row_endpoints(const Inputs &in, int64_t i, const
     return endpoints_cs(g, tc.c, tc.s, in.u_in[i], in.v_in[i], in.u_out[i], in.v_out[i], r);
 }
 
-struct CountInHull {
-    const uint8_t *hull;
-    int64_t count;
-    __device__ __forceinline__ void operator()(uint32_t v) { count += hull[v] != 0 ? 1 : 0; }
-};
-
-struct EmitInHull {
-    const uint8_t *hull;
-    int32_t *out;
-    __device__ __forceinline__ void operator()(uint32_t v)
+// The hull as a bitmap (voxel v at bit v & 31 of word v >> 5), in shared
+// memory when it fits there, else read as bytes from global memory.
+template <bool kBits>
+struct HullTest {
+    const uint8_t *bytes;
+    const uint32_t *bits;
+    __device__ __forceinline__ bool operator()(uint32_t v) const
     {
-        if (hull[v] != 0) *out++ = static_cast<int32_t>(v);
+        if (kBits) return (bits[v >> 5] >> (v & 31u)) & 1u;
+        return bytes[v] != 0;
     }
 };
 
+template <bool kBits>
+struct CountInHull {
+    HullTest<kBits> in;
+    int64_t count;
+    __device__ __forceinline__ void operator()(uint32_t v) { count += in(v) ? 1 : 0; }
+};
+
+template <bool kBits>
+struct EmitInHull {
+    HullTest<kBits> in;
+    int32_t *out;
+    __device__ __forceinline__ void operator()(uint32_t v)
+    {
+        if (in(v)) *out++ = static_cast<int32_t>(v);
+    }
+};
+
+// Copies the packed hull (words 32-bit words) into shared memory.
+__device__ __forceinline__ void stage_hull(uint32_t *s_bits, const uint32_t *bits, int64_t words)
+{
+    for (int64_t w = threadIdx.x; w < words; w += blockDim.x) s_bits[w] = __ldg(bits + w);
+    __syncthreads();
+}
+
+template <bool kBits>
 __global__ void __launch_bounds__(kRowsThreads) rows_count_kernel(Inputs in, int64_t n, GeomQ g,
                                                                   Cordic cd, const uint8_t *hull,
-                                                                  int64_t *row_ptr)
+                                                                  const uint32_t *hull_bits,
+                                                                  int64_t words, int64_t *row_ptr)
 {
+    extern __shared__ uint32_t s_bits[];
+    if (kBits) stage_hull(s_bits, hull_bits, words);
     RowsTrig tc;
     const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
     for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
          i += stride) {
         int32_t r[6];
-        CountInHull c{hull, 0};
+        CountInHull<kBits> c{{hull, s_bits}, 0};
         if (row_endpoints(in, i, g, cd, tc, r)) walk_path(r, g.nx, g.ny, g.nz, c);
         row_ptr[i + 1] = c.count;
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) row_ptr[0] = 0;
 }
 
+template <bool kBits>
 __global__ void __launch_bounds__(kRowsThreads) rows_emit_kernel(Inputs in, int64_t n, GeomQ g,
                                                                  Cordic cd, const uint8_t *hull,
+                                                                 const uint32_t *hull_bits,
+                                                                 int64_t words,
                                                                  const int64_t *row_ptr,
                                                                  int32_t *cols)
 {
+    extern __shared__ uint32_t s_bits[];
+    if (kBits) stage_hull(s_bits, hull_bits, words);
     RowsTrig tc;
     const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
     for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
          i += stride) {
         int32_t r[6];
-        EmitInHull e{hull, cols + row_ptr[i]};
+        EmitInHull<kBits> e{{hull, s_bits}, cols + row_ptr[i]};
         if (row_endpoints(in, i, g, cd, tc, r)) walk_path(r, g.nx, g.ny, g.nz, e);
     }
 }
@@ -162,23 +196,46 @@ __global__ void __launch_bounds__(kScanThreads) scan_add_kernel(int64_t *a, int6
     }
 }
 
-int64_t grid_for(int64_t n, int sm_count)
+int64_t grid_for(int64_t n, int sm_count, bool bits)
 {
     int64_t blocks = (n + kRowsThreads - 1) / kRowsThreads;
-    const int64_t cap = static_cast<int64_t>(sm_count > 0 ? sm_count : 1) * 8;
+    const int64_t cap = static_cast<int64_t>(sm_count > 0 ? sm_count : 1) * (bits ? 1 : 2);
     if (blocks > cap) blocks = cap;
     return blocks < 1 ? 1 : blocks;
+}
+
+constexpr int64_t kMaxHullWords = 48 * 1024;  // 192 KB of shared memory
+
+template <class K>
+cudaError_t allow_smem(K kernel)
+{
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                static_cast<int>(sizeof(uint32_t) * kMaxHullWords));
 }
 
 }  // namespace
 
 int64_t rows_scan_scratch(int64_t n) { return (n + kScanTile - 1) / kScanTile; }
 
+int64_t rows_hull_words(int64_t V) { return (V + 31) / 32; }
+
+// hull_bits: the packed hull (rows_hull_words(V) words) or null; with it,
+// when it fits, each block holds the hull in shared memory.
 cudaError_t launch_rows_count(const Inputs &in, int64_t n, const GeomQ &g, const Cordic &cd,
-                              const uint8_t *hull, int64_t *row_ptr, int sm_count, cudaStream_t s)
+                              const uint8_t *hull, const uint32_t *hull_bits, int64_t *row_ptr,
+                              int sm_count, cudaStream_t s)
 {
-    rows_count_kernel<<<static_cast<unsigned>(grid_for(n, sm_count)), kRowsThreads, 0, s>>>(
-        in, n, g, cd, hull, row_ptr);
+    const int64_t words = rows_hull_words(int64_t(g.nx) * g.ny * g.nz);
+    if (hull_bits && words <= kMaxHullWords) {
+        const cudaError_t e = allow_smem(rows_count_kernel<true>);
+        if (e != cudaSuccess) return e;
+        rows_count_kernel<true><<<static_cast<unsigned>(grid_for(n, sm_count, true)), kRowsThreads,
+                                  sizeof(uint32_t) * words, s>>>(in, n, g, cd, hull, hull_bits,
+                                                                 words, row_ptr);
+    } else {
+        rows_count_kernel<false><<<static_cast<unsigned>(grid_for(n, sm_count, false)),
+                                   kRowsThreads, 0, s>>>(in, n, g, cd, hull, nullptr, 0, row_ptr);
+    }
     return cudaGetLastError();
 }
 
@@ -193,11 +250,21 @@ cudaError_t launch_rows_scan(int64_t *a, int64_t n, int64_t *scratch, cudaStream
 }
 
 cudaError_t launch_rows_emit(const Inputs &in, int64_t n, const GeomQ &g, const Cordic &cd,
-                             const uint8_t *hull, const int64_t *row_ptr, int32_t *cols,
-                             int sm_count, cudaStream_t s)
+                             const uint8_t *hull, const uint32_t *hull_bits,
+                             const int64_t *row_ptr, int32_t *cols, int sm_count, cudaStream_t s)
 {
-    rows_emit_kernel<<<static_cast<unsigned>(grid_for(n, sm_count)), kRowsThreads, 0, s>>>(
-        in, n, g, cd, hull, row_ptr, cols);
+    const int64_t words = rows_hull_words(int64_t(g.nx) * g.ny * g.nz);
+    if (hull_bits && words <= kMaxHullWords) {
+        const cudaError_t e = allow_smem(rows_emit_kernel<true>);
+        if (e != cudaSuccess) return e;
+        rows_emit_kernel<true><<<static_cast<unsigned>(grid_for(n, sm_count, true)), kRowsThreads,
+                                 sizeof(uint32_t) * words, s>>>(in, n, g, cd, hull, hull_bits,
+                                                                words, row_ptr, cols);
+    } else {
+        rows_emit_kernel<false><<<static_cast<unsigned>(grid_for(n, sm_count, false)),
+                                  kRowsThreads, 0, s>>>(in, n, g, cd, hull, nullptr, 0, row_ptr,
+                                                        cols);
+    }
     return cudaGetLastError();
 }
 
