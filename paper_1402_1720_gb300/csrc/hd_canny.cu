@@ -8,8 +8,8 @@
 //
 //   canny_smooth_kernel    thread per voxel: S = [1 2 1]^T [1 2 1] * M
 //   canny_gradient_kernel  thread per voxel: Sobel of S, magnitude, direction
-//   canny_nms_kernel       thread per voxel: local maximum test, slice maximum
-//   canny_slice_kernel     block per slice: hysteresis on bitmaps in shared
+//   canny_nms_kernel       thread per voxel: local maximum test
+//   canny_slice_kernel     block per slice: the slice maximum, hysteresis on bitmaps in shared
 //                          memory, the edge voxels' M listed in shared memory,
 //                          the quantile by a 32-step radix select, the hull
 #include <cuda_runtime.h>
@@ -27,7 +27,6 @@ struct CannyWs {
     long long *S, *mag;
     uint8_t *dir;  // (dx + 1) | (dy + 1) << 2 of the gradient direction
     uint8_t *nms;
-    unsigned long long *smax;  // nz slice maxima of the suppressed magnitude
 };
 
 __device__ __forceinline__ int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
@@ -96,8 +95,7 @@ __global__ void __launch_bounds__(kVoxThreads) canny_gradient_kernel(const long 
 
 __global__ void __launch_bounds__(kVoxThreads) canny_nms_kernel(const long long *mag,
                                                                 const uint8_t *dir, int nx, int ny,
-                                                                int64_t V, uint8_t *nms,
-                                                                unsigned long long *smax)
+                                                                int64_t V, uint8_t *nms)
 {
     const int64_t v = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
     if (v >= V) return;
@@ -112,9 +110,7 @@ __global__ void __launch_bounds__(kVoxThreads) canny_nms_kernel(const long long 
     if (x + dx >= 0 && x + dx < nx && y + dy >= 0 && y + dy < ny) fwd = mg[(x + dx) + nx * (y + dy)];
     if (x - dx >= 0 && x - dx < nx && y - dy >= 0 && y - dy < ny) bwd = mg[(x - dx) + nx * (y - dy)];
     const long long m = mg[j];
-    const bool keep = m > 0 && m >= bwd && m > fwd;
-    nms[v] = keep ? 1 : 0;
-    if (keep) atomicMax(smax + z, static_cast<unsigned long long>(m));
+    nms[v] = (m > 0 && m >= bwd && m > fwd) ? 1 : 0;
 }
 
 // Horizontal dilation of row word k by one voxel, across word boundaries.
@@ -165,9 +161,22 @@ __device__ __forceinline__ long long block_sum(long long v, long long *s_red)
     return t;  // in every thread
 }
 
+__device__ __forceinline__ long long block_max(long long v, long long *s_red)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) s_red[warp] = v;
+    __syncthreads();
+    long long t = 0;
+    for (int k = 0; k < static_cast<int>(blockDim.x >> 5); ++k) t = max(t, s_red[k]);
+    __syncthreads();
+    return t;  // in every thread
+}
+
 __global__ void __launch_bounds__(kSliceThreads) canny_slice_kernel(
-    const uint32_t *M, const long long *mag, const uint8_t *nms, const unsigned long long *smax,
-    int nx, int ny, int rw, int q_pct, uint32_t *mt, uint8_t *has_edge, uint8_t *H3)
+    const uint32_t *M, const long long *mag, const uint8_t *nms, int nx, int ny, int rw, int q_pct,
+    uint32_t *mt, uint8_t *has_edge, uint8_t *H3)
 {
     extern __shared__ uint32_t s_bits[];
     __shared__ long long s_red[32];
@@ -175,10 +184,14 @@ __global__ void __launch_bounds__(kSliceThreads) canny_slice_kernel(
     uint32_t *E = s_bits + ny * rw;  // edge voxels found so far
     const int z = blockIdx.x;
     const int64_t plane = static_cast<int64_t>(nx) * ny;
-    const long long mmax = static_cast<long long>(smax[z]);
     const uint32_t *m = M + z * plane;
     const long long *mg = mag + z * plane;
     const uint8_t *nm = nms + z * plane;
+    // the slice's largest suppressed magnitude
+    long long mloc = 0;
+    for (int64_t j = threadIdx.x; j < plane; j += blockDim.x)
+        if (nm[j]) mloc = max(mloc, mg[j]);
+    const long long mmax = block_max(mloc, s_red);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     const int words = ny * rw;
     for (int k = warp; k < words; k += nwarps) {  // a warp per word: one ballot each
@@ -290,8 +303,6 @@ bool layout(int32_t nx, int32_t ny, int32_t nz, void *base, CannyWs *ws, size_t 
     off += align256(V);
     const size_t oN = off;
     off += align256(V);
-    const size_t oX = off;
-    off += align256(8 * static_cast<size_t>(nz));
     if (bytes) *bytes = off;
     if (ws && base) {
         char *p = static_cast<char *>(base);
@@ -299,7 +310,6 @@ bool layout(int32_t nx, int32_t ny, int32_t nz, void *base, CannyWs *ws, size_t 
         ws->mag = reinterpret_cast<long long *>(p + oM);
         ws->dir = reinterpret_cast<uint8_t *>(p + oD);
         ws->nms = reinterpret_cast<uint8_t *>(p + oN);
-        ws->smax = reinterpret_cast<unsigned long long *>(p + oX);
     }
     return true;
 }
@@ -342,18 +352,17 @@ hd_status hd_sm_canny(const uint32_t *M, int32_t nx, int32_t ny, int32_t nz, int
     const int64_t V = static_cast<int64_t>(nx) * ny * nz;
     const unsigned blocks = static_cast<unsigned>((V + kVoxThreads - 1) / kVoxThreads);
     const int rw = (nx + 31) / 32;
-    cudaError_t e = cudaMemsetAsync(ws.smax, 0, 8 * static_cast<size_t>(nz), st);
-    if (e == cudaSuccess) {
+    cudaError_t e = cudaSuccess;
+    {
         canny_smooth_kernel<<<blocks, kVoxThreads, 0, st>>>(M, nx, ny, V, ws.S);
         canny_gradient_kernel<<<blocks, kVoxThreads, 0, st>>>(ws.S, nx, ny, V, ws.mag, ws.dir);
-        canny_nms_kernel<<<blocks, kVoxThreads, 0, st>>>(ws.mag, ws.dir, nx, ny, V, ws.nms,
-                                                         ws.smax);
+        canny_nms_kernel<<<blocks, kVoxThreads, 0, st>>>(ws.mag, ws.dir, nx, ny, V, ws.nms);
         e = cudaFuncSetAttribute(canny_slice_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  static_cast<int>(sizeof(uint32_t) * (2 * kMaxWords + kListCap)));
     }
     if (e == cudaSuccess) {
         canny_slice_kernel<<<nz, kSliceThreads, sizeof(uint32_t) * (2 * rw * ny + kListCap), st>>>(
-            M, ws.mag, ws.nms, ws.smax, nx, ny, rw, q_pct, mt, has_edge, H3);
+            M, ws.mag, ws.nms, nx, ny, rw, q_pct, mt, has_edge, H3);
         e = cudaGetLastError();
     }
     if (e != cudaSuccess) {
