@@ -261,8 +261,11 @@ HD_API hd_status hd_scan_get_tuning(hd_scan *scan, hd_tuning *out);
  * reset): HD_ERR_STATE otherwise; HD_ERR_RANGE for k outside [0, 16].  A scan
  * with SC and without MSC then counts N (H_1 = [N = 0]) instead of keeping a
  * carve mask; allocates the thick rays' difference arrays (about 16 bytes
- * per voxel).  Thick scans cannot join a batch (hd_batch_add_item returns
- * HD_ERR_STATE). */
+ * per voxel).  When the scan's tiles are whole one-slice planes (the
+ * default plan whenever a slice fits the shared-memory budget) the thick
+ * sets are counted in the tiled traversal; otherwise each history is walked
+ * over the whole grid as in hd_accumulate_thick.  Thick scans cannot join a
+ * batch (hd_batch_add_item returns HD_ERR_STATE). */
 HD_API hd_status hd_scan_set_thick(hd_scan *scan, int32_t k);
 
 /* Start (enable = 1) or stop (0) recording CUDA events around the scan's
@@ -518,6 +521,9 @@ HD_API hd_status hd_classify(const float *wepl, int64_t n, const hd_params *para
  * |dy| <= k, same z.  For in-plane voxel size s, k = floor(d_0 / s) (a
  * thickness below the slice thickness).  k = 0 gives A_i itself.
  *
+ * A standalone accumulation (no scan, no tiles: each history is walked over
+ * the whole grid by one lane; a scan set to thick rays with hd_scan_set_thick
+ * counts on its tiled traversal instead).
  * Classifies the n histories (device SoA arrays, as hd_scan_add_histories
  * with on_device = 1) and ADDS one to N[v] for every voxel v of the thick set
  * of every missed history and to M[v] for every hit one (each voxel once per
