@@ -106,3 +106,12 @@ def test_count_thick_voxels_equals_accumulation(oracle_mod):
     vox = np.random.default_rng(32).choice(g.nx * g.ny * g.nz, 40, replace=False)
     assert np.array_equal(oracle_mod.count_thick_voxels(g, w.histories, 2, 1, vox), r["N"][vox])
     assert np.array_equal(oracle_mod.count_thick_voxels(g, w.histories, 2, 2, vox), r["M"][vox])
+
+
+def test_run_thick_k0_is_run(oracle_mod):
+    """At k = 0 the thick-ray run is the thin run: counts, hulls, thresholds."""
+    w = synth.make_config(1, fraction=0.1)
+    a = oracle_mod.run_thick(w.geometry, w.histories, 0)
+    b = oracle_mod.run(w.geometry, w.histories)
+    for key in ("N", "M", "H1", "H2", "H3", "Mt"):
+        assert np.array_equal(a[key], b[key]), key
