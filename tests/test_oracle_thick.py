@@ -8,6 +8,7 @@ import numpy as np
 import pytest
 
 from paper_1402_1720_gb300 import synth
+from tests.test_oracle_pins import _random_segments
 
 
 def _meets_box(a, b, lo, hi):
@@ -115,3 +116,13 @@ def test_run_thick_k0_is_run(oracle_mod):
     b = oracle_mod.run(w.geometry, w.histories)
     for key in ("N", "M", "H1", "H2", "H3", "Mt"):
         assert np.array_equal(a[key], b[key]), key
+
+
+def test_unit_box_is_the_voxel_test(oracle_mod):
+    """A box of one voxel is the voxel slab test of the thin sets."""
+    rng = np.random.default_rng(34)
+    dims = (6, 5, 4)
+    for a, b in _random_segments(rng, 1500, dims):
+        x, y, z = (int(rng.integers(0, d)) for d in dims)
+        assert oracle_mod.segment_meets_box(a, b, [x, y, z], [x + 1, y + 1, z + 1]) == \
+            oracle_mod.segment_meets_voxel(a, b, x, y, z)
