@@ -37,15 +37,6 @@ METRIC = "proton histories/s (SC+MSC+SM hull detection)"
 UNIT = "histories/s"
 WORKLOAD = "head-200x200x32 voxels 1x1x2.5mm, 90 angles x 100000 = 9e6 float32 histories"
 
-# Algorithmic integer operations per voxel-step of the DDA: choose the next
-# crossing (2 compares), advance the voxel index (1), update two
-# crossing-order terms (2 x 64-bit add = 4), decrement and test the remaining
-# count (2), increment the count or clear the bit (1).
-OPS_PER_STEP = 10
-# GB300: 152 SMs x 128 INT32 lanes per SM per clock.
-SMS, INT32_LANES_PER_SM = 152, 128
-
-
 def _peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -131,7 +122,9 @@ def _kernel_sources_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def _profiled_traffic():
+def _profile_fields():
+    """Fields of the committed ncu summary of the traversal kernel, when it
+    was captured on the current kernel sources (None otherwise)."""
     path = os.path.join(ROOT, TRACE_PROFILE)
     try:
         text = open(path).read()
@@ -144,8 +137,15 @@ def _profiled_traffic():
             fields[k.strip()] = v.strip().strip("`")
     if fields.get("kernel sources sha256") != _kernel_sources_hash():
         return None, f"{TRACE_PROFILE} was captured on other kernel sources"
+    return fields, TRACE_PROFILE
+
+
+def _profiled_traffic():
+    fields, note = _profile_fields()
+    if fields is None:
+        return None, note
     try:
-        return int(fields["dram bytes per full launch"]), TRACE_PROFILE
+        return int(fields["dram bytes per full launch"]), note
     except (KeyError, ValueError):
         return None, "no traffic figure in the capture summary"
 
@@ -216,37 +216,39 @@ def cpu_baseline(seconds_target: float):
             "voxel_steps_per_s": (r["stats"]["steps_miss"] + r["stats"]["steps_hit"]) / dt}
 
 
-def run_batched(args):
-    """48 independent scans (volumes from {64x64x16, 128x128x32, 256x256x64}
-    voxels, random ellipsoid phantoms, log-uniform 2e5-2e7 histories): one
-    batched run per step (CUDA-graph replay of a single persistent traversal
-    over all scans) against 48 one-at-a-time scans on the same GPU."""
-    import torch
-    from paper_1402_1720_gb300 import build as hbuild
-    from paper_1402_1720_gb300 import hulld, synth
-    ws, rank, local = _dist()
-    torch.cuda.set_device(local)
-    hbuild.build()
-    hulld.load()
+def mix48(args, pool=None):
+    """The 48 scans of the batched/served mix (volumes from {64x64x16,
+    128x128x32, 256x256x64} voxels, random ellipsoid phantoms, log-uniform
+    2e5-2e7 histories each) as host arrays, generated in parallel by `pool`
+    when one is given."""
+    from paper_1402_1720_gb300 import synth
     specs = synth.batch_scan_specs(48, fraction=args.batch_fraction)
-    dev = []
-    total = 0
-    for sp in specs:
-        h = synth.scan_histories(sp)
-        total += len(h)
-        dev.append([torch.from_numpy(a).cuda() for a in h.arrays()])
+    if pool is not None:
+        hosts = synth.batch_scans_parallel(pool, fraction=args.batch_fraction)
+    else:
+        hosts = [synth.scan_histories(sp) for sp in specs]
+    return specs, hosts
+
+
+def measure_batched(args, specs, hosts, steps, warmup):
+    """One batched run per step (all scans, one persistent traversal,
+    CUDA-graph replay) against the same scans one at a time on the same
+    GPU; inputs resident in HBM."""
+    import torch
+    from paper_1402_1720_gb300 import autotune, hulld
+    dev = [[torch.from_numpy(a).cuda() for a in h.arrays()] for h in hosts]
+    total = sum(len(h) for h in hosts)
     scans = [hulld.Scan(sp.geometry) for sp in specs]
     # launch parameters per volume class, from the autotuner (tuned on the
     # class's largest scan, cached per grid and GPU)
-    from paper_1402_1720_gb300 import autotune
     tuning = {}
     if not args.no_tune:
         for cls in sorted({(sp.geometry.nx, sp.geometry.ny, sp.geometry.nz) for sp in specs}):
             k = max((i for i, sp in enumerate(specs)
                      if (sp.geometry.nx, sp.geometry.ny, sp.geometry.nz) == cls),
-                    key=lambda i: specs[i].n_histories)
-            setting = autotune.tuned_setting(specs[k].geometry, dev[k], repeats=2)
-            tuning["x".join(map(str, cls))] = setting
+                    key=lambda i: len(hosts[i]))
+            tuning["x".join(map(str, cls))] = autotune.tuned_setting(specs[k].geometry, dev[k],
+                                                                     repeats=2)
         for s, sp in zip(scans, specs):
             autotune.apply(s, tuning["x".join(map(str, (sp.geometry.nx, sp.geometry.ny,
                                                         sp.geometry.nz)))])
@@ -279,58 +281,47 @@ def run_batched(args):
             torch.cuda.synchronize()
         return e0.elapsed_time(e1) / k
 
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         batched_step()
     torch.cuda.synchronize()
     st0 = batch.stats()
-    sampler = ClockSampler(local)
-    sampler.start()
-    ms_b = timed(batched_step, args.steps, 0)
-    clocks = sampler.stop()
-    launches = (batch.stats()["kernel_launches"] - st0["kernel_launches"]) // max(1, args.steps)
+    ms_b = timed(batched_step, steps, 0)
+    launches = (batch.stats()["kernel_launches"] - st0["kernel_launches"]) // max(1, steps)
     steps_total = sum(s.stats()["steps_miss"] + s.stats()["steps_hit"] for s in scans)
-    ms_s = timed(sequential_step, args.steps, args.warmup)
-    line = {"metric": "proton histories/s (48 batched scans, SC+MSC+SM)",
-            "value": total / (ms_b * 1e-3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms_b, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
-            "config": {"workload": "48 scans, grids {64x64x16,128x128x32,256x256x64} of "
-                                   "1x1x2.5 mm, log-uniform 2e5-2e7 histories each "
-                                   f"(x{args.batch_fraction:g}), 90 angles",
-                       "total_histories": total, "tuning": tuning,
-                       "grids": [f"{sp.geometry.nx}x{sp.geometry.ny}x{sp.geometry.nz}" for sp in specs]},
-            "voxel_steps_per_s": steps_total / (ms_b * 1e-3),
-            "sequential_48": {"value": total / (ms_s * 1e-3), "unit": UNIT, "ms_per_step": ms_s},
-            "batched_over_sequential": ms_s / ms_b,
-            "graph": batch.stats(), "gpu_launches_per_step": launches,
-            "gpu_launches": launches * args.steps, "clocks": clocks}
-    print(json.dumps(line), flush=True)
+    ms_s = timed(sequential_step, steps, warmup)
+    out = {"workload": "48 scans, grids {64x64x16,128x128x32,256x256x64} of 1x1x2.5 mm, "
+                       f"log-uniform 2e5-2e7 histories each (x{args.batch_fraction:g}), "
+                       "90 angles, inputs resident in HBM",
+           "total_histories": total, "steps": steps, "warmup": warmup,
+           "ms": ms_b, "histories_per_s": total / (ms_b * 1e-3),
+           "voxel_steps_per_s": steps_total / (ms_b * 1e-3),
+           "sequential_ms": ms_s, "sequential_histories_per_s": total / (ms_s * 1e-3),
+           "speedup": ms_s / ms_b, "tuning": tuning, "graph": batch.stats(),
+           "gpu_launches_per_step": launches,
+           "grids": [f"{sp.geometry.nx}x{sp.geometry.ny}x{sp.geometry.nz}" for sp in specs]}
     batch.close()
     for s in scans:
         s.close()
+    del dev
+    torch.cuda.empty_cache()
+    return out
 
 
-def run_serving(args):
-    """Poisson arrivals of scans from the 48-scan distribution, each streamed
-    as per-angle chunks of 1e4-1e5 histories from pinned host memory, served
-    by the continuous-batching server.  First the saturated throughput X is
+def measure_serving(args, specs, hosts):
+    """Poisson arrivals of the scans, each streamed as per-angle chunks of
+    1e4-1e5 histories from page-locked host memory, served by the
+    continuous-batching server.  First the saturated throughput X is
     measured (all scans at once); then scans arrive at rate
-    0.7 X / (mean histories per scan).  time-to-hull = hull ready - last chunk
-    submitted (and - first chunk)."""
+    load * X / (mean histories per scan).  time-to-hull = hull ready - last
+    chunk submitted (and - first chunk).  Also: the same chunks added one
+    scan at a time through the plain scan calls."""
     import queue
     import torch
-    from paper_1402_1720_gb300 import build as hbuild
-    from paper_1402_1720_gb300 import hulld, synth
-    _, _, local = _dist()
-    torch.cuda.set_device(local)
-    hbuild.build()
-    hulld.load()
+    from paper_1402_1720_gb300 import hulld
     rng = np.random.default_rng(20140207)
-    specs = synth.batch_scan_specs(args.serve_scans, fraction=args.batch_fraction)
     scans = []  # (spec, [chunk views of pinned tensors])
     total = 0
-    for sp in specs:
-        h = synth.scan_histories(sp)
+    for sp, h in zip(specs, hosts):
         pinned = [torch.from_numpy(a).pin_memory() for a in h.arrays()]
         bounds = []
         angles = h.angle_deg
@@ -352,9 +343,8 @@ def run_serving(args):
     # reported per experiment as differences
     srv = hulld.Server(cfg)
 
-    def serve(arrivals, which=None):
-        """Run one experiment; arrivals[k] = start time (s) of scan which[k]."""
-        which = list(range(len(scans))) if which is None else list(which)
+    def serve(arrivals):
+        """Run one experiment; arrivals[k] = start time (s) of scan k."""
         before = srv.stats()
         ids = {}
         t0 = time.perf_counter()
@@ -370,7 +360,6 @@ def run_serving(args):
                         if k is None:
                             done = True
                             break
-                        k = which[k]
                         sp, chunks = scans[k]
                         ids[k] = srv.open_scan(sp.geometry, None, len(chunks))
                         active.append([k, 0])
@@ -402,7 +391,7 @@ def run_serving(args):
         for t in threads:
             t.join()
         infos = []
-        for k in which:
+        for k in range(len(scans)):
             sid = ids[k]
             assert srv.wait(sid, 600_000) == hulld.HD_OK
             infos.append(srv.info(sid))
@@ -445,27 +434,85 @@ def run_serving(args):
     ttl = np.array([i["t_ready"] - i["t_last_chunk"] for i in infos])
     ttf = np.array([i["t_ready"] - i["t_first_chunk"] for i in infos])
     span = max(i["t_ready"] for i in infos) - min(i["t_open"] for i in infos)
-    line = {"metric": "served time-to-hull p50 (hull ready - last chunk), 48-scan mix",
-            "value": float(np.percentile(ttl, 50)) * 1e3, "unit": "ms", "n_gpus": 1,
-            "steps": 1, "warmup": 1, "higher_is_better": False, "scaling": "weak",
-            "vs_baseline": None, "dtype": "int64", "data": "synthetic",
-            "config": {"workload": f"{len(scans)} scans from the 48-scan distribution, Poisson "
-                                   f"arrivals at {args.serve_load:g} x saturated throughput, "
-                                   "per-angle chunks of 1e4-1e5 histories from pinned host memory",
-                       "total_histories": total, "chunks": int(st["chunks_submitted"]),
-                       "client_threads": args.serve_clients},
-            "time_to_hull_ms": {"p50": float(np.percentile(ttl, 50)) * 1e3,
-                                "p99": float(np.percentile(ttl, 99)) * 1e3,
-                                "max": float(ttl.max()) * 1e3},
-            "time_from_first_chunk_ms": {"p50": float(np.percentile(ttf, 50)) * 1e3,
-                                         "p99": float(np.percentile(ttf, 99)) * 1e3},
-            "served_histories_per_s": total / span,
+    return {"workload": f"{len(scans)} scans from the 48-scan mix, Poisson arrivals at "
+                        f"{args.serve_load:g} x saturated throughput, per-angle chunks of "
+                        "1e4-1e5 histories from pinned host memory",
+            "total_histories": total, "chunks": int(st["chunks_submitted"]),
+            "client_threads": args.serve_clients, "load": args.serve_load,
+            "p50_ms": float(np.percentile(ttl, 50)) * 1e3,
+            "p99_ms": float(np.percentile(ttl, 99)) * 1e3,
+            "max_ms": float(ttl.max()) * 1e3,
+            "from_first_chunk_ms": {"p50": float(np.percentile(ttf, 50)) * 1e3,
+                                    "p99": float(np.percentile(ttf, 99)) * 1e3},
+            "histories_per_s": total / span,
             "saturated_histories_per_s": X, "arrival_rate_scans_per_s": lam,
-            "sequential_streamed": {"histories_per_s": total / seq_s, "seconds": seq_s,
-                                    "what": "one scan at a time, each chunk added from pinned "
-                                            "host memory through the plain scan calls"},
+            "sequential_histories_per_s": total / seq_s, "sequential_seconds": seq_s,
+            "sequential_what": "one scan at a time, each chunk added from pinned host memory "
+                               "through the plain scan calls",
             "saturated_over_sequential": X / (total / seq_s),
             "server": st, "server_saturated": st_sat}
+
+
+def run_batched(args):
+    """The 48-scan mix, batched against one at a time (its own JSON line)."""
+    import multiprocessing as mp
+    import torch
+    from paper_1402_1720_gb300 import build as hbuild
+    from paper_1402_1720_gb300 import hulld
+    with mp.get_context("spawn").Pool(min(16, os.cpu_count() or 1)) as pool:
+        specs, hosts = mix48(args, pool)
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    hbuild.build()
+    hulld.load()
+    sampler = ClockSampler(local)
+    sampler.start()
+    b = measure_batched(args, specs, hosts, args.steps, args.warmup)
+    clocks = sampler.stop()
+    line = {"metric": "proton histories/s (48 batched scans, SC+MSC+SM)",
+            "value": b["histories_per_s"], "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": b["ms"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+            "config": {"workload": b["workload"], "total_histories": b["total_histories"],
+                       "tuning": b["tuning"], "grids": b["grids"]},
+            "voxel_steps_per_s": b["voxel_steps_per_s"],
+            "sequential_48": {"value": b["sequential_histories_per_s"], "unit": UNIT,
+                              "ms_per_step": b["sequential_ms"]},
+            "batched_over_sequential": b["speedup"], "graph": b["graph"],
+            "gpu_launches_per_step": b["gpu_launches_per_step"],
+            "gpu_launches": b["gpu_launches_per_step"] * args.steps, "clocks": clocks}
+    print(json.dumps(line), flush=True)
+
+
+def run_serving(args):
+    """The 48-scan mix served (its own JSON line)."""
+    import multiprocessing as mp
+    import torch
+    from paper_1402_1720_gb300 import build as hbuild
+    from paper_1402_1720_gb300 import hulld
+    with mp.get_context("spawn").Pool(min(16, os.cpu_count() or 1)) as pool:
+        specs, hosts = mix48(args, pool)
+    _, _, local = _dist()
+    torch.cuda.set_device(local)
+    hbuild.build()
+    hulld.load()
+    sv = measure_serving(args, specs[:args.serve_scans], hosts[:args.serve_scans])
+    line = {"metric": "served time-to-hull p50 (hull ready - last chunk), 48-scan mix",
+            "value": sv["p50_ms"], "unit": "ms", "n_gpus": 1,
+            "steps": 1, "warmup": 1, "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+            "config": {"workload": sv["workload"], "total_histories": sv["total_histories"],
+                       "chunks": sv["chunks"], "client_threads": sv["client_threads"]},
+            "time_to_hull_ms": {"p50": sv["p50_ms"], "p99": sv["p99_ms"], "max": sv["max_ms"]},
+            "time_from_first_chunk_ms": sv["from_first_chunk_ms"],
+            "served_histories_per_s": sv["histories_per_s"],
+            "saturated_histories_per_s": sv["saturated_histories_per_s"],
+            "arrival_rate_scans_per_s": sv["arrival_rate_scans_per_s"],
+            "sequential_streamed": {"histories_per_s": sv["sequential_histories_per_s"],
+                                    "seconds": sv["sequential_seconds"],
+                                    "what": sv["sequential_what"]},
+            "saturated_over_sequential": sv["saturated_over_sequential"],
+            "server": sv["server"], "server_saturated": sv["server_saturated"]}
     print(json.dumps(line), flush=True)
 
 
@@ -847,6 +894,10 @@ def main():
     ap.add_argument("--serve-scans", type=int, default=48)
     ap.add_argument("--serve-load", type=float, default=0.7)
     ap.add_argument("--serve-clients", type=int, default=8)
+    ap.add_argument("--no-mix", action="store_true",
+                    help="head-200 workload: skip the batched and served 48-scan sections")
+    ap.add_argument("--mix-steps", type=int, default=5,
+                    help="head-200 workload: timed batched steps of the 48-scan section")
     args = ap.parse_args()
 
     if args.workload == "batched-48":
@@ -871,6 +922,18 @@ def main():
     if args.impl == "reference":
         run_reference(args)
         return
+
+    # the 48-scan mix for the batched and served sections, generated on the
+    # host cores by spawned processes while the GPU measures the head scan
+    ws0, _, _ = _dist()
+    mix_pool = mix_job = None
+    if ws0 == 1 and not args.no_mix:
+        import multiprocessing as mp
+        from paper_1402_1720_gb300 import synth as _synth
+        mix_pool = mp.get_context("spawn").Pool(min(16, os.cpu_count() or 1))
+        jobs = [(k, a, min(90, a + 10), args.batch_fraction) for k in range(48)
+                for a in range(0, 90, 10)]
+        mix_job = (jobs, mix_pool.map_async(_synth.batch_scan_part, jobs))
 
     import torch
     import torch.distributed as dist
@@ -932,6 +995,14 @@ def main():
             scan.set_profiling(False)
         return ms, prof, prof["kernel_launches"] - l0, clocks
 
+    # the mix's generation ends before any timed region, so that no host
+    # core is busy with it while kernels are launched and timed
+    mix_parts = None
+    if mix_job is not None:
+        mix_parts = mix_job[1].get()
+        mix_pool.close()
+        mix_pool.join()
+
     # ---- main measurement: all three methods
     scan = hulld.Scan(g)
     sampler = ClockSampler(local)
@@ -942,22 +1013,13 @@ def main():
     steps_per_scan = st["steps_miss"] + st["steps_hit"]
     value = ws * n / (ms * 1e-3)
 
-    # roofline of the dominant kernel (the traversal)
+    # roofline of the dominant kernel (the traversal).  Its algorithmic work
+    # is one counter update per voxel-step (the oracle's exact sum |A_i|;
+    # one launch covers the whole scan), and the ceiling of a design that
+    # privatises the counts in shared memory is the random-address
+    # shared-memory atomic rate, measured here by the same process.
     peaks = _peaks()
     trace_ms = prof["ms_trace"] / max(1, prof["trace_launches"])
-    ops = OPS_PER_STEP * steps_per_scan  # one traversal launch covers the whole scan
-    achieved = ops / (trace_ms * 1e-3) / 1e12
-    peak_tops = SMS * INT32_LANES_PER_SM * peaks["sm_max_mhz"] * 1e6 / 1e12
-    traffic, traffic_note = _profiled_traffic()
-    roofline = {"bound": "alu", "achieved": achieved, "peak": peak_tops, "unit": "Tops/s",
-                "frac": achieved / peak_tops, "traffic": traffic, "traffic_source": traffic_note,
-                "kernel": "trace_tiles_kernel", "kernel_ms": trace_ms,
-                "ops_per_voxel_step": OPS_PER_STEP, "voxel_steps_per_launch": steps_per_scan,
-                "peak_source": f"152 SMs x 128 INT32 lanes x {peaks['sm_max_mhz']:.0f} MHz "
-                               f"({peaks['source']} max clock)"}
-    # the traversal against the measured atomic ceilings: a design spending
-    # one shared-memory atomic per voxel-step is bounded by the random-address
-    # probe; this one spends two per run of several voxels
     runs = st.get("runs", 0)
     probes = {name: hulld.hd_probe_atomics(kind) for name, kind in
               [("smem_random", hulld.HD_PROBE_SMEM_RANDOM),
@@ -965,16 +1027,30 @@ def main():
                ("l2_random", hulld.HD_PROBE_L2_RANDOM),
                ("hbm_random", hulld.HD_PROBE_HBM_RANDOM)]}
     vsteps = steps_per_scan / (trace_ms * 1e-3)
+    traffic, traffic_note = _profiled_traffic()
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+    roofline = {"bound": "smem_atomic", "achieved": vsteps, "peak": probes["smem_random"],
+                "unit": "atomics/s", "frac": vsteps / probes["smem_random"],
+                "traffic": traffic, "traffic_source": traffic_note,
+                "kernel": "trace_tiles_kernel", "kernel_ms": trace_ms,
+                "voxel_steps_per_launch": steps_per_scan,
+                "work_per_unit": "one counter update per voxel-step (sum |A_i| of the scan)",
+                "peak_source": "hd_probe_atomics shared-memory random-address rate, measured "
+                               "in this run (1024-thread blocks, xorshift addresses, best of 3)",
+                "sm_count": sms}
+    fields, _ = _profile_fields()
+    if fields and "executed thread instructions per voxel-step" in fields:
+        roofline["executed_thread_instructions_per_voxel_step"] = float(
+            fields["executed thread instructions per voxel-step"])
     atomic_roofline = {
         "ceilings_atomics_per_s": probes,
         "voxel_steps_per_s": vsteps,
-        "voxel_steps_over_smem_random_ceiling": vsteps / probes["smem_random"],
+        "voxel_steps_over_l2_random_ceiling": vsteps / probes["l2_random"],
         "runs_per_scan": runs,
         "voxels_per_run": steps_per_scan / runs if runs else None,
         "trace_smem_atomics_per_s": 2.0 * runs / (trace_ms * 1e-3),
         "trace_smem_atomics_over_smem_random_ceiling":
-            2.0 * runs / (trace_ms * 1e-3) / probes["smem_random"],
-        "probe": "hd_probe_atomics: 1024-thread blocks, xorshift addresses, best of 3"}
+            2.0 * runs / (trace_ms * 1e-3) / probes["smem_random"]}
 
     # prepare = ingest + plan + scatter (everything before the traversal)
     phases = {"prepare_ms": prof["ms_ingest"] / args.steps, "trace_ms": trace_ms,
@@ -1027,6 +1103,32 @@ def main():
                "d2h_bytes_per_step": 3 * g.n_voxels, "ms_per_step": dt * 1e3}
         s3.close()
 
+    # ---- the 48-scan mix: batched (one persistent launch, graph replay)
+    # against one scan at a time, and served (Poisson arrivals of streamed
+    # scans) with its time-to-hull percentiles
+    batched = serving = None
+    if mix_job is not None:
+        jobs, parts = mix_job[0], mix_parts
+        from paper_1402_1720_gb300 import synth as _synth
+        specs = _synth.batch_scan_specs(48, fraction=args.batch_fraction)
+        hosts = [_synth.Histories.concat([p for j, p in zip(jobs, parts) if j[0] == k])
+                 for k in range(48)]
+        del parts, mix_parts
+        b = measure_batched(args, specs, hosts, args.mix_steps, 2)
+        batched = {k: b[k] for k in ("workload", "total_histories", "steps", "ms",
+                                     "histories_per_s", "sequential_ms",
+                                     "sequential_histories_per_s", "speedup",
+                                     "gpu_launches_per_step", "tuning")}
+        batched["graph_replays"] = b["graph"]["graph_replays"]
+        sv = measure_serving(args, specs, hosts)
+        serving = {k: sv[k] for k in ("workload", "total_histories", "chunks", "load",
+                                      "client_threads", "p50_ms", "p99_ms", "max_ms",
+                                      "histories_per_s", "saturated_histories_per_s",
+                                      "sequential_histories_per_s",
+                                      "saturated_over_sequential")}
+        serving["server_launches"] = sv["server"]["launches"]
+        del hosts
+
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(args.cpu_seconds)
@@ -1046,6 +1148,7 @@ def main():
                 "per_method": per_method, "phases": phases,
                 "roofline": roofline, "atomic_roofline": atomic_roofline,
                 "cpu_baseline": cpu, "e2e": e2e,
+                "batched": batched, "serving": serving,
                 "gpu_launches": launches, "clocks": clocks}
         print(json.dumps(line), flush=True)
     scan.close()

@@ -152,9 +152,9 @@ HD_API const char *hd_last_cuda_error(void);
 HD_API hd_status hd_params_default(hd_params *out);
 
 /* Create a scan on the current CUDA device: validates geometry and
- * parameters, allocates the count volumes N (Eq. 3.4) and M (Eq. 3.9), the
- * carve mask for SC (Alg. 1 starts from all ones) and the output masks,
- * and zeroes them on the legacy default stream (synchronised before
+ * parameters, allocates the count volumes N (Eq. 3.4; also for SC alone,
+ * whose hull H_1 = [N = 0] of Eq. 3.3 is the carve of Alg. 1 written as a
+ * set difference) and M (Eq. 3.9) and the output masks, and zeroes them on the legacy default stream (synchronised before
  * return).  HD_ERR_RANGE for unsupported geometry, HD_ERR_ARG for bad
  * parameters (including wepl_miss_lt > wepl_hit_gt or a NaN cutoff). */
 HD_API hd_status hd_scan_create(const hd_geometry *geom, const hd_params *params, hd_scan **out);
@@ -163,8 +163,8 @@ HD_API hd_status hd_scan_create(const hd_geometry *geom, const hd_params *params
  * NULL is accepted. */
 HD_API hd_status hd_scan_destroy(hd_scan *scan);
 
-/* Zero the counts and statistics and restore the carve mask to all ones,
- * stream-ordered, so the scan can take a new acquisition. */
+/* Zero the counts and statistics, stream-ordered, so the scan can take a
+ * new acquisition. */
 HD_API hd_status hd_scan_reset(hd_scan *scan, void *stream);
 
 /* Size the scan's per-chunk scratch (records, tile pairs, job table) for
@@ -175,8 +175,8 @@ HD_API hd_status hd_scan_reserve(hd_scan *scan, int64_t n, void *stream);
 
 /* Add n proton histories (structure of arrays, float32, n entries each):
  * classify each (Eq. 3.1, Eq. 3.7), traverse the voxel set A_i of every
- * missed and hit history (Eq. 3.2) and accumulate N (Eq. 3.4), M (Eq. 3.9)
- * and, when SC runs without MSC, the SC carve (Alg. 1).  Counts stay
+ * missed and hit history (Eq. 3.2) and accumulate N (Eq. 3.4, which SC and
+ * MSC read) and M (Eq. 3.9).  Counts stay
  * resident on the device, so histories may arrive in any number of calls
  * (streamed per-angle chunks, Sec. 4 online mode) in any order; the result
  * depends only on the multiset of histories.  on_device = 0 takes host
@@ -258,9 +258,8 @@ HD_API hd_status hd_scan_get_tuning(hd_scan *scan, hd_tuning *out);
  * thresholds and statistics follow from the thick sets (the statistics'
  * voxel counts are the thick sets' sizes; runs and pairs_general stay 0).
  * k = 0 restores the thin paths.  Only before any histories (after create or
- * reset): HD_ERR_STATE otherwise; HD_ERR_RANGE for k outside [0, 16].  A scan
- * with SC and without MSC then counts N (H_1 = [N = 0]) instead of keeping a
- * carve mask; allocates the thick rays' difference arrays (about 16 bytes
+ * reset): HD_ERR_STATE otherwise; HD_ERR_RANGE for k outside [0, 16].
+ * Allocates the thick rays' difference arrays (about 16 bytes
  * per voxel).  When the scan's tiles are whole one-slice planes (the
  * default plan whenever a slice fits the shared-memory budget) the thick
  * sets are counted in the tiled traversal; otherwise each history is walked

@@ -109,7 +109,7 @@ struct hd_scan {
     hd::Cordic cordic{};
     int64_t V = 0;
     int64_t words = 0;
-    uint32_t *N = nullptr, *M = nullptr, *carve = nullptr;
+    uint32_t *N = nullptr, *M = nullptr;
     uint8_t *H1 = nullptr, *H2 = nullptr, *H3 = nullptr;
     uint32_t *bits_out = nullptr;
     unsigned long long *slice_key = nullptr;
@@ -205,7 +205,7 @@ void free_scan(hd_scan *s)
     drain_profile(s);
     for (cudaEvent_t e : s->event_pool) cudaEventDestroy(e);
 
-    void *ptrs[] = {s->N, s->M, s->carve, s->H1, s->H2, s->H3, s->bits_out, s->slice_key,
+    void *ptrs[] = {s->N, s->M, s->H1, s->H2, s->H3, s->bits_out, s->slice_key,
                     s->mt, s->slope, s->index, s->ctrl, s->rec_buf, s->staging,
                     s->compact_blocks, s->d_count, s->compact_out, s->pair_buf, s->jobs,
                     s->rows_scratch, s->rows_bits, s->thick_ws,
@@ -392,7 +392,6 @@ hd::ScanDesc make_desc(const hd_scan *s)
     d.ctrl = s->ctrl;
     d.N = s->N;
     d.M = s->M;
-    d.carve = s->carve;
     return d;
 }
 
@@ -438,8 +437,8 @@ hd_status stage_prepare(hd_scan *s, const hd::Inputs &in, int64_t n, cudaStream_
 // Records outside the tiled path, walked with global-memory updates.
 hd_status stage_global(hd_scan *s, int64_t n, cudaStream_t st)
 {
-    HD_CUDA(hd::launch_trace_global(records_of(s, n), s->ctrl, n, s->gq, s->N, s->M, s->carve,
-                                    0, s->sm_count, st));
+    HD_CUDA(hd::launch_trace_global(records_of(s, n), s->ctrl, n, s->gq, s->N, s->M, 0,
+                                    s->sm_count, st));
     s->launches += 1;
     return HD_OK;
 }
@@ -449,7 +448,6 @@ hd_status stage_reset(hd_scan *scan, cudaStream_t st)
     const size_t V = static_cast<size_t>(scan->V);
     if (scan->N) HD_CUDA(cudaMemsetAsync(scan->N, 0, sizeof(uint32_t) * V, st));
     if (scan->M) HD_CUDA(cudaMemsetAsync(scan->M, 0, sizeof(uint32_t) * V, st));
-    if (scan->carve) HD_CUDA(cudaMemsetAsync(scan->carve, 0xff, sizeof(uint32_t) * scan->words, st));
     HD_CUDA(cudaMemsetAsync(scan->ctrl, 0, sizeof(hd::Ctrl), st));
     return HD_OK;
 }
@@ -467,7 +465,6 @@ hd_status stage_finalize(hd_scan *scan, cudaStream_t st)
     a.sm_per_slice = scan->params.sm_per_slice;
     a.N = scan->N;
     a.M = scan->M;
-    a.carve = scan->carve;
     a.slice_key = scan->slice_key;
     a.mt = scan->mt;
     a.slope = scan->slope;
@@ -601,9 +598,9 @@ hd_status hd_scan_create(const hd_geometry *geom, const hd_params *params, hd_sc
             ok = false;
         }
     };
-    if (m & HD_MSC) alloc(reinterpret_cast<void **>(&s->N), sizeof(uint32_t) * V);
-    if ((m & HD_SC) && !(m & HD_MSC))
-        alloc(reinterpret_cast<void **>(&s->carve), sizeof(uint32_t) * s->words);
+    // SC and MSC both read N: H_1 = [N = 0] (Eq. 3.3, the carve of Alg. 1
+    // as a set difference) and Eq. 3.6
+    if (m & (HD_SC | HD_MSC)) alloc(reinterpret_cast<void **>(&s->N), sizeof(uint32_t) * V);
     if (m & HD_SM) {
         alloc(reinterpret_cast<void **>(&s->M), sizeof(uint32_t) * V);
         alloc(reinterpret_cast<void **>(&s->slice_key), sizeof(unsigned long long) * geom->nz);
@@ -968,18 +965,6 @@ hd_status hd_scan_set_thick(hd_scan *scan, int32_t k)
                 scan->thick_ws = nullptr;
                 return HD_ERR_NOMEM;
             }
-        }
-        // SC alone keeps a carve mask; thick rays count N instead, and
-        // H_1 = [N = 0] (the decision reads N whenever it exists)
-        if (!scan->N && (scan->params.methods & HD_SC)) {
-            if (cudaMalloc(&scan->N, sizeof(uint32_t) * static_cast<size_t>(scan->V)) !=
-                cudaSuccess) {
-                cudaGetLastError();
-                scan->N = nullptr;
-                return HD_ERR_NOMEM;
-            }
-            HD_CUDA(cudaMemset(scan->N, 0, sizeof(uint32_t) * static_cast<size_t>(scan->V)));
-            scan->desc_dirty = true;
         }
     }
     scan->thick_k = k;

@@ -84,12 +84,7 @@ __global__ void __launch_bounds__(256) decide_kernel(DecideArgs a)
     if (q >= plane) return;
     const int x = q % a.nx, y = q / a.nx;
     const int64_t v = static_cast<int64_t>(z) * plane + q;
-    if (a.methods & HD_SC) {
-        uint8_t h;
-        if (a.N != nullptr) h = a.N[v] == 0;
-        else h = (a.carve[v >> 5] >> (v & 31)) & 1u;
-        a.H1[v] = h;
-    }
+    if (a.methods & HD_SC) a.H1[v] = a.N[v] == 0;  // Eq. 3.3
     if (a.methods & HD_MSC) {
         const uint32_t n = a.N[v];
         uint32_t mn = n;

@@ -7,19 +7,10 @@
 namespace hd {
 namespace {
 
-// Global-memory voxel update of one history: count (atomic add) or SC carve.
+// Global-memory voxel update of one history: one atomic add into N or M.
 struct GlobalVisit {
-    uint32_t *vol;   // N or M (count mode)
-    uint32_t *bits;  // carve mask (carve mode, vol == nullptr)
-    __device__ __forceinline__ void operator()(uint32_t v) const
-    {
-        if (vol != nullptr) {
-            atomicAdd(vol + v, 1u);
-        } else {
-            const uint32_t w = v >> 5, b = 1u << (v & 31u);
-            if (__ldcg(bits + w) & b) atomicAnd(bits + w, ~b);
-        }
-    }
+    uint32_t *vol;  // N or M
+    __device__ __forceinline__ void operator()(uint32_t v) const { atomicAdd(vol + v, 1u); }
 };
 
 // The voxels of a segment clipped to one tile of tp (gi, go relative to the

@@ -85,7 +85,7 @@ struct Pairs {
 
 struct TileJob {
     int tile;   // tile id within its class
-    int cls;    // 0 missed (N or carve), 1 hit (M)
+    int cls;    // 0 missed (N), 1 hit (M)
     int start;  // pair range [start, end)
     int end;
 };
@@ -97,7 +97,7 @@ struct ScanDesc {
     Pairs pairs;
     const TileJob *jobs;
     Ctrl *ctrl;  // njobs of the scan (read) and its step counters (added to)
-    uint32_t *N, *M, *carve;
+    uint32_t *N, *M;
 };
 
 constexpr int kMaxBatch = 64;  // scans per batched traversal launch
@@ -129,7 +129,7 @@ cudaError_t launch_trace_tiles(const ScanDesc *descs, int nscans, int *job_count
 // Global-memory traversal of the records whose status is 2 (or of every
 // record when all_records is set).
 cudaError_t launch_trace_global(const Records &rec, Ctrl *ctrl, int64_t upper, const GeomQ &g,
-                                uint32_t *N, uint32_t *M, uint32_t *carve, int all_records,
+                                uint32_t *N, uint32_t *M, int all_records,
                                 int sm_count, cudaStream_t s);
 
 cudaError_t launch_classify(const float *wepl, int64_t n, float tau_l, float tau_h,
@@ -143,9 +143,8 @@ struct DecideArgs {
     int32_t nx, ny, nz;
     int32_t methods;
     int32_t nt, nbhd, sm_ge, sm_per_slice;
-    const uint32_t *N;       // may be null when MSC is off
-    const uint32_t *M;       // may be null when SM is off
-    const uint32_t *carve;   // SC carve bits (used when N is null)
+    const uint32_t *N;       // null when neither SC nor MSC is on
+    const uint32_t *M;       // null when SM is off
     unsigned long long *slice_key;  // nz entries (SM)
     uint32_t *mt, *slope;    // nz entries (SM)
     long long *index;        // nz entries (SM)

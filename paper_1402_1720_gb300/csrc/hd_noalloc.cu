@@ -153,7 +153,7 @@ extern "C" hd_status hd_accumulate_noalloc(const hd_geometry *geom, const hd_par
                               use_miss, use_hit, tp, rec, ctrl, nullptr, sm_count, s);
     if (e == cudaSuccess)
         e = hd::launch_trace_global(rec, ctrl, n, gq, use_miss ? N : nullptr,
-                                    use_hit ? M : nullptr, nullptr, 0, sm_count, s);
+                                    use_hit ? M : nullptr, 0, sm_count, s);
     if (e != cudaSuccess) {
         cudaGetLastError();
         return HD_ERR_CUDA;

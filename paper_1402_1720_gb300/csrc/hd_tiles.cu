@@ -1,7 +1,7 @@
 // Shared-memory privatised traversal: the grid is cut into tiles whose
 // counters fit in one block's shared memory, every (record, tile) pair is
 // walked with the exact traversal clipped to the tile, and each block adds
-// its private tile into N or M (or clears the SC carve bits) once per job.
+// its private tile into N or M once per job.
 //
 // Pipeline per chunk of histories (after ingest has counted pairs per tile):
 //   plan     exclusive scan of the tile counts -> cursors and a job table
@@ -238,26 +238,11 @@ __global__ void __launch_bounds__(kScatterThreads, 4) scatter_kernel(TilePlan tp
 // share a 32-bit word; each job covers at most 32767 pairs, so every
 // difference and every prefix sum stays inside int16 and a word read as
 // lo + 65536 hi decodes exactly even after carries between the halves.
-// In carve mode (SC without MSC) the arrays are bit masks instead and a run
-// clears its bits.
 
 __device__ __forceinline__ void load_lean(const Pairs &pairs, int idx, uint4 &a, uint4 &b)
 {
     a = __ldg(&pairs.v[2 * static_cast<size_t>(idx)]);
     b = __ldg(&pairs.v[2 * static_cast<size_t>(idx) + 1]);
-}
-
-__device__ __forceinline__ void bits_clear(uint32_t *bits, int e0, int e1)
-{
-    // clear bits e0..e1 inclusive
-    int w = e0 >> 5;
-    const int wl = e1 >> 5;
-    for (; w <= wl; ++w) {
-        const int b0 = w == (e0 >> 5) ? (e0 & 31) : 0;
-        const int b1 = w == wl ? (e1 & 31) : 31;
-        const uint32_t m = (b1 == 31 ? 0xffffffffu : ((2u << b1) - 1u)) & ~((1u << b0) - 1u);
-        if (bits[w] & m) atomicAnd(&bits[w], ~m);
-    }
 }
 
 // In-place inclusive prefix sums of int16 rows: `rows` rows of `len`
@@ -295,10 +280,9 @@ __device__ __forceinline__ void rows_prefix(int16_t *a, int rows, int len)
 // the block's counter *s_next.  Count mode adds +1 at a run's first voxel
 // and -1 just past its last one in the int16 difference arrays (x runs at
 // word 0, y runs at word arr_words; the -1 of a run that ends at its row's
-// end goes to the scratch word 2 arr_words); carve mode clears the run's
-// bits.  Adds the lane's runs to `runs` and returns the sum of its walks'
-// end counts (voxels = runs + ends, see lean_run).
-template <bool kCarve>
+// end goes to the scratch word 2 arr_words).  Adds the lane's runs to `runs`
+// and returns the sum of its walks' end counts (voxels = runs + ends, see
+// lean_run).
 __device__ __forceinline__ unsigned walk_job(uint32_t *tile, int arr_words, int dx, int dy,
                                              const Pairs &pairs, int start, int total, int refill,
                                              unsigned *s_next, unsigned &runs)
@@ -356,14 +340,10 @@ __device__ __forceinline__ unsigned walk_job(uint32_t *tile, int arr_words, int 
                 int rb, lo, hi;
                 active = lean_run(c, rb, lo, hi, ends);
                 ++runs;
-                if (!kCarve) {
-                    const int e0 = rb + lo, e1 = rb + hi + 1;
-                    atomicAdd(&tile[aoff + (e0 >> 1)], (e0 & 1) ? 65536u : 1u);
-                    atomicAdd(&tile[hi + 1 < nmaj ? aoff + (e1 >> 1) : scratch],
-                              (e1 & 1) ? 0xffff0000u : 0xffffffffu);
-                } else {
-                    bits_clear(tile + aoff, rb + lo, rb + hi);
-                }
+                const int e0 = rb + lo, e1 = rb + hi + 1;
+                atomicAdd(&tile[aoff + (e0 >> 1)], (e0 & 1) ? 65536u : 1u);
+                atomicAdd(&tile[hi + 1 < nmaj ? aoff + (e1 >> 1) : scratch],
+                          (e1 & 1) ? 0xffff0000u : 0xffffffffu);
                 if (!active) break;
             }
         }
@@ -402,7 +382,6 @@ __device__ __noinline__ void walk_fallback_lists(const ScanDesc *__restrict__ de
                 const bool miss = (b.w & 1u) == 0;
                 GlobalVisit v;
                 v.vol = miss ? N : M;
-                v.bits = d.carve;
                 const unsigned c = walk_tile_global(d.tp, gi, go, static_cast<int>(b.w >> 1), v);
                 sm = miss ? c : 0u;
                 sh = miss ? 0u : c;
@@ -457,7 +436,6 @@ __global__ void __launch_bounds__(kThreads, 1) trace_tiles_kernel(
         const Pairs pairs = d.pairs;
         uint32_t *const N = d.N;
         uint32_t *const M = d.M;
-        uint32_t *const carve = d.carve;
         const TileJob job = d.jobs[s_job - s_prefix[s_scan]];
         const int tix = job.tile % tp.ntx;
         const int tiy = (job.tile / tp.ntx) % tp.nty;
@@ -466,25 +444,20 @@ __global__ void __launch_bounds__(kThreads, 1) trace_tiles_kernel(
         const int dx = min(tp.tx, tp.nx - x0), dy = min(tp.ty, tp.ny - y0),
                   dz = min(tp.tz, tp.nz - z0);
         const int nvox = dx * dy * dz;
-        const bool carve_mode = job.cls == 0 && N == nullptr;
-        // two arrays of nvox int16 (count) or nvox bits (carve)
-        const int arr_words = carve_mode ? (nvox + 31) >> 5 : (nvox + 1) >> 1;
+        // two arrays of nvox int16
+        const int arr_words = (nvox + 1) >> 1;
         uint32_t *arrX = tile;
         uint32_t *arrY = tile + arr_words;
-        const uint32_t init = carve_mode ? 0xffffffffu : 0u;
-        for (int w = threadIdx.x; w < 2 * arr_words; w += blockDim.x) tile[w] = init;
+        for (int w = threadIdx.x; w < 2 * arr_words; w += blockDim.x) tile[w] = 0u;
         __syncthreads();
 
         const int total = job.end - job.start;
         unsigned runs = 0;
-        const unsigned ends =
-            carve_mode ? walk_job<true>(tile, arr_words, dx, dy, pairs, job.start, total, tp.refill,
-                                        &s_next, runs)
-                       : walk_job<false>(tile, arr_words, dx, dy, pairs, job.start, total, tp.refill,
-                                         &s_next, runs);
+        const unsigned ends = walk_job(tile, arr_words, dx, dy, pairs, job.start, total,
+                                       tp.refill, &s_next, runs);
         __syncthreads();
         uint32_t *vol = job.cls == 0 ? N : M;
-        if (!carve_mode) {
+        {
             // a word holds lo + 65536 hi (mod 2^32) after carries between the
             // halves: split it into two plain int16 values
             for (int wd = threadIdx.x; wd < 2 * arr_words; wd += blockDim.x) {
@@ -506,22 +479,6 @@ __global__ void __launch_bounds__(kThreads, 1) trace_tiles_kernel(
                 for (int lx = lane; lx < dx; lx += 32) {
                     const int v = X[row * dx + lx] + Y[(lx + dx * lz) * dy + ly];
                     if (v) atomicAdd(&vol[gbase + lx], static_cast<uint32_t>(v));
-                }
-            }
-        } else {
-            for (int row = warp; row < dy * dz; row += nwarps) {
-                const int ly = row % dy, lz = row / dy;
-                const long long gbase = x0 + static_cast<long long>(tp.nx) *
-                                                 ((y0 + ly) + static_cast<long long>(tp.ny) * (z0 + lz));
-                for (int lx = lane; lx < dx; lx += 32) {
-                    const int ex = row * dx + lx, ey = (lx + dx * lz) * dy + ly;
-                    const bool kept = ((arrX[ex >> 5] >> (ex & 31)) & 1u) &&
-                                      ((arrY[ey >> 5] >> (ey & 31)) & 1u);
-                    if (!kept) {
-                        const long long gv = gbase + lx;
-                        const uint32_t gb = 1u << (gv & 31);
-                        if (__ldcg(&carve[gv >> 5]) & gb) atomicAnd(&carve[gv >> 5], ~gb);
-                    }
                 }
             }
         }

@@ -1,11 +1,11 @@
 // Ingest (classification + fixed-point geometry + compaction) and the voxel
-// traversal that accumulates N, M and the SC carve.
+// traversal that accumulates N and M.
 //
 // Classification: Eq. 3.1 (missed, WEPL below the cutoff) and Eq. 3.7 (hit,
 // WEPL above the cutoff).  Path: the closed segment between entry and exit
 // (Sec. 2.1), A_i of Eq. 3.2 read with d_0 = 0 against half-open voxel
-// cubes.  Accumulation: N of Eq. 3.4 (Alg. 2), M of Eq. 3.9 (Alg. 3), the SC
-// carve of Alg. 1.
+// cubes.  Accumulation: N of Eq. 3.4 (Alg. 2; SC's H_1 = [N = 0] of Eq. 3.3
+// is the carve of Alg. 1 as a set difference), M of Eq. 3.9 (Alg. 3).
 //
 // The traversal is an exact integer DDA.  For the segment
 // P(t) = G_in + t D (grid coordinates with 16 fractional bits) the next
@@ -275,7 +275,7 @@ __global__ void __launch_bounds__(256, 4) ingest_kernel(Inputs in, int64_t n, Ge
 
 __global__ void __launch_bounds__(256) trace_global_kernel(Records rec, Ctrl *ctrl, GeomQ g,
                                                            uint32_t *N, uint32_t *M,
-                                                           uint32_t *carve, int all_records)
+                                                           int all_records)
 {
     const unsigned nm = ctrl->rec_miss, nh = ctrl->rec_hit;
     const int64_t total = static_cast<int64_t>(nm) + nh;
@@ -290,7 +290,6 @@ __global__ void __launch_bounds__(256) trace_global_kernel(Records rec, Ctrl *ct
         const int32_t go[3] = {rec.g[3][slot], rec.g[4][slot], rec.g[5][slot]};
         GlobalVisit v;
         v.vol = miss ? N : M;
-        v.bits = carve;
         const unsigned c = walk_all(gi, go, g.nx, g.ny, g.nz, v);
         if (miss) steps_m += c; else steps_h += c;
         ++taken;
@@ -343,14 +342,14 @@ cudaError_t launch_ingest(const Inputs &in, int64_t n, const GeomQ &g, const Cor
 }
 
 cudaError_t launch_trace_global(const Records &rec, Ctrl *ctrl, int64_t upper, const GeomQ &g,
-                                uint32_t *N, uint32_t *M, uint32_t *carve, int all_records,
+                                uint32_t *N, uint32_t *M, int all_records,
                                 int sm_count, cudaStream_t s)
 {
     if (upper <= 0) return cudaSuccess;
     int64_t blocks = (upper + 255) / 256;
     const int64_t cap_blocks = static_cast<int64_t>(sm_count) * 8;
     if (blocks > cap_blocks) blocks = cap_blocks;
-    trace_global_kernel<<<static_cast<unsigned>(blocks), 256, 0, s>>>(rec, ctrl, g, N, M, carve,
+    trace_global_kernel<<<static_cast<unsigned>(blocks), 256, 0, s>>>(rec, ctrl, g, N, M,
                                                                        all_records);
     return cudaGetLastError();
 }

@@ -292,17 +292,24 @@ def make_config(cid: int, seed: Optional[int] = None, noise_free: bool = False,
     return Workload(CONFIG_NAMES[cid], g, ph, h)
 
 
+def config3_chunk(k: int, seed: Optional[int] = None, fraction: float = 1.0,
+                  noise_free: bool = False) -> Histories:
+    """Chunk k (gantry angle 2k degrees) of config 3; each chunk has its own
+    seed, so chunks can be generated independently and in any order."""
+    base = SEED_BASE + 3 if seed is None else seed
+    per = max(1, int(round(550_000 * fraction)))
+    ang = np.arange(0, 360, 2)[k]
+    rng = np.random.Generator(np.random.PCG64([base, k]))
+    return make_histories(rng, geometry_for(3), head_phantom(), [ang], per, 141.5, 80.0,
+                          2.0, 0.01, 0.3, noise_free)
+
+
 def iter_config_chunks(cid: int, seed: Optional[int] = None, fraction: float = 1.0,
                        noise_free: bool = False) -> Iterator[Histories]:
     """Config 3 as per-angle chunks (the streamed acquisition of Sec. 4)."""
     assert cid == 3
-    base = SEED_BASE + cid if seed is None else seed
-    g = geometry_for(3)
-    ph = head_phantom()
-    per = max(1, int(round(550_000 * fraction)))
-    for k, ang in enumerate(np.arange(0, 360, 2)):
-        rng = np.random.Generator(np.random.PCG64([base, k]))
-        yield make_histories(rng, g, ph, [ang], per, 141.5, 80.0, 2.0, 0.01, 0.3, noise_free)
+    for k in range(180):
+        yield config3_chunk(k, seed, fraction, noise_free)
 
 
 BATCH_GRIDS = ((64, 64, 16), (128, 128, 32), (256, 256, 64))
@@ -348,6 +355,24 @@ def scan_histories(spec: ScanSpec, angle_range: Optional[Tuple[int, int]] = None
                                     _half_diag(g) + 1.0, g.nz * g.sz / 2,
                                     2.0, 0.01, 0.3))
     return Histories.concat(parts)
+
+
+def batch_scan_part(job: Tuple) -> Histories:
+    """Angles [a0, a1) of scan k of the 48-scan mix (`job` = (k, a0, a1) or
+    (k, a0, a1, fraction)): concatenating the parts of consecutive angle
+    ranges gives scan_histories(batch_scan_specs(48, fraction=fraction)[k]),
+    so a scan can be generated in pieces by several processes."""
+    k, a0, a1 = job[:3]
+    fraction = job[3] if len(job) > 3 else 1.0
+    return scan_histories(batch_scan_specs(48, fraction=fraction)[k], angle_range=(a0, a1))
+
+
+def batch_scans_parallel(pool, fraction: float = 1.0, step: int = 10) -> List[Histories]:
+    """All 48 scans of the mix, generated by `pool` (a multiprocessing pool)
+    in pieces of `step` angles; identical to scan_histories of each spec."""
+    jobs = [(k, a, min(90, a + step), fraction) for k in range(48) for a in range(0, 90, step)]
+    parts = pool.map(batch_scan_part, jobs)
+    return [Histories.concat([p for j, p in zip(jobs, parts) if j[0] == k]) for k in range(48)]
 
 
 def tiny_random_case(rng: np.random.Generator, n: int, geom: Geometry,

@@ -3,7 +3,6 @@
 Everything here is integer work, so the bar is bit-exactness: counts N and M,
 masks H1/H2/H3, SM thresholds and the statistics must equal the oracle's.
 """
-import threading
 
 import numpy as np
 import pytest
@@ -333,107 +332,6 @@ def test_api_errors(hd):
         with pytest.raises(hd.HDError) as e:
             hd.hd_scan_get_mask(s.handle, hd.HD_SM, hd.HD_MASK_U8, np.zeros(10, np.uint8))
         assert e.value.status == hd.HD_ERR_ARG
-
-
-def test_config2_full_size_sampled(hd, oracle_mod):
-    """The benchmark workload (config 2, 9e6 histories, one add call as the
-    benchmark issues it): decisions re-derived by the oracle from the GPU
-    counts, single voxels counted by the oracle over all histories, sum and
-    classification identities, and an exact oracle comparison on a 3% sample."""
-    w = synth.make_config(2)
-    g, h = w.geometry, w.histories
-    got = _run_gpu(hd, g, h)
-    st = got["stats"]
-    # classification counts straight from the float compares
-    assert st["n_miss"] == int((h.wepl < 1.0).sum())
-    assert st["n_hit"] == int((h.wepl > 5.0).sum())
-    assert st["n_in"] == len(h) and st["n_reject"] == 0
-    assert int(got["N"].sum(dtype=np.int64)) == st["steps_miss"]
-    assert int(got["M"].sum(dtype=np.int64)) == st["steps_hit"]
-    dims = (g.nx, g.ny, g.nz)
-    assert np.array_equal(got["H1"], oracle_mod.sc_from_counts(got["N"]))
-    assert np.array_equal(got["H2"], oracle_mod.msc_decide(got["N"], dims))
-    sm = oracle_mod.sm_decide(got["M"], dims)
-    for k in ["H3", "Mt", "slope", "index"]:
-        assert np.array_equal(got[k], sm[k]), k
-    # single voxels: near the head outline, inside and outside
-    rng = np.random.default_rng(2)
-    picks = [(100, 100, 16), (100, 10, 16), (28, 100, 5), (172, 100, 27),
-             (int(rng.integers(200)), int(rng.integers(200)), int(rng.integers(32)))]
-    res = {}
-
-    def work(key, cls, x, y, z):
-        res[key] = oracle_mod.count_through_voxel(g, h, cls, x, y, z)
-
-    ths = [threading.Thread(target=work, args=((p, c), c) + p) for p in picks for c in (1, 2)]
-    for t in ths:
-        t.start()
-    for t in ths:
-        t.join()
-    for (p, c), val in res.items():
-        v = p[0] + g.nx * (p[1] + g.ny * p[2])
-        assert (got["N"] if c == 1 else got["M"])[v] == val, (p, c)
-    # exact comparison on a sample of the same workload
-    sub = h.take(np.arange(0, len(h), 33))
-    ref = oracle_mod.run(g, sub, threads=16)
-    got_sub = _run_gpu(hd, g, sub)
-    _assert_same(got_sub, ref, ALL)
-    _assert_stats(got_sub, ref)
-
-
-def test_config3_streamed_sampled(hd, oracle_mod):
-    """The large streamed workload (400x400x128 voxels of 0.5x0.5x1.25 mm,
-    180 angles x 550000 histories, one add call per angle as acquired, Sec. 4
-    online mode): decisions re-derived by the oracle from the GPU counts,
-    single voxels counted by the oracle over every history, sum and
-    classification identities, and an exact oracle comparison on a 1%
-    sample of every angle."""
-    from concurrent.futures import ThreadPoolExecutor
-    g = synth.geometry_for(3)
-    picks = [(200, 200, 64), (60, 200, 64), (200, 30, 40), (340, 260, 100)]
-    totals = {(p, c): 0 for p in picks for c in (1, 2)}
-    n_miss = n_hit = n_all = 0
-    samples = []
-    pool = ThreadPoolExecutor(max_workers=8)
-    futs = []
-    with hd.Scan(g) as s:
-        for chunk in synth.iter_config_chunks(3):
-            s.add([torch.from_numpy(a).cuda() for a in chunk.arrays()])
-            n_all += len(chunk)
-            n_miss += int((chunk.wepl < 1.0).sum())
-            n_hit += int((chunk.wepl > 5.0).sum())
-            samples.append(chunk.take(np.arange(0, len(chunk), 100)))
-            for p in picks:
-                for c in (1, 2):
-                    futs.append(((p, c), pool.submit(oracle_mod.count_through_voxel, g, chunk,
-                                                     c, *p)))
-        s.finalize()
-        torch.cuda.synchronize()
-        st = s.stats()
-        N, M = s.counts(hd.HD_MSC), s.counts(hd.HD_SM)
-        H1, H2, H3 = s.mask(hd.HD_SC), s.mask(hd.HD_MSC), s.mask(hd.HD_SM)
-        mt, slope, index = s.thresholds()
-    for key, f in futs:
-        totals[key] += f.result()
-    pool.shutdown()
-    assert st["n_in"] == n_all == 180 * 550_000
-    assert st["n_miss"] == n_miss and st["n_hit"] == n_hit and st["n_reject"] == 0
-    assert int(N.sum(dtype=np.int64)) == st["steps_miss"]
-    assert int(M.sum(dtype=np.int64)) == st["steps_hit"]
-    for (p, c), val in totals.items():
-        v = p[0] + g.nx * (p[1] + g.ny * p[2])
-        assert (N if c == 1 else M)[v] == val, (p, c)
-    dims = (g.nx, g.ny, g.nz)
-    assert np.array_equal(H1, oracle_mod.sc_from_counts(N))
-    assert np.array_equal(H2, oracle_mod.msc_decide(N, dims))
-    sm = oracle_mod.sm_decide(M, dims)
-    assert np.array_equal(H3, sm["H3"]) and np.array_equal(mt, sm["Mt"])
-    assert np.array_equal(index, sm["index"])
-    sub = synth.Histories.concat(samples)
-    ref = oracle_mod.run(g, sub, threads=16)
-    got = _run_gpu(hd, g, sub)
-    _assert_same(got, ref, ALL)
-    _assert_stats(got, ref)
 
 
 @pytest.mark.parametrize("setting", [

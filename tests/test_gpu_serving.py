@@ -62,8 +62,13 @@ def scans_case():
     return [(sp, h, _chunks(h, rng)) for sp in specs for h in [synth.scan_histories(sp)]]
 
 
-def test_served_equals_alone(hd, scans_case):
+def test_served_equals_alone(hd, oracle_mod, scans_case):
+    """Every served scan equals the same scan run alone and the oracle."""
     refs = [_alone(hd, sp.geometry, h) for sp, h, _ in scans_case]
+    for (sp, h, _), ref in zip(scans_case, refs):
+        orc = oracle_mod.run(sp.geometry, h, threads=8)
+        for k in ref:
+            assert np.array_equal(ref[k], orc[k]), k
     with hd.Server() as srv:
         ids = [srv.open_scan(sp.geometry, None, len(ch)) for sp, _, ch in scans_case]
         # chunks alternate between pageable numpy arrays, page-locked host
