@@ -337,11 +337,12 @@ void make_tile_plan(hd_scan *s)
 {
     hd::TilePlan &tp = s->tp;
     const int nx = s->geom.nx, ny = s->geom.ny, nz = s->geom.nz;
-    const int budget = hd::kTileSmemBytes / 4 - 2;  // two int16 arrays and a scratch word
+    // one word per voxel of a tile box padded by a column and a row
+    const int budget = hd::kTileSmemBytes / 4;
     tp.nx = nx;
     tp.ny = ny;
     tp.nz = nz;
-    const int64_t plane = int64_t(nx) * ny;
+    const int64_t plane = int64_t(nx + 1) * (ny + 1);
     if (plane <= budget) {
         // slabs of one z-slice by default: walks inside them never cross z, so
         // nearly all of them have the closed-form (lean) runs; deeper slabs
@@ -357,7 +358,7 @@ void make_tile_plan(hd_scan *s)
         tp.tz = (nz + ntz - 1) / ntz;
     } else {
         tp.tx = nx;
-        tp.ty = budget / nx;
+        tp.ty = budget / (nx + 1) - 1;
         const int nty = (ny + tp.ty - 1) / tp.ty;
         tp.ty = (ny + nty - 1) / nty;
         tp.tz = 1;
@@ -371,9 +372,9 @@ void make_tile_plan(hd_scan *s)
     tp.job_size = s->tuning.job_size;  // <= 32767: int16 differences in the tiled traversal
     tp.refill = s->tuning.refill;
     tp.threads = s->tuning.threads;
-    // two int16 difference arrays per tile (x runs and y runs) and a
-    // scratch word for the -1 of runs that end at their row's end
-    tp.tile_words = 2 * ((tp.tx * tp.ty * tp.tz + 1) / 2) + 1;
+    // one 32-bit word per voxel (x-run and y-run difference counts in its
+    // two halves), plus a padding column and row for the ends of runs
+    tp.tile_words = (tp.tx + 1) * (tp.ty + 1) * tp.tz;
     auto magic = [](int t) {
         return t == 1 ? 0u : static_cast<unsigned>((1ull << 32) / static_cast<unsigned>(t)) + 1u;
     };
@@ -885,6 +886,11 @@ hd_status hd_scan_get_stats(hd_scan *scan, hd_stats *out, void *stream)
     if (!g.ok) return HD_ERR_CUDA;
     hd::Ctrl c;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
+    // voxel memberships: sum_v N(v) = sum over missed histories of |A_i|
+    // (Eq. 3.4), likewise M for the hit ones, so no traversal kernel counts
+    // them
+    HD_CUDA(hd::launch_volume_sums(scan->N, scan->M, scan->V, &scan->ctrl->steps_miss,
+                                   scan->sm_count, st));
     HD_CUDA(cudaMemcpyAsync(&c, scan->ctrl, sizeof(c), cudaMemcpyDeviceToHost, st));
     HD_CUDA(cudaStreamSynchronize(st));
     out->n_in = static_cast<int64_t>(c.n_in);

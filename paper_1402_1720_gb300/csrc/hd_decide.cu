@@ -199,7 +199,43 @@ __global__ void __launch_bounds__(kCompactBlock) compact_write_kernel(const uint
     }
 }
 
+// Sums of the two count volumes (64-bit, exact): grid-stride, four words
+// per thread and step, a warp reduction and one atomic per warp and volume.
+__global__ void __launch_bounds__(256) volume_sums_kernel(const uint32_t *__restrict__ N,
+                                                          const uint32_t *__restrict__ M,
+                                                          int64_t V, unsigned long long *out)
+{
+    unsigned long long sn = 0, sm = 0;
+    const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+    for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < V;
+         i += stride) {
+        if (N) sn += N[i];
+        if (M) sm += M[i];
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        sn += __shfl_xor_sync(0xffffffffu, sn, o);
+        sm += __shfl_xor_sync(0xffffffffu, sm, o);
+    }
+    if ((threadIdx.x & 31u) == 0) {
+        if (sn) atomicAdd(&out[0], sn);
+        if (sm) atomicAdd(&out[1], sm);
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_volume_sums(const uint32_t *N, const uint32_t *M, int64_t V,
+                               unsigned long long *out, int sm_count, cudaStream_t s)
+{
+    cudaError_t e = cudaMemsetAsync(out, 0, 2 * sizeof(unsigned long long), s);
+    if (e != cudaSuccess || V <= 0 || (!N && !M)) return e;
+    int64_t blocks = (V + 255) / 256;
+    const int64_t cap = static_cast<int64_t>(sm_count > 0 ? sm_count : 1) * 4;
+    if (blocks > cap) blocks = cap;
+    volume_sums_kernel<<<static_cast<unsigned>(blocks), 256, 0, s>>>(N, M, V, out);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_finalize(const DecideArgs &a, int sm_count, cudaStream_t s)
 {

@@ -930,6 +930,82 @@ HD_HD bool lean_step(LeanWalk &L, int &row, int &lo, int &hi, unsigned &steps)
     return true;
 }
 
+// The tiled traversal's form of a lean walk: the same runs as lean_run, as
+// byte offsets into a tile box of dx x dy x dz voxels stored one 32-bit
+// word per voxel, x fastest, with one padding column and one padding row:
+// word(x, y, z) = x + Wx (y + Hy z), Wx = dx + 1, Hy = dy + 1.  A run adds
+// inc (1 for runs along x, 65536 for runs along y: the two halves of a
+// word) at its first voxel and subtracts it just past its last one, which
+// for a run ending at the box's edge lies in the padding.  The row base and
+// the major position are kept as byte offsets, so a run costs a few
+// integer steps.
+struct TileCursor {
+    unsigned ad, Ru, rem;  // Bresenham state of minor 0 (as in LeanWalk)
+    int jn, Qu, kmz, kleft;
+    int m0b;    // byte offset of the first voxel's major index within its row
+    int sgm;    // signed bytes per major step
+    int mstep;  // bytes per major step (4 along x, 4 Wx along y)
+    int msb;    // byte offset of the current run's start within its row
+    int rowb;   // byte offset of the current row's major index 0
+    int rstep;  // change of rowb per minor-0 crossing
+    uint32_t inc;  // 1 (x runs) or 65536 (y runs)
+};
+
+// Start a packed lean walk (lean_pack's form) in a box of dx x dy x dz
+// voxels; false for an empty walk.
+HD_HD bool tile_cursor_start(const uint32_t o[kLeanWords], int dx, int dy, int dz, TileCursor &c)
+{
+    const int fl = static_cast<int>(o[5] >> 16);
+    const bool ymaj = (fl >> 2) & 1;
+    const int Wx = dx + 1, Hy = dy + 1;
+    c.ad = o[0];
+    c.Ru = o[1];
+    c.rem = o[2];
+    c.jn = static_cast<int>(o[3] & 0xffffu);
+    c.Qu = static_cast<int>(o[3] >> 16);
+    c.kmz = static_cast<int>(o[4] & 0xffffu);
+    c.kleft = static_cast<int>(o[4] >> 16);
+    const int im0 = static_cast<int>(o[5] & 0xffffu);
+    // the row in the major axis' layout of the box: x-major y + dy z,
+    // y-major x + dx z; a lean walk never changes z
+    const int row = static_cast<int>(o[6]);
+    const int nminor = ymaj ? dx : dy;
+    const int z = dz == 1 ? 0 : row / nminor;
+    const int a = row - z * nminor;  // the minor-0 index (y for x-major, x for y-major)
+    c.mstep = ymaj ? 4 * Wx : 4;
+    c.sgm = (fl & 1) ? c.mstep : -c.mstep;
+    c.m0b = im0 * c.mstep;
+    c.msb = c.m0b;
+    c.rowb = ymaj ? 4 * (a + Wx * Hy * z) : 4 * Wx * (a + Hy * z);
+    const int rs = ymaj ? 4 : 4 * Wx;
+    c.rstep = (fl & 2) ? rs : -rs;
+    c.inc = ymaj ? 65536u : 1u;
+    return !((fl >> 3) & 1);
+}
+
+// The current run: `plus` and `minus` receive the byte offsets where inc is
+// added and subtracted.  Returns whether more runs follow.  Past its last
+// run the cursor holds kleft = (crossings left at the start) - (runs walked).
+HD_HD bool tile_cursor_run(TileCursor &c, int &plus, int &minus)
+{
+    const int jn = c.jn;
+    const int e = jn < c.kmz ? jn : c.kmz;
+    const int b = c.m0b + c.sgm * e;
+    const int lo = c.msb < b ? c.msb : b;
+    const int hi = c.msb < b ? b : c.msb;
+    plus = c.rowb + lo;
+    minus = c.rowb + hi + c.mstep;
+    const bool last = c.kleft == 0 || jn > c.kmz;
+    c.msb = b;  // the next run starts where this one ends (in the next row)
+    const unsigned rem = c.rem + c.Ru;
+    const bool carry = rem >= c.ad;
+    c.rem = carry ? rem - c.ad : rem;
+    c.jn = jn + c.Qu + (carry ? 1 : 0);
+    --c.kleft;
+    c.rowb += c.rstep;
+    return !last;
+}
+
 // Packed run-walk state: 16 32-bit words, so a walk prepared by one kernel
 // can be resumed by another.  The row strides and the major size follow
 // from the box (nx, ny) and the flags.

@@ -153,6 +153,12 @@ struct DecideArgs {
 
 cudaError_t launch_finalize(const DecideArgs &a, int sm_count, cudaStream_t s);
 
+// sum_v N(v) and sum_v M(v) (each 0 when its volume is null) into out[0],
+// out[1]: by Eq. 3.4 and 3.9 these are the sums of |A_i| over the missed and
+// the hit histories, the voxel memberships the statistics report.
+cudaError_t launch_volume_sums(const uint32_t *N, const uint32_t *M, int64_t V,
+                               unsigned long long *out, int sm_count, cudaStream_t s);
+
 cudaError_t launch_pack_bits(const uint8_t *mask, int64_t V, uint32_t *bits, cudaStream_t s);
 
 // Compaction: writes ascending indices of mask != 0 to out (if count fits

@@ -230,14 +230,7 @@ __global__ void __launch_bounds__(kThickThreads) thick_records_kernel(Records re
         thick_walk_all(wk, ymaj ? g.nx : g.ny, ymaj ? g.ny : g.nx, 0, k, (wk.flags & 2) ? 1 : -1,
                        ymaj ? td.dy[cls] : td.dx[cls], rg, vox[cls]);
     }
-#pragma unroll
-    for (int c = 0; c < 2; ++c) {
-        unsigned long long e = vox[c];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) e += __shfl_xor_sync(0xffffffffu, e, o);
-        if ((threadIdx.x & 31) == 0 && e != 0)
-            atomicAdd(c == 0 ? &ctrl->steps_miss : &ctrl->steps_hit, e);
-    }
+    (void)ctrl;  // voxel memberships are read from the counts (sum of N, M)
 }
 
 __global__ void __launch_bounds__(kThickThreads) thick_rows_kernel(

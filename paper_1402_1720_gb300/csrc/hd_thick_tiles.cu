@@ -200,14 +200,6 @@ __device__ __noinline__ void thick_fallback(const ScanDesc *__restrict__ dp, int
                                vox[cls]);
             }
         }
-        unsigned long long a0 = vox[0], a1 = vox[1];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            a0 += __shfl_xor_sync(kAllLanes, a0, o);
-            a1 += __shfl_xor_sync(kAllLanes, a1, o);
-        }
-        if (lane == 0 && a0) atomicAdd(&d.ctrl->steps_miss, a0);
-        if (lane == 0 && a1) atomicAdd(&d.ctrl->steps_hit, a1);
     }
 }
 
@@ -266,10 +258,6 @@ __global__ void __launch_bounds__(kThreads, 1) trace_thick_kernel(const ScanDesc
                 if (v) atomicAdd(&vol[gbase + lx], static_cast<uint32_t>(v));
             }
         }
-        unsigned long long st = vox;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) st += __shfl_xor_sync(kAllLanes, st, o);
-        if (lane == 0 && st) atomicAdd(job.cls == 0 ? &d.ctrl->steps_miss : &d.ctrl->steps_hit, st);
         __syncthreads();
     }
     thick_fallback(dp, k, td);

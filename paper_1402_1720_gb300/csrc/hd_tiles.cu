@@ -230,14 +230,20 @@ __global__ void __launch_bounds__(kScatterThreads, 4) scatter_kernel(TilePlan tp
 
 // ---------------------------------------------------------------- traversal
 //
-// A block's private tile holds two arrays of int16 difference counts over
-// the tile's voxels: one laid out x-fastest for runs along x, one
-// y-fastest for runs along y (z-fastest runs are never formed: z is always
-// a minor axis).  A run lo..hi of a row adds +1 at lo and -1 at hi + 1; the
-// flush takes prefix sums along the rows and adds the two arrays.  Two int16
-// share a 32-bit word; each job covers at most 32767 pairs, so every
-// difference and every prefix sum stays inside int16 and a word read as
-// lo + 65536 hi decodes exactly even after carries between the halves.
+// A block's private tile holds one 32-bit word per voxel of the tile box,
+// laid out x fastest with one padding column and one padding row:
+// word(x, y, z) = x + Wx (y + Hy z), Wx = dx + 1, Hy = dy + 1.  Its low
+// 16 bits are the difference counts of runs along x, its high 16 bits those
+// of runs along y (z is never a run axis: it is always a minor one).  A run
+// lo..hi adds +1 (x runs) or +65536 (y runs) at its first voxel and the
+// negative just past its last one, which for a run ending at the box's edge
+// is the padding column or row, so no run needs a bounds test.  Each job
+// covers at most 32767 pairs, so every difference and every prefix sum of
+// either half stays inside int16, and a word read as lo + 65536 hi (mod
+// 2^32) decodes exactly even after carries between the halves.  Rows of
+// words are an odd number of words apart (for the 200-voxel planes here),
+// so lanes walking parallel paths at the same major index hit distinct
+// banks.
 
 __device__ __forceinline__ void load_lean(const Pairs &pairs, int idx, uint4 &a, uint4 &b)
 {
@@ -245,31 +251,9 @@ __device__ __forceinline__ void load_lean(const Pairs &pairs, int idx, uint4 &a,
     b = __ldg(&pairs.v[2 * static_cast<size_t>(idx) + 1]);
 }
 
-// In-place inclusive prefix sums of int16 rows: `rows` rows of `len`
-// elements, one warp per row.
-__device__ __forceinline__ void rows_prefix(int16_t *a, int rows, int len)
+__device__ __forceinline__ void tile_add(char *tile, int byte_off, uint32_t v)
 {
-    const unsigned lane = threadIdx.x & 31u;
-    const int warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    const int chunk = (len + 31) >> 5;
-    for (int r = warp; r < rows; r += nw) {
-        int16_t *row = a + static_cast<long long>(r) * len;
-        const int b = lane * chunk;
-        const int e = min(b + chunk, len);
-        int acc = 0;
-        for (int i = b; i < e; ++i) acc += row[i];
-        int incl = acc;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int t = __shfl_up_sync(kFull, incl, o);
-            if (lane >= static_cast<unsigned>(o)) incl += t;
-        }
-        int run = incl - acc;
-        for (int i = b; i < e; ++i) {
-            run += row[i];
-            row[i] = static_cast<int16_t>(run);
-        }
-    }
+    atomicAdd(reinterpret_cast<uint32_t *>(tile + byte_off), v);
 }
 
 // Walks the pairs [start, start + total) of a job into the block's tile:
@@ -277,23 +261,14 @@ __device__ __forceinline__ void rows_prefix(int16_t *a, int rows, int len)
 // (loaded a refill ahead, so starting a walk never waits on memory).  A
 // refill happens once enough lanes are idle; then every idle lane with a
 // prefetched pair starts it and fetches another, the pair index coming from
-// the block's counter *s_next.  Count mode adds +1 at a run's first voxel
-// and -1 just past its last one in the int16 difference arrays (x runs at
-// word 0, y runs at word arr_words; the -1 of a run that ends at its row's
-// end goes to the scratch word 2 arr_words).  Adds the lane's runs to `runs`
-// and returns the sum of its walks' end counts (voxels = runs + ends, see
-// lean_run).
-__device__ __forceinline__ unsigned walk_job(uint32_t *tile, int arr_words, int dx, int dy,
-                                             const Pairs &pairs, int start, int total, int refill,
-                                             unsigned *s_next, unsigned &runs)
+// the block's counter *s_next.  Adds the runs walked to `runs`.
+__device__ __forceinline__ void walk_job(char *tile, int dx, int dy, int dz, const Pairs &pairs,
+                                         int start, int total, int refill, unsigned *s_next,
+                                         unsigned &runs)
 {
     const unsigned lane = threadIdx.x & 31u;
-    const int scratch = 2 * arr_words;
-    LeanCursor c;
+    TileCursor c;
     bool active = false;
-    int nmaj = 0;
-    int aoff = 0;  // word offset in `tile` of the current walk's array
-    unsigned ends = 0;
     uint4 na = make_uint4(0, 0, 0, 0), nb = na;
     int nidx = -1;
     {
@@ -313,10 +288,10 @@ __device__ __forceinline__ unsigned walk_job(uint32_t *tile, int arr_words, int 
         if (want != 0 && (__popc(want) >= static_cast<unsigned>(refill) || busy == 0)) {
             if (!active && nidx >= 0) {
                 const uint32_t o[kLeanWords] = {na.x, na.y, na.z, na.w, nb.x, nb.y, nb.z, nb.w};
-                const bool ymaj = (o[5] >> 18) & 1u;  // LeanWalk::fl bit 2
-                nmaj = ymaj ? dy : dx;
-                aoff = ymaj ? arr_words : 0;
-                active = lean_start(o, nmaj, c);
+                active = tile_cursor_start(o, dx, dy, dz, c);
+                // runs of a walk = its minor-0 crossings left at the start
+                // minus those left after its last run (see tile_cursor_run)
+                if (active) runs += static_cast<unsigned>(c.kleft);
                 nidx = -1;
             }
             unsigned base = 0;
@@ -334,21 +309,103 @@ __device__ __forceinline__ unsigned walk_job(uint32_t *tile, int arr_words, int 
         }
         if (active) {
             // up to kRunsPerStep runs before the warp checks for refills again
-            // (the refill test costs as much as a run)
+            // (the refill test costs about as much as a run)
 #pragma unroll
             for (int u = 0; u < kRunsPerStep; ++u) {
-                int rb, lo, hi;
-                active = lean_run(c, rb, lo, hi, ends);
-                ++runs;
-                const int e0 = rb + lo, e1 = rb + hi + 1;
-                atomicAdd(&tile[aoff + (e0 >> 1)], (e0 & 1) ? 65536u : 1u);
-                atomicAdd(&tile[hi + 1 < nmaj ? aoff + (e1 >> 1) : scratch],
-                          (e1 & 1) ? 0xffff0000u : 0xffffffffu);
-                if (!active) break;
+                int plus, minus;
+                active = tile_cursor_run(c, plus, minus);
+                tile_add(tile, plus, c.inc);
+                tile_add(tile, minus, 0u - c.inc);
+                if (!active) {
+                    runs -= static_cast<unsigned>(c.kleft);
+                    break;
+                }
             }
         }
     }
-    return ends;
+}
+
+// Flush of a job's tile into vol (the scan's N or M) and zeroing of the
+// tile for the next job: (1) warps take rows, decode each word into two
+// plain int16 halves and prefix-sum the low halves along x; (2) warps take
+// columns and prefix-sum the high halves along y; (3) every voxel adds the
+// sum of its two halves to vol (one global atomic per nonzero voxel) and
+// every word, padding included, is cleared.
+__device__ __forceinline__ void flush_tile(uint32_t *tile, int dx, int dy, int dz, uint32_t *vol,
+                                           int nx, int ny, int x0, int y0, int z0)
+{
+    const unsigned lane = threadIdx.x & 31u;
+    const int warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    const int Wx = dx + 1, Hy = dy + 1;
+    // (1) rows along x: decode, then inclusive prefix of the low halves
+    {
+        const int chunk = (dx + 31) >> 5;
+        for (int r = warp; r < dy * dz; r += nwarps) {
+            const int y = r % dy, z = r / dy;
+            uint32_t *row = tile + Wx * (y + Hy * z);
+            const int b = lane * chunk;
+            const int e = min(b + chunk, dx);
+            int acc = 0;
+            for (int i = b; i < e; ++i) acc += static_cast<int16_t>(row[i] & 0xffffu);
+            int incl = acc;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int t = __shfl_up_sync(kFull, incl, o);
+                if (lane >= static_cast<unsigned>(o)) incl += t;
+            }
+            int run = incl - acc;
+            for (int i = b; i < e; ++i) {
+                const uint32_t w = row[i];
+                const int lo = static_cast<int16_t>(w & 0xffffu);
+                const int hi = static_cast<int>(w - static_cast<uint32_t>(lo)) >> 16;
+                run += lo;
+                row[i] = (static_cast<uint32_t>(run) & 0xffffu) | (static_cast<uint32_t>(hi) << 16);
+            }
+        }
+        // (the padding column and row are never read: step 3 clears them)
+    }
+    __syncthreads();
+    // (2) columns along y: inclusive prefix of the (decoded) high halves
+    {
+        const int chunk = (dy + 31) >> 5;
+        for (int col = warp; col < dx * dz; col += nwarps) {
+            const int x = col % dx, z = col / dx;
+            uint32_t *base = tile + x + Wx * Hy * z;
+            const int b = lane * chunk;
+            const int e = min(b + chunk, dy);
+            int acc = 0;
+            for (int i = b; i < e; ++i) acc += static_cast<int>(base[Wx * i]) >> 16;
+            int incl = acc;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int t = __shfl_up_sync(kFull, incl, o);
+                if (lane >= static_cast<unsigned>(o)) incl += t;
+            }
+            int run = incl - acc;
+            for (int i = b; i < e; ++i) {
+                const uint32_t w = base[Wx * i];
+                run += static_cast<int>(w) >> 16;
+                base[Wx * i] = (w & 0xffffu) | (static_cast<uint32_t>(run) << 16);
+            }
+        }
+    }
+    __syncthreads();
+    // (3) add to the volume and clear every word of the box
+    const int words = Wx * Hy * dz;
+    for (int wd = threadIdx.x; wd < words; wd += blockDim.x) {
+        const int x = wd % Wx, t = wd / Wx;
+        const int y = t % Hy, z = t / Hy;
+        const uint32_t w = tile[wd];
+        tile[wd] = 0u;
+        if (x < dx && y < dy) {
+            const int v = static_cast<int>(w & 0xffffu) + static_cast<int>(w >> 16);
+            if (v) {
+                const long long g = (x0 + x) + static_cast<long long>(nx) *
+                                                   ((y0 + y) + static_cast<long long>(ny) * (z0 + z));
+                atomicAdd(&vol[g], static_cast<uint32_t>(v));
+            }
+        }
+    }
 }
 
 // No job left: the pairs without a lean form (the fallback lists), walked
@@ -370,7 +427,6 @@ __device__ __noinline__ void walk_fallback_lists(const ScanDesc *__restrict__ de
             base = __shfl_sync(kFull, base, 0);
             if (base >= nf) break;
             const unsigned i = base + lane;
-            unsigned sm = 0, sh = 0;
             if (i < nf) {
                 const uint32_t pos = d.pairs.fb[i].x;
                 uint4 a, b;
@@ -379,36 +435,28 @@ __device__ __noinline__ void walk_fallback_lists(const ScanDesc *__restrict__ de
                                        static_cast<int32_t>(a.z)};
                 const int32_t go[3] = {static_cast<int32_t>(a.w), static_cast<int32_t>(b.x),
                                        static_cast<int32_t>(b.z)};
-                const bool miss = (b.w & 1u) == 0;
                 GlobalVisit v;
-                v.vol = miss ? N : M;
-                const unsigned c = walk_tile_global(d.tp, gi, go, static_cast<int>(b.w >> 1), v);
-                sm = miss ? c : 0u;
-                sh = miss ? 0u : c;
+                v.vol = (b.w & 1u) == 0 ? N : M;
+                walk_tile_global(d.tp, gi, go, static_cast<int>(b.w >> 1), v);
             }
-            unsigned long long a0 = sm, a1 = sh;
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                a0 += __shfl_xor_sync(kFull, a0, o);
-                a1 += __shfl_xor_sync(kFull, a1, o);
-            }
-            if (lane == 0 && a0) atomicAdd(&d.ctrl->steps_miss, a0);
-            if (lane == 0 && a1) atomicAdd(&d.ctrl->steps_hit, a1);
         }
     }
 }
 }
 
+// Persistent traversal: blocks take jobs (one tile's range of pairs) from
+// the job counter until none is left, walk them into their shared-memory
+// tile and flush it; then they walk the fallback lists.  max_words is the
+// largest tile of the scans (the dynamic shared memory of the launch).
 template <int kThreads>
 __global__ void __launch_bounds__(kThreads, 1) trace_tiles_kernel(
-    const ScanDesc *__restrict__ descs, int nscans, int *job_counter)
+    const ScanDesc *__restrict__ descs, int nscans, int *job_counter, int max_words)
 {
     extern __shared__ uint32_t tile[];
     __shared__ int s_job, s_scan;
     __shared__ unsigned s_next;
     __shared__ int s_prefix[kMaxBatch + 1];
     const unsigned lane = threadIdx.x & 31u;
-    const unsigned warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     // jobs of scan k are the global job numbers [s_prefix[k], s_prefix[k+1])
     if (threadIdx.x == 0) {
         int acc = 0;
@@ -418,6 +466,8 @@ __global__ void __launch_bounds__(kThreads, 1) trace_tiles_kernel(
         }
         s_prefix[nscans] = acc;
     }
+    // each flush clears its box: the tile starts cleared once
+    for (int w = threadIdx.x; w < max_words; w += blockDim.x) tile[w] = 0u;
     __syncthreads();
     const int total_jobs = s_prefix[nscans];
     for (;;) {
@@ -433,9 +483,6 @@ __global__ void __launch_bounds__(kThreads, 1) trace_tiles_kernel(
         if (s_job >= total_jobs) break;
         const ScanDesc &d = descs[s_scan];
         const TilePlan tp = d.tp;
-        const Pairs pairs = d.pairs;
-        uint32_t *const N = d.N;
-        uint32_t *const M = d.M;
         const TileJob job = d.jobs[s_job - s_prefix[s_scan]];
         const int tix = job.tile % tp.ntx;
         const int tiy = (job.tile / tp.ntx) % tp.nty;
@@ -443,60 +490,20 @@ __global__ void __launch_bounds__(kThreads, 1) trace_tiles_kernel(
         const int x0 = tix * tp.tx, y0 = tiy * tp.ty, z0 = tiz * tp.tz;
         const int dx = min(tp.tx, tp.nx - x0), dy = min(tp.ty, tp.ny - y0),
                   dz = min(tp.tz, tp.nz - z0);
-        const int nvox = dx * dy * dz;
-        // two arrays of nvox int16
-        const int arr_words = (nvox + 1) >> 1;
-        uint32_t *arrX = tile;
-        uint32_t *arrY = tile + arr_words;
-        for (int w = threadIdx.x; w < 2 * arr_words; w += blockDim.x) tile[w] = 0u;
-        __syncthreads();
-
-        const int total = job.end - job.start;
         unsigned runs = 0;
-        const unsigned ends = walk_job(tile, arr_words, dx, dy, pairs, job.start, total,
-                                       tp.refill, &s_next, runs);
+        walk_job(reinterpret_cast<char *>(tile), dx, dy, dz, d.pairs, job.start,
+                 job.end - job.start, tp.refill, &s_next, runs);
         __syncthreads();
-        uint32_t *vol = job.cls == 0 ? N : M;
-        {
-            // a word holds lo + 65536 hi (mod 2^32) after carries between the
-            // halves: split it into two plain int16 values
-            for (int wd = threadIdx.x; wd < 2 * arr_words; wd += blockDim.x) {
-                const uint32_t v = tile[wd];
-                const int lo = static_cast<int16_t>(v & 0xffffu);
-                const int hi = static_cast<int>(v - static_cast<uint32_t>(lo)) >> 16;
-                tile[wd] = (static_cast<uint32_t>(lo) & 0xffffu) | (static_cast<uint32_t>(hi) << 16);
-            }
-            __syncthreads();
-            rows_prefix(reinterpret_cast<int16_t *>(arrX), dy * dz, dx);
-            rows_prefix(reinterpret_cast<int16_t *>(arrY), dx * dz, dy);
-            __syncthreads();
-            const int16_t *X = reinterpret_cast<const int16_t *>(arrX);
-            const int16_t *Y = reinterpret_cast<const int16_t *>(arrY);
-            for (int row = warp; row < dy * dz; row += nwarps) {
-                const int ly = row % dy, lz = row / dy;
-                const long long gbase = x0 + static_cast<long long>(tp.nx) *
-                                                 ((y0 + ly) + static_cast<long long>(tp.ny) * (z0 + lz));
-                for (int lx = lane; lx < dx; lx += 32) {
-                    const int v = X[row * dx + lx] + Y[(lx + dx * lz) * dy + ly];
-                    if (v) atomicAdd(&vol[gbase + lx], static_cast<uint32_t>(v));
-                }
-            }
-        }
-        // voxel memberships of this job, added to its scan's counters
-        unsigned long long ru = runs, st = static_cast<unsigned long long>(ends) + runs;
+        flush_tile(tile, dx, dy, dz, job.cls == 0 ? d.N : d.M, tp.nx, tp.ny, x0, y0, z0);
+        // runs walked by this job, added to its scan's counter
+        unsigned long long ru = runs;
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            st += __shfl_xor_sync(kFull, st, o);
-            ru += __shfl_xor_sync(kFull, ru, o);
-        }
-        if (lane == 0 && st) atomicAdd(job.cls == 0 ? &d.ctrl->steps_miss : &d.ctrl->steps_hit, st);
+        for (int o = 16; o > 0; o >>= 1) ru += __shfl_xor_sync(kFull, ru, o);
         if (lane == 0 && ru) atomicAdd(&d.ctrl->runs, ru);
         __syncthreads();
     }
     walk_fallback_lists(descs, nscans);
-
-
-}  // namespace
+}
 
 cudaError_t launch_plan(const TilePlan &tp, const uint32_t *tile_count, uint32_t *tile_cursor,
                         TileJob *jobs, Ctrl *ctrl, int sm_count, cudaStream_t s)
@@ -565,16 +572,16 @@ cudaError_t launch_trace_tiles(const ScanDesc *descs, int nscans, int *job_count
     const size_t smem = static_cast<size_t>(smem_words) * 4;
     switch (threads) {
     case 256:
-        trace_tiles_kernel<256><<<grid, 256, smem, s>>>(descs, nscans, job_counter);
+        trace_tiles_kernel<256><<<grid, 256, smem, s>>>(descs, nscans, job_counter, smem_words);
         break;
     case 512:
-        trace_tiles_kernel<512><<<grid, 512, smem, s>>>(descs, nscans, job_counter);
+        trace_tiles_kernel<512><<<grid, 512, smem, s>>>(descs, nscans, job_counter, smem_words);
         break;
     case 768:
-        trace_tiles_kernel<768><<<grid, 768, smem, s>>>(descs, nscans, job_counter);
+        trace_tiles_kernel<768><<<grid, 768, smem, s>>>(descs, nscans, job_counter, smem_words);
         break;
     case 1024:
-        trace_tiles_kernel<1024><<<grid, 1024, smem, s>>>(descs, nscans, job_counter);
+        trace_tiles_kernel<1024><<<grid, 1024, smem, s>>>(descs, nscans, job_counter, smem_words);
         break;
     default: return cudaErrorInvalidValue;
     }

@@ -280,7 +280,7 @@ __global__ void __launch_bounds__(256) trace_global_kernel(Records rec, Ctrl *ct
     const unsigned nm = ctrl->rec_miss, nh = ctrl->rec_hit;
     const int64_t total = static_cast<int64_t>(nm) + nh;
     const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
-    unsigned steps_m = 0, steps_h = 0, taken = 0;
+    unsigned taken = 0;
     for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < total;
          i += stride) {
         const bool miss = i < nm;
@@ -290,17 +290,11 @@ __global__ void __launch_bounds__(256) trace_global_kernel(Records rec, Ctrl *ct
         const int32_t go[3] = {rec.g[3][slot], rec.g[4][slot], rec.g[5][slot]};
         GlobalVisit v;
         v.vol = miss ? N : M;
-        const unsigned c = walk_all(gi, go, g.nx, g.ny, g.nz, v);
-        if (miss) steps_m += c; else steps_h += c;
+        walk_all(gi, go, g.nx, g.ny, g.nz, v);
         ++taken;
     }
-    const unsigned sm_ = warp_sum_u32(steps_m), sh_ = warp_sum_u32(steps_h);
     const unsigned tk = warp_sum_u32(taken);
-    if ((threadIdx.x & 31u) == 0) {
-        if (sm_) atomicAdd(&ctrl->steps_miss, static_cast<unsigned long long>(sm_));
-        if (sh_) atomicAdd(&ctrl->steps_hit, static_cast<unsigned long long>(sh_));
-        if (tk && !all_records) atomicAdd(&ctrl->n_fallback, tk);
-    }
+    if ((threadIdx.x & 31u) == 0 && tk && !all_records) atomicAdd(&ctrl->n_fallback, tk);
 }
 
 __global__ void classify_kernel(const float *__restrict__ w, int64_t n, float tau_l, float tau_h,

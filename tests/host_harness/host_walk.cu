@@ -154,3 +154,56 @@ extern "C" int hx_runs_lean(const int32_t *gi, const int32_t *go, int nx, int ny
         if (!emit(ymaj, w.nmaj, row, lo, hi)) return -1000000;
     return n;
 }
+// the tiled traversal's byte-offset cursor on a lean walk in a box of
+// dx x dy x dz voxels: its +inc / -inc updates are applied to a copy of the
+// padded word layout (each half kept as a plain integer), decoded by prefix
+// sums along x (low halves) and y (high halves), and the voxels with a
+// nonzero count are returned as box-linear indices (x fastest).  Returns
+// -1 when the walk has no lean form, -5000000 when an offset falls outside
+// the box's words or is not word-aligned, -6000000 when a voxel is counted
+// other than once, -7000000 when the run count disagrees with the cursor.
+extern "C" int hx_tile_cursor(const int32_t *gi, const int32_t *go, int dx, int dy, int dz,
+                              int32_t *out, int cap, int *nruns)
+{
+    hd::RunWalk w;
+    *nruns = 0;
+    if (!hd::run_begin(w, gi, go, dx, dy, dz)) return 0;
+    hd::LeanWalk L;
+    if (!hd::lean_of(w, L)) return -1;
+    uint32_t o[hd::kLeanWords];
+    hd::lean_pack(L, o);
+    hd::TileCursor c;
+    if (!hd::tile_cursor_start(o, dx, dy, dz, c)) return 0;
+    const int Wx = dx + 1, Hy = dy + 1;
+    const long long words = (long long)Wx * Hy * dz;
+    std::vector<long long> lo(words, 0), hi(words, 0);
+    const int k0 = c.kleft;
+    int runs = 0;
+    bool more;
+    do {
+        int p, m;
+        more = hd::tile_cursor_run(c, p, m);
+        ++runs;
+        if (p < 0 || m < 0 || (p & 3) || (m & 3) || p / 4 >= words || m / 4 >= words) return -5000000;
+        if (c.inc == 1u) { lo[p / 4] += 1; lo[m / 4] -= 1; }
+        else { hi[p / 4] += 1; hi[m / 4] -= 1; }
+        if (runs > 100000) return -5000000;
+    } while (more);
+    if (k0 - c.kleft != runs) return -7000000;
+    *nruns = runs;
+    int n = 0;
+    for (int z = 0; z < dz; ++z)
+        for (int y = 0; y < dy; ++y)
+            for (int x = 0; x < dx; ++x) {
+                long long sx = 0, sy = 0;
+                for (int i = 0; i <= x; ++i) sx += lo[i + (long long)Wx * (y + Hy * z)];
+                for (int j = 0; j <= y; ++j) sy += hi[x + (long long)Wx * (j + Hy * z)];
+                const long long v = sx + sy;
+                if (v != 0 && v != 1) return -6000000;
+                if (v) {
+                    if (n < cap) out[n] = x + dx * (y + dy * z);
+                    ++n;
+                }
+            }
+    return n;
+}

@@ -238,3 +238,42 @@ def test_lean_run_walk_nearly_axis_aligned(oracle_mod, hx):
                 n_lean += 1
                 assert steps == len(got)
     assert n_lean > 1000
+
+
+def _tile_cursor(L, a, b, dims):
+    L.hx_tile_cursor.restype = ctypes.c_int
+    out = np.zeros(int(np.prod(dims)) + 8, np.int32)
+    nr = ctypes.c_int(0)
+    n = L.hx_tile_cursor(np.asarray(a, np.int32).ctypes.data_as(I32P),
+                         np.asarray(b, np.int32).ctypes.data_as(I32P), *dims,
+                         out.ctypes.data_as(I32P), out.size, ctypes.byref(nr))
+    return n, np.sort(out[:max(n, 0)]), nr.value
+
+
+@pytest.mark.parametrize("dims", [(200, 200, 1), (41, 30, 1), (7, 1, 1), (1, 7, 1), (40, 30, 3),
+                                  (64, 3, 2)])
+def test_tile_cursor_equals_oracle(oracle_mod, hx, dims):
+    """The traversal's byte-offset form of a lean walk: its +1/-1 updates in
+    the padded one-word-per-voxel tile (x runs in the low halves, y runs in
+    the high halves) stay inside the box's words, and the prefix sums along
+    x and y give every voxel of the oracle's set exactly once and no other
+    voxel; its run count is what the kernel reports."""
+    rng = np.random.default_rng(sum(dims) + 29)
+    Q = 65536
+    hi = np.array(dims, np.int64) * Q
+    n_lean = 0
+    for k in range(1500):
+        a = rng.integers(-Q, hi + Q)
+        b = rng.integers(-Q, hi + Q)
+        if k % 2:
+            a[2] = rng.integers(0, hi[2])
+            b[2] = a[2] + rng.integers(-Q // 2, Q // 2 + 1)
+        n, got, runs = _tile_cursor(hx, a, b, dims)
+        assert n >= -1, (n, a.tolist(), b.tolist())
+        if n == -1:
+            continue
+        n_lean += 1
+        assert np.array_equal(got, oracle_mod.voxel_set(a, b, *dims)), (a.tolist(), b.tolist())
+        if n > 0:
+            assert 1 <= runs <= n
+    assert n_lean > 300
