@@ -235,9 +235,9 @@ HD_API hd_status hd_scan_get_hull_indices(hd_scan *scan, int32_t method, int32_t
 
 /* Launch parameters of the traversal, chosen per volume class by the
  * autotuner (paper_1402_1720_gb300/autotune.py) or left at their defaults:
- *   threads     threads per block of the traversal: 256, 512, 768 or 1024 (768)
- *   refill      idle lanes of a warp that trigger taking new walks, 1..32 (8)
- *   job_size    (record, tile) pairs per job, 256..32767 (16384)
+ *   threads     threads per block of the traversal: 256, 512, 768 or 1024 (1024)
+ *   refill      idle lanes of a warp that trigger taking new walks, 1..32 (12)
+ *   job_size    (record, tile) pairs per job, 256..32767 (32767)
  *   slab_depth  z-slices per shared-memory tile when whole x-y planes fit,
  *               at most as many as fit; 0 = one slice (0).  Walks that cross
  *               z inside a deeper slab take the general walk in global memory

@@ -15,7 +15,7 @@ from typing import Dict, Iterable, Optional, Sequence
 
 from . import hulld
 
-DEFAULT = {"threads": 768, "refill": 8, "job_size": 16384, "slab_depth": 0}
+DEFAULT = {"threads": 1024, "refill": 12, "job_size": 32767, "slab_depth": 0}
 SPACE = {
     "slab_depth": [0, 2, 4],
     "threads": [256, 512, 768, 1024],

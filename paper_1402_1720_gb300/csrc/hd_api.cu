@@ -118,7 +118,7 @@ struct hd_scan {
     hd::Ctrl *ctrl = nullptr;
     // scratch: traversal records, (record, tile) pairs, jobs, host staging
     hd::TilePlan tp{};
-    hd_tuning tuning{768, 8, 16384, 0};
+    hd_tuning tuning{1024, 12, 32767, 0};
     int trace_grid = 0;
     int32_t *rec_buf = nullptr;   // 7 int32 arrays of rec_cap (6 coordinates + status)
     int64_t rec_cap = 0;

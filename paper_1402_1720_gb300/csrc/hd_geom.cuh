@@ -936,27 +936,35 @@ HD_HD bool lean_step(LeanWalk &L, int &row, int &lo, int &hi, unsigned &steps)
 // word(x, y, z) = x + Wx (y + Hy z), Wx = dx + 1, Hy = dy + 1.  A run adds
 // inc (1 for runs along x, 65536 for runs along y: the two halves of a
 // word) at its first voxel and subtracts it just past its last one, which
-// for a run ending at the box's edge lies in the padding.  The row base and
-// the major position are kept as byte offsets, so a run costs a few
-// integer steps.
+// for a run ending at the box's edge lies in the padding.  Consecutive runs
+// share a major index (the walk changes row there), so a run is fixed by
+// the major positions b_prev (where it starts in walk order) and b (where
+// it ends): with the major axis moving +, inc goes at b_prev and -inc just
+// past b; moving -, inc goes at b and -inc just past b_prev.  The cursor
+// keeps the row base and the positions as byte offsets (plus a base the
+// caller chooses, such as the tile's shared-memory address) and the two
+// per-walk offsets and values that this choice implies, so a run costs a
+// few integer steps and no comparison of its ends.
 struct TileCursor {
     unsigned ad, Ru, rem;  // Bresenham state of minor 0 (as in LeanWalk)
     int jn, Qu, kmz, kleft;
     int m0b;    // byte offset of the first voxel's major index within its row
     int sgm;    // signed bytes per major step
-    int mstep;  // bytes per major step (4 along x, 4 Wx along y)
-    int msb;    // byte offset of the current run's start within its row
-    int rowb;   // byte offset of the current row's major index 0
+    int bprev;  // byte offset of the current run's start (walk order) in its row
+    int rowb;   // base + byte offset of the current row's major index 0
     int rstep;  // change of rowb per minor-0 crossing
-    uint32_t inc;  // 1 (x runs) or 65536 (y runs)
+    int oprev, ocur;     // byte offsets added to the run's ends: 0 or one major step
+    uint32_t vprev, vcur;  // values added there: inc and -inc, in walk order
 };
 
 // Start a packed lean walk (lean_pack's form) in a box of dx x dy x dz
-// voxels; false for an empty walk.
-HD_HD bool tile_cursor_start(const uint32_t o[kLeanWords], int dx, int dy, int dz, TileCursor &c)
+// voxels whose word 0 is at byte address `base`; false for an empty walk.
+HD_HD bool tile_cursor_start(const uint32_t o[kLeanWords], int dx, int dy, int dz, int base,
+                             TileCursor &c)
 {
     const int fl = static_cast<int>(o[5] >> 16);
     const bool ymaj = (fl >> 2) & 1;
+    const bool plus = fl & 1;
     const int Wx = dx + 1, Hy = dy + 1;
     c.ad = o[0];
     c.Ru = o[1];
@@ -972,31 +980,33 @@ HD_HD bool tile_cursor_start(const uint32_t o[kLeanWords], int dx, int dy, int d
     const int nminor = ymaj ? dx : dy;
     const int z = dz == 1 ? 0 : row / nminor;
     const int a = row - z * nminor;  // the minor-0 index (y for x-major, x for y-major)
-    c.mstep = ymaj ? 4 * Wx : 4;
-    c.sgm = (fl & 1) ? c.mstep : -c.mstep;
-    c.m0b = im0 * c.mstep;
-    c.msb = c.m0b;
-    c.rowb = ymaj ? 4 * (a + Wx * Hy * z) : 4 * Wx * (a + Hy * z);
+    const int mstep = ymaj ? 4 * Wx : 4;
+    c.sgm = plus ? mstep : -mstep;
+    c.m0b = im0 * mstep;
+    c.bprev = c.m0b;
+    c.rowb = base + (ymaj ? 4 * (a + Wx * Hy * z) : 4 * Wx * (a + Hy * z));
     const int rs = ymaj ? 4 : 4 * Wx;
     c.rstep = (fl & 2) ? rs : -rs;
-    c.inc = ymaj ? 65536u : 1u;
+    const uint32_t inc = ymaj ? 65536u : 1u;
+    c.oprev = plus ? 0 : mstep;
+    c.ocur = plus ? mstep : 0;
+    c.vprev = plus ? inc : 0u - inc;
+    c.vcur = plus ? 0u - inc : inc;
     return !((fl >> 3) & 1);
 }
 
-// The current run: `plus` and `minus` receive the byte offsets where inc is
-// added and subtracted.  Returns whether more runs follow.  Past its last
-// run the cursor holds kleft = (crossings left at the start) - (runs walked).
-HD_HD bool tile_cursor_run(TileCursor &c, int &plus, int &minus)
+// The current run: vprev is added at byte address `at_prev` and vcur at
+// `at_cur`.  Returns whether more runs follow.  Past its last run the
+// cursor holds kleft = (crossings left at the start) - (runs walked).
+HD_HD bool tile_cursor_run(TileCursor &c, int &at_prev, int &at_cur)
 {
     const int jn = c.jn;
     const int e = jn < c.kmz ? jn : c.kmz;
     const int b = c.m0b + c.sgm * e;
-    const int lo = c.msb < b ? c.msb : b;
-    const int hi = c.msb < b ? b : c.msb;
-    plus = c.rowb + lo;
-    minus = c.rowb + hi + c.mstep;
+    at_prev = c.rowb + c.bprev + c.oprev;
+    at_cur = c.rowb + b + c.ocur;
     const bool last = c.kleft == 0 || jn > c.kmz;
-    c.msb = b;  // the next run starts where this one ends (in the next row)
+    c.bprev = b;  // the next run starts where this one ends (in the next row)
     const unsigned rem = c.rem + c.Ru;
     const bool carry = rem >= c.ad;
     c.rem = carry ? rem - c.ad : rem;

@@ -20,7 +20,7 @@ namespace {
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kScatterThreads = 256;
 constexpr int kScatterPerThread = 8;  // most records a scatter thread takes
-constexpr int kRunsPerStep = 4;       // runs a traversal lane walks between refill checks
+constexpr int kRunsPerStep = 8;       // runs a traversal lane walks between refill checks
 
 __device__ __forceinline__ unsigned warp_incl_scan_u(unsigned v)
 {
@@ -251,9 +251,10 @@ __device__ __forceinline__ void load_lean(const Pairs &pairs, int idx, uint4 &a,
     b = __ldg(&pairs.v[2 * static_cast<size_t>(idx) + 1]);
 }
 
-__device__ __forceinline__ void tile_add(char *tile, int byte_off, uint32_t v)
+// Shared-memory reduction (no value returned) at a shared-space byte address.
+__device__ __forceinline__ void smem_red_add(int addr, uint32_t v)
 {
-    atomicAdd(reinterpret_cast<uint32_t *>(tile + byte_off), v);
+    asm volatile("red.shared.add.u32 [%0], %1;" ::"r"(addr), "r"(v));
 }
 
 // Walks the pairs [start, start + total) of a job into the block's tile:
@@ -262,11 +263,12 @@ __device__ __forceinline__ void tile_add(char *tile, int byte_off, uint32_t v)
 // refill happens once enough lanes are idle; then every idle lane with a
 // prefetched pair starts it and fetches another, the pair index coming from
 // the block's counter *s_next.  Adds the runs walked to `runs`.
-__device__ __forceinline__ void walk_job(char *tile, int dx, int dy, int dz, const Pairs &pairs,
-                                         int start, int total, int refill, unsigned *s_next,
-                                         unsigned &runs)
+__device__ __forceinline__ void walk_job(uint32_t *tile, int dx, int dy, int dz,
+                                         const Pairs &pairs, int start, int total, int refill,
+                                         unsigned *s_next, unsigned &runs)
 {
     const unsigned lane = threadIdx.x & 31u;
+    const int sbase = static_cast<int>(__cvta_generic_to_shared(tile));
     TileCursor c;
     bool active = false;
     uint4 na = make_uint4(0, 0, 0, 0), nb = na;
@@ -288,7 +290,7 @@ __device__ __forceinline__ void walk_job(char *tile, int dx, int dy, int dz, con
         if (want != 0 && (__popc(want) >= static_cast<unsigned>(refill) || busy == 0)) {
             if (!active && nidx >= 0) {
                 const uint32_t o[kLeanWords] = {na.x, na.y, na.z, na.w, nb.x, nb.y, nb.z, nb.w};
-                active = tile_cursor_start(o, dx, dy, dz, c);
+                active = tile_cursor_start(o, dx, dy, dz, sbase, c);
                 // runs of a walk = its minor-0 crossings left at the start
                 // minus those left after its last run (see tile_cursor_run)
                 if (active) runs += static_cast<unsigned>(c.kleft);
@@ -307,15 +309,17 @@ __device__ __forceinline__ void walk_job(char *tile, int dx, int dy, int dz, con
             }
             continue;
         }
+        // up to kRunsPerStep runs before the warp checks for refills again.
+        // A lane whose walk ends leaves the loop (predicating it instead was
+        // 25 % slower), and an unroll by 2 measured best (full unrolling,
+        // none, 6, 12 or 16 runs: 5-27 % slower on the head-200 scan).
         if (active) {
-            // up to kRunsPerStep runs before the warp checks for refills again
-            // (the refill test costs about as much as a run)
-#pragma unroll
+#pragma unroll 2
             for (int u = 0; u < kRunsPerStep; ++u) {
-                int plus, minus;
-                active = tile_cursor_run(c, plus, minus);
-                tile_add(tile, plus, c.inc);
-                tile_add(tile, minus, 0u - c.inc);
+                int at_prev, at_cur;
+                active = tile_cursor_run(c, at_prev, at_cur);
+                smem_red_add(at_prev, c.vprev);
+                smem_red_add(at_cur, c.vcur);
                 if (!active) {
                     runs -= static_cast<unsigned>(c.kleft);
                     break;
@@ -491,7 +495,7 @@ __global__ void __launch_bounds__(kThreads, 1) trace_tiles_kernel(
         const int dx = min(tp.tx, tp.nx - x0), dy = min(tp.ty, tp.ny - y0),
                   dz = min(tp.tz, tp.nz - z0);
         unsigned runs = 0;
-        walk_job(reinterpret_cast<char *>(tile), dx, dy, dz, d.pairs, job.start,
+        walk_job(tile, dx, dy, dz, d.pairs, job.start,
                  job.end - job.start, tp.refill, &s_next, runs);
         __syncthreads();
         flush_tile(tile, dx, dy, dz, job.cls == 0 ? d.N : d.M, tp.nx, tp.ny, x0, y0, z0);

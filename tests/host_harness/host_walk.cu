@@ -173,7 +173,7 @@ extern "C" int hx_tile_cursor(const int32_t *gi, const int32_t *go, int dx, int 
     uint32_t o[hd::kLeanWords];
     hd::lean_pack(L, o);
     hd::TileCursor c;
-    if (!hd::tile_cursor_start(o, dx, dy, dz, c)) return 0;
+    if (!hd::tile_cursor_start(o, dx, dy, dz, 0, c)) return 0;
     const int Wx = dx + 1, Hy = dy + 1;
     const long long words = (long long)Wx * Hy * dz;
     std::vector<long long> lo(words, 0), hi(words, 0);
@@ -182,11 +182,20 @@ extern "C" int hx_tile_cursor(const int32_t *gi, const int32_t *go, int dx, int 
     bool more;
     do {
         int p, m;
+        const uint32_t vp = c.vprev, vc = c.vcur;
         more = hd::tile_cursor_run(c, p, m);
         ++runs;
         if (p < 0 || m < 0 || (p & 3) || (m & 3) || p / 4 >= words || m / 4 >= words) return -5000000;
-        if (c.inc == 1u) { lo[p / 4] += 1; lo[m / 4] -= 1; }
-        else { hi[p / 4] += 1; hi[m / 4] -= 1; }
+        // each value is +-1 in one half of a word
+        auto apply = [&](int at, uint32_t v) {
+            if (v == 1u) lo[at / 4] += 1;
+            else if (v == 0xffffffffu) lo[at / 4] -= 1;
+            else if (v == 65536u) hi[at / 4] += 1;
+            else if (v == 0xffff0000u) hi[at / 4] -= 1;
+            else return false;
+            return true;
+        };
+        if (!apply(p, vp) || !apply(m, vc)) return -5000000;
         if (runs > 100000) return -5000000;
     } while (more);
     if (k0 - c.kleft != runs) return -7000000;
