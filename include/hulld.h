@@ -210,10 +210,24 @@ HD_API hd_status hd_scan_get_mask(hd_scan *scan, int32_t method, int32_t layout,
                            size_t dst_bytes, int32_t dst_on_device, void *stream);
 
 /* Copy the count volume of a method into dst (n >= V uint32):
- * HD_MSC or HD_SC -> N (missed paths per voxel, Eq. 3.4; requires MSC, or
- * SC run together with MSC), HD_SM -> M (hit paths per voxel, Eq. 3.9). */
+ * HD_MSC or HD_SC -> N (missed paths per voxel, Eq. 3.4; the scan must have
+ * SC or MSC), HD_SM -> M (hit paths per voxel, Eq. 3.9).  HD_ERR_STATE when
+ * the scan does not hold that volume. */
 HD_API hd_status hd_scan_get_counts(hd_scan *scan, int32_t method, uint32_t *dst, int64_t n,
                              int32_t dst_on_device, void *stream);
+
+/* Replace a count volume with src (exactly V uint32, host or device):
+ * HD_MSC or HD_SC -> N, HD_SM -> M, as hd_scan_get_counts names them.  For a
+ * scan whose histories were split over several processes or GPUs (each
+ * accumulating its share, Eq. 3.4 and 3.9 being sums over histories): load
+ * the element-wise sum of the shares' counts, then hd_scan_finalize decides
+ * the hulls of the whole acquisition.  The statistics' voxel memberships
+ * follow the loaded counts; the history counts stay this scan's own.
+ * Stream-ordered; src must stay valid until the copy has run.  HD_ERR_STATE
+ * when the scan does not hold that volume, HD_ERR_ARG when n != V.  A
+ * deployment aid: the paper processes one data set in one place. */
+HD_API hd_status hd_scan_set_counts(hd_scan *scan, int32_t method, const uint32_t *src,
+                                    int64_t n, int32_t src_on_device, void *stream);
 
 /* Copy the SM thresholds of the last finalize to host arrays of nz entries:
  * M_t per slice, the steepest drop per slice and the linear index of v*.
@@ -497,7 +511,9 @@ HD_API hd_status hd_probe_atomics(int32_t kind, double *ops_per_s);
  * loads the library until the process exits.  n above 262144 returns
  * HD_ERR_RANGE: split larger batches into several calls.  The first call on
  * a device looks up the array's device address (once per device), so make
- * that first call before any stream capture.  All calls share the array:
+ * that first call before any stream capture (made during a capture of
+ * `stream` it returns HD_ERR_STATE).  The address is kept for the life of
+ * the process: do not use this entry point across a reset of the device.  All calls share the array:
  * calls that overlap on the GPU (different streams, or unordered host
  * threads) race on it, so order them on one stream.  Nothing is allocated
  * or freed by any call.  Stream-ordered on `stream`; errors as elsewhere. */

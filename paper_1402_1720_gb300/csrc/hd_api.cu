@@ -296,7 +296,9 @@ hd_status ensure_staging(hd_scan *s, int64_t cap, cudaStream_t st)
 }
 
 // Whether the device can read all six host arrays in place: page-locked
-// memory mapped at the same address (pageable memory is copied instead).
+// memory mapped at the same address and allocated or registered with this
+// device current (other host memory, including page-locked memory of another
+// device's context, is copied instead).  Called with `device` current.
 bool all_mapped_host(const float *const src[6], int device)
 {
     for (int a = 0; a < 6; ++a) {
@@ -305,8 +307,8 @@ bool all_mapped_host(const float *const src[6], int device)
             cudaGetLastError();
             return false;
         }
-        if (at.type != cudaMemoryTypeHost || at.devicePointer != src[a]) return false;
-        (void)device;
+        if (at.type != cudaMemoryTypeHost || at.devicePointer != src[a] || at.device != device)
+            return false;
     }
     return true;
 }
@@ -859,6 +861,25 @@ hd_status hd_scan_get_counts(hd_scan *scan, int32_t method, uint32_t *dst, int64
     HD_CUDA(cudaMemcpyAsync(dst, src, sizeof(uint32_t) * static_cast<size_t>(scan->V),
                             dst_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
                             static_cast<cudaStream_t>(stream)));
+    return HD_OK;
+}
+
+hd_status hd_scan_set_counts(hd_scan *scan, int32_t method, const uint32_t *src, int64_t n,
+                             int32_t src_on_device, void *stream)
+{
+    if (!scan || !src) return HD_ERR_ARG;
+    uint32_t *dst = nullptr;
+    if (method == HD_MSC || method == HD_SC) dst = scan->N;
+    else if (method == HD_SM) dst = scan->M;
+    else return HD_ERR_ARG;
+    if (!dst) return HD_ERR_STATE;
+    if (n != scan->V) return HD_ERR_ARG;
+    DeviceGuard g(scan->device);
+    if (!g.ok) return HD_ERR_CUDA;
+    HD_CUDA(cudaMemcpyAsync(dst, src, sizeof(uint32_t) * static_cast<size_t>(scan->V),
+                            src_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                            static_cast<cudaStream_t>(stream)));
+    scan->finalized = false;
     return HD_OK;
 }
 

@@ -28,6 +28,7 @@ constexpr size_t kNoAllocBytes =
     kNoAllocCtrlBytes + sizeof(int32_t) * 7 * static_cast<size_t>(kNoAllocMaxHistories);
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+static_assert(sizeof(hd::Ctrl) <= kNoAllocCtrlBytes, "the counters must fit their slot");
 
 constexpr int kMaxDevices = 64;
 std::mutex g_setup_mutex;
@@ -36,12 +37,22 @@ int g_sm_count[kMaxDevices] = {};
 
 // Address of the scratch array on `dev` (the current device).  In host code
 // the symbol itself is only a host-side stand-in, so the device address has
-// to be asked for once per device.
-hd_status scratch_for(int dev, void **addr, int *sm_count)
+// to be asked for once per device; that first look-up may load the module
+// and must not happen while `stream` is being captured (HD_ERR_STATE then).
+// The address is cached for the life of the process: after a reset of the
+// device (cudaDeviceReset) the module is loaded again and the array may
+// move, so this entry point is not for use across a device reset.
+hd_status scratch_for(int dev, cudaStream_t stream, void **addr, int *sm_count)
 {
     if (dev < 0 || dev >= kMaxDevices) return HD_ERR_RANGE;
     std::lock_guard<std::mutex> lock(g_setup_mutex);
     if (!g_scratch_addr[dev]) {
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        if (cudaStreamIsCapturing(stream, &cs) != cudaSuccess) {
+            cudaGetLastError();
+            return HD_ERR_CUDA;
+        }
+        if (cs != cudaStreamCaptureStatusNone) return HD_ERR_STATE;
         void *p = nullptr;
         if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || p == nullptr) {
             cudaGetLastError();
@@ -60,36 +71,15 @@ hd_status scratch_for(int dev, void **addr, int *sm_count)
     return HD_OK;
 }
 
-// The gantry-rotation constants, evaluated in double and accepted only away
-// from a rounding boundary (see the scan set-up, which does the same).
+// The gantry-rotation constants (the scans' table), built once per process.
 bool cordic_constants(hd::Cordic &c)
 {
-    const double pi = 3.14159265358979323846;
-    for (int i = 0; i < 32; ++i) {
-        const double v = std::atan(std::ldexp(1.0, -i)) * (180.0 / pi) * 1073741824.0;
-        if (std::fabs(v - std::floor(v) - 0.5) < 5e-5) return false;
-        c.theta[i] = static_cast<long long>(std::floor(v + 0.5));
-    }
-    double k = 1073741824.0;
-    for (int i = 0; i < 32; ++i) k /= std::sqrt(1.0 + std::ldexp(1.0, -2 * i));
-    if (std::fabs(k - std::floor(k) - 0.5) < 1e-3) return false;
-    c.K = static_cast<long long>(std::floor(k + 0.5));
-    return true;
-}
-
-bool geometry_ok(const hd_geometry *g)
-{
-    const int32_t n[3] = {g->nx, g->ny, g->nz};
-    const float s[3] = {g->sx, g->sy, g->sz};
-    int64_t V = 1;
-    for (int a = 0; a < 3; ++a) {
-        if (n[a] < 1 || n[a] > hd::kMaxN) return false;
-        if (!(s[a] >= 1.0f / 64.0f && s[a] <= 64.0f)) return false;
-        if (static_cast<double>(n[a]) * s[a] > 8192.0) return false;
-        V *= n[a];
-    }
-    if (V > (int64_t(1) << 31) - (int64_t(1) << 26)) return false;
-    return g->tracker_half_sep_mm > 0.0f && g->tracker_half_sep_mm < 4096.0f;
+    static std::once_flag once;
+    static hd::Cordic table;
+    static bool ok = false;
+    std::call_once(once, [] { ok = hd::make_cordic_table(table); });
+    c = table;
+    return ok;
 }
 
 }  // namespace
@@ -102,7 +92,8 @@ extern "C" hd_status hd_accumulate_noalloc(const hd_geometry *geom, const hd_par
 {
     if (!geom || !params || n < 0) return HD_ERR_ARG;
     if (n > kNoAllocMaxHistories) return HD_ERR_RANGE;
-    if (!geometry_ok(geom)) return HD_ERR_RANGE;
+    const hd_status gs = hd::check_geometry(geom);
+    if (gs != HD_OK) return gs;
     if (std::isnan(params->wepl_miss_lt) || std::isnan(params->wepl_hit_gt) ||
         params->wepl_miss_lt > params->wepl_hit_gt)
         return HD_ERR_ARG;
@@ -121,7 +112,7 @@ extern "C" hd_status hd_accumulate_noalloc(const hd_geometry *geom, const hd_par
     }
     void *base = nullptr;
     int sm_count = 0;
-    const hd_status st = scratch_for(dev, &base, &sm_count);
+    const hd_status st = scratch_for(dev, static_cast<cudaStream_t>(stream), &base, &sm_count);
     if (st != HD_OK) return st;
     hd::Cordic cordic;
     if (!cordic_constants(cordic)) return HD_ERR_RANGE;

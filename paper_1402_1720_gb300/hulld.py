@@ -156,6 +156,7 @@ _SIGS = {
     "hd_scan_finalize": ([_VP, _VP], ctypes.c_int),
     "hd_scan_get_mask": ([_VP, _I32, _I32, _VP, _SZ, _I32, _VP], ctypes.c_int),
     "hd_scan_get_counts": ([_VP, _I32, _VP, _I64, _I32, _VP], ctypes.c_int),
+    "hd_scan_set_counts": ([_VP, _I32, _VP, _I64, _I32, _VP], ctypes.c_int),
     "hd_scan_get_thresholds": ([_VP, _VP, _VP, _VP, _I32, _VP], ctypes.c_int),
     "hd_scan_get_stats": ([_VP, ctypes.POINTER(hd_stats), _VP], ctypes.c_int),
     "hd_scan_get_hull_indices": ([_VP, _I32, _VP, _I64, ctypes.POINTER(_I64), _I32, _VP],
@@ -395,6 +396,13 @@ def hd_scan_get_counts(scan: int, method: int, dst, stream=None) -> None:
     n = dst.numel() if _is_torch(dst) else dst.size
     _check(load().hd_scan_get_counts(scan, method, p, n, on, _stream(stream)),
            "hd_scan_get_counts")
+
+
+def hd_scan_set_counts(scan: int, method: int, src, stream=None) -> None:
+    p, on = _ptr(src)
+    n = src.numel() if _is_torch(src) else src.size
+    _check(load().hd_scan_set_counts(scan, method, p, n, on, _stream(stream)),
+           "hd_scan_set_counts")
 
 
 def hd_scan_get_thresholds(scan: int, nz: int, stream=None):

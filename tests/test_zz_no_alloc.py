@@ -74,3 +74,26 @@ def test_noalloc_accumulates_chunks_and_limits(hd):
     with pytest.raises(hd.HDError) as e:
         hd.hd_accumulate_noalloc(g, params, *dev, N, None)
     assert e.value.status == hd.HD_ERR_ARG
+
+
+def test_noalloc_method_subsets_unaligned_inputs_and_oracle(hd, oracle_mod):
+    """SM alone with no N volume, on inputs starting one element into their
+    arrays (not 16-byte aligned: the ingest kernel's scalar loads), against
+    the oracle; then SC alone (N only) on the same inputs."""
+    w = synth.make_config(1, fraction=0.3)
+    g, h = w.geometry, w.histories
+    dev = [torch.from_numpy(a).cuda()[1:] for a in h.arrays()]
+    assert dev[0].data_ptr() % 16 != 0
+    sub = h.take(np.arange(1, len(h)))
+    ref = oracle_mod.run(g, sub, threads=8)
+    p = hd.hd_params_default()
+    p.methods = hd.HD_SM
+    M = torch.zeros(g.n_voxels, dtype=torch.int32, device="cuda")
+    hd.hd_accumulate_noalloc(g, p, *dev, None, M)
+    torch.cuda.synchronize()
+    assert np.array_equal(M.cpu().numpy().view(np.uint32), ref["M"])
+    p.methods = hd.HD_SC
+    N = torch.zeros(g.n_voxels, dtype=torch.int32, device="cuda")
+    hd.hd_accumulate_noalloc(g, p, *dev, N, None)
+    torch.cuda.synchronize()
+    assert np.array_equal(N.cpu().numpy().view(np.uint32), ref["N"])
