@@ -127,6 +127,26 @@ static int64_t to_grid(int64_t w, int32_t n, int64_t s_q)
  * history is usable and 1 when it is rejected (a non-finite or out-of-range
  * coordinate: |u|, |v| >= 4096 mm, |angle| >= 2^20 degrees, or a grid
  * coordinate of magnitude >= 2^30). */
+/* World entry and exit points of one history in mm with 16 fractional bits
+ * (the frame of Sec. 2.1 made exact: CORDIC cos/sin, floor division by 2^30):
+ * win = -T b + u_in e_u + v_in e_v, wout = +T b + u_out e_u + v_out e_v. */
+static void world_endpoints(const og_geom *g, const int64_t *theta, int64_t K, float angle,
+                            float u_in, float v_in, float u_out, float v_out, int64_t *win,
+                            int64_t *wout)
+{
+    int64_t c, s;
+    oracle_cordic(q16_of(angle), theta, K, &c, &s);
+    int64_t T = q16_of(g->T);
+    int64_t ui = q16_of(u_in), vi = q16_of(v_in);
+    int64_t uo = q16_of(u_out), vo = q16_of(v_out);
+    win[0] = (-T * c - ui * s) >> 30;
+    win[1] = (-T * s + ui * c) >> 30;
+    win[2] = vi;
+    wout[0] = (T * c - uo * s) >> 30;
+    wout[1] = (T * s + uo * c) >> 30;
+    wout[2] = vo;
+}
+
 int oracle_grid_endpoints(const og_geom *g, const int64_t *theta, int64_t K,
                           float angle, float u_in, float v_in, float u_out,
                           float v_out, int64_t *gin, int64_t *gout)
@@ -430,6 +450,123 @@ int oracle_accumulate_thick(const og_geom *g, float tau_l, float tau_h, int32_t 
     }
     free(set);
     free(stamp);
+    return 0;
+}
+
+/* ---------------------------- thick rays, Euclidean distance (next row f4) */
+
+/* Thick rays as Eq. 3.2 states them with d_0 > 0 and d the Euclidean
+ * distance: A_i(d_0) = the voxels whose centre lies within d_0 mm of the
+ * closed segment L_i (entry to exit point, Sec. 2.1).  Exact in integers:
+ * with every coordinate doubled from mm * 2^16 (so voxel centres
+ * ((2 i + 1 - n) s / 2) are integers too), A = 2 win, B = 2 wout, the centre
+ * C = ((2 i + 1 - nx) sx, (2 j + 1 - ny) sy, (2 k + 1 - nz) sz) (s in mm *
+ * 2^16, rounded once as all inputs are) and R = 2 q16(d_0), u = B - A,
+ * w = C - A:
+ *   w.u <= 0      : |w|^2 <= R^2            (nearest point A)
+ *   w.u >= |u|^2  : |C - B|^2 <= R^2        (nearest point B)
+ *   otherwise     : |w x u|^2 <= R^2 |u|^2  (the line between them).
+ * |coordinates| < 2^30, so |u|, |w| < 2^31, products of two < 2^62, cross
+ * components < 2^63 and |w x u|^2 < 3 2^126 fit unsigned 128 bits. */
+typedef unsigned __int128 u128;
+
+static u128 sq64(int64_t a) { return (u128)((i128)a * (i128)a); }
+
+int oracle_in_capsule(const int64_t *A, const int64_t *B, const int64_t *C, int64_t R)
+{
+    int64_t u[3], w[3], wb[3];
+    for (int a = 0; a < 3; ++a) {
+        u[a] = B[a] - A[a];
+        w[a] = C[a] - A[a];
+        wb[a] = C[a] - B[a];
+    }
+    i128 dot = 0, uu = 0;
+    for (int a = 0; a < 3; ++a) {
+        dot += (i128)w[a] * u[a];
+        uu += (i128)u[a] * u[a];
+    }
+    const u128 RR = (u128)((i128)R * R);
+    if (dot <= 0) return (sq64(w[0]) + sq64(w[1]) + sq64(w[2])) <= RR;
+    if (dot >= uu) return (sq64(wb[0]) + sq64(wb[1]) + sq64(wb[2])) <= RR;
+    const int64_t cx = w[1] * u[2] - w[2] * u[1];
+    const int64_t cy = w[2] * u[0] - w[0] * u[2];
+    const int64_t cz = w[0] * u[1] - w[1] * u[0];
+    return (sq64(cx) + sq64(cy) + sq64(cz)) <= RR * (u128)uu;
+}
+
+/* Doubled world endpoints of a usable history and the doubled radius; 1 when
+ * the history is rejected (the thin path's rule, oracle_grid_endpoints). */
+int oracle_capsule_of(const og_geom *g, const int64_t *theta, int64_t K, float d0, float angle,
+                      float u_in, float v_in, float u_out, float v_out, int64_t *A, int64_t *B,
+                      int64_t *R)
+{
+    int64_t gin[3], gout[3];
+    if (oracle_grid_endpoints(g, theta, K, angle, u_in, v_in, u_out, v_out, gin, gout)) return 1;
+    int64_t win[3], wout[3];
+    world_endpoints(g, theta, K, angle, u_in, v_in, u_out, v_out, win, wout);
+    for (int a = 0; a < 3; ++a) {
+        A[a] = 2 * win[a];
+        B[a] = 2 * wout[a];
+    }
+    *R = 2 * q16_of(d0);
+    return 0;
+}
+
+/* N and M over the Euclidean thick sets: for every usable missed (hit)
+ * history, every voxel of the grid box bounding its capsule (segment grown
+ * by d_0) is tested with oracle_in_capsule and counted once when inside.
+ * stats as oracle_accumulate ([5], [6]: the voxels of the thick sets). */
+int oracle_accumulate_euclid(const og_geom *g, float tau_l, float tau_h, int32_t methods,
+                             const int64_t *theta, int64_t K, float d0, const float *angle,
+                             const float *u_in, const float *v_in, const float *u_out,
+                             const float *v_out, const float *wepl, int64_t n, uint32_t *N,
+                             uint32_t *M, int64_t *stats)
+{
+    const int32_t nn[3] = {g->nx, g->ny, g->nz};
+    const int64_t sq[3] = {q16_of(g->sx), q16_of(g->sy), q16_of(g->sz)};
+    const int use_miss = (methods & (OM_SC | OM_MSC)) != 0;
+    const int use_hit = (methods & OM_SM) != 0;
+    for (int64_t i = 0; i < n; ++i) {
+        stats[0] += 1;
+        const int cls = oracle_classify(wepl[i], tau_l, tau_h);
+        if (cls == 1) stats[1] += 1;
+        else if (cls == 2) stats[2] += 1;
+        else stats[3] += 1;
+        if (!((cls == 1 && use_miss) || (cls == 2 && use_hit))) continue;
+        int64_t A[3], B[3], R;
+        if (oracle_capsule_of(g, theta, K, d0, angle[i], u_in[i], v_in[i], u_out[i], v_out[i], A,
+                              B, &R)) {
+            stats[4] += 1;
+            continue;
+        }
+        /* index range of each axis: centres (2 i + 1 - n) s within
+         * [min(A, B) - R, max(A, B) + R], widened by one and clipped */
+        int64_t lo[3], hi[3];
+        for (int a = 0; a < 3; ++a) {
+            const int64_t mn = (A[a] < B[a] ? A[a] : B[a]) - R;
+            const int64_t mx = (A[a] < B[a] ? B[a] : A[a]) + R;
+            lo[a] = (floordiv(mn, sq[a]) + nn[a] - 1) / 2 - 1;
+            hi[a] = (floordiv(mx, sq[a]) + nn[a] + 1) / 2 + 1;
+            if (lo[a] < 0) lo[a] = 0;
+            if (hi[a] > nn[a] - 1) hi[a] = nn[a] - 1;
+        }
+        int64_t count = 0;
+        for (int64_t z = lo[2]; z <= hi[2]; ++z)
+            for (int64_t y = lo[1]; y <= hi[1]; ++y)
+                for (int64_t x = lo[0]; x <= hi[0]; ++x) {
+                    const int64_t C[3] = {(2 * x + 1 - nn[0]) * sq[0], (2 * y + 1 - nn[1]) * sq[1],
+                                          (2 * z + 1 - nn[2]) * sq[2]};
+                    if (!oracle_in_capsule(A, B, C, R)) continue;
+                    ++count;
+                    const int64_t v = x + (int64_t)nn[0] * (y + (int64_t)nn[1] * z);
+                    if (cls == 1) {
+                        if (N) N[v] += 1;
+                    } else if (M) {
+                        M[v] += 1;
+                    }
+                }
+        stats[cls == 1 ? 5 : 6] += count;
+    }
     return 0;
 }
 

@@ -96,6 +96,16 @@ def lib():
                                                   ctypes.c_int32] + [f32p] * 6 + \
                 [ctypes.c_int64, u32p, u32p, i64p]
             L.oracle_accumulate_thick.restype = ctypes.c_int
+            L.oracle_in_capsule.argtypes = [i64p, i64p, i64p, ctypes.c_int64]
+            L.oracle_in_capsule.restype = ctypes.c_int
+            L.oracle_capsule_of.argtypes = [ctypes.c_void_p, i64p, ctypes.c_int64] + \
+                [ctypes.c_float] * 6 + [i64p, i64p, i64p]
+            L.oracle_capsule_of.restype = ctypes.c_int
+            L.oracle_accumulate_euclid.argtypes = [ctypes.c_void_p, ctypes.c_float,
+                                                   ctypes.c_float, ctypes.c_int32, i64p,
+                                                   ctypes.c_int64, ctypes.c_float] + \
+                [f32p] * 6 + [ctypes.c_int64, u32p, u32p, i64p]
+            L.oracle_accumulate_euclid.restype = ctypes.c_int
             L.oracle_segment_meets_box.argtypes = [i64p, i64p, i64p, i64p]
             L.oracle_segment_meets_box.restype = ctypes.c_int
             L.oracle_count_thick_voxels.argtypes = [ctypes.c_void_p, ctypes.c_float,
@@ -565,6 +575,87 @@ def run_thick(g, hist, k: int, params: Params = Params()) -> Dict:
     """run() with every A_i replaced by its thick set A_i(k): counts from
     accumulate_thick, then the same decisions (H_1 = [N = 0])."""
     acc = accumulate_thick(g, hist, k, params)
+    dims = (g.nx, g.ny, g.nz)
+    out = dict(acc)
+    out["H1"] = sc_from_counts(acc["N"])
+    out["H2"] = msc_decide(acc["N"], dims, params.nt, params.nbhd)
+    out.update(sm_decide(acc["M"], dims, params.sm_per_slice, params.nbhd, params.sm_ge))
+    return out
+
+
+# ------------------------------ thick rays, Euclidean distance (next row f4)
+def in_capsule(A, B, C, R) -> bool:
+    """Is the point C within R of the closed segment A-B (integer coordinates,
+    the doubled mm * 2^16 units of capsule_of)?"""
+    arrs = [np.ascontiguousarray(a, dtype=np.int64) for a in (A, B, C)]
+    return bool(lib().oracle_in_capsule(*[_p(a, ctypes.c_int64) for a in arrs], int(R)))
+
+
+def capsule_of(g, d0: float, angle, u_in, v_in, u_out, v_out):
+    """(rejected, A, B, R): the doubled world entry and exit points (mm * 2^17)
+    and the doubled radius 2 q16(d0) of one history."""
+    th, K = _table_arrays()
+    A = np.zeros(3, np.int64)
+    B = np.zeros(3, np.int64)
+    R = np.zeros(1, np.int64)
+    og = _ogeom(g)
+    rej = lib().oracle_capsule_of(ctypes.byref(og), _p(th, ctypes.c_int64), K, float(d0),
+                                  float(angle), float(u_in), float(v_in), float(u_out),
+                                  float(v_out), _p(A, ctypes.c_int64), _p(B, ctypes.c_int64),
+                                  _p(R, ctypes.c_int64))
+    return bool(rej), A, B, int(R[0])
+
+
+def voxel_centre2(g, x: int, y: int, z: int) -> np.ndarray:
+    """Doubled centre of voxel (x, y, z) in mm * 2^16 units: (2 i + 1 - n) q16(s)."""
+    q = lambda s: int(np.rint(np.float64(np.float32(s)) * 65536.0))
+    return np.array([(2 * x + 1 - g.nx) * q(g.sx), (2 * y + 1 - g.ny) * q(g.sy),
+                     (2 * z + 1 - g.nz) * q(g.sz)], np.int64)
+
+
+def _accumulate_euclid_into(g, hist, s, e, d0, params, N, M, stats):
+    th, K = _table_arrays()
+    arrs = [np.ascontiguousarray(a[s:e], dtype=np.float32) for a in hist.arrays()]
+    og = _ogeom(g)
+    lib().oracle_accumulate_euclid(ctypes.byref(og), params.tau_l, params.tau_h, params.methods,
+                                   _p(th, ctypes.c_int64), K, float(d0),
+                                   *[_p(a, ctypes.c_float) for a in arrs], e - s,
+                                   _p(N, ctypes.c_uint32), _p(M, ctypes.c_uint32),
+                                   _p(stats, ctypes.c_int64))
+
+
+def accumulate_euclid(g, hist, d0: float, params: Params = Params(),
+                      threads: Optional[int] = 1) -> Dict:
+    """N and M with Euclidean thick rays (Eq. 3.2, d the Euclidean distance
+    from the voxel centre to the closed segment, d_0 in mm): every voxel of
+    each capsule's bounding box tested exactly; split over `threads` history
+    ranges with private volumes (integer sums, so the result is the same)."""
+    n = len(hist)
+    threads = max(1, min(threads or os.cpu_count() or 1, n // 200 + 1))
+    V = g.nx * g.ny * g.nz
+    parts = [(np.zeros(V, np.uint32), np.zeros(V, np.uint32), np.zeros(8, np.int64))
+             for _ in range(threads)]
+    bounds = np.linspace(0, n, threads + 1).astype(np.int64)
+    ths = [threading.Thread(target=_accumulate_euclid_into,
+                            args=(g, hist, int(bounds[t]), int(bounds[t + 1]), d0, params) + parts[t])
+           for t in range(threads)]
+    for t in ths:
+        t.start()
+    for t in ths:
+        t.join()
+    N = np.zeros(V, np.uint32)
+    M = np.zeros(V, np.uint32)
+    stats = np.zeros(8, np.int64)
+    for pN, pM, ps in parts:
+        N += pN
+        M += pM
+        stats += ps
+    return {"N": N, "M": M, "stats": stats}
+
+
+def run_euclid(g, hist, d0: float, params: Params = Params(), threads: Optional[int] = 1) -> Dict:
+    """run() with every A_i replaced by its Euclidean thick set A_i(d0)."""
+    acc = accumulate_euclid(g, hist, d0, params, threads)
     dims = (g.nx, g.ny, g.nz)
     out = dict(acc)
     out["H1"] = sc_from_counts(acc["N"])
