@@ -560,6 +560,43 @@ HD_API hd_status hd_accumulate_thick(const hd_geometry *geom, const hd_params *p
                                      size_t workspace_bytes, int64_t *intervals, void *stream);
 
 /* ------------------------------------------------------------------------
+ * Thick rays as Eq. 3.2 states them with d the Euclidean distance:
+ * A_i(d_0) = the voxels whose centre lies within d_0 mm of the closed segment
+ * L_i from the entry to the exit point (Sec. 2.1).  Exact: the entry and exit
+ * points are the thin paths' fixed-point world points (mm * 2^16, after the
+ * integer CORDIC), voxel centres ((2 i + 1 - n) s / 2 with s rounded to
+ * 2^-16 mm) and d_0 (rounded to 2^-16 mm, ties to even) enter the distance
+ * test in integers, so membership never depends on floating-point rounding.
+ * Thickness reaches across slices whenever d_0 exceeds the distance to the
+ * neighbouring slice's centres.
+ *
+ * Standalone accumulation: classifies the n histories (device SoA arrays)
+ * and ADDS one to N[v] for every voxel v of A_i(d_0) of every usable missed
+ * history and to M[v] for every hit one (N required when params->methods has
+ * HD_SC or HD_MSC, M when it has HD_SM; uint32, V entries, device; the caller
+ * zeroes them first).  Histories rejected by the thin paths' rule add
+ * nothing.  workspace: at least hd_accumulate_thick_workspace bytes, 256-byte
+ * aligned; the call clears it.  rows (device, one int64, may be NULL)
+ * receives the number of row intervals added (two atomics each; a
+ * measurement aid).  HD_ERR_RANGE for d_0 outside [0, 64] mm or an
+ * unsupported geometry.  Stream-ordered on `stream`. */
+HD_API hd_status hd_accumulate_euclid(const hd_geometry *geom, const hd_params *params,
+                                      float d0_mm, const float *angle_deg, const float *u_in,
+                                      const float *v_in, const float *u_out, const float *v_out,
+                                      const float *wepl, int64_t n, uint32_t *N, uint32_t *M,
+                                      void *workspace, size_t workspace_bytes, int64_t *rows,
+                                      void *stream);
+
+/* Set a scan to the Euclidean thick rays above (d_0 in (0, 64] mm) or back to
+ * thin paths (0): N, M, the three hulls, the thresholds and the statistics
+ * then follow from the sets A_i(d_0) (the statistics' voxel counts are their
+ * sizes).  Replaces an in-plane dilation set with hd_scan_set_thick (and is
+ * replaced by one).  Only before any histories: HD_ERR_STATE otherwise;
+ * HD_ERR_RANGE outside [0, 64] mm.  Allocates the thick rays' workspace.
+ * Such scans cannot join a batch (hd_batch_add_item returns HD_ERR_STATE). */
+HD_API hd_status hd_scan_set_thick_distance(hd_scan *scan, float d0_mm);
+
+/* ------------------------------------------------------------------------
  * Hull diagnostics (not steps of the method: the measures the paper reports
  * and a fill variant of MSC's hull).  All pointers are device pointers; the
  * volumes are uint8 masks of nx * ny * nz voxels, x fastest.

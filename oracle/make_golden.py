@@ -87,8 +87,6 @@ def _c3_chunk(k):
     return synth.config3_chunk(k)
 
 
-_scan_part = synth.batch_scan_part
-
 
 # -------------------------------------------------------------- workloads
 def head200(threads: int) -> dict:

@@ -134,6 +134,7 @@ struct hd_scan {
     int64_t rows_scratch_cap = 0;
     uint32_t *rows_bits = nullptr;    // the hull packed for the row passes
     int32_t thick_k = 0;             // thick rays: in-plane dilation (0 = thin paths)
+    float euclid_d0 = 0.0f;          // thick rays by Euclidean distance, mm (0 = off)
     void *thick_ws = nullptr;        // their difference arrays
     float *staging = nullptr;  // copied host inputs: 6 columns of staging_half floats
     int64_t staging_half = 0;
@@ -484,6 +485,16 @@ int finalize_launches(const hd_scan *scan) { return (scan->params.methods & HD_S
 // One chunk through the whole path on st.
 hd_status run_chunk(hd_scan *s, const hd::Inputs &in, int64_t n, cudaStream_t st)
 {
+    if (s->euclid_d0 > 0.0f) {
+        // Euclidean thick rays: a warp per history over the rows of its capsule
+        const uint32_t m = s->params.methods;
+        HD_CUDA(hd::launch_euclid(in, n, &s->geom, s->gq, s->cordic, s->params.wepl_miss_lt,
+                                  s->params.wepl_hit_gt, (m & (HD_SC | HD_MSC)) ? 1 : 0,
+                                  (m & HD_SM) ? 1 : 0, s->euclid_d0, s->thick_ws, s->N, s->M,
+                                  &s->ctrl->n_in, nullptr, s->sm_count, st));
+        s->launches += 4;
+        return HD_OK;
+    }
     if (s->thick_k > 0) {
         const hd::TilePlan &tp = s->tp;
         if (tp.ntiles > 0 && tp.ntx == 1 && tp.nty == 1 && tp.tz == 1) {
@@ -995,6 +1006,27 @@ hd_status hd_scan_set_thick(hd_scan *scan, int32_t k)
         }
     }
     scan->thick_k = k;
+    if (k > 0) scan->euclid_d0 = 0.0f;
+    return HD_OK;
+}
+
+hd_status hd_scan_set_thick_distance(hd_scan *scan, float d0_mm)
+{
+    if (!scan) return HD_ERR_ARG;
+    if (!(d0_mm >= 0.0f && d0_mm <= 64.0f)) return HD_ERR_RANGE;
+    if (scan->n_total != 0) return HD_ERR_STATE;
+    DeviceGuard g(scan->device);
+    if (!g.ok) return HD_ERR_CUDA;
+    if (d0_mm > 0.0f && !scan->thick_ws) {
+        HD_CUDA(cudaDeviceSynchronize());
+        if (cudaMalloc(&scan->thick_ws, hd::thick_workspace_bytes(&scan->geom)) != cudaSuccess) {
+            cudaGetLastError();
+            scan->thick_ws = nullptr;
+            return HD_ERR_NOMEM;
+        }
+    }
+    scan->euclid_d0 = d0_mm;
+    if (d0_mm > 0.0f) scan->thick_k = 0;
     return HD_OK;
 }
 
@@ -1284,7 +1316,8 @@ hd_status hd_batch_add_item(hd_batch *batch, hd_scan *scan, const float *angle_d
     if (flags & ~(HD_BATCH_RESET | HD_BATCH_FINALIZE)) return HD_ERR_ARG;
     if (n > 0 && (!angle_deg || !u_in || !v_in || !u_out || !v_out || !wepl)) return HD_ERR_ARG;
     if (scan->device != batch->device) return HD_ERR_ARG;
-    if (scan->thick_k > 0) return HD_ERR_STATE;  // batches run the tiled thin paths
+    if (scan->thick_k > 0 || scan->euclid_d0 > 0.0f)
+        return HD_ERR_STATE;  // batches run the tiled thin paths
     if (static_cast<int>(batch->items.size()) >= batch->max_items) return HD_ERR_STATE;
     hd_batch::Item it;
     it.scan = scan;

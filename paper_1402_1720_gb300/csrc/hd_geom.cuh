@@ -183,6 +183,26 @@ inline GeomQ make_geomq(int nx, int ny, int nz, float sx, float sy, float sz, fl
     return g;
 }
 
+// World entry and exit points (mm, Q16) of one history from its gantry
+// cos/sin: W = (x_in, y_in, z_in, x_out, y_out, z_out).  The inputs must
+// satisfy |u|, |v| < 4096 mm (endpoints_cs checks it).
+HD_HD void world_cs(const GeomQ &g, long long c, long long s, float ui, float vi, float uo,
+                    float vo, long long W[6])
+{
+    // every factor fits 32 bits (T < 2^28 since the tracker distance is below
+    // 4096 mm, |c|, |s| <= 2^30, |u| Q16 < 2^28): exact 32 x 32 -> 64 products
+    const int T = static_cast<int>(g.T);
+    const int ci = static_cast<int>(c), si = static_cast<int>(s);
+    const int qui = q16_small(ui), quo = q16_small(uo);
+    auto mul = [](int a, int b) { return static_cast<long long>(a) * static_cast<long long>(b); };
+    W[0] = (-mul(T, ci) - mul(qui, si)) >> 30;
+    W[1] = (-mul(T, si) + mul(qui, ci)) >> 30;
+    W[2] = q16_small(vi);
+    W[3] = (mul(T, ci) - mul(quo, si)) >> 30;
+    W[4] = (mul(T, si) + mul(quo, ci)) >> 30;
+    W[5] = q16_small(vo);
+}
+
 // Grid Q16 endpoints of one history from its gantry cos/sin; false when the
 // history is rejected.
 HD_HD bool endpoints_cs(const GeomQ &g, long long c, long long s, float ui, float vi, float uo,
@@ -191,20 +211,11 @@ HD_HD bool endpoints_cs(const GeomQ &g, long long c, long long s, float ui, floa
     if (!(fabsf(ui) < 4096.0f) || !(fabsf(vi) < 4096.0f) || !(fabsf(uo) < 4096.0f) ||
         !(fabsf(vo) < 4096.0f))
         return false;
-    // every factor fits 32 bits (T < 2^28 since the tracker distance is below
-    // 4096 mm, |c|, |s| <= 2^30, |u| Q16 < 2^28): exact 32 x 32 -> 64 products
-    const int T = static_cast<int>(g.T);
-    const int ci = static_cast<int>(c), si = static_cast<int>(s);
-    const int qui = q16_small(ui), quo = q16_small(uo);
-    const long long qvi = q16_small(vi), qvo = q16_small(vo);
-    auto mul = [](int a, int b) { return static_cast<long long>(a) * static_cast<long long>(b); };
-    const long long wxi = (-mul(T, ci) - mul(qui, si)) >> 30;
-    const long long wyi = (-mul(T, si) + mul(qui, ci)) >> 30;
-    const long long wxo = (mul(T, ci) - mul(quo, si)) >> 30;
-    const long long wyo = (mul(T, si) + mul(quo, ci)) >> 30;
-    const long long G[6] = {to_grid(wxi, g.nx, g.sx, g.mx), to_grid(wyi, g.ny, g.sy, g.my),
-                            to_grid(qvi, g.nz, g.sz, g.mz), to_grid(wxo, g.nx, g.sx, g.mx),
-                            to_grid(wyo, g.ny, g.sy, g.my), to_grid(qvo, g.nz, g.sz, g.mz)};
+    long long W[6];
+    world_cs(g, c, s, ui, vi, uo, vo, W);
+    const long long G[6] = {to_grid(W[0], g.nx, g.sx, g.mx), to_grid(W[1], g.ny, g.sy, g.my),
+                            to_grid(W[2], g.nz, g.sz, g.mz), to_grid(W[3], g.nx, g.sx, g.mx),
+                            to_grid(W[4], g.ny, g.sy, g.my), to_grid(W[5], g.nz, g.sz, g.mz)};
     const long long lim = 1LL << 30;
 #pragma unroll
     for (int a = 0; a < 6; ++a) {

@@ -318,6 +318,13 @@ cudaError_t launch_thick(const Inputs &in, int64_t n, const hd_geometry *geom, c
     return e;
 }
 
+unsigned long long *thick_counters_of(const hd_geometry *geom, void *workspace)
+{
+    ThickWs ws{};
+    thick_layout(geom, workspace, &ws);
+    return ws.stats;
+}
+
 ThickDiff thick_diff_of(const hd_geometry *geom, void *workspace)
 {
     ThickWs ws{};
@@ -345,6 +352,20 @@ static cudaError_t launch_thick_rows(const hd_geometry *geom, const ThickWs &ws,
             ws.dy[c], ry, geom->ny, geom->nx, geom->nx, plane, 1, out);
     }
     return cudaGetLastError();
+}
+
+cudaError_t launch_thick_finish(const hd_geometry *geom, void *workspace, uint32_t *N,
+                                uint32_t *M, unsigned long long *stats, int64_t *intervals,
+                                cudaStream_t st)
+{
+    ThickWs ws{};
+    thick_layout(geom, workspace, &ws);
+    cudaError_t e = launch_thick_rows(geom, ws, N, M, st);
+    if (e == cudaSuccess && (stats || intervals)) {
+        thick_stats_kernel<<<1, 32, 0, st>>>(ws.stats, stats, intervals);
+        e = cudaGetLastError();
+    }
+    return e;
 }
 
 cudaError_t launch_thick_scan(const ScanDesc *desc_dev, const hd_geometry *geom,

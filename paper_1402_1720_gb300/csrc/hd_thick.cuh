@@ -92,6 +92,16 @@ __device__ __forceinline__ unsigned thick_walk_all(RunWalk &wk, int nminor, int 
 size_t thick_workspace_bytes(const hd_geometry *geom);
 ThickDiff thick_diff_of(const hd_geometry *geom, void *workspace);
 
+// The workspace's 8 counters (see launch_thick) and its work counter.
+unsigned long long *thick_counters_of(const hd_geometry *geom, void *workspace);
+
+// Adds the workspace's difference arrays to N and M (either may be null)
+// by prefix sums along their rows, and, when `stats` / `intervals` are not
+// null, adds the counters 0..6 to stats and stores counter 7 in *intervals.
+cudaError_t launch_thick_finish(const hd_geometry *geom, void *workspace, uint32_t *N,
+                                uint32_t *M, unsigned long long *stats, int64_t *intervals,
+                                cudaStream_t st);
+
 // Clears the workspace, adds the thick sets of n histories to N (missed) and
 // M (hit) (either may be null when its class is not used), and, when
 // `stats` is not null, adds to stats[0..6]: histories, missed, hit, neither,
@@ -102,6 +112,17 @@ cudaError_t launch_thick(const Inputs &in, int64_t n, const hd_geometry *geom, c
                          int k, void *workspace, uint32_t *N, uint32_t *M,
                          unsigned long long *stats, int64_t *intervals, int sm_count,
                          cudaStream_t st);
+
+// Euclidean thick rays (hd_euclid.cu): clears the workspace, adds the sets
+// A_i(d0) = {v : centre of v within d0 mm of L_i} of n histories to N and M
+// (either may be null when its class is not used), and, when `stats` is not
+// null, adds to stats[0..6] as launch_thick does; *rows (may be null)
+// receives the number of row intervals added.
+cudaError_t launch_euclid(const Inputs &in, int64_t n, const hd_geometry *geom, const GeomQ &g,
+                          const Cordic &cd, float tau_l, float tau_h, int use_miss, int use_hit,
+                          float d0, void *workspace, uint32_t *N, uint32_t *M,
+                          unsigned long long *stats, int64_t *rows, int sm_count,
+                          cudaStream_t st);
 
 // The tiled traversal of thick rays over one scan's jobs (trace_thick_kernel).
 cudaError_t launch_trace_thick(const ScanDesc *desc_dev, int *job_counter, int k,

@@ -194,6 +194,10 @@ _SIGS = {
                                       ctypes.c_int),
     "hd_accumulate_thick": ([ctypes.POINTER(hd_geometry), ctypes.POINTER(hd_params), _I32] +
                             [_VP] * 6 + [_I64, _VP, _VP, _VP, _SZ, _VP, _VP], ctypes.c_int),
+    "hd_accumulate_euclid": ([ctypes.POINTER(hd_geometry), ctypes.POINTER(hd_params),
+                              ctypes.c_float] + [_VP] * 6 + [_I64, _VP, _VP, _VP, _SZ, _VP, _VP],
+                             ctypes.c_int),
+    "hd_scan_set_thick_distance": ([_VP, ctypes.c_float], ctypes.c_int),
     "hd_sm_canny_workspace": ([_I32, _I32, _I32, ctypes.POINTER(_SZ)], ctypes.c_int),
     "hd_sm_canny": ([_VP, _I32, _I32, _I32, _I32, _VP, _SZ, _VP, _VP, _VP, _VP], ctypes.c_int),
     "hd_fill_enclosed": ([_VP, _I32, _I32, _I32, _VP, _VP], ctypes.c_int),
@@ -449,6 +453,10 @@ def hd_scan_get_tuning(scan: int) -> dict:
 
 def hd_scan_set_thick(scan: int, k: int) -> None:
     _check(load().hd_scan_set_thick(scan, int(k)), "hd_scan_set_thick")
+
+
+def hd_scan_set_thick_distance(scan: int, d0_mm: float) -> None:
+    _check(load().hd_scan_set_thick_distance(scan, float(d0_mm)), "hd_scan_set_thick_distance")
 
 
 def hd_scan_set_profiling(scan: int, enable: bool) -> None:
@@ -768,6 +776,11 @@ class Scan:
         """Thick rays: A_i dilated by k voxels in-plane (before any add)."""
         hd_scan_set_thick(self.handle, k)
 
+    def set_thick_distance(self, d0_mm: float):
+        """Thick rays by Euclidean distance d0 (mm) from voxel centres to the
+        path (before any add); 0 restores thin paths."""
+        hd_scan_set_thick_distance(self.handle, d0_mm)
+
     def system_rows(self, method: int, hist_arrays: Sequence, stream=None):
         """(row_ptr, cols) device tensors of the hull-restricted system
         matrix for device histories (angle, u_in, v_in, u_out, v_out, ...)."""
@@ -1074,3 +1087,25 @@ def hd_accumulate_thick(geometry, params, k: int, arrays, N, M, workspace=None, 
                                       mptr, _dev_ptr(workspace, "workspace"),
                                       int(workspace.numel() * workspace.element_size()), iptr,
                                       _stream(stream)), "hd_accumulate_thick")
+
+
+def hd_accumulate_euclid(geometry, params, d0_mm: float, arrays, N, M, workspace=None,
+                         stream=None, rows=None):
+    """Adds Euclidean thick-ray counts (voxel centres within d0_mm of the path)
+    of device history arrays into device N, M (uint32 viewed as int32
+    tensors); `rows` (a one-element int64 device tensor) receives the number
+    of row intervals added."""
+    import torch
+    g = _geometry(geometry)
+    p = _params(params)
+    ptrs, n = _hist_ptrs(list(arrays))
+    if workspace is None:
+        workspace = torch.empty(hd_accumulate_thick_workspace(geometry), dtype=torch.uint8,
+                                device="cuda")
+    nptr = _dev_ptr(N, "N") if N is not None else None
+    mptr = _dev_ptr(M, "M") if M is not None else None
+    rptr = _dev_ptr(rows, "rows") if rows is not None else None
+    _check(load().hd_accumulate_euclid(ctypes.byref(g), ctypes.byref(p), float(d0_mm), *ptrs, n,
+                                       nptr, mptr, _dev_ptr(workspace, "workspace"),
+                                       int(workspace.numel() * workspace.element_size()), rptr,
+                                       _stream(stream)), "hd_accumulate_euclid")
