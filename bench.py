@@ -791,6 +791,98 @@ def run_thick(args):
     print(json.dumps(line), flush=True)
 
 
+def run_euclid(args):
+    """Thick rays by Euclidean distance on the head-sized scan: each step adds
+    the missed and hit counts of all 9e6 histories with A_i(d_0) = the voxels
+    whose centre lies within d_0 mm of the path (hd_accumulate_euclid: clear,
+    rows of every capsule, prefix sums); then a scan set to the same distance
+    (reset, add, finalize of SC, MSC and SM)."""
+    import torch
+    from paper_1402_1720_gb300 import build as hbuild
+    from paper_1402_1720_gb300 import hulld, synth
+    _, _, local = _dist()
+    torch.cuda.set_device(local)
+    hbuild.build()
+    hulld.load()
+    w = synth.make_config(2, fraction=args.fraction)
+    g, h = w.geometry, w.histories
+    n = len(h)
+    d0 = args.thick_mm
+    dev = [torch.from_numpy(a).cuda() for a in h.arrays()]
+    V = g.nx * g.ny * g.nz
+    N = torch.zeros(V, dtype=torch.int32, device="cuda")
+    M = torch.zeros(V, dtype=torch.int32, device="cuda")
+    ws = torch.empty(hulld.hd_accumulate_thick_workspace(g), dtype=torch.uint8, device="cuda")
+    rows = torch.zeros(1, dtype=torch.int64, device="cuda")
+    stream = torch.cuda.Stream()
+
+    def timed(fn, k):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(k):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / k
+
+    def step():
+        hulld.hd_accumulate_euclid(g, None, d0, dev, N, M, ws, stream, rows)
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            step()
+        torch.cuda.synchronize()
+        N.zero_()
+        M.zero_()
+        sampler = ClockSampler(local)
+        sampler.start()
+        ms = timed(step, args.steps)
+        clocks = sampler.stop()
+    voxels = (int(N.sum().item()) + int(M.sum().item())) // args.steps
+    n_rows = int(rows.item())
+    scan = hulld.Scan(g)
+    scan.set_thick_distance(d0)
+
+    def scan_step():
+        hulld.hd_scan_reset(scan.handle, stream)
+        hulld.hd_scan_add_histories(scan.handle, *dev, stream=stream)
+        hulld.hd_scan_finalize(scan.handle, stream)
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            scan_step()
+        torch.cuda.synchronize()
+        ms_scan = timed(scan_step, args.steps)
+    scan.close()
+    line = {"metric": f"histories/s (SC+MSC+SM on Euclidean thick rays, d_0 = {d0:g} mm)",
+            "value": n / (ms_scan * 1e-3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_scan, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int64/int128",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD + f"; voxel centres within {d0:g} mm of each path",
+                       "histories": n, "fraction": args.fraction,
+                       "step": "a scan set to the distance (hd_scan_set_thick_distance): "
+                               "reset, add, finalize"},
+            "standalone": {"what": "hd_accumulate_euclid (counts only)", "ms_per_step": ms,
+                           "histories_per_s": n / (ms * 1e-3),
+                           "thick_voxels_per_s": voxels / (ms * 1e-3),
+                           "rows_per_s": n_rows / (ms * 1e-3), "rows_per_step": n_rows,
+                           "voxels_per_row": voxels / n_rows if n_rows else None},
+            "gpu_launches": 4 * args.steps, "clocks": clocks}
+    if not args.no_cpu_baseline:
+        import oracle
+        import time as _time
+        sub = synth.make_config(2, fraction=0.0005)
+        t0 = _time.perf_counter()
+        oracle.accumulate_euclid(g, sub.histories, d0)
+        dt = _time.perf_counter() - t0
+        line["cpu_baseline"] = {"value": len(sub.histories) / dt, "unit": UNIT, "cores": 1,
+                                "kind": "oracle",
+                                "sample": f"{len(sub.histories)} histories (50 per angle)"}
+    print(json.dumps(line), flush=True)
+
+
 def run_diagnostics(args):
     """Extra and missing voxels of every hull against the synthetic object
     (the measures of Tables 1-2) on the head-sized scan, all computed on the
@@ -883,7 +975,7 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--workload", default="head-200",
                     choices=["head-200", "batched-48", "serving", "rows", "binned",
-                             "diagnostics", "thick"])
+                             "diagnostics", "thick", "euclid"])
     ap.add_argument("--batch-fraction", type=float, default=1.0)
     ap.add_argument("--fraction", type=float, default=1.0,
                     help="head-200 workload: keep this fraction of the histories "
@@ -891,6 +983,8 @@ def main():
     ap.add_argument("--no-tune", action="store_true")
     ap.add_argument("--thick-k", type=int, default=2,
                     help="thick workload: in-plane dilation in voxels")
+    ap.add_argument("--thick-mm", type=float, default=2.5,
+                    help="euclid workload: distance d_0 from voxel centres to the path, mm")
     ap.add_argument("--serve-scans", type=int, default=48)
     ap.add_argument("--serve-load", type=float, default=0.7)
     ap.add_argument("--serve-clients", type=int, default=8)
@@ -917,6 +1011,9 @@ def main():
         return
     if args.workload == "thick":
         run_thick(args)
+        return
+    if args.workload == "euclid":
+        run_euclid(args)
         return
 
     if args.impl == "reference":

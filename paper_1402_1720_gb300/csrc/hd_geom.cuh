@@ -235,10 +235,52 @@ HD_HD bool endpoints(const GeomQ &g, const Cordic &cd, float ang, float ui, floa
     return endpoints_cs(g, c, s, ui, vi, uo, vo, out);
 }
 
-// Tiles a record can touch: the bounding box of its segment clamped to the
-// grid, in tile units.  Returns the number of tiles, 0 when the box misses
-// the grid (the segment then has no voxel at all).
-HD_HD int tile_range(const TilePlan &tp, const int32_t r[6], int lo[3], int hi[3])
+// The slices the part of a segment inside the grid's x-y extent can touch:
+// the parameter interval [t_lo, t_hi] of the segment r (grid Q16) inside
+// [0, nx) x [0, ny) (closed at its ends, exact rationals), and the z
+// indices at its two ends, ordered and clamped to the grid.  A superset of
+// the slices that hold voxels of the segment (z is monotone along it);
+// false when the segment misses the grid.
+HD_HD bool grid_z_range(const TilePlan &tp, const int32_t r[6], int &zlo, int &zhi)
+{
+    // t_lo = nl / dl, t_hi = nh / dh (den > 0)
+    long long nl = 0, dl = 1, nh = 1, dh = 1;
+    const int H[2] = {tp.nx << 16, tp.ny << 16};
+#pragma unroll
+    for (int a = 0; a < 2; ++a) {
+        const long long p = r[a], d = static_cast<long long>(r[a + 3]) - r[a];
+        long long en = 0, ed = 1, xn = 1, xd = 1;  // entry and exit parameters
+        if (d > 0) {
+            if (p >= H[a] || p + d < 0) return false;
+            if (p < 0) { en = -p; ed = d; }
+            if (p + d > H[a]) { xn = H[a] - p; xd = d; }
+        } else if (d < 0) {
+            if (p < 0 || p + d >= H[a]) return false;
+            if (p >= H[a]) { en = p - H[a]; ed = -d; }
+            if (p + d < 0) { xn = p; xd = -d; }
+        } else if (p < 0 || p >= H[a]) {
+            return false;
+        }
+        if (en * dl > nl * ed) { nl = en; dl = ed; }
+        if (xn * dh < nh * xd) { nh = xn; dh = xd; }
+    }
+    if (nl * dh > nh * dl) return false;
+    const long long z = r[2], dz = static_cast<long long>(r[5]) - r[2];
+    int z0 = static_cast<int>(floordiv_small(z * dl + nl * dz, dl << 16));
+    int z1 = static_cast<int>(floordiv_small(z * dh + nh * dz, dh << 16));
+    if (z0 > z1) { const int t = z0; z0 = z1; z1 = t; }
+    if (z1 < 0 || z0 >= tp.nz) return false;
+    zlo = z0 < 0 ? 0 : z0;
+    zhi = z1 >= tp.nz ? tp.nz - 1 : z1;
+    return true;
+}
+
+// Tiles a record can touch, given its slices zlo..zhi (grid_z_range): in x
+// and y the bounding box of its segment clamped to the grid, in z those
+// slices, in tile units.  Returns the number of tiles (0 when the box
+// misses the grid).
+HD_HD int tile_range_z(const TilePlan &tp, const int32_t r[6], int zlo, int zhi, int lo[3],
+                       int hi[3])
 {
     const int n[3] = {tp.nx, tp.ny, tp.nz};
     const unsigned m[3] = {tp.mtx, tp.mty, tp.mtz};
@@ -247,6 +289,10 @@ HD_HD int tile_range(const TilePlan &tp, const int32_t r[6], int lo[3], int hi[3
     for (int a = 0; a < 3; ++a) {
         const int a0 = r[a] >> 16, a1 = r[a + 3] >> 16;
         int mn = a0 < a1 ? a0 : a1, mx = a0 < a1 ? a1 : a0;
+        if (a == 2) {
+            mn = zlo;
+            mx = zhi;
+        }
         if (mx < 0 || mn >= n[a]) return 0;
         mn = mn < 0 ? 0 : mn;
         mx = mx >= n[a] ? n[a] - 1 : mx;
@@ -258,6 +304,26 @@ HD_HD int tile_range(const TilePlan &tp, const int32_t r[6], int lo[3], int hi[3
     }
     return cnt;
 }
+
+// tile_range_z with the slices of grid_z_range; 0 when the segment misses
+// the grid (it then has no voxel at all).
+HD_HD int tile_range(const TilePlan &tp, const int32_t r[6], int lo[3], int hi[3])
+{
+    int zlo, zhi;
+    if (!grid_z_range(tp, r, zlo, zhi)) return 0;
+    return tile_range_z(tp, r, zlo, zhi, lo, hi);
+}
+
+// A record's status word: bits 0-7 the path (1 tiled, 2 global), bits 8-19
+// and 20-31 its first and last slice (grid_z_range, computed once).
+HD_HD int32_t record_status(int path, int zlo, int zhi)
+{
+    return static_cast<int32_t>(static_cast<uint32_t>(path) | (static_cast<uint32_t>(zlo) << 8) |
+                                (static_cast<uint32_t>(zhi) << 20));
+}
+HD_HD int status_path(int32_t s) { return s & 0xff; }
+HD_HD int status_zlo(int32_t s) { return (static_cast<uint32_t>(s) >> 8) & 0xfff; }
+HD_HD int status_zhi(int32_t s) { return static_cast<uint32_t>(s) >> 20; }
 
 // ------------------------------------------------------------------ walk
 
@@ -829,6 +895,204 @@ HD_HD void lean_pack(const LeanWalk &L, uint32_t o[kLeanWords])
     o[5] = static_cast<uint32_t>(L.im0) | (static_cast<uint32_t>(L.fl) << 16);
     o[6] = static_cast<uint32_t>(L.row);
     o[7] = 0;
+}
+
+// The lean walk of the segment gi -> go (grid Q16, relative to the box
+// origin) in a one-slice box [0, nx) x [0, ny) x [0, 1), computed directly:
+// the same LeanWalk as lean_of(run_begin(...)) gives, without the general
+// set-up's machinery.  In a one-slice box z never crosses inside (its only
+// crossing ends the walk), the z index at the entry point is 0 or 1 (one
+// comparison), the axis that sets the entry parameter needs no division,
+// and z's crossing matters only through j_z, so its major-step quotient is
+// not needed.  An axis moving - that enters through its upper face starts
+// one voxel outside and takes that crossing first (as walk_begin does);
+// when another axis moving - is exactly on a plane at the entry (a tie) or
+// two axes enter that way, and for walks without in-plane motion, it
+// returns -1 and the caller takes the general set-up.  Returns 1 (lean, L
+// filled), 0 (no voxel in the box) or -1 (use run_begin and lean_of).
+HD_HD int slab_lean(const int32_t gi[3], const int32_t go[3], int nx, int ny, LeanWalk &L)
+{
+    // 32-bit storage throughout (|P| < 2^30, |D| < 2^31, plane distances
+    // below 2^31); only products are 64-bit
+    const int P[3] = {gi[0], gi[1], gi[2]};
+    const int D[3] = {go[0] - gi[0], go[1] - gi[1], go[2] - gi[2]};
+    const int n[3] = {nx, ny, 1};
+    const int H[3] = {nx << 16, ny << 16, 1 << 16};
+    if (D[0] == 0 && D[1] == 0) return -1;
+    // entry parameter tN / tQ (the largest per-axis entry) and its axis
+    unsigned tN = 0, tQ = 1;
+    int lim = -1;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        unsigned cN = 0, cQ = 1;
+        bool cand = false;
+        if (D[a] > 0) {
+            if (P[a] >= H[a]) return 0;
+            if (P[a] < 0) { cN = static_cast<unsigned>(-P[a]); cQ = static_cast<unsigned>(D[a]); cand = true; }
+        } else if (D[a] < 0) {
+            if (P[a] < 0) return 0;
+            if (P[a] >= H[a]) { cN = static_cast<unsigned>(P[a] - H[a]); cQ = static_cast<unsigned>(-D[a]); cand = true; }
+        } else if (P[a] < 0 || P[a] >= H[a]) {
+            return 0;
+        }
+        if (cand && static_cast<unsigned long long>(cN) * tQ > static_cast<unsigned long long>(tN) * cQ) {
+            tN = cN;
+            tQ = cQ;
+            lim = a;
+        }
+    }
+    if (tN > tQ) return 0;
+    // voxel indices at the entry point, and whether that point lies on a
+    // plane of each axis (remainder 0)
+    int idx[3];
+    bool onp[3];
+    const long long den = static_cast<long long>(tQ) << 16;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        if (tN == 0) {
+            idx[a] = P[a] >> 16;
+            onp[a] = (P[a] & 0xffff) == 0;
+        } else if (a == lim) {
+            idx[a] = D[a] > 0 ? 0 : n[a];
+            onp[a] = true;
+        } else {
+            const long long num = static_cast<long long>(P[a]) * tQ + static_cast<long long>(tN) * D[a];
+            if (a == 2) {
+                // the z index is all the emptiness checks and the upper-face
+                // entry need: below the slab, in it, or on or above its top
+                idx[2] = num < 0 ? -1 : (num >= den ? 1 : 0);
+                onp[2] = num == 0 || num == den;
+            } else {
+                const long long q = floordiv_small(num, den);
+                idx[a] = static_cast<int>(q);
+                onp[a] = num == q * den;
+            }
+        }
+    }
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+        if ((D[a] > 0 && idx[a] >= n[a]) || (D[a] < 0 && idx[a] < 0)) return 0;
+    // an axis moving - that enters through its upper face starts one voxel
+    // outside; its crossing at the entry parameter comes first unless another
+    // axis moving - is on a plane there too (a tie: general set-up)
+    int out = -1;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        if (idx[a] >= n[a]) {
+            if (out >= 0) return -1;
+            out = a;
+        }
+    }
+    if (out >= 0) {
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            if (a != out && D[a] < 0 && onp[a]) return -1;
+            if (a == out) idx[a] -= 1;
+        }
+    }
+    // distances from the segment's start to each axis' next plane, and the
+    // crossings left inside the box
+    int nm[3], k[3];
+    unsigned A[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const int f = go[a] >> 16;
+        if (D[a] > 0) {
+            A[a] = static_cast<unsigned>(D[a]);
+            nm[a] = ((idx[a] + 1) << 16) - P[a];
+            k[a] = (f < n[a] - 1 ? f : n[a] - 1) - idx[a];
+        } else if (D[a] < 0) {
+            A[a] = static_cast<unsigned>(-D[a]);
+            nm[a] = P[a] - (idx[a] << 16);
+            k[a] = idx[a] - (f > 0 ? f : 0);
+        } else {
+            A[a] = 0;
+            nm[a] = 1;
+            k[a] = 0;
+        }
+        if (k[a] < 0) return 0;  // the walk ends where it enters
+    }
+    if (k[2] != 0) return -1;
+    // axes: major m, minor 0 (the other in-plane axis), minor 1 (z); every
+    // array is read at constant indices (a runtime index would put it in
+    // local memory)
+    const bool ymaj = A[1] > A[0];
+    const unsigned am = ymaj ? A[1] : A[0];
+    const unsigned a0 = ymaj ? A[0] : A[1];
+    const unsigned a1 = A[2];
+    const long long nmm = ymaj ? nm[1] : nm[0], nmc = ymaj ? nm[0] : nm[1];
+    const long long nmz = nm[2];
+    // crossing-order terms against the major axis (D_c of run_begin), and
+    // between the minors (e12); two axes that never move never cross
+    const long long d0 = a0 == 0 ? -1 : nmc * am - nmm * a0;
+    const long long d1 = a1 == 0 ? -1 : nmz * am - nmm * a1;
+    const long long e12 = (a0 == 0 && a1 == 0) ? 1 : nmc * a1 - nmz * a0;
+    const bool act0 = a0 != 0, act1 = a1 != 0;
+    int q0 = kQBig, q1 = kQBig;
+    unsigned rh0 = 0, Ru0 = 0;
+    int Qu0 = kQBig;
+    if (act0) {
+        if ((d0 & 0xffff) == 0) return -1;  // minor 0 may tie with the major axis
+        const unsigned qu = am / a0;
+        Qu0 = qu >= (1u << 20) ? kQBig : static_cast<int>(qu);
+        Ru0 = am - qu * a0;
+        const long long dh = d0 >> 16;
+        if (float_of(dh) >= 1048576.0f * static_cast<float>(a0)) {
+            q0 = kQBig;
+            rh0 = 1;
+        } else {
+            const long long q = floordiv_small(dh, static_cast<long long>(a0));
+            q0 = static_cast<int>(q);
+            rh0 = static_cast<unsigned>(dh - q * static_cast<long long>(a0));
+        }
+    }
+    if (act1) {
+        if ((d1 & 0xffff) == 0) return -1;  // z may tie with the major axis
+        const long long dh = d1 >> 16;
+        if (float_of(dh) >= 1048576.0f * static_cast<float>(a1)) {
+            q1 = kQBig;
+        } else {
+            q1 = static_cast<int>(floordiv_small(dh, static_cast<long long>(a1)));
+        }
+    }
+    if (q0 < -1 || q1 < -1) return -1;
+    const int km = ymaj ? k[1] : k[0], kc0 = ymaj ? k[0] : k[1];
+    int kz;  // minor-0 crossings before z's
+    if (!act0) {
+        kz = 0;
+    } else if (!act1) {
+        kz = kc0;
+    } else {
+        if ((e12 & 0xffff) == 0) return -1;  // minor 0 and z may tie
+        if (e12 > 0) {
+            kz = 0;
+        } else {
+            const long long step = static_cast<long long>(a1) << 16;
+            const long long num = -e12 - 1;
+            if (float_of(num) >= (static_cast<float>(kc0) + 2.0f) * float_of(step)) {
+                kz = kc0;
+            } else {
+                const long long q = floordiv_small(num, step) + 1;
+                kz = q < kc0 ? static_cast<int>(q) : kc0;
+            }
+        }
+    }
+    L.K = act0 ? (kz < kc0 ? kz : kc0) : 0;
+    L.kleft = L.K;
+    const int jz = act1 ? q1 + 1 : kQBig;
+    L.kmz = km < jz ? km : jz;
+    const int j1 = act0 ? q0 + 1 : kQBig;
+    L.jn = j1 < kLeanJCap ? j1 : kLeanJCap;
+    L.Qu = Qu0 < kLeanQuCap ? Qu0 : kLeanQuCap;
+    L.ad = act0 ? a0 : 1u;
+    L.Ru = Ru0;
+    L.rem = rh0;
+    L.s = 0;
+    L.im0 = ymaj ? idx[1] : idx[0];
+    L.row = ymaj ? idx[0] : idx[1];
+    const bool pm = (ymaj ? D[1] : D[0]) > 0, pc = (ymaj ? D[0] : D[1]) > 0;
+    L.fl = (pm ? 1 : 0) | ((pc ? 1 : 0) << 1) | ((ymaj ? 1 : 0) << 2);
+    return 1;
 }
 
 // A packed walk with no voxel.

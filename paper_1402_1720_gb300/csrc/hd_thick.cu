@@ -220,7 +220,7 @@ __global__ void __launch_bounds__(kThickThreads) thick_records_kernel(Records re
          i += stride) {
         const bool miss = i < nm;
         const int64_t slot = miss ? i : rec.cap - 1 - (i - nm);
-        if (rec.status[slot] != 2) continue;
+        if (status_path(rec.status[slot]) != 2) continue;
         const int32_t gi[3] = {rec.g[0][slot], rec.g[1][slot], rec.g[2][slot]};
         const int32_t go[3] = {rec.g[3][slot], rec.g[4][slot], rec.g[5][slot]};
         RunWalk wk;

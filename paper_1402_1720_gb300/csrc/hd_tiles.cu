@@ -105,6 +105,30 @@ __global__ void __launch_bounds__(1024) plan_kernel(TilePlan tp, const uint32_t 
     }
 }
 
+// The general set-up of one (record, tile) pair: its packed lean walk, an
+// empty walk, or (returns true) the general form for the fallback list.
+__device__ __noinline__ bool general_setup(const int32_t gi[3], const int32_t go[3], int dx,
+                                           int dy, int dz, int tile, int cls, uint4 &p0,
+                                           uint4 &p1)
+{
+    RunWalk w;
+    LeanWalk L;
+    uint32_t pk[kLeanWords];
+    bool fallback = false;
+    if (!run_begin(w, gi, go, dx, dy, dz)) {
+        lean_pack_empty(pk);
+    } else if (lean_of(w, L)) {
+        lean_pack(L, pk);
+    } else {
+        // walked from the fallback list by the general run walk
+        general_pack(gi, go, tile, cls, pk);
+        fallback = true;
+    }
+    p0 = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+    p1 = make_uint4(pk[4], pk[5], pk[6], pk[7]);
+    return fallback;
+}
+
 // Counting sort of (record, tile) pairs by tile.  Each block takes a range
 // of record slots, histograms its pairs, reserves one range per tile with a
 // single global atomic, then writes its pairs.
@@ -121,21 +145,24 @@ __global__ void __launch_bounds__(kScatterThreads, 4) scatter_kernel(TilePlan tp
     __syncthreads();
     const unsigned nm = ctrl->rec_miss, nh = ctrl->rec_hit;
     const int64_t slot0 = static_cast<int64_t>(blockIdx.x) * kScatterThreads * per_thread;
-    auto valid = [&](int64_t slot, int &cls) -> bool {
+    // a tiled record of either class, and its status word
+    auto valid = [&](int64_t slot, int &cls, int32_t &stw) -> bool {
         if (slot < nm) { cls = 0; }
         else if (slot >= rec.cap - nh) { cls = 1; }
         else return false;
-        return rec.status[slot] == 1;
+        stw = rec.status[slot];
+        return status_path(stw) == 1;
     };
     for (int k = 0; k < per_thread; ++k) {
         const int64_t slot = slot0 + k * kScatterThreads + threadIdx.x;
         int cls;
-        if (slot >= rec.cap || !valid(slot, cls)) continue;
+        int32_t stw;
+        if (slot >= rec.cap || !valid(slot, cls, stw)) continue;
         int32_t r[6];
 #pragma unroll
         for (int a = 0; a < 6; ++a) r[a] = rec.g[a][slot];
         int lo[3], hi[3];
-        if (tile_range(tp, r, lo, hi) == 0) continue;
+        if (tile_range_z(tp, r, status_zlo(stw), status_zhi(stw), lo, hi) == 0) continue;
         for (int z = lo[2]; z <= hi[2]; ++z)
             for (int y = lo[1]; y <= hi[1]; ++y)
                 for (int x = lo[0]; x <= hi[0]; ++x)
@@ -157,10 +184,11 @@ __global__ void __launch_bounds__(kScatterThreads, 4) scatter_kernel(TilePlan tp
         int32_t r[6] = {0, 0, 0, 0, 0, 0};
         int lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
         int cnt = 0;
-        if (slot < rec.cap && valid(slot, cls)) {
+        int32_t stw;
+        if (slot < rec.cap && valid(slot, cls, stw)) {
 #pragma unroll
             for (int a = 0; a < 6; ++a) r[a] = rec.g[a][slot];
-            cnt = tile_range(tp, r, lo, hi);
+            cnt = tile_range_z(tp, r, status_zlo(stw), status_zhi(stw), lo, hi);
         }
         const int incl = static_cast<int>(warp_incl_scan_u(static_cast<unsigned>(cnt)));
         const int total = __shfl_sync(kFull, incl, 31);
@@ -197,21 +225,31 @@ __global__ void __launch_bounds__(kScatterThreads, 4) scatter_kernel(TilePlan tp
                       dz = min(tp.tz, tp.nz - z0);
             const int32_t gi[3] = {q[0] - (x0 << 16), q[1] - (y0 << 16), q[2] - (z0 << 16)};
             const int32_t go[3] = {q[3] - (x0 << 16), q[4] - (y0 << 16), q[5] - (z0 << 16)};
-            RunWalk w;
-            LeanWalk L;
-            uint32_t pk[kLeanWords];
+            // one-slice tiles (the default plan): the direct set-up; the
+            // walks it declines (ties at the start, no in-plane motion) go to
+            // the fallback list, whose general run walk is exact for any walk.
+            // Deeper slabs: the general set-up (out of line).
+            uint4 p0, p1;
             bool fallback = false;
-            if (!run_begin(w, gi, go, dx, dy, dz)) {
-                lean_pack_empty(pk);
-            } else if (lean_of(w, L)) {
-                lean_pack(L, pk);
+            if (dz == 1) {
+                LeanWalk L;
+                const int rl = slab_lean(gi, go, dx, dy, L);
+                uint32_t pk[kLeanWords];
+                if (rl == 1) {
+                    lean_pack(L, pk);
+                } else if (rl == 0) {
+                    lean_pack_empty(pk);
+                } else {
+                    general_pack(gi, go, t - ocls * tp.ntiles, ocls, pk);
+                    fallback = true;
+                }
+                p0 = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+                p1 = make_uint4(pk[4], pk[5], pk[6], pk[7]);
             } else {
-                // walked from the fallback list by the general run walk
-                general_pack(gi, go, t - ocls * tp.ntiles, ocls, pk);
-                fallback = true;
+                fallback = general_setup(gi, go, dx, dy, dz, t - ocls * tp.ntiles, ocls, p0, p1);
             }
-            pairs.v[2 * static_cast<size_t>(pos)] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
-            pairs.v[2 * static_cast<size_t>(pos) + 1] = make_uint4(pk[4], pk[5], pk[6], pk[7]);
+            pairs.v[2 * static_cast<size_t>(pos)] = p0;
+            pairs.v[2 * static_cast<size_t>(pos) + 1] = p1;
             if (fallback) {
                 // append to the fallback list, one counter update per group of
                 // lanes arriving together

@@ -122,17 +122,20 @@ __device__ __forceinline__ void admit_and_append(const TilePlan &tp, const Recor
 {
     const unsigned lane = threadIdx.x & 31u;
     int tcount[4];
+    int zr[4];  // the record's slices, zlo + 4096 zhi (computed once here)
     unsigned demand = 0;
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
         tcount[k] = 0;
+        zr[k] = 0;
         if (cls[k] == 0) continue;
-        int lo[3], hi[3];
-        const int c = tile_range(tp, r[k], lo, hi);
+        int lo[3], hi[3], zlo, zhi;
+        const int c = grid_z_range(tp, r[k], zlo, zhi) ? tile_range_z(tp, r[k], zlo, zhi, lo, hi) : 0;
         if (c == 0) {
             cls[k] = 0;  // no voxel of the grid: nothing to traverse
             continue;
         }
+        zr[k] = zlo + 4096 * zhi;
         tcount[k] = (tp.ntiles > 0 && c <= tp.max_tiles) ? c : -1;
         if (tcount[k] > 0) demand += static_cast<unsigned>(c);
     }
@@ -177,7 +180,7 @@ __device__ __forceinline__ void admit_and_append(const TilePlan &tp, const Recor
         }
         if (cls[k] != 0 && status[k] == 1) {
             int lo[3], hi[3];
-            tile_range(tp, r[k], lo, hi);
+            tile_range_z(tp, r[k], zr[k] & 4095, zr[k] >> 12, lo, hi);
             const int off = (cls[k] - 1) * tp.ntiles;
             for (int z = lo[2]; z <= hi[2]; ++z)
                 for (int y = lo[1]; y <= hi[1]; ++y)
@@ -197,7 +200,7 @@ __device__ __forceinline__ void admit_and_append(const TilePlan &tp, const Recor
             cls[k] == 1 ? static_cast<int64_t>(pm++) : rec.cap - 1 - static_cast<int64_t>(ph++);
 #pragma unroll
         for (int a = 0; a < 6; ++a) rec.g[a][slot] = r[k][a];
-        rec.status[slot] = status[k];
+        rec.status[slot] = record_status(status[k], zr[k] & 4095, zr[k] >> 12);
     }
 }
 
@@ -285,7 +288,7 @@ __global__ void __launch_bounds__(256) trace_global_kernel(Records rec, Ctrl *ct
          i += stride) {
         const bool miss = i < nm;
         const int64_t slot = miss ? i : rec.cap - 1 - (i - nm);
-        if (!all_records && rec.status[slot] != 2) continue;
+        if (!all_records && status_path(rec.status[slot]) != 2) continue;
         const int32_t gi[3] = {rec.g[0][slot], rec.g[1][slot], rec.g[2][slot]};
         const int32_t go[3] = {rec.g[3][slot], rec.g[4][slot], rec.g[5][slot]};
         GlobalVisit v;

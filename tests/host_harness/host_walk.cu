@@ -216,3 +216,41 @@ extern "C" int hx_tile_cursor(const int32_t *gi, const int32_t *go, int dx, int 
             }
     return n;
 }
+// the direct one-slice set-up against the general one: returns 1 when both
+// give the same packed lean walk, 2 when both find no voxel, 3 when the
+// direct one declines (-1) and the general one is lean or not, 4 when both
+// decline; negative on a disagreement (-10: emptiness differs, -11: the
+// direct one is lean where the general one is not, -12: packed words differ)
+extern "C" int hx_slab_lean(const int32_t *gi, const int32_t *go, int nx, int ny)
+{
+    hd::LeanWalk Ld;
+    const int rd = hd::slab_lean(gi, go, nx, ny, Ld);
+    hd::RunWalk w;
+    const bool nonempty = hd::run_begin(w, gi, go, nx, ny, 1);
+    hd::LeanWalk Lg;
+    const bool lean = nonempty && hd::lean_of(w, Lg);
+    if (rd == 0) return nonempty ? -10 : 2;
+    if (rd < 0) return lean ? 3 : 4;
+    if (!nonempty) return -10;
+    if (!lean) return -11;
+    uint32_t a[hd::kLeanWords], b[hd::kLeanWords];
+    hd::lean_pack(Ld, a);
+    hd::lean_pack(Lg, b);
+    for (int i = 0; i < hd::kLeanWords; ++i)
+        if (a[i] != b[i]) return -12;
+    return 1;
+}
+// tile_range of a segment for a plan of (tx, ty, tz) tiles over the grid
+extern "C" int hx_tile_range(const int32_t *r, int nx, int ny, int nz, int tx, int ty, int tz,
+                             int32_t *lo, int32_t *hi)
+{
+    hd::TilePlan tp{};
+    tp.nx = nx; tp.ny = ny; tp.nz = nz;
+    tp.tx = tx; tp.ty = ty; tp.tz = tz;
+    auto magic = [](int t) { return t == 1 ? 0u : static_cast<unsigned>((1ull << 32) / static_cast<unsigned>(t)) + 1u; };
+    tp.mtx = magic(tx); tp.mty = magic(ty); tp.mtz = magic(tz);
+    int l[3], h[3];
+    const int c = hd::tile_range(tp, r, l, h);
+    for (int a = 0; a < 3; ++a) { lo[a] = l[a]; hi[a] = h[a]; }
+    return c;
+}

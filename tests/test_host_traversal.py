@@ -277,3 +277,101 @@ def test_tile_cursor_equals_oracle(oracle_mod, hx, dims):
         if n > 0:
             assert 1 <= runs <= n
     assert n_lean > 300
+
+
+def _slab_segments(rng, count, dims):
+    """Segments for one-slice boxes: generic ones, ones with lattice-aligned
+    end points (shared planes, corners, entry through edges), nearly
+    axis-parallel ones and ones starting on faces of the box."""
+    Q = 65536
+    nx, ny = dims
+    hi = np.array([nx, ny, 1], np.int64) * Q
+    for k in range(count):
+        kind = k % 5
+        a = rng.integers(-2 * Q, hi + 2 * Q)
+        b = rng.integers(-2 * Q, hi + 2 * Q)
+        if kind == 0:
+            a[2] = rng.integers(-Q, 2 * Q)
+            b[2] = a[2] + rng.integers(-Q, Q + 1)
+        elif kind == 1:  # lattice points and planes
+            a = (rng.integers(-2, np.array([nx, ny, 1]) + 3) * Q).astype(np.int64)
+            b = (rng.integers(-2, np.array([nx, ny, 1]) + 3) * Q).astype(np.int64)
+            if k % 2:
+                b[rng.integers(0, 3)] += rng.integers(-3, 4)
+        elif kind == 2:  # nearly axis-parallel in the plane
+            ax = rng.integers(0, 2)
+            b[1 - ax] = a[1 - ax] + rng.integers(-2, 3)
+            b[2] = a[2] + rng.integers(-2, 3)
+        elif kind == 3:  # start or end exactly on a face of the slab or grid
+            a[rng.integers(0, 3)] = rng.choice([0, hi[0], hi[1], Q])
+            b[2] = rng.choice([0, Q, a[2]])
+        else:  # through the slab from above or below, steep in z
+            a[2] = rng.integers(-3 * Q, 0) if k % 2 else rng.integers(Q, 4 * Q)
+            b[2] = rng.integers(Q, 4 * Q) if k % 2 else rng.integers(-3 * Q, 0)
+        yield a, b
+
+
+@pytest.mark.parametrize("dims", [(200, 200), (41, 30), (7, 1), (1, 7), (400, 126), (3, 3)])
+def test_slab_lean_equals_general_setup(hx, dims):
+    """The direct set-up for one-slice boxes gives, bit for bit, the packed
+    lean walk of the general set-up (walk_begin, run_begin, lean_of), finds
+    the same empty walks, and never claims a lean form the general set-up
+    lacks; it declines (to the general set-up) only rarely on generic
+    segments."""
+    hx.hx_slab_lean.restype = ctypes.c_int
+    rng = np.random.default_rng(sum(dims) + 31)
+    counts = {}
+    for a, b in _slab_segments(rng, 20000, dims):
+        r = hx.hx_slab_lean(np.asarray(a, np.int32).ctypes.data_as(I32P),
+                            np.asarray(b, np.int32).ctypes.data_as(I32P), *dims)
+        assert r > 0, (r, a.tolist(), b.tolist())
+        counts[r] = counts.get(r, 0) + 1
+    assert counts.get(1, 0) > 2000
+    # generic segments (kind 0): the direct set-up covers nearly every lean one
+    gen = {}
+    rng = np.random.default_rng(sum(dims) + 37)
+    for k, (a, b) in enumerate(_slab_segments(rng, 5000, dims)):
+        if k % 5:
+            continue
+        r = hx.hx_slab_lean(np.asarray(a, np.int32).ctypes.data_as(I32P),
+                            np.asarray(b, np.int32).ctypes.data_as(I32P), *dims)
+        gen[r] = gen.get(r, 0) + 1
+    assert gen.get(3, 0) <= 0.02 * (gen.get(1, 0) + gen.get(3, 0)) + 2, gen
+
+
+@pytest.mark.parametrize("dims,tiles", [((200, 200, 32), (200, 200, 1)), ((40, 30, 20), (40, 30, 3)),
+                                        ((64, 48, 9), (64, 13, 1)), ((9, 9, 40), (9, 9, 7))])
+def test_tile_range_covers_the_voxel_set(oracle_mod, hx, dims, tiles):
+    """The tiles a record is bucketed into (x-y bounding box, slices of the
+    part inside the grid's x-y extent) hold every voxel of its set, and a
+    record gets no tile only when its set is empty."""
+    hx.hx_tile_range.restype = ctypes.c_int
+    rng = np.random.default_rng(sum(dims) + 43)
+    Q = 65536
+    hi = np.array(dims, np.int64) * Q
+    tight = 0
+    for k in range(3000):
+        a = rng.integers(-hi // 2, hi + hi // 2)
+        b = rng.integers(-hi // 2, hi + hi // 2)
+        if k % 3 == 0:  # lattice-aligned end points
+            a = (a >> 16) << 16
+            b = (b >> 16) << 16
+        r = np.concatenate([a, b]).astype(np.int32)
+        lo = np.zeros(3, np.int32)
+        up = np.zeros(3, np.int32)
+        c = hx.hx_tile_range(r.ctypes.data_as(I32P), *dims, *tiles, lo.ctypes.data_as(I32P),
+                             up.ctypes.data_as(I32P))
+        vs = oracle_mod.voxel_set(a, b, *dims)
+        if c == 0:
+            assert vs.size == 0, (a.tolist(), b.tolist())
+            continue
+        assert c == int(np.prod(up - lo + 1))
+        x = vs % dims[0]
+        y = (vs // dims[0]) % dims[1]
+        z = vs // (dims[0] * dims[1])
+        for v, t, l, u in ((x, tiles[0], lo[0], up[0]), (y, tiles[1], lo[1], up[1]),
+                           (z, tiles[2], lo[2], up[2])):
+            assert np.all(v // t >= l) and np.all(v // t <= u), (a.tolist(), b.tolist())
+        zb = np.clip(np.array([a[2], b[2]]) >> 16, 0, dims[2] - 1) // tiles[2]
+        tight += (up[2] - lo[2]) < (zb.max() - zb.min())
+    assert tight > 0  # the x-y clip removes slices the bounding box would add
