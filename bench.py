@@ -322,7 +322,10 @@ def measure_serving(args, specs, hosts):
     scans = []  # (spec, [chunk views of pinned tensors])
     total = 0
     for sp, h in zip(specs, hosts):
-        pinned = [torch.from_numpy(a).pin_memory() for a in h.arrays()]
+        # the six columns of a scan as rows of one page-locked 6 x n array:
+        # a chunk is submitted with one strided copy (hd_server_submit_rows)
+        block = torch.from_numpy(np.stack(h.arrays())).pin_memory()
+        pinned = [block[a] for a in range(6)]
         bounds = []
         angles = h.angle_deg
         starts = np.flatnonzero(np.r_[True, angles[1:] != angles[:-1]])
@@ -333,7 +336,7 @@ def measure_serving(args, specs, hosts):
                 e0 = min(a1, s0 + int(rng.integers(10_000, 100_001)))
                 bounds.append((s0, e0))
                 s0 = e0
-        scans.append((sp, [[p[a:b] for p in pinned] for a, b in bounds]))
+        scans.append((sp, [[p[a:b] for p in pinned] for a, b in bounds], block, bounds))
         total += len(h)
     cfg = hulld.hd_server_config_default()
     cfg.max_chunk = 100_000
@@ -360,7 +363,7 @@ def measure_serving(args, specs, hosts):
                         if k is None:
                             done = True
                             break
-                        sp, chunks = scans[k]
+                        sp, chunks = scans[k][0], scans[k][1]
                         ids[k] = srv.open_scan(sp.geometry, None, len(chunks))
                         active.append([k, 0])
                 except queue.Empty:
@@ -371,7 +374,8 @@ def measure_serving(args, specs, hosts):
                     continue
                 for item in list(active):
                     k, j = item
-                    srv.submit(ids[k], scans[k][1][j])
+                    a, b = scans[k][3][j]
+                    srv.submit_rows(ids[k], scans[k][2], int(a), int(b - a))
                     item[1] += 1
                     if item[1] == len(scans[k][1]):
                         active.remove(item)
@@ -424,7 +428,7 @@ def measure_serving(args, specs, hosts):
     torch.cuda.synchronize()
     t_seq = time.perf_counter()
     with torch.cuda.stream(seq_stream):
-        for sp, chunks in scans:
+        for sp, chunks, _, _ in scans:
             with hulld.Scan(sp.geometry) as s:
                 for c in chunks:
                     s.add(c, seq_stream)

@@ -426,7 +426,7 @@ HD_API hd_status hd_server_open_scan(hd_server *server, const hd_geometry *geom,
 
 /* Submit the next chunk of a scan (1 <= n <= max_chunk; host arrays, or
  * device arrays with on_device = 1).  The data is copied before the call
- * returns.  HD_ERR_STATE when the scan already has all its chunks (or is
+ * returns, one copy per array.  HD_ERR_STATE when the scan already has all its chunks (or is
  * finished); HD_ERR_TIMEOUT when no staging space freed up within
  * submit_timeout_ms (the chunk was not taken: submit it again);
  * HD_ERR_CUDA when the copy failed (the scan is then failed).  Several
@@ -436,6 +436,15 @@ HD_API hd_status hd_server_submit_chunk(hd_server *server, int64_t scan_id,
                                         const float *v_in, const float *u_out,
                                         const float *v_out, const float *wepl, int64_t n,
                                         int32_t on_device);
+
+/* The same for a chunk whose six columns are rows of one array (one
+ * allocation): angle, u_in, v_in, u_out, v_out and WEPL at rows,
+ * rows + pitch, ..., rows + 5 pitch (floats; pitch >= n), as a detector
+ * readout or a 6 x N tensor holds them.  One strided copy instead of six,
+ * which matters when many client threads submit small chunks.  HD_ERR_ARG
+ * when pitch < n; otherwise as hd_server_submit_chunk. */
+HD_API hd_status hd_server_submit_rows(hd_server *server, int64_t scan_id, const float *rows,
+                                       int64_t pitch, int64_t n, int32_t on_device);
 
 /* *done = 1 once the scan's hulls are ready (or it failed: see scan_status). */
 HD_API hd_status hd_server_poll(hd_server *server, int64_t scan_id, int32_t *done,

@@ -17,6 +17,7 @@
 // segments.  The server uses only the public scan and batch calls.
 #include <chrono>
 #include <condition_variable>
+#include <cstddef>
 #include <cstring>
 #include <deque>
 #include <map>
@@ -516,10 +517,15 @@ hd_status hd_server_open_scan(hd_server *sv, const hd_geometry *geom, const hd_p
     return HD_OK;
 }
 
-hd_status hd_server_submit_chunk(hd_server *sv, int64_t scan_id, const float *angle_deg,
-                                 const float *u_in, const float *v_in, const float *u_out,
-                                 const float *v_out, const float *wepl, int64_t n,
-                                 int32_t on_device)
+}  // extern "C"
+
+namespace {
+
+// A submit: reserve staging space, copy the chunk in (per column, or one
+// strided copy when pitch > 0: column a at angle_deg + a pitch), account.
+hd_status submit(hd_server *sv, int64_t scan_id, const float *angle_deg, const float *u_in,
+                 const float *v_in, const float *u_out, const float *v_out, const float *wepl,
+                 int64_t n, int64_t pitch, int32_t on_device)
 {
     if (!sv || n < 1 || n > sv->cfg.max_chunk) return HD_ERR_ARG;
     if (!angle_deg || !u_in || !v_in || !u_out || !v_out || !wepl) return HD_ERR_ARG;
@@ -597,10 +603,17 @@ hd_status hd_server_submit_chunk(hd_server *sv, int64_t scan_id, const float *an
     const auto t_copy = std::chrono::steady_clock::now();
     const cudaStream_t up = upload_stream(sv->device);
     const float *src[6] = {angle_deg, u_in, v_in, u_out, v_out, wepl};
+    const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
     cudaError_t e = up ? cudaSuccess : cudaErrorUnknown;
-    for (int a = 0; e == cudaSuccess && a < 6; ++a)
-        e = cudaMemcpyAsync(seg->dev + a * cap + off, src[a], sizeof(float) * n,
-                            on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, up);
+    if (e == cudaSuccess && pitch > 0) {
+        // the six columns are rows of one array: one strided copy
+        e = cudaMemcpy2DAsync(seg->dev + off, sizeof(float) * static_cast<size_t>(cap), src[0],
+                              sizeof(float) * static_cast<size_t>(pitch),
+                              sizeof(float) * static_cast<size_t>(n), 6, kind, up);
+    } else {
+        for (int a = 0; e == cudaSuccess && a < 6; ++a)
+            e = cudaMemcpyAsync(seg->dev + a * cap + off, src[a], sizeof(float) * n, kind, up);
+    }
     // the caller may reuse its buffers as soon as this call returns
     if (e == cudaSuccess) e = cudaStreamSynchronize(up);
     if (e != cudaSuccess) cudaGetLastError();
@@ -630,6 +643,26 @@ hd_status hd_server_submit_chunk(hd_server *sv, int64_t scan_id, const float *an
         std::chrono::duration<double>(std::chrono::steady_clock::now() - t_submit).count();
     sv->cv_work.notify_all();
     return HD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+hd_status hd_server_submit_chunk(hd_server *sv, int64_t scan_id, const float *angle_deg,
+                                 const float *u_in, const float *v_in, const float *u_out,
+                                 const float *v_out, const float *wepl, int64_t n,
+                                 int32_t on_device)
+{
+    return submit(sv, scan_id, angle_deg, u_in, v_in, u_out, v_out, wepl, n, 0, on_device);
+}
+
+hd_status hd_server_submit_rows(hd_server *sv, int64_t scan_id, const float *rows, int64_t pitch,
+                                int64_t n, int32_t on_device)
+{
+    if (!rows || pitch < n) return HD_ERR_ARG;
+    return submit(sv, scan_id, rows, rows + pitch, rows + 2 * pitch, rows + 3 * pitch,
+                  rows + 4 * pitch, rows + 5 * pitch, n, pitch, on_device);
 }
 
 hd_status hd_server_poll(hd_server *sv, int64_t scan_id, int32_t *done, hd_status *scan_status)

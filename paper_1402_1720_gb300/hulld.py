@@ -181,6 +181,7 @@ _SIGS = {
     "hd_server_open_scan": ([_VP, ctypes.POINTER(hd_geometry), ctypes.POINTER(hd_params), _I32,
                              ctypes.POINTER(_I64)], ctypes.c_int),
     "hd_server_submit_chunk": ([_VP, _I64] + [_VP] * 6 + [_I64, _I32], ctypes.c_int),
+    "hd_server_submit_rows": ([_VP, _I64, _VP, _I64, _I64, _I32], ctypes.c_int),
     "hd_server_poll": ([_VP, _I64, ctypes.POINTER(_I32), ctypes.POINTER(ctypes.c_int)],
                        ctypes.c_int),
     "hd_server_wait": ([_VP, _I64, _I64], ctypes.c_int),
@@ -593,6 +594,21 @@ def hd_server_submit_chunk(server: int, scan_id: int, angle_deg, u_in, v_in, u_o
                                          len(arrs[0]), ons.pop()), "hd_server_submit_chunk")
 
 
+def hd_server_submit_rows(server: int, scan_id: int, rows, start: int, n: int) -> None:
+    """Submit histories start .. start + n of a 6 x N float32 array `rows`
+    (host or device torch tensor, or numpy array; row a is column a of the
+    structure of arrays) with one strided copy."""
+    if getattr(rows, "ndim", 0) != 2 or rows.shape[0] != 6:
+        raise ValueError("rows must be a 6 x N array")
+    stride = rows.stride(0) if _is_torch(rows) else rows.strides[0] // rows.itemsize
+    inner = rows.stride(1) if _is_torch(rows) else rows.strides[1] // rows.itemsize
+    if inner != 1 or start < 0 or start + n > rows.shape[1]:
+        raise ValueError("rows must be contiguous along histories and hold the range")
+    base, on = _ptr(rows)
+    _check(load().hd_server_submit_rows(server, int(scan_id), int(base) + 4 * int(start),
+                                        int(stride), int(n), on), "hd_server_submit_rows")
+
+
 def hd_server_poll(server: int, scan_id: int):
     done = _I32()
     st = ctypes.c_int()
@@ -681,6 +697,10 @@ class Server:
 
     def submit(self, scan_id: int, arrays):
         hd_server_submit_chunk(self.handle, scan_id, *arrays)
+
+    def submit_rows(self, scan_id: int, rows, start: int, n: int):
+        """Histories start .. start + n of a 6 x N array (one strided copy)."""
+        hd_server_submit_rows(self.handle, scan_id, rows, start, n)
 
     def wait(self, scan_id: int, timeout_ms: int) -> int:
         return hd_server_wait(self.handle, scan_id, timeout_ms)

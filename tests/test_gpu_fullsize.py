@@ -168,14 +168,17 @@ def test_batch48_full_size_exact(hd, mix48):
 
 def test_served48_full_size_exact(hd, mix48):
     """The same 48 scans served: per-angle chunks of 1e4-1e5 histories from
-    page-locked host memory, submitted by four client threads round-robin
+    page-locked host memory (rows of one 6 x n array per scan, so each
+    submit is one strided copy), submitted by four client threads round-robin
     over their scans, all scans open at once; every served scan equals the
     oracle."""
     rec, scans = mix48
     rng = np.random.default_rng(20140207)
     payload = []
     for sp, h in scans:
-        pinned = [torch.from_numpy(a).pin_memory() for a in h.arrays()]
+        # rows of one page-locked 6 x n array, as a client would hold them
+        block = torch.from_numpy(np.stack(h.arrays())).pin_memory()
+        pinned = [block[a] for a in range(6)]
         starts = np.flatnonzero(np.r_[True, h.angle_deg[1:] != h.angle_deg[:-1]])
         ends = np.r_[starts[1:], len(h)]
         chunks = []
@@ -183,11 +186,11 @@ def test_served48_full_size_exact(hd, mix48):
             s0 = a0
             while s0 < a1:
                 e0 = min(a1, s0 + int(rng.integers(10_000, 100_001)))
-                chunks.append([p[s0:e0] for p in pinned])
+                chunks.append((int(s0), int(e0 - s0)))
                 s0 = e0
-        payload.append(chunks)
+        payload.append((block, chunks))
     with hd.Server() as srv:
-        ids = [srv.open_scan(sp.geometry, None, len(ch)) for (sp, _), ch in zip(scans, payload)]
+        ids = [srv.open_scan(sp.geometry, None, len(ch)) for (sp, _), (_, ch) in zip(scans, payload)]
         errors = []
 
         def client(me, nclients=4):
@@ -196,9 +199,10 @@ def test_served48_full_size_exact(hd, mix48):
             try:
                 while mine:
                     for k in list(mine):
-                        srv.submit(ids[k], payload[k][pos[k]])
+                        block, chunks = payload[k]
+                        srv.submit_rows(ids[k], block, *chunks[pos[k]])
                         pos[k] += 1
-                        if pos[k] == len(payload[k]):
+                        if pos[k] == len(chunks):
                             mine.remove(k)
             except Exception as e:  # pragma: no cover - reported below
                 errors.append(e)

@@ -72,18 +72,22 @@ def test_served_equals_alone(hd, oracle_mod, scans_case):
     with hd.Server() as srv:
         ids = [srv.open_scan(sp.geometry, None, len(ch)) for sp, _, ch in scans_case]
         # chunks alternate between pageable numpy arrays, page-locked host
-        # tensors and device tensors
+        # tensors, device tensors, and the rows of one page-locked or device
+        # 6 x n array (equally spaced columns: one strided copy per submit)
         payload = []
         for k, (_, _, ch) in enumerate(scans_case):
             row = []
             for j, c in enumerate(ch):
-                kind = (k + j) % 3
+                kind = (k + j) % 5
                 if kind == 0:
                     row.append(c.arrays())
                 elif kind == 1:
                     row.append([torch.from_numpy(a).pin_memory() for a in c.arrays()])
-                else:
+                elif kind == 2:
                     row.append([torch.from_numpy(a).cuda() for a in c.arrays()])
+                else:
+                    block = torch.from_numpy(np.stack(c.arrays()))
+                    row.append(block.pin_memory() if kind == 3 else block.cuda())
             payload.append(row)
         torch.cuda.synchronize()
 
@@ -93,7 +97,11 @@ def test_served_equals_alone(hd, oracle_mod, scans_case):
             while any(p < len(ch) for p, (_, _, ch) in zip(pos, scans_case)):
                 for k, (sid, (_, _, ch)) in enumerate(zip(ids, scans_case)):
                     if pos[k] < len(ch):
-                        srv.submit(sid, payload[k][pos[k]])
+                        item = payload[k][pos[k]]
+                        if isinstance(item, list):
+                            srv.submit(sid, item)
+                        else:  # a 6 x n array: one strided copy
+                            srv.submit_rows(sid, item, 0, item.shape[1])
                         pos[k] += 1
         t = threading.Thread(target=client)
         t.start()
