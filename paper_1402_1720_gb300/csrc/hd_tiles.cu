@@ -158,11 +158,20 @@ __global__ void __launch_bounds__(kScatterThreads, 4) scatter_kernel(TilePlan tp
         int cls;
         int32_t stw;
         if (slot >= rec.cap || !valid(slot, cls, stw)) continue;
-        int32_t r[6];
-#pragma unroll
-        for (int a = 0; a < 6; ++a) r[a] = rec.g[a][slot];
         int lo[3], hi[3];
-        if (tile_range_z(tp, r, status_zlo(stw), status_zhi(stw), lo, hi) == 0) continue;
+        if (tp.ntx == 1 && tp.nty == 1) {
+            // whole-plane tiles: the slices in the status word are all it takes
+            lo[0] = hi[0] = lo[1] = hi[1] = 0;
+            lo[2] = tp.mtz ? static_cast<int>(umulhi32(static_cast<unsigned>(status_zlo(stw)), tp.mtz))
+                           : status_zlo(stw);
+            hi[2] = tp.mtz ? static_cast<int>(umulhi32(static_cast<unsigned>(status_zhi(stw)), tp.mtz))
+                           : status_zhi(stw);
+        } else {
+            int32_t r[6];
+#pragma unroll
+            for (int a = 0; a < 6; ++a) r[a] = rec.g[a][slot];
+            if (tile_range_z(tp, r, status_zlo(stw), status_zhi(stw), lo, hi) == 0) continue;
+        }
         for (int z = lo[2]; z <= hi[2]; ++z)
             for (int y = lo[1]; y <= hi[1]; ++y)
                 for (int x = lo[0]; x <= hi[0]; ++x)

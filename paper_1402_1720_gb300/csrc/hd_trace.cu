@@ -217,14 +217,18 @@ __global__ void __launch_bounds__(256, 4) ingest_kernel(Inputs in, int64_t n, Ge
     __syncthreads();
     LaneAcc acc;
     TrigCache tc;
-    const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
-    const int64_t tid = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
-    // every thread runs the same number of iterations (warp-wide appends and
-    // the block-wide histogram flush), so the bound is rounded up
+    // each block takes a contiguous range of units (histories arrive grouped
+    // by gantry angle, so a thread's angle, and its cos/sin, rarely change),
+    // in coalesced steps of one unit per thread; every thread of a block runs
+    // the same number of steps (block-wide appends and histogram flush)
     const int64_t units = kVec ? (n + 3) / 4 : n;
-    const int64_t iters = (units + stride - 1) / stride;
+    const int64_t per_block = (units + gridDim.x - 1) / gridDim.x;
+    const int64_t u0 = static_cast<int64_t>(blockIdx.x) * per_block;
+    const int64_t u1 = u0 + per_block < units ? u0 + per_block : units;
+    const int64_t iters = (per_block + blockDim.x - 1) / blockDim.x;
     for (int64_t it = 0; it < iters; ++it) {
-        const int64_t u = tid + it * stride;
+        const int64_t uu = u0 + it * blockDim.x + threadIdx.x;
+        const int64_t u = uu < u1 ? uu : units;  // past the block's range: no history
         int cls[4] = {0, 0, 0, 0};
         int32_t r[4][6];
         if (kVec) {
