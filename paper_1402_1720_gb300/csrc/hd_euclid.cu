@@ -40,10 +40,17 @@ constexpr int kEuRunHistories = 16;  // consecutive histories a warp takes at on
 
 typedef unsigned __int128 u128;
 
+// Full product of two 64-bit unsigned values (two multiplies, not a
+// general 128 x 128 one).
+__device__ __forceinline__ u128 mul64(unsigned long long a, unsigned long long b)
+{
+    return (static_cast<u128>(__umul64hi(a, b)) << 64) | static_cast<u128>(a * b);
+}
+
 __device__ __forceinline__ u128 sq64(long long a)
 {
     const unsigned long long m = static_cast<unsigned long long>(a < 0 ? -a : a);
-    return static_cast<u128>(m) * m;
+    return mul64(m, m);
 }
 
 // One history's capsule in the permuted frame (axis 0 the major in-plane
@@ -52,7 +59,11 @@ struct Capsule {
     long long A[3], B[3], u[3];
     unsigned long long uu;  // |u|^2 (< 3 2^62)
     u128 T;                 // the threshold R^2 |u|^2 (or R^2 when u = 0)
+    unsigned long long RR;  // R^2
+    unsigned long long uu2; // u_1^2 + u_2^2: the segment projected along axis 0
+    u128 T2;                // R^2 uu2
     float Af[3], df[3], L2f, Rf;
+    float inv_L2, inv_d0, inv_s0;  // 1 / L2f, 1 / df[0], 1 / sf[0] (estimates only)
     int n[3];
     long long s2[3];  // voxel sizes, mm * 2^16 (centres are (2 i + 1 - n) s2)
     float sf[3];      // voxel sizes, mm
@@ -83,18 +94,19 @@ __device__ __forceinline__ Row row_of(const Capsule &cp, int a, int k)
     return r;
 }
 
-// F at index i of the row (see the file comment).
-__device__ __forceinline__ u128 F_at(const Capsule &cp, const Row &r, int i)
+// F at index i of the row (see the file comment).  Out of line: one copy of
+// the 128-bit arithmetic serves every test of the row search (inlined at
+// each of them, the kernel's code outgrew the instruction cache: 35 % slower).
+__device__ __noinline__ u128 F_at(const Capsule &cp, const Row &r, int i)
 {
     const long long cm = (2LL * i + 1 - cp.n[0]) * cp.s2[0];
     const long long wm = cm - cp.A[0];
     if (cp.uu == 0) return static_cast<u128>(static_cast<unsigned long long>(wm * wm) + r.hA);
     const __int128 dot = r.dot0 + static_cast<__int128>(wm) * cp.u[0];
-    if (dot <= 0)
-        return static_cast<u128>(static_cast<unsigned long long>(wm * wm) + r.hA) * cp.uu;
+    if (dot <= 0) return mul64(static_cast<unsigned long long>(wm * wm) + r.hA, cp.uu);
     if (dot >= static_cast<__int128>(cp.uu)) {
         const long long wbm = cm - cp.B[0];
-        return static_cast<u128>(static_cast<unsigned long long>(wbm * wbm) + r.hB) * cp.uu;
+        return mul64(static_cast<unsigned long long>(wbm * wbm) + r.hB, cp.uu);
     }
     const long long k1 = r.wz * cp.u[0] - wm * cp.u[2];
     const long long k2 = wm * cp.u[1] - r.wc * cp.u[0];
@@ -106,12 +118,26 @@ __device__ __forceinline__ bool in_at(const Capsule &cp, const Row &r, int i)
     return F_at(cp, r, i) <= cp.T;
 }
 
+// Does the row meet the capsule at all?  The row is a line along axis 0, so
+// it does iff its point in the plane of axes 1 and 2 lies within R of the
+// segment's projection onto that plane (the projection of the capsule is the
+// disc-swept projected segment): the same three cases in two dimensions,
+// with the row's constants (dot0 and k0 are that plane's dot and cross).
+__device__ __forceinline__ bool row_meets(const Capsule &cp, const Row &r)
+{
+    if (cp.uu2 == 0 || r.dot0 <= 0) return r.hA <= cp.RR;
+    if (r.dot0 >= static_cast<__int128>(cp.uu2)) return r.hB <= cp.RR;
+    return sq64(r.k0) <= cp.T2;
+}
+
 // Float estimate of the row's cross-section of the capsule, as a range of
 // major indices (lo > hi when the estimate finds none); also a float guess
 // of where along the row the distance is smallest.
 __device__ __forceinline__ void estimate(const Capsule &cp, int a, int k, int &ilo, int &ihi,
                                          int &imin)
 {
+    // approximate arithmetic throughout (fast square roots and quotients):
+    // these numbers only choose where the exact tests start
     const float cc = 0.5f * static_cast<float>(2 * a + 1 - cp.n[1]) * cp.sf[1];
     const float cz = 0.5f * static_cast<float>(2 * k + 1 - cp.n[2]) * cp.sf[2];
     const float wc = cc - cp.Af[1], wz = cz - cp.Af[2];
@@ -120,14 +146,14 @@ __device__ __forceinline__ void estimate(const Capsule &cp, int a, int k, int &i
     // the caps: balls around A and B
     const float hA = wc * wc + wz * wz;
     if (hA <= R2) {
-        const float s = sqrtf(R2 - hA);
+        const float s = __fsqrt_rz(R2 - hA);
         lo = fminf(lo, -s);
         hi = fmaxf(hi, s);
     }
     const float bc = wc - cp.df[1], bz = wz - cp.df[2];
     const float hB = bc * bc + bz * bz;
     if (hB <= R2) {
-        const float s = sqrtf(R2 - hB);
+        const float s = __fsqrt_rz(R2 - hB);
         lo = fminf(lo, cp.df[0] - s);
         hi = fmaxf(hi, cp.df[0] + s);
     }
@@ -135,24 +161,25 @@ __device__ __forceinline__ void estimate(const Capsule &cp, int a, int k, int &i
     float smin = 0.0f;
     if (cp.L2f > 0.0f) {
         const float g = wc * cp.df[1] + wz * cp.df[2];
-        const float a2 = 1.0f - cp.df[0] * cp.df[0] / cp.L2f;
-        const float b = -cp.df[0] * g / cp.L2f;
-        const float c0 = hA - g * g / cp.L2f;
+        const float a2 = 1.0f - cp.df[0] * cp.df[0] * cp.inv_L2;
+        const float b = -cp.df[0] * g * cp.inv_L2;
+        const float c0 = hA - g * g * cp.inv_L2;
         // the parameter along the segment stays in [0, 1]
         float tlo = -INFINITY, thi = INFINITY;
         if (cp.df[0] != 0.0f) {
-            const float t0 = -g / cp.df[0], t1 = (cp.L2f - g) / cp.df[0];
+            const float t0 = -g * cp.inv_d0, t1 = (cp.L2f - g) * cp.inv_d0;
             tlo = fminf(t0, t1);
             thi = fmaxf(t0, t1);
         } else if (g < 0.0f || g > cp.L2f) {
             tlo = INFINITY;  // the row never faces the segment's interior
         }
         if (a2 > 1e-6f) {
-            smin = -b / a2;
+            const float ia = __frcp_rz(a2);
+            smin = -b * ia;
             const float disc = b * b - a2 * (c0 - R2);
             if (disc >= 0.0f) {
-                const float q = sqrtf(disc);
-                const float s1 = fmaxf((-b - q) / a2, tlo), s2 = fminf((-b + q) / a2, thi);
+                const float q = __fsqrt_rz(disc);
+                const float s1 = fmaxf((-b - q) * ia, tlo), s2 = fminf((-b + q) * ia, thi);
                 if (s1 <= s2) {
                     lo = fminf(lo, s1);
                     hi = fmaxf(hi, s2);
@@ -169,7 +196,7 @@ __device__ __forceinline__ void estimate(const Capsule &cp, int a, int k, int &i
     }
     // index of a major coordinate x: x = (2 i + 1 - n) s / 2
     const float off = 0.5f * static_cast<float>(cp.n[0] - 1);
-    const float inv = 1.0f / cp.sf[0];
+    const float inv = cp.inv_s0;
     const float flo = (lo + cp.Af[0]) * inv + off, fhi = (hi + cp.Af[0]) * inv + off;
     const float fm = (smin + cp.Af[0]) * inv + off;
     const float top = static_cast<float>(cp.n[0] - 1);
@@ -182,20 +209,38 @@ __device__ __forceinline__ void estimate(const Capsule &cp, int a, int k, int &i
     imin = static_cast<int>(rintf(fminf(fmaxf(fm, 0.0f), top)));
 }
 
-// The exact interval [lo, hi] of the row (false when empty).
+// The exact interval [lo, hi] of voxels of a row whose line meets the
+// capsule (false when no voxel centre of the row lies inside: the row's
+// chord can fall between two centres).
 __device__ __forceinline__ bool row_interval(const Capsule &cp, int a, int k, int &lo, int &hi)
 {
     const int n = cp.n[0];
+    const Row r = row_of(cp, a, k);
     int elo, ehi, emin;
     estimate(cp, a, k, elo, ehi, emin);
-    const Row r = row_of(cp, a, k);
     elo = max(0, min(elo, n - 1));
     ehi = max(0, min(ehi, n - 1));
     int m = -1;
     if (elo <= ehi) {
-        const int mid = (elo + ehi) >> 1;
-        if (in_at(cp, r, mid)) m = mid;
-        else emin = mid;
+        // the usual case: both estimated ends inside, their outer
+        // neighbours outside (convexity: exactly [elo, ehi]); otherwise
+        // settle the ends below from an inside point
+        const bool in_lo = in_at(cp, r, elo);
+        const bool in_hi = in_lo && (ehi == elo || in_at(cp, r, ehi));
+        if (in_hi) {
+            if ((elo == 0 || !in_at(cp, r, elo - 1)) && (ehi + 1 >= n || !in_at(cp, r, ehi + 1))) {
+                lo = elo;
+                hi = ehi;
+                return true;
+            }
+            m = elo;
+        } else if (in_lo) {
+            m = elo;
+        } else {
+            const int mid = (elo + ehi) >> 1;
+            if (in_at(cp, r, mid)) m = mid;
+            else emin = mid;
+        }
     }
     if (m < 0) {
         // exact descent to F's minimum along the row (F is convex in i)
@@ -216,7 +261,7 @@ __device__ __forceinline__ bool row_interval(const Capsule &cp, int a, int k, in
                 f = g;
             }
         }
-        if (f > cp.T) return false;
+        if (f > cp.T) return false;  // no voxel centre of the row is inside
         m = i;
         elo = ehi = i;
     }
@@ -242,7 +287,7 @@ struct EuCounts {
     unsigned n_in = 0, n_miss = 0, n_hit = 0, n_none = 0, n_reject = 0;
 };
 
-__global__ void __launch_bounds__(kEuThreads) euclid_kernel(Inputs in, int64_t n, GeomQ g,
+__global__ void __launch_bounds__(kEuThreads, 3) euclid_kernel(Inputs in, int64_t n, GeomQ g,
                                                             Cordic cd, float tau_l, float tau_h,
                                                             int use_miss, int use_hit,
                                                             long long R2, float d0, ThickDiff td,
@@ -250,6 +295,9 @@ __global__ void __launch_bounds__(kEuThreads) euclid_kernel(Inputs in, int64_t n
                                                             unsigned long long *next)
 {
     const unsigned lane = threadIdx.x & 31u;
+    // per warp: a queue of rows to process (at most 31 left + 32 new)
+    __shared__ int s_queue[kEuThreads / 32][64];
+    int *const queue = s_queue[threadIdx.x >> 5];
     EuCounts nc;
     unsigned long long vox[2] = {0, 0}, rows = 0;
     bool tc_valid = false;
@@ -297,28 +345,43 @@ __global__ void __launch_bounds__(kEuThreads) euclid_kernel(Inputs in, int64_t n
                 A[q] = 2 * W[q];
                 B[q] = 2 * W[q + 3];
             }
-            // the major in-plane axis (rows run along it)
-            const int mj = llabs(B[1] - A[1]) > llabs(B[0] - A[0]) ? 1 : 0;
-            const int perm[3] = {mj, 1 - mj, 2};
+            // the major in-plane axis (rows run along it): frame axes 0, 1, 2
+            // are (x, y, z) or (y, x, z), chosen with selects (a runtime
+            // array index would put the arrays in local memory)
+            const bool mj = llabs(B[1] - A[1]) > llabs(B[0] - A[0]);
             Capsule cp;
+            cp.A[0] = mj ? A[1] : A[0];
+            cp.A[1] = mj ? A[0] : A[1];
+            cp.A[2] = A[2];
+            cp.B[0] = mj ? B[1] : B[0];
+            cp.B[1] = mj ? B[0] : B[1];
+            cp.B[2] = B[2];
+            cp.n[0] = mj ? ng[1] : ng[0];
+            cp.n[1] = mj ? ng[0] : ng[1];
+            cp.n[2] = ng[2];
+            cp.s2[0] = mj ? s2g[1] : s2g[0];
+            cp.s2[1] = mj ? s2g[0] : s2g[1];
+            cp.s2[2] = s2g[2];
+#pragma unroll
             for (int q = 0; q < 3; ++q) {
-                const int ax = perm[q];
-                cp.A[q] = A[ax];
-                cp.B[q] = B[ax];
-                cp.u[q] = B[ax] - A[ax];
-                cp.n[q] = ng[ax];
-                cp.s2[q] = s2g[ax];
-                cp.sf[q] = static_cast<float>(s2g[ax]) * (1.0f / 65536.0f);
-                cp.Af[q] = static_cast<float>(A[ax]) * (1.0f / 131072.0f);
+                cp.u[q] = cp.B[q] - cp.A[q];
+                cp.sf[q] = static_cast<float>(cp.s2[q]) * (1.0f / 65536.0f);
+                cp.Af[q] = static_cast<float>(cp.A[q]) * (1.0f / 131072.0f);
                 cp.df[q] = static_cast<float>(cp.u[q]) * (1.0f / 131072.0f);
             }
             cp.uu = static_cast<unsigned long long>(cp.u[0] * cp.u[0]) +
                     static_cast<unsigned long long>(cp.u[1] * cp.u[1]) +
                     static_cast<unsigned long long>(cp.u[2] * cp.u[2]);
-            const u128 RR = static_cast<u128>(static_cast<unsigned long long>(R2 * R2));
-            cp.T = cp.uu == 0 ? RR : RR * cp.uu;
+            cp.RR = static_cast<unsigned long long>(R2 * R2);
+            cp.T = cp.uu == 0 ? static_cast<u128>(cp.RR) : mul64(cp.RR, cp.uu);
+            cp.uu2 = static_cast<unsigned long long>(cp.u[1] * cp.u[1]) +
+                     static_cast<unsigned long long>(cp.u[2] * cp.u[2]);
+            cp.T2 = mul64(cp.RR, cp.uu2);
             cp.L2f = cp.df[0] * cp.df[0] + cp.df[1] * cp.df[1] + cp.df[2] * cp.df[2];
             cp.Rf = d0;
+            cp.inv_L2 = cp.L2f > 0.0f ? __frcp_rz(cp.L2f) : 0.0f;
+            cp.inv_d0 = cp.df[0] != 0.0f ? __frcp_rz(cp.df[0]) : 0.0f;
+            cp.inv_s0 = __frcp_rz(cp.sf[0]);
             // index box of the capsule on axes 1 and 2: centres within
             // [min(A, B) - R, max(A, B) + R], widened by one
             int blo[3], bhi[3];
@@ -334,17 +397,48 @@ __global__ void __launch_bounds__(kEuThreads) euclid_kernel(Inputs in, int64_t n
             const int na = bhi[1] - blo[1] + 1;
             const int nrows = na * (bhi[2] - blo[2] + 1);
             int32_t *diff = mj ? td.dy[cls] : td.dx[cls];
-            for (int rw = static_cast<int>(lane); rw < nrows; rw += 32) {
-                const int a = blo[1] + rw % na, k = blo[2] + rw / na;
-                int lo, hi;
-                if (!row_interval(cp, a, k, lo, hi)) continue;
-                // x-major rows: (nx + 1) entries per (y, z); y-major: (ny + 1) per (x, z)
-                int32_t *row = diff + (static_cast<int64_t>(a) + static_cast<int64_t>(cp.n[1]) * k) *
-                                          (cp.n[0] + 1);
-                atomicAdd(row + lo, 1);
-                atomicAdd(row + hi + 1, -1);
-                vox[cls] += static_cast<unsigned>(hi - lo + 1);
-                rows += 1;
+            // the rows of the box that meet the capsule (cheap exact test)
+            // queue up in shared memory; whenever 32 are queued all lanes take
+            // one each, so the costly interval search runs with full warps
+            int qn = 0;
+            for (int base = 0; base < nrows; base += 32) {
+                const int rw = base + static_cast<int>(lane);
+                bool meets = false;
+                int a = 0, k = 0;
+                if (rw < nrows) {
+                    a = blo[1] + rw % na;
+                    k = blo[2] + rw / na;
+                    meets = row_meets(cp, row_of(cp, a, k));
+                }
+                const unsigned bal = __ballot_sync(0xffffffffu, meets);
+                if (meets) queue[qn + __popc(bal & ((1u << lane) - 1u))] = a | (k << 16);
+                qn += __popc(bal);
+                const bool last = base + 32 >= nrows;
+                while (qn >= 32 || (last && qn > 0)) {
+                    __syncwarp();
+                    int lo, hi;
+                    if (static_cast<int>(lane) < qn &&
+                        row_interval(cp, queue[lane] & 0xffff, queue[lane] >> 16, lo, hi)) {
+                        const int ra = queue[lane] & 0xffff, rk = queue[lane] >> 16;
+                        // x-major rows: (nx + 1) entries per (y, z); y-major:
+                        // (ny + 1) per (x, z)
+                        int32_t *row = diff + (static_cast<int64_t>(ra) +
+                                               static_cast<int64_t>(cp.n[1]) * rk) *
+                                                  (cp.n[0] + 1);
+                        atomicAdd(row + lo, 1);
+                        atomicAdd(row + hi + 1, -1);
+                        vox[cls] += static_cast<unsigned>(hi - lo + 1);
+                        rows += 1;
+                    }
+                    __syncwarp();
+                    // keep what did not fit (fewer than 32 entries)
+                    const int rest = qn > 32 ? qn - 32 : 0;
+                    const int moved = static_cast<int>(lane) < rest ? queue[32 + lane] : 0;
+                    __syncwarp();
+                    if (static_cast<int>(lane) < rest) queue[lane] = moved;
+                    __syncwarp();
+                    qn = rest;
+                }
             }
         }
     }
