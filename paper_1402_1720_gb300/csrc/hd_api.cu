@@ -128,7 +128,9 @@ struct hd_scan {
     hd::ScanDesc *desc_dev = nullptr;  // this scan's traversal descriptor
     hd::ScanDesc desc_host{};
     bool desc_dirty = true;
-    uint32_t *tile_count = nullptr;   // 2 * ntiles
+    // 2 * ntiles tile totals, then the ingest blocks' pair counts per tile
+    // (tile_count_words)
+    uint32_t *tile_count = nullptr;
     uint32_t *tile_cursor = nullptr;  // 2 * ntiles
     int64_t *rows_scratch = nullptr;  // tile sums of the system-row offset scan
     int64_t rows_scratch_cap = 0;
@@ -251,7 +253,8 @@ hd_status ensure_records(hd_scan *s, int64_t n, cudaStream_t st)
     s->pair_buf = nullptr;
     s->jobs = nullptr;
     s->rec_cap = 0;
-    bool ok = cudaMalloc(&s->rec_buf, sizeof(int32_t) * 7 * static_cast<size_t>(n)) == cudaSuccess;
+    bool ok = cudaMalloc(&s->rec_buf, sizeof(int32_t) * 7 *
+                                          static_cast<size_t>(hd::records_stride(n))) == cudaSuccess;
     if (ok && s->tp.ntiles > 0) {
         const int64_t pair_cap = pairs_per_record(s->tp) * n;
         const int64_t min_job = s->tp.job_size < hd::kMinJob ? s->tp.job_size : hd::kMinJob;
@@ -314,13 +317,26 @@ bool all_mapped_host(const float *const src[6], int device)
     return true;
 }
 
+// The records of a chunk of n histories: seven arrays of n slots, each
+// starting on a 16-byte boundary.
 hd::Records records_of(const hd_scan *s, int64_t n)
 {
     hd::Records r;
-    for (int a = 0; a < 6; ++a) r.g[a] = s->rec_buf + static_cast<size_t>(a) * n;
-    r.status = s->rec_buf + static_cast<size_t>(6) * n;
+    const size_t stride = static_cast<size_t>(hd::records_stride(n));
+    for (int a = 0; a < 6; ++a) r.g[a] = s->rec_buf + a * stride;
+    r.status = s->rec_buf + 6 * stride;
     r.cap = n;
     return r;
+}
+
+// Words of tile_count: the 2 * ntiles totals, then a column of pair counts
+// per tile and class for the most ingest blocks a chunk can use.
+size_t tile_count_words(const hd_scan *s)
+{
+    const size_t cols = 2 * static_cast<size_t>(s->tp.ntiles);
+    const size_t blocks = static_cast<size_t>(s->sm_count > 0 ? s->sm_count : 1) *
+                          static_cast<size_t>(hd::kIngestBlocksPerSm);
+    return cols * (1 + blocks);
 }
 
 hd::Pairs pairs_of(const hd_scan *s)
@@ -372,6 +388,7 @@ void make_tile_plan(hd_scan *s)
     tp.ntiles = tp.ntx * tp.nty * tp.ntz;
     if (tp.ntiles > hd::kMaxTiles) tp.ntiles = 0;
     tp.max_tiles = 8;
+    tp.pairs_per_record = static_cast<int>(pairs_per_record(tp));
     tp.job_size = s->tuning.job_size;  // <= 32767: int16 differences in the tiled traversal
     tp.refill = s->tuning.refill;
     tp.threads = s->tuning.threads;
@@ -420,20 +437,18 @@ hd_status stage_prepare(hd_scan *s, const hd::Inputs &in, int64_t n, cudaStream_
     const hd::Records rec = records_of(s, n);
     hd::TilePlan tp = s->tp;
     if (s->trace_grid <= 0) tp.ntiles = 0;
-    HD_CUDA(cudaMemsetAsync(&s->ctrl->rec_miss, 0,
-                            sizeof(hd::Ctrl) - offsetof(hd::Ctrl, rec_miss), st));
-    if (tp.ntiles > 0)
-        HD_CUDA(cudaMemsetAsync(s->tile_count, 0, sizeof(uint32_t) * 2 * tp.ntiles, st));
+    HD_CUDA(cudaMemsetAsync(&s->ctrl->njobs, 0, sizeof(hd::Ctrl) - offsetof(hd::Ctrl, njobs), st));
+    uint32_t *block_count = s->tile_count + 2 * static_cast<size_t>(s->tp.ntiles);
     HD_CUDA(hd::launch_ingest(in, n, s->gq, s->cordic, s->params.wepl_miss_lt,
                               s->params.wepl_hit_gt, use_miss, use_hit, tp, rec, s->ctrl,
-                              s->tile_count, s->sm_count, st));
+                              tp.ntiles > 0 ? block_count : nullptr, s->sm_count, st));
     s->launches += 1;
     if (tp.ntiles > 0) {
-        HD_CUDA(hd::launch_plan(tp, s->tile_count, s->tile_cursor, s->jobs, s->ctrl, s->sm_count,
-                                st));
-        HD_CUDA(hd::launch_scatter(tp, rec, s->ctrl, s->tile_cursor, pairs_of(s), n, s->sm_count,
-                                   st));
-        s->launches += 2;
+        HD_CUDA(hd::launch_plan(tp, n, block_count, s->tile_count, s->tile_cursor, s->jobs, s->ctrl,
+                                s->sm_count, st));
+        HD_CUDA(hd::launch_scatter(tp, rec, n, s->ctrl, s->tile_cursor, block_count, pairs_of(s),
+                                   s->sm_count, st));
+        s->launches += 3;
     }
     return HD_OK;
 }
@@ -628,7 +643,7 @@ hd_status hd_scan_create(const hd_geometry *geom, const hd_params *params, hd_sc
     alloc(reinterpret_cast<void **>(&s->bits_out), sizeof(uint32_t) * s->words);
     make_tile_plan(s);
     if (s->tp.ntiles > 0) {
-        alloc(reinterpret_cast<void **>(&s->tile_count), sizeof(uint32_t) * 2 * s->tp.ntiles);
+        alloc(reinterpret_cast<void **>(&s->tile_count), sizeof(uint32_t) * tile_count_words(s));
         alloc(reinterpret_cast<void **>(&s->tile_cursor), sizeof(uint32_t) * 2 * s->tp.ntiles);
         const int per_sm = hd::trace_tiles_occupancy(s->tp.tile_words, s->tp.threads);
         s->trace_grid = per_sm > 0 ? per_sm * s->sm_count : 0;
@@ -1055,7 +1070,7 @@ hd_status hd_scan_set_tuning(hd_scan *scan, const hd_tuning *t)
     make_tile_plan(scan);
     scan->trace_grid = 0;
     if (scan->tp.ntiles > 0) {
-        if (cudaMalloc(&scan->tile_count, sizeof(uint32_t) * 2 * scan->tp.ntiles) != cudaSuccess ||
+        if (cudaMalloc(&scan->tile_count, sizeof(uint32_t) * tile_count_words(scan)) != cudaSuccess ||
             cudaMalloc(&scan->tile_cursor, sizeof(uint32_t) * 2 * scan->tp.ntiles) != cudaSuccess) {
             cudaGetLastError();
             return HD_ERR_NOMEM;

@@ -314,14 +314,17 @@ HD_HD int tile_range(const TilePlan &tp, const int32_t r[6], int lo[3], int hi[3
     return tile_range_z(tp, r, zlo, zhi, lo, hi);
 }
 
-// A record's status word: bits 0-7 the path (1 tiled, 2 global), bits 8-19
-// and 20-31 its first and last slice (grid_z_range, computed once).
-HD_HD int32_t record_status(int path, int zlo, int zhi)
+// A record's status word: bits 0-1 the path (0 no record, 1 tiled, 2
+// global), bit 2 the class (0 missed, 1 hit), bits 8-19 and 20-31 its first
+// and last slice (grid_z_range, computed once).
+HD_HD int32_t record_status(int path, int cls, int zlo, int zhi)
 {
-    return static_cast<int32_t>(static_cast<uint32_t>(path) | (static_cast<uint32_t>(zlo) << 8) |
+    return static_cast<int32_t>(static_cast<uint32_t>(path) | (static_cast<uint32_t>(cls) << 2) |
+                                (static_cast<uint32_t>(zlo) << 8) |
                                 (static_cast<uint32_t>(zhi) << 20));
 }
-HD_HD int status_path(int32_t s) { return s & 0xff; }
+HD_HD int status_path(int32_t s) { return s & 3; }
+HD_HD int status_cls(int32_t s) { return (s >> 2) & 1; }
 HD_HD int status_zlo(int32_t s) { return (static_cast<uint32_t>(s) >> 8) & 0xfff; }
 HD_HD int status_zhi(int32_t s) { return static_cast<uint32_t>(s) >> 20; }
 

@@ -30,16 +30,13 @@ struct GeomQ {
     unsigned long long mx, my, mz;  // floor(2^64 / (2 s)): division by multiply-high
 };
 
-// Device-side counters of one scan.  The block from rec_miss to job_next is
+// Device-side counters of one scan.  The block from njobs to the end is
 // cleared before every chunk of histories.
 struct Ctrl {
     unsigned long long n_in, n_miss, n_hit, n_none, n_reject;
     unsigned long long steps_miss, steps_hit;
     unsigned long long pairs_general;  // pairs sent to the fallback list (cumulative)
     unsigned long long runs;           // runs walked by the tiled pass (cumulative)
-    unsigned int rec_miss;    // records appended from the front of the list
-    unsigned int rec_hit;     // records appended from the back of the list
-    unsigned int pairs_used;  // (record, tile) pairs admitted to the tiled path
     int njobs;                // jobs of the tiled traversal
     int job_next;             // next job to hand out
     unsigned int n_fallback;  // records traversed by the global-memory path
@@ -47,14 +44,43 @@ struct Ctrl {
     unsigned int fb_next;          // next fallback entry to hand out
 };
 
-// Compacted traversal records: grid Q16 entry and exit points, int32 each
-// (|G| < 2^30), and a status (1 tiled, 2 global path).  Missed histories
-// fill [0, rec_miss), hit ones [cap - rec_hit, cap).  Structure of arrays.
+// Traversal records of one chunk, one slot per history (slot = the
+// history's index in the chunk): grid Q16 entry and exit points, int32 each
+// (|G| < 2^30), and a status word (record_status in hd_geom.cuh: path 0 for
+// a history without a record, 1 tiled, 2 global; its class; its slices).
+// Structure of arrays; each array starts on a 16-byte boundary when the
+// chunk's slot count is padded to a multiple of four (records_stride).
 struct Records {
     int32_t *g[6];  // x0, y0, z0, x1, y1, z1
     int32_t *status;
-    int64_t cap;
+    int64_t cap;    // slots (the chunk's histories)
 };
+
+inline int64_t records_stride(int64_t n) { return (n + 3) & ~int64_t(3); }
+
+// How a chunk of n histories is split among the ingest blocks; the scatter
+// uses the same split, so that each of its blocks finds the pairs of the
+// records one ingest block wrote.  Block b takes histories
+// [b per_block, min((b + 1) per_block, n)); per_block is a multiple of 4.
+constexpr int kIngestThreads = 256;
+constexpr int kIngestBlocksPerSm = 8;
+struct ChunkSplit {
+    int blocks;
+    int64_t per_block;
+};
+inline ChunkSplit chunk_split(int64_t n, int sm_count)
+{
+    const int64_t units = (n + 3) / 4;  // groups of four histories
+    int64_t blocks = (units + kIngestThreads - 1) / kIngestThreads;
+    const int64_t cap = static_cast<int64_t>(sm_count > 0 ? sm_count : 1) * kIngestBlocksPerSm;
+    if (blocks > cap) blocks = cap;
+    if (blocks < 1) blocks = 1;
+    ChunkSplit c;
+    c.per_block = 4 * ((units + blocks - 1) / blocks);
+    c.blocks = static_cast<int>((n + c.per_block - 1) / c.per_block);
+    if (c.blocks < 1) c.blocks = 1;
+    return c;
+}
 
 // Tiling of the grid into boxes whose counters fit in shared memory.
 struct TilePlan {
@@ -63,6 +89,7 @@ struct TilePlan {
     int ntx, nty, ntz;  // tiles per axis
     int ntiles;         // tiles per class (0: tiled path off)
     int max_tiles;      // records touching more tiles take the global path
+    int pairs_per_record;  // pair budget per history (pair_cap = this * slots)
     int job_size;       // pairs per job
     long long pair_cap;
     int tile_words;     // 32-bit words of shared memory per block
@@ -108,17 +135,31 @@ struct Inputs {
 };
 
 // ---- launchers (stream-ordered; return the launch's cudaError_t) ----
+
+// Classification, records and pair counts of a chunk.  block_count (null
+// when tp.ntiles is 0) receives, per tile-class column c (2 tp.ntiles of
+// them) and ingest block b, the pairs of that block's records in that tile
+// at [c * blocks + b]; each block keeps to a pair budget of
+// tp.pairs_per_record per history, and its records beyond it take the
+// global path.
 cudaError_t launch_ingest(const Inputs &in, int64_t n, const GeomQ &g, const Cordic &cordic,
                           float tau_l, float tau_h, int use_miss, int use_hit, const TilePlan &tp,
-                          const Records &rec, Ctrl *ctrl, uint32_t *tile_count, int sm_count,
+                          const Records &rec, Ctrl *ctrl, uint32_t *block_count, int sm_count,
                           cudaStream_t s);
 
-cudaError_t launch_plan(const TilePlan &tp, const uint32_t *tile_count, uint32_t *tile_cursor,
-                        TileJob *jobs, Ctrl *ctrl, int sm_count, cudaStream_t s);
+// Per column: the exclusive prefix over blocks of block_count (in place) and
+// the column total into tile_count; then the plan (tile offsets into
+// tile_cursor, the job table).
+cudaError_t launch_plan(const TilePlan &tp, int64_t n, uint32_t *block_count,
+                        uint32_t *tile_count, uint32_t *tile_cursor, TileJob *jobs, Ctrl *ctrl,
+                        int sm_count, cudaStream_t s);
 
-cudaError_t launch_scatter(const TilePlan &tp, const Records &rec, Ctrl *ctrl,
-                           uint32_t *tile_cursor, const Pairs &pairs, int64_t n, int sm_count,
-                           cudaStream_t s);
+// Counting sort of the (record, tile) pairs by tile, with the walk set-up of
+// each pair; block b of the chunk split writes the pairs of its records from
+// tile_cursor[c] + block_count[c * blocks + b] on.
+cudaError_t launch_scatter(const TilePlan &tp, const Records &rec, int64_t n, Ctrl *ctrl,
+                           const uint32_t *tile_cursor, const uint32_t *block_count,
+                           const Pairs &pairs, int sm_count, cudaStream_t s);
 
 // Persistent traversal over the jobs of nscans scans (descs on the device),
 // handed out through *job_counter (zero before the launch).  smem_words is
@@ -126,8 +167,8 @@ cudaError_t launch_scatter(const TilePlan &tp, const Records &rec, Ctrl *ctrl,
 cudaError_t launch_trace_tiles(const ScanDesc *descs, int nscans, int *job_counter,
                                int smem_words, int threads, int grid, cudaStream_t s);
 
-// Global-memory traversal of the records whose status is 2 (or of every
-// record when all_records is set).
+// Global-memory traversal of the records whose path is 2 (or of every
+// record when all_records is set); upper is the chunk's slot count.
 cudaError_t launch_trace_global(const Records &rec, Ctrl *ctrl, int64_t upper, const GeomQ &g,
                                 uint32_t *N, uint32_t *M, int all_records,
                                 int sm_count, cudaStream_t s);

@@ -21,8 +21,9 @@
 
 namespace {
 
-// Histories per call; the records take 7 int32 each.
+// Histories per call (a multiple of 4); the records take 7 int32 each.
 constexpr int64_t kNoAllocMaxHistories = int64_t(1) << 18;
+static_assert(kNoAllocMaxHistories % 4 == 0, "record arrays are padded to four slots");
 constexpr size_t kNoAllocCtrlBytes = 256;
 constexpr size_t kNoAllocBytes =
     kNoAllocCtrlBytes + sizeof(int32_t) * 7 * static_cast<size_t>(kNoAllocMaxHistories);
@@ -131,9 +132,10 @@ extern "C" hd_status hd_accumulate_noalloc(const hd_geometry *geom, const hd_par
     auto *bytes = static_cast<unsigned char *>(base);
     hd::Ctrl *ctrl = reinterpret_cast<hd::Ctrl *>(bytes);
     int32_t *rec_base = reinterpret_cast<int32_t *>(bytes + kNoAllocCtrlBytes);
-    hd::Records rec;
-    for (int a = 0; a < 6; ++a) rec.g[a] = rec_base + static_cast<size_t>(a) * n;
-    rec.status = rec_base + static_cast<size_t>(6) * n;
+    hd::Records rec;  // seven arrays of n slots, each on a 16-byte boundary
+    const size_t stride = static_cast<size_t>(hd::records_stride(n));
+    for (int a = 0; a < 6; ++a) rec.g[a] = rec_base + a * stride;
+    rec.status = rec_base + 6 * stride;
     rec.cap = n;
 
     cudaStream_t s = static_cast<cudaStream_t>(stream);

@@ -211,22 +211,19 @@ __global__ void __launch_bounds__(kThickThreads) thick_records_kernel(Records re
                                                                       GeomQ g, int k,
                                                                       ThickDiff td)
 {
-    const unsigned nm = ctrl->rec_miss, nh = ctrl->rec_hit;
-    const int64_t total = static_cast<int64_t>(nm) + nh;
     const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
     ThickRing rg;
     unsigned vox[2] = {0, 0};
-    for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < total;
+    for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < rec.cap;
          i += stride) {
-        const bool miss = i < nm;
-        const int64_t slot = miss ? i : rec.cap - 1 - (i - nm);
-        if (status_path(rec.status[slot]) != 2) continue;
-        const int32_t gi[3] = {rec.g[0][slot], rec.g[1][slot], rec.g[2][slot]};
-        const int32_t go[3] = {rec.g[3][slot], rec.g[4][slot], rec.g[5][slot]};
+        const int32_t stw = rec.status[i];
+        if (status_path(stw) != 2) continue;
+        const int32_t gi[3] = {rec.g[0][i], rec.g[1][i], rec.g[2][i]};
+        const int32_t go[3] = {rec.g[3][i], rec.g[4][i], rec.g[5][i]};
         RunWalk wk;
         if (!run_begin(wk, gi, go, g.nx, g.ny, g.nz)) continue;
         const bool ymaj = (wk.flags >> 5) & 1;
-        const int cls = miss ? 0 : 1;
+        const int cls = status_cls(stw);
         thick_walk_all(wk, ymaj ? g.nx : g.ny, ymaj ? g.ny : g.nx, 0, k, (wk.flags & 2) ? 1 : -1,
                        ymaj ? td.dy[cls] : td.dx[cls], rg, vox[cls]);
     }

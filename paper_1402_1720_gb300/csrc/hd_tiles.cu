@@ -3,9 +3,12 @@
 // walked with the exact traversal clipped to the tile, and each block adds
 // its private tile into N or M once per job.
 //
-// Pipeline per chunk of histories (after ingest has counted pairs per tile):
-//   plan     exclusive scan of the tile counts -> cursors and a job table
-//   scatter  counting sort of the pairs by tile (block-level reservation)
+// Pipeline per chunk of histories (after ingest has counted, per ingest
+// block, its pairs in each tile):
+//   bases    per tile, exclusive scan over the blocks -> each block's offset
+//   plan     exclusive scan of the tile totals -> tile offsets, job table
+//   scatter  counting sort of the pairs by tile: block b of the ingest split
+//            writes its pairs from its offsets, with each pair's walk set-up
 //   trace    persistent blocks take jobs; warps refill idle lanes from the
 //            job's pair range, so lanes do not wait for the longest path
 #include <cooperative_groups.h>
@@ -19,7 +22,6 @@ namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kScatterThreads = 256;
-constexpr int kScatterPerThread = 8;  // most records a scatter thread takes
 constexpr int kRunsPerStep = 8;       // runs a traversal lane walks between refill checks
 
 __device__ __forceinline__ unsigned warp_incl_scan_u(unsigned v)
@@ -54,6 +56,26 @@ __device__ __forceinline__ unsigned block_excl_scan(unsigned v, unsigned *s_warp
     return r;
 }
 
+
+// One warp per tile-class column: the exclusive prefix over the ingest
+// blocks of their pair counts (in place) and the column's total.
+__global__ void __launch_bounds__(256) bases_kernel(int ncols, int nblocks, uint32_t *counts,
+                                                    uint32_t *totals)
+{
+    const int c = static_cast<int>(blockIdx.x) * 8 + static_cast<int>(threadIdx.x >> 5);
+    const int lane = static_cast<int>(threadIdx.x & 31u);
+    if (c >= ncols) return;  // the whole warp
+    uint32_t *col = counts + static_cast<size_t>(c) * nblocks;
+    unsigned run = 0;
+    for (int b0 = 0; b0 < nblocks; b0 += 32) {
+        const int b = b0 + lane;
+        const unsigned v = b < nblocks ? col[b] : 0u;
+        const unsigned incl = warp_incl_scan_u(v);
+        if (b < nblocks) col[b] = run + incl - v;
+        run += __shfl_sync(kFull, incl, 31);
+    }
+    if (lane == 0) totals[c] = run;
+}
 
 // One block: tile offsets (exclusive scan of the counts), cursors for the
 // scatter, and the job table (chunks of one tile's pairs).  The job size
@@ -129,75 +151,42 @@ __device__ __noinline__ bool general_setup(const int32_t gi[3], const int32_t go
     return fallback;
 }
 
-// Counting sort of (record, tile) pairs by tile.  Each block takes a range
-// of record slots, histograms its pairs, reserves one range per tile with a
-// single global atomic, then writes its pairs.
-__global__ void __launch_bounds__(kScatterThreads, 4) scatter_kernel(TilePlan tp, Records rec,
-                                                                  Ctrl *ctrl,
-                                                                  uint32_t *tile_cursor,
-                                                                  Pairs pairs, int per_thread)
+// Counting sort of (record, tile) pairs by tile.  Block b takes the slots
+// of ingest block b and writes its pairs of tile c from
+// tile_start[c] + block_base[c * blocks + b] on (a shared-memory cursor per
+// tile orders them within the block).
+__global__ void __launch_bounds__(kScatterThreads, 4) scatter_kernel(
+    TilePlan tp, Records rec, int64_t per_block, const uint32_t *tile_start,
+    const uint32_t *block_base, Ctrl *ctrl, Pairs pairs)
 {
     extern __shared__ uint32_t s_mem[];
     const int nt = 2 * tp.ntiles;
-    uint32_t *s_hist = s_mem;
-    uint32_t *s_base = s_mem + nt;
-    for (int t = threadIdx.x; t < nt; t += blockDim.x) s_hist[t] = 0;
-    __syncthreads();
-    const unsigned nm = ctrl->rec_miss, nh = ctrl->rec_hit;
-    const int64_t slot0 = static_cast<int64_t>(blockIdx.x) * kScatterThreads * per_thread;
-    // a tiled record of either class, and its status word
-    auto valid = [&](int64_t slot, int &cls, int32_t &stw) -> bool {
-        if (slot < nm) { cls = 0; }
-        else if (slot >= rec.cap - nh) { cls = 1; }
-        else return false;
-        stw = rec.status[slot];
-        return status_path(stw) == 1;
-    };
-    for (int k = 0; k < per_thread; ++k) {
-        const int64_t slot = slot0 + k * kScatterThreads + threadIdx.x;
-        int cls;
-        int32_t stw;
-        if (slot >= rec.cap || !valid(slot, cls, stw)) continue;
-        int lo[3], hi[3];
-        if (tp.ntx == 1 && tp.nty == 1) {
-            // whole-plane tiles: the slices in the status word are all it takes
-            lo[0] = hi[0] = lo[1] = hi[1] = 0;
-            lo[2] = tp.mtz ? static_cast<int>(umulhi32(static_cast<unsigned>(status_zlo(stw)), tp.mtz))
-                           : status_zlo(stw);
-            hi[2] = tp.mtz ? static_cast<int>(umulhi32(static_cast<unsigned>(status_zhi(stw)), tp.mtz))
-                           : status_zhi(stw);
-        } else {
-            int32_t r[6];
-#pragma unroll
-            for (int a = 0; a < 6; ++a) r[a] = rec.g[a][slot];
-            if (tile_range_z(tp, r, status_zlo(stw), status_zhi(stw), lo, hi) == 0) continue;
-        }
-        for (int z = lo[2]; z <= hi[2]; ++z)
-            for (int y = lo[1]; y <= hi[1]; ++y)
-                for (int x = lo[0]; x <= hi[0]; ++x)
-                    atomicAdd(&s_hist[cls * tp.ntiles + x + tp.ntx * (y + tp.nty * z)], 1u);
-    }
-    __syncthreads();
+    uint32_t *s_base = s_mem;       // this block's first position in each tile
+    uint32_t *s_next = s_mem + nt;  // pairs written per tile so far
     for (int t = threadIdx.x; t < nt; t += blockDim.x) {
-        const uint32_t c = s_hist[t];
-        s_base[t] = c ? atomicAdd(&tile_cursor[t], c) : 0u;
-        s_hist[t] = 0;
+        s_base[t] = tile_start[t] + block_base[static_cast<size_t>(t) * gridDim.x + blockIdx.x];
+        s_next[t] = 0;
     }
     __syncthreads();
+    const int64_t h0 = static_cast<int64_t>(blockIdx.x) * per_block;
+    const int64_t h1 = h0 + per_block < rec.cap ? h0 + per_block : rec.cap;
     // The warp's (record, tile) pairs are dealt out one per lane, so the
     // set-up below runs on all lanes whatever each record's tile count.
     const int lane = static_cast<int>(threadIdx.x & 31u);
-    for (int k = 0; k < per_thread; ++k) {
-        const int64_t slot = slot0 + k * kScatterThreads + threadIdx.x;
+    for (int64_t base = h0; base < h1; base += kScatterThreads) {
+        const int64_t slot = base + threadIdx.x;
         int cls = 0;
         int32_t r[6] = {0, 0, 0, 0, 0, 0};
         int lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
         int cnt = 0;
-        int32_t stw;
-        if (slot < rec.cap && valid(slot, cls, stw)) {
+        if (slot < h1) {
+            const int32_t stw = rec.status[slot];
+            if (status_path(stw) == 1) {
+                cls = status_cls(stw);
 #pragma unroll
-            for (int a = 0; a < 6; ++a) r[a] = rec.g[a][slot];
-            cnt = tile_range_z(tp, r, status_zlo(stw), status_zhi(stw), lo, hi);
+                for (int a = 0; a < 6; ++a) r[a] = rec.g[a][slot];
+                cnt = tile_range_z(tp, r, status_zlo(stw), status_zhi(stw), lo, hi);
+            }
         }
         const int incl = static_cast<int>(warp_incl_scan_u(static_cast<unsigned>(cnt)));
         const int total = __shfl_sync(kFull, incl, 31);
@@ -227,7 +216,7 @@ __global__ void __launch_bounds__(kScatterThreads, 4) scatter_kernel(TilePlan tp
                 z = lz + j / (oex * oey);
             }
             const int t = ocls * tp.ntiles + x + tp.ntx * (y + tp.nty * z);
-            const uint32_t pos = s_base[t] + atomicAdd(&s_hist[t], 1u);
+            const uint32_t pos = s_base[t] + atomicAdd(&s_next[t], 1u);
             // set up the walk of this record clipped to this tile
             const int x0 = x * tp.tx, y0 = y * tp.ty, z0 = z * tp.tz;
             const int dx = min(tp.tx, tp.nx - x0), dy = min(tp.ty, tp.ny - y0),
@@ -556,30 +545,28 @@ __global__ void __launch_bounds__(kThreads, 1) trace_tiles_kernel(
     walk_fallback_lists(descs, nscans);
 }
 
-cudaError_t launch_plan(const TilePlan &tp, const uint32_t *tile_count, uint32_t *tile_cursor,
-                        TileJob *jobs, Ctrl *ctrl, int sm_count, cudaStream_t s)
+cudaError_t launch_plan(const TilePlan &tp, int64_t n, uint32_t *block_count,
+                        uint32_t *tile_count, uint32_t *tile_cursor, TileJob *jobs, Ctrl *ctrl,
+                        int sm_count, cudaStream_t s)
 {
+    const int ncols = 2 * tp.ntiles;
+    const ChunkSplit sp = chunk_split(n, sm_count);
+    bases_kernel<<<static_cast<unsigned>((ncols + 7) / 8), 256, 0, s>>>(ncols, sp.blocks,
+                                                                        block_count, tile_count);
     plan_kernel<<<1, 1024, 0, s>>>(tp, tile_count, tile_cursor, jobs, ctrl,
                                    sm_count > 0 ? sm_count : 1);
     return cudaGetLastError();
 }
 
-cudaError_t launch_scatter(const TilePlan &tp, const Records &rec, Ctrl *ctrl,
-                           uint32_t *tile_cursor, const Pairs &pairs, int64_t n, int sm_count,
-                           cudaStream_t s)
+cudaError_t launch_scatter(const TilePlan &tp, const Records &rec, int64_t n, Ctrl *ctrl,
+                           const uint32_t *tile_cursor, const uint32_t *block_count,
+                           const Pairs &pairs, int sm_count, cudaStream_t s)
 {
     if (n <= 0) return cudaSuccess;
-    // records per thread: up to kScatterPerThread, fewer when that would
-    // leave SMs idle (eight blocks of 256 per SM fill it)
-    const int64_t fill = static_cast<int64_t>(sm_count > 0 ? sm_count : 1) * 8 * kScatterThreads;
-    int64_t per = (n + fill - 1) / fill;
-    if (per > kScatterPerThread) per = kScatterPerThread;
-    if (per < 1) per = 1;
-    const int64_t per_block = static_cast<int64_t>(kScatterThreads) * per;
-    const int64_t blocks = (n + per_block - 1) / per_block;
+    const ChunkSplit sp = chunk_split(n, sm_count);
     const size_t smem = sizeof(uint32_t) * 4 * static_cast<size_t>(tp.ntiles);
-    scatter_kernel<<<static_cast<unsigned>(blocks), kScatterThreads, smem, s>>>(
-        tp, rec, ctrl, tile_cursor, pairs, static_cast<int>(per));
+    scatter_kernel<<<static_cast<unsigned>(sp.blocks), kScatterThreads, smem, s>>>(
+        tp, rec, sp.per_block, tile_cursor, block_count, ctrl, pairs);
     return cudaGetLastError();
 }
 

@@ -100,87 +100,59 @@ __device__ __forceinline__ unsigned warp_incl_scan(unsigned v)
     return v;
 }
 
-// Per-block staging of the appends: each warp's pair demand and record
-// counts, and the block's bases (two sets, alternating by iteration, so that
-// a warp starting the next iteration never overwrites what a slower warp of
-// this one still reads).
-constexpr int kIngestWarps = 8;  // 256-thread blocks
-struct AppendStage {
-    unsigned pairs[2][kIngestWarps];
-    unsigned recs[2][kIngestWarps];  // missed + 65536 hit
-    unsigned base_pairs[2], base_miss[2], base_hit[2];
-};
-
-// Decide tiled / global path for up to 4 records per lane, count tiles in
-// the block histogram, and append the records.  The pair budget and the two
-// record counters are reserved once per block and iteration (all threads
-// call this together): same-address atomics on the three counters are what
-// limit a warp-per-reservation scheme.
-__device__ __forceinline__ void admit_and_append(const TilePlan &tp, const Records &rec,
-                                                 Ctrl *ctrl, uint32_t *s_hist, int cls[4],
-                                                 const int32_t r[4][6], AppendStage &st, int par)
+// Decide the path of up to 4 records per lane (tiled within the block's pair
+// budget, else global), count their tiles in the block histogram and write
+// them at their histories' slots (i0 .. i0 + 3, or i0 alone when kOne).
+// Budget reservations are per warp on a shared-memory counter, so the
+// block never waits at a barrier; once a reservation overruns the budget
+// the records it covers take the global path (exact either way).
+template <bool kOne>
+__device__ __forceinline__ void admit_and_write(const TilePlan &tp, const Records &rec,
+                                                uint32_t *s_hist, unsigned *s_demand,
+                                                unsigned budget, int64_t i0, int64_t i1,
+                                                const int cls[4], const int32_t r[4][6])
 {
-    const unsigned lane = threadIdx.x & 31u;
-    int tcount[4];
-    int zr[4];  // the record's slices, zlo + 4096 zhi (computed once here)
+    constexpr int kK = kOne ? 1 : 4;
+    int tcount[kK];
+    int zr[kK];  // the record's slices, zlo + 4096 zhi (computed once here)
+    int ok[kK];
     unsigned demand = 0;
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
+    for (int k = 0; k < kK; ++k) {
         tcount[k] = 0;
         zr[k] = 0;
+        ok[k] = 0;
         if (cls[k] == 0) continue;
         int lo[3], hi[3], zlo, zhi;
         const int c = grid_z_range(tp, r[k], zlo, zhi) ? tile_range_z(tp, r[k], zlo, zhi, lo, hi) : 0;
-        if (c == 0) {
-            cls[k] = 0;  // no voxel of the grid: nothing to traverse
-            continue;
-        }
+        if (c == 0) continue;  // no voxel of the grid: nothing to traverse
+        ok[k] = 1;
         zr[k] = zlo + 4096 * zhi;
         tcount[k] = (tp.ntiles > 0 && c <= tp.max_tiles) ? c : -1;
         if (tcount[k] > 0) demand += static_cast<unsigned>(c);
     }
-    // records this lane appends: missed + 65536 hit (a record kept here
-    // keeps its class whatever path it takes)
-    unsigned mine = 0;
-#pragma unroll
-    for (int k = 0; k < 4; ++k) mine += (cls[k] == 1) ? 1u : (cls[k] == 2 ? 65536u : 0u);
-    const unsigned warp = threadIdx.x >> 5;
+    const unsigned lane = threadIdx.x & 31u;
     const unsigned incl = warp_incl_scan(demand);
-    const unsigned inc2 = warp_incl_scan(mine);
-    if (lane == 31) {
-        st.pairs[par][warp] = incl;
-        st.recs[par][warp] = inc2;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        unsigned tp_ = 0, tr = 0;
-        for (int w = 0; w < kIngestWarps; ++w) {
-            tp_ += st.pairs[par][w];
-            tr += st.recs[par][w];
-        }
-        st.base_pairs[par] = tp_ ? atomicAdd(&ctrl->pairs_used, tp_) : 0u;
-        st.base_miss[par] = (tr & 0xffffu) ? atomicAdd(&ctrl->rec_miss, tr & 0xffffu) : 0u;
-        st.base_hit[par] = (tr >> 16) ? atomicAdd(&ctrl->rec_hit, tr >> 16) : 0u;
-    }
-    __syncthreads();
-    unsigned wp = 0, wr = 0;  // earlier warps' pairs and records
-    for (unsigned w = 0; w < warp; ++w) {
-        wp += st.pairs[par][w];
-        wr += st.recs[par][w];
-    }
-    const unsigned base = st.base_pairs[par] + wp;
-    unsigned long long end = static_cast<unsigned long long>(base) + (incl - demand);
-    int status[4];
+    const unsigned tot = __shfl_sync(0xffffffffu, incl, 31);
+    unsigned wbase = 0;
+    if (lane == 31 && tot) wbase = atomicAdd(s_demand, tot);
+    wbase = __shfl_sync(0xffffffffu, wbase, 31);
+    unsigned long long end = static_cast<unsigned long long>(wbase) + (incl - demand);
+    int32_t st[kK];
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        status[k] = 2;
+    for (int k = 0; k < kK; ++k) {
+        st[k] = 0;
+        if (!ok[k]) continue;
+        int path = 2;
         if (tcount[k] > 0) {
             end += static_cast<unsigned>(tcount[k]);
-            if (end <= static_cast<unsigned long long>(tp.pair_cap)) status[k] = 1;
+            if (end <= budget) path = 1;
         }
-        if (cls[k] != 0 && status[k] == 1) {
+        const int zlo = zr[k] & 4095, zhi = zr[k] >> 12;
+        st[k] = record_status(path, cls[k] - 1, zlo, zhi);
+        if (path == 1) {
             int lo[3], hi[3];
-            tile_range_z(tp, r[k], zr[k] & 4095, zr[k] >> 12, lo, hi);
+            tile_range_z(tp, r[k], zlo, zhi, lo, hi);
             const int off = (cls[k] - 1) * tp.ntiles;
             for (int z = lo[2]; z <= hi[2]; ++z)
                 for (int y = lo[1]; y <= hi[1]; ++y)
@@ -188,52 +160,57 @@ __device__ __forceinline__ void admit_and_append(const TilePlan &tp, const Recor
                         atomicAdd(&s_hist[off + x + tp.ntx * (y + tp.nty * z)], 1u);
         }
     }
-    // append at the block's bases plus the earlier warps' and lanes' records
-    if (mine == 0) return;
-    const unsigned excl = inc2 - mine;
-    unsigned pm = st.base_miss[par] + (wr & 0xffffu) + (excl & 0xffffu);
-    unsigned ph = st.base_hit[par] + (wr >> 16) + (excl >> 16);
+    if (!kOne && i0 + 3 < i1) {
+        // four consecutive slots: one 16-byte store per array
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        if (cls[k] == 0) continue;
-        const int64_t slot =
-            cls[k] == 1 ? static_cast<int64_t>(pm++) : rec.cap - 1 - static_cast<int64_t>(ph++);
+        for (int a = 0; a < 6; ++a)
+            *reinterpret_cast<int4 *>(rec.g[a] + i0) =
+                make_int4(r[0][a], r[1][a], r[2][a], r[3][a]);
+        *reinterpret_cast<int4 *>(rec.status + i0) = make_int4(st[0], st[kK > 1 ? 1 : 0],
+                                                               st[kK > 2 ? 2 : 0], st[kK > 3 ? 3 : 0]);
+    } else {
 #pragma unroll
-        for (int a = 0; a < 6; ++a) rec.g[a][slot] = r[k][a];
-        rec.status[slot] = record_status(status[k], zr[k] & 4095, zr[k] >> 12);
+        for (int k = 0; k < kK; ++k) {
+            const int64_t i = i0 + k;
+            if (i >= i1) break;
+#pragma unroll
+            for (int a = 0; a < 6; ++a) rec.g[a][i] = r[k][a];
+            rec.status[i] = st[k];
+        }
     }
 }
 
+// One block per range of the chunk split.  kVec: the inputs and the records
+// start on 16-byte boundaries, and each thread takes four consecutive
+// histories per step (128-bit loads and stores).
 template <bool kVec>
-__global__ void __launch_bounds__(256, 4) ingest_kernel(Inputs in, int64_t n, GeomQ g, Cordic cd,
-                                                     float tau_l, float tau_h, int use_miss,
-                                                     int use_hit, TilePlan tp, Records rec,
-                                                     Ctrl *ctrl, uint32_t *tile_count)
+__global__ void __launch_bounds__(kIngestThreads, 4) ingest_kernel(
+    Inputs in, int64_t n, int64_t per_block, GeomQ g, Cordic cd, float tau_l, float tau_h,
+    int use_miss, int use_hit, TilePlan tp, Records rec, Ctrl *ctrl, uint32_t *block_count)
 {
     extern __shared__ uint32_t s_hist[];  // 2 * ntiles counters
-    __shared__ AppendStage s_stage;
+    __shared__ unsigned s_demand;
     const int nh = 2 * tp.ntiles;
     for (int t = threadIdx.x; t < nh; t += blockDim.x) s_hist[t] = 0;
+    if (threadIdx.x == 0) s_demand = 0;
     __syncthreads();
     LaneAcc acc;
     TrigCache tc;
-    // each block takes a contiguous range of units (histories arrive grouped
-    // by gantry angle, so a thread's angle, and its cos/sin, rarely change),
-    // in coalesced steps of one unit per thread; every thread of a block runs
-    // the same number of steps (block-wide appends and histogram flush)
-    const int64_t units = kVec ? (n + 3) / 4 : n;
-    const int64_t per_block = (units + gridDim.x - 1) / gridDim.x;
-    const int64_t u0 = static_cast<int64_t>(blockIdx.x) * per_block;
-    const int64_t u1 = u0 + per_block < units ? u0 + per_block : units;
-    const int64_t iters = (per_block + blockDim.x - 1) / blockDim.x;
-    for (int64_t it = 0; it < iters; ++it) {
-        const int64_t uu = u0 + it * blockDim.x + threadIdx.x;
-        const int64_t u = uu < u1 ? uu : units;  // past the block's range: no history
+    // the block's histories arrive grouped by gantry angle, so a thread's
+    // angle, and its cos/sin, rarely change; every thread of a block runs
+    // the same number of steps (warp-wide budget reservations)
+    const int64_t h0 = static_cast<int64_t>(blockIdx.x) * per_block;
+    const int64_t h1 = h0 + per_block < n ? h0 + per_block : n;
+    const unsigned budget =
+        h1 > h0 ? static_cast<unsigned>(h1 - h0) * static_cast<unsigned>(tp.pairs_per_record) : 0u;
+    constexpr int kStep = kVec ? 4 : 1;
+    for (int64_t base = h0; base < h1; base += kStep * static_cast<int64_t>(blockDim.x)) {
+        const int64_t i0 = base + kStep * static_cast<int64_t>(threadIdx.x);
         int cls[4] = {0, 0, 0, 0};
-        int32_t r[4][6];
+        int32_t r[4][6] = {};
         if (kVec) {
-            const int64_t i0 = u * 4;
-            if (i0 + 3 < n) {
+            if (i0 + 3 < h1) {
+                const int64_t u = i0 >> 2;
                 const float4 A = __ldg(reinterpret_cast<const float4 *>(in.angle) + u);
                 const float4 UI = __ldg(reinterpret_cast<const float4 *>(in.u_in) + u);
                 const float4 VI = __ldg(reinterpret_cast<const float4 *>(in.v_in) + u);
@@ -251,17 +228,20 @@ __global__ void __launch_bounds__(256, 4) ingest_kernel(Inputs in, int64_t n, Ge
             } else {
                 for (int k = 0; k < 4; ++k) {
                     const int64_t i = i0 + k;
-                    if (i < n)
+                    if (i < h1)
                         cls[k] = ingest_one(g, cd, tau_l, tau_h, use_miss, use_hit,
                                             in.angle[i], in.u_in[i], in.v_in[i], in.u_out[i],
                                             in.v_out[i], in.wepl[i], r[k], acc, tc);
                 }
             }
-        } else if (u < n) {
-            cls[0] = ingest_one(g, cd, tau_l, tau_h, use_miss, use_hit, in.angle[u], in.u_in[u],
-                                in.v_in[u], in.u_out[u], in.v_out[u], in.wepl[u], r[0], acc, tc);
+            admit_and_write<false>(tp, rec, s_hist, &s_demand, budget, i0, h1, cls, r);
+        } else {
+            if (i0 < h1)
+                cls[0] = ingest_one(g, cd, tau_l, tau_h, use_miss, use_hit, in.angle[i0],
+                                    in.u_in[i0], in.v_in[i0], in.u_out[i0], in.v_out[i0],
+                                    in.wepl[i0], r[0], acc, tc);
+            admit_and_write<true>(tp, rec, s_hist, &s_demand, budget, i0, h1, cls, r);
         }
-        admit_and_append(tp, rec, ctrl, s_hist, cls, r, s_stage, static_cast<int>(it & 1));
     }
     const unsigned a0 = warp_sum_u32(acc.n_in), a1 = warp_sum_u32(acc.n_miss),
                    a2 = warp_sum_u32(acc.n_hit), a3 = warp_sum_u32(acc.n_none),
@@ -273,9 +253,10 @@ __global__ void __launch_bounds__(256, 4) ingest_kernel(Inputs in, int64_t n, Ge
         if (a3) atomicAdd(&ctrl->n_none, static_cast<unsigned long long>(a3));
         if (a4) atomicAdd(&ctrl->n_reject, static_cast<unsigned long long>(a4));
     }
+    if (block_count == nullptr) return;
     __syncthreads();
     for (int t = threadIdx.x; t < nh; t += blockDim.x)
-        if (s_hist[t]) atomicAdd(&tile_count[t], s_hist[t]);
+        block_count[static_cast<size_t>(t) * gridDim.x + blockIdx.x] = s_hist[t];
 }
 
 // ---------------------------------------------------------------- traversal
@@ -284,19 +265,17 @@ __global__ void __launch_bounds__(256) trace_global_kernel(Records rec, Ctrl *ct
                                                            uint32_t *N, uint32_t *M,
                                                            int all_records)
 {
-    const unsigned nm = ctrl->rec_miss, nh = ctrl->rec_hit;
-    const int64_t total = static_cast<int64_t>(nm) + nh;
     const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
     unsigned taken = 0;
-    for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < total;
+    for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < rec.cap;
          i += stride) {
-        const bool miss = i < nm;
-        const int64_t slot = miss ? i : rec.cap - 1 - (i - nm);
-        if (!all_records && status_path(rec.status[slot]) != 2) continue;
-        const int32_t gi[3] = {rec.g[0][slot], rec.g[1][slot], rec.g[2][slot]};
-        const int32_t go[3] = {rec.g[3][slot], rec.g[4][slot], rec.g[5][slot]};
+        const int32_t stw = rec.status[i];
+        const int path = status_path(stw);
+        if (all_records ? path == 0 : path != 2) continue;
+        const int32_t gi[3] = {rec.g[0][i], rec.g[1][i], rec.g[2][i]};
+        const int32_t go[3] = {rec.g[3][i], rec.g[4][i], rec.g[5][i]};
         GlobalVisit v;
-        v.vol = miss ? N : M;
+        v.vol = status_cls(stw) ? M : N;
         walk_all(gi, go, g.nx, g.ny, g.nz, v);
         ++taken;
     }
@@ -319,26 +298,25 @@ __global__ void classify_kernel(const float *__restrict__ w, int64_t n, float ta
 
 cudaError_t launch_ingest(const Inputs &in, int64_t n, const GeomQ &g, const Cordic &cordic,
                           float tau_l, float tau_h, int use_miss, int use_hit, const TilePlan &tp,
-                          const Records &rec, Ctrl *ctrl, uint32_t *tile_count, int sm_count,
+                          const Records &rec, Ctrl *ctrl, uint32_t *block_count, int sm_count,
                           cudaStream_t s)
 {
     if (n <= 0) return cudaSuccess;
-    const bool vec = ((reinterpret_cast<uintptr_t>(in.angle) | reinterpret_cast<uintptr_t>(in.u_in) |
-                       reinterpret_cast<uintptr_t>(in.v_in) | reinterpret_cast<uintptr_t>(in.u_out) |
-                       reinterpret_cast<uintptr_t>(in.v_out) | reinterpret_cast<uintptr_t>(in.wepl)) &
-                      15u) == 0;
-    const int64_t units = vec ? (n + 3) / 4 : n;
-    int64_t blocks = (units + 255) / 256;
-    const int64_t cap_blocks = static_cast<int64_t>(sm_count) * 8;
-    if (blocks > cap_blocks) blocks = cap_blocks;
-    if (blocks < 1) blocks = 1;
+    uintptr_t bits = reinterpret_cast<uintptr_t>(in.angle) | reinterpret_cast<uintptr_t>(in.u_in) |
+                     reinterpret_cast<uintptr_t>(in.v_in) | reinterpret_cast<uintptr_t>(in.u_out) |
+                     reinterpret_cast<uintptr_t>(in.v_out) | reinterpret_cast<uintptr_t>(in.wepl) |
+                     reinterpret_cast<uintptr_t>(rec.status);
+    for (int a = 0; a < 6; ++a) bits |= reinterpret_cast<uintptr_t>(rec.g[a]);
+    const bool vec = (bits & 15u) == 0;
+    const ChunkSplit sp = chunk_split(n, sm_count);
     const size_t smem = sizeof(uint32_t) * 2 * static_cast<size_t>(tp.ntiles);
+    uint32_t *bc = tp.ntiles > 0 ? block_count : nullptr;
     if (vec)
-        ingest_kernel<true><<<static_cast<unsigned>(blocks), 256, smem, s>>>(
-            in, n, g, cordic, tau_l, tau_h, use_miss, use_hit, tp, rec, ctrl, tile_count);
+        ingest_kernel<true><<<static_cast<unsigned>(sp.blocks), kIngestThreads, smem, s>>>(
+            in, n, sp.per_block, g, cordic, tau_l, tau_h, use_miss, use_hit, tp, rec, ctrl, bc);
     else
-        ingest_kernel<false><<<static_cast<unsigned>(blocks), 256, smem, s>>>(
-            in, n, g, cordic, tau_l, tau_h, use_miss, use_hit, tp, rec, ctrl, tile_count);
+        ingest_kernel<false><<<static_cast<unsigned>(sp.blocks), kIngestThreads, smem, s>>>(
+            in, n, sp.per_block, g, cordic, tau_l, tau_h, use_miss, use_hit, tp, rec, ctrl, bc);
     return cudaGetLastError();
 }
 
