@@ -913,6 +913,27 @@ HD_HD void lean_pack(const LeanWalk &L, uint32_t o[kLeanWords])
 // two axes enter that way, and for walks without in-plane motion, it
 // returns -1 and the caller takes the general set-up.  Returns 1 (lean, L
 // filled), 0 (no voxel in the box) or -1 (use run_begin and lean_of).
+// floor(a / b) for b > 0 and |a / b| < 2^20: a correctly rounded float
+// quotient estimate (relative error below 2^-21) is within one of the
+// floor, so one correction step each way settles it; unlike floordiv_small
+// it needs no loop, which keeps the lanes of a warp together.
+HD_HD long long fdiv_small(long long a, long long b)
+{
+#ifdef __CUDA_ARCH__
+    long long q = static_cast<long long>(
+        static_cast<int>(floorf(__fdividef(__ll2float_rn(a), __ll2float_rn(b)))));
+#else
+    long long q = static_cast<long long>(
+        static_cast<int>(std::floor(static_cast<float>(a) / static_cast<float>(b))));
+#endif
+    long long r = a - q * b;
+    if (r < 0) {
+        --q;
+        r += b;
+    }
+    if (r >= b) ++q;
+    return q;
+}
 HD_HD int slab_lean(const int32_t gi[3], const int32_t go[3], int nx, int ny, LeanWalk &L)
 {
     // 32-bit storage throughout (|P| < 2^30, |D| < 2^31, plane distances
@@ -924,7 +945,6 @@ HD_HD int slab_lean(const int32_t gi[3], const int32_t go[3], int nx, int ny, Le
     if (D[0] == 0 && D[1] == 0) return -1;
     // entry parameter tN / tQ (the largest per-axis entry) and its axis
     unsigned tN = 0, tQ = 1;
-    int lim = -1;
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
         unsigned cN = 0, cQ = 1;
@@ -941,7 +961,6 @@ HD_HD int slab_lean(const int32_t gi[3], const int32_t go[3], int nx, int ny, Le
         if (cand && static_cast<unsigned long long>(cN) * tQ > static_cast<unsigned long long>(tN) * cQ) {
             tN = cN;
             tQ = cQ;
-            lim = a;
         }
     }
     if (tN > tQ) return 0;
@@ -950,26 +969,18 @@ HD_HD int slab_lean(const int32_t gi[3], const int32_t go[3], int nx, int ny, Le
     int idx[3];
     bool onp[3];
     const long long den = static_cast<long long>(tQ) << 16;
+    // the entry point's coordinate along each axis, P tQ + tN D over den
+    // (also right for the entry axis and when the segment starts inside)
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-        if (tN == 0) {
-            idx[a] = P[a] >> 16;
-            onp[a] = (P[a] & 0xffff) == 0;
-        } else if (a == lim) {
-            idx[a] = D[a] > 0 ? 0 : n[a];
-            onp[a] = true;
+        const long long num = static_cast<long long>(P[a]) * tQ + static_cast<long long>(tN) * D[a];
+        if (a == 2) {
+            idx[2] = num < 0 ? -1 : (num >= den ? 1 : 0);
+            onp[2] = num == 0 || num == den;
         } else {
-            const long long num = static_cast<long long>(P[a]) * tQ + static_cast<long long>(tN) * D[a];
-            if (a == 2) {
-                // the z index is all the emptiness checks and the upper-face
-                // entry need: below the slab, in it, or on or above its top
-                idx[2] = num < 0 ? -1 : (num >= den ? 1 : 0);
-                onp[2] = num == 0 || num == den;
-            } else {
-                const long long q = floordiv_small(num, den);
-                idx[a] = static_cast<int>(q);
-                onp[a] = num == q * den;
-            }
+            const long long q = fdiv_small(num >> 16, static_cast<long long>(tQ));
+            idx[a] = static_cast<int>(q);
+            onp[a] = num == q * den;
         }
     }
 #pragma unroll
@@ -1000,21 +1011,12 @@ HD_HD int slab_lean(const int32_t gi[3], const int32_t go[3], int nx, int ny, Le
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
         const int f = go[a] >> 16;
-        if (D[a] > 0) {
-            A[a] = static_cast<unsigned>(D[a]);
-            nm[a] = ((idx[a] + 1) << 16) - P[a];
-            k[a] = (f < n[a] - 1 ? f : n[a] - 1) - idx[a];
-        } else if (D[a] < 0) {
-            A[a] = static_cast<unsigned>(-D[a]);
-            nm[a] = P[a] - (idx[a] << 16);
-            k[a] = idx[a] - (f > 0 ? f : 0);
-        } else {
-            A[a] = 0;
-            nm[a] = 1;
-            k[a] = 0;
-        }
-        if (k[a] < 0) return 0;  // the walk ends where it enters
+        const bool pos = D[a] > 0, neg = D[a] < 0;
+        A[a] = pos ? static_cast<unsigned>(D[a]) : (neg ? static_cast<unsigned>(-D[a]) : 0u);
+        nm[a] = pos ? ((idx[a] + 1) << 16) - P[a] : (neg ? P[a] - (idx[a] << 16) : 1);
+        k[a] = pos ? (f < n[a] - 1 ? f : n[a] - 1) - idx[a] : (neg ? idx[a] - (f > 0 ? f : 0) : 0);
     }
+    if (k[0] < 0 || k[1] < 0 || k[2] < 0) return 0;  // the walk ends where it enters
     if (k[2] != 0) return -1;
     // axes: major m, minor 0 (the other in-plane axis), minor 1 (z); every
     // array is read at constant indices (a runtime index would put it in
@@ -1044,7 +1046,7 @@ HD_HD int slab_lean(const int32_t gi[3], const int32_t go[3], int nx, int ny, Le
             q0 = kQBig;
             rh0 = 1;
         } else {
-            const long long q = floordiv_small(dh, static_cast<long long>(a0));
+            const long long q = fdiv_small(dh, static_cast<long long>(a0));
             q0 = static_cast<int>(q);
             rh0 = static_cast<unsigned>(dh - q * static_cast<long long>(a0));
         }
@@ -1055,7 +1057,7 @@ HD_HD int slab_lean(const int32_t gi[3], const int32_t go[3], int nx, int ny, Le
         if (float_of(dh) >= 1048576.0f * static_cast<float>(a1)) {
             q1 = kQBig;
         } else {
-            q1 = static_cast<int>(floordiv_small(dh, static_cast<long long>(a1)));
+            q1 = static_cast<int>(fdiv_small(dh, static_cast<long long>(a1)));
         }
     }
     if (q0 < -1 || q1 < -1) return -1;
@@ -1075,7 +1077,7 @@ HD_HD int slab_lean(const int32_t gi[3], const int32_t go[3], int nx, int ny, Le
             if (float_of(num) >= (static_cast<float>(kc0) + 2.0f) * float_of(step)) {
                 kz = kc0;
             } else {
-                const long long q = floordiv_small(num, step) + 1;
+                const long long q = fdiv_small(num, step) + 1;
                 kz = q < kc0 ? static_cast<int>(q) : kc0;
             }
         }
