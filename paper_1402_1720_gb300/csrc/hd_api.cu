@@ -259,7 +259,7 @@ hd_status ensure_records(hd_scan *s, int64_t n, cudaStream_t st)
         const int64_t pair_cap = pairs_per_record(s->tp) * n;
         const int64_t min_job = s->tp.job_size < hd::kMinJob ? s->tp.job_size : hd::kMinJob;
         const int64_t job_cap = pair_cap / min_job + 2 * s->tp.ntiles + 1;
-        ok = cudaMalloc(&s->pair_buf, sizeof(uint32_t) * (hd::kLeanWords + 2) *
+        ok = cudaMalloc(&s->pair_buf, sizeof(uint32_t) * (hd::kLeanWords + 3) *
                                           static_cast<size_t>(pair_cap)) == cudaSuccess &&
              cudaMalloc(&s->jobs, sizeof(hd::TileJob) * static_cast<size_t>(job_cap)) == cudaSuccess;
         s->tp.pair_cap = pair_cap;
@@ -329,24 +329,31 @@ hd::Records records_of(const hd_scan *s, int64_t n)
     return r;
 }
 
-// Words of tile_count: the 2 * ntiles totals, then a column of pair counts
-// per tile and class for the most ingest blocks a chunk can use.
+// Most ingest blocks a chunk can use.
+size_t ingest_blocks_max(const hd_scan *s)
+{
+    return static_cast<size_t>(s->sm_count > 0 ? s->sm_count : 1) *
+           static_cast<size_t>(hd::kIngestBlocksPerSm);
+}
+
+// Words of tile_count: the 2 * ntiles totals, a column of pair counts per
+// tile and class for the most ingest blocks, then each block's pairs in all.
 size_t tile_count_words(const hd_scan *s)
 {
     const size_t cols = 2 * static_cast<size_t>(s->tp.ntiles);
-    const size_t blocks = static_cast<size_t>(s->sm_count > 0 ? s->sm_count : 1) *
-                          static_cast<size_t>(hd::kIngestBlocksPerSm);
-    return cols * (1 + blocks);
+    return cols * (1 + ingest_blocks_max(s)) + ingest_blocks_max(s);
 }
 
 hd::Pairs pairs_of(const hd_scan *s)
 {
     hd::Pairs p;
-    p.v = reinterpret_cast<uint4 *>(s->pair_buf);
-    // the fallback list follows the lean walks (kLeanWords words per pair)
-    p.fb = s->pair_buf ? reinterpret_cast<uint2 *>(reinterpret_cast<uint32_t *>(s->pair_buf) +
-                                                   hd::kLeanWords * static_cast<size_t>(s->tp.pair_cap))
-                       : nullptr;
+    // the lean walks (kLeanWords words per pair), then the fallback list (two
+    // words per pair), then the ingest blocks' pair lists (one word per pair)
+    uint32_t *base = reinterpret_cast<uint32_t *>(s->pair_buf);
+    const size_t cap = static_cast<size_t>(s->tp.pair_cap);
+    p.v = reinterpret_cast<uint4 *>(base);
+    p.fb = base ? reinterpret_cast<uint2 *>(base + hd::kLeanWords * cap) : nullptr;
+    p.stage = base ? base + (hd::kLeanWords + 2) * cap : nullptr;
     return p;
 }
 
@@ -387,7 +394,7 @@ void make_tile_plan(hd_scan *s)
     tp.ntz = (nz + tp.tz - 1) / tp.tz;
     tp.ntiles = tp.ntx * tp.nty * tp.ntz;
     if (tp.ntiles > hd::kMaxTiles) tp.ntiles = 0;
-    tp.max_tiles = 8;
+    tp.max_tiles = hd::kMaxRecordTiles;
     tp.pairs_per_record = static_cast<int>(pairs_per_record(tp));
     tp.job_size = s->tuning.job_size;  // <= 32767: int16 differences in the tiled traversal
     tp.refill = s->tuning.refill;
@@ -438,16 +445,20 @@ hd_status stage_prepare(hd_scan *s, const hd::Inputs &in, int64_t n, cudaStream_
     hd::TilePlan tp = s->tp;
     if (s->trace_grid <= 0) tp.ntiles = 0;
     HD_CUDA(cudaMemsetAsync(&s->ctrl->njobs, 0, sizeof(hd::Ctrl) - offsetof(hd::Ctrl, njobs), st));
-    uint32_t *block_count = s->tile_count + 2 * static_cast<size_t>(s->tp.ntiles);
+    const size_t cols = 2 * static_cast<size_t>(s->tp.ntiles);
+    uint32_t *block_count = s->tile_count + cols;
+    uint32_t *block_pairs = block_count + cols * ingest_blocks_max(s);
+    const hd::Pairs pairs = pairs_of(s);
     HD_CUDA(hd::launch_ingest(in, n, s->gq, s->cordic, s->params.wepl_miss_lt,
                               s->params.wepl_hit_gt, use_miss, use_hit, tp, rec, s->ctrl,
-                              tp.ntiles > 0 ? block_count : nullptr, s->sm_count, st));
+                              tp.ntiles > 0 ? block_count : nullptr, block_pairs, pairs.stage,
+                              s->sm_count, st));
     s->launches += 1;
     if (tp.ntiles > 0) {
         HD_CUDA(hd::launch_plan(tp, n, block_count, s->tile_count, s->tile_cursor, s->jobs, s->ctrl,
                                 s->sm_count, st));
-        HD_CUDA(hd::launch_scatter(tp, rec, n, s->ctrl, s->tile_cursor, block_count, pairs_of(s),
-                                   s->sm_count, st));
+        HD_CUDA(hd::launch_scatter(tp, rec, n, s->ctrl, s->tile_cursor, block_count, block_pairs,
+                                   pairs, s->sm_count, st));
         s->launches += 3;
     }
     return HD_OK;

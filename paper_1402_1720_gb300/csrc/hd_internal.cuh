@@ -108,7 +108,14 @@ struct TilePlan {
 struct Pairs {
     uint4 *v;   // 2 per pair
     uint2 *fb;  // fallback list: (pair position, 0), pair_cap entries
+    // Each ingest block's pairs in the order its budget assigned them, from
+    // the block's share (block * per_block * pairs_per_record) on: the
+    // record's slot less the block's first slot, times 8, plus the pair's
+    // tile index within the record (below kMaxRecordTiles).
+    uint32_t *stage;
 };
+
+constexpr int kMaxRecordTiles = 8;  // tiles a record may touch on the tiled path
 
 struct TileJob {
     int tile;   // tile id within its class
@@ -139,13 +146,14 @@ struct Inputs {
 // Classification, records and pair counts of a chunk.  block_count (null
 // when tp.ntiles is 0) receives, per tile-class column c (2 tp.ntiles of
 // them) and ingest block b, the pairs of that block's records in that tile
-// at [c * blocks + b]; each block keeps to a pair budget of
-// tp.pairs_per_record per history, and its records beyond it take the
-// global path.
+// at [c * blocks + b]; block_pairs[b] the block's pairs in all, listed in
+// stage (Pairs::stage).  Each block keeps to a pair budget of
+// tp.pairs_per_record per history; its records beyond it take the global
+// path.
 cudaError_t launch_ingest(const Inputs &in, int64_t n, const GeomQ &g, const Cordic &cordic,
                           float tau_l, float tau_h, int use_miss, int use_hit, const TilePlan &tp,
-                          const Records &rec, Ctrl *ctrl, uint32_t *block_count, int sm_count,
-                          cudaStream_t s);
+                          const Records &rec, Ctrl *ctrl, uint32_t *block_count,
+                          uint32_t *block_pairs, uint32_t *stage, int sm_count, cudaStream_t s);
 
 // Per column: the exclusive prefix over blocks of block_count (in place) and
 // the column total into tile_count; then the plan (tile offsets into
@@ -155,11 +163,13 @@ cudaError_t launch_plan(const TilePlan &tp, int64_t n, uint32_t *block_count,
                         int sm_count, cudaStream_t s);
 
 // Counting sort of the (record, tile) pairs by tile, with the walk set-up of
-// each pair; block b of the chunk split writes the pairs of its records from
+// each pair; block b of the chunk split takes the block_pairs[b] pairs that
+// ingest block b listed and writes those of tile c from
 // tile_cursor[c] + block_count[c * blocks + b] on.
 cudaError_t launch_scatter(const TilePlan &tp, const Records &rec, int64_t n, Ctrl *ctrl,
                            const uint32_t *tile_cursor, const uint32_t *block_count,
-                           const Pairs &pairs, int sm_count, cudaStream_t s);
+                           const uint32_t *block_pairs, const Pairs &pairs, int sm_count,
+                           cudaStream_t s);
 
 // Persistent traversal over the jobs of nscans scans (descs on the device),
 // handed out through *job_counter (zero before the launch).  smem_words is

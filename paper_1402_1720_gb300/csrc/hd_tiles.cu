@@ -151,13 +151,13 @@ __device__ __noinline__ bool general_setup(const int32_t gi[3], const int32_t go
     return fallback;
 }
 
-// Counting sort of (record, tile) pairs by tile.  Block b takes the slots
-// of ingest block b and writes its pairs of tile c from
+// Counting sort of (record, tile) pairs by tile.  Block b takes the pairs
+// ingest block b listed, one per thread, and writes those of tile c from
 // tile_start[c] + block_base[c * blocks + b] on (a shared-memory cursor per
 // tile orders them within the block).
 __global__ void __launch_bounds__(kScatterThreads, 4) scatter_kernel(
     TilePlan tp, Records rec, int64_t per_block, const uint32_t *tile_start,
-    const uint32_t *block_base, Ctrl *ctrl, Pairs pairs)
+    const uint32_t *block_base, const uint32_t *block_pairs, Ctrl *ctrl, Pairs pairs)
 {
     extern __shared__ uint32_t s_mem[];
     const int nt = 2 * tp.ntiles;
@@ -169,97 +169,71 @@ __global__ void __launch_bounds__(kScatterThreads, 4) scatter_kernel(
     }
     __syncthreads();
     const int64_t h0 = static_cast<int64_t>(blockIdx.x) * per_block;
-    const int64_t h1 = h0 + per_block < rec.cap ? h0 + per_block : rec.cap;
-    // The warp's (record, tile) pairs are dealt out one per lane, so the
-    // set-up below runs on all lanes whatever each record's tile count.
-    const int lane = static_cast<int>(threadIdx.x & 31u);
-    for (int64_t base = h0; base < h1; base += kScatterThreads) {
-        const int64_t slot = base + threadIdx.x;
-        int cls = 0;
-        int32_t r[6] = {0, 0, 0, 0, 0, 0};
-        int lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
-        int cnt = 0;
-        if (slot < h1) {
-            const int32_t stw = rec.status[slot];
-            if (status_path(stw) == 1) {
-                cls = status_cls(stw);
+    const unsigned npairs = block_pairs[blockIdx.x];
+    const uint32_t *list = pairs.stage + static_cast<int64_t>(blockIdx.x) * per_block * tp.pairs_per_record;
+    for (unsigned e = threadIdx.x; e < npairs; e += kScatterThreads) {
+        const uint32_t code = list[e];
+        const int64_t slot = h0 + (code >> 3);
+        const int j = static_cast<int>(code & 7u);
+        const int32_t stw = rec.status[slot];
+        const int cls = status_cls(stw);
+        int32_t q[6];
 #pragma unroll
-                for (int a = 0; a < 6; ++a) r[a] = rec.g[a][slot];
-                cnt = tile_range_z(tp, r, status_zlo(stw), status_zhi(stw), lo, hi);
-            }
-        }
-        const int incl = static_cast<int>(warp_incl_scan_u(static_cast<unsigned>(cnt)));
-        const int total = __shfl_sync(kFull, incl, 31);
+        for (int a = 0; a < 6; ++a) q[a] = rec.g[a][slot];
+        int lo[3], hi[3];
+        tile_range_z(tp, q, status_zlo(stw), status_zhi(stw), lo, hi);
+        // the j-th tile of the record's box, x fastest
         const int ex = hi[0] - lo[0] + 1, ey = hi[1] - lo[1] + 1;
-        for (int first = 0; first < total; first += 32) {
-            const int p = first + lane;
-            const int pc = p < total ? p : total - 1;
-            // owner: the first lane whose inclusive count exceeds pc
-            int own = 0;
-#pragma unroll
-            for (int b = 16; b >= 1; b >>= 1)
-                if (__shfl_sync(kFull, incl, own + b - 1) <= pc) own += b;
-            const int j = pc - (__shfl_sync(kFull, incl, own) - __shfl_sync(kFull, cnt, own));
-            int32_t q[6];
-#pragma unroll
-            for (int a = 0; a < 6; ++a) q[a] = __shfl_sync(kFull, r[a], own);
-            const int lx = __shfl_sync(kFull, lo[0], own), ly = __shfl_sync(kFull, lo[1], own);
-            const int lz = __shfl_sync(kFull, lo[2], own);
-            const int oex = __shfl_sync(kFull, ex, own), oey = __shfl_sync(kFull, ey, own);
-            const int ocls = __shfl_sync(kFull, cls, own);
-            if (p >= total) continue;
-            // the j-th tile of the owner's box, x fastest
-            int x = lx, y = ly, z = lz + j;
-            if (oex != 1 || oey != 1) {
-                x = lx + j % oex;
-                y = ly + (j / oex) % oey;
-                z = lz + j / (oex * oey);
-            }
-            const int t = ocls * tp.ntiles + x + tp.ntx * (y + tp.nty * z);
-            const uint32_t pos = s_base[t] + atomicAdd(&s_next[t], 1u);
-            // set up the walk of this record clipped to this tile
-            const int x0 = x * tp.tx, y0 = y * tp.ty, z0 = z * tp.tz;
-            const int dx = min(tp.tx, tp.nx - x0), dy = min(tp.ty, tp.ny - y0),
-                      dz = min(tp.tz, tp.nz - z0);
-            const int32_t gi[3] = {q[0] - (x0 << 16), q[1] - (y0 << 16), q[2] - (z0 << 16)};
-            const int32_t go[3] = {q[3] - (x0 << 16), q[4] - (y0 << 16), q[5] - (z0 << 16)};
-            // one-slice tiles (the default plan): the direct set-up; the
-            // walks it declines (ties at the start, no in-plane motion) go to
-            // the fallback list, whose general run walk is exact for any walk.
-            // Deeper slabs: the general set-up (out of line).
-            uint4 p0, p1;
-            bool fallback = false;
-            if (dz == 1) {
-                LeanWalk L;
-                const int rl = slab_lean(gi, go, dx, dy, L);
-                uint32_t pk[kLeanWords];
-                if (rl == 1) {
-                    lean_pack(L, pk);
-                } else if (rl == 0) {
-                    lean_pack_empty(pk);
-                } else {
-                    general_pack(gi, go, t - ocls * tp.ntiles, ocls, pk);
-                    fallback = true;
-                }
-                p0 = make_uint4(pk[0], pk[1], pk[2], pk[3]);
-                p1 = make_uint4(pk[4], pk[5], pk[6], pk[7]);
+        int x = lo[0], y = lo[1], z = lo[2] + j;
+        if (ex != 1 || ey != 1) {
+            x = lo[0] + j % ex;
+            y = lo[1] + (j / ex) % ey;
+            z = lo[2] + j / (ex * ey);
+        }
+        const int t = cls * tp.ntiles + x + tp.ntx * (y + tp.nty * z);
+        const uint32_t pos = s_base[t] + atomicAdd(&s_next[t], 1u);
+        // set up the walk of this record clipped to this tile
+        const int x0 = x * tp.tx, y0 = y * tp.ty, z0 = z * tp.tz;
+        const int dx = min(tp.tx, tp.nx - x0), dy = min(tp.ty, tp.ny - y0),
+                  dz = min(tp.tz, tp.nz - z0);
+        const int32_t gi[3] = {q[0] - (x0 << 16), q[1] - (y0 << 16), q[2] - (z0 << 16)};
+        const int32_t go[3] = {q[3] - (x0 << 16), q[4] - (y0 << 16), q[5] - (z0 << 16)};
+        // one-slice tiles (the default plan): the direct set-up; the
+        // walks it declines (ties at the start, no in-plane motion) go to
+        // the fallback list, whose general run walk is exact for any walk.
+        // Deeper slabs: the general set-up (out of line).
+        uint4 p0, p1;
+        bool fallback = false;
+        if (dz == 1) {
+            LeanWalk L;
+            const int rl = slab_lean(gi, go, dx, dy, L);
+            uint32_t pk[kLeanWords];
+            if (rl == 1) {
+                lean_pack(L, pk);
+            } else if (rl == 0) {
+                lean_pack_empty(pk);
             } else {
-                fallback = general_setup(gi, go, dx, dy, dz, t - ocls * tp.ntiles, ocls, p0, p1);
+                general_pack(gi, go, t - cls * tp.ntiles, cls, pk);
+                fallback = true;
             }
-            pairs.v[2 * static_cast<size_t>(pos)] = p0;
-            pairs.v[2 * static_cast<size_t>(pos) + 1] = p1;
-            if (fallback) {
-                // append to the fallback list, one counter update per group of
-                // lanes arriving together
-                cg::coalesced_group grp = cg::coalesced_threads();
-                unsigned at = 0;
-                if (grp.thread_rank() == 0) {
-                    at = atomicAdd(&ctrl->n_pair_fallback, grp.size());
-                    atomicAdd(&ctrl->pairs_general, static_cast<unsigned long long>(grp.size()));
-                }
-                at = grp.shfl(at, 0) + grp.thread_rank();
-                pairs.fb[at] = make_uint2(pos, 0u);
+            p0 = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+            p1 = make_uint4(pk[4], pk[5], pk[6], pk[7]);
+        } else {
+            fallback = general_setup(gi, go, dx, dy, dz, t - cls * tp.ntiles, cls, p0, p1);
+        }
+        pairs.v[2 * static_cast<size_t>(pos)] = p0;
+        pairs.v[2 * static_cast<size_t>(pos) + 1] = p1;
+        if (fallback) {
+            // append to the fallback list, one counter update per group of
+            // lanes arriving together
+            cg::coalesced_group grp = cg::coalesced_threads();
+            unsigned at = 0;
+            if (grp.thread_rank() == 0) {
+                at = atomicAdd(&ctrl->n_pair_fallback, grp.size());
+                atomicAdd(&ctrl->pairs_general, static_cast<unsigned long long>(grp.size()));
             }
+            at = grp.shfl(at, 0) + grp.thread_rank();
+            pairs.fb[at] = make_uint2(pos, 0u);
         }
     }
 }
@@ -560,13 +534,14 @@ cudaError_t launch_plan(const TilePlan &tp, int64_t n, uint32_t *block_count,
 
 cudaError_t launch_scatter(const TilePlan &tp, const Records &rec, int64_t n, Ctrl *ctrl,
                            const uint32_t *tile_cursor, const uint32_t *block_count,
-                           const Pairs &pairs, int sm_count, cudaStream_t s)
+                           const uint32_t *block_pairs, const Pairs &pairs, int sm_count,
+                           cudaStream_t s)
 {
     if (n <= 0) return cudaSuccess;
     const ChunkSplit sp = chunk_split(n, sm_count);
     const size_t smem = sizeof(uint32_t) * 4 * static_cast<size_t>(tp.ntiles);
     scatter_kernel<<<static_cast<unsigned>(sp.blocks), kScatterThreads, smem, s>>>(
-        tp, rec, sp.per_block, tile_cursor, block_count, ctrl, pairs);
+        tp, rec, sp.per_block, tile_cursor, block_count, block_pairs, ctrl, pairs);
     return cudaGetLastError();
 }
 

@@ -101,16 +101,21 @@ __device__ __forceinline__ unsigned warp_incl_scan(unsigned v)
 }
 
 // Decide the path of up to 4 records per lane (tiled within the block's pair
-// budget, else global), count their tiles in the block histogram and write
-// them at their histories' slots (i0 .. i0 + 3, or i0 alone when kOne).
+// budget, else global), count their tiles in the block histogram, list
+// their pairs in the block's share of stage, and write them at their
+// histories' slots (i0 .. i0 + 3, or i0 alone when kOne).  The pairs the
+// budget admits fill the list from its start without gaps: reservations
+// tile [0, total) in order of their ends, and only the one record that
+// straddles the budget, and the records after it, are turned away.
 // Budget reservations are per warp on a shared-memory counter, so the
 // block never waits at a barrier; once a reservation overruns the budget
 // the records it covers take the global path (exact either way).
 template <bool kOne>
 __device__ __forceinline__ void admit_and_write(const TilePlan &tp, const Records &rec,
                                                 uint32_t *s_hist, unsigned *s_demand,
-                                                unsigned budget, int64_t i0, int64_t i1,
-                                                const int cls[4], const int32_t r[4][6])
+                                                unsigned budget, int64_t h0, int64_t i0,
+                                                int64_t i1, uint32_t *stage, const int cls[4],
+                                                const int32_t r[4][6])
 {
     constexpr int kK = kOne ? 1 : 4;
     int tcount[kK];
@@ -158,6 +163,11 @@ __device__ __forceinline__ void admit_and_write(const TilePlan &tp, const Record
                 for (int y = lo[1]; y <= hi[1]; ++y)
                     for (int x = lo[0]; x <= hi[0]; ++x)
                         atomicAdd(&s_hist[off + x + tp.ntx * (y + tp.nty * z)], 1u);
+            // the record's pairs hold positions end - c .. end - 1 of the
+            // block's list (all below its budget)
+            const uint32_t code = static_cast<uint32_t>(i0 + k - h0) << 3;
+            const unsigned first = static_cast<unsigned>(end) - static_cast<unsigned>(tcount[k]);
+            for (int j = 0; j < tcount[k]; ++j) stage[first + j] = code | static_cast<uint32_t>(j);
         }
     }
     if (!kOne && i0 + 3 < i1) {
@@ -186,13 +196,17 @@ __device__ __forceinline__ void admit_and_write(const TilePlan &tp, const Record
 template <bool kVec>
 __global__ void __launch_bounds__(kIngestThreads, 4) ingest_kernel(
     Inputs in, int64_t n, int64_t per_block, GeomQ g, Cordic cd, float tau_l, float tau_h,
-    int use_miss, int use_hit, TilePlan tp, Records rec, Ctrl *ctrl, uint32_t *block_count)
+    int use_miss, int use_hit, TilePlan tp, Records rec, Ctrl *ctrl, uint32_t *block_count,
+    uint32_t *block_pairs, uint32_t *stage)
 {
     extern __shared__ uint32_t s_hist[];  // 2 * ntiles counters
-    __shared__ unsigned s_demand;
+    __shared__ unsigned s_demand, s_total;
     const int nh = 2 * tp.ntiles;
     for (int t = threadIdx.x; t < nh; t += blockDim.x) s_hist[t] = 0;
-    if (threadIdx.x == 0) s_demand = 0;
+    if (threadIdx.x == 0) {
+        s_demand = 0;
+        s_total = 0;
+    }
     __syncthreads();
     LaneAcc acc;
     TrigCache tc;
@@ -203,6 +217,8 @@ __global__ void __launch_bounds__(kIngestThreads, 4) ingest_kernel(
     const int64_t h1 = h0 + per_block < n ? h0 + per_block : n;
     const unsigned budget =
         h1 > h0 ? static_cast<unsigned>(h1 - h0) * static_cast<unsigned>(tp.pairs_per_record) : 0u;
+    uint32_t *const list =
+        stage ? stage + static_cast<int64_t>(blockIdx.x) * per_block * tp.pairs_per_record : nullptr;
     constexpr int kStep = kVec ? 4 : 1;
     for (int64_t base = h0; base < h1; base += kStep * static_cast<int64_t>(blockDim.x)) {
         const int64_t i0 = base + kStep * static_cast<int64_t>(threadIdx.x);
@@ -234,13 +250,13 @@ __global__ void __launch_bounds__(kIngestThreads, 4) ingest_kernel(
                                             in.v_out[i], in.wepl[i], r[k], acc, tc);
                 }
             }
-            admit_and_write<false>(tp, rec, s_hist, &s_demand, budget, i0, h1, cls, r);
+            admit_and_write<false>(tp, rec, s_hist, &s_demand, budget, h0, i0, h1, list, cls, r);
         } else {
             if (i0 < h1)
                 cls[0] = ingest_one(g, cd, tau_l, tau_h, use_miss, use_hit, in.angle[i0],
                                     in.u_in[i0], in.v_in[i0], in.u_out[i0], in.v_out[i0],
                                     in.wepl[i0], r[0], acc, tc);
-            admit_and_write<true>(tp, rec, s_hist, &s_demand, budget, i0, h1, cls, r);
+            admit_and_write<true>(tp, rec, s_hist, &s_demand, budget, h0, i0, h1, list, cls, r);
         }
     }
     const unsigned a0 = warp_sum_u32(acc.n_in), a1 = warp_sum_u32(acc.n_miss),
@@ -255,8 +271,15 @@ __global__ void __launch_bounds__(kIngestThreads, 4) ingest_kernel(
     }
     if (block_count == nullptr) return;
     __syncthreads();
-    for (int t = threadIdx.x; t < nh; t += blockDim.x)
+    unsigned mine = 0;
+    for (int t = threadIdx.x; t < nh; t += blockDim.x) {
         block_count[static_cast<size_t>(t) * gridDim.x + blockIdx.x] = s_hist[t];
+        mine += s_hist[t];
+    }
+    mine = warp_sum_u32(mine);
+    if ((threadIdx.x & 31u) == 0 && mine) atomicAdd(&s_total, mine);
+    __syncthreads();
+    if (threadIdx.x == 0) block_pairs[blockIdx.x] = s_total;
 }
 
 // ---------------------------------------------------------------- traversal
@@ -298,8 +321,8 @@ __global__ void classify_kernel(const float *__restrict__ w, int64_t n, float ta
 
 cudaError_t launch_ingest(const Inputs &in, int64_t n, const GeomQ &g, const Cordic &cordic,
                           float tau_l, float tau_h, int use_miss, int use_hit, const TilePlan &tp,
-                          const Records &rec, Ctrl *ctrl, uint32_t *block_count, int sm_count,
-                          cudaStream_t s)
+                          const Records &rec, Ctrl *ctrl, uint32_t *block_count,
+                          uint32_t *block_pairs, uint32_t *stage, int sm_count, cudaStream_t s)
 {
     if (n <= 0) return cudaSuccess;
     uintptr_t bits = reinterpret_cast<uintptr_t>(in.angle) | reinterpret_cast<uintptr_t>(in.u_in) |
@@ -309,14 +332,20 @@ cudaError_t launch_ingest(const Inputs &in, int64_t n, const GeomQ &g, const Cor
     for (int a = 0; a < 6; ++a) bits |= reinterpret_cast<uintptr_t>(rec.g[a]);
     const bool vec = (bits & 15u) == 0;
     const ChunkSplit sp = chunk_split(n, sm_count);
-    const size_t smem = sizeof(uint32_t) * 2 * static_cast<size_t>(tp.ntiles);
-    uint32_t *bc = tp.ntiles > 0 ? block_count : nullptr;
+    // without the tiled path's buffers every record takes the global path
+    const bool tiled = tp.ntiles > 0 && block_count && block_pairs && stage;
+    TilePlan tpl = tp;
+    if (!tiled) tpl.ntiles = 0;
+    const size_t smem = sizeof(uint32_t) * 2 * static_cast<size_t>(tpl.ntiles);
+    uint32_t *bc = tiled ? block_count : nullptr;
+    uint32_t *bp = tiled ? block_pairs : nullptr;
+    uint32_t *sg = tiled ? stage : nullptr;
     if (vec)
         ingest_kernel<true><<<static_cast<unsigned>(sp.blocks), kIngestThreads, smem, s>>>(
-            in, n, sp.per_block, g, cordic, tau_l, tau_h, use_miss, use_hit, tp, rec, ctrl, bc);
+            in, n, sp.per_block, g, cordic, tau_l, tau_h, use_miss, use_hit, tpl, rec, ctrl, bc, bp, sg);
     else
         ingest_kernel<false><<<static_cast<unsigned>(sp.blocks), kIngestThreads, smem, s>>>(
-            in, n, sp.per_block, g, cordic, tau_l, tau_h, use_miss, use_hit, tp, rec, ctrl, bc);
+            in, n, sp.per_block, g, cordic, tau_l, tau_h, use_miss, use_hit, tpl, rec, ctrl, bc, bp, sg);
     return cudaGetLastError();
 }
 
