@@ -121,6 +121,27 @@ HD_HD long long floordiv_small(long long a, long long b)
     return q;
 }
 
+// floor(a / b) for b > 0 and |a / b| < 2^20: a correctly rounded float
+// quotient estimate (relative error below 2^-21) is within one of the
+// floor, so one correction step each way settles it; unlike floordiv_small
+// it needs no loop, which keeps the lanes of a warp together.
+HD_HD long long fdiv_small(long long a, long long b)
+{
+#ifdef __CUDA_ARCH__
+    long long q = static_cast<long long>(
+        static_cast<int>(floorf(__fdividef(__ll2float_rn(a), __ll2float_rn(b)))));
+#else
+    long long q = static_cast<long long>(
+        static_cast<int>(std::floor(static_cast<float>(a) / static_cast<float>(b))));
+#endif
+    long long r = a - q * b;
+    if (r < 0) {
+        --q;
+        r += b;
+    }
+    if (r >= b) ++q;
+    return q;
+}
 // Rotation-mode CORDIC of an angle in degrees * 2^16: cos and sin * 2^30.
 HD_HD void cordic_cs(long long a_q16, const Cordic &cd, long long &c, long long &s)
 {
@@ -913,27 +934,6 @@ HD_HD void lean_pack(const LeanWalk &L, uint32_t o[kLeanWords])
 // two axes enter that way, and for walks without in-plane motion, it
 // returns -1 and the caller takes the general set-up.  Returns 1 (lean, L
 // filled), 0 (no voxel in the box) or -1 (use run_begin and lean_of).
-// floor(a / b) for b > 0 and |a / b| < 2^20: a correctly rounded float
-// quotient estimate (relative error below 2^-21) is within one of the
-// floor, so one correction step each way settles it; unlike floordiv_small
-// it needs no loop, which keeps the lanes of a warp together.
-HD_HD long long fdiv_small(long long a, long long b)
-{
-#ifdef __CUDA_ARCH__
-    long long q = static_cast<long long>(
-        static_cast<int>(floorf(__fdividef(__ll2float_rn(a), __ll2float_rn(b)))));
-#else
-    long long q = static_cast<long long>(
-        static_cast<int>(std::floor(static_cast<float>(a) / static_cast<float>(b))));
-#endif
-    long long r = a - q * b;
-    if (r < 0) {
-        --q;
-        r += b;
-    }
-    if (r >= b) ++q;
-    return q;
-}
 HD_HD int slab_lean(const int32_t gi[3], const int32_t go[3], int nx, int ny, LeanWalk &L)
 {
     // 32-bit storage throughout (|P| < 2^30, |D| < 2^31, plane distances

@@ -100,100 +100,67 @@ __device__ __forceinline__ unsigned warp_incl_scan(unsigned v)
     return v;
 }
 
-// Decide the path of up to 4 records per lane (tiled within the block's pair
-// budget, else global), count their tiles in the block histogram, list
-// their pairs in the block's share of stage, and write them at their
-// histories' slots (i0 .. i0 + 3, or i0 alone when kOne).  The pairs the
-// budget admits fill the list from its start without gaps: reservations
-// tile [0, total) in order of their ends, and only the one record that
-// straddles the budget, and the records after it, are turned away.
-// Budget reservations are per warp on a shared-memory counter, so the
-// block never waits at a barrier; once a reservation overruns the budget
-// the records it covers take the global path (exact either way).
-template <bool kOne>
+// Decide the path of each lane's record (tiled within the block's pair
+// budget, else global), count its tiles in the block histogram, list its
+// pairs in the block's share of stage, and write it at its history's slot
+// i (when i < i1; cls 0: no record).  Budget reservations are per warp on a
+// shared-memory counter, so the block never waits at a barrier.  The pairs
+// the budget admits fill the list from its start without gaps: the
+// reservations tile [0, total) in the order of their ends, and only the one
+// record that straddles the budget, and the records after it, are turned
+// away (they take the global path, exact either way).
 __device__ __forceinline__ void admit_and_write(const TilePlan &tp, const Records &rec,
                                                 uint32_t *s_hist, unsigned *s_demand,
-                                                unsigned budget, int64_t h0, int64_t i0,
-                                                int64_t i1, uint32_t *stage, const int cls[4],
-                                                const int32_t r[4][6])
+                                                unsigned budget, int64_t h0, int64_t i,
+                                                int64_t i1, uint32_t *stage, int cls,
+                                                const int32_t r[6])
 {
-    constexpr int kK = kOne ? 1 : 4;
-    int tcount[kK];
-    int zr[kK];  // the record's slices, zlo + 4096 zhi (computed once here)
-    int ok[kK];
-    unsigned demand = 0;
-#pragma unroll
-    for (int k = 0; k < kK; ++k) {
-        tcount[k] = 0;
-        zr[k] = 0;
-        ok[k] = 0;
-        if (cls[k] == 0) continue;
-        int lo[3], hi[3], zlo, zhi;
-        const int c = grid_z_range(tp, r[k], zlo, zhi) ? tile_range_z(tp, r[k], zlo, zhi, lo, hi) : 0;
-        if (c == 0) continue;  // no voxel of the grid: nothing to traverse
-        ok[k] = 1;
-        zr[k] = zlo + 4096 * zhi;
-        tcount[k] = (tp.ntiles > 0 && c <= tp.max_tiles) ? c : -1;
-        if (tcount[k] > 0) demand += static_cast<unsigned>(c);
+    int tcount = 0;
+    int zlo = 0, zhi = 0;
+    bool ok = false;
+    if (cls != 0) {
+        int lo[3], hi[3];
+        const int c = grid_z_range(tp, r, zlo, zhi) ? tile_range_z(tp, r, zlo, zhi, lo, hi) : 0;
+        ok = c != 0;  // else no voxel of the grid: nothing to traverse
+        tcount = (tp.ntiles > 0 && c <= tp.max_tiles) ? c : -1;
     }
+    const unsigned demand = ok && tcount > 0 ? static_cast<unsigned>(tcount) : 0u;
     const unsigned lane = threadIdx.x & 31u;
     const unsigned incl = warp_incl_scan(demand);
     const unsigned tot = __shfl_sync(0xffffffffu, incl, 31);
     unsigned wbase = 0;
     if (lane == 31 && tot) wbase = atomicAdd(s_demand, tot);
     wbase = __shfl_sync(0xffffffffu, wbase, 31);
-    unsigned long long end = static_cast<unsigned long long>(wbase) + (incl - demand);
-    int32_t st[kK];
-#pragma unroll
-    for (int k = 0; k < kK; ++k) {
-        st[k] = 0;
-        if (!ok[k]) continue;
-        int path = 2;
-        if (tcount[k] > 0) {
-            end += static_cast<unsigned>(tcount[k]);
-            if (end <= budget) path = 1;
-        }
-        const int zlo = zr[k] & 4095, zhi = zr[k] >> 12;
-        st[k] = record_status(path, cls[k] - 1, zlo, zhi);
+    const unsigned long long end = static_cast<unsigned long long>(wbase) + incl;
+    if (i >= i1) return;
+    int32_t st = 0;
+    if (ok) {
+        const int path = demand > 0 && end <= budget ? 1 : 2;
+        st = record_status(path, cls - 1, zlo, zhi);
         if (path == 1) {
             int lo[3], hi[3];
-            tile_range_z(tp, r[k], zlo, zhi, lo, hi);
-            const int off = (cls[k] - 1) * tp.ntiles;
+            tile_range_z(tp, r, zlo, zhi, lo, hi);
+            const int off = (cls - 1) * tp.ntiles;
             for (int z = lo[2]; z <= hi[2]; ++z)
                 for (int y = lo[1]; y <= hi[1]; ++y)
                     for (int x = lo[0]; x <= hi[0]; ++x)
                         atomicAdd(&s_hist[off + x + tp.ntx * (y + tp.nty * z)], 1u);
             // the record's pairs hold positions end - c .. end - 1 of the
             // block's list (all below its budget)
-            const uint32_t code = static_cast<uint32_t>(i0 + k - h0) << 3;
-            const unsigned first = static_cast<unsigned>(end) - static_cast<unsigned>(tcount[k]);
-            for (int j = 0; j < tcount[k]; ++j) stage[first + j] = code | static_cast<uint32_t>(j);
+            const uint32_t code = static_cast<uint32_t>(i - h0) << 3;
+            const unsigned first = static_cast<unsigned>(end) - demand;
+            for (int j = 0; j < tcount; ++j) stage[first + j] = code | static_cast<uint32_t>(j);
         }
+#pragma unroll
+        for (int a = 0; a < 6; ++a) rec.g[a][i] = r[a];
     }
-    if (!kOne && i0 + 3 < i1) {
-        // four consecutive slots: one 16-byte store per array
-#pragma unroll
-        for (int a = 0; a < 6; ++a)
-            *reinterpret_cast<int4 *>(rec.g[a] + i0) =
-                make_int4(r[0][a], r[1][a], r[2][a], r[3][a]);
-        *reinterpret_cast<int4 *>(rec.status + i0) = make_int4(st[0], st[kK > 1 ? 1 : 0],
-                                                               st[kK > 2 ? 2 : 0], st[kK > 3 ? 3 : 0]);
-    } else {
-#pragma unroll
-        for (int k = 0; k < kK; ++k) {
-            const int64_t i = i0 + k;
-            if (i >= i1) break;
-#pragma unroll
-            for (int a = 0; a < 6; ++a) rec.g[a][i] = r[k][a];
-            rec.status[i] = st[k];
-        }
-    }
+    rec.status[i] = st;
 }
 
-// One block per range of the chunk split.  kVec: the inputs and the records
-// start on 16-byte boundaries, and each thread takes four consecutive
-// histories per step (128-bit loads and stores).
-template <bool kVec>
+// One block per range of the chunk split, one history per thread and step
+// (coalesced 32-bit loads of each array).  One history per step keeps a
+// single inlined copy of the per-history code: four per step, with 128-bit
+// loads, ran slower for the instruction-cache misses and register spills.
 __global__ void __launch_bounds__(kIngestThreads, 4) ingest_kernel(
     Inputs in, int64_t n, int64_t per_block, GeomQ g, Cordic cd, float tau_l, float tau_h,
     int use_miss, int use_hit, TilePlan tp, Records rec, Ctrl *ctrl, uint32_t *block_count,
@@ -219,45 +186,14 @@ __global__ void __launch_bounds__(kIngestThreads, 4) ingest_kernel(
         h1 > h0 ? static_cast<unsigned>(h1 - h0) * static_cast<unsigned>(tp.pairs_per_record) : 0u;
     uint32_t *const list =
         stage ? stage + static_cast<int64_t>(blockIdx.x) * per_block * tp.pairs_per_record : nullptr;
-    constexpr int kStep = kVec ? 4 : 1;
-    for (int64_t base = h0; base < h1; base += kStep * static_cast<int64_t>(blockDim.x)) {
-        const int64_t i0 = base + kStep * static_cast<int64_t>(threadIdx.x);
-        int cls[4] = {0, 0, 0, 0};
-        int32_t r[4][6] = {};
-        if (kVec) {
-            if (i0 + 3 < h1) {
-                const int64_t u = i0 >> 2;
-                const float4 A = __ldg(reinterpret_cast<const float4 *>(in.angle) + u);
-                const float4 UI = __ldg(reinterpret_cast<const float4 *>(in.u_in) + u);
-                const float4 VI = __ldg(reinterpret_cast<const float4 *>(in.v_in) + u);
-                const float4 UO = __ldg(reinterpret_cast<const float4 *>(in.u_out) + u);
-                const float4 VO = __ldg(reinterpret_cast<const float4 *>(in.v_out) + u);
-                const float4 W = __ldg(reinterpret_cast<const float4 *>(in.wepl) + u);
-                cls[0] = ingest_one(g, cd, tau_l, tau_h, use_miss, use_hit, A.x, UI.x, VI.x,
-                                    UO.x, VO.x, W.x, r[0], acc, tc);
-                cls[1] = ingest_one(g, cd, tau_l, tau_h, use_miss, use_hit, A.y, UI.y, VI.y,
-                                    UO.y, VO.y, W.y, r[1], acc, tc);
-                cls[2] = ingest_one(g, cd, tau_l, tau_h, use_miss, use_hit, A.z, UI.z, VI.z,
-                                    UO.z, VO.z, W.z, r[2], acc, tc);
-                cls[3] = ingest_one(g, cd, tau_l, tau_h, use_miss, use_hit, A.w, UI.w, VI.w,
-                                    UO.w, VO.w, W.w, r[3], acc, tc);
-            } else {
-                for (int k = 0; k < 4; ++k) {
-                    const int64_t i = i0 + k;
-                    if (i < h1)
-                        cls[k] = ingest_one(g, cd, tau_l, tau_h, use_miss, use_hit,
-                                            in.angle[i], in.u_in[i], in.v_in[i], in.u_out[i],
-                                            in.v_out[i], in.wepl[i], r[k], acc, tc);
-                }
-            }
-            admit_and_write<false>(tp, rec, s_hist, &s_demand, budget, h0, i0, h1, list, cls, r);
-        } else {
-            if (i0 < h1)
-                cls[0] = ingest_one(g, cd, tau_l, tau_h, use_miss, use_hit, in.angle[i0],
-                                    in.u_in[i0], in.v_in[i0], in.u_out[i0], in.v_out[i0],
-                                    in.wepl[i0], r[0], acc, tc);
-            admit_and_write<true>(tp, rec, s_hist, &s_demand, budget, h0, i0, h1, list, cls, r);
-        }
+    for (int64_t base = h0; base < h1; base += blockDim.x) {
+        const int64_t i = base + threadIdx.x;
+        int cls = 0;
+        int32_t r[6] = {0, 0, 0, 0, 0, 0};
+        if (i < h1)
+            cls = ingest_one(g, cd, tau_l, tau_h, use_miss, use_hit, in.angle[i], in.u_in[i],
+                             in.v_in[i], in.u_out[i], in.v_out[i], in.wepl[i], r, acc, tc);
+        admit_and_write(tp, rec, s_hist, &s_demand, budget, h0, i, h1, list, cls, r);
     }
     const unsigned a0 = warp_sum_u32(acc.n_in), a1 = warp_sum_u32(acc.n_miss),
                    a2 = warp_sum_u32(acc.n_hit), a3 = warp_sum_u32(acc.n_none),
@@ -325,27 +261,15 @@ cudaError_t launch_ingest(const Inputs &in, int64_t n, const GeomQ &g, const Cor
                           uint32_t *block_pairs, uint32_t *stage, int sm_count, cudaStream_t s)
 {
     if (n <= 0) return cudaSuccess;
-    uintptr_t bits = reinterpret_cast<uintptr_t>(in.angle) | reinterpret_cast<uintptr_t>(in.u_in) |
-                     reinterpret_cast<uintptr_t>(in.v_in) | reinterpret_cast<uintptr_t>(in.u_out) |
-                     reinterpret_cast<uintptr_t>(in.v_out) | reinterpret_cast<uintptr_t>(in.wepl) |
-                     reinterpret_cast<uintptr_t>(rec.status);
-    for (int a = 0; a < 6; ++a) bits |= reinterpret_cast<uintptr_t>(rec.g[a]);
-    const bool vec = (bits & 15u) == 0;
     const ChunkSplit sp = chunk_split(n, sm_count);
     // without the tiled path's buffers every record takes the global path
     const bool tiled = tp.ntiles > 0 && block_count && block_pairs && stage;
     TilePlan tpl = tp;
     if (!tiled) tpl.ntiles = 0;
     const size_t smem = sizeof(uint32_t) * 2 * static_cast<size_t>(tpl.ntiles);
-    uint32_t *bc = tiled ? block_count : nullptr;
-    uint32_t *bp = tiled ? block_pairs : nullptr;
-    uint32_t *sg = tiled ? stage : nullptr;
-    if (vec)
-        ingest_kernel<true><<<static_cast<unsigned>(sp.blocks), kIngestThreads, smem, s>>>(
-            in, n, sp.per_block, g, cordic, tau_l, tau_h, use_miss, use_hit, tpl, rec, ctrl, bc, bp, sg);
-    else
-        ingest_kernel<false><<<static_cast<unsigned>(sp.blocks), kIngestThreads, smem, s>>>(
-            in, n, sp.per_block, g, cordic, tau_l, tau_h, use_miss, use_hit, tpl, rec, ctrl, bc, bp, sg);
+    ingest_kernel<<<static_cast<unsigned>(sp.blocks), kIngestThreads, smem, s>>>(
+        in, n, sp.per_block, g, cordic, tau_l, tau_h, use_miss, use_hit, tpl, rec, ctrl,
+        tiled ? block_count : nullptr, tiled ? block_pairs : nullptr, tiled ? stage : nullptr);
     return cudaGetLastError();
 }
 
