@@ -138,6 +138,7 @@ struct hd_scan {
     int32_t thick_k = 0;             // thick rays: in-plane dilation (0 = thin paths)
     float euclid_d0 = 0.0f;          // thick rays by Euclidean distance, mm (0 = off)
     void *thick_ws = nullptr;        // their difference arrays
+    bool inputs_on_host = false;  // the chunk being added is read in place from host memory
     float *staging = nullptr;  // copied host inputs: 6 columns of staging_half floats
     int64_t staging_half = 0;
     uint32_t *compact_blocks = nullptr;
@@ -452,7 +453,7 @@ hd_status stage_prepare(hd_scan *s, const hd::Inputs &in, int64_t n, cudaStream_
     HD_CUDA(hd::launch_ingest(in, n, s->gq, s->cordic, s->params.wepl_miss_lt,
                               s->params.wepl_hit_gt, use_miss, use_hit, tp, rec, s->ctrl,
                               tp.ntiles > 0 ? block_count : nullptr, block_pairs, pairs.stage,
-                              s->sm_count, st));
+                              s->inputs_on_host ? 1 : 0, s->sm_count, st));
     s->launches += 1;
     if (tp.ntiles > 0) {
         HD_CUDA(hd::launch_plan(tp, n, block_count, s->tile_count, s->tile_cursor, s->jobs, s->ctrl,
@@ -742,13 +743,15 @@ hd_status hd_scan_add_histories(hd_scan *scan, const float *angle_deg, const flo
         const int64_t chunk = n < kChunk ? n : kChunk;
         hd_status r = ensure_records(scan, chunk, st);
         if (r != HD_OK) return r;
-        for (int64_t off = 0; off < n; off += chunk) {
+        scan->inputs_on_host = true;
+        for (int64_t off = 0; off < n && r == HD_OK; off += chunk) {
             const int64_t c = (n - off) < chunk ? (n - off) : chunk;
             const hd::Inputs in{src[0] + off, src[1] + off, src[2] + off,
                                 src[3] + off, src[4] + off, src[5] + off};
             r = run_chunk(scan, in, c, st);
-            if (r != HD_OK) return r;
         }
+        scan->inputs_on_host = false;
+        if (r != HD_OK) return r;
     } else {
         // other host memory: copied to the scan's staging buffer, one chunk
         // at a time, on st

@@ -149,11 +149,12 @@ struct Inputs {
 // at [c * blocks + b]; block_pairs[b] the block's pairs in all, listed in
 // stage (Pairs::stage).  Each block keeps to a pair budget of
 // tp.pairs_per_record per history; its records beyond it take the global
-// path.
+// path.  on_host: the inputs are page-locked host memory read in place.
 cudaError_t launch_ingest(const Inputs &in, int64_t n, const GeomQ &g, const Cordic &cordic,
                           float tau_l, float tau_h, int use_miss, int use_hit, const TilePlan &tp,
                           const Records &rec, Ctrl *ctrl, uint32_t *block_count,
-                          uint32_t *block_pairs, uint32_t *stage, int sm_count, cudaStream_t s);
+                          uint32_t *block_pairs, uint32_t *stage, int on_host, int sm_count,
+                          cudaStream_t s);
 
 // Per column: the exclusive prefix over blocks of block_count (in place) and
 // the column total into tile_count; then the plan (tile offsets into

@@ -143,7 +143,7 @@ extern "C" hd_status hd_accumulate_noalloc(const hd_geometry *geom, const hd_par
     cudaError_t e = cudaMemsetAsync(ctrl, 0, sizeof(hd::Ctrl), s);
     if (e == cudaSuccess)
         e = hd::launch_ingest(in, n, gq, cordic, params->wepl_miss_lt, params->wepl_hit_gt,
-                              use_miss, use_hit, tp, rec, ctrl, nullptr, nullptr, nullptr,
+                              use_miss, use_hit, tp, rec, ctrl, nullptr, nullptr, nullptr, 0,
                               sm_count, s);
     if (e == cudaSuccess)
         e = hd::launch_trace_global(rec, ctrl, n, gq, use_miss ? N : nullptr,

@@ -157,10 +157,14 @@ __device__ __forceinline__ void admit_and_write(const TilePlan &tp, const Record
     rec.status[i] = st;
 }
 
-// One block per range of the chunk split, one history per thread and step
-// (coalesced 32-bit loads of each array).  One history per step keeps a
-// single inlined copy of the per-history code: four per step, with 128-bit
-// loads, ran slower for the instruction-cache misses and register spills.
+// One block per range of the chunk split.  Inputs in device memory: one
+// history per thread and step (coalesced 32-bit loads of each array), which
+// keeps a single inlined copy of the per-history code (four per step ran
+// slower from HBM, for the instruction-cache misses and register spills).
+// kWide, for inputs read in place from page-locked host memory: four
+// consecutive histories per thread and step from 128-bit loads, since the
+// host link serves fewer, larger requests faster.
+template <bool kWide>
 __global__ void __launch_bounds__(kIngestThreads, 4) ingest_kernel(
     Inputs in, int64_t n, int64_t per_block, GeomQ g, Cordic cd, float tau_l, float tau_h,
     int use_miss, int use_hit, TilePlan tp, Records rec, Ctrl *ctrl, uint32_t *block_count,
@@ -186,14 +190,57 @@ __global__ void __launch_bounds__(kIngestThreads, 4) ingest_kernel(
         h1 > h0 ? static_cast<unsigned>(h1 - h0) * static_cast<unsigned>(tp.pairs_per_record) : 0u;
     uint32_t *const list =
         stage ? stage + static_cast<int64_t>(blockIdx.x) * per_block * tp.pairs_per_record : nullptr;
-    for (int64_t base = h0; base < h1; base += blockDim.x) {
-        const int64_t i = base + threadIdx.x;
-        int cls = 0;
-        int32_t r[6] = {0, 0, 0, 0, 0, 0};
-        if (i < h1)
-            cls = ingest_one(g, cd, tau_l, tau_h, use_miss, use_hit, in.angle[i], in.u_in[i],
-                             in.v_in[i], in.u_out[i], in.v_out[i], in.wepl[i], r, acc, tc);
-        admit_and_write(tp, rec, s_hist, &s_demand, budget, h0, i, h1, list, cls, r);
+    if (kWide) {
+        for (int64_t base = h0; base < h1; base += 4 * static_cast<int64_t>(blockDim.x)) {
+            const int64_t i0 = base + 4 * static_cast<int64_t>(threadIdx.x);
+            float a[4] = {0, 0, 0, 0}, ui[4] = {0, 0, 0, 0}, vi[4] = {0, 0, 0, 0},
+                  uo[4] = {0, 0, 0, 0}, vo[4] = {0, 0, 0, 0}, w[4] = {0, 0, 0, 0};
+            if (i0 + 3 < h1) {
+                const int64_t u = i0 >> 2;
+                const float4 A = __ldg(reinterpret_cast<const float4 *>(in.angle) + u);
+                const float4 UI = __ldg(reinterpret_cast<const float4 *>(in.u_in) + u);
+                const float4 VI = __ldg(reinterpret_cast<const float4 *>(in.v_in) + u);
+                const float4 UO = __ldg(reinterpret_cast<const float4 *>(in.u_out) + u);
+                const float4 VO = __ldg(reinterpret_cast<const float4 *>(in.v_out) + u);
+                const float4 W = __ldg(reinterpret_cast<const float4 *>(in.wepl) + u);
+                a[0] = A.x; a[1] = A.y; a[2] = A.z; a[3] = A.w;
+                ui[0] = UI.x; ui[1] = UI.y; ui[2] = UI.z; ui[3] = UI.w;
+                vi[0] = VI.x; vi[1] = VI.y; vi[2] = VI.z; vi[3] = VI.w;
+                uo[0] = UO.x; uo[1] = UO.y; uo[2] = UO.z; uo[3] = UO.w;
+                vo[0] = VO.x; vo[1] = VO.y; vo[2] = VO.z; vo[3] = VO.w;
+                w[0] = W.x; w[1] = W.y; w[2] = W.z; w[3] = W.w;
+            } else {
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const int64_t i = i0 + k;
+                    if (i < h1) {
+                        a[k] = in.angle[i]; ui[k] = in.u_in[i]; vi[k] = in.v_in[i];
+                        uo[k] = in.u_out[i]; vo[k] = in.v_out[i]; w[k] = in.wepl[i];
+                    }
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const int64_t i = i0 + k;
+                int cls = 0;
+                int32_t r[6] = {0, 0, 0, 0, 0, 0};
+                if (i < h1)
+                    cls = ingest_one(g, cd, tau_l, tau_h, use_miss, use_hit, a[k], ui[k], vi[k],
+                                     uo[k], vo[k], w[k], r, acc, tc);
+                admit_and_write(tp, rec, s_hist, &s_demand, budget, h0, i, h1, list, cls, r);
+            }
+        }
+    } else {
+        for (int64_t base = h0; base < h1; base += blockDim.x) {
+            const int64_t i = base + threadIdx.x;
+            int cls = 0;
+            int32_t r[6] = {0, 0, 0, 0, 0, 0};
+            if (i < h1)
+                cls = ingest_one(g, cd, tau_l, tau_h, use_miss, use_hit, in.angle[i],
+                                 in.u_in[i], in.v_in[i], in.u_out[i], in.v_out[i], in.wepl[i], r,
+                                 acc, tc);
+            admit_and_write(tp, rec, s_hist, &s_demand, budget, h0, i, h1, list, cls, r);
+        }
     }
     const unsigned a0 = warp_sum_u32(acc.n_in), a1 = warp_sum_u32(acc.n_miss),
                    a2 = warp_sum_u32(acc.n_hit), a3 = warp_sum_u32(acc.n_none),
@@ -258,7 +305,8 @@ __global__ void classify_kernel(const float *__restrict__ w, int64_t n, float ta
 cudaError_t launch_ingest(const Inputs &in, int64_t n, const GeomQ &g, const Cordic &cordic,
                           float tau_l, float tau_h, int use_miss, int use_hit, const TilePlan &tp,
                           const Records &rec, Ctrl *ctrl, uint32_t *block_count,
-                          uint32_t *block_pairs, uint32_t *stage, int sm_count, cudaStream_t s)
+                          uint32_t *block_pairs, uint32_t *stage, int on_host, int sm_count,
+                          cudaStream_t s)
 {
     if (n <= 0) return cudaSuccess;
     const ChunkSplit sp = chunk_split(n, sm_count);
@@ -267,9 +315,21 @@ cudaError_t launch_ingest(const Inputs &in, int64_t n, const GeomQ &g, const Cor
     TilePlan tpl = tp;
     if (!tiled) tpl.ntiles = 0;
     const size_t smem = sizeof(uint32_t) * 2 * static_cast<size_t>(tpl.ntiles);
-    ingest_kernel<<<static_cast<unsigned>(sp.blocks), kIngestThreads, smem, s>>>(
-        in, n, sp.per_block, g, cordic, tau_l, tau_h, use_miss, use_hit, tpl, rec, ctrl,
-        tiled ? block_count : nullptr, tiled ? block_pairs : nullptr, tiled ? stage : nullptr);
+    uint32_t *bc = tiled ? block_count : nullptr;
+    uint32_t *bp = tiled ? block_pairs : nullptr;
+    uint32_t *sg = tiled ? stage : nullptr;
+    const uintptr_t bits =
+        reinterpret_cast<uintptr_t>(in.angle) | reinterpret_cast<uintptr_t>(in.u_in) |
+        reinterpret_cast<uintptr_t>(in.v_in) | reinterpret_cast<uintptr_t>(in.u_out) |
+        reinterpret_cast<uintptr_t>(in.v_out) | reinterpret_cast<uintptr_t>(in.wepl);
+    if (on_host && (bits & 15u) == 0)
+        ingest_kernel<true><<<static_cast<unsigned>(sp.blocks), kIngestThreads, smem, s>>>(
+            in, n, sp.per_block, g, cordic, tau_l, tau_h, use_miss, use_hit, tpl, rec, ctrl, bc,
+            bp, sg);
+    else
+        ingest_kernel<false><<<static_cast<unsigned>(sp.blocks), kIngestThreads, smem, s>>>(
+            in, n, sp.per_block, g, cordic, tau_l, tau_h, use_miss, use_hit, tpl, rec, ctrl, bc,
+            bp, sg);
     return cudaGetLastError();
 }
 
