@@ -120,7 +120,7 @@ struct hd_scan {
     hd::TilePlan tp{};
     hd_tuning tuning{1024, 12, 32767, 0};
     int trace_grid = 0;
-    int32_t *rec_buf = nullptr;   // 7 int32 arrays of rec_cap (6 coordinates + status)
+    int32_t *rec_buf = nullptr;   // 8 int32 arrays of rec_cap (coordinates, status, global list)
     int64_t rec_cap = 0;
     uint32_t *pair_buf = nullptr;  // lean walks (kLeanWords per pair), then the fallback list
     hd::TileJob *jobs = nullptr;
@@ -254,7 +254,7 @@ hd_status ensure_records(hd_scan *s, int64_t n, cudaStream_t st)
     s->pair_buf = nullptr;
     s->jobs = nullptr;
     s->rec_cap = 0;
-    bool ok = cudaMalloc(&s->rec_buf, sizeof(int32_t) * 7 *
+    bool ok = cudaMalloc(&s->rec_buf, sizeof(int32_t) * 8 *
                                           static_cast<size_t>(hd::records_stride(n))) == cudaSuccess;
     if (ok && s->tp.ntiles > 0) {
         const int64_t pair_cap = pairs_per_record(s->tp) * n;
@@ -318,14 +318,15 @@ bool all_mapped_host(const float *const src[6], int device)
     return true;
 }
 
-// The records of a chunk of n histories: seven arrays of n slots, each
-// starting on a 16-byte boundary.
+// The records of a chunk of n histories: seven arrays of n slots and the
+// global path's list, each starting on a 16-byte boundary.
 hd::Records records_of(const hd_scan *s, int64_t n)
 {
     hd::Records r;
     const size_t stride = static_cast<size_t>(hd::records_stride(n));
     for (int a = 0; a < 6; ++a) r.g[a] = s->rec_buf + a * stride;
     r.status = s->rec_buf + 6 * stride;
+    r.glist = s->rec_buf + 7 * stride;
     r.cap = n;
     return r;
 }

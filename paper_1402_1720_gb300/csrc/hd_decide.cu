@@ -56,9 +56,17 @@ __global__ void __launch_bounds__(256) sm_slope_kernel(const uint32_t *__restric
         have = true;
     }
     // a lane without a voxel contributes 0, the value the keys start from,
-    // so it changes no maximum
+    // so it changes no maximum; the block's maximum goes out in one atomic
+    // (one per warp made the same-address atomics of a slice the bottleneck)
+    __shared__ unsigned long long s_max[8];
     key = warp_max_u64(have ? key : 0ull);
-    if ((threadIdx.x & 31u) == 0 && key != 0) atomicMax(&slice_key[per_slice ? z : 0], key);
+    if ((threadIdx.x & 31u) == 0) s_max[threadIdx.x >> 5] = key;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        key = threadIdx.x < (blockDim.x >> 5) ? s_max[threadIdx.x] : 0ull;
+        key = warp_max_u64(key);
+        if (threadIdx.x == 0 && key != 0) atomicMax(&slice_key[per_slice ? z : 0], key);
+    }
 }
 
 __global__ void sm_threshold_kernel(const uint32_t *__restrict__ M, int nx, int ny, int nz,

@@ -38,6 +38,7 @@ struct Ctrl {
     unsigned long long pairs_general;  // pairs sent to the fallback list (cumulative)
     unsigned long long runs;           // runs walked by the tiled pass (cumulative)
     int njobs;                // jobs of the tiled traversal
+    unsigned int n_global;    // records listed for the global path (Records::glist)
     int job_next;             // next job to hand out
     unsigned int n_fallback;  // records traversed by the global-memory path
     unsigned int n_pair_fallback;  // entries of the pair fallback list
@@ -53,7 +54,9 @@ struct Ctrl {
 struct Records {
     int32_t *g[6];  // x0, y0, z0, x1, y1, z1
     int32_t *status;
-    int64_t cap;    // slots (the chunk's histories)
+    int32_t *glist;  // slots of the global-path records, Ctrl::n_global of them
+                     // (null: that path finds them by their status words)
+    int64_t cap;     // slots (the chunk's histories)
 };
 
 inline int64_t records_stride(int64_t n) { return (n + 3) & ~int64_t(3); }

@@ -136,6 +136,7 @@ extern "C" hd_status hd_accumulate_noalloc(const hd_geometry *geom, const hd_par
     const size_t stride = static_cast<size_t>(hd::records_stride(n));
     for (int a = 0; a < 6; ++a) rec.g[a] = rec_base + a * stride;
     rec.status = rec_base + 6 * stride;
+    rec.glist = nullptr;  // the global pass finds its records by their status words
     rec.cap = n;
 
     cudaStream_t s = static_cast<cudaStream_t>(stream);

@@ -212,10 +212,12 @@ __global__ void __launch_bounds__(kThickThreads) thick_records_kernel(Records re
                                                                       ThickDiff td)
 {
     const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+    const int64_t total = rec.glist ? static_cast<int64_t>(ctrl->n_global) : rec.cap;
     ThickRing rg;
     unsigned vox[2] = {0, 0};
-    for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < rec.cap;
-         i += stride) {
+    for (int64_t k = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; k < total;
+         k += stride) {
+        const int64_t i = rec.glist ? static_cast<int64_t>(rec.glist[k]) : k;
         const int32_t stw = rec.status[i];
         if (status_path(stw) != 2) continue;
         const int32_t gi[3] = {rec.g[0][i], rec.g[1][i], rec.g[2][i]};
@@ -227,7 +229,6 @@ __global__ void __launch_bounds__(kThickThreads) thick_records_kernel(Records re
         thick_walk_all(wk, ymaj ? g.nx : g.ny, ymaj ? g.ny : g.nx, 0, k, (wk.flags & 2) ? 1 : -1,
                        ymaj ? td.dy[cls] : td.dx[cls], rg, vox[cls]);
     }
-    (void)ctrl;  // voxel memberships are read from the counts (sum of N, M)
 }
 
 __global__ void __launch_bounds__(kThickThreads) thick_rows_kernel(

@@ -110,7 +110,7 @@ __device__ __forceinline__ unsigned warp_incl_scan(unsigned v)
 // record that straddles the budget, and the records after it, are turned
 // away (they take the global path, exact either way).
 __device__ __forceinline__ void admit_and_write(const TilePlan &tp, const Records &rec,
-                                                uint32_t *s_hist, unsigned *s_demand,
+                                                Ctrl *ctrl, uint32_t *s_hist, unsigned *s_demand,
                                                 unsigned budget, int64_t h0, int64_t i,
                                                 int64_t i1, uint32_t *stage, int cls,
                                                 const int32_t r[6])
@@ -132,10 +132,21 @@ __device__ __forceinline__ void admit_and_write(const TilePlan &tp, const Record
     if (lane == 31 && tot) wbase = atomicAdd(s_demand, tot);
     wbase = __shfl_sync(0xffffffffu, wbase, 31);
     const unsigned long long end = static_cast<unsigned long long>(wbase) + incl;
+    const int path = ok ? (demand > 0 && end <= budget ? 1 : 2) : 0;
+    if (rec.glist) {
+        // the global path's list: one counter update per warp
+        const unsigned gm = __ballot_sync(0xffffffffu, path == 2);
+        if (gm) {
+            const int lead = __ffs(gm) - 1;
+            unsigned gb = 0;
+            if (static_cast<int>(lane) == lead) gb = atomicAdd(&ctrl->n_global, __popc(gm));
+            gb = __shfl_sync(0xffffffffu, gb, lead);
+            if (path == 2) rec.glist[gb + __popc(gm & ((1u << lane) - 1u))] = static_cast<int32_t>(i);
+        }
+    }
     if (i >= i1) return;
     int32_t st = 0;
     if (ok) {
-        const int path = demand > 0 && end <= budget ? 1 : 2;
         st = record_status(path, cls - 1, zlo, zhi);
         if (path == 1) {
             int lo[3], hi[3];
@@ -227,7 +238,7 @@ __global__ void __launch_bounds__(kIngestThreads, 4) ingest_kernel(
                 if (i < h1)
                     cls = ingest_one(g, cd, tau_l, tau_h, use_miss, use_hit, a[k], ui[k], vi[k],
                                      uo[k], vo[k], w[k], r, acc, tc);
-                admit_and_write(tp, rec, s_hist, &s_demand, budget, h0, i, h1, list, cls, r);
+                admit_and_write(tp, rec, ctrl, s_hist, &s_demand, budget, h0, i, h1, list, cls, r);
             }
         }
     } else {
@@ -239,7 +250,7 @@ __global__ void __launch_bounds__(kIngestThreads, 4) ingest_kernel(
                 cls = ingest_one(g, cd, tau_l, tau_h, use_miss, use_hit, in.angle[i],
                                  in.u_in[i], in.v_in[i], in.u_out[i], in.v_out[i], in.wepl[i], r,
                                  acc, tc);
-            admit_and_write(tp, rec, s_hist, &s_demand, budget, h0, i, h1, list, cls, r);
+            admit_and_write(tp, rec, ctrl, s_hist, &s_demand, budget, h0, i, h1, list, cls, r);
         }
     }
     const unsigned a0 = warp_sum_u32(acc.n_in), a1 = warp_sum_u32(acc.n_miss),
@@ -272,9 +283,11 @@ __global__ void __launch_bounds__(256) trace_global_kernel(Records rec, Ctrl *ct
                                                            int all_records)
 {
     const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+    const int64_t total = rec.glist ? static_cast<int64_t>(ctrl->n_global) : rec.cap;
     unsigned taken = 0;
-    for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < rec.cap;
-         i += stride) {
+    for (int64_t k = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; k < total;
+         k += stride) {
+        const int64_t i = rec.glist ? static_cast<int64_t>(rec.glist[k]) : k;
         const int32_t stw = rec.status[i];
         const int path = status_path(stw);
         if (all_records ? path == 0 : path != 2) continue;
