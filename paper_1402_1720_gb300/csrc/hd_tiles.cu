@@ -180,12 +180,16 @@ __global__ void __launch_bounds__(kScatterThreads, 4) scatter_kernel(
         int32_t q[6];
 #pragma unroll
         for (int a = 0; a < 6; ++a) q[a] = rec.g[a][slot];
-        int lo[3], hi[3];
-        tile_range_z(tp, q, status_zlo(stw), status_zhi(stw), lo, hi);
-        // the j-th tile of the record's box, x fastest
-        const int ex = hi[0] - lo[0] + 1, ey = hi[1] - lo[1] + 1;
-        int x = lo[0], y = lo[1], z = lo[2] + j;
-        if (ex != 1 || ey != 1) {
+        // the j-th tile of the record's box, x fastest; with whole-plane
+        // tiles the box is the record's slices alone (in its status word)
+        int x = 0, y = 0, z;
+        if (tp.ntx == 1 && tp.nty == 1) {
+            const unsigned zl = static_cast<unsigned>(status_zlo(stw));
+            z = (tp.mtz ? static_cast<int>(umulhi32(zl, tp.mtz)) : static_cast<int>(zl)) + j;
+        } else {
+            int lo[3], hi[3];
+            tile_range_z(tp, q, status_zlo(stw), status_zhi(stw), lo, hi);
+            const int ex = hi[0] - lo[0] + 1, ey = hi[1] - lo[1] + 1;
             x = lo[0] + j % ex;
             y = lo[1] + (j / ex) % ey;
             z = lo[2] + j / (ex * ey);
