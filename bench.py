@@ -15,6 +15,16 @@ Under torchrun (N > 1) every rank runs its own scan (independent problems,
 no collective on the data path); the step time is the maximum over ranks.
 `--impl reference` times the CPU oracle (the plain C statement of the
 method) on a bounded sample of the same workload.
+
+The default line also carries the traversal kernel's roofline (voxel-steps
+per second against the random-address shared-memory atomic rate measured
+by hd_probe_atomics in the same run), the oracle on the host cores, and two
+sections on the 48-scan mix (48 scans of {64x64x16, 128x128x32, 256x256x64}
+voxels, log-uniform 2e5-2e7 histories each): batched in one persistent
+launch against one scan at a time, and served as per-angle chunks with
+Poisson arrivals (time-to-hull percentiles).  Other workloads:
+--workload batched-48 | serving | rows | binned | diagnostics | thick |
+euclid | configs.
 """
 from __future__ import annotations
 
@@ -966,6 +976,90 @@ def run_diagnostics(args):
     scan.close()
 
 
+def run_configs(args):
+    """Per-configuration figures beside the head-sized benchmark: the tiny
+    scan (64x64x8 voxels, 1.8e5 histories) and the large streamed scan
+    (400x400x128 voxels, 9.9e7 histories added in 180 per-angle chunks from
+    device memory) timed on the GPU, and the oracle as it stands, on one
+    host thread and on all of them, on bounded samples of the tiny, the
+    head-sized and the large scan."""
+    import multiprocessing as mp
+    import numpy as _np
+    # the large scan's chunks are generated by a spawn pool started before
+    # any CUDA call, and collected before the first timed region
+    pool = mp.get_context("spawn").Pool(min(16, os.cpu_count() or 1))
+    from paper_1402_1720_gb300 import synth
+    chunks_job = pool.map_async(synth.config3_chunk, range(180))
+    import torch
+    import oracle
+    from paper_1402_1720_gb300 import build as hbuild
+    from paper_1402_1720_gb300 import hulld
+    _, _, local = _dist()
+    torch.cuda.set_device(local)
+    hbuild.build()
+    hulld.load()
+    oracle.build()
+    cores = os.cpu_count() or 1
+    chunks = chunks_job.get()
+    pool.close()
+    pool.join()
+
+    def gpu_ms(g, parts, steps, warmup):
+        devs = [[torch.from_numpy(a).cuda() for a in p.arrays()] for p in parts]
+        stream = torch.cuda.current_stream()
+        with hulld.Scan(g) as s:
+            def step():
+                s.reset()
+                for d in devs:
+                    s.add(d)
+                s.finalize()
+            for _ in range(warmup):
+                step()
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(steps):
+                step()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            st = s.stats()
+        return e0.elapsed_time(e1) / steps, st
+
+    def oracle_rate(g, h, every, threads):
+        sub = h.take(_np.arange(0, len(h), every))
+        t0 = time.perf_counter()
+        oracle.run(g, sub, threads=threads)
+        dt = time.perf_counter() - t0
+        return {"histories_per_s": len(sub) / dt, "threads": threads,
+                "sample": f"{len(sub)} histories (every {every}th), {dt:.1f} s wall"}
+
+    out = {}
+    w1 = synth.make_config(1)
+    ms1, st1 = gpu_ms(w1.geometry, [w1.histories], args.steps, args.warmup)
+    out["tiny 64x64x8, 1.8e5 histories"] = {
+        "gpu_ms_per_scan": ms1, "gpu_histories_per_s": len(w1.histories) / (ms1 * 1e-3),
+        "oracle_1_thread": oracle_rate(w1.geometry, w1.histories, 4, 1),
+        "oracle_all_threads": oracle_rate(w1.geometry, w1.histories, 1, cores)}
+    w2 = synth.make_config(2)
+    out["head 200x200x32, 9e6 histories"] = {
+        "oracle_1_thread": oracle_rate(w2.geometry, w2.histories, 400, 1),
+        "oracle_all_threads": oracle_rate(w2.geometry, w2.histories, 25, cores)}
+    g3 = synth.geometry_for(3)
+    ms3, st3 = gpu_ms(g3, chunks, 3, 1)
+    n3 = sum(len(c) for c in chunks)
+    big = synth.Histories.concat(chunks[::45])
+    out["large 400x400x128, 9.9e7 histories in 180 chunks"] = {
+        "gpu_ms_per_scan": ms3, "gpu_histories_per_s": n3 / (ms3 * 1e-3),
+        "gpu_voxel_steps_per_s": (st3["steps_miss"] + st3["steps_hit"]) / (ms3 * 1e-3),
+        "oracle_1_thread": oracle_rate(g3, big, 200, 1),
+        "oracle_all_threads": oracle_rate(g3, big, 10, cores)}
+    line = {"metric": "per-configuration throughput (GPU and the oracle as it stands)",
+            "unit": UNIT, "host_cores": cores, "configs": out,
+            "data": "synthetic", "steps": args.steps, "warmup": args.warmup}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -979,7 +1073,7 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--workload", default="head-200",
                     choices=["head-200", "batched-48", "serving", "rows", "binned",
-                             "diagnostics", "thick", "euclid"])
+                             "diagnostics", "thick", "euclid", "configs"])
     ap.add_argument("--batch-fraction", type=float, default=1.0)
     ap.add_argument("--fraction", type=float, default=1.0,
                     help="head-200 workload: keep this fraction of the histories "
@@ -998,6 +1092,9 @@ def main():
                     help="head-200 workload: timed batched steps of the 48-scan section")
     args = ap.parse_args()
 
+    if args.workload == "configs":
+        run_configs(args)
+        return
     if args.workload == "batched-48":
         run_batched(args)
         return
