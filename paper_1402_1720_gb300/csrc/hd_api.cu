@@ -50,6 +50,8 @@ struct DeviceGuard {
 };
 
 constexpr int64_t kChunk = int64_t(1) << 25;  // histories per internal launch sequence
+// a block's slot offsets (below the chunk size) fit a pair-list entry
+static_assert(kChunk <= (int64_t(1) << (32 - hd::kRecordTileBits)), "pair-list entry width");
 constexpr int64_t kMaxScanHistories = 4294967295LL;
 
 // theta_i = round(atan(2^-i) * 180/pi * 2^30), K = round(2^30 prod (1 + 2^-2i)^-1/2),

@@ -113,12 +113,16 @@ struct Pairs {
     uint2 *fb;  // fallback list: (pair position, 0), pair_cap entries
     // Each ingest block's pairs in the order its budget assigned them, from
     // the block's share (block * per_block * pairs_per_record) on: the
-    // record's slot less the block's first slot, times 8, plus the pair's
-    // tile index within the record (below kMaxRecordTiles).
+    // record's slot less the block's first slot, times kMaxRecordTiles,
+    // plus the pair's tile index within the record.
     uint32_t *stage;
 };
 
-constexpr int kMaxRecordTiles = 8;  // tiles a record may touch on the tiled path
+// Tiles a record may touch on the tiled path (its box of tiles; more take
+// the global path), and the bits of a tile index within a record.
+constexpr int kMaxRecordTiles = 32;
+constexpr int kRecordTileBits = 5;
+static_assert(kMaxRecordTiles == 1 << kRecordTileBits, "tile index bits");
 
 struct TileJob {
     int tile;   // tile id within its class

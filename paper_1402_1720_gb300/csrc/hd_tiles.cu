@@ -173,8 +173,8 @@ __global__ void __launch_bounds__(kScatterThreads, 4) scatter_kernel(
     const uint32_t *list = pairs.stage + static_cast<int64_t>(blockIdx.x) * per_block * tp.pairs_per_record;
     for (unsigned e = threadIdx.x; e < npairs; e += kScatterThreads) {
         const uint32_t code = list[e];
-        const int64_t slot = h0 + (code >> 3);
-        const int j = static_cast<int>(code & 7u);
+        const int64_t slot = h0 + (code >> kRecordTileBits);
+        const int j = static_cast<int>(code & (kMaxRecordTiles - 1u));
         const int32_t stw = rec.status[slot];
         const int cls = status_cls(stw);
         int32_t q[6];

@@ -158,7 +158,7 @@ __device__ __forceinline__ void admit_and_write(const TilePlan &tp, const Record
                         atomicAdd(&s_hist[off + x + tp.ntx * (y + tp.nty * z)], 1u);
             // the record's pairs hold positions end - c .. end - 1 of the
             // block's list (all below its budget)
-            const uint32_t code = static_cast<uint32_t>(i - h0) << 3;
+            const uint32_t code = static_cast<uint32_t>(i - h0) << kRecordTileBits;
             const unsigned first = static_cast<unsigned>(end) - demand;
             for (int j = 0; j < tcount; ++j) stage[first + j] = code | static_cast<uint32_t>(j);
         }
