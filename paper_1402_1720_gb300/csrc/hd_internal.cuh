@@ -142,7 +142,7 @@ struct ScanDesc {
 };
 
 constexpr int kMaxBatch = 64;  // scans per batched traversal launch
-constexpr int kMinJob = 2048;  // smallest job the plan makes (pairs), unless the tuning is lower
+constexpr int kMinJob = 8192;  // smallest job the plan makes (pairs), unless the tuning is lower
 
 struct Inputs {
     const float *angle, *u_in, *v_in, *u_out, *v_out, *wepl;

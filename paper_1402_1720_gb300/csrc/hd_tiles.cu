@@ -80,8 +80,9 @@ __global__ void __launch_bounds__(256) bases_kernel(int ncols, int nblocks, uint
 // One block: tile offsets (exclusive scan of the counts), cursors for the
 // scatter, and the job table (chunks of one tile's pairs).  The job size
 // adapts to the amount of work: at most tp.job_size pairs, and small enough
-// that there are about two jobs per SM (not below kMinJob, so a job's flush
-// stays small against its walks).
+// that there are about three jobs per SM (not below kMinJob, so a job's
+// flush stays small against its walks; two or four per SM, or a smaller
+// floor, measured slower).
 __global__ void __launch_bounds__(1024) plan_kernel(TilePlan tp, const uint32_t *tile_count,
                                                     uint32_t *tile_cursor, TileJob *jobs,
                                                     Ctrl *ctrl, int sm_count)
@@ -96,7 +97,7 @@ __global__ void __launch_bounds__(1024) plan_kernel(TilePlan tp, const uint32_t 
     unsigned tot_pairs;
     unsigned off = block_excl_scan(my_pairs, s_warp, tot_pairs);
     if (threadIdx.x == 0) {
-        const unsigned want = (tot_pairs + 2u * sm_count - 1u) / (2u * sm_count);
+        const unsigned want = (tot_pairs + 3u * sm_count - 1u) / (3u * sm_count);
         unsigned js = want < static_cast<unsigned>(tp.job_size) ? want : tp.job_size;
         if (js < static_cast<unsigned>(kMinJob)) js = kMinJob;
         if (js > static_cast<unsigned>(tp.job_size)) js = tp.job_size;
