@@ -119,8 +119,20 @@ __device__ __forceinline__ void admit_and_write(const TilePlan &tp, const Record
     int zlo = 0, zhi = 0;
     bool ok = false;
     if (cls != 0) {
-        int lo[3], hi[3];
-        const int c = grid_z_range(tp, r, zlo, zhi) ? tile_range_z(tp, r, zlo, zhi, lo, hi) : 0;
+        int c = 0;
+        if (grid_z_range(tp, r, zlo, zhi)) {
+            if (tp.ntx == 1 && tp.nty == 1) {
+                // whole-plane tiles: the part inside the grid's x-y extent
+                // meets every plane tile of its slices
+                const unsigned m = tp.mtz;
+                const int t0 = m ? static_cast<int>(umulhi32(static_cast<unsigned>(zlo), m)) : zlo;
+                const int t1 = m ? static_cast<int>(umulhi32(static_cast<unsigned>(zhi), m)) : zhi;
+                c = t1 - t0 + 1;
+            } else {
+                int lo[3], hi[3];
+                c = tile_range_z(tp, r, zlo, zhi, lo, hi);
+            }
+        }
         ok = c != 0;  // else no voxel of the grid: nothing to traverse
         tcount = (tp.ntiles > 0 && c <= tp.max_tiles) ? c : -1;
     }
@@ -150,7 +162,14 @@ __device__ __forceinline__ void admit_and_write(const TilePlan &tp, const Record
         st = record_status(path, cls - 1, zlo, zhi);
         if (path == 1) {
             int lo[3], hi[3];
-            tile_range_z(tp, r, zlo, zhi, lo, hi);
+            if (tp.ntx == 1 && tp.nty == 1) {
+                const unsigned m = tp.mtz;
+                lo[0] = hi[0] = lo[1] = hi[1] = 0;
+                lo[2] = m ? static_cast<int>(umulhi32(static_cast<unsigned>(zlo), m)) : zlo;
+                hi[2] = m ? static_cast<int>(umulhi32(static_cast<unsigned>(zhi), m)) : zhi;
+            } else {
+                tile_range_z(tp, r, zlo, zhi, lo, hi);
+            }
             const int off = (cls - 1) * tp.ntiles;
             for (int z = lo[2]; z <= hi[2]; ++z)
                 for (int y = lo[1]; y <= hi[1]; ++y)
