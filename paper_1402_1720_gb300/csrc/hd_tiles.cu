@@ -409,19 +409,20 @@ __device__ __forceinline__ void flush_tile(uint32_t *tile, int dx, int dy, int d
         }
     }
     __syncthreads();
-    // (3) add to the volume and clear every word of the box
-    const int words = Wx * Hy * dz;
-    for (int wd = threadIdx.x; wd < words; wd += blockDim.x) {
-        const int x = wd % Wx, t = wd / Wx;
-        const int y = t % Hy, z = t / Hy;
-        const uint32_t w = tile[wd];
-        tile[wd] = 0u;
-        if (x < dx && y < dy) {
-            const int v = static_cast<int>(w & 0xffffu) + static_cast<int>(w >> 16);
-            if (v) {
-                const long long g = (x0 + x) + static_cast<long long>(nx) *
-                                                   ((y0 + y) + static_cast<long long>(ny) * (z0 + z));
-                atomicAdd(&vol[g], static_cast<uint32_t>(v));
+    // (3) add to the volume and clear every word of the box, a warp per row
+    // of words (padding row included), its lanes along x
+    for (int r = warp; r < Hy * dz; r += nwarps) {
+        const int y = r % Hy, z = r / Hy;
+        uint32_t *row = tile + Wx * r;
+        const bool real = y < dy;
+        const long long g0 =
+            x0 + static_cast<long long>(nx) * ((y0 + y) + static_cast<long long>(ny) * (z0 + z));
+        for (int x = static_cast<int>(lane); x < Wx; x += 32) {
+            const uint32_t w = row[x];
+            row[x] = 0u;
+            if (real && x < dx) {
+                const int v = static_cast<int>(w & 0xffffu) + static_cast<int>(w >> 16);
+                if (v) atomicAdd(&vol[g0 + x], static_cast<uint32_t>(v));
             }
         }
     }
