@@ -1,5 +1,7 @@
-// Ingest (classification + fixed-point geometry + compaction) and the voxel
-// traversal that accumulates N and M.
+// Ingest (classification, fixed-point geometry, each record at its
+// history's slot with its path decided against the block's pair budget) and
+// the global-memory traversal that accumulates N and M for the records that
+// do not take the tiled path.
 //
 // Classification: Eq. 3.1 (missed, WEPL below the cutoff) and Eq. 3.7 (hit,
 // WEPL above the cutoff).  Path: the closed segment between entry and exit
@@ -7,7 +9,7 @@
 // cubes.  Accumulation: N of Eq. 3.4 (Alg. 2; SC's H_1 = [N = 0] of Eq. 3.3
 // is the carve of Alg. 1 as a set difference), M of Eq. 3.9 (Alg. 3).
 //
-// The traversal is an exact integer DDA.  For the segment
+// The global traversal is an exact integer DDA.  For the segment
 // P(t) = G_in + t D (grid coordinates with 16 fractional bits) the next
 // plane crossing of axis a happens at t_a = num_a / |D_a|; the walk keeps the
 // three cross-multiplied differences E_ab = num_a |D_b| - num_b |D_a| (their

@@ -254,3 +254,15 @@ extern "C" int hx_tile_range(const int32_t *r, int nx, int ny, int nz, int tx, i
     for (int a = 0; a < 3; ++a) { lo[a] = l[a]; hi[a] = h[a]; }
     return c;
 }
+
+// The chunk split shared by the ingest and the scatter (hd_internal.cuh).
+extern "C" void hx_chunk_split(long long n, int sm_count, int *blocks, long long *per_block)
+{
+    const hd::ChunkSplit c = hd::chunk_split(n, sm_count);
+    *blocks = c.blocks;
+    *per_block = c.per_block;
+}
+
+// The loop-free floor division against the looping one (hd_geom.cuh), for
+// operand pairs whose quotient is below 2^20 in magnitude.
+extern "C" long long hx_fdiv_small(long long a, long long b) { return hd::fdiv_small(a, b); }

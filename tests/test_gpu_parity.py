@@ -124,6 +124,9 @@ TILED_GEOMS = [
     synth.Geometry(256, 256, 4, 1.0, 1.0, 2.5, 190.0),    # x-y strips, one slice
     synth.Geometry(64, 64, 40, 1.0, 1.0, 0.5, 100.0),     # slabs of 10 slices
     synth.Geometry(400, 130, 3, 0.5, 0.5, 1.25, 155.0),   # x-y strips
+    # 20 x-y strips per slice: steep diagonal paths touch more than 32 tiles
+    # of their box and take the global path's list
+    synth.Geometry(1000, 1000, 4, 0.2, 0.2, 2.5, 155.0),
 ]
 
 
@@ -139,7 +142,7 @@ def test_multi_tile_grids(hd, oracle_mod, gi):
         got = _run_gpu(hd, g, h)
         _assert_same(got, ref, ALL)
         _assert_stats(got, ref)
-    # SC alone uses the carve masks of the same tiles
+    # SC alone counts N over the same tiles and keeps {N = 0}
     p = oracle_mod.Params(methods=oracle_mod.SC)
     ref = oracle_mod.run(g, h, p, threads=8)
     got = _run_gpu(hd, g, h, p)

@@ -375,3 +375,38 @@ def test_tile_range_covers_the_voxel_set(oracle_mod, hx, dims, tiles):
         zb = np.clip(np.array([a[2], b[2]]) >> 16, 0, dims[2] - 1) // tiles[2]
         tight += (up[2] - lo[2]) < (zb.max() - zb.min())
     assert tight > 0  # the x-y clip removes slices the bounding box would add
+
+
+def test_chunk_split_covers_every_history_once(hx):
+    """The split that ingest and scatter share: blocks of per_block
+    consecutive histories (a multiple of 4), at most 8 per SM, covering
+    [0, n) with no empty block."""
+    hx.hx_chunk_split.restype = None
+    blocks, per = ctypes.c_int(), ctypes.c_longlong()
+    rng = np.random.default_rng(5)
+    ns = [1, 2, 3, 4, 5, 255, 256, 257, 1023, 1024, 4096, 4097, 180000, 550000, 9000000,
+          1 << 25] + [int(x) for x in rng.integers(1, 1 << 25, 200)]
+    for sm in (1, 7, 152):
+        for n in ns:
+            hx.hx_chunk_split(ctypes.c_longlong(n), sm, ctypes.byref(blocks), ctypes.byref(per))
+            b, p = blocks.value, per.value
+            assert p % 4 == 0 and p > 0, (n, sm, p)
+            assert 1 <= b <= 8 * sm, (n, sm, b)
+            assert b * p >= n and (b - 1) * p < n, (n, sm, b, p)
+
+
+def test_loop_free_floor_division(hx):
+    """fdiv_small, the set-up's loop-free floor division, equals floor
+    division wherever the quotient stays below 2^20: random operands at
+    every scale, exact multiples and their neighbours, negative numerators."""
+    hx.hx_fdiv_small.restype = ctypes.c_longlong
+    hx.hx_fdiv_small.argtypes = [ctypes.c_longlong, ctypes.c_longlong]
+    rng = np.random.default_rng(8)
+    for _ in range(20000):
+        b = int(rng.integers(1, 1 << int(rng.integers(1, 47))))
+        q = int(rng.integers(-(1 << 20) + 1, 1 << 20))
+        r = int(rng.integers(-2, 3))
+        a = q * b + r
+        if abs(a) >= 1 << 62:
+            continue
+        assert hx.hx_fdiv_small(a, b) == a // b, (a, b)
