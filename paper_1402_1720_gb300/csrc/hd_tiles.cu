@@ -21,7 +21,7 @@ namespace hd {
 namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
-constexpr int kScatterThreads = 256;
+constexpr int kScatterThreads = 512;
 constexpr int kRunsPerStep = 8;       // runs a traversal lane walks between refill checks
 
 __device__ __forceinline__ unsigned warp_incl_scan_u(unsigned v)
@@ -156,7 +156,7 @@ __device__ __noinline__ bool general_setup(const int32_t gi[3], const int32_t go
 // ingest block b listed, one per thread, and writes those of tile c from
 // tile_start[c] + block_base[c * blocks + b] on (a shared-memory cursor per
 // tile orders them within the block).
-__global__ void __launch_bounds__(kScatterThreads, 4) scatter_kernel(
+__global__ void __launch_bounds__(kScatterThreads, 2) scatter_kernel(
     TilePlan tp, Records rec, int64_t per_block, const uint32_t *tile_start,
     const uint32_t *block_base, const uint32_t *block_pairs, Ctrl *ctrl, Pairs pairs)
 {
