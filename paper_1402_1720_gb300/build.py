@@ -21,7 +21,7 @@ INCLUDE = PKG.parent / "include"
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
               "-Xcompiler", "-fvisibility=hidden"]
-SOURCES = ["hd_api.cu", "hd_trace.cu", "hd_tiles.cu", "hd_decide.cu", "hd_noalloc.cu", "hd_server.cu",
+SOURCES = ["hd_api.cu", "hd_trace.cu", "hd_tiles.cu", "hd_scatter.cu", "hd_decide.cu", "hd_noalloc.cu", "hd_server.cu",
            "hd_probe.cu", "hd_rows.cu", "hd_binned.cu", "hd_diag.cu",
            "hd_canny.cu", "hd_thick.cu", "hd_thick_tiles.cu", "hd_euclid.cu"]
 
