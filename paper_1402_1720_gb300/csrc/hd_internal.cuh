@@ -12,7 +12,7 @@ constexpr int64_t kQ16 = 65536;
 constexpr int kMaxN = 4096;
 constexpr int kMaxTiles = 2048;       // tiles per class for the shared-memory path
 constexpr int kTraceThreads = 512;    // threads per block of the tiled traversal
-constexpr int kTileSmemBytes = 200 * 1024;  // shared memory per block for a private tile
+constexpr int kTileSmemBytes = 224 * 1024;  // shared memory per block for a private tile
 
 // Gantry-rotation constants: theta[i] = round(atan(2^-i) * 180/pi * 2^30)
 // (degrees, 30 fractional bits) and K = round(2^30 prod (1 + 2^-2i)^-1/2).
