@@ -266,3 +266,79 @@ extern "C" void hx_chunk_split(long long n, int sm_count, int *blocks, long long
 // The loop-free floor division against the looping one (hd_geom.cuh), for
 // operand pairs whose quotient is below 2^20 in magnitude.
 extern "C" long long hx_fdiv_small(long long a, long long b) { return hd::fdiv_small(a, b); }
+
+// The Euclidean thick rays' row search (hd_euclid.cuh) against a voxel-by-
+// voxel exact search: for every history the capsule is set up as the kernel
+// does it, and every row of the grid is searched both ways (rows outside the
+// capsule's index box must hold no voxel).  The float filter's certificates
+// are checked at every centre, with the empty-row certificate around every
+// centre of every nonempty row and the filtered row-meets test on every row.
+// st: [rows with voxels, voxels, interval
+// mismatches, filter errors, centres settled by the exact test, centres
+// tested, histories set up]; returns 0, or -1 on bad arguments.
+#include "../../paper_1402_1720_gb300/csrc/hd_euclid.cuh"
+extern "C" int hx_euclid_rows(int nx, int ny, int nz, float sx, float sy, float sz, float T,
+                              const long long *theta, long long K, float d0, const float *ang,
+                              const float *ui, const float *vi, const float *uo, const float *vo,
+                              int n, long long *st)
+{
+    if (n < 0 || !(d0 >= 0.0f)) return -1;
+    hd::GeomQ g = hd::make_geomq(nx, ny, nz, sx, sy, sz, T);
+    hd::Cordic cd;
+    for (int i = 0; i < 32; ++i) cd.theta[i] = theta[i];
+    cd.K = K;
+    const long long R = 2 * hd::q16_of(d0);
+    for (int q = 0; q < 7; ++q) st[q] = 0;
+    for (int h = 0; h < n; ++h) {
+        long long c, s;
+        hd::cordic_cs(hd::q16_of(ang[h]), cd, c, s);
+        int32_t G[6];
+        if (!hd::endpoints_cs(g, c, s, ui[h], vi[h], uo[h], vo[h], G)) continue;
+        long long W[6];
+        hd::world_cs(g, c, s, ui[h], vi[h], uo[h], vo[h], W);
+        long long A[3], B[3];
+        int blo[3], bhi[3];
+        bool ymaj;
+        float S;
+        const bool box = hd::capsule_frame(g, W, R, A, B, ymaj, blo, bhi, S);
+        hd::CapX cx;
+        hd::capx_of(g, A, B, ymaj, R, cx);
+        const hd::CapF cf = hd::capf_of(cx, S, R);
+        st[6] += 1;
+        for (int k = 0; k < cx.n[2]; ++k)
+            for (int a = 0; a < cx.n[1]; ++a) {
+                const hd::RowF r = hd::rowf_of(cf, a, k);
+                int blo_i = -1, bhi_i = -2, cnt = 0;
+                for (int i = 0; i < cx.n[0]; ++i) {
+                    const bool in = hd::F_exact(cx, a, k, i) <= cx.T;
+                    float e0;
+                    const float d2 = hd::d2_filter(cf, r, i, e0);
+                    st[5] += 1;
+                    if ((d2 <= cf.Tin && !in) || (d2 > cf.Tout && in)) st[3] += 1;
+                    if (!(d2 <= cf.Tin) && !(d2 > cf.Tout)) st[4] += 1;
+                    if (in) {
+                        if (blo_i < 0) blo_i = i;
+                        if (bhi_i != i - 1 && bhi_i >= 0) st[2] += 1;  // not one interval
+                        bhi_i = i;
+                        ++cnt;
+                    }
+                }
+                const bool inbox = box && a >= blo[1] && a <= bhi[1] && k >= blo[2] && k <= bhi[2];
+                const bool meets = hd::row_meets_at(cf, cx, a, k);
+                if (meets != hd::meets_exact(cx, a, k)) st[3] += 1;
+                // the empty-row certificate around every centre of the row
+                for (int j = 0; j < cx.n[0]; ++j)
+                    if (cnt > 0 && hd::row_empty(cf, r, j)) st[3] += 1;
+                int lo = 0, hi = -1;
+                const bool got = inbox && meets && hd::row_interval(cf, cx, a, k, lo, hi);
+                if (cnt == 0) {
+                    if (got) st[2] += 1;
+                } else {
+                    st[0] += 1;
+                    st[1] += cnt;
+                    if (!got || lo != blo_i || hi != bhi_i) st[2] += 1;
+                }
+            }
+    }
+    return 0;
+}

@@ -1,7 +1,8 @@
 """The CUDA library's geometry and traversal code (hd_geom.cuh), compiled for
 the host, against the CPU oracle: exact voxel sets for adversarial segments,
 the same sets when the walk is clipped to shared-memory tiles, and identical
-fixed-point endpoints.  Runs without a GPU (nvcc compiles host code)."""
+fixed-point endpoints, and the Euclidean thick rays' row search against a
+voxel-by-voxel exact search.  Runs without a GPU (nvcc compiles host code)."""
 import ctypes
 import os
 import shutil
@@ -410,3 +411,58 @@ def test_loop_free_floor_division(hx):
         if abs(a) >= 1 << 62:
             continue
         assert hx.hx_fdiv_small(a, b) == a // b, (a, b)
+
+
+def _euclid_rows(L, oracle_mod, g, h, d0):
+    theta, K = oracle_mod.cordic_table()
+    th = (ctypes.c_longlong * 32)(*theta)
+    FP = ctypes.POINTER(ctypes.c_float)
+    arrs = [np.ascontiguousarray(a, np.float32)
+            for a in (h.angle_deg, h.u_in, h.v_in, h.u_out, h.v_out)]
+    st = (ctypes.c_longlong * 7)()
+    r = L.hx_euclid_rows(g.nx, g.ny, g.nz, ctypes.c_float(g.sx), ctypes.c_float(g.sy),
+                         ctypes.c_float(g.sz), ctypes.c_float(g.T), th, ctypes.c_longlong(K),
+                         ctypes.c_float(d0), *[a.ctypes.data_as(FP) for a in arrs], len(h), st)
+    assert r == 0
+    return dict(zip(["rows", "voxels", "mismatch", "filter_errors", "exact", "tested",
+                     "histories"], list(st)))
+
+
+@pytest.mark.parametrize("dims,sizes", [((23, 17, 9), (1.0, 1.0, 2.5)),
+                                        ((16, 40, 12), (0.5, 1.25, 0.75)),
+                                        ((50, 6, 3), (2.0, 0.8, 3.0)),
+                                        ((7, 1, 1), (1.0, 1.0, 1.0))])
+def test_euclid_row_search_equals_voxel_search(oracle_mod, hx, dims, sizes):
+    """The Euclidean thick rays' row search (float filter, empty-row
+    certificate, filtered row-meets test, exact tests in the band) gives, row
+    by row, the interval a voxel-by-voxel exact search finds, and no filter
+    certificate contradicts the exact test (Eq. 3.2 with d_0 > 0)."""
+    g = synth.Geometry(*dims, *sizes, 40.0)
+    rng = np.random.default_rng(sum(dims) + 5)
+    h = synth.tiny_random_case(rng, 600, g, span=1.3)
+    h.u_out[:60] = h.u_in[:60] + rng.normal(0, 1e-3, 60).astype(np.float32)
+    h.v_out[60:120] = h.v_in[60:120]
+    for d0 in (0.3, 1.7, 4.0):
+        st = _euclid_rows(hx, oracle_mod, g, h, d0)
+        assert st["mismatch"] == 0 and st["filter_errors"] == 0, (d0, st)
+        assert st["histories"] > 0 and st["rows"] > 0
+        # the band is narrow: nearly every test settled in float
+        assert st["exact"] < 1e-3 * st["tested"], st
+
+
+def test_euclid_row_search_centres_on_the_boundary(oracle_mod, hx):
+    """Paths along rows of voxel centres, radii at and next to multiples of
+    the spacing: centres lie on the capsule's surface up to the fixed-point
+    rounding, inside the filter's band, and the exact test decides."""
+    g = synth.Geometry(32, 32, 8, 1.0, 1.0, 2.5, 40.0)
+    n = 64
+    ang = np.repeat(np.array([0.0, 90.0], np.float32), n // 2)
+    u = (np.arange(n) % 16 - 8 + 0.5).astype(np.float32)
+    v = ((np.arange(n) % 8) * 2.5 - 10.0 + 1.25).astype(np.float32)
+    h = synth.Histories(ang, u, v, u.copy(), v.copy(), np.full(n, 0.5, np.float32))
+    exact = 0
+    for d0 in (0.0, 2.0**-15, 0.5, 1.0, 1.0 - 2**-16, 2.5, 2.5 + 2**-16):
+        st = _euclid_rows(hx, oracle_mod, g, h, d0)
+        assert st["mismatch"] == 0 and st["filter_errors"] == 0, (d0, st)
+        exact += st["exact"]
+    assert exact > 0
