@@ -23,6 +23,7 @@ namespace hd {
 namespace {
 
 constexpr int kEuThreads = 256;
+constexpr int kEuBlocksPerSm = 2;  // resident blocks per SM (the launch bounds)
 constexpr int kEuGroup = 32;  // consecutive histories a warp takes at once, one per lane
 
 struct EuCounts {
@@ -37,7 +38,7 @@ struct EuSlot {
     int flags;             // bit 0: hit class, bit 1: rows along y, bit 2: has rows
 };
 
-__global__ void __launch_bounds__(kEuThreads, 2) euclid_kernel(Inputs in, int64_t n, GeomQ g,
+__global__ void __launch_bounds__(kEuThreads, kEuBlocksPerSm) euclid_kernel(Inputs in, int64_t n, GeomQ g,
                                                             Cordic cd, float tau_l, float tau_h,
                                                             int use_miss, int use_hit,
                                                             long long R2, ThickDiff td,
@@ -127,29 +128,16 @@ __global__ void __launch_bounds__(kEuThreads, 2) euclid_kernel(Inputs in, int64_
             if (lane == 0) capx_of(g, slot[j].A, slot[j].B, ymaj, R2, *cxs);
             __syncwarp();
             const CapF cf = capf_of(*cxs, slot[j].S, R2);
-            const int blo1 = slot[j].blo1, blo2 = slot[j].blo2;
-            const int na = slot[j].bhi1 - blo1 + 1;
-            const int nrows = na * (slot[j].bhi2 - blo2 + 1);
+            const int blo1 = slot[j].blo1, bhi1 = slot[j].bhi1;
+            const int blo2 = slot[j].blo2, bhi2 = slot[j].bhi2;
             int32_t *diff = ymaj ? td.dy[cls] : td.dx[cls];
             const int n1 = ymaj ? g.nx : g.ny;
-            // the rows of the box that meet the capsule (filtered test)
-            // queue up in shared memory; whenever 32 are queued all lanes take
-            // one each, so the interval search runs with full warps
+            // the rows that can meet the capsule queue up in shared memory;
+            // whenever 32 are queued all lanes take one each, so the interval
+            // search runs with full warps
             int qn = 0;
-            for (int rb = 0; rb < nrows; rb += 32) {
-                const int rw = rb + static_cast<int>(lane);
-                bool meets = false;
-                int a = 0, k = 0;
-                if (rw < nrows) {
-                    a = blo1 + rw % na;
-                    k = blo2 + rw / na;
-                    meets = row_meets_at(cf, *cxs, a, k);
-                }
-                const unsigned bal = __ballot_sync(0xffffffffu, meets);
-                if (meets) queue[qn + __popc(bal & ((1u << lane) - 1u))] = a | (k << 16);
-                qn += __popc(bal);
-                const bool last = rb + 32 >= nrows;
-                while (qn >= 32 || (last && qn > 0)) {
+            auto drain = [&](int keep) {
+                while (qn > keep) {
                     __syncwarp();
                     int lo, hi;
                     if (static_cast<int>(lane) < qn &&
@@ -174,7 +162,28 @@ __global__ void __launch_bounds__(kEuThreads, 2) euclid_kernel(Inputs in, int64_
                     __syncwarp();
                     qn = rest;
                 }
+            };
+            // each lane one index a of the box, with the band of k whose rows
+            // can meet the capsule
+            for (int ab = blo1; ab <= bhi1; ab += 32) {
+                const int a = ab + static_cast<int>(lane);
+                int klo = 1, khi = 0;
+                if (a <= bhi1) k_range(cf, a, blo2, bhi2, klo, khi);
+                const int cnt = khi >= klo ? khi - klo + 1 : 0;
+                const int most = __reduce_max_sync(0xffffffffu, cnt);
+                for (int t = 0; t < most; ++t) {
+                    const int k = klo + t;
+                    // inside the band nearly every row meets the capsule, and
+                    // the row search is exact for any row: the band's rows go
+                    // to it directly; a whole box is filtered first
+                    const bool meets = t < cnt && (cf.kband || row_meets_at(cf, *cxs, a, k));
+                    const unsigned bal = __ballot_sync(0xffffffffu, meets);
+                    if (meets) queue[qn + __popc(bal & ((1u << lane) - 1u))] = a | (k << 16);
+                    qn += __popc(bal);
+                    drain(31);
+                }
             }
+            drain(0);
         }
     }
     const unsigned long long part[8] = {nc.n_in, nc.n_miss, nc.n_hit, nc.n_none, nc.n_reject,
@@ -202,7 +211,8 @@ cudaError_t launch_euclid(const Inputs &in, int64_t n, const hd_geometry *geom, 
         const long long R2 = 2 * q16_of(d0);
         const ThickDiff td = thick_diff_of(geom, workspace);
         unsigned long long *cnt = thick_counters_of(geom, workspace);
-        int64_t blocks = int64_t(sm_count > 0 ? sm_count : 1) * 8;  // persistent warps
+        // persistent warps
+        int64_t blocks = int64_t(sm_count > 0 ? sm_count : 1) * kEuBlocksPerSm;
         const int64_t want = (n + kEuGroup * (kEuThreads / 32) - 1) /
                              (kEuGroup * (kEuThreads / 32));
         if (blocks > want) blocks = want;

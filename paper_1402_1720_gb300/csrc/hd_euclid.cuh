@@ -136,6 +136,11 @@ struct CapF {
     float Tin, Tout;  // certain inside at or below Tin, outside above Tout
     float margin;     // 2^-19 S
     int n0;           // centres along a row
+    // the band of rows that can meet the capsule (k_range)
+    float ratio;      // u_2 / u_1
+    float Hk;         // R sqrt(1 + ratio^2) plus the error margin
+    float inv_step2;  // 1 / step[2]
+    bool kband;       // |u_2| <= 4 |u_1| and u_1 != 0 (else the whole box)
 };
 
 // The float constants of row (a, k).
@@ -352,9 +357,9 @@ HD_HD void estimate(const CapF &cf, const RowF &r, int &ilo, int &ihi, int &imin
     imin = static_cast<int>(rintf(fminf(fmaxf(fm, 0.0f), top)));
 }
 
-// The exact interval [lo, hi] of voxels of row (a, k), a row whose line
-// meets the capsule (false when no voxel centre of the row lies inside: the
-// row's chord can fall between two centres).
+// The exact interval [lo, hi] of voxels of row (a, k) inside the capsule
+// (false when no voxel centre of the row lies inside: the row may miss the
+// capsule, or its chord fall between two centres).
 HD_HD bool row_interval(const CapF &cf, const CapX &cx, int a, int k, int &lo, int &hi)
 {
     const int n = cf.n0;
@@ -429,6 +434,8 @@ HD_HD bool row_interval(const CapF &cf, const CapX &cx, int a, int k, int &lo, i
 }
 
 HD_HD long long abs_ll(long long v) { return v < 0 ? -v : v; }
+HD_HD int max_i(int a, int b) { return a > b ? a : b; }
+HD_HD int min_i(int a, int b) { return a < b ? a : b; }
 
 // floor(v / s) for s > 0 (|v| < 2^62).
 HD_HD long long floor_div(long long v, long long s)
@@ -534,7 +541,37 @@ HD_HD CapF capf_of(const CapX &cx, float S, long long R)
     cf.margin = m;
     cf.Tin = lo > 0.0f ? (lo * lo) * (1.0f - 1.0f / 524288.0f) : -1.0f;
     cf.Tout = (hi * hi) * (1.0f + 1.0f / 524288.0f);
+    const float au1 = fabsf(cf.uf[1]), au2 = fabsf(cf.uf[2]);
+    cf.kband = cx.u[1] != 0 && au2 <= 4.0f * au1;
+    cf.ratio = cf.kband ? cf.uf[2] * rcp_est(cf.uf[1]) : 0.0f;
+    cf.Hk = cf.Rf * sqrt_est(1.0f + cf.ratio * cf.ratio) + (S + cf.Rf) * (1.0f / 65536.0f);
+    cf.inv_step2 = rcp_est(cf.step[2]);
     return cf;
+}
+
+// The rows (a, k) of the capsule's index box that can meet it, for one a:
+// k in [klo, khi] (empty when klo > khi).  A row meets the capsule only if
+// its point lies within R of the projected segment's line in the plane of
+// axes 1 and 2, that is within R sqrt(1 + r^2) of it along axis 2 (r the
+// line's slope u_2 / u_1).  In float, with |r| <= 4, the line's height at
+// the row, that distance and the division into indices are off by less
+// than 100 eps (S + R) together, so widening the distance by 2^-16 (S + R)
+// makes [klo, khi] a superset of the meeting rows; steeper or axis-parallel
+// projections take the whole box.
+HD_HD void k_range(const CapF &cf, int a, int blo2, int bhi2, int &klo, int &khi)
+{
+    if (!cf.kband) {
+        klo = blo2;
+        khi = bhi2;
+        return;
+    }
+    const float wc = fmaf(float_small(a), cf.step[1], cf.wb[1]);
+    const float zc = wc * cf.ratio;
+    const float fb = float_small(blo2 - 1), ft = float_small(bhi2 + 1);
+    const float lo = fminf(fmaxf((zc - cf.Hk - cf.wb[2]) * cf.inv_step2, fb), ft);
+    const float hi = fminf(fmaxf((zc + cf.Hk - cf.wb[2]) * cf.inv_step2, fb), ft);
+    klo = max_i(blo2, static_cast<int>(ceilf(lo)));
+    khi = min_i(bhi2, static_cast<int>(floorf(hi)));
 }
 
 }  // namespace

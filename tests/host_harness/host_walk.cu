@@ -272,7 +272,8 @@ extern "C" long long hx_fdiv_small(long long a, long long b) { return hd::fdiv_s
 // does it, and every row of the grid is searched both ways (rows outside the
 // capsule's index box must hold no voxel).  The float filter's certificates
 // are checked at every centre, with the empty-row certificate around every
-// centre of every nonempty row and the filtered row-meets test on every row.
+// centre of every nonempty row, the filtered row-meets test on every row and
+// the band of candidate rows (k_range) around every meeting row of the box.
 // st: [rows with voxels, voxels, interval
 // mismatches, filter errors, centres settled by the exact test, centres
 // tested, histories set up]; returns 0, or -1 on bad arguments.
@@ -326,17 +327,24 @@ extern "C" int hx_euclid_rows(int nx, int ny, int nz, float sx, float sy, float 
                 const bool inbox = box && a >= blo[1] && a <= bhi[1] && k >= blo[2] && k <= bhi[2];
                 const bool meets = hd::row_meets_at(cf, cx, a, k);
                 if (meets != hd::meets_exact(cx, a, k)) st[3] += 1;
+                // a meeting row of the box lies in its band of k
+                if (meets && inbox) {
+                    int klo, khi;
+                    hd::k_range(cf, a, blo[2], bhi[2], klo, khi);
+                    if (k < klo || k > khi) st[3] += 1;
+                }
                 // the empty-row certificate around every centre of the row
                 for (int j = 0; j < cx.n[0]; ++j)
                     if (cnt > 0 && hd::row_empty(cf, r, j)) st[3] += 1;
+                // the row search on every row of the box, meeting or not
                 int lo = 0, hi = -1;
-                const bool got = inbox && meets && hd::row_interval(cf, cx, a, k, lo, hi);
+                const bool got = inbox && hd::row_interval(cf, cx, a, k, lo, hi);
                 if (cnt == 0) {
                     if (got) st[2] += 1;
                 } else {
                     st[0] += 1;
                     st[1] += cnt;
-                    if (!got || lo != blo_i || hi != bhi_i) st[2] += 1;
+                    if (!meets || !got || lo != blo_i || hi != bhi_i) st[2] += 1;
                 }
             }
     }
