@@ -40,32 +40,94 @@ __device__ __forceinline__ bool row_endpoints(const Inputs &in, int64_t i, const
 }
 
 // The hull as a bitmap (voxel v at bit v & 31 of word v >> 5), in shared
-// memory when it fits there, else read as bytes from global memory.
+// memory when it fits there, else read as bytes from global memory; and the
+// hull voxels of one run of a path.  A run along x covers consecutive bits
+// (v = nx row + m): with the bitmap they are counted by population counts
+// of its words and listed from its set bits; a run along y has stride nx.
 template <bool kBits>
-struct HullTest {
+struct HullRuns {
     const uint8_t *bytes;
     const uint32_t *bits;
-    __device__ __forceinline__ bool operator()(uint32_t v) const
+    int nx, ny;
+
+    __device__ __forceinline__ bool test(uint32_t v) const
     {
         if (kBits) return (bits[v >> 5] >> (v & 31u)) & 1u;
         return bytes[v] != 0;
     }
-};
 
-template <bool kBits>
-struct CountInHull {
-    HullTest<kBits> in;
-    int64_t count;
-    __device__ __forceinline__ void operator()(uint32_t v) { count += in(v) ? 1 : 0; }
-};
-
-template <bool kBits>
-struct EmitInHull {
-    HullTest<kBits> in;
-    int32_t *out;
-    __device__ __forceinline__ void operator()(uint32_t v)
+    // first voxel and stride of run row (the major axis' layout: y + ny z
+    // along x, x + nx z along y)
+    __device__ __forceinline__ void frame(bool ymaj, int row, uint32_t &base,
+                                          uint32_t &stride) const
     {
-        if (in(v)) *out++ = static_cast<int32_t>(v);
+        if (!ymaj) {
+            base = static_cast<uint32_t>(nx) * static_cast<uint32_t>(row);
+            stride = 1;
+        } else {
+            const int z = static_cast<int>(fdiv_small(row, nx));
+            base = static_cast<uint32_t>(row - z * nx) +
+                   static_cast<uint32_t>(nx) * static_cast<uint32_t>(ny) * static_cast<uint32_t>(z);
+            stride = static_cast<uint32_t>(nx);
+        }
+    }
+
+    // number of hull voxels of the run
+    __device__ __forceinline__ int count(bool ymaj, int row, int lo, int hi) const
+    {
+        uint32_t base, stride;
+        frame(ymaj, row, base, stride);
+        if (kBits && !ymaj) {
+            const uint32_t s = base + lo, e = base + hi;
+            const uint32_t ws = s >> 5, we = e >> 5;
+            const uint32_t ml = ~0u << (s & 31u), mh = ~0u >> (31u - (e & 31u));
+            if (ws == we) return __popc(bits[ws] & ml & mh);
+            int c = __popc(bits[ws] & ml) + __popc(bits[we] & mh);
+            for (uint32_t w = ws + 1; w < we; ++w) c += __popc(bits[w]);
+            return c;
+        }
+        int c = 0;
+        for (int m = lo; m <= hi; ++m) c += test(base + stride * static_cast<uint32_t>(m)) ? 1 : 0;
+        return c;
+    }
+
+    // writes the run's hull voxels to out in path order (m rising when up)
+    __device__ __forceinline__ int32_t *emit(bool ymaj, bool up, int row, int lo, int hi,
+                                             int32_t *out) const
+    {
+        uint32_t base, stride;
+        frame(ymaj, row, base, stride);
+        if (kBits && !ymaj) {
+            const uint32_t s = base + lo, e = base + hi;
+            const int ws = static_cast<int>(s >> 5), we = static_cast<int>(e >> 5);
+            const uint32_t ml = ~0u << (s & 31u), mh = ~0u >> (31u - (e & 31u));
+            if (up) {
+                for (int w = ws; w <= we; ++w) {
+                    uint32_t b = bits[w] & (w == ws ? ml : ~0u) & (w == we ? mh : ~0u);
+                    while (b) {
+                        *out++ = static_cast<int32_t>((static_cast<uint32_t>(w) << 5) +
+                                                      static_cast<uint32_t>(__ffs(b) - 1));
+                        b &= b - 1u;
+                    }
+                }
+            } else {
+                for (int w = we; w >= ws; --w) {
+                    uint32_t b = bits[w] & (w == ws ? ml : ~0u) & (w == we ? mh : ~0u);
+                    while (b) {
+                        const int j = 31 - __clz(b);
+                        *out++ = static_cast<int32_t>((static_cast<uint32_t>(w) << 5) +
+                                                      static_cast<uint32_t>(j));
+                        b ^= 1u << j;
+                    }
+                }
+            }
+            return out;
+        }
+        for (int k = 0; k <= hi - lo; ++k) {
+            const uint32_t v = base + stride * static_cast<uint32_t>(up ? lo + k : hi - k);
+            if (test(v)) *out++ = static_cast<int32_t>(v);
+        }
+        return out;
     }
 };
 
@@ -76,6 +138,9 @@ __device__ __forceinline__ void stage_hull(uint32_t *s_bits, const uint32_t *bit
     __syncthreads();
 }
 
+// Every lane walks its history's path as runs of the whole-grid run walk
+// (one loop for all lanes; the runs come in path order, each expanded in
+// the direction the major axis moves).
 template <bool kBits>
 __global__ void __launch_bounds__(kRowsThreads) rows_count_kernel(Inputs in, int64_t n, GeomQ g,
                                                                   Cordic cd, const uint8_t *hull,
@@ -84,14 +149,20 @@ __global__ void __launch_bounds__(kRowsThreads) rows_count_kernel(Inputs in, int
 {
     extern __shared__ uint32_t s_bits[];
     if (kBits) stage_hull(s_bits, hull_bits, words);
+    const HullRuns<kBits> h{hull, s_bits, g.nx, g.ny};
     RowsTrig tc;
     const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
     for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
          i += stride) {
         int32_t r[6];
-        CountInHull<kBits> c{{hull, s_bits}, 0};
-        if (row_endpoints(in, i, g, cd, tc, r)) walk_path(r, g.nx, g.ny, g.nz, c);
-        row_ptr[i + 1] = c.count;
+        int64_t count = 0;
+        RunWalk w;
+        if (row_endpoints(in, i, g, cd, tc, r) && run_begin(w, r, r + 3, g.nx, g.ny, g.nz)) {
+            const bool ymaj = (w.flags >> 5) & 1;
+            int row, lo, hi;
+            while (run_next(w, row, lo, hi)) count += h.count(ymaj, row, lo, hi);
+        }
+        row_ptr[i + 1] = count;
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) row_ptr[0] = 0;
 }
@@ -106,13 +177,19 @@ __global__ void __launch_bounds__(kRowsThreads) rows_emit_kernel(Inputs in, int6
 {
     extern __shared__ uint32_t s_bits[];
     if (kBits) stage_hull(s_bits, hull_bits, words);
+    const HullRuns<kBits> h{hull, s_bits, g.nx, g.ny};
     RowsTrig tc;
     const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
     for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
          i += stride) {
         int32_t r[6];
-        EmitInHull<kBits> e{{hull, s_bits}, cols + row_ptr[i]};
-        if (row_endpoints(in, i, g, cd, tc, r)) walk_path(r, g.nx, g.ny, g.nz, e);
+        RunWalk w;
+        if (row_endpoints(in, i, g, cd, tc, r) && run_begin(w, r, r + 3, g.nx, g.ny, g.nz)) {
+            const bool ymaj = (w.flags >> 5) & 1, up = w.flags & 1;
+            int32_t *out = cols + row_ptr[i];
+            int row, lo, hi;
+            while (run_next(w, row, lo, hi)) out = h.emit(ymaj, up, row, lo, hi, out);
+        }
     }
 }
 

@@ -350,3 +350,87 @@ extern "C" int hx_euclid_rows(int nx, int ny, int nz, float sx, float sy, float 
     }
     return 0;
 }
+
+// The run walk expanded in path order (each run from its start in the
+// direction the major axis moves), as linear voxel indices.
+extern "C" int hx_runs_path_order(const int32_t *gi, const int32_t *go, int nx, int ny, int nz,
+                                  int32_t *out, int cap)
+{
+    hd::RunWalk w;
+    int n = 0;
+    if (!hd::run_begin(w, gi, go, nx, ny, nz)) return 0;
+    const bool ymaj = (w.flags >> 5) & 1, up = w.flags & 1;
+    int row, lo, hi;
+    while (hd::run_next(w, row, lo, hi)) {
+        for (int j = 0; j <= hi - lo; ++j) {
+            const int m = up ? lo + j : hi - j;
+            const int v = !ymaj ? m + nx * row : (row % nx) + nx * (m + ny * (row / nx));
+            if (n < cap) out[n] = v;
+            ++n;
+        }
+    }
+    return n;
+}
+
+// The whole-grid walk as one-slice walks, slice by slice in the direction
+// the path moves along z: each slice's walk from the direct one-slice set-up
+// (slab_lean) stepped as a lean cursor, or from the general set-up when
+// slab_lean declines; runs expanded in path order, as linear voxel indices.
+extern "C" int hx_slices_path_order(const int32_t *gi, const int32_t *go, int nx, int ny, int nz,
+                                    int32_t *out, int cap)
+{
+    int n = 0;
+    hd::TilePlan tp{};
+    tp.nx = nx;
+    tp.ny = ny;
+    tp.nz = nz;
+    const int32_t r[6] = {gi[0], gi[1], gi[2], go[0], go[1], go[2]};
+    int zlo, zhi;
+    if (!hd::grid_z_range(tp, r, zlo, zhi)) return 0;
+    const bool zup = go[2] >= gi[2];
+    for (int t = 0; t <= zhi - zlo; ++t) {
+        const int z = zup ? zlo + t : zhi - t;
+        const int32_t a[3] = {gi[0], gi[1], gi[2] - (z << 16)};
+        const int32_t b[3] = {go[0], go[1], go[2] - (z << 16)};
+        const int zoff = z * nx * ny;
+        hd::LeanWalk L;
+        const int rl = hd::slab_lean(a, b, nx, ny, L);
+        if (rl == 0) continue;
+        if (rl == 1) {
+            uint32_t o[hd::kLeanWords];
+            hd::lean_pack(L, o);
+            const bool ymaj = (L.fl >> 2) & 1;
+            hd::LeanCursor c;
+            if (!hd::lean_start(o, ymaj ? ny : nx, c)) continue;
+            bool more = true;
+            while (more) {
+                int rb, lo, hi;
+                unsigned ends = 0;
+                const int start = c.ms;
+                more = hd::lean_run(c, rb, lo, hi, ends);
+                const bool up = start == lo;  // a run goes from where it starts
+                for (int j = 0; j <= hi - lo; ++j) {
+                    const int m = up ? lo + j : hi - j;
+                    const int row = rb / (ymaj ? ny : nx);
+                    const int v = zoff + (!ymaj ? m + nx * row : row + nx * m);
+                    if (n < cap) out[n] = v;
+                    ++n;
+                }
+            }
+        } else {
+            hd::RunWalk w;
+            if (!hd::run_begin(w, a, b, nx, ny, 1)) continue;
+            const bool ymaj = (w.flags >> 5) & 1, up = w.flags & 1;
+            int row, lo, hi;
+            while (hd::run_next(w, row, lo, hi)) {
+                for (int j = 0; j <= hi - lo; ++j) {
+                    const int m = up ? lo + j : hi - j;
+                    const int v = zoff + (!ymaj ? m + nx * row : row + nx * m);
+                    if (n < cap) out[n] = v;
+                    ++n;
+                }
+            }
+        }
+    }
+    return n;
+}

@@ -466,3 +466,43 @@ def test_euclid_row_search_centres_on_the_boundary(oracle_mod, hx):
         assert st["mismatch"] == 0 and st["filter_errors"] == 0, (d0, st)
         exact += st["exact"]
     assert exact > 0
+
+
+@pytest.mark.parametrize("dims", [(5, 4, 3), (1, 1, 1), (7, 1, 2), (40, 30, 20), (1, 7, 3),
+                                  (9, 1, 1), (3, 3, 3)])
+def test_runs_in_path_order(hx, dims):
+    """The run walk, each run expanded from its start in the direction the
+    major axis moves, visits the voxels in the voxel walk's order (the rows
+    of the system matrix list them in that order)."""
+    rng = np.random.default_rng(sum(dims) + 99)
+    for a, b in _random_segments(rng, 2000, dims):
+        a = np.asarray(a, np.int32)
+        b = np.asarray(b, np.int32)
+        o1 = np.zeros(4 * sum(dims) + 64, np.int32)
+        o2 = np.zeros_like(o1)
+        n1 = hx.hx_walk(a.ctypes.data_as(I32P), b.ctypes.data_as(I32P), *dims,
+                        o1.ctypes.data_as(I32P), o1.size)
+        n2 = hx.hx_runs_path_order(a.ctypes.data_as(I32P), b.ctypes.data_as(I32P), *dims,
+                                   o2.ctypes.data_as(I32P), o2.size)
+        assert n1 == n2 and np.array_equal(o1[:n1], o2[:n2]), (a.tolist(), b.tolist())
+
+
+@pytest.mark.parametrize("dims", [(5, 4, 3), (1, 1, 1), (7, 1, 2), (40, 30, 20), (1, 7, 3),
+                                  (9, 1, 1), (3, 3, 3), (200, 200, 32)])
+def test_slice_walks_in_path_order(hx, dims):
+    """The path cut at its z planes, each slice's walk from the direct
+    one-slice set-up (or the general one where it declines), slices taken in
+    the direction the path moves along z: the voxel walk's voxels in the
+    voxel walk's order (the one-slice tiles of the traversal split every
+    walk this way; this pins the split voxel for voxel and in order)."""
+    rng = np.random.default_rng(sum(dims) + 99)
+    for a, b in _random_segments(rng, 2000, dims):
+        a = np.asarray(a, np.int32)
+        b = np.asarray(b, np.int32)
+        o1 = np.zeros(4 * sum(dims) + 64, np.int32)
+        o2 = np.zeros_like(o1)
+        n1 = hx.hx_walk(a.ctypes.data_as(I32P), b.ctypes.data_as(I32P), *dims,
+                        o1.ctypes.data_as(I32P), o1.size)
+        n2 = hx.hx_slices_path_order(a.ctypes.data_as(I32P), b.ctypes.data_as(I32P), *dims,
+                                     o2.ctypes.data_as(I32P), o2.size)
+        assert n1 == n2 and np.array_equal(o1[:n1], o2[:n2]), (a.tolist(), b.tolist())
