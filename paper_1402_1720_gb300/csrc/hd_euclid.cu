@@ -7,7 +7,7 @@
 //
 // Work.  A warp takes groups of 32 consecutive histories (so each lane's
 // gantry cos/sin rarely change); each lane classifies one history and sets
-// its capsule's frame up (endpoints, index box) in shared memory.  Then the
+// its capsule up (endpoints, index box, the float part) in shared memory.  Then the
 // warp takes the group's histories one at a time: its lanes take the rows of
 // voxels along the segment's major in-plane axis that cross the box bounding
 // the capsule (segment grown by d_0).  Each nonempty row adds +1 / -1 to a
@@ -33,7 +33,7 @@ struct EuCounts {
 // One history of a warp's group, as the lane that set it up left it.
 struct EuSlot {
     long long A[3], B[3];  // doubled endpoints in the capsule's frame
-    float S;               // S of the float filter
+    CapF cf;               // the float part of its capsule
     int16_t blo1, bhi1, blo2, bhi2;  // index box of the rows on axes 1 and 2
     int flags;             // bit 0: hit class, bit 1: rows along y, bit 2: has rows
 };
@@ -106,7 +106,9 @@ __global__ void __launch_bounds__(kEuThreads, kEuBlocksPerSm) euclid_kernel(Inpu
                             e.A[q] = A[q];
                             e.B[q] = B[q];
                         }
-                        e.S = S;
+                        CapX cx;
+                        capx_of(g, A, B, ymaj, R2, cx);
+                        e.cf = capf_of(cx, S, R2);
                         e.blo1 = static_cast<int16_t>(blo[1]);
                         e.bhi1 = static_cast<int16_t>(bhi[1]);
                         e.blo2 = static_cast<int16_t>(blo[2]);
@@ -127,7 +129,7 @@ __global__ void __launch_bounds__(kEuThreads, kEuBlocksPerSm) euclid_kernel(Inpu
             __syncwarp();  // the previous history is done with *cxs
             if (lane == 0) capx_of(g, slot[j].A, slot[j].B, ymaj, R2, *cxs);
             __syncwarp();
-            const CapF cf = capf_of(*cxs, slot[j].S, R2);
+            const CapF cf = slot[j].cf;
             const int blo1 = slot[j].blo1, bhi1 = slot[j].bhi1;
             const int blo2 = slot[j].blo2, bhi2 = slot[j].bhi2;
             int32_t *diff = ymaj ? td.dy[cls] : td.dx[cls];
