@@ -428,21 +428,28 @@ def _euclid_rows(L, oracle_mod, g, h, d0):
                      "histories"], list(st)))
 
 
-@pytest.mark.parametrize("dims,sizes", [((23, 17, 9), (1.0, 1.0, 2.5)),
-                                        ((16, 40, 12), (0.5, 1.25, 0.75)),
-                                        ((50, 6, 3), (2.0, 0.8, 3.0)),
-                                        ((7, 1, 1), (1.0, 1.0, 1.0))])
-def test_euclid_row_search_equals_voxel_search(oracle_mod, hx, dims, sizes):
+@pytest.mark.parametrize("dims,sizes,T,radii", [
+    ((23, 17, 9), (1.0, 1.0, 2.5), 40.0, (0.3, 1.7, 4.0)),
+    ((16, 40, 12), (0.5, 1.25, 0.75), 40.0, (0.3, 1.7, 4.0)),
+    ((50, 6, 3), (2.0, 0.8, 3.0), 40.0, (0.3, 1.7, 4.0)),
+    ((7, 1, 1), (1.0, 1.0, 1.0), 40.0, (0.3, 1.7, 4.0)),
+    # the extremes of the geometry the library takes: 1/64 mm voxels (the
+    # filter's band widest against a voxel), 64 mm voxels and radii with a
+    # 4 m tracker distance (its coordinates largest)
+    ((40, 30, 8), (1 / 64, 1 / 64, 1 / 64), 12.0, (0.0005, 0.01, 0.3)),
+    ((12, 10, 6), (64.0, 64.0, 64.0), 4000.0, (10.0, 63.9, 64.0))])
+def test_euclid_row_search_equals_voxel_search(oracle_mod, hx, dims, sizes, T, radii):
     """The Euclidean thick rays' row search (float filter, empty-row
-    certificate, filtered row-meets test, exact tests in the band) gives, row
-    by row, the interval a voxel-by-voxel exact search finds, and no filter
-    certificate contradicts the exact test (Eq. 3.2 with d_0 > 0)."""
-    g = synth.Geometry(*dims, *sizes, 40.0)
+    certificate, filtered row-meets test, band of candidate rows, exact
+    tests in the band) gives, row by row, the interval a voxel-by-voxel
+    exact search finds, and no filter certificate contradicts the exact test
+    (Eq. 3.2 with d_0 > 0)."""
+    g = synth.Geometry(*dims, *sizes, T)
     rng = np.random.default_rng(sum(dims) + 5)
     h = synth.tiny_random_case(rng, 600, g, span=1.3)
     h.u_out[:60] = h.u_in[:60] + rng.normal(0, 1e-3, 60).astype(np.float32)
     h.v_out[60:120] = h.v_in[60:120]
-    for d0 in (0.3, 1.7, 4.0):
+    for d0 in radii:
         st = _euclid_rows(hx, oracle_mod, g, h, d0)
         assert st["mismatch"] == 0 and st["filter_errors"] == 0, (d0, st)
         assert st["histories"] > 0 and st["rows"] > 0
