@@ -68,6 +68,28 @@ def test_random_segments_anisotropic(hd, oracle_mod, dims, sizes):
         assert np.array_equal(M, ref["M"]), d0
 
 
+@pytest.mark.parametrize("dims,sizes,T,radii", [
+    ((40, 30, 8), (1 / 64, 1 / 64, 1 / 64), 12.0, (0.0005, 0.01, 0.3)),
+    ((12, 10, 6), (64.0, 64.0, 64.0), 4000.0, (10.0, 63.9, 64.0)),
+    ((20, 7, 9), (2.0, 0.125, 0.0625), 100.0, (0.05, 0.3, 5.0))])
+def test_extreme_geometries(hd, oracle_mod, dims, sizes, T, radii):
+    """The geometry's extremes (1/64 mm and 64 mm voxels, a 4 m tracker
+    distance, strongly anisotropic voxels), where the kernel's float filter
+    works with its widest band against a voxel or its largest coordinates:
+    counts equal the oracle's."""
+    g = synth.Geometry(*dims, *sizes, T)
+    rng = np.random.default_rng(sum(dims) + 17)
+    h = synth.tiny_random_case(rng, 2000, g, span=1.3)
+    h.u_out[:200] = h.u_in[:200] + rng.normal(0, 1e-4, 200).astype(np.float32)
+    h.v_out[200:400] = h.v_in[200:400]
+    for d0 in radii:
+        ref = oracle_mod.accumulate_euclid(g, h, d0, threads=16)
+        N, M, _ = _gpu_counts(hd, g, h, d0)
+        assert ref["N"].sum() + ref["M"].sum() > 0, d0
+        assert np.array_equal(N, ref["N"]), d0
+        assert np.array_equal(M, ref["M"]), d0
+
+
 def test_rows_of_centres_and_zero_radius(hd, oracle_mod):
     """Paths along rows of voxel centres at angle 0 (x) and 90 degrees (y)
     (the fixed-point rotation leaves them within a unit of 2^-16 mm of the
