@@ -62,6 +62,18 @@ def test_rows_lattice_ties(hd, oracle_mod, g):
     s.close()
 
 
+def test_rows_hull_beyond_shared_memory(hd, oracle_mod):
+    """A grid whose hull bitmap (51 200 words) exceeds what a block keeps in
+    shared memory: the kernels test the hull as bytes from global memory,
+    voxel by voxel along either axis; every row of every hull equals the
+    oracle's."""
+    g = synth.Geometry(160, 160, 64, 1.0, 1.0, 1.0, 120.0)
+    h = synth.tiny_random_case(np.random.default_rng(21), 4000, g, span=1.3)
+    s, dev = _scan(hd, g, h)
+    _check_rows(hd, oracle_mod, s, g, h, dev)
+    s.close()
+
+
 def test_rows_rejected_histories_are_empty(hd, oracle_mod):
     w = synth.make_config(1, fraction=0.05)
     h = w.histories
