@@ -24,7 +24,7 @@ voxels, log-uniform 2e5-2e7 histories each): batched in one persistent
 launch against one scan at a time, and served as per-angle chunks with
 Poisson arrivals (time-to-hull percentiles).  Other workloads:
 --workload batched-48 | serving | rows | binned | diagnostics | thick |
-euclid | configs.
+euclid | configs | large.
 """
 from __future__ import annotations
 
@@ -1060,6 +1060,67 @@ def run_configs(args):
     print(json.dumps(line), flush=True)
 
 
+def run_large(args):
+    """The large streamed scan alone (400x400x128 voxels of 0.5x0.5x1.25 mm,
+    9.9e7 histories added in 180 per-angle chunks from device memory, one add
+    per chunk): reset, the adds and finalize per step, timed on the GPU, with
+    the traversal's voxel-steps per second against the random-address
+    shared-memory atomic rate hd_probe_atomics measures in the same run."""
+    import multiprocessing as mp
+    # the chunks come from a spawn pool started before any CUDA call
+    pool = mp.get_context("spawn").Pool(min(16, os.cpu_count() or 1))
+    from paper_1402_1720_gb300 import synth
+    chunks = pool.map(synth.config3_chunk, range(180))
+    pool.close()
+    pool.join()
+    import torch
+    from paper_1402_1720_gb300 import build as hbuild
+    from paper_1402_1720_gb300 import hulld
+    _, _, local = _dist()
+    torch.cuda.set_device(local)
+    hbuild.build()
+    hulld.load()
+    g3 = synth.geometry_for(3)
+    devs = [[torch.from_numpy(a).cuda() for a in p.arrays()] for p in chunks]
+    n = sum(len(c) for c in chunks)
+    stream = torch.cuda.current_stream()
+    with hulld.Scan(g3) as s:
+        def step():
+            s.reset()
+            for d in devs:
+                s.add(d)
+            s.finalize()
+        for _ in range(args.warmup):
+            step()
+        torch.cuda.synchronize()
+        sampler = ClockSampler(local)
+        sampler.start()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        clocks = sampler.stop()
+        st = s.stats()
+    ms = e0.elapsed_time(e1) / args.steps
+    steps_per_scan = (st["steps_miss"] + st["steps_hit"])
+    smem_rate = hulld.hd_probe_atomics(hulld.HD_PROBE_SMEM_RANDOM)
+    line = {"metric": "histories/s (large streamed scan, SC+MSC+SM)", "value": n / (ms * 1e-3),
+            "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "int32/int64", "data": "synthetic",
+            "config": {"workload": "large 400x400x128 voxels 0.5x0.5x1.25 mm, 9.9e7 float32 "
+                                   "histories added in 180 per-angle chunks from device memory",
+                       "histories": n, "chunks": len(chunks)},
+            "voxel_steps_per_scan": steps_per_scan,
+            "voxel_steps_per_s": steps_per_scan / (ms * 1e-3),
+            "smem_atomic_rate": smem_rate,
+            "gpu_launches": 6 * len(chunks) * args.steps, "clocks": clocks}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -1073,7 +1134,7 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--workload", default="head-200",
                     choices=["head-200", "batched-48", "serving", "rows", "binned",
-                             "diagnostics", "thick", "euclid", "configs"])
+                             "diagnostics", "thick", "euclid", "configs", "large"])
     ap.add_argument("--batch-fraction", type=float, default=1.0)
     ap.add_argument("--fraction", type=float, default=1.0,
                     help="head-200 workload: keep this fraction of the histories "
@@ -1094,6 +1155,9 @@ def main():
 
     if args.workload == "configs":
         run_configs(args)
+        return
+    if args.workload == "large":
+        run_large(args)
         return
     if args.workload == "batched-48":
         run_batched(args)
