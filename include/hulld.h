@@ -575,8 +575,10 @@ HD_API hd_status hd_accumulate_thick(const hd_geometry *geom, const hd_params *p
  * points are the thin paths' fixed-point world points (mm * 2^16, after the
  * integer CORDIC), voxel centres ((2 i + 1 - n) s / 2 with s rounded to
  * 2^-16 mm) and d_0 (rounded to 2^-16 mm, ties to even) enter the distance
- * test in integers, so membership never depends on floating-point rounding.
- * Thickness reaches across slices whenever d_0 exceeds the distance to the
+ * test in integers, so membership never depends on floating-point rounding
+ * (a float filter with certified error bounds settles the tests whose
+ * answer it makes certain; the integer test decides the rest).  Thickness
+ * reaches across slices whenever d_0 exceeds the distance to the
  * neighbouring slice's centres.
  *
  * Standalone accumulation: classifies the n histories (device SoA arrays)
