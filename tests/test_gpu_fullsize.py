@@ -10,7 +10,7 @@ compares every output hash and every statistic; a mismatch names the first
 slice of N or M that differs and both sums there.
 
 Workloads: the head-sized scan (200x200x32 voxels, 9e6 histories, one add
-call); the large streamed scan (400x400x128 voxels, 180 per-angle chunks of
+call), also set to Euclidean thick rays at d_0 = 2.5 mm; the large streamed scan (400x400x128 voxels, 180 per-angle chunks of
 550 000 histories, Sec. 4 online mode); the 48-scan mix in one batched run
 (CUDA graph, one persistent traversal); the same 48 scans served as
 per-angle chunks of 1e4-1e5 histories from page-locked host memory through
@@ -110,6 +110,22 @@ def test_head200_full_size_exact(hd):
         s.finalize()
         torch.cuda.synchronize()
         _check(rec, _outputs(hd, s), "head200")
+
+
+def test_euclid200_full_size_exact(hd):
+    """The head-sized scan set to Euclidean thick rays at d_0 = 2.5 mm (the
+    benchmark's euclid workload), 9e6 histories in one add call: counts,
+    hulls, thresholds and statistics against the oracle's record."""
+    rec = _golden("euclid200")
+    w = synth.make_config(2)
+    g, h = w.geometry, w.histories
+    assert _sha(h.arrays()) == rec["inputs_sha256"], "generated inputs differ from the oracle's"
+    with hd.Scan(g) as s:
+        s.set_thick_distance(rec["d0_mm"])
+        s.add([torch.from_numpy(a).cuda() for a in h.arrays()])
+        s.finalize()
+        torch.cuda.synchronize()
+        _check(rec, _outputs(hd, s), "euclid200")
 
 
 def test_head400_streamed_full_size_exact(hd):
