@@ -5,8 +5,8 @@ histories), the large streamed scan (400x400x128 voxels, 180 per-angle
 chunks of 550 000 histories), the 48 scans of the batched/served mix
 (grids 64x64x16, 128x128x32, 256x256x64; 2e5-2e7 histories each) and, on
 request, the head-sized scan with Euclidean thick rays at d_0 = 2.5 mm
-(euclid200), and writes to tests/golden/ what the GPU tests compare
-against:
+(euclid200) and with in-plane thick rays at k = 2 (thick200), and writes
+to tests/golden/ what the GPU tests compare against:
 
 * the SHA-256 of the generated inputs (the whole scan, every chunk or every
   scan), so a test first checks that it fed the GPU the same histories;
@@ -21,7 +21,8 @@ against:
 Only `oracle` and the seeded input generator are called; nothing here reads
 or runs the CUDA library.
 
-    python oracle/make_golden.py [head200] [head400] [batch48] [euclid200] [--threads N]
+    python oracle/make_golden.py [head200] [head400] [batch48] [euclid200] [thick200]
+                                 [--threads N]
 """
 from __future__ import annotations
 
@@ -117,6 +118,24 @@ def euclid200(threads: int) -> dict:
             "inputs_sha256": sha(h.arrays()), **output_record(g, res)}
 
 
+def thick200(threads: int) -> dict:
+    """The head-sized scan with A_i the in-plane Chebyshev thick set A_i(k),
+    k = 2 voxels (reading 13a of Eq. 3.2 with d_0 > 0), the hulls decided
+    from its counts (the oracle's thick accumulation runs on one thread)."""
+    del threads
+    w = synth.make_config(2)
+    g, h = w.geometry, w.histories
+    k = 2
+    res = oracle.run_thick(g, h, k)
+    s = [int(x) for x in res["stats"]]
+    res["stats"] = {"n_in": s[0], "n_miss": s[1], "n_hit": s[2], "n_none": s[3],
+                    "n_reject": s[4], "steps_miss": s[5], "steps_hit": s[6]}
+    return {"workload": "head-200x200x32, 90 angles x 100000 histories (config 2), in-plane "
+                        "thick rays, k = 2",
+            "k": k, "geometry": geometry_record(g), "histories": len(h),
+            "inputs_sha256": sha(h.arrays()), **output_record(g, res)}
+
+
 def head400(threads: int, pool) -> dict:
     g = synth.geometry_for(3)
     V = g.nx * g.ny * g.nz
@@ -172,6 +191,8 @@ def main():
                 rec = batch48(args.threads, pool)
             elif name == "euclid200":
                 rec = euclid200(args.threads)
+            elif name == "thick200":
+                rec = thick200(args.threads)
             else:
                 raise SystemExit(f"unknown workload {name}")
             rec["made_by"] = "oracle/make_golden.py (CPU oracle only)"

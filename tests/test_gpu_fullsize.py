@@ -10,7 +10,8 @@ compares every output hash and every statistic; a mismatch names the first
 slice of N or M that differs and both sums there.
 
 Workloads: the head-sized scan (200x200x32 voxels, 9e6 histories, one add
-call), also set to Euclidean thick rays at d_0 = 2.5 mm; the large streamed scan (400x400x128 voxels, 180 per-angle chunks of
+call), also set to Euclidean thick rays at d_0 = 2.5 mm and to in-plane thick
+rays at k = 2; the large streamed scan (400x400x128 voxels, 180 per-angle chunks of
 550 000 histories, Sec. 4 online mode); the 48-scan mix in one batched run
 (CUDA graph, one persistent traversal); the same 48 scans served as
 per-angle chunks of 1e4-1e5 histories from page-locked host memory through
@@ -126,6 +127,23 @@ def test_euclid200_full_size_exact(hd):
         s.finalize()
         torch.cuda.synchronize()
         _check(rec, _outputs(hd, s), "euclid200")
+
+
+def test_thick200_full_size_exact(hd):
+    """The head-sized scan set to in-plane thick rays at k = 2 (the
+    benchmark's thick workload, tiled thick traversal), 9e6 histories in one
+    add call: counts, hulls, thresholds and statistics against the oracle's
+    record."""
+    rec = _golden("thick200")
+    w = synth.make_config(2)
+    g, h = w.geometry, w.histories
+    assert _sha(h.arrays()) == rec["inputs_sha256"], "generated inputs differ from the oracle's"
+    with hd.Scan(g) as s:
+        s.set_thick(rec["k"])
+        s.add([torch.from_numpy(a).cuda() for a in h.arrays()])
+        s.finalize()
+        torch.cuda.synchronize()
+        _check(rec, _outputs(hd, s), "thick200")
 
 
 def test_head400_streamed_full_size_exact(hd):
