@@ -5,8 +5,9 @@ histories), the large streamed scan (400x400x128 voxels, 180 per-angle
 chunks of 550 000 histories), the 48 scans of the batched/served mix
 (grids 64x64x16, 128x128x32, 256x256x64; 2e5-2e7 histories each) and, on
 request, the head-sized scan with Euclidean thick rays at d_0 = 2.5 mm
-(euclid200) and with in-plane thick rays at k = 2 (thick200), and writes
-to tests/golden/ what the GPU tests compare against:
+(euclid200) and with in-plane thick rays at k = 2 (thick200), and the
+system-matrix rows of the head-sized scan inside its MSC hull (rows200),
+and writes to tests/golden/ what the GPU tests compare against:
 
 * the SHA-256 of the generated inputs (the whole scan, every chunk or every
   scan), so a test first checks that it fed the GPU the same histories;
@@ -22,7 +23,7 @@ Only `oracle` and the seeded input generator are called; nothing here reads
 or runs the CUDA library.
 
     python oracle/make_golden.py [head200] [head400] [batch48] [euclid200] [thick200]
-                                 [--threads N]
+                                 [rows200] [--threads N]
 """
 from __future__ import annotations
 
@@ -136,6 +137,30 @@ def thick200(threads: int) -> dict:
             "inputs_sha256": sha(h.arrays()), **output_record(g, res)}
 
 
+def rows200(threads: int) -> dict:
+    """The rows of the hull-restricted system matrix of every history of the
+    head-sized scan inside its MSC hull (the hull the oracle decides), in
+    path order; hashes of the row offsets and of the column indices, the
+    latter also per block of 2^20 histories so that a mismatch can be
+    located."""
+    w = synth.make_config(2)
+    g, h = w.geometry, w.histories
+    res = oracle.run(g, h, threads=threads)
+    hull = np.asarray(res["H2"], np.uint8)
+    ptr, cols = oracle.system_rows(g, h, hull, threads=threads)
+    ptr = np.asarray(ptr, np.int64)
+    cols = np.asarray(cols, np.int32)
+    block = 1 << 20
+    blocks = [sha([cols[ptr[b]:ptr[min(b + block, len(h))]]])[:16]
+              for b in range(0, len(h), block)]
+    return {"workload": "head-200x200x32, 90 angles x 100000 histories (config 2): system-matrix "
+                        "rows inside the MSC hull",
+            "geometry": geometry_record(g), "histories": len(h),
+            "inputs_sha256": sha(h.arrays()), "hull_sha256": sha([hull]),
+            "nnz": int(len(cols)), "row_ptr_sha256": sha([ptr]), "cols_sha256": sha([cols]),
+            "cols_block_histories": block, "cols_block_sha256": blocks}
+
+
 def head400(threads: int, pool) -> dict:
     g = synth.geometry_for(3)
     V = g.nx * g.ny * g.nz
@@ -193,6 +218,8 @@ def main():
                 rec = euclid200(args.threads)
             elif name == "thick200":
                 rec = thick200(args.threads)
+            elif name == "rows200":
+                rec = rows200(args.threads)
             else:
                 raise SystemExit(f"unknown workload {name}")
             rec["made_by"] = "oracle/make_golden.py (CPU oracle only)"

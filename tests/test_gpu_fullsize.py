@@ -11,7 +11,8 @@ slice of N or M that differs and both sums there.
 
 Workloads: the head-sized scan (200x200x32 voxels, 9e6 histories, one add
 call), also set to Euclidean thick rays at d_0 = 2.5 mm and to in-plane thick
-rays at k = 2; the large streamed scan (400x400x128 voxels, 180 per-angle chunks of
+rays at k = 2, and its system-matrix rows inside the MSC hull; the large
+streamed scan (400x400x128 voxels, 180 per-angle chunks of
 550 000 histories, Sec. 4 online mode); the 48-scan mix in one batched run
 (CUDA graph, one persistent traversal); the same 48 scans served as
 per-angle chunks of 1e4-1e5 histories from page-locked host memory through
@@ -144,6 +145,37 @@ def test_thick200_full_size_exact(hd):
         s.finalize()
         torch.cuda.synchronize()
         _check(rec, _outputs(hd, s), "thick200")
+
+
+def test_rows200_full_size_exact(hd):
+    """The system-matrix rows of every history of the head-sized scan inside
+    its MSC hull (the benchmark's rows workload: 8.3e8 column indices), in
+    path order, against the oracle's record; a mismatch names the first
+    block of 2^20 histories whose columns differ."""
+    rec = _golden("rows200")
+    w = synth.make_config(2)
+    g, h = w.geometry, w.histories
+    assert _sha(h.arrays()) == rec["inputs_sha256"], "generated inputs differ from the oracle's"
+    with hd.Scan(g) as s:
+        dev = [torch.from_numpy(a).cuda() for a in h.arrays()]
+        s.add(dev)
+        s.finalize()
+        hull = np.asarray(s.mask(hd.HD_MSC), np.uint8)
+        assert _sha([hull]) == rec["hull_sha256"], "rows200: MSC hull differs"
+        row_ptr, cols = s.system_rows(hd.HD_MSC, dev)
+        torch.cuda.synchronize()
+        ptr = row_ptr.cpu().numpy().astype(np.int64)
+        c = cols.cpu().numpy().astype(np.int32)
+    assert len(c) == rec["nnz"], f"rows200: {len(c)} nonzeros != oracle {rec['nnz']}"
+    assert _sha([ptr]) == rec["row_ptr_sha256"], "rows200: row lengths differ"
+    if _sha([c]) != rec["cols_sha256"]:
+        b = rec["cols_block_histories"]
+        for k, ref in enumerate(rec["cols_block_sha256"]):
+            lo = k * b
+            hi = min(lo + b, len(h))
+            if _sha([c[ptr[lo]:ptr[hi]]])[:16] != ref:
+                pytest.fail(f"rows200: columns first differ in histories {lo}..{hi - 1}")
+        pytest.fail("rows200: columns differ")
 
 
 def test_head400_streamed_full_size_exact(hd):
