@@ -5,7 +5,7 @@ histories), the large streamed scan (400x400x128 voxels, 180 per-angle
 chunks of 550 000 histories), the 48 scans of the batched/served mix
 (grids 64x64x16, 128x128x32, 256x256x64; 2e5-2e7 histories each) and, on
 request, the head-sized scan with Euclidean thick rays at d_0 = 2.5 mm
-(euclid200) and with in-plane thick rays at k = 2 (thick200), and the
+and 0.5 mm (euclid200, euclid200_d05) and with in-plane thick rays at k = 2 (thick200), and the
 system-matrix rows of the head-sized scan inside its MSC hull (rows200),
 and writes to tests/golden/ what the GPU tests compare against:
 
@@ -22,8 +22,8 @@ and writes to tests/golden/ what the GPU tests compare against:
 Only `oracle` and the seeded input generator are called; nothing here reads
 or runs the CUDA library.
 
-    python oracle/make_golden.py [head200] [head400] [batch48] [euclid200] [thick200]
-                                 [rows200] [--threads N]
+    python oracle/make_golden.py [head200] [head400] [batch48] [euclid200] [euclid200_d05]
+                                 [thick200] [rows200] [--threads N]
 """
 from __future__ import annotations
 
@@ -102,19 +102,18 @@ def head200(threads: int) -> dict:
             "inputs_sha256": sha(h.arrays()), **output_record(g, res)}
 
 
-def euclid200(threads: int) -> dict:
-    """The head-sized scan with A_i the Euclidean thick set A_i(d_0), d_0 =
-    2.5 mm (Eq. 3.2, d the distance from a voxel's centre to the closed
-    segment), the hulls decided from its counts."""
+def euclid200(threads: int, d0: float = 2.5) -> dict:
+    """The head-sized scan with A_i the Euclidean thick set A_i(d_0) (Eq.
+    3.2, d the distance from a voxel's centre to the closed segment), the
+    hulls decided from its counts."""
     w = synth.make_config(2)
     g, h = w.geometry, w.histories
-    d0 = 2.5
     res = oracle.run_euclid(g, h, d0, threads=threads)
     s = [int(x) for x in res["stats"]]
     res["stats"] = {"n_in": s[0], "n_miss": s[1], "n_hit": s[2], "n_none": s[3],
                     "n_reject": s[4], "steps_miss": s[5], "steps_hit": s[6]}
     return {"workload": "head-200x200x32, 90 angles x 100000 histories (config 2), Euclidean "
-                        "thick rays, d_0 = 2.5 mm",
+                        f"thick rays, d_0 = {d0:g} mm",
             "d0_mm": d0, "geometry": geometry_record(g), "histories": len(h),
             "inputs_sha256": sha(h.arrays()), **output_record(g, res)}
 
@@ -216,6 +215,8 @@ def main():
                 rec = batch48(args.threads, pool)
             elif name == "euclid200":
                 rec = euclid200(args.threads)
+            elif name == "euclid200_d05":
+                rec = euclid200(args.threads, 0.5)
             elif name == "thick200":
                 rec = thick200(args.threads)
             elif name == "rows200":

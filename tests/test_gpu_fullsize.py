@@ -10,7 +10,7 @@ compares every output hash and every statistic; a mismatch names the first
 slice of N or M that differs and both sums there.
 
 Workloads: the head-sized scan (200x200x32 voxels, 9e6 histories, one add
-call), also set to Euclidean thick rays at d_0 = 2.5 mm and to in-plane thick
+call), also set to Euclidean thick rays at d_0 = 2.5 and 0.5 mm and to in-plane thick
 rays at k = 2, and its system-matrix rows inside the MSC hull; the large
 streamed scan (400x400x128 voxels, 180 per-angle chunks of
 550 000 histories, Sec. 4 online mode); the 48-scan mix in one batched run
@@ -114,11 +114,12 @@ def test_head200_full_size_exact(hd):
         _check(rec, _outputs(hd, s), "head200")
 
 
-def test_euclid200_full_size_exact(hd):
+@pytest.mark.parametrize("name", ["euclid200", "euclid200_d05"])
+def test_euclid200_full_size_exact(hd, name):
     """The head-sized scan set to Euclidean thick rays at d_0 = 2.5 mm (the
-    benchmark's euclid workload), 9e6 histories in one add call: counts,
-    hulls, thresholds and statistics against the oracle's record."""
-    rec = _golden("euclid200")
+    benchmark's euclid workload) and 0.5 mm, 9e6 histories in one add call:
+    counts, hulls, thresholds and statistics against the oracle's record."""
+    rec = _golden(name)
     w = synth.make_config(2)
     g, h = w.geometry, w.histories
     assert _sha(h.arrays()) == rec["inputs_sha256"], "generated inputs differ from the oracle's"
@@ -127,7 +128,7 @@ def test_euclid200_full_size_exact(hd):
         s.add([torch.from_numpy(a).cuda() for a in h.arrays()])
         s.finalize()
         torch.cuda.synchronize()
-        _check(rec, _outputs(hd, s), "euclid200")
+        _check(rec, _outputs(hd, s), name)
 
 
 def test_thick200_full_size_exact(hd):
